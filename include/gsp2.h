@@ -1,0 +1,208 @@
+/*
+ * gsp2.h -- C ABI of the GB300 graph-partitioned SP2 (G-SP2) density-matrix library.
+ *
+ * The library computes the density matrix P of a sparse symmetric Hamiltonian H by
+ * the data-parallel G-SP2 method (Ghale et al., "Task-based Parallel Computation of
+ * the Density Matrix in Quantum-based Molecular Dynamics using Graph Partitioning"):
+ *
+ *   1. a graph G_tau over the orbitals is partitioned into parts; part k owns its
+ *      core vertices and sees as halo every vertex adjacent to a core (Section 2.2);
+ *   2. each part's dense core+halo submatrix H[S_k, S_k] is gathered and mapped to
+ *      X0 = (eps_max I - H)/(eps_max - eps_min) with Gershgorin bounds (Eq. 1);
+ *   3. all parts are purified together, X <- X^2 or X <- 2X - X^2 (Eq. 2), with one
+ *      branch per step chosen from the global sum of core traces (Section 2.1);
+ *   4. core columns are scattered back into P (Section 1.1, Fig. 1).
+ *
+ * Everything after gsp2_bind_workspace runs on the GPU in hand-written sm_103a
+ * kernels; there is no CPU fallback.  The library never allocates device memory:
+ * the caller passes one device workspace of the size gsp2_workspace_bytes reports.
+ *
+ * Conventions for every call:
+ *  - "host" pointers are ordinary CPU memory, read during the call and not kept;
+ *  - "device" pointers are CUDA global memory on the current device, owned by the
+ *    caller, which must keep them alive until the work queued on the stream ends;
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream);
+ *  - a call returns GSP2_OK or an error code; on error gsp2_last_error(h) gives a
+ *    one-line reason, nothing is queued, and the handle stays usable;
+ *  - a handle is not thread-safe: one host thread at a time per handle.
+ */
+#ifndef GSP2_H
+#define GSP2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gsp2_plan* gsp2_handle;
+
+typedef enum {
+  GSP2_OK = 0,
+  GSP2_E_ARG = 1,            /* invalid argument: bad CSR, part map, size, pointer */
+  GSP2_E_OOM = 2,            /* host allocation failed */
+  GSP2_E_STATE = 3,          /* call out of order (no workspace, no forward pass) */
+  GSP2_E_CUDA = 4,           /* a CUDA runtime call failed (see gsp2_last_error) */
+  GSP2_E_NOT_CONVERGED = 5,  /* device: max_steps reached before the stopping test */
+  GSP2_E_TRACE = 6,          /* device: replayed sequence ended with |Tr P - Nocc| > trace_tol */
+  GSP2_E_NONFINITE = 7,      /* device: NaN/Inf met in H, the bounds or a trace */
+  GSP2_E_WORKSPACE = 8       /* workspace too small or misaligned (256 bytes) */
+} gsp2_status;
+
+/* Arithmetic of the purification steps.  Traces, bounds and branch decisions are
+ * always FP64.  The low-precision modes keep an FP32 master copy of every X_k, run
+ * the squarings on tcgen05 tensor cores with FP32 accumulation, and finish with
+ * `fp64_tail_steps` purification steps in FP64. */
+typedef enum {
+  GSP2_PREC_FP64 = 0,
+  GSP2_PREC_FP32 = 1,   /* FP32 CUDA-core squarings (no tensor cores) */
+  GSP2_PREC_TF32 = 2,
+  GSP2_PREC_BF16 = 3,
+  GSP2_PREC_BF16X3 = 4  /* split operands hi+lo in BF16, three products, FP32 accumulate */
+} gsp2_precision;
+
+typedef enum {
+  GSP2_MODE_RECORD = 0, /* choose each branch on the device from the global trace */
+  GSP2_MODE_REPLAY = 1  /* apply a given branch sequence (Section 2.1, sequence reuse) */
+} gsp2_mode;
+
+typedef struct {
+  int32_t max_steps;       /* cap on purification steps (default 45), 1..1024 */
+  double idem_tol;         /* stopping gate on e = Tr X - Tr X^2 (default 1e-3) */
+  double trace_tol;        /* replay check on |Tr P - Nocc| (default 1e-2) */
+  int32_t precision;       /* gsp2_precision (default FP64) */
+  int32_t fp64_tail_steps; /* low-precision modes: FP64 steps at the end (default 2) */
+  int32_t ckpt_every;      /* adjoint: keep every k-th iterate (default 8); 0 = no adjoint */
+  int32_t use_graph;       /* 1 (default): capture the whole step sequence in a CUDA graph */
+  int32_t time_steps;      /* 1: record CUDA events around every purification-step launch
+                              (read with gsp2_step_times); default 0 */
+  int32_t reserved[7];
+} gsp2_options;
+
+/* Per-call report, read back by gsp2_sync_status. */
+typedef struct {
+  int32_t status;       /* gsp2_status detected on the device for the last density call */
+  int32_t steps;        /* purification steps applied */
+  int32_t stopped;      /* 1 if the stopping test ended the loop */
+  int32_t fp64_steps;   /* of which FP64 steps (low-precision modes) */
+  double eps_min;       /* Gershgorin bounds (Section 2.1) */
+  double eps_max;
+  double trace;         /* Tr P = sum of core diagonal entries of the final iterates */
+  double idem;          /* last idempotency error e computed */
+} gsp2_report;
+
+/* Plan sizes, for accounting (flops from the real part sizes). */
+typedef struct {
+  int64_t n;            /* orbitals */
+  int64_t nocc;
+  int32_t nparts;
+  int32_t max_s;        /* largest core+halo size */
+  int64_t sum_s;        /* sum_k s_k */
+  double sum_s2;        /* sum_k s_k^2  (elements of one arena) */
+  double sum_s3;        /* sum_k s_k^3  (Eq. 5 cost) */
+  int64_t nnz_h;
+  int64_t nnz_p;        /* sum_k c_k s_k */
+  int64_t arena_elems;  /* sum_k ld_k^2 (padded) */
+  int64_t ntiles;       /* upper-triangular square tiles per step */
+  int32_t tile;         /* square tile edge */
+  int32_t ld_pad;       /* padding multiple of ld_k */
+} gsp2_plan_info;
+
+/* Fill `opt` with the defaults listed above. */
+void gsp2_default_options(gsp2_options* opt);
+
+/*
+ * Build a plan from the sparsity pattern of H, the partition and the graph G_tau
+ * (Section 2.2).  Host-only: validates, builds halos, the per-part vertex lists
+ * S_k (cores ascending, then halo ascending), the padded dense layout, the tile work
+ * list and the pattern of P.  Allocates host memory only.
+ *
+ *  n                 orbitals, 1..2^31-1
+ *  rowptr, colind    host CSR of H (full symmetric pattern, both triangles), int64
+ *                    rowptr[n+1], int32 colind[nnz], columns strictly ascending per
+ *                    row, every diagonal entry present, pattern symmetric
+ *  nocc              occupied orbitals (N_el = 2 nocc), 0..n
+ *  part              host int32[n], part id of each orbital, in [0, nparts)
+ *  nparts            number of parts, >= 1, no part may be empty
+ *  g_rowptr/g_colind host CSR of G_tau (same format; self loops ignored; must be
+ *                    symmetric); both NULL = use the pattern of H
+ *  opt               options (NULL = defaults)
+ *  out               receives the handle (NULL on error)
+ * Errors: GSP2_E_ARG, GSP2_E_OOM; the reason is gsp2_last_error(NULL).
+ */
+gsp2_status gsp2_create(int64_t n, const int64_t* rowptr, const int32_t* colind, int64_t nocc,
+                        const int32_t* part, int32_t nparts, const int64_t* g_rowptr,
+                        const int32_t* g_colind, const gsp2_options* opt, gsp2_handle* out);
+
+/* Device workspace bytes the plan needs (arenas, tables, checkpoints). */
+gsp2_status gsp2_workspace_bytes(gsp2_handle h, size_t* bytes);
+
+/* Attach a caller-owned device workspace of at least gsp2_workspace_bytes bytes,
+ * 256-byte aligned, on the current device, and upload the plan tables into it
+ * (queued on `stream`).  May be called again to move the plan to another buffer. */
+gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_workspace, size_t bytes, void* stream);
+
+/* Pattern of P in core-column CSC form (host output): column g holds the rows
+ * S_{part(g)} in ascending order.  colptr: int64[n+1]; rowind: int32[nnz_p].
+ * Either array may be NULL to query only nnz_p. */
+gsp2_status gsp2_p_pattern(gsp2_handle h, int64_t* colptr, int32_t* rowind, int64_t* nnz_p);
+
+/* Sizes of the plan; s and c (host int32[nparts], may be NULL) receive s_k and c_k. */
+gsp2_status gsp2_plan_query(gsp2_handle h, gsp2_plan_info* info, int32_t* s, int32_t* c);
+
+/*
+ * Density matrix P(H) (Sections 1.1, 2.1, 2.2; Eqs. 1-3).  Asynchronous on `stream`.
+ *
+ *  d_hvals  device double[nnz_h]: values of H on the pattern given to gsp2_create
+ *           (symmetric values expected; a new SCF/MD H reuses the plan, Section 1.1)
+ *  d_pvals  device double[nnz_p]: output, P on the pattern of gsp2_p_pattern
+ *  d_alpha  device int8[max_steps] or NULL.  RECORD: receives the branch sequence
+ *           (+1: 2X - X^2, -1: X^2) of the applied steps, zeros after the last.
+ *           REPLAY: the sequence to apply; its length is `nsteps`.
+ *  mode     gsp2_mode
+ *  nsteps   REPLAY: number of steps to apply (1..max_steps); RECORD: ignored
+ * Host-visible errors are argument/state errors only; numerical outcomes
+ * (convergence, trace check, non-finite values) are read with gsp2_sync_status.
+ */
+gsp2_status gsp2_density(gsp2_handle h, const double* d_hvals, double* d_pvals, int8_t* d_alpha,
+                         int32_t mode, int32_t nsteps, void* stream);
+
+/* Wait for the last density call and return its device status (GSP2_OK or one of
+ * GSP2_E_NOT_CONVERGED / GSP2_E_TRACE / GSP2_E_NONFINITE); `r` may be NULL. */
+gsp2_status gsp2_sync_status(gsp2_handle h, gsp2_report* r);
+
+/* Per-step history of the last density call, copied to host after a sync:
+ * traces[0..steps] (core traces T_i of X_i), idem[0..steps-1] (e_i), alpha[0..steps-1].
+ * `cap` bounds each array; any pointer may be NULL. */
+gsp2_status gsp2_history(gsp2_handle h, double* traces, double* idem, int8_t* alpha, int32_t cap);
+
+/* Device time of each purification-step launch of the last density call, in
+ * milliseconds, ms[i-1] for step i (1..max_steps); needs time_steps = 1.  Steps after
+ * the stopping test return at once and show a few microseconds.  Waits for the call. */
+gsp2_status gsp2_step_times(gsp2_handle h, float* ms, int32_t cap);
+
+/*
+ * Adjoint of P(H): given Pbar = dL/dP on the pattern of P, write Hbar = dL/dH on the
+ * pattern of H, through the branch sequence of the last density call (its bounds
+ * held fixed).  X^2 steps map Xbar -> Xbar X + X Xbar, 2X - X^2 steps map
+ * Xbar -> 2 Xbar - Xbar X - X Xbar; dX0/dH = -1/(eps_max - eps_min) (Eq. 1).
+ * Iterates are recomputed from checkpoints kept every `ckpt_every` steps.
+ *  d_pbar  device double[nnz_p]
+ *  d_hbar  device double[nnz_h], overwritten; symmetric for a symmetric problem
+ * Requires ckpt_every > 0 at create and a completed density call (GSP2_E_STATE).
+ */
+gsp2_status gsp2_backward(gsp2_handle h, const double* d_pbar, double* d_hbar, void* stream);
+
+/* Last error message of the handle; with h == NULL, the reason the last failed
+ * gsp2_create on the calling thread gave. */
+const char* gsp2_last_error(gsp2_handle h);
+
+/* Release the plan (host memory and CUDA graphs; the workspace stays the caller's). */
+void gsp2_destroy(gsp2_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GSP2_H */

@@ -1,0 +1,535 @@
+// C ABI of the G-SP2 library: plan construction on the host (validation, halos,
+// padded layout, work lists, pattern of P), workspace binding, and the queued step
+// sequence of a density call, captured once into a CUDA graph and replayed.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/gsp2.h"
+#include "gsp2_internal.cuh"
+#include "gsp2_kernels.h"
+
+using namespace gsp2;
+
+namespace {
+
+constexpr int BOUNDS_BLOCKS = 608;  // 152 SMs x 4
+
+struct WsLayout {
+  size_t parts, S, perm, tiles, gblocks, sblocks, pcolptr, rowptr, colind, slots, state, alpha, traces, idem;
+  size_t arena0, arena1;
+  size_t total;
+};
+
+struct GraphKey {
+  const void* h;
+  void* p;
+  void* a;
+  int mode, nsteps;
+  bool operator==(const GraphKey& o) const {
+    return h == o.h && p == o.p && a == o.a && mode == o.mode && nsteps == o.nsteps;
+  }
+};
+
+}  // namespace
+
+struct gsp2_plan {
+  int64_t n = 0, nocc = 0, nnz_h = 0;
+  int32_t nparts = 0;
+  gsp2_options opt{};
+  std::vector<int64_t> rowptr;
+  std::vector<int32_t> colind;
+  std::vector<PartDesc> parts;
+  std::vector<int32_t> S, perm;
+  std::vector<Tile> tiles;
+  std::vector<ColBlock> gblocks, sblocks;
+  std::vector<int64_t> pcolptr;
+  std::vector<int32_t> prowind;
+  int32_t nslots = 0, max_s = 0;
+  int64_t arena_elems = 0, sum_s = 0;
+  double sum_s2 = 0, sum_s3 = 0;
+  WsLayout L{};
+  char* ws = nullptr;
+  size_t ws_size = 0;
+  int device = -1;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  GraphKey key{};
+  std::vector<cudaEvent_t> ev;  // 2 per step when time_steps is set
+  bool have_forward = false;
+  std::string err;
+};
+
+// reason of the last failed gsp2_create on this thread (read with gsp2_last_error(NULL))
+static thread_local std::string t_create_err = "invalid handle";
+
+static gsp2_status fail(gsp2_plan* h, gsp2_status s, const std::string& msg) {
+  if (h) h->err = msg;
+  return s;
+}
+
+static gsp2_status cuda_fail(gsp2_plan* h, cudaError_t e, const char* where) {
+  return fail(h, GSP2_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CU(h, call)                                     \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+  } while (0)
+
+static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+static std::string check_csr(int64_t n, const int64_t* rowptr, const int32_t* colind, bool need_diag,
+                             const char* what) {
+  if (!rowptr) return std::string(what) + ": rowptr is NULL";
+  if (rowptr[0] != 0) return std::string(what) + ": rowptr[0] != 0";
+  for (int64_t i = 0; i < n; ++i) {
+    if (rowptr[i + 1] < rowptr[i]) return std::string(what) + ": rowptr not monotone at row " + std::to_string(i);
+  }
+  if (rowptr[n] > 0 && !colind) return std::string(what) + ": colind is NULL";
+  for (int64_t i = 0; i < n; ++i) {
+    bool diag = false;
+    for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+      const int32_t c = colind[p];
+      if (c < 0 || c >= n) return std::string(what) + ": column index out of range in row " + std::to_string(i);
+      if (p > rowptr[i] && colind[p - 1] >= c)
+        return std::string(what) + ": columns not strictly ascending in row " + std::to_string(i);
+      if (c == i) diag = true;
+    }
+    if (need_diag && !diag) return std::string(what) + ": diagonal entry missing in row " + std::to_string(i);
+  }
+  return "";
+}
+
+static bool has_entry(const int64_t* rowptr, const int32_t* colind, int64_t i, int32_t j) {
+  const int32_t* b = colind + rowptr[i];
+  const int32_t* e = colind + rowptr[i + 1];
+  const int32_t* q = std::lower_bound(b, e, j);
+  return q != e && *q == j;
+}
+
+extern "C" void gsp2_default_options(gsp2_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->max_steps = 45;
+  o->idem_tol = 1e-3;
+  o->trace_tol = 1e-2;
+  o->precision = GSP2_PREC_FP64;
+  o->fp64_tail_steps = 2;
+  o->ckpt_every = 8;
+  o->use_graph = 1;
+}
+
+extern "C" const char* gsp2_last_error(gsp2_handle h) { return h ? h->err.c_str() : t_create_err.c_str(); }
+
+static void build_layout(gsp2_plan* h) {
+  WsLayout& L = h->L;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o = align256(o + bytes);
+    return at;
+  };
+  L.parts = take(h->parts.size() * sizeof(PartDesc));
+  L.S = take(h->S.size() * sizeof(int32_t));
+  L.perm = take(h->perm.size() * sizeof(int32_t));
+  L.tiles = take(h->tiles.size() * sizeof(Tile));
+  L.gblocks = take(h->gblocks.size() * sizeof(ColBlock));
+  L.sblocks = take(h->sblocks.size() * sizeof(ColBlock));
+  L.pcolptr = take(h->pcolptr.size() * sizeof(int64_t));
+  L.rowptr = take(h->rowptr.size() * sizeof(int64_t));
+  L.colind = take(h->colind.size() * sizeof(int32_t));
+  const size_t nsl = std::max<size_t>({(size_t)h->nslots, h->gblocks.size(), (size_t)BOUNDS_BLOCKS, 1});
+  L.slots = take(nsl * sizeof(double2));
+  L.state = take(sizeof(DevState));
+  L.alpha = take((size_t)h->opt.max_steps + 2);
+  L.traces = take(((size_t)h->opt.max_steps + 2) * sizeof(double));
+  L.idem = take(((size_t)h->opt.max_steps + 2) * sizeof(double));
+  L.arena0 = take((size_t)h->arena_elems * sizeof(double));
+  L.arena1 = take((size_t)h->arena_elems * sizeof(double));
+  L.total = o;
+}
+
+extern "C" gsp2_status gsp2_create(int64_t n, const int64_t* rowptr, const int32_t* colind, int64_t nocc,
+                                   const int32_t* part, int32_t nparts, const int64_t* g_rowptr,
+                                   const int32_t* g_colind, const gsp2_options* opt, gsp2_handle* out) {
+  if (!out) return GSP2_E_ARG;
+  *out = nullptr;
+  gsp2_plan* h = new (std::nothrow) gsp2_plan();
+  if (!h) return GSP2_E_OOM;
+  auto bail = [&](gsp2_status s, const std::string& m) {
+    t_create_err = m;
+    delete h;
+    return s;
+  };
+  try {
+    if (opt) h->opt = *opt; else gsp2_default_options(&h->opt);
+    const gsp2_options& o = h->opt;
+    if (n < 1 || n > INT32_MAX) return bail(GSP2_E_ARG, "n out of range");
+    if (nocc < 0 || nocc > n) return bail(GSP2_E_ARG, "nocc must be in [0, n]");
+    if (nparts < 1 || nparts > n) return bail(GSP2_E_ARG, "nparts must be in [1, n]");
+    if (!part) return bail(GSP2_E_ARG, "part is NULL");
+    if (o.max_steps < 1 || o.max_steps > 1024) return bail(GSP2_E_ARG, "max_steps must be in [1, 1024]");
+    if (!(o.idem_tol >= 0.0) || !(o.trace_tol >= 0.0)) return bail(GSP2_E_ARG, "tolerances must be >= 0");
+    if (o.precision != GSP2_PREC_FP64) return bail(GSP2_E_ARG, "precision not supported by this build");
+    if (o.ckpt_every < 0) return bail(GSP2_E_ARG, "ckpt_every must be >= 0");
+    if ((g_rowptr == nullptr) != (g_colind == nullptr)) return bail(GSP2_E_ARG, "graph: give both arrays or neither");
+    std::string m = check_csr(n, rowptr, colind, true, "H");
+    if (!m.empty()) return bail(GSP2_E_ARG, m);
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p)
+        if (!has_entry(rowptr, colind, colind[p], (int32_t)i))
+          return bail(GSP2_E_ARG, "H pattern is not symmetric at (" + std::to_string(i) + ", " +
+                                      std::to_string(colind[p]) + ")");
+    const int64_t* grp = g_rowptr ? g_rowptr : rowptr;
+    const int32_t* gci = g_rowptr ? g_colind : colind;
+    if (g_rowptr) {
+      m = check_csr(n, g_rowptr, g_colind, false, "graph");
+      if (!m.empty()) return bail(GSP2_E_ARG, m);
+    }
+    h->n = n;
+    h->nocc = nocc;
+    h->nparts = nparts;
+    h->nnz_h = rowptr[n];
+    h->rowptr.assign(rowptr, rowptr + n + 1);
+    h->colind.assign(colind, colind + rowptr[n]);
+
+    // cores per part (ascending by construction)
+    std::vector<std::vector<int32_t>> core(nparts), halo(nparts);
+    for (int64_t i = 0; i < n; ++i) {
+      const int32_t k = part[i];
+      if (k < 0 || k >= nparts) return bail(GSP2_E_ARG, "part id out of range at vertex " + std::to_string(i));
+      core[k].push_back((int32_t)i);
+    }
+    // halo: vertices outside part k adjacent (out-edges of G_tau) to a core of k
+    std::vector<int32_t> stamp(n, -1);
+    for (int32_t k = 0; k < nparts; ++k) {
+      if (core[k].empty()) return bail(GSP2_E_ARG, "part " + std::to_string(k) + " is empty");
+      for (int32_t u : core[k])
+        for (int64_t p = grp[u]; p < grp[u + 1]; ++p) {
+          const int32_t v = gci[p];
+          if (part[v] != k && stamp[v] != k) {
+            stamp[v] = k;
+            halo[k].push_back(v);
+          }
+        }
+      std::sort(halo[k].begin(), halo[k].end());
+    }
+    // layout
+    h->parts.resize(nparts);
+    int64_t off = 0, soff = 0;
+    for (int32_t k = 0; k < nparts; ++k) {
+      PartDesc& d = h->parts[k];
+      d.c = (int32_t)core[k].size();
+      d.s = d.c + (int32_t)halo[k].size();
+      d.ld = (d.s + LD_PAD - 1) / LD_PAD * LD_PAD;
+      d.nt = (d.s + SQ_TILE - 1) / SQ_TILE;
+      d.off = off;
+      d.soff = soff;
+      off += (int64_t)d.ld * d.ld;
+      soff += d.s;
+      h->max_s = std::max(h->max_s, d.s);
+      h->sum_s2 += (double)d.s * d.s;
+      h->sum_s3 += (double)d.s * d.s * d.s;
+      h->S.insert(h->S.end(), core[k].begin(), core[k].end());
+      h->S.insert(h->S.end(), halo[k].begin(), halo[k].end());
+    }
+    h->arena_elems = off;
+    h->sum_s = soff;
+    // scatter permutation and the pattern of P (rows of column g = sorted S_part(g))
+    h->perm.resize(soff);
+    std::vector<int64_t> colstart(nparts);
+    for (int32_t k = 0; k < nparts; ++k) {
+      const PartDesc& d = h->parts[k];
+      int32_t* pk = h->perm.data() + d.soff;
+      std::iota(pk, pk + d.s, 0);
+      const int32_t* Sk = h->S.data() + d.soff;
+      std::sort(pk, pk + d.s, [&](int32_t a, int32_t b) { return Sk[a] < Sk[b]; });
+    }
+    h->pcolptr.assign(n + 1, 0);
+    for (int64_t g = 0; g < n; ++g) h->pcolptr[g + 1] = h->pcolptr[g] + h->parts[part[g]].s;
+    h->prowind.resize(h->pcolptr[n]);
+    for (int64_t g = 0; g < n; ++g) {
+      const PartDesc& d = h->parts[part[g]];
+      const int32_t* Sk = h->S.data() + d.soff;
+      const int32_t* pk = h->perm.data() + d.soff;
+      int32_t* r = h->prowind.data() + h->pcolptr[g];
+      for (int32_t t = 0; t < d.s; ++t) r[t] = Sk[pk[t]];
+    }
+    // work lists: parts in descending size, so the longest tiles start first
+    std::vector<int32_t> order(nparts);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t a, int32_t b) { return h->parts[a].s > h->parts[b].s; });
+    int32_t slot = 0;
+    for (int32_t k : order) {
+      const PartDesc& d = h->parts[k];
+      for (int32_t ti = 0; ti < d.nt; ++ti)
+        for (int32_t tj = ti; tj < d.nt; ++tj) h->tiles.push_back(Tile{k, ti, tj, ti == tj ? slot++ : -1});
+      for (int32_t j = 0; j < d.nt * SQ_TILE; j += COLS_PER_BLOCK) h->gblocks.push_back(ColBlock{k, j});
+      for (int32_t j = 0; j < d.c; j += COLS_PER_BLOCK) h->sblocks.push_back(ColBlock{k, j});
+    }
+    h->nslots = slot;
+    if (h->tiles.size() > (size_t)INT32_MAX || h->gblocks.size() > (size_t)INT32_MAX)
+      return bail(GSP2_E_ARG, "problem too large for one launch");
+    build_layout(h);
+  } catch (const std::bad_alloc&) {
+    t_create_err = "host allocation failed";
+    delete h;
+    return GSP2_E_OOM;
+  }
+  *out = h;
+  return GSP2_OK;
+}
+
+static bool usable(gsp2_plan* h) { return h && !h->parts.empty(); }
+
+extern "C" gsp2_status gsp2_workspace_bytes(gsp2_handle h, size_t* bytes) {
+  if (!usable(h) || !bytes) return fail(h, GSP2_E_ARG, "invalid handle or NULL output");
+  *bytes = h->L.total;
+  return GSP2_OK;
+}
+
+extern "C" gsp2_status gsp2_plan_query(gsp2_handle h, gsp2_plan_info* info, int32_t* s, int32_t* c) {
+  if (!usable(h)) return fail(h, GSP2_E_ARG, "invalid handle");
+  if (info) {
+    info->n = h->n;
+    info->nocc = h->nocc;
+    info->nparts = h->nparts;
+    info->max_s = h->max_s;
+    info->sum_s = h->sum_s;
+    info->sum_s2 = h->sum_s2;
+    info->sum_s3 = h->sum_s3;
+    info->nnz_h = h->nnz_h;
+    info->nnz_p = h->pcolptr[h->n];
+    info->arena_elems = h->arena_elems;
+    info->ntiles = (int64_t)h->tiles.size();
+    info->tile = SQ_TILE;
+    info->ld_pad = LD_PAD;
+  }
+  for (int32_t k = 0; k < h->nparts; ++k) {
+    if (s) s[k] = h->parts[k].s;
+    if (c) c[k] = h->parts[k].c;
+  }
+  return GSP2_OK;
+}
+
+extern "C" gsp2_status gsp2_p_pattern(gsp2_handle h, int64_t* colptr, int32_t* rowind, int64_t* nnz_p) {
+  if (!usable(h)) return fail(h, GSP2_E_ARG, "invalid handle");
+  if (nnz_p) *nnz_p = h->pcolptr[h->n];
+  if (colptr) std::memcpy(colptr, h->pcolptr.data(), h->pcolptr.size() * sizeof(int64_t));
+  if (rowind) std::memcpy(rowind, h->prowind.data(), h->prowind.size() * sizeof(int32_t));
+  return GSP2_OK;
+}
+
+static void drop_graph(gsp2_plan* h) {
+  if (h->exec) cudaGraphExecDestroy(h->exec);
+  h->exec = nullptr;
+  h->key = GraphKey{};
+}
+
+extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t bytes, void* stream) {
+  if (!usable(h)) return fail(h, GSP2_E_ARG, "invalid handle");
+  if (!d_ws || ((uintptr_t)d_ws & 255)) return fail(h, GSP2_E_WORKSPACE, "workspace NULL or not 256-byte aligned");
+  if (bytes < h->L.total) return fail(h, GSP2_E_WORKSPACE, "workspace smaller than gsp2_workspace_bytes");
+  cudaPointerAttributes at{};
+  CU(h, cudaPointerGetAttributes(&at, d_ws));
+  if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+    return fail(h, GSP2_E_WORKSPACE, "workspace is not device memory");
+  int dev = 0;
+  CU(h, cudaGetDevice(&dev));
+  cudaStream_t s = (cudaStream_t)stream;
+  drop_graph(h);
+  h->ws = (char*)d_ws;
+  h->ws_size = bytes;
+  h->device = dev;
+  h->have_forward = false;
+  if (!h->cap_stream) CU(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  if (h->opt.time_steps && h->ev.empty()) {
+    h->ev.resize(2 * (size_t)h->opt.max_steps);
+    for (auto& e : h->ev) CU(h, cudaEventCreate(&e));
+  }
+  const WsLayout& L = h->L;
+  auto up = [&](size_t off, const void* src, size_t n) -> cudaError_t {
+    if (n == 0) return cudaSuccess;
+    return cudaMemcpyAsync(h->ws + off, src, n, cudaMemcpyHostToDevice, s);
+  };
+  CU(h, up(L.parts, h->parts.data(), h->parts.size() * sizeof(PartDesc)));
+  CU(h, up(L.S, h->S.data(), h->S.size() * sizeof(int32_t)));
+  CU(h, up(L.perm, h->perm.data(), h->perm.size() * sizeof(int32_t)));
+  CU(h, up(L.tiles, h->tiles.data(), h->tiles.size() * sizeof(Tile)));
+  CU(h, up(L.gblocks, h->gblocks.data(), h->gblocks.size() * sizeof(ColBlock)));
+  CU(h, up(L.sblocks, h->sblocks.data(), h->sblocks.size() * sizeof(ColBlock)));
+  CU(h, up(L.pcolptr, h->pcolptr.data(), h->pcolptr.size() * sizeof(int64_t)));
+  CU(h, up(L.rowptr, h->rowptr.data(), h->rowptr.size() * sizeof(int64_t)));
+  CU(h, up(L.colind, h->colind.data(), h->colind.size() * sizeof(int32_t)));
+  CU(h, cudaMemsetAsync(h->ws + L.state, 0, sizeof(DevState), s));
+  CU(h, cudaMemsetAsync(h->ws + L.alpha, 0, (size_t)h->opt.max_steps + 2, s));
+  // the uploads read pageable host vectors; finish them before the call returns
+  CU(h, cudaStreamSynchronize(s));
+  return GSP2_OK;
+}
+
+// Queue the whole forward pass on `s`.
+static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, int8_t* alpha_user, int mode,
+                                   int nsteps, cudaStream_t s) {
+  const WsLayout& L = h->L;
+  char* w = h->ws;
+  auto parts = (const PartDesc*)(w + L.parts);
+  auto Sall = (const int32_t*)(w + L.S);
+  auto perm = (const int32_t*)(w + L.perm);
+  auto tiles = (const Tile*)(w + L.tiles);
+  auto gbl = (const ColBlock*)(w + L.gblocks);
+  auto sbl = (const ColBlock*)(w + L.sblocks);
+  auto pcol = (const int64_t*)(w + L.pcolptr);
+  auto rp = (const int64_t*)(w + L.rowptr);
+  auto ci = (const int32_t*)(w + L.colind);
+  auto slots = (double2*)(w + L.slots);
+  auto st = (DevState*)(w + L.state);
+  auto alpha = (int8_t*)(w + L.alpha);
+  double* a0 = (double*)(w + L.arena0);
+  double* a1 = (double*)(w + L.arena1);
+  StepCtl ctl{st, alpha, (double*)(w + L.traces), (double*)(w + L.idem), h->nocc, h->opt.idem_tol,
+              h->opt.trace_tol, mode, mode == MODE_REPLAY ? nsteps : h->opt.max_steps};
+  CU(h, launch_reset(st, alpha, mode == MODE_REPLAY ? alpha_user : nullptr, nsteps, h->opt.max_steps + 2, s));
+  CU(h, launch_bounds(h->n, rp, ci, hv, slots, BOUNDS_BLOCKS, st, s));
+  CU(h, launch_gather(parts, gbl, (int)h->gblocks.size(), Sall, rp, ci, hv, a0, (double*)slots, ctl, s));
+  for (int i = 1; i <= ctl.last_step; ++i) {
+    const double* xin = (i & 1) ? a0 : a1;
+    double* xout = (i & 1) ? a1 : a0;
+    if (!h->ev.empty()) CU(h, cudaEventRecordWithFlags(h->ev[2 * (i - 1)], s, cudaEventRecordExternal));
+    CU(h, launch_square_fp64(parts, tiles, (int)h->tiles.size(), xin, xout, slots, h->nslots, ctl, i, s));
+    if (!h->ev.empty()) CU(h, cudaEventRecordWithFlags(h->ev[2 * (i - 1) + 1], s, cudaEventRecordExternal));
+  }
+  CU(h, launch_scatter(parts, sbl, (int)h->sblocks.size(), Sall, perm, pcol, a0, a1, pv, st, s));
+  if (mode == MODE_RECORD && alpha_user)
+    CU(h, cudaMemcpyAsync(alpha_user, alpha + 1, (size_t)h->opt.max_steps, cudaMemcpyDeviceToDevice, s));
+  return GSP2_OK;
+}
+
+extern "C" gsp2_status gsp2_density(gsp2_handle h, const double* d_hvals, double* d_pvals, int8_t* d_alpha,
+                                    int32_t mode, int32_t nsteps, void* stream) {
+  if (!usable(h)) return fail(h, GSP2_E_ARG, "invalid handle");
+  if (!h->ws) return fail(h, GSP2_E_STATE, "no workspace bound");
+  if (!d_hvals || !d_pvals) return fail(h, GSP2_E_ARG, "NULL H or P buffer");
+  if (mode != MODE_RECORD && mode != MODE_REPLAY) return fail(h, GSP2_E_ARG, "mode must be RECORD or REPLAY");
+  if (mode == MODE_REPLAY && (!d_alpha || nsteps < 1 || nsteps > h->opt.max_steps))
+    return fail(h, GSP2_E_ARG, "REPLAY needs d_alpha and 1 <= nsteps <= max_steps");
+  if (mode == MODE_RECORD) nsteps = 0;
+  int dev = 0;
+  CU(h, cudaGetDevice(&dev));
+  if (dev != h->device) return fail(h, GSP2_E_STATE, "current device differs from the workspace's device");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (h->opt.use_graph) {
+    GraphKey k{d_hvals, d_pvals, d_alpha, mode, nsteps};
+    if (!h->exec || !(k == h->key)) {
+      drop_graph(h);
+      cudaGraph_t g = nullptr;
+      CU(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+      gsp2_status st = enqueue_forward(h, d_hvals, d_pvals, d_alpha, mode, nsteps, h->cap_stream);
+      cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+      if (st != GSP2_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+      }
+      if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+      e = cudaGraphInstantiate(&h->exec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        h->exec = nullptr;
+        return cuda_fail(h, e, "cudaGraphInstantiate");
+      }
+      h->key = k;
+    }
+    CU(h, cudaGraphLaunch(h->exec, s));
+  } else {
+    gsp2_status st = enqueue_forward(h, d_hvals, d_pvals, d_alpha, mode, nsteps, s);
+    if (st != GSP2_OK) return st;
+  }
+  h->have_forward = true;
+  return GSP2_OK;
+}
+
+extern "C" gsp2_status gsp2_sync_status(gsp2_handle h, gsp2_report* r) {
+  if (!usable(h)) return fail(h, GSP2_E_ARG, "invalid handle");
+  if (!h->ws || !h->have_forward) return fail(h, GSP2_E_STATE, "no density call to report on");
+  CU(h, cudaDeviceSynchronize());
+  DevState st{};
+  CU(h, cudaMemcpy(&st, h->ws + h->L.state, sizeof(DevState), cudaMemcpyDeviceToHost));
+  double tr = 0.0, e = 0.0;
+  CU(h, cudaMemcpy(&tr, h->ws + h->L.traces + sizeof(double) * st.steps, sizeof(double), cudaMemcpyDeviceToHost));
+  if (st.steps > 0)
+    CU(h, cudaMemcpy(&e, h->ws + h->L.idem + sizeof(double) * (st.steps - 1), sizeof(double),
+                     cudaMemcpyDeviceToHost));
+  if (r) {
+    r->status = st.status;
+    r->steps = st.steps;
+    r->stopped = st.stopped;
+    r->fp64_steps = st.fp64_steps;
+    r->eps_min = st.eps_min;
+    r->eps_max = st.eps_max;
+    r->trace = tr;
+    r->idem = e;
+  }
+  if (st.status != 0) {
+    const char* what = st.status == ST_NOT_CONVERGED ? "not converged within max_steps"
+                       : st.status == ST_TRACE       ? "replayed sequence gave the wrong trace"
+                       : st.status == ST_NONFINITE   ? "non-finite value in H, bounds or traces"
+                                                     : "device error";
+    h->err = what;
+  }
+  return (gsp2_status)st.status;
+}
+
+extern "C" gsp2_status gsp2_history(gsp2_handle h, double* traces, double* idem, int8_t* alpha, int32_t cap) {
+  if (!usable(h)) return fail(h, GSP2_E_ARG, "invalid handle");
+  if (!h->ws || !h->have_forward) return fail(h, GSP2_E_STATE, "no density call");
+  if (cap < 0) return fail(h, GSP2_E_ARG, "cap < 0");
+  CU(h, cudaDeviceSynchronize());
+  const size_t m = (size_t)std::min<int32_t>(cap, h->opt.max_steps + 1);
+  if (traces) CU(h, cudaMemcpy(traces, h->ws + h->L.traces, m * sizeof(double), cudaMemcpyDeviceToHost));
+  if (idem) CU(h, cudaMemcpy(idem, h->ws + h->L.idem, std::min<size_t>(m, h->opt.max_steps) * sizeof(double),
+                             cudaMemcpyDeviceToHost));
+  if (alpha) CU(h, cudaMemcpy(alpha, h->ws + h->L.alpha + 1, std::min<size_t>(m, h->opt.max_steps),
+                              cudaMemcpyDeviceToHost));
+  return GSP2_OK;
+}
+
+extern "C" gsp2_status gsp2_step_times(gsp2_handle h, float* ms, int32_t cap) {
+  if (!usable(h) || !ms) return fail(h, GSP2_E_ARG, "invalid handle or NULL output");
+  if (h->ev.empty() || !h->have_forward) return fail(h, GSP2_E_STATE, "time_steps not set or no density call");
+  CU(h, cudaDeviceSynchronize());
+  const int32_t m = std::min<int32_t>(cap, h->opt.max_steps);
+  for (int32_t i = 0; i < m; ++i) {
+    ms[i] = 0.0f;
+    cudaError_t e = cudaEventElapsedTime(&ms[i], h->ev[2 * i], h->ev[2 * i + 1]);
+    if (e == cudaErrorNotReady || e == cudaErrorInvalidResourceHandle) {
+      (void)cudaGetLastError();
+      ms[i] = 0.0f;
+    } else if (e != cudaSuccess) {
+      return cuda_fail(h, e, "cudaEventElapsedTime");
+    }
+  }
+  return GSP2_OK;
+}
+
+extern "C" gsp2_status gsp2_backward(gsp2_handle h, const double* d_pbar, double* d_hbar, void* stream) {
+  (void)d_pbar;
+  (void)d_hbar;
+  (void)stream;
+  if (!usable(h)) return fail(h, GSP2_E_ARG, "invalid handle");
+  return fail(h, GSP2_E_STATE, "adjoint not available in this build");
+}
+
+extern "C" void gsp2_destroy(gsp2_handle h) {
+  if (!h) return;
+  drop_graph(h);
+  for (auto& e : h->ev) cudaEventDestroy(e);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  delete h;
+}

@@ -1,0 +1,146 @@
+// Internal data structures shared by the G-SP2 kernels and the host plan code.
+//
+// Layout in device memory (all inside the caller's workspace):
+//   * one "arena" per buffer holds every part's dense s_k x s_k matrix, column-major,
+//     padded to ld_k = roundup(s_k, LD_PAD) rows and columns, at element offset off_k;
+//     rows/columns in [s_k, ld_k) are zero so padded products stay exact;
+//   * part descriptors, the per-part vertex lists S_k (cores ascending, then halo
+//     ascending), the scatter permutation, the work lists and the per-step state.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gsp2 {
+
+constexpr int LD_PAD = 128;      // ld_k multiple (tile edge of every square kernel)
+constexpr int SQ_TILE = 64;      // FP64 square tile edge
+constexpr int COLS_PER_BLOCK = 8;  // gather/scatter: one warp per column, 8 warps
+
+struct PartDesc {
+  int64_t off;   // arena element offset of X_k
+  int64_t soff;  // offset of S_k in the vertex-list table
+  int32_t s;     // core + halo size
+  int32_t c;     // core count
+  int32_t ld;    // padded leading dimension
+  int32_t nt;    // FP64 square tiles per edge: ceil(s / SQ_TILE)
+};
+
+struct Tile {  // one upper-triangular output tile of one part
+  int32_t part, ti, tj, slot;  // slot: diagonal-tile trace slot, -1 otherwise
+};
+
+struct ColBlock {  // COLS_PER_BLOCK consecutive local columns of one part
+  int32_t part, j0;
+};
+
+// Per-call device state.  `counter` is the ticket of the last-block-done
+// reductions; the block that finishes a reduction sets it back to zero.
+struct DevState {
+  double eps_min, eps_max;
+  unsigned int counter;
+  int32_t stopped;     // 1: no further purification steps this call
+  int32_t steps;       // purification steps applied so far
+  int32_t status;      // gsp2_status detected on the device
+  int32_t nonfinite;   // set by any block that meets NaN/Inf
+  int32_t fp64_steps;
+  int32_t pad[6];
+};
+
+enum : int32_t { ST_OK = 0, ST_NOT_CONVERGED = 5, ST_TRACE = 6, ST_NONFINITE = 7 };
+enum : int32_t { MODE_RECORD = 0, MODE_REPLAY = 1 };
+
+// Arguments of the per-step trace bookkeeping done by the last block of a step.
+struct StepCtl {
+  DevState* st;
+  int8_t* alpha;     // alpha[i] = branch of step i (1-based), int8
+  double* traces;    // traces[i] = T_i (core trace of X_i)
+  double* idem;      // idem[i] = e_i = T_i - Tr_core[X_i^2]
+  int64_t nocc;
+  double idem_tol;
+  double trace_tol;
+  int32_t mode;
+  int32_t last_step;  // max_steps (RECORD) or nsteps (REPLAY)
+};
+
+// ------------------------------------------------------------------ device helpers
+
+__device__ __forceinline__ double ld_cg(const double* p) { return __ldcg(p); }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Last-block-done ticket.  Every block calls it once, after its partial results are
+// stored; returns true in exactly one block (the last), which may then read all
+// partials.  All threads of the block must call it.
+__device__ __forceinline__ bool last_block_ticket(unsigned int* counter) {
+  __shared__ int s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    unsigned int t = atomicAdd(counter, 1u);
+    s_last = (t == gridDim.x - 1) ? 1 : 0;
+  }
+  __syncthreads();
+  if (s_last) __threadfence();
+  return s_last != 0;
+}
+
+// Deterministic block-wide sum of two doubles per thread (fixed tree).  Result valid
+// in thread 0.  blockDim.x must be a multiple of 32 and <= 1024.
+__device__ __forceinline__ double2 block_sum2(double a, double b) {
+  __shared__ double2 red[32];
+  a = warp_sum(a);
+  b = warp_sum(b);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = make_double2(a, b);
+  __syncthreads();
+  double2 r = make_double2(0.0, 0.0);
+  if (threadIdx.x == 0) {
+    const int nw = blockDim.x >> 5;
+    for (int i = 0; i < nw; ++i) { r.x += red[i].x; r.y += red[i].y; }
+  }
+  return r;
+}
+
+// Bookkeeping of step `step` (0 = the initial guess X0), run by one thread of the
+// last block once the global sums are known:
+//   tN = Tr_core[X_step], tY = Tr_core[X_{step-1}^2] (unused for step 0).
+// Records T_step and e_{step-1}, applies the stopping test, and in RECORD mode
+// chooses the branch of the next step: alpha = +1 iff T_step <= Nocc.
+__device__ __forceinline__ void finish_step(const StepCtl& c, int step, double tN, double tY) {
+  DevState* st = c.st;
+  c.traces[step] = tN;
+  st->steps = step;
+  bool stop = false;
+  if (step > 0) {
+    const double e = c.traces[step - 1] - tY;
+    c.idem[step - 1] = e;
+    if (c.mode == MODE_RECORD && step >= 3 && e <= c.idem_tol && e >= c.idem[step - 3]) stop = true;
+    if (!isfinite(e)) st->nonfinite = 1;
+  }
+  if (!isfinite(tN)) st->nonfinite = 1;
+  if (st->nonfinite) {
+    st->status = ST_NONFINITE;
+    stop = true;
+  }
+  if (!stop && step >= c.last_step) {
+    stop = true;
+    if (c.mode == MODE_RECORD && step > 0 && !(c.idem[step - 1] <= c.idem_tol)) st->status = ST_NOT_CONVERGED;
+  }
+  if (stop) {
+    st->stopped = 1;
+    if (c.mode == MODE_REPLAY && st->status == ST_OK) {
+      const double d = tN - (double)c.nocc;
+      if (!(fabs(d) <= c.trace_tol)) st->status = ST_TRACE;
+    }
+  } else if (c.mode == MODE_RECORD) {
+    c.alpha[step + 1] = (tN <= (double)c.nocc) ? (int8_t)1 : (int8_t)-1;
+  }
+}
+
+}  // namespace gsp2

@@ -1,0 +1,22 @@
+// Launch wrappers of the G-SP2 kernels (host-callable, internal to the library).
+#pragma once
+
+#include "gsp2_internal.cuh"
+
+namespace gsp2 {
+
+cudaError_t launch_reset(DevState* st, int8_t* alpha, const int8_t* alpha_in, int n_in, int n_alpha,
+                         cudaStream_t s);
+cudaError_t launch_bounds(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* vals,
+                          double2* slots, int nblocks, DevState* st, cudaStream_t s);
+cudaError_t launch_gather(const PartDesc* parts, const ColBlock* blocks, int nblocks, const int32_t* Sall,
+                          const int64_t* rowptr, const int32_t* colind, const double* vals, double* arena,
+                          double* slots, const StepCtl& ctl, cudaStream_t s);
+cudaError_t launch_square_fp64(const PartDesc* parts, const Tile* tiles, int ntiles, const double* xin,
+                               double* xout, double2* slots, int nslots, const StepCtl& ctl, int step,
+                               cudaStream_t s);
+cudaError_t launch_scatter(const PartDesc* parts, const ColBlock* blocks, int nblocks, const int32_t* Sall,
+                           const int32_t* perm, const int64_t* pcolptr, const double* arena0,
+                           const double* arena1, double* pvals, const DevState* st, cudaStream_t s);
+
+}  // namespace gsp2

@@ -1,0 +1,343 @@
+// FP64 kernels of the G-SP2 forward pass: Gershgorin bounds, submatrix gather with
+// the initial guess, grouped symmetric squaring with the fused branch/trace epilogue,
+// and the core-column scatter into P.
+#include "gsp2_internal.cuh"
+#include "gsp2_kernels.h"
+
+namespace gsp2 {
+
+// ------------------------------------------------------------------------------------
+// Gershgorin bounds (Section 2.1): eps_min = min_i (H_ii - R_i), eps_max = max_i (H_ii
+// + R_i), R_i = sum_{j != i} |H_ij|.  One warp per row; block min/max into a slot; the
+// last block reduces the slots and resets the per-call state.
+// ------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) bounds_kernel(int64_t n, const int64_t* __restrict__ rowptr,
+                                                     const int32_t* __restrict__ colind,
+                                                     const double* __restrict__ vals,
+                                                     double2* __restrict__ slots, DevState* st) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  double lo = INFINITY, hi = -INFINITY;
+  int bad = 0;
+  for (int64_t i = warp; i < n; i += nwarps) {
+    double rad = 0.0, dia = 0.0;
+    for (int64_t p = rowptr[i] + lane; p < rowptr[i + 1]; p += 32) {
+      const double v = vals[p];
+      if (!isfinite(v)) bad = 1;
+      if (colind[p] == i) dia = v; else rad += fabs(v);
+    }
+    rad = warp_sum(rad);
+    dia = warp_sum(dia);  // exactly one lane holds the diagonal
+    lo = fmin(lo, dia - rad);
+    hi = fmax(hi, dia + rad);
+  }
+  __shared__ double s_lo[8], s_hi[8];
+  __shared__ int s_bad;
+  if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
+  if (bad) s_bad = 1;
+  if (lane == 0) { s_lo[threadIdx.x >> 5] = lo; s_hi[threadIdx.x >> 5] = hi; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { lo = fmin(lo, s_lo[w]); hi = fmax(hi, s_hi[w]); }
+    slots[blockIdx.x] = make_double2(lo, hi);
+    if (s_bad) st->nonfinite = 1;
+  }
+  if (last_block_ticket(&st->counter)) {
+    if (threadIdx.x == 0) {
+      double a = INFINITY, b = -INFINITY;
+      for (unsigned int k = 0; k < gridDim.x; ++k) {
+        a = fmin(a, ld_cg(&slots[k].x));
+        b = fmax(b, ld_cg(&slots[k].y));
+      }
+      st->eps_min = a;
+      st->eps_max = b;
+      if (!isfinite(a) || !isfinite(b) || !(b > a)) st->nonfinite = 1;
+      st->counter = 0;
+    }
+  }
+}
+
+// Resets the per-call state; must run before bounds_kernel on the same stream.
+__global__ void reset_kernel(DevState* st, int8_t* alpha, const int8_t* alpha_in, int n_in, int n_alpha) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    st->stopped = 0;
+    st->steps = 0;
+    st->status = ST_OK;
+    st->nonfinite = 0;
+    st->fp64_steps = 0;
+    st->counter = 0;
+  }
+  for (int i = threadIdx.x; i < n_alpha; i += blockDim.x)
+    alpha[i] = (alpha_in != nullptr && i >= 1 && i <= n_in) ? alpha_in[i - 1] : (int8_t)0;
+}
+
+// ------------------------------------------------------------------------------------
+// Gather + Eq. 1: X0_k[a, j] = (eps_max [a == j] - H[S_k[j], S_k[a]]) / (eps_max - eps_min)
+// for a, j < s_k; zero in the padding.  One warp per local column j; the row S_k[j]
+// of H is walked once and every stored column is located in S_k by binary search
+// in the (ascending) core and halo lists.  The diagonal entry must be stored.
+// Blocks store the core-diagonal sum of their columns; the last block forms T_0 and
+// chooses the first branch.
+// ------------------------------------------------------------------------------------
+__device__ __forceinline__ int find_local(const int32_t* __restrict__ S, int c, int s, int32_t g) {
+  int lo = 0, hi = c;  // cores [0, c)
+  while (lo < hi) {
+    const int m = (lo + hi) >> 1;
+    if (S[m] < g) lo = m + 1; else hi = m;
+  }
+  if (lo < c && S[lo] == g) return lo;
+  lo = c; hi = s;  // halo [c, s)
+  while (lo < hi) {
+    const int m = (lo + hi) >> 1;
+    if (S[m] < g) lo = m + 1; else hi = m;
+  }
+  if (lo < s && S[lo] == g) return lo;
+  return -1;
+}
+
+__global__ void __launch_bounds__(256) gather_kernel(const PartDesc* __restrict__ parts,
+                                                     const ColBlock* __restrict__ blocks,
+                                                     const int32_t* __restrict__ Sall,
+                                                     const int64_t* __restrict__ rowptr,
+                                                     const int32_t* __restrict__ colind,
+                                                     const double* __restrict__ vals, double* __restrict__ arena,
+                                                     double* __restrict__ slots, StepCtl ctl) {
+  const ColBlock b = blocks[blockIdx.x];
+  const PartDesc p = parts[b.part];
+  const int lane = threadIdx.x & 31;
+  const int j = b.j0 + (threadIdx.x >> 5);
+  const int32_t* S = Sall + p.soff;
+  const double emax = ctl.st->eps_max, emin = ctl.st->eps_min;
+  const double den = emax - emin;
+  double tr = 0.0;
+  const int jend = p.nt * SQ_TILE;  // columns [s, nt*TILE) are zero padding read by the squares
+  if (j < jend) {
+    double* col = arena + p.off + (int64_t)j * p.ld;
+    for (int r = lane; r < p.ld; r += 32) col[r] = 0.0;
+    __syncwarp();
+    if (j < p.s) {
+      const int32_t g = S[j];
+      for (int64_t q = rowptr[g] + lane; q < rowptr[g + 1]; q += 32) {
+        const int a = find_local(S, p.c, p.s, colind[q]);
+        if (a >= 0) {
+          const double x = (a == j) ? (emax - vals[q]) / den : (0.0 - vals[q]) / den;
+          col[a] = x;
+          if (a == j && j < p.c) tr = x;
+        }
+      }
+    }
+  }
+  const double2 t = block_sum2(tr, 0.0);
+  if (threadIdx.x == 0) slots[blockIdx.x] = t.x;
+  if (last_block_ticket(&ctl.st->counter)) {
+    double2 acc = make_double2(0.0, 0.0);
+    double a = 0.0;
+    for (unsigned int k = threadIdx.x; k < gridDim.x; k += blockDim.x) a += ld_cg(&slots[k]);
+    acc = block_sum2(a, 0.0);
+    if (threadIdx.x == 0) {
+      if (ctl.st->nonfinite) ctl.st->status = ST_NONFINITE;
+      finish_step(ctl, 0, acc.x, 0.0);
+      ctl.st->counter = 0;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// One purification step for every part (Eq. 2), FP64 on the CUDA cores.
+//
+// Work item = one upper-triangular 64x64 output tile (ti <= tj) of one part.  X is
+// symmetric, so both operands of Y = X X stream from columns of X: the A slice
+// X[I, k] is column k rows I, and the B slice X[k, J] = X[J, k] is column k rows J.
+// Each of the 256 threads owns a 4x4 block of the tile; 16-wide K slices are double
+// buffered in shared memory with cp.async.
+// Epilogue: X_new = Y (alpha = -1) or 2 X - Y (alpha = +1), written to (I, J) and
+// mirrored to (J, I); diagonal tiles add Tr_core[Y] and Tr_core[X_new] to their slot.
+// The last block sums the slots in a fixed order and runs finish_step.
+// ------------------------------------------------------------------------------------
+constexpr int BK = 16;
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+
+__global__ void __launch_bounds__(256, 2) square_fp64_kernel(const PartDesc* __restrict__ parts,
+                                                             const Tile* __restrict__ tiles,
+                                                             const double* __restrict__ xin,
+                                                             double* __restrict__ xout,
+                                                             double2* __restrict__ slots, int nslots,
+                                                             StepCtl ctl, int step) {
+  if (*(volatile int32_t*)&ctl.st->stopped) return;  // uniform: set before this launch
+  __shared__ __align__(16) double As[2][BK][SQ_TILE];
+  __shared__ __align__(16) double Bs[2][BK][SQ_TILE];
+  const Tile t = tiles[blockIdx.x];
+  const PartDesc p = parts[t.part];
+  const double* X = xin + p.off;
+  const int64_t ld = p.ld;
+  const int r0 = t.ti * SQ_TILE, c0 = t.tj * SQ_TILE;
+  const int kend = (p.s + BK - 1) / BK * BK;
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+
+  // loader mapping: 512 16-byte chunks per operand slice, two per thread
+  auto load_slice = [&](int buf, int k0) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int q = tid + h * 256;
+      const int kr = q >> 5, c2 = (q & 31) * 2;
+      const double* col = X + (int64_t)(k0 + kr) * ld;
+      cp_async16(&As[buf][kr][c2], col + r0 + c2);
+      cp_async16(&Bs[buf][kr][c2], col + c0 + c2);
+    }
+    cp_async_commit();
+  };
+
+  double acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) acc[i][jj] = 0.0;
+
+  const int nk = kend / BK;
+  load_slice(0, 0);
+  for (int it = 0; it < nk; ++it) {
+    const int buf = it & 1;
+    if (it + 1 < nk) {
+      load_slice(buf ^ 1, (it + 1) * BK);
+      cp_async_wait_1();
+    } else {
+      cp_async_wait_all();
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      const double2 a01 = *reinterpret_cast<const double2*>(&As[buf][kk][tx * 4]);
+      const double2 a23 = *reinterpret_cast<const double2*>(&As[buf][kk][tx * 4 + 2]);
+      const double2 b01 = *reinterpret_cast<const double2*>(&Bs[buf][kk][ty * 4]);
+      const double2 b23 = *reinterpret_cast<const double2*>(&Bs[buf][kk][ty * 4 + 2]);
+      const double a[4] = {a01.x, a01.y, a23.x, a23.y};
+      const double b[4] = {b01.x, b01.y, b23.x, b23.y};
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) acc[i][jj] = fma(a[i], b[jj], acc[i][jj]);
+    }
+    __syncthreads();
+  }
+
+  // epilogue
+  const int8_t al = ctl.alpha[step];
+  double* Y = xout + p.off;
+  double tY = 0.0, tN = 0.0;
+  const int rb = r0 + tx * 4, cb = c0 + ty * 4;
+#pragma unroll
+  for (int jj = 0; jj < 4; ++jj) {
+    const int c = cb + jj;
+    const double2 x01 = *reinterpret_cast<const double2*>(X + (int64_t)c * ld + rb);
+    const double2 x23 = *reinterpret_cast<const double2*>(X + (int64_t)c * ld + rb + 2);
+    const double xv[4] = {x01.x, x01.y, x23.x, x23.y};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const double y = acc[i][jj];
+      const double xn = (al > 0) ? (2.0 * xv[i] - y) : y;
+      if (t.slot >= 0 && rb + i == c && c < p.c) { tY += y; tN += xn; }
+      acc[i][jj] = xn;
+    }
+    *reinterpret_cast<double2*>(Y + (int64_t)c * ld + rb) = make_double2(acc[0][jj], acc[1][jj]);
+    *reinterpret_cast<double2*>(Y + (int64_t)c * ld + rb + 2) = make_double2(acc[2][jj], acc[3][jj]);
+  }
+  if (t.ti != t.tj) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = rb + i;
+      *reinterpret_cast<double2*>(Y + (int64_t)r * ld + cb) = make_double2(acc[i][0], acc[i][1]);
+      *reinterpret_cast<double2*>(Y + (int64_t)r * ld + cb + 2) = make_double2(acc[i][2], acc[i][3]);
+    }
+  }
+  if (t.slot >= 0) {
+    const double2 s = block_sum2(tY, tN);
+    if (tid == 0) slots[t.slot] = s;
+  }
+  if (last_block_ticket(&ctl.st->counter)) {
+    double a = 0.0, b = 0.0;
+    for (int k = tid; k < nslots; k += blockDim.x) {
+      a += ld_cg(&slots[k].x);
+      b += ld_cg(&slots[k].y);
+    }
+    const double2 s = block_sum2(a, b);
+    if (tid == 0) {
+      finish_step(ctl, step, s.y, s.x);
+      ctl.st->counter = 0;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Scatter of core columns (Section 1.1, Fig. 1): for core j of part k with global
+// index g = S_k[j], P[:, g] on rows sorted(S_k) = X_k[perm_k[t], j].  The final
+// iterate sits in arena (steps % 2).
+// ------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) scatter_kernel(const PartDesc* __restrict__ parts,
+                                                      const ColBlock* __restrict__ blocks,
+                                                      const int32_t* __restrict__ Sall,
+                                                      const int32_t* __restrict__ perm,
+                                                      const int64_t* __restrict__ pcolptr,
+                                                      const double* __restrict__ arena0,
+                                                      const double* __restrict__ arena1,
+                                                      double* __restrict__ pvals, const DevState* st) {
+  const ColBlock b = blocks[blockIdx.x];
+  const PartDesc p = parts[b.part];
+  const int j = b.j0 + (threadIdx.x >> 5);
+  if (j >= p.c) return;
+  const int lane = threadIdx.x & 31;
+  const double* X = ((st->steps & 1) ? arena1 : arena0) + p.off + (int64_t)j * p.ld;
+  const int32_t g = Sall[p.soff + j];
+  const int32_t* pm = perm + p.soff;
+  double* out = pvals + pcolptr[g];
+  for (int t = lane; t < p.s; t += 32) out[t] = X[pm[t]];
+}
+
+// ------------------------------------------------------------------------------------
+// launch wrappers
+// ------------------------------------------------------------------------------------
+cudaError_t launch_reset(DevState* st, int8_t* alpha, const int8_t* alpha_in, int n_in, int n_alpha,
+                         cudaStream_t s) {
+  reset_kernel<<<1, 256, 0, s>>>(st, alpha, alpha_in, n_in, n_alpha);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bounds(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* vals,
+                          double2* slots, int nblocks, DevState* st, cudaStream_t s) {
+  bounds_kernel<<<nblocks, 256, 0, s>>>(n, rowptr, colind, vals, slots, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather(const PartDesc* parts, const ColBlock* blocks, int nblocks, const int32_t* Sall,
+                          const int64_t* rowptr, const int32_t* colind, const double* vals, double* arena,
+                          double* slots, const StepCtl& ctl, cudaStream_t s) {
+  gather_kernel<<<nblocks, 32 * COLS_PER_BLOCK, 0, s>>>(parts, blocks, Sall, rowptr, colind, vals, arena, slots,
+                                                       ctl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_square_fp64(const PartDesc* parts, const Tile* tiles, int ntiles, const double* xin,
+                               double* xout, double2* slots, int nslots, const StepCtl& ctl, int step,
+                               cudaStream_t s) {
+  square_fp64_kernel<<<ntiles, 256, 0, s>>>(parts, tiles, xin, xout, slots, nslots, ctl, step);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const PartDesc* parts, const ColBlock* blocks, int nblocks, const int32_t* Sall,
+                           const int32_t* perm, const int64_t* pcolptr, const double* arena0,
+                           const double* arena1, double* pvals, const DevState* st, cudaStream_t s) {
+  scatter_kernel<<<nblocks, 32 * COLS_PER_BLOCK, 0, s>>>(parts, blocks, Sall, perm, pcolptr, arena0, arena1,
+                                                        pvals, st);
+  return cudaGetLastError();
+}
+
+}  // namespace gsp2
