@@ -194,6 +194,32 @@ gsp2_status gsp2_step_times(gsp2_handle h, float* ms, int32_t cap);
  */
 gsp2_status gsp2_backward(gsp2_handle h, const double* d_pbar, double* d_hbar, void* stream);
 
+/*
+ * Allocation-free Gershgorin bounds (the paper has no counterpart: this entry point
+ * exists for callers that may not allocate device memory, such as code running in
+ * another framework's memory pool or a plugin barred from growing the process's
+ * device footprint).  Computes d_bounds[0] = min_i (A_ii - sum_{j!=i} |A_ij|) and
+ * d_bounds[1] = max_i (A_ii + sum_{j!=i} |A_ij|) of a CSR matrix, the same bounds
+ * gsp2_density uses, with no cudaMalloc/cudaFree and no allocating library call.
+ *
+ *  n         rows, 1 .. 1,048,576 (4096 blocks of 256 rows); larger n -> GSP2_E_ARG
+ *  d_rowptr  device int64[n+1]; d_colind device int32[nnz]; d_vals device double[nnz]
+ *            (each row's diagonal entry stored once; rows may be in any column order)
+ *  d_bounds  device double[2], output
+ *  stream    cudaStream_t as void*; the call is asynchronous
+ * Returns GSP2_E_ARG for a bad size or a NULL pointer, GSP2_E_CUDA if a CUDA call fails
+ * (no message is stored).  Non-finite values give non-finite bounds.
+ *
+ * Its scratch (one 16-byte partial per block and a counter, about 64 KB) is a fixed
+ * device array inside the library, held on every GPU that loads the library until
+ * the process exits.  All calls on a device share that array: calls that can overlap
+ * on the GPU (different streams without ordering) race and must not be issued.  The
+ * first call on each device looks the array's device address up; make that first call
+ * outside any CUDA stream capture.
+ */
+gsp2_status gsp2_bounds_noalloc(int64_t n, const int64_t* d_rowptr, const int32_t* d_colind,
+                                const double* d_vals, double* d_bounds, void* stream);
+
 /* Last error message of the handle; with h == NULL, the reason the last failed
  * gsp2_create on the calling thread gave. */
 const char* gsp2_last_error(gsp2_handle h);
