@@ -20,8 +20,12 @@ namespace {
 constexpr int BOUNDS_BLOCKS = 608;  // 152 SMs x 4
 
 struct WsLayout {
-  size_t parts, S, perm, tiles, gblocks, sblocks, pcolptr, rowptr, colind, slots, state, alpha, traces, idem;
-  size_t arena0, arena1;
+  size_t parts, S, perm, invperm, tiles, gblocks, sblocks, pcolptr, rowptr, colind, memptr, mempart, memloc;
+  size_t slots, state, alpha, traces, idem, step_arena;
+  size_t arena0, arena1;       // ping-pong iterates
+  std::vector<size_t> ckpt;    // X_0, X_k, X_2k, ... (adjoint checkpoints)
+  std::vector<size_t> seg;     // seg[j] = X_{c0+j}, j = 1..k-1, recomputed in the adjoint
+  size_t xb0, xb1;             // adjoint Xbar ping-pong
   size_t total;
 };
 
@@ -44,7 +48,9 @@ struct gsp2_plan {
   std::vector<int64_t> rowptr;
   std::vector<int32_t> colind;
   std::vector<PartDesc> parts;
-  std::vector<int32_t> S, perm;
+  std::vector<int32_t> S, perm, invperm;
+  std::vector<int64_t> memptr;           // vertex -> parts holding it (CSR)
+  std::vector<int32_t> mempart, memloc;  // part id, local index in S_part
   std::vector<Tile> tiles;
   std::vector<ColBlock> gblocks, sblocks;
   std::vector<int64_t> pcolptr;
@@ -59,6 +65,10 @@ struct gsp2_plan {
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t exec = nullptr;
   GraphKey key{};
+  cudaGraphExec_t bexec = nullptr;  // adjoint graph
+  const void* bkey_pbar = nullptr;
+  void* bkey_hbar = nullptr;
+  std::vector<size_t> step_arena_off;  // workspace offset of the arena holding X_i
   std::vector<cudaEvent_t> ev;  // 2 per step when time_steps is set
   bool have_forward = false;
   std::string err;
@@ -138,6 +148,10 @@ static void build_layout(gsp2_plan* h) {
   L.parts = take(h->parts.size() * sizeof(PartDesc));
   L.S = take(h->S.size() * sizeof(int32_t));
   L.perm = take(h->perm.size() * sizeof(int32_t));
+  L.invperm = take(h->invperm.size() * sizeof(int32_t));
+  L.memptr = take(h->memptr.size() * sizeof(int64_t));
+  L.mempart = take(h->mempart.size() * sizeof(int32_t));
+  L.memloc = take(h->memloc.size() * sizeof(int32_t));
   L.tiles = take(h->tiles.size() * sizeof(Tile));
   L.gblocks = take(h->gblocks.size() * sizeof(ColBlock));
   L.sblocks = take(h->sblocks.size() * sizeof(ColBlock));
@@ -150,9 +164,27 @@ static void build_layout(gsp2_plan* h) {
   L.alpha = take((size_t)h->opt.max_steps + 2);
   L.traces = take(((size_t)h->opt.max_steps + 2) * sizeof(double));
   L.idem = take(((size_t)h->opt.max_steps + 2) * sizeof(double));
-  L.arena0 = take((size_t)h->arena_elems * sizeof(double));
-  L.arena1 = take((size_t)h->arena_elems * sizeof(double));
+  L.step_arena = take(((size_t)h->opt.max_steps + 1) * sizeof(double*));
+  const size_t ab = (size_t)h->arena_elems * sizeof(double);
+  L.arena0 = take(ab);
+  L.arena1 = take(ab);
+  const int k = h->opt.ckpt_every;
+  L.ckpt.clear();
+  L.seg.clear();
+  L.xb0 = L.xb1 = 0;
+  if (k > 0) {
+    for (int c = 0; c <= h->opt.max_steps / k; ++c) L.ckpt.push_back(take(ab));
+    for (int j = 1; j < k; ++j) L.seg.push_back(take(ab));
+    L.xb0 = take(ab);
+    L.xb1 = take(ab);
+  }
   L.total = o;
+  // arena of each iterate X_i: checkpoints where i is a multiple of k, else ping-pong
+  h->step_arena_off.assign((size_t)h->opt.max_steps + 1, 0);
+  for (int i = 0; i <= h->opt.max_steps; ++i) {
+    if (k > 0 && i % k == 0) h->step_arena_off[i] = L.ckpt[i / k];
+    else h->step_arena_off[i] = (i & 1) ? L.arena1 : L.arena0;
+  }
 }
 
 extern "C" gsp2_status gsp2_create(int64_t n, const int64_t* rowptr, const int32_t* colind, int64_t nocc,
@@ -251,6 +283,29 @@ extern "C" gsp2_status gsp2_create(int64_t n, const int64_t* rowptr, const int32
       const int32_t* Sk = h->S.data() + d.soff;
       std::sort(pk, pk + d.s, [&](int32_t a, int32_t b) { return Sk[a] < Sk[b]; });
     }
+    h->invperm.resize(soff);
+    for (int32_t k = 0; k < nparts; ++k) {
+      const PartDesc& d = h->parts[k];
+      for (int32_t t = 0; t < d.s; ++t) h->invperm[d.soff + h->perm[d.soff + t]] = t;
+    }
+    // memberships: for every vertex, the parts whose S_k hold it, in part order
+    h->memptr.assign(n + 1, 0);
+    for (size_t q = 0; q < h->S.size(); ++q) h->memptr[h->S[q] + 1]++;
+    for (int64_t v = 0; v < n; ++v) h->memptr[v + 1] += h->memptr[v];
+    h->mempart.resize(soff);
+    h->memloc.resize(soff);
+    {
+      std::vector<int64_t> fill(h->memptr.begin(), h->memptr.end() - 1);
+      for (int32_t k = 0; k < nparts; ++k) {
+        const PartDesc& d = h->parts[k];
+        for (int32_t a = 0; a < d.s; ++a) {
+          const int32_t v = h->S[d.soff + a];
+          h->mempart[fill[v]] = k;
+          h->memloc[fill[v]] = a;
+          fill[v]++;
+        }
+      }
+    }
     h->pcolptr.assign(n + 1, 0);
     for (int64_t g = 0; g < n; ++g) h->pcolptr[g + 1] = h->pcolptr[g] + h->parts[part[g]].s;
     h->prowind.resize(h->pcolptr[n]);
@@ -331,6 +386,10 @@ static void drop_graph(gsp2_plan* h) {
   if (h->exec) cudaGraphExecDestroy(h->exec);
   h->exec = nullptr;
   h->key = GraphKey{};
+  if (h->bexec) cudaGraphExecDestroy(h->bexec);
+  h->bexec = nullptr;
+  h->bkey_pbar = nullptr;
+  h->bkey_hbar = nullptr;
 }
 
 extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t bytes, void* stream) {
@@ -362,6 +421,13 @@ extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t byt
   CU(h, up(L.parts, h->parts.data(), h->parts.size() * sizeof(PartDesc)));
   CU(h, up(L.S, h->S.data(), h->S.size() * sizeof(int32_t)));
   CU(h, up(L.perm, h->perm.data(), h->perm.size() * sizeof(int32_t)));
+  CU(h, up(L.invperm, h->invperm.data(), h->invperm.size() * sizeof(int32_t)));
+  CU(h, up(L.memptr, h->memptr.data(), h->memptr.size() * sizeof(int64_t)));
+  CU(h, up(L.mempart, h->mempart.data(), h->mempart.size() * sizeof(int32_t)));
+  CU(h, up(L.memloc, h->memloc.data(), h->memloc.size() * sizeof(int32_t)));
+  std::vector<const double*> tab(h->step_arena_off.size());
+  for (size_t i = 0; i < tab.size(); ++i) tab[i] = (const double*)(h->ws + h->step_arena_off[i]);
+  CU(h, up(L.step_arena, tab.data(), tab.size() * sizeof(double*)));
   CU(h, up(L.tiles, h->tiles.data(), h->tiles.size() * sizeof(Tile)));
   CU(h, up(L.gblocks, h->gblocks.data(), h->gblocks.size() * sizeof(ColBlock)));
   CU(h, up(L.sblocks, h->sblocks.data(), h->sblocks.size() * sizeof(ColBlock)));
@@ -392,21 +458,21 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
   auto slots = (double2*)(w + L.slots);
   auto st = (DevState*)(w + L.state);
   auto alpha = (int8_t*)(w + L.alpha);
-  double* a0 = (double*)(w + L.arena0);
-  double* a1 = (double*)(w + L.arena1);
+  auto A = [&](int i) { return (double*)(w + h->step_arena_off[i]); };
   StepCtl ctl{st, alpha, (double*)(w + L.traces), (double*)(w + L.idem), h->nocc, h->opt.idem_tol,
               h->opt.trace_tol, mode, mode == MODE_REPLAY ? nsteps : h->opt.max_steps};
   CU(h, launch_reset(st, alpha, mode == MODE_REPLAY ? alpha_user : nullptr, nsteps, h->opt.max_steps + 2, s));
   CU(h, launch_bounds(h->n, rp, ci, hv, slots, BOUNDS_BLOCKS, st, s));
-  CU(h, launch_gather(parts, gbl, (int)h->gblocks.size(), Sall, rp, ci, hv, a0, (double*)slots, ctl, s));
+  CU(h, launch_gather(parts, gbl, (int)h->gblocks.size(), Sall, rp, ci, hv, A(0), (double*)slots, ctl, s));
   for (int i = 1; i <= ctl.last_step; ++i) {
-    const double* xin = (i & 1) ? a0 : a1;
-    double* xout = (i & 1) ? a1 : a0;
+    const double* xin = A(i - 1);
+    double* xout = A(i);
     if (!h->ev.empty()) CU(h, cudaEventRecordWithFlags(h->ev[2 * (i - 1)], s, cudaEventRecordExternal));
-    CU(h, launch_square_fp64(parts, tiles, (int)h->tiles.size(), xin, xout, slots, h->nslots, ctl, i, s));
+    CU(h, launch_square_fp64(parts, tiles, (int)h->tiles.size(), xin, xout, slots, h->nslots, ctl, i, 0, s));
     if (!h->ev.empty()) CU(h, cudaEventRecordWithFlags(h->ev[2 * (i - 1) + 1], s, cudaEventRecordExternal));
   }
-  CU(h, launch_scatter(parts, sbl, (int)h->sblocks.size(), Sall, perm, pcol, a0, a1, pv, st, s));
+  CU(h, launch_scatter(parts, sbl, (int)h->sblocks.size(), Sall, perm, pcol, (const double* const*)(w + L.step_arena),
+                       pv, st, s));
   if (mode == MODE_RECORD && alpha_user)
     CU(h, cudaMemcpyAsync(alpha_user, alpha + 1, (size_t)h->opt.max_steps, cudaMemcpyDeviceToDevice, s));
   return GSP2_OK;
@@ -518,12 +584,79 @@ extern "C" gsp2_status gsp2_step_times(gsp2_handle h, float* ms, int32_t cap) {
   return GSP2_OK;
 }
 
+// Queue the adjoint on `s`: seed, then per checkpoint segment (last first) the
+// recomputed iterates and the reverse steps, then the scatter-add onto H.  The
+// schedule covers max_steps; kernels for steps beyond the applied count return at once.
+static gsp2_status enqueue_backward(gsp2_plan* h, const double* pbar, double* hbar, cudaStream_t s) {
+  const WsLayout& L = h->L;
+  char* w = h->ws;
+  auto parts = (const PartDesc*)(w + L.parts);
+  auto Sall = (const int32_t*)(w + L.S);
+  auto tiles = (const Tile*)(w + L.tiles);
+  auto gbl = (const ColBlock*)(w + L.gblocks);
+  auto st = (DevState*)(w + L.state);
+  auto alpha = (int8_t*)(w + L.alpha);
+  double* xb0 = (double*)(w + L.xb0);
+  double* xb1 = (double*)(w + L.xb1);
+  const int k = h->opt.ckpt_every, M = h->opt.max_steps;
+  const int nt = (int)h->tiles.size();
+  StepCtl ctl{st, alpha, (double*)(w + L.traces), (double*)(w + L.idem), h->nocc, h->opt.idem_tol,
+              h->opt.trace_tol, MODE_REPLAY, M};
+  CU(h, launch_adj_seed(parts, gbl, (int)h->gblocks.size(), Sall, (const int32_t*)(w + L.invperm),
+                        (const int64_t*)(w + L.pcolptr), pbar, xb0, s));
+  for (int c0 = (M / k) * k; c0 >= 0; c0 -= k) {
+    const double* ck = (const double*)(w + L.ckpt[c0 / k]);
+    for (int j = 1; j < k && c0 + j < M; ++j) {
+      const double* xin = (j == 1) ? ck : (const double*)(w + L.seg[j - 2]);
+      double* xout = (double*)(w + L.seg[j - 1]);
+      CU(h, launch_square_fp64(parts, tiles, nt, xin, xout, nullptr, 0, ctl, c0 + j, 1, s));
+    }
+    for (int i = std::min(c0 + k, M); i >= c0 + 1; --i) {
+      const double* X = (i - 1 == c0) ? ck : (const double*)(w + L.seg[i - 1 - c0 - 1]);
+      CU(h, launch_adj_step_fp64(parts, tiles, nt, X, xb0, xb1, alpha, st, i, s));
+    }
+  }
+  CU(h, launch_adj_hbar(h->n, (const int64_t*)(w + L.rowptr), (const int32_t*)(w + L.colind),
+                        (const int64_t*)(w + L.memptr), (const int32_t*)(w + L.mempart),
+                        (const int32_t*)(w + L.memloc), parts, Sall, xb0, xb1, hbar, st, s));
+  return GSP2_OK;
+}
+
 extern "C" gsp2_status gsp2_backward(gsp2_handle h, const double* d_pbar, double* d_hbar, void* stream) {
-  (void)d_pbar;
-  (void)d_hbar;
-  (void)stream;
   if (!usable(h)) return fail(h, GSP2_E_ARG, "invalid handle");
-  return fail(h, GSP2_E_STATE, "adjoint not available in this build");
+  if (h->opt.ckpt_every <= 0) return fail(h, GSP2_E_STATE, "plan built with ckpt_every = 0: no adjoint");
+  if (!h->ws || !h->have_forward) return fail(h, GSP2_E_STATE, "gsp2_backward needs a completed density call");
+  if (!d_pbar || !d_hbar) return fail(h, GSP2_E_ARG, "NULL Pbar or Hbar buffer");
+  int dev = 0;
+  CU(h, cudaGetDevice(&dev));
+  if (dev != h->device) return fail(h, GSP2_E_STATE, "current device differs from the workspace's device");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (h->opt.use_graph) {
+    if (!h->bexec || h->bkey_pbar != d_pbar || h->bkey_hbar != d_hbar) {
+      if (h->bexec) cudaGraphExecDestroy(h->bexec);
+      h->bexec = nullptr;
+      cudaGraph_t g = nullptr;
+      CU(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+      gsp2_status st = enqueue_backward(h, d_pbar, d_hbar, h->cap_stream);
+      cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
+      if (st != GSP2_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+      }
+      if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+      e = cudaGraphInstantiate(&h->bexec, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        h->bexec = nullptr;
+        return cuda_fail(h, e, "cudaGraphInstantiate");
+      }
+      h->bkey_pbar = d_pbar;
+      h->bkey_hbar = d_hbar;
+    }
+    CU(h, cudaGraphLaunch(h->bexec, s));
+    return GSP2_OK;
+  }
+  return enqueue_backward(h, d_pbar, d_hbar, s);
 }
 
 extern "C" void gsp2_destroy(gsp2_handle h) {

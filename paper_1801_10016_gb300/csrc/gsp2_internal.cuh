@@ -73,6 +73,33 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// 16-byte asynchronous global->shared copies (both addresses 16-byte aligned).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::); }
+
+// Local index of global vertex g in S_k (cores [0, c) ascending, halo [c, s)
+// ascending), or -1.
+__device__ __forceinline__ int find_local(const int32_t* __restrict__ S, int c, int s, int32_t g) {
+  int lo = 0, hi = c;
+  while (lo < hi) {
+    const int m = (lo + hi) >> 1;
+    if (S[m] < g) lo = m + 1; else hi = m;
+  }
+  if (lo < c && S[lo] == g) return lo;
+  lo = c; hi = s;
+  while (lo < hi) {
+    const int m = (lo + hi) >> 1;
+    if (S[m] < g) lo = m + 1; else hi = m;
+  }
+  if (lo < s && S[lo] == g) return lo;
+  return -1;
+}
+
 // Last-block-done ticket.  Every block calls it once, after its partial results are
 // stored; returns true in exactly one block (the last), which may then read all
 // partials.  All threads of the block must call it.

@@ -14,9 +14,21 @@ cudaError_t launch_gather(const PartDesc* parts, const ColBlock* blocks, int nbl
                           double* slots, const StepCtl& ctl, cudaStream_t s);
 cudaError_t launch_square_fp64(const PartDesc* parts, const Tile* tiles, int ntiles, const double* xin,
                                double* xout, double2* slots, int nslots, const StepCtl& ctl, int step,
-                               cudaStream_t s);
+                               int recompute, cudaStream_t s);
 cudaError_t launch_scatter(const PartDesc* parts, const ColBlock* blocks, int nblocks, const int32_t* Sall,
-                           const int32_t* perm, const int64_t* pcolptr, const double* arena0,
-                           const double* arena1, double* pvals, const DevState* st, cudaStream_t s);
+                           const int32_t* perm, const int64_t* pcolptr, const double* const* arena_of_step,
+                           double* pvals, const DevState* st, cudaStream_t s);
+
+// adjoint (k_adjoint.cu)
+cudaError_t launch_adj_seed(const PartDesc* parts, const ColBlock* blocks, int nblocks, const int32_t* Sall,
+                            const int32_t* invperm, const int64_t* pcolptr, const double* pbar, double* xbar,
+                            cudaStream_t s);
+cudaError_t launch_adj_step_fp64(const PartDesc* parts, const Tile* tiles, int ntiles, const double* X,
+                                 double* xb0, double* xb1, const int8_t* alpha, const DevState* st, int step,
+                                 cudaStream_t s);
+cudaError_t launch_adj_hbar(int64_t n, const int64_t* rowptr, const int32_t* colind, const int64_t* memptr,
+                            const int32_t* mempart, const int32_t* memloc, const PartDesc* parts,
+                            const int32_t* Sall, const double* xb0, const double* xb1, double* hbar,
+                            const DevState* st, cudaStream_t s);
 
 }  // namespace gsp2

@@ -81,22 +81,6 @@ __global__ void reset_kernel(DevState* st, int8_t* alpha, const int8_t* alpha_in
 // Blocks store the core-diagonal sum of their columns; the last block forms T_0 and
 // chooses the first branch.
 // ------------------------------------------------------------------------------------
-__device__ __forceinline__ int find_local(const int32_t* __restrict__ S, int c, int s, int32_t g) {
-  int lo = 0, hi = c;  // cores [0, c)
-  while (lo < hi) {
-    const int m = (lo + hi) >> 1;
-    if (S[m] < g) lo = m + 1; else hi = m;
-  }
-  if (lo < c && S[lo] == g) return lo;
-  lo = c; hi = s;  // halo [c, s)
-  while (lo < hi) {
-    const int m = (lo + hi) >> 1;
-    if (S[m] < g) lo = m + 1; else hi = m;
-  }
-  if (lo < s && S[lo] == g) return lo;
-  return -1;
-}
-
 __global__ void __launch_bounds__(256) gather_kernel(const PartDesc* __restrict__ parts,
                                                      const ColBlock* __restrict__ blocks,
                                                      const int32_t* __restrict__ Sall,
@@ -158,21 +142,20 @@ __global__ void __launch_bounds__(256) gather_kernel(const PartDesc* __restrict_
 // ------------------------------------------------------------------------------------
 constexpr int BK = 16;
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
-__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::); }
-
 __global__ void __launch_bounds__(256, 2) square_fp64_kernel(const PartDesc* __restrict__ parts,
                                                              const Tile* __restrict__ tiles,
                                                              const double* __restrict__ xin,
                                                              double* __restrict__ xout,
                                                              double2* __restrict__ slots, int nslots,
-                                                             StepCtl ctl, int step) {
-  if (*(volatile int32_t*)&ctl.st->stopped) return;  // uniform: set before this launch
+                                                             StepCtl ctl, int step, int recompute) {
+  // forward: nothing to do once the loop has stopped.  recompute (adjoint): rebuild
+  // X_step from X_{step-1} with the recorded branch, only if step < steps applied,
+  // with no trace bookkeeping.  Both tests are uniform over the launch.
+  if (recompute) {
+    if (step >= *(volatile int32_t*)&ctl.st->steps) return;
+  } else if (*(volatile int32_t*)&ctl.st->stopped) {
+    return;
+  }
   __shared__ __align__(16) double As[2][BK][SQ_TILE];
   __shared__ __align__(16) double Bs[2][BK][SQ_TILE];
   const Tile t = tiles[blockIdx.x];
@@ -245,7 +228,7 @@ __global__ void __launch_bounds__(256, 2) square_fp64_kernel(const PartDesc* __r
     for (int i = 0; i < 4; ++i) {
       const double y = acc[i][jj];
       const double xn = (al > 0) ? (2.0 * xv[i] - y) : y;
-      if (t.slot >= 0 && rb + i == c && c < p.c) { tY += y; tN += xn; }
+      if (!recompute && t.slot >= 0 && rb + i == c && c < p.c) { tY += y; tN += xn; }
       acc[i][jj] = xn;
     }
     *reinterpret_cast<double2*>(Y + (int64_t)c * ld + rb) = make_double2(acc[0][jj], acc[1][jj]);
@@ -259,6 +242,7 @@ __global__ void __launch_bounds__(256, 2) square_fp64_kernel(const PartDesc* __r
       *reinterpret_cast<double2*>(Y + (int64_t)r * ld + cb + 2) = make_double2(acc[i][2], acc[i][3]);
     }
   }
+  if (recompute) return;
   if (t.slot >= 0) {
     const double2 s = block_sum2(tY, tN);
     if (tid == 0) slots[t.slot] = s;
@@ -280,22 +264,21 @@ __global__ void __launch_bounds__(256, 2) square_fp64_kernel(const PartDesc* __r
 // ------------------------------------------------------------------------------------
 // Scatter of core columns (Section 1.1, Fig. 1): for core j of part k with global
 // index g = S_k[j], P[:, g] on rows sorted(S_k) = X_k[perm_k[t], j].  The final
-// iterate sits in arena (steps % 2).
+// iterate X_steps sits in the arena arena_of_step[steps].
 // ------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) scatter_kernel(const PartDesc* __restrict__ parts,
                                                       const ColBlock* __restrict__ blocks,
                                                       const int32_t* __restrict__ Sall,
                                                       const int32_t* __restrict__ perm,
                                                       const int64_t* __restrict__ pcolptr,
-                                                      const double* __restrict__ arena0,
-                                                      const double* __restrict__ arena1,
+                                                      const double* const* __restrict__ arena_of_step,
                                                       double* __restrict__ pvals, const DevState* st) {
   const ColBlock b = blocks[blockIdx.x];
   const PartDesc p = parts[b.part];
   const int j = b.j0 + (threadIdx.x >> 5);
   if (j >= p.c) return;
   const int lane = threadIdx.x & 31;
-  const double* X = ((st->steps & 1) ? arena1 : arena0) + p.off + (int64_t)j * p.ld;
+  const double* X = arena_of_step[st->steps] + p.off + (int64_t)j * p.ld;
   const int32_t g = Sall[p.soff + j];
   const int32_t* pm = perm + p.soff;
   double* out = pvals + pcolptr[g];
@@ -327,15 +310,15 @@ cudaError_t launch_gather(const PartDesc* parts, const ColBlock* blocks, int nbl
 
 cudaError_t launch_square_fp64(const PartDesc* parts, const Tile* tiles, int ntiles, const double* xin,
                                double* xout, double2* slots, int nslots, const StepCtl& ctl, int step,
-                               cudaStream_t s) {
-  square_fp64_kernel<<<ntiles, 256, 0, s>>>(parts, tiles, xin, xout, slots, nslots, ctl, step);
+                               int recompute, cudaStream_t s) {
+  square_fp64_kernel<<<ntiles, 256, 0, s>>>(parts, tiles, xin, xout, slots, nslots, ctl, step, recompute);
   return cudaGetLastError();
 }
 
 cudaError_t launch_scatter(const PartDesc* parts, const ColBlock* blocks, int nblocks, const int32_t* Sall,
-                           const int32_t* perm, const int64_t* pcolptr, const double* arena0,
-                           const double* arena1, double* pvals, const DevState* st, cudaStream_t s) {
-  scatter_kernel<<<nblocks, 32 * COLS_PER_BLOCK, 0, s>>>(parts, blocks, Sall, perm, pcolptr, arena0, arena1,
+                           const int32_t* perm, const int64_t* pcolptr, const double* const* arena_of_step,
+                           double* pvals, const DevState* st, cudaStream_t s) {
+  scatter_kernel<<<nblocks, 32 * COLS_PER_BLOCK, 0, s>>>(parts, blocks, Sall, perm, pcolptr, arena_of_step,
                                                         pvals, st);
   return cudaGetLastError();
 }

@@ -1,0 +1,97 @@
+"""GPU parity of the hand-written adjoint (gsp2_backward) against the oracle's
+reverse-mode adjoint, which the CPU suite pins to finite differences and to the
+Daleckii-Krein divided differences of the same SP2 polynomial."""
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import make_workload, dense_from_csr, random_symmetric_on_pattern
+from synth.tb import make_tb_system
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1801_10016_gb300 import gsp2
+    return gsp2
+
+
+def pbar_for_trace_loss(s, plan):
+    """L = tr(P A) with A a seeded symmetric Gaussian matrix on H's pattern:
+    dL/dP_ij = A_ji = A_ij on the pattern of P."""
+    A = dense_from_csr(s.n, s.rowptr, s.colind, random_symmetric_on_pattern(s.rowptr, s.colind, 5678))
+    cols = np.repeat(np.arange(s.n), np.diff(plan.p_colptr))
+    pb = A[plan.p_rowind, cols]
+    Pbar = np.zeros((s.n, s.n))
+    Pbar[plan.p_rowind, cols] = pb
+    return pb, Pbar
+
+
+def run_adjoint(g, s, **opt):
+    import torch
+    plan = g.GSP2(s.n, s.rowptr, s.colind, s.nocc, s.part, s.nparts, s.g_rowptr, s.g_colind, device="cuda:0", **opt)
+    h = torch.from_numpy(s.vals).to("cuda:0")
+    plan.density(h)
+    hist = plan.history()
+    pb, Pbar = pbar_for_trace_loss(s, plan)
+    hb = plan.backward(torch.from_numpy(pb).to("cuda:0"))
+    return plan, h, hist, pb, Pbar, hb
+
+
+@pytest.mark.parametrize("case", ["small", "tb512", "tb4k"])
+def test_adjoint_matches_oracle(g, case):
+    s = {"small": lambda: make_tb_system(48, 4, 3.0, seed=21), "tb512": lambda: make_workload("tb512"),
+         "tb4k": lambda: make_workload("tb4k")}[case]()
+    plan, h, hist, pb, Pbar, hb = run_adjoint(g, s)
+    assert hist["status"] == 0
+    ref = oracle.gsp2(s.n, s.rowptr, s.colind, s.vals, s.nocc, s.part, s.nparts, s.g_rowptr, s.g_colind)
+    assert hist["alphas"] == ref.alphas  # same polynomial on both sides
+    want = oracle.gsp2_adjoint(s.n, s.rowptr, s.colind, s.vals, ref, Pbar)
+    got = hb.cpu().numpy()
+    scale = max(1.0, np.max(np.abs(want)))
+    assert np.max(np.abs(got - want)) <= 1e-9 * scale, np.max(np.abs(got - want))
+
+
+@pytest.mark.parametrize("k", [1, 3, 45])
+def test_checkpoint_interval_does_not_change_the_gradient(g, k):
+    import torch
+    s = make_tb_system(48, 4, 3.0, seed=21)
+    _, _, _, _, _, hb8 = run_adjoint(g, s)
+    _, _, _, _, _, hbk = run_adjoint(g, s, ckpt_every=k)
+    assert torch.equal(hb8, hbk)
+
+
+def test_autograd_function_uses_the_adjoint(g):
+    import torch
+    s = make_tb_system(48, 4, 3.0, seed=21)
+    plan = g.GSP2(s.n, s.rowptr, s.colind, s.nocc, s.part, s.nparts, s.g_rowptr, s.g_colind, device="cuda:0")
+    pb, _ = pbar_for_trace_loss(s, plan)
+    pbt = torch.from_numpy(pb).to("cuda:0")
+    h = torch.from_numpy(s.vals).to("cuda:0").requires_grad_(True)
+    P = g.gsp2_density(h, plan)
+    loss = (P * pbt).sum()
+    loss.backward()
+    direct = plan.backward(pbt)
+    assert torch.equal(h.grad, direct)
+
+
+def test_backward_state_errors(g):
+    import torch
+    s = make_tb_system(20, 2, 3.0, seed=4)
+    plan = g.GSP2(s.n, s.rowptr, s.colind, s.nocc, s.part, s.nparts, s.g_rowptr, s.g_colind, device="cuda:0")
+    with pytest.raises(g.GSP2Error) as e:
+        plan.backward(torch.zeros(plan.nnz_p, dtype=torch.float64, device="cuda:0"))
+    assert e.value.status == g.E_STATE
+    plan0 = g.GSP2(s.n, s.rowptr, s.colind, s.nocc, s.part, s.nparts, s.g_rowptr, s.g_colind, device="cuda:0",
+                   ckpt_every=0)
+    plan0.density(torch.from_numpy(s.vals).to("cuda:0"))
+    with pytest.raises(g.GSP2Error) as e:
+        plan0.backward(torch.zeros(plan0.nnz_p, dtype=torch.float64, device="cuda:0"))
+    assert e.value.status == g.E_STATE
