@@ -47,19 +47,25 @@ typedef enum {
   GSP2_E_NOT_CONVERGED = 5,  /* device: max_steps reached before the stopping test */
   GSP2_E_TRACE = 6,          /* device: replayed sequence ended with |Tr P - Nocc| > trace_tol */
   GSP2_E_NONFINITE = 7,      /* device: NaN/Inf met in H, the bounds or a trace */
-  GSP2_E_WORKSPACE = 8       /* workspace too small or misaligned (256 bytes) */
+  GSP2_E_WORKSPACE = 8,      /* workspace too small or misaligned (256 bytes) */
+  GSP2_E_TIMEOUT = 9         /* device: a bounded wait inside a kernel gave up */
 } gsp2_status;
 
 /* Arithmetic of the purification steps.  Traces, bounds and branch decisions are
  * always FP64.  The low-precision modes keep an FP32 master copy of every X_k, run
- * the squarings on tcgen05 tensor cores with FP32 accumulation, and finish with
- * `fp64_tail_steps` purification steps in FP64. */
+ * the squarings in that precision (TF32/BF16: tcgen05 tensor cores, FP32 accumulation
+ * in TMEM; FP32: CUDA cores), stop when the idempotency error e no longer falls below
+ * max(idem_tol, 16 N u) (u: unit roundoff of one product), and finish with
+ * `fp64_tail_steps` FP64 steps: the first takes its branch from the trace rule, each
+ * further one the opposite branch, so eigenvalues near 0 and near 1 are both purified.
+ * The low-precision modes support RECORD only and have no adjoint. */
 typedef enum {
   GSP2_PREC_FP64 = 0,
   GSP2_PREC_FP32 = 1,   /* FP32 CUDA-core squarings (no tensor cores) */
   GSP2_PREC_TF32 = 2,
   GSP2_PREC_BF16 = 3,
-  GSP2_PREC_BF16X3 = 4  /* split operands hi+lo in BF16, three products, FP32 accumulate */
+  GSP2_PREC_BF16X3 = 4, /* split operands hi+lo in BF16, three products, FP32 accumulate */
+  GSP2_PREC_TF32X3 = 5  /* split operands hi+lo in TF32, three products, FP32 accumulate */
 } gsp2_precision;
 
 typedef enum {
@@ -72,7 +78,7 @@ typedef struct {
   double idem_tol;         /* stopping gate on e = Tr X - Tr X^2 (default 1e-3) */
   double trace_tol;        /* replay check on |Tr P - Nocc| (default 1e-2) */
   int32_t precision;       /* gsp2_precision (default FP64) */
-  int32_t fp64_tail_steps; /* low-precision modes: FP64 steps at the end (default 2) */
+  int32_t fp64_tail_steps; /* low-precision modes: FP64 steps at the end, 0..8 (default 2) */
   int32_t ckpt_every;      /* adjoint: keep every k-th iterate (default 8); 0 = no adjoint */
   int32_t use_graph;       /* 1 (default): capture the whole step sequence in a CUDA graph */
   int32_t time_steps;      /* 1: record CUDA events around every purification-step launch

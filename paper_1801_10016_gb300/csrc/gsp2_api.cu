@@ -20,7 +20,15 @@ namespace {
 constexpr int BOUNDS_BLOCKS = 608;  // 152 SMs x 4
 
 struct WsLayout {
-  size_t parts, S, perm, invperm, tiles, gblocks, sblocks, pcolptr, rowptr, colind, memptr, mempart, memloc;
+  size_t parts, S, perm, invperm, tiles, tc_tiles, gblocks, gblocks_ld, sblocks, pcolptr, rowptr, colind;
+  size_t memptr, mempart, memloc;
+  // low-precision paths
+  size_t mf[2];        // FP32 master copies of X (ping-pong)
+  size_t op_hi[2];     // operand arenas (BF16 or TF32), ping-pong
+  size_t op_lo[2];     // split-mode low parts
+  size_t maps;         // CUtensorMap[2 buffers][hi, lo][nparts]
+  size_t master_of_step;
+  size_t d[2];         // FP64 arenas of the tail steps
   size_t slots, state, alpha, traces, idem, step_arena;
   size_t arena0, arena1;       // ping-pong iterates
   std::vector<size_t> ckpt;    // X_0, X_k, X_2k, ... (adjoint checkpoints)
@@ -51,8 +59,11 @@ struct gsp2_plan {
   std::vector<int32_t> S, perm, invperm;
   std::vector<int64_t> memptr;           // vertex -> parts holding it (CSR)
   std::vector<int32_t> mempart, memloc;  // part id, local index in S_part
-  std::vector<Tile> tiles;
-  std::vector<ColBlock> gblocks, sblocks;
+  std::vector<Tile> tiles;                 // 64x64 upper tiles (CUDA-core steps)
+  std::vector<Tile> tc_tiles;              // 128x128 upper tiles (tensor-core steps)
+  std::vector<ColBlock> gblocks, sblocks;  // gather (to nt*64) and scatter (cores) columns
+  std::vector<ColBlock> gblocks_ld;        // low-precision gather: every column up to ld
+  int32_t nslots_tc = 0;
   std::vector<int64_t> pcolptr;
   std::vector<int32_t> prowind;
   int32_t nslots = 0, max_s = 0;
@@ -93,6 +104,27 @@ static gsp2_status cuda_fail(gsp2_plan* h, cudaError_t e, const char* where) {
   } while (0)
 
 static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// history slots beyond max_steps: the FP64 tail steps of the low-precision paths
+constexpr int HIST_EXTRA = 16;
+constexpr int MAX_TAIL = 8;
+
+// tensor-core operand kind (-1: FP32 CUDA cores, 0: BF16, 1: TF32) and products per tile
+static int prec_kind(int prec) {
+  return prec == GSP2_PREC_FP32 ? -1 : (prec == GSP2_PREC_BF16 || prec == GSP2_PREC_BF16X3) ? 0 : 1;
+}
+static int prec_nprod(int prec) { return (prec == GSP2_PREC_BF16X3 || prec == GSP2_PREC_TF32X3) ? 3 : 1; }
+// unit roundoff of one product of the low-precision phase
+static double prec_unit(int prec) {
+  switch (prec) {
+    case GSP2_PREC_FP32: return 0x1p-24;
+    case GSP2_PREC_TF32: return 0x1p-11;
+    case GSP2_PREC_BF16: return 0x1p-8;
+    case GSP2_PREC_BF16X3: return 0x1p-16;
+    case GSP2_PREC_TF32X3: return 0x1p-22;
+    default: return 0x1p-53;
+  }
+}
 
 static std::string check_csr(int64_t n, const int64_t* rowptr, const int32_t* colind, bool need_diag,
                              const char* what) {
@@ -153,19 +185,52 @@ static void build_layout(gsp2_plan* h) {
   L.mempart = take(h->mempart.size() * sizeof(int32_t));
   L.memloc = take(h->memloc.size() * sizeof(int32_t));
   L.tiles = take(h->tiles.size() * sizeof(Tile));
+  L.tc_tiles = take(h->tc_tiles.size() * sizeof(Tile));
   L.gblocks = take(h->gblocks.size() * sizeof(ColBlock));
+  L.gblocks_ld = take(h->gblocks_ld.size() * sizeof(ColBlock));
   L.sblocks = take(h->sblocks.size() * sizeof(ColBlock));
   L.pcolptr = take(h->pcolptr.size() * sizeof(int64_t));
   L.rowptr = take(h->rowptr.size() * sizeof(int64_t));
   L.colind = take(h->colind.size() * sizeof(int32_t));
-  const size_t nsl = std::max<size_t>({(size_t)h->nslots, h->gblocks.size(), (size_t)BOUNDS_BLOCKS, 1});
+  const size_t nsl = std::max<size_t>({(size_t)h->nslots, (size_t)h->nslots_tc, h->gblocks.size(),
+                                        h->gblocks_ld.size(), (size_t)BOUNDS_BLOCKS, 1});
   L.slots = take(nsl * sizeof(double2));
   L.state = take(sizeof(DevState));
-  L.alpha = take((size_t)h->opt.max_steps + 2);
-  L.traces = take(((size_t)h->opt.max_steps + 2) * sizeof(double));
-  L.idem = take(((size_t)h->opt.max_steps + 2) * sizeof(double));
+  L.alpha = take((size_t)h->opt.max_steps + HIST_EXTRA);
+  L.traces = take(((size_t)h->opt.max_steps + HIST_EXTRA) * sizeof(double));
+  L.idem = take(((size_t)h->opt.max_steps + HIST_EXTRA) * sizeof(double));
   L.step_arena = take(((size_t)h->opt.max_steps + 1) * sizeof(double*));
+  L.master_of_step = take(((size_t)h->opt.max_steps + 1) * sizeof(float*));
   const size_t ab = (size_t)h->arena_elems * sizeof(double);
+  const int prec = h->opt.precision;
+  if (prec != GSP2_PREC_FP64) {
+    // low precision: FP32 masters, operands, tensor maps, FP64 tail arenas; no adjoint
+    const size_t af = (size_t)h->arena_elems * sizeof(float);
+    L.mf[0] = take(af);
+    L.mf[1] = take(af);
+    const int kind = prec_kind(prec), nprod = prec_nprod(prec);
+    const size_t es = kind == 0 ? 2 : 4;
+    L.op_hi[0] = L.op_hi[1] = L.op_lo[0] = L.op_lo[1] = 0;
+    if (kind >= 0) {
+      L.op_hi[0] = take((size_t)h->arena_elems * es);
+      L.op_hi[1] = take((size_t)h->arena_elems * es);
+      if (nprod == 3) {
+        L.op_lo[0] = take((size_t)h->arena_elems * es);
+        L.op_lo[1] = take((size_t)h->arena_elems * es);
+      }
+      L.maps = take(4 * h->parts.size() * 128);
+    }
+    L.d[0] = take(ab);
+    L.d[1] = take(ab);
+    L.ckpt.clear();
+    L.seg.clear();
+    L.arena0 = L.d[0];
+    L.arena1 = L.d[1];
+    L.xb0 = L.xb1 = 0;
+    L.total = o;
+    h->step_arena_off.assign((size_t)h->opt.max_steps + 1, L.d[0]);
+    return;
+  }
   L.arena0 = take(ab);
   L.arena1 = take(ab);
   const int k = h->opt.ckpt_every;
@@ -208,7 +273,9 @@ extern "C" gsp2_status gsp2_create(int64_t n, const int64_t* rowptr, const int32
     if (!part) return bail(GSP2_E_ARG, "part is NULL");
     if (o.max_steps < 1 || o.max_steps > 1024) return bail(GSP2_E_ARG, "max_steps must be in [1, 1024]");
     if (!(o.idem_tol >= 0.0) || !(o.trace_tol >= 0.0)) return bail(GSP2_E_ARG, "tolerances must be >= 0");
-    if (o.precision != GSP2_PREC_FP64) return bail(GSP2_E_ARG, "precision not supported by this build");
+    if (o.precision < GSP2_PREC_FP64 || o.precision > GSP2_PREC_TF32X3) return bail(GSP2_E_ARG, "unknown precision");
+    if (o.fp64_tail_steps < 0 || o.fp64_tail_steps > MAX_TAIL)
+      return bail(GSP2_E_ARG, "fp64_tail_steps must be in [0, 8]");
     if (o.ckpt_every < 0) return bail(GSP2_E_ARG, "ckpt_every must be >= 0");
     if ((g_rowptr == nullptr) != (g_colind == nullptr)) return bail(GSP2_E_ARG, "graph: give both arrays or neither");
     std::string m = check_csr(n, rowptr, colind, true, "H");
@@ -327,6 +394,11 @@ extern "C" gsp2_status gsp2_create(int64_t n, const int64_t* rowptr, const int32
       for (int32_t ti = 0; ti < d.nt; ++ti)
         for (int32_t tj = ti; tj < d.nt; ++tj) h->tiles.push_back(Tile{k, ti, tj, ti == tj ? slot++ : -1});
       for (int32_t j = 0; j < d.nt * SQ_TILE; j += COLS_PER_BLOCK) h->gblocks.push_back(ColBlock{k, j});
+      for (int32_t j = 0; j < d.ld; j += COLS_PER_BLOCK) h->gblocks_ld.push_back(ColBlock{k, j});
+      const int32_t nt128 = (d.s + TC_TILE - 1) / TC_TILE;
+      for (int32_t ti = 0; ti < nt128; ++ti)
+        for (int32_t tj = ti; tj < nt128; ++tj)
+          h->tc_tiles.push_back(Tile{k, ti, tj, ti == tj ? h->nslots_tc++ : -1});
       for (int32_t j = 0; j < d.c; j += COLS_PER_BLOCK) h->sblocks.push_back(ColBlock{k, j});
     }
     h->nslots = slot;
@@ -429,13 +501,39 @@ extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t byt
   for (size_t i = 0; i < tab.size(); ++i) tab[i] = (const double*)(h->ws + h->step_arena_off[i]);
   CU(h, up(L.step_arena, tab.data(), tab.size() * sizeof(double*)));
   CU(h, up(L.tiles, h->tiles.data(), h->tiles.size() * sizeof(Tile)));
+  CU(h, up(L.tc_tiles, h->tc_tiles.data(), h->tc_tiles.size() * sizeof(Tile)));
+  CU(h, up(L.gblocks_ld, h->gblocks_ld.data(), h->gblocks_ld.size() * sizeof(ColBlock)));
+  if (h->opt.precision != GSP2_PREC_FP64) {
+    std::vector<const float*> mt((size_t)h->opt.max_steps + 1);
+    for (size_t i = 0; i < mt.size(); ++i) mt[i] = (const float*)(h->ws + L.mf[i & 1]);
+    CU(h, up(L.master_of_step, mt.data(), mt.size() * sizeof(float*)));
+    const int kind = prec_kind(h->opt.precision), nprod = prec_nprod(h->opt.precision);
+    if (kind >= 0) {
+      void* enc = nullptr;
+      cudaDriverEntryPointQueryResult q{};
+      CU(h, cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &enc, 12000, cudaEnableDefault, &q));
+      if (!enc || q != cudaDriverEntryPointSuccess)
+        return fail(h, GSP2_E_CUDA, "cuTensorMapEncodeTiled not available from the driver");
+      const size_t np = h->parts.size();
+      std::vector<unsigned char> maps(4 * np * 128, 0);
+      for (int b = 0; b < 2; ++b) {
+        int r = encode_part_maps(enc, maps.data() + (size_t)(2 * b + 0) * np * 128, h->parts.data(), (int)np,
+                                 h->ws + L.op_hi[b], kind);
+        if (r == 0 && nprod == 3)
+          r = encode_part_maps(enc, maps.data() + (size_t)(2 * b + 1) * np * 128, h->parts.data(), (int)np,
+                               h->ws + L.op_lo[b], kind);
+        if (r != 0) return fail(h, GSP2_E_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string(r));
+      }
+      CU(h, up(L.maps, maps.data(), maps.size()));
+    }
+  }
   CU(h, up(L.gblocks, h->gblocks.data(), h->gblocks.size() * sizeof(ColBlock)));
   CU(h, up(L.sblocks, h->sblocks.data(), h->sblocks.size() * sizeof(ColBlock)));
   CU(h, up(L.pcolptr, h->pcolptr.data(), h->pcolptr.size() * sizeof(int64_t)));
   CU(h, up(L.rowptr, h->rowptr.data(), h->rowptr.size() * sizeof(int64_t)));
   CU(h, up(L.colind, h->colind.data(), h->colind.size() * sizeof(int32_t)));
   CU(h, cudaMemsetAsync(h->ws + L.state, 0, sizeof(DevState), s));
-  CU(h, cudaMemsetAsync(h->ws + L.alpha, 0, (size_t)h->opt.max_steps + 2, s));
+  CU(h, cudaMemsetAsync(h->ws + L.alpha, 0, (size_t)h->opt.max_steps + HIST_EXTRA, s));
   // the uploads read pageable host vectors; finish them before the call returns
   CU(h, cudaStreamSynchronize(s));
   return GSP2_OK;
@@ -461,18 +559,66 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
   auto A = [&](int i) { return (double*)(w + h->step_arena_off[i]); };
   StepCtl ctl{st, alpha, (double*)(w + L.traces), (double*)(w + L.idem), h->nocc, h->opt.idem_tol,
               h->opt.trace_tol, mode, mode == MODE_REPLAY ? nsteps : h->opt.max_steps};
-  CU(h, launch_reset(st, alpha, mode == MODE_REPLAY ? alpha_user : nullptr, nsteps, h->opt.max_steps + 2, s));
+  CU(h, launch_reset(st, alpha, mode == MODE_REPLAY ? alpha_user : nullptr, nsteps, h->opt.max_steps + HIST_EXTRA, s));
   CU(h, launch_bounds(h->n, rp, ci, hv, slots, BOUNDS_BLOCKS, st, s));
+  const int prec = h->opt.precision;
+  if (prec != GSP2_PREC_FP64) {
+    // low-precision phase, stopping test gated at max(idem_tol, 16 N u)
+    const int kind = prec_kind(prec), nprod = prec_nprod(prec);
+    StepCtl lp = ctl;
+    lp.idem_tol = std::max(h->opt.idem_tol, 16.0 * (double)h->n * prec_unit(prec));
+    float* mf[2] = {(float*)(w + L.mf[0]), (float*)(w + L.mf[1])};
+    void* oh[2] = {w + L.op_hi[0], w + L.op_hi[1]};
+    void* ol[2] = {w + L.op_lo[0], w + L.op_lo[1]};
+    CU(h, launch_gather_lp(kind, nprod, parts, (const ColBlock*)(w + L.gblocks_ld), (int)h->gblocks_ld.size(), Sall,
+                           rp, ci, hv, mf[0], kind >= 0 ? oh[0] : nullptr, nprod == 3 ? ol[0] : nullptr,
+                           (double*)slots, lp, s));
+    const size_t np = h->parts.size();
+    for (int i = 1; i <= lp.last_step; ++i) {
+      const int bi = (i - 1) & 1, bo = i & 1;
+      if (!h->ev.empty()) CU(h, cudaEventRecordWithFlags(h->ev[2 * (i - 1)], s, cudaEventRecordExternal));
+      if (kind < 0) {
+        CU(h, launch_square_fp32(parts, tiles, (int)h->tiles.size(), mf[bi], mf[bo], slots, h->nslots, lp, i, s));
+      } else {
+        TcStepArgs a{};
+        a.parts = parts;
+        a.tiles = (const Tile*)(w + L.tc_tiles);
+        a.map_hi = w + L.maps + (size_t)(2 * bi + 0) * np * 128;
+        a.map_lo = w + L.maps + (size_t)(2 * bi + 1) * np * 128;
+        a.xin = mf[bi];
+        a.xout = mf[bo];
+        a.op_hi_out = oh[bo];
+        a.op_lo_out = nprod == 3 ? ol[bo] : nullptr;
+        a.slots = slots;
+        a.nslots = h->nslots_tc;
+        a.ctl = lp;
+        a.step = i;
+        CU(h, launch_square_tc(kind, nprod, a, (int)h->tc_tiles.size(), s));
+      }
+      if (!h->ev.empty()) CU(h, cudaEventRecordWithFlags(h->ev[2 * (i - 1) + 1], s, cudaEventRecordExternal));
+    }
+    // FP64 tail: convert the last FP32 iterate, then purification steps in FP64
+    double* d[2] = {(double*)(w + L.d[0]), (double*)(w + L.d[1])};
+    CU(h, launch_convert((const float* const*)(w + L.master_of_step), d[0], h->arena_elems, st, s));
+    const int T = h->opt.fp64_tail_steps;
+    for (int t = 0; t < T; ++t)
+      CU(h, launch_square_fp64(parts, tiles, (int)h->tiles.size(), d[t & 1], d[(t + 1) & 1], slots, h->nslots, ctl, 0,
+                               t == 0 ? SQ_TAIL_FIRST : SQ_TAIL_NEXT, s));
+    CU(h, launch_scatter(parts, sbl, (int)h->sblocks.size(), Sall, perm, pcol, nullptr, d[T & 1], pv, st, s));
+    if (alpha_user)
+      CU(h, cudaMemcpyAsync(alpha_user, alpha + 1, (size_t)h->opt.max_steps, cudaMemcpyDeviceToDevice, s));
+    return GSP2_OK;
+  }
   CU(h, launch_gather(parts, gbl, (int)h->gblocks.size(), Sall, rp, ci, hv, A(0), (double*)slots, ctl, s));
   for (int i = 1; i <= ctl.last_step; ++i) {
     const double* xin = A(i - 1);
     double* xout = A(i);
     if (!h->ev.empty()) CU(h, cudaEventRecordWithFlags(h->ev[2 * (i - 1)], s, cudaEventRecordExternal));
-    CU(h, launch_square_fp64(parts, tiles, (int)h->tiles.size(), xin, xout, slots, h->nslots, ctl, i, 0, s));
+    CU(h, launch_square_fp64(parts, tiles, (int)h->tiles.size(), xin, xout, slots, h->nslots, ctl, i, SQ_FORWARD, s));
     if (!h->ev.empty()) CU(h, cudaEventRecordWithFlags(h->ev[2 * (i - 1) + 1], s, cudaEventRecordExternal));
   }
   CU(h, launch_scatter(parts, sbl, (int)h->sblocks.size(), Sall, perm, pcol, (const double* const*)(w + L.step_arena),
-                       pv, st, s));
+                       nullptr, pv, st, s));
   if (mode == MODE_RECORD && alpha_user)
     CU(h, cudaMemcpyAsync(alpha_user, alpha + 1, (size_t)h->opt.max_steps, cudaMemcpyDeviceToDevice, s));
   return GSP2_OK;
@@ -486,6 +632,8 @@ extern "C" gsp2_status gsp2_density(gsp2_handle h, const double* d_hvals, double
   if (mode != MODE_RECORD && mode != MODE_REPLAY) return fail(h, GSP2_E_ARG, "mode must be RECORD or REPLAY");
   if (mode == MODE_REPLAY && (!d_alpha || nsteps < 1 || nsteps > h->opt.max_steps))
     return fail(h, GSP2_E_ARG, "REPLAY needs d_alpha and 1 <= nsteps <= max_steps");
+  if (mode == MODE_REPLAY && h->opt.precision != GSP2_PREC_FP64)
+    return fail(h, GSP2_E_ARG, "REPLAY is available for the FP64 precision only");
   if (mode == MODE_RECORD) nsteps = 0;
   int dev = 0;
   CU(h, cudaGetDevice(&dev));
@@ -546,6 +694,7 @@ extern "C" gsp2_status gsp2_sync_status(gsp2_handle h, gsp2_report* r) {
     const char* what = st.status == ST_NOT_CONVERGED ? "not converged within max_steps"
                        : st.status == ST_TRACE       ? "replayed sequence gave the wrong trace"
                        : st.status == ST_NONFINITE   ? "non-finite value in H, bounds or traces"
+                       : st.status == ST_TIMEOUT     ? "a bounded device wait gave up"
                                                      : "device error";
     h->err = what;
   }
@@ -557,12 +706,10 @@ extern "C" gsp2_status gsp2_history(gsp2_handle h, double* traces, double* idem,
   if (!h->ws || !h->have_forward) return fail(h, GSP2_E_STATE, "no density call");
   if (cap < 0) return fail(h, GSP2_E_ARG, "cap < 0");
   CU(h, cudaDeviceSynchronize());
-  const size_t m = (size_t)std::min<int32_t>(cap, h->opt.max_steps + 1);
+  const size_t m = (size_t)std::min<int32_t>(cap, h->opt.max_steps + MAX_TAIL + 1);
   if (traces) CU(h, cudaMemcpy(traces, h->ws + h->L.traces, m * sizeof(double), cudaMemcpyDeviceToHost));
-  if (idem) CU(h, cudaMemcpy(idem, h->ws + h->L.idem, std::min<size_t>(m, h->opt.max_steps) * sizeof(double),
-                             cudaMemcpyDeviceToHost));
-  if (alpha) CU(h, cudaMemcpy(alpha, h->ws + h->L.alpha + 1, std::min<size_t>(m, h->opt.max_steps),
-                              cudaMemcpyDeviceToHost));
+  if (idem) CU(h, cudaMemcpy(idem, h->ws + h->L.idem, m * sizeof(double), cudaMemcpyDeviceToHost));
+  if (alpha) CU(h, cudaMemcpy(alpha, h->ws + h->L.alpha + 1, m, cudaMemcpyDeviceToHost));
   return GSP2_OK;
 }
 
@@ -609,7 +756,7 @@ static gsp2_status enqueue_backward(gsp2_plan* h, const double* pbar, double* hb
     for (int j = 1; j < k && c0 + j < M; ++j) {
       const double* xin = (j == 1) ? ck : (const double*)(w + L.seg[j - 2]);
       double* xout = (double*)(w + L.seg[j - 1]);
-      CU(h, launch_square_fp64(parts, tiles, nt, xin, xout, nullptr, 0, ctl, c0 + j, 1, s));
+      CU(h, launch_square_fp64(parts, tiles, nt, xin, xout, nullptr, 0, ctl, c0 + j, SQ_RECOMPUTE, s));
     }
     for (int i = std::min(c0 + k, M); i >= c0 + 1; --i) {
       const double* X = (i - 1 == c0) ? ck : (const double*)(w + L.seg[i - 1 - c0 - 1]);
@@ -624,7 +771,8 @@ static gsp2_status enqueue_backward(gsp2_plan* h, const double* pbar, double* hb
 
 extern "C" gsp2_status gsp2_backward(gsp2_handle h, const double* d_pbar, double* d_hbar, void* stream) {
   if (!usable(h)) return fail(h, GSP2_E_ARG, "invalid handle");
-  if (h->opt.ckpt_every <= 0) return fail(h, GSP2_E_STATE, "plan built with ckpt_every = 0: no adjoint");
+  if (h->opt.ckpt_every <= 0 || h->opt.precision != GSP2_PREC_FP64)
+    return fail(h, GSP2_E_STATE, "the adjoint needs an FP64 plan built with ckpt_every > 0");
   if (!h->ws || !h->have_forward) return fail(h, GSP2_E_STATE, "gsp2_backward needs a completed density call");
   if (!d_pbar || !d_hbar) return fail(h, GSP2_E_ARG, "NULL Pbar or Hbar buffer");
   int dev = 0;

@@ -15,6 +15,7 @@ namespace gsp2 {
 
 constexpr int LD_PAD = 128;      // ld_k multiple (tile edge of every square kernel)
 constexpr int SQ_TILE = 64;      // FP64 square tile edge
+constexpr int TC_TILE = 128;     // tensor-core square tile edge
 constexpr int COLS_PER_BLOCK = 8;  // gather/scatter: one warp per column, 8 warps
 
 struct PartDesc {
@@ -44,11 +45,13 @@ struct DevState {
   int32_t status;      // gsp2_status detected on the device
   int32_t nonfinite;   // set by any block that meets NaN/Inf
   int32_t fp64_steps;
-  int32_t pad[6];
+  int32_t timeout;     // a bounded device wait gave up
+  int32_t pad[5];
 };
 
-enum : int32_t { ST_OK = 0, ST_NOT_CONVERGED = 5, ST_TRACE = 6, ST_NONFINITE = 7 };
+enum : int32_t { ST_OK = 0, ST_NOT_CONVERGED = 5, ST_TRACE = 6, ST_NONFINITE = 7, ST_TIMEOUT = 9 };
 enum : int32_t { MODE_RECORD = 0, MODE_REPLAY = 1 };
+enum : int32_t { SQ_FORWARD = 0, SQ_RECOMPUTE = 1, SQ_TAIL_FIRST = 2, SQ_TAIL_NEXT = 3 };
 
 // Arguments of the per-step trace bookkeeping done by the last block of a step.
 struct StepCtl {
@@ -61,6 +64,22 @@ struct StepCtl {
   double trace_tol;
   int32_t mode;
   int32_t last_step;  // max_steps (RECORD) or nsteps (REPLAY)
+};
+
+// Arguments of one tensor-core purification step (k_tc.cu).
+struct TcStepArgs {
+  const PartDesc* parts;
+  const Tile* tiles;       // 128x128 upper tiles
+  const void* map_hi;      // CUtensorMap[nparts] over the input operand arena (hi part)
+  const void* map_lo;      // CUtensorMap[nparts] over the input lo arena (split mode)
+  const float* xin;        // FP32 master of X_{step-1}
+  float* xout;             // FP32 master of X_step
+  void* op_hi_out;         // operand arenas of X_step
+  void* op_lo_out;
+  double2* slots;
+  int nslots;
+  StepCtl ctl;
+  int step;
 };
 
 // ------------------------------------------------------------------ device helpers
@@ -167,6 +186,20 @@ __device__ __forceinline__ void finish_step(const StepCtl& c, int step, double t
     }
   } else if (c.mode == MODE_RECORD) {
     c.alpha[step + 1] = (tN <= (double)c.nocc) ? (int8_t)1 : (int8_t)-1;
+  }
+}
+
+// Bookkeeping of an FP64 tail step of a low-precision run: records T_step, e_{step-1}
+// and the step count; no stopping test and no branch choice.
+__device__ __forceinline__ void finish_tail(const StepCtl& c, int step, double tN, double tY) {
+  DevState* st = c.st;
+  c.traces[step] = tN;
+  c.idem[step - 1] = c.traces[step - 1] - tY;
+  st->steps = step;
+  st->fp64_steps += 1;
+  if (!isfinite(tN) || !isfinite(c.idem[step - 1])) {
+    st->nonfinite = 1;
+    st->status = ST_NONFINITE;
   }
 }
 

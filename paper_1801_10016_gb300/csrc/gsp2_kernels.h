@@ -13,11 +13,23 @@ cudaError_t launch_gather(const PartDesc* parts, const ColBlock* blocks, int nbl
                           const int64_t* rowptr, const int32_t* colind, const double* vals, double* arena,
                           double* slots, const StepCtl& ctl, cudaStream_t s);
 cudaError_t launch_square_fp64(const PartDesc* parts, const Tile* tiles, int ntiles, const double* xin,
-                               double* xout, double2* slots, int nslots, const StepCtl& ctl, int step,
-                               int recompute, cudaStream_t s);
+                               double* xout, double2* slots, int nslots, const StepCtl& ctl, int step, int mode,
+                               cudaStream_t s);
+cudaError_t launch_square_fp32(const PartDesc* parts, const Tile* tiles, int ntiles, const float* xin, float* xout,
+                               double2* slots, int nslots, const StepCtl& ctl, int step, cudaStream_t s);
 cudaError_t launch_scatter(const PartDesc* parts, const ColBlock* blocks, int nblocks, const int32_t* Sall,
                            const int32_t* perm, const int64_t* pcolptr, const double* const* arena_of_step,
-                           double* pvals, const DevState* st, cudaStream_t s);
+                           const double* fixed_arena, double* pvals, const DevState* st, cudaStream_t s);
+
+// low-precision paths (k_tc.cu)
+cudaError_t launch_square_tc(int kind, int nprod, const TcStepArgs& a, int ntiles, cudaStream_t s);
+cudaError_t launch_gather_lp(int kind, int nprod, const PartDesc* parts, const ColBlock* blocks, int nblocks,
+                             const int32_t* Sall, const int64_t* rowptr, const int32_t* colind, const double* vals,
+                             float* master, void* op_hi, void* op_lo, double* slots, const StepCtl& ctl,
+                             cudaStream_t s);
+cudaError_t launch_convert(const float* const* master_of_step, double* out, int64_t n, const DevState* st,
+                           cudaStream_t s);
+int encode_part_maps(void* enc_fn, void* out_maps, const PartDesc* parts, int nparts, void* arena, int kind);
 
 // adjoint (k_adjoint.cu)
 cudaError_t launch_adj_seed(const PartDesc* parts, const ColBlock* blocks, int nblocks, const int32_t* Sall,

@@ -67,6 +67,7 @@ __global__ void reset_kernel(DevState* st, int8_t* alpha, const int8_t* alpha_in
     st->status = ST_OK;
     st->nonfinite = 0;
     st->fp64_steps = 0;
+    st->timeout = 0;
     st->counter = 0;
   }
   for (int i = threadIdx.x; i < n_alpha; i += blockDim.x)
@@ -129,7 +130,8 @@ __global__ void __launch_bounds__(256) gather_kernel(const PartDesc* __restrict_
 }
 
 // ------------------------------------------------------------------------------------
-// One purification step for every part (Eq. 2), FP64 on the CUDA cores.
+// One purification step for every part (Eq. 2) on the CUDA cores, T = double (FP64
+// path and the FP64 tail of the low-precision paths) or float (FP32 path).
 //
 // Work item = one upper-triangular 64x64 output tile (ti <= tj) of one part.  X is
 // symmetric, so both operands of Y = X X stream from columns of X: the A slice
@@ -137,54 +139,76 @@ __global__ void __launch_bounds__(256) gather_kernel(const PartDesc* __restrict_
 // Each of the 256 threads owns a 4x4 block of the tile; 16-wide K slices are double
 // buffered in shared memory with cp.async.
 // Epilogue: X_new = Y (alpha = -1) or 2 X - Y (alpha = +1), written to (I, J) and
-// mirrored to (J, I); diagonal tiles add Tr_core[Y] and Tr_core[X_new] to their slot.
-// The last block sums the slots in a fixed order and runs finish_step.
+// mirrored to (J, I); diagonal tiles add Tr_core[Y] and Tr_core[X_new] (FP64) to their
+// slot.  The last block sums the slots in a fixed order and runs the bookkeeping.
+//
+// mode: SQ_FORWARD   - step `step`; nothing to do once the loop has stopped;
+//       SQ_RECOMPUTE - adjoint: rebuild X_step from X_{step-1} with the recorded branch
+//                      if step < steps applied; no bookkeeping;
+//       SQ_TAIL_FIRST/SQ_TAIL_NEXT - FP64 tail of a low-precision run: step = steps+1;
+//                      the first tail step takes its branch from the trace rule, each
+//                      further one the opposite of the previous, so that eigenvalues
+//                      near 0 and near 1 are both purified.
 // ------------------------------------------------------------------------------------
 constexpr int BK = 16;
 
-__global__ void __launch_bounds__(256, 2) square_fp64_kernel(const PartDesc* __restrict__ parts,
+template <typename T>
+struct Vec2;
+template <>
+struct Vec2<double> {
+  using V = double2;
+};
+template <>
+struct Vec2<float> {
+  using V = float2;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256, 2) square_simt_kernel(const PartDesc* __restrict__ parts,
                                                              const Tile* __restrict__ tiles,
-                                                             const double* __restrict__ xin,
-                                                             double* __restrict__ xout,
-                                                             double2* __restrict__ slots, int nslots,
-                                                             StepCtl ctl, int step, int recompute) {
-  // forward: nothing to do once the loop has stopped.  recompute (adjoint): rebuild
-  // X_step from X_{step-1} with the recorded branch, only if step < steps applied,
-  // with no trace bookkeeping.  Both tests are uniform over the launch.
-  if (recompute) {
+                                                             const T* __restrict__ xin, T* __restrict__ xout,
+                                                             double2* __restrict__ slots, int nslots, StepCtl ctl,
+                                                             int step, int mode) {
+  using V2 = typename Vec2<T>::V;
+  if (mode == SQ_RECOMPUTE) {
     if (step >= *(volatile int32_t*)&ctl.st->steps) return;
-  } else if (*(volatile int32_t*)&ctl.st->stopped) {
-    return;
+  } else if (mode == SQ_FORWARD) {
+    if (*(volatile int32_t*)&ctl.st->stopped) return;
+  } else {
+    const int32_t stt = *(volatile int32_t*)&ctl.st->status;
+    if (stt == ST_NONFINITE || stt == ST_TIMEOUT) return;
+    step = *(volatile int32_t*)&ctl.st->steps + 1;
   }
-  __shared__ __align__(16) double As[2][BK][SQ_TILE];
-  __shared__ __align__(16) double Bs[2][BK][SQ_TILE];
+  __shared__ __align__(16) T As[2][BK][SQ_TILE];
+  __shared__ __align__(16) T Bs[2][BK][SQ_TILE];
   const Tile t = tiles[blockIdx.x];
   const PartDesc p = parts[t.part];
-  const double* X = xin + p.off;
+  const T* X = xin + p.off;
   const int64_t ld = p.ld;
   const int r0 = t.ti * SQ_TILE, c0 = t.tj * SQ_TILE;
   const int kend = (p.s + BK - 1) / BK * BK;
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
+  constexpr int EPC = 16 / sizeof(T);             // elements per 16-byte chunk
+  constexpr int CPR = SQ_TILE / EPC;              // chunks per slice row
+  constexpr int CHUNKS = BK * CPR;                // chunks per operand slice
 
-  // loader mapping: 512 16-byte chunks per operand slice, two per thread
   auto load_slice = [&](int buf, int k0) {
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int q = tid + h * 256;
-      const int kr = q >> 5, c2 = (q & 31) * 2;
-      const double* col = X + (int64_t)(k0 + kr) * ld;
+    for (int q = tid; q < CHUNKS; q += 256) {
+      const int kr = q / CPR, c2 = (q % CPR) * EPC;
+      const T* col = X + (int64_t)(k0 + kr) * ld;
       cp_async16(&As[buf][kr][c2], col + r0 + c2);
       cp_async16(&Bs[buf][kr][c2], col + c0 + c2);
     }
     cp_async_commit();
   };
 
-  double acc[4][4];
+  T acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int jj = 0; jj < 4; ++jj) acc[i][jj] = 0.0;
+    for (int jj = 0; jj < 4; ++jj) acc[i][jj] = T(0);
 
   const int nk = kend / BK;
   load_slice(0, 0);
@@ -199,12 +223,12 @@ __global__ void __launch_bounds__(256, 2) square_fp64_kernel(const PartDesc* __r
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      const double2 a01 = *reinterpret_cast<const double2*>(&As[buf][kk][tx * 4]);
-      const double2 a23 = *reinterpret_cast<const double2*>(&As[buf][kk][tx * 4 + 2]);
-      const double2 b01 = *reinterpret_cast<const double2*>(&Bs[buf][kk][ty * 4]);
-      const double2 b23 = *reinterpret_cast<const double2*>(&Bs[buf][kk][ty * 4 + 2]);
-      const double a[4] = {a01.x, a01.y, a23.x, a23.y};
-      const double b[4] = {b01.x, b01.y, b23.x, b23.y};
+      const V2 a01 = *reinterpret_cast<const V2*>(&As[buf][kk][tx * 4]);
+      const V2 a23 = *reinterpret_cast<const V2*>(&As[buf][kk][tx * 4 + 2]);
+      const V2 b01 = *reinterpret_cast<const V2*>(&Bs[buf][kk][ty * 4]);
+      const V2 b23 = *reinterpret_cast<const V2*>(&Bs[buf][kk][ty * 4 + 2]);
+      const T a[4] = {a01.x, a01.y, a23.x, a23.y};
+      const T b[4] = {b01.x, b01.y, b23.x, b23.y};
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -213,36 +237,50 @@ __global__ void __launch_bounds__(256, 2) square_fp64_kernel(const PartDesc* __r
     __syncthreads();
   }
 
-  // epilogue
-  const int8_t al = ctl.alpha[step];
-  double* Y = xout + p.off;
+  // branch of this step
+  int8_t al;
+  if (mode == SQ_TAIL_FIRST) al = (ctl.traces[step - 1] <= (double)ctl.nocc) ? (int8_t)1 : (int8_t)-1;
+  else if (mode == SQ_TAIL_NEXT) al = (int8_t)(-ctl.alpha[step - 1]);
+  else al = ctl.alpha[step];
+  const bool book = mode != SQ_RECOMPUTE;
+
+  T* Y = xout + p.off;
   double tY = 0.0, tN = 0.0;
   const int rb = r0 + tx * 4, cb = c0 + ty * 4;
 #pragma unroll
   for (int jj = 0; jj < 4; ++jj) {
     const int c = cb + jj;
-    const double2 x01 = *reinterpret_cast<const double2*>(X + (int64_t)c * ld + rb);
-    const double2 x23 = *reinterpret_cast<const double2*>(X + (int64_t)c * ld + rb + 2);
-    const double xv[4] = {x01.x, x01.y, x23.x, x23.y};
+    const V2 x01 = *reinterpret_cast<const V2*>(X + (int64_t)c * ld + rb);
+    const V2 x23 = *reinterpret_cast<const V2*>(X + (int64_t)c * ld + rb + 2);
+    const T xv[4] = {x01.x, x01.y, x23.x, x23.y};
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const double y = acc[i][jj];
-      const double xn = (al > 0) ? (2.0 * xv[i] - y) : y;
-      if (!recompute && t.slot >= 0 && rb + i == c && c < p.c) { tY += y; tN += xn; }
+      const T y = acc[i][jj];
+      const T xn = (al > 0) ? (T(2) * xv[i] - y) : y;
+      if (book && t.slot >= 0 && rb + i == c && c < p.c) {
+        tY += (double)y;
+        tN += (double)xn;
+      }
       acc[i][jj] = xn;
     }
-    *reinterpret_cast<double2*>(Y + (int64_t)c * ld + rb) = make_double2(acc[0][jj], acc[1][jj]);
-    *reinterpret_cast<double2*>(Y + (int64_t)c * ld + rb + 2) = make_double2(acc[2][jj], acc[3][jj]);
+    V2 v;
+    v.x = acc[0][jj]; v.y = acc[1][jj];
+    *reinterpret_cast<V2*>(Y + (int64_t)c * ld + rb) = v;
+    v.x = acc[2][jj]; v.y = acc[3][jj];
+    *reinterpret_cast<V2*>(Y + (int64_t)c * ld + rb + 2) = v;
   }
   if (t.ti != t.tj) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int r = rb + i;
-      *reinterpret_cast<double2*>(Y + (int64_t)r * ld + cb) = make_double2(acc[i][0], acc[i][1]);
-      *reinterpret_cast<double2*>(Y + (int64_t)r * ld + cb + 2) = make_double2(acc[i][2], acc[i][3]);
+      V2 v;
+      v.x = acc[i][0]; v.y = acc[i][1];
+      *reinterpret_cast<V2*>(Y + (int64_t)r * ld + cb) = v;
+      v.x = acc[i][2]; v.y = acc[i][3];
+      *reinterpret_cast<V2*>(Y + (int64_t)r * ld + cb + 2) = v;
     }
   }
-  if (recompute) return;
+  if (!book) return;
   if (t.slot >= 0) {
     const double2 s = block_sum2(tY, tN);
     if (tid == 0) slots[t.slot] = s;
@@ -255,7 +293,12 @@ __global__ void __launch_bounds__(256, 2) square_fp64_kernel(const PartDesc* __r
     }
     const double2 s = block_sum2(a, b);
     if (tid == 0) {
-      finish_step(ctl, step, s.y, s.x);
+      if (mode == SQ_FORWARD) {
+        finish_step(ctl, step, s.y, s.x);
+      } else {
+        ctl.alpha[step] = al;
+        finish_tail(ctl, step, s.y, s.x);
+      }
       ctl.st->counter = 0;
     }
   }
@@ -272,13 +315,15 @@ __global__ void __launch_bounds__(256) scatter_kernel(const PartDesc* __restrict
                                                       const int32_t* __restrict__ perm,
                                                       const int64_t* __restrict__ pcolptr,
                                                       const double* const* __restrict__ arena_of_step,
+                                                      const double* __restrict__ fixed_arena,
                                                       double* __restrict__ pvals, const DevState* st) {
   const ColBlock b = blocks[blockIdx.x];
   const PartDesc p = parts[b.part];
   const int j = b.j0 + (threadIdx.x >> 5);
   if (j >= p.c) return;
   const int lane = threadIdx.x & 31;
-  const double* X = arena_of_step[st->steps] + p.off + (int64_t)j * p.ld;
+  const double* A = fixed_arena ? fixed_arena : arena_of_step[st->steps];
+  const double* X = A + p.off + (int64_t)j * p.ld;
   const int32_t g = Sall[p.soff + j];
   const int32_t* pm = perm + p.soff;
   double* out = pvals + pcolptr[g];
@@ -309,17 +354,23 @@ cudaError_t launch_gather(const PartDesc* parts, const ColBlock* blocks, int nbl
 }
 
 cudaError_t launch_square_fp64(const PartDesc* parts, const Tile* tiles, int ntiles, const double* xin,
-                               double* xout, double2* slots, int nslots, const StepCtl& ctl, int step,
-                               int recompute, cudaStream_t s) {
-  square_fp64_kernel<<<ntiles, 256, 0, s>>>(parts, tiles, xin, xout, slots, nslots, ctl, step, recompute);
+                               double* xout, double2* slots, int nslots, const StepCtl& ctl, int step, int mode,
+                               cudaStream_t s) {
+  square_simt_kernel<double><<<ntiles, 256, 0, s>>>(parts, tiles, xin, xout, slots, nslots, ctl, step, mode);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_square_fp32(const PartDesc* parts, const Tile* tiles, int ntiles, const float* xin, float* xout,
+                               double2* slots, int nslots, const StepCtl& ctl, int step, cudaStream_t s) {
+  square_simt_kernel<float><<<ntiles, 256, 0, s>>>(parts, tiles, xin, xout, slots, nslots, ctl, step, SQ_FORWARD);
   return cudaGetLastError();
 }
 
 cudaError_t launch_scatter(const PartDesc* parts, const ColBlock* blocks, int nblocks, const int32_t* Sall,
                            const int32_t* perm, const int64_t* pcolptr, const double* const* arena_of_step,
-                           double* pvals, const DevState* st, cudaStream_t s) {
+                           const double* fixed_arena, double* pvals, const DevState* st, cudaStream_t s) {
   scatter_kernel<<<nblocks, 32 * COLS_PER_BLOCK, 0, s>>>(parts, blocks, Sall, perm, pcolptr, arena_of_step,
-                                                        pvals, st);
+                                                        fixed_arena, pvals, st);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,471 @@
+// Low-precision purification steps on the tcgen05 tensor cores (sm_103a).
+//
+// One launch = one SP2 step (Eq. 2) for every part.  Work item = one upper-triangular
+// 128x128 output tile (ti <= tj) of one part.  Operands are the previous iterate in
+// BF16 or TF32 (pre-rounded, in their own arena); X is symmetric, so both the A tile
+// (rows I) and the B tile (rows J) are K-major slices of columns of X and stream with
+// the same per-part TMA tensor map (128-byte swizzle).  Accumulation is FP32 in TMEM.
+// With NPROD = 3 the operand is split X = hi + lo and Y = hi hi + hi lo + lo hi.
+//
+// Roles (128 threads): warp 0 lane 0 issues TMA loads into a ring of stages, warp 1
+// allocates TMEM and its lane 0 issues tcgen05.mma, then all four warps drain TMEM
+// (warp w owns rows 32w..32w+31), form X_new = Y or 2X - Y against the FP32 master
+// copy, write X_new (master and next operands) to (I, J) and mirrored to (J, I), and
+// add the core-diagonal traces of Y and X_new in FP64.  The last block runs the same
+// FP64 trace/branch/stopping bookkeeping as the FP64 path.
+//
+// Every mbarrier wait is bounded; a wait that gives up sets the device timeout flag,
+// lets the block finish without further waits, frees its TMEM and returns.
+#include <cuda.h>
+
+#include "gsp2_internal.cuh"
+#include "gsp2_kernels.h"
+
+namespace gsp2 {
+
+namespace {
+
+constexpr uint64_t kWaitNs = 200ull * 1000ull * 1000ull;  // 200 ms; normal waits take microseconds
+constexpr uint32_t kTileBytes = 128 * 128;  // 128 rows x 128 bytes
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(bar), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;\n" : "=l"(t));
+  return t;
+}
+
+// Bounded wait: gives up after kWaitNs nanoseconds, or at once when another block
+// has already given up (the shared abort flag), and then raises the flag itself.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int32_t* abort_flag) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t i = 1;; ++i) {
+    if (mbar_try(bar, parity)) return true;
+    if ((i & 255u) == 0u) {
+      if (*(volatile int32_t*)abort_flag != 0 || global_ns() - t0 > kWaitNs) {
+        *(volatile int32_t*)abort_flag = 1;
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+          dst),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major tile, rows of 128 bytes, 128-byte swizzle,
+// 8-row groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)(16 >> 4) << 16;    // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset: next 8-row group
+  d |= (uint64_t)1 << 46;            // descriptor version
+  d |= (uint64_t)2 << 61;            // 128-byte swizzle
+  return d;
+}
+
+template <int KIND>
+__device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  if (KIND == 0) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+
+// operand rounding: BF16 round-to-nearest-even, TF32 round-to-nearest (ties away)
+template <int KIND>
+struct Operand;
+template <>
+struct Operand<0> {
+  static __device__ __forceinline__ uint16_t bits(float x) {
+    uint16_t h;
+    asm("cvt.rn.bf16.f32 %0, %1;\n" : "=h"(h) : "f"(x));
+    return h;
+  }
+  static __device__ __forceinline__ float value(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
+};
+template <>
+struct Operand<1> {
+  static __device__ __forceinline__ uint32_t bits(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
+    return r;
+  }
+  static __device__ __forceinline__ float value(uint32_t b) { return __uint_as_float(b); }
+};
+
+}  // namespace
+
+// Store the operand(s) of x at element index e of the operand arena(s).
+template <int KIND, int NPROD>
+__device__ __forceinline__ void store_operands(void* hi, void* lo, int64_t e, float x) {
+  if (KIND == 0) {
+    const uint16_t h = Operand<0>::bits(x);
+    reinterpret_cast<uint16_t*>(hi)[e] = h;
+    if (NPROD == 3) reinterpret_cast<uint16_t*>(lo)[e] = Operand<0>::bits(x - Operand<0>::value(h));
+  } else {
+    const uint32_t h = Operand<1>::bits(x);
+    reinterpret_cast<uint32_t*>(hi)[e] = h;
+    if (NPROD == 3) reinterpret_cast<uint32_t*>(lo)[e] = Operand<1>::bits(x - Operand<1>::value(h));
+  }
+}
+
+template <int KIND, int NPROD>
+__global__ void __launch_bounds__(128, 1) square_tc_kernel(TcStepArgs a) {
+  constexpr int NOPS = NPROD == 3 ? 4 : 2;
+  constexpr int STAGES = NPROD == 3 ? 2 : 3;
+  constexpr uint32_t STAGE_B = NOPS * kTileBytes;
+  constexpr int ES = KIND == 0 ? 2 : 4;  // operand element bytes
+  constexpr int BKE = 128 / ES;          // K elements per stage (one 128-byte swizzle row)
+  constexpr int KMMA = KIND == 0 ? 16 : 8;
+  constexpr int NMMA = BKE / KMMA;       // MMAs per stage and product (4)
+  // instruction descriptor: FP32 accumulate, A/B format, K-major A and B, N = 128, M = 128
+  constexpr uint32_t FMT = KIND == 0 ? 1u : 2u;
+  constexpr uint32_t IDESC = (1u << 4) | (FMT << 7) | (FMT << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+
+  if (*(volatile int32_t*)&a.ctl.st->stopped) return;
+
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* sb = smem_raw + (base - raw);
+  const uint32_t bars = base + STAGES * STAGE_B;  // full[s], empty[s], done
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sb + STAGES * STAGE_B + 8 * (2 * STAGES + 1));
+  int* s_err = reinterpret_cast<int*>(tmem_slot + 1);
+  auto full = [&](int s) { return bars + 8u * s; };
+  auto empty = [&](int s) { return bars + 8u * (STAGES + s); };
+  const uint32_t done = bars + 8u * (2 * STAGES);
+  auto tile_addr = [&](int s, int op) { return base + (uint32_t)s * STAGE_B + (uint32_t)op * kTileBytes; };
+
+  int32_t* abort_flag = &a.ctl.st->timeout;
+  const Tile t = a.tiles[blockIdx.x];
+  const PartDesc p = a.parts[t.part];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int r0 = t.ti * 128, c0 = t.tj * 128;
+  const int nk = (p.s + BKE - 1) / BKE;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(empty(s), 1);
+    }
+    mbar_init(done, 1);
+    *s_err = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;\n" ::"r"(smem_u32(tmem_slot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // producer
+    const CUtensorMap* mhi = reinterpret_cast<const CUtensorMap*>(a.map_hi) + t.part;
+    const CUtensorMap* mlo = reinterpret_cast<const CUtensorMap*>(a.map_lo) + t.part;
+    int issued = 0;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      if (kb >= STAGES && !mbar_wait(empty(s), ((kb / STAGES) - 1) & 1, abort_flag)) {
+        *s_err = 1;
+        break;
+      }
+      mbar_expect_tx(full(s), STAGE_B);
+      const int k0 = kb * BKE;
+      tma_load_2d(tile_addr(s, 0), mhi, k0, r0, full(s));
+      tma_load_2d(tile_addr(s, 1), mhi, k0, c0, full(s));
+      if (NPROD == 3) {
+        tma_load_2d(tile_addr(s, 2), mlo, k0, r0, full(s));
+        tma_load_2d(tile_addr(s, 3), mlo, k0, c0, full(s));
+      }
+      issued = kb + 1;
+    }
+    // do not leave while copies are in flight: wait (bounded) for the last stages issued
+    for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb) {
+      if (!mbar_wait(full(kb % STAGES), (kb / STAGES) & 1, abort_flag)) *s_err = 1;
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      if (!mbar_wait(full(s), (kb / STAGES) & 1, abort_flag)) {
+        *s_err = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint64_t ah = smem_desc(tile_addr(s, 0)), bh = smem_desc(tile_addr(s, 1));
+      const uint64_t al = smem_desc(tile_addr(s, 2)), bl = smem_desc(tile_addr(s, 3));
+#pragma unroll
+      for (int kk = 0; kk < NMMA; ++kk) {
+        const uint64_t adv = (uint64_t)((kk * KMMA * ES) >> 4);
+        mma<KIND>(tmem, ah + adv, bh + adv, IDESC, (kb > 0 || kk > 0) ? 1u : 0u);
+        if (NPROD == 3) {
+          mma<KIND>(tmem, ah + adv, bl + adv, IDESC, 1u);
+          mma<KIND>(tmem, al + adv, bh + adv, IDESC, 1u);
+        }
+      }
+      mma_commit(empty(s));
+    }
+    mma_commit(done);
+  }
+  __syncwarp();
+
+  // epilogue
+  const bool ok = mbar_wait(done, 0, abort_flag);
+  if (!ok) *s_err = 1;
+  tc_fence_after();
+  const int8_t al = a.ctl.alpha[a.step];
+  const float* Xi = a.xin + p.off;
+  float* Xo = a.xout + p.off;
+  const int64_t ld = p.ld;
+  const int m = warp * 32 + lane;
+  const int r = r0 + m;
+  const bool diag = t.slot >= 0;
+  double tY = 0.0, tN = 0.0;
+  if (ok) {
+#pragma unroll 1
+    for (int cb = 0; cb < 4; ++cb) {
+      uint32_t v[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cb * 32), v);
+      float xn[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int c = c0 + cb * 32 + j;
+        const int64_t e = (int64_t)c * ld + r;
+        const float y = __uint_as_float(v[j]);
+        const float x = Xi[e];
+        const float z = (al > 0) ? (2.0f * x - y) : y;
+        xn[j] = z;
+        Xo[e] = z;
+        store_operands<KIND, NPROD>(a.op_hi_out, a.op_lo_out, p.off + e, z);
+        if (diag && c == r && r < p.c) {
+          tY += (double)y;
+          tN += (double)z;
+        }
+      }
+      if (t.ti != t.tj) {
+        const int64_t e0 = (int64_t)r * ld + c0 + cb * 32;
+        float4* dst = reinterpret_cast<float4*>(Xo + e0);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) dst[q] = make_float4(xn[4 * q], xn[4 * q + 1], xn[4 * q + 2], xn[4 * q + 3]);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) store_operands<KIND, NPROD>(a.op_hi_out, a.op_lo_out, p.off + e0 + j, xn[j]);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;\n" ::"r"(tmem));
+  if (threadIdx.x == 0 && *s_err) a.ctl.st->timeout = 1;
+
+  if (diag) {
+    const double2 sum = block_sum2(tY, tN);
+    if (threadIdx.x == 0) a.slots[t.slot] = sum;
+  }
+  if (last_block_ticket(&a.ctl.st->counter)) {
+    double u = 0.0, w = 0.0;
+    for (int k = threadIdx.x; k < a.nslots; k += blockDim.x) {
+      u += ld_cg(&a.slots[k].x);
+      w += ld_cg(&a.slots[k].y);
+    }
+    const double2 sum = block_sum2(u, w);
+    if (threadIdx.x == 0) {
+      if (a.ctl.st->timeout) {
+        a.ctl.st->status = ST_TIMEOUT;
+        a.ctl.st->stopped = 1;
+      } else {
+        finish_step(a.ctl, a.step, sum.y, sum.x);
+      }
+      a.ctl.st->counter = 0;
+    }
+  }
+}
+
+template <int KIND, int NPROD>
+static cudaError_t launch_tc(const TcStepArgs& a, int ntiles, cudaStream_t s) {
+  constexpr int NOPS = NPROD == 3 ? 4 : 2;
+  constexpr int STAGES = NPROD == 3 ? 2 : 3;
+  const int smem = STAGES * NOPS * (int)kTileBytes + 1024 + 8 * (2 * STAGES + 1) + 16;
+  cudaError_t e = cudaFuncSetAttribute(square_tc_kernel<KIND, NPROD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  square_tc_kernel<KIND, NPROD><<<ntiles, 128, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_square_tc(int kind, int nprod, const TcStepArgs& a, int ntiles, cudaStream_t s) {
+  if (kind == 0 && nprod == 1) return launch_tc<0, 1>(a, ntiles, s);
+  if (kind == 0 && nprod == 3) return launch_tc<0, 3>(a, ntiles, s);
+  if (kind == 1 && nprod == 1) return launch_tc<1, 1>(a, ntiles, s);
+  if (kind == 1 && nprod == 3) return launch_tc<1, 3>(a, ntiles, s);
+  return cudaErrorInvalidValue;
+}
+
+// Gather + Eq. 1 for the low-precision paths: like the FP64 gather, but X0 is stored
+// as the FP32 master copy and, for the tensor-core kinds, as the rounded operand(s);
+// every column of the padded part (up to ld) is written.  T_0 is summed in FP64 from
+// the stored FP32 values.  KIND = -1: FP32 master only (CUDA-core FP32 path).
+template <int KIND, int NPROD>
+__global__ void __launch_bounds__(256) gather_lp_kernel(const PartDesc* __restrict__ parts,
+                                                        const ColBlock* __restrict__ blocks,
+                                                        const int32_t* __restrict__ Sall,
+                                                        const int64_t* __restrict__ rowptr,
+                                                        const int32_t* __restrict__ colind,
+                                                        const double* __restrict__ vals, float* __restrict__ master,
+                                                        void* op_hi, void* op_lo, double* __restrict__ slots,
+                                                        StepCtl ctl) {
+  const ColBlock b = blocks[blockIdx.x];
+  const PartDesc p = parts[b.part];
+  const int lane = threadIdx.x & 31;
+  const int j = b.j0 + (threadIdx.x >> 5);
+  const int32_t* S = Sall + p.soff;
+  const double emax = ctl.st->eps_max, emin = ctl.st->eps_min;
+  const double den = emax - emin;
+  double tr = 0.0;
+  if (j < p.ld) {
+    const int64_t cbase = p.off + (int64_t)j * p.ld;
+    for (int r = lane; r < p.ld; r += 32) {
+      master[cbase + r] = 0.0f;
+      if (KIND >= 0) store_operands<(KIND < 0 ? 0 : KIND), NPROD>(op_hi, op_lo, cbase + r, 0.0f);
+    }
+    __syncwarp();
+    if (j < p.s) {
+      const int32_t g = S[j];
+      for (int64_t q = rowptr[g] + lane; q < rowptr[g + 1]; q += 32) {
+        const int a = find_local(S, p.c, p.s, colind[q]);
+        if (a >= 0) {
+          const double x = (a == j) ? (emax - vals[q]) / den : (0.0 - vals[q]) / den;
+          const float xf = (float)x;
+          master[cbase + a] = xf;
+          if (KIND >= 0) store_operands<(KIND < 0 ? 0 : KIND), NPROD>(op_hi, op_lo, cbase + a, xf);
+          if (a == j && j < p.c) tr = (double)xf;
+        }
+      }
+    }
+  }
+  const double2 t = block_sum2(tr, 0.0);
+  if (threadIdx.x == 0) slots[blockIdx.x] = t.x;
+  if (last_block_ticket(&ctl.st->counter)) {
+    double acc = 0.0;
+    for (unsigned int k = threadIdx.x; k < gridDim.x; k += blockDim.x) acc += ld_cg(&slots[k]);
+    const double2 sum = block_sum2(acc, 0.0);
+    if (threadIdx.x == 0) {
+      if (ctl.st->nonfinite) ctl.st->status = ST_NONFINITE;
+      finish_step(ctl, 0, sum.x, 0.0);
+      ctl.st->counter = 0;
+    }
+  }
+}
+
+cudaError_t launch_gather_lp(int kind, int nprod, const PartDesc* parts, const ColBlock* blocks, int nblocks,
+                             const int32_t* Sall, const int64_t* rowptr, const int32_t* colind, const double* vals,
+                             float* master, void* op_hi, void* op_lo, double* slots, const StepCtl& ctl,
+                             cudaStream_t s) {
+  const dim3 g(nblocks), b(32 * COLS_PER_BLOCK);
+  if (kind < 0)
+    gather_lp_kernel<-1, 1><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, colind, vals, master, op_hi, op_lo, slots, ctl);
+  else if (kind == 0 && nprod == 1)
+    gather_lp_kernel<0, 1><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, colind, vals, master, op_hi, op_lo, slots, ctl);
+  else if (kind == 0 && nprod == 3)
+    gather_lp_kernel<0, 3><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, colind, vals, master, op_hi, op_lo, slots, ctl);
+  else if (kind == 1 && nprod == 1)
+    gather_lp_kernel<1, 1><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, colind, vals, master, op_hi, op_lo, slots, ctl);
+  else if (kind == 1 && nprod == 3)
+    gather_lp_kernel<1, 3><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, colind, vals, master, op_hi, op_lo, slots, ctl);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+// FP32 master of the last low-precision iterate -> FP64 arena for the tail steps.
+__global__ void convert_kernel(const float* const* __restrict__ master_of_step, double* __restrict__ out, int64_t n,
+                               const DevState* st) {
+  const float* in = master_of_step[st->steps];
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = (double)in[i];
+}
+
+cudaError_t launch_convert(const float* const* master_of_step, double* out, int64_t n, const DevState* st,
+                           cudaStream_t s) {
+  convert_kernel<<<152 * 8, 256, 0, s>>>(master_of_step, out, n, st);
+  return cudaGetLastError();
+}
+
+// Encode one tensor map per part over an operand arena: 2-D, inner dimension = rows
+// of a column (contiguous), outer = columns, box = 128 bytes x 128 columns, 128-byte
+// swizzle.  `enc` is cuTensorMapEncodeTiled obtained from the driver.
+int encode_part_maps(void* enc_fn, void* out_maps, const PartDesc* parts, int nparts, void* arena, int kind) {
+  CUtensorMap* out = reinterpret_cast<CUtensorMap*>(out_maps);
+  using Enc = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*, const cuuint64_t*,
+                           const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                           CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  Enc enc = reinterpret_cast<Enc>(enc_fn);
+  const int es = kind == 0 ? 2 : 4;
+  for (int k = 0; k < nparts; ++k) {
+    const PartDesc& p = parts[k];
+    cuuint64_t dims[2] = {(cuuint64_t)p.ld, (cuuint64_t)p.ld};
+    cuuint64_t strides[1] = {(cuuint64_t)p.ld * es};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / es), 128u};
+    cuuint32_t estr[2] = {1u, 1u};
+    void* addr = (char*)arena + (size_t)p.off * es;
+    CUresult r = enc(&out[k], kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, addr,
+                     dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return (int)r;
+  }
+  return 0;
+}
+
+}  // namespace gsp2

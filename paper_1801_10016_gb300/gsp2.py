@@ -19,10 +19,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libgsp2.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "gsp2.h")
 
-OK, E_ARG, E_OOM, E_STATE, E_CUDA, E_NOT_CONVERGED, E_TRACE, E_NONFINITE, E_WORKSPACE = range(9)
+OK, E_ARG, E_OOM, E_STATE, E_CUDA, E_NOT_CONVERGED, E_TRACE, E_NONFINITE, E_WORKSPACE, E_TIMEOUT = range(10)
 STATUS_NAMES = {0: "OK", 1: "E_ARG", 2: "E_OOM", 3: "E_STATE", 4: "E_CUDA", 5: "E_NOT_CONVERGED",
-                6: "E_TRACE", 7: "E_NONFINITE", 8: "E_WORKSPACE"}
-PRECISIONS = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3, "bf16x3": 4}
+                6: "E_TRACE", 7: "E_NONFINITE", 8: "E_WORKSPACE", 9: "E_TIMEOUT"}
+PRECISIONS = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3, "bf16x3": 4, "tf32x3": 5}
 MODES = {"record": 0, "replay": 1}
 
 
@@ -210,15 +210,15 @@ class GSP2:
         """(status code, report dict) of the last density call; waits for it."""
         r = Report()
         st = self._lib.gsp2_sync_status(self._h, C.byref(r))
-        if st in (E_ARG, E_STATE, E_CUDA):
+        if st in (E_ARG, E_STATE, E_CUDA, E_TIMEOUT):
             self._check(st)
         return st, {f: getattr(r, f) for f, _ in Report._fields_}
 
     def history(self):
-        m = self.options.max_steps + 1
+        m = self.options.max_steps + 9
         tr = np.zeros(m)
-        e = np.zeros(m - 1)
-        a = np.zeros(m - 1, np.int8)
+        e = np.zeros(m)
+        a = np.zeros(m, np.int8)
         self._check(self._lib.gsp2_history(self._h, _ptr(tr), _ptr(e), _ptr(a), m))
         st, rep = self.status()
         k = rep["steps"]

@@ -1,0 +1,86 @@
+"""GPU checks of the low-precision purification paths (TF32/BF16 on tcgen05 tensor
+cores, FP32 on CUDA cores) against the FP64 oracle.
+
+* one step, element by element, inside the rounding bound of the arithmetic:
+  operands rounded to the format's unit roundoff u, FP32 accumulation over K terms;
+* a full run with the FP64 tail, reported against the oracle's P with the accuracy
+  gates max|dP|, part idempotency and |Tr P - Nocc|.
+"""
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle
+from synth import make_workload
+from synth.tb import make_tb_system
+
+pytestmark = pytest.mark.gpu
+
+# unit roundoff of one operand, and of one product of the split (x3) forms
+U_OPERAND = {"tf32": 2.0 ** -11, "bf16": 2.0 ** -8, "tf32x3": 2.0 ** -21, "bf16x3": 2.0 ** -15, "fp32": 2.0 ** -24}
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def g():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1801_10016_gb300 import gsp2
+    return gsp2
+
+
+def run(g, s, prec, **opt):
+    import torch
+    plan = g.GSP2(s.n, s.rowptr, s.colind, s.nocc, s.part, s.nparts, s.g_rowptr, s.g_colind, device="cuda:0",
+                  precision=prec, **opt)
+    p = plan.density(torch.from_numpy(s.vals).to("cuda:0"))
+    return plan, p.cpu().numpy(), plan.history()
+
+
+@pytest.mark.parametrize("prec", ["tf32", "bf16", "tf32x3", "bf16x3", "fp32"])
+@pytest.mark.parametrize("case", ["tb512", "ragged132"])
+def test_one_step_within_rounding_bound(g, prec, case):
+    s = make_workload("tb512") if case == "tb512" else make_tb_system(33, 1, 3.0, seed=9)
+    plan, p, hist = run(g, s, prec, max_steps=1, fp64_tail_steps=0)
+    assert hist["report"]["steps"] == 1
+    ref = oracle.gsp2(s.n, s.rowptr, s.colind, s.vals, s.nocc, s.part, s.nparts, s.g_rowptr, s.g_colind,
+                      max_steps=1)
+    assert hist["alphas"][:1] == ref.alphas
+    Hs = sp.csr_matrix((s.vals, s.colind, s.rowptr), shape=(s.n, s.n))
+    worst = 0.0
+    for S, c, X1 in zip(ref.S, ref.ncore, ref.X):
+        X0 = oracle.initial_guess(Hs[S][:, S].toarray(), *ref.bounds)
+        A = np.abs(X0)
+        K = len(S)
+        scale = 2.0 if ref.alphas[0] == 1 else 1.0
+        # operand rounding (both factors), the FP32 master of X0, FP32 accumulation, output rounding
+        bound = (2.0 * U_OPERAND[prec] + 2.0 * U32 + (K + 2) * U32) * (A @ A) + scale * 2 * U32 * A + U32 * np.abs(X1)
+        bound = 2.0 * bound + 1e-30
+        got = np.empty_like(X1[:, :c])
+        for j in range(c):
+            gcol = S[j]
+            rows = plan.p_rowind[plan.p_colptr[gcol]:plan.p_colptr[gcol + 1]]
+            pos = {int(v): i for i, v in enumerate(S)}
+            got[[pos[int(r)] for r in rows], j] = p[plan.p_colptr[gcol]:plan.p_colptr[gcol + 1]]
+        ratio = np.abs(got - X1[:, :c]) / bound[:, :c]
+        worst = max(worst, float(ratio.max()))
+    assert worst <= 1.0, worst
+
+
+@pytest.mark.parametrize("prec,max_dp", [("tf32x3", 3e-6), ("fp32", 3e-6), ("tf32", 3e-3), ("bf16", 5e-2),
+                                         ("bf16x3", 1e-3)])
+def test_full_run_against_fp64_oracle(g, prec, max_dp):
+    s = make_workload("tb512")
+    plan, p, hist = run(g, s, prec)
+    ref = oracle.gsp2(s.n, s.rowptr, s.colind, s.vals, s.nocc, s.part, s.nparts, s.g_rowptr, s.g_colind)
+    want = ref.p_on_pattern(plan.p_colptr, plan.p_rowind)
+    err = float(np.max(np.abs(p - want)))
+    rep = hist["report"]
+    print(f"{prec}: steps={rep['steps']} fp64_steps={rep['fp64_steps']} max|dP|={err:.3e} "
+          f"|trP-N|={abs(rep['trace'] - s.nocc):.3e} status={hist['status']}")
+    assert rep["fp64_steps"] == 2
+    assert err <= max_dp, err
