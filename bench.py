@@ -30,6 +30,9 @@ UNIT = "P-builds/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # nominal dense rates (TFLOP/s) used to derive a dtype's peak from the measured bf16 one
 NOMINAL = {"bf16": 2250.0, "tf32": 1100.0, "fp64": 1.25}
+# DRAM bytes per launch of the dominant kernel from one ncu capture (workload, precision);
+# entries are removed when the kernel changes
+TRAFFIC = {("tb30k", "fp64"): 2.80e9}
 
 
 def dist_env():
@@ -163,6 +166,28 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def time_builds(plan, h_dev, p_dev, steps, flush, stream):
+    """Device time (ms) of `steps` P-builds, L2 flushed before each, plus the per-step
+    kernel times of each build."""
+    import torch
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    step_ms = []
+    for i in range(steps):
+        flush.fill_(i & 0xFF)
+        starts[i].record(stream)
+        plan.density(h_dev, out=p_dev)
+        ends[i].record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(plan.step_times())
+    return [a.elapsed_time(b) for a, b in zip(starts, ends)], step_ms
+
+
+def kernel_avg_ms(step_ms, nwork):
+    work = [float(x) for ms in step_ms for x in ms[:nwork]]
+    return sum(work) / max(1, len(work)), sum(work)
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -187,34 +212,25 @@ def run_ours(args):
                 precision=args.precision, max_steps=args.max_steps, time_steps=1)
     h_dev = torch.from_numpy(s.vals).to(dev)
     p_dev = torch.empty(plan.nnz_p, dtype=torch.float64, device=dev)
-    alpha = torch.zeros(plan.options.max_steps, dtype=torch.int8, device=dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
     stream = torch.cuda.current_stream()
+    warm = max(3, args.warmup)
 
-    for _ in range(max(3, args.warmup)):
-        plan.density(h_dev, out=p_dev, alpha=alpha)
+    for _ in range(warm):
+        plan.density(h_dev, out=p_dev)
     st, rep = plan.status()
-    steps_applied = rep["steps"]
+    steps_applied = rep["steps"] - rep["fp64_steps"]
+    p_ref = p_dev.clone()
 
     # ---- timed region (device): K P-builds, L2 flushed between them
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    step_ms = []
     if world > 1:
         torch.distributed.barrier(device_ids=[local])
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
     with ClockSampler(local) as clk:
-        for i in range(args.steps):
-            flush.fill_(i & 0xFF)
-            starts[i].record(stream)
-            plan.density(h_dev, out=p_dev, alpha=alpha)
-            ends[i].record(stream)
-            torch.cuda.synchronize()
-            step_ms.append(plan.step_times())
+        dev_ms, step_ms = time_builds(plan, h_dev, p_dev, args.steps, flush, stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
-    dev_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     tot = sum(dev_ms) / 1e3
     if world > 1:
         t = torch.tensor([tot], device=dev, dtype=torch.float64)
@@ -224,7 +240,7 @@ def run_ours(args):
     value = world * args.steps / tot
     ms_per_step = 1e3 * tot / args.steps
 
-    # ---- end to end: pinned host H in, P back to pinned host, every step
+    # ---- end to end through the public API: pinned host H in, P back to pinned host
     h_host = torch.from_numpy(s.vals).pin_memory()
     p_host = torch.empty(plan.nnz_p, dtype=torch.float64).pin_memory()
     e_steps = max(1, min(args.steps, 3))
@@ -234,7 +250,7 @@ def run_ours(args):
     e0.record(stream)
     for _ in range(e_steps):
         h_dev.copy_(h_host, non_blocking=True)
-        plan.density(h_dev, out=p_dev, alpha=alpha)
+        plan.density(h_dev, out=p_dev)
         p_host.copy_(p_dev, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -247,43 +263,88 @@ def run_ours(args):
 
     # ---- roofline of the dominant kernel (the purification step)
     peaks, src = load_peaks()
-    nominal_ratio = NOMINAL["fp64"] / NOMINAL["bf16"]
-    fp64_peak = peaks["bf16_tflops"] * nominal_ratio
     sizes = plan.part_sizes.astype(np.float64)
     alg_flops = float(np.sum(sizes * sizes * (sizes + 1.0)))  # upper triangle incl. diagonal: s(s+1)/2 * 2s
-    work_ms = []
-    for ms in step_ms:
-        k = steps_applied
-        work_ms.extend(float(x) for x in ms[:k])
-    avg_launch_ms = sum(work_ms) / max(1, len(work_ms))
-    achieved = alg_flops / (avg_launch_ms / 1e3) / 1e12
     dgemm_equiv = 2.0 * float(np.sum(sizes ** 3))
-    share = sum(work_ms) / (sum(dev_ms) + 1e-30)
-
+    avg_launch_ms, work_ms = kernel_avg_ms(step_ms, steps_applied)
+    fp64_peak = peaks["bf16_tflops"] * NOMINAL["fp64"] / NOMINAL["bf16"]
+    achieved = alg_flops / (avg_launch_ms / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp64_peak, "traffic": TRAFFIC.get((args.workload, args.precision)),
+            "kernel": "square_simt_kernel<double>",
+            "peak_source": f"{src}: bf16 burst {peaks['bf16_tflops']} TF/s x nominal fp64/bf16 "
+                           f"{NOMINAL['fp64']}/{NOMINAL['bf16']} (of measured)",
+            "avg_launch_ms": avg_launch_ms, "share_of_step": work_ms / (sum(dev_ms) + 1e-30),
+            "flops_per_launch": alg_flops}
+    launches_per_build = 4 + plan.options.max_steps
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "warmup": warm, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else args.precision,
+        "data": "synthetic",
         "config": {"workload": args.workload, "n": int(s.n), "nocc": int(s.nocc), "parts": int(s.nparts),
                    "part_size_min": int(sizes.min()), "part_size_max": int(sizes.max()),
                    "precision": args.precision, "sp2_steps": int(steps_applied),
-                   "l2": "flushed (256 MB write) between timed P-builds; two FP64 arenas of "
-                         f"{plan.info.arena_elems * 8 / 1e9:.2f} GB each also exceed L2",
+                   "l2": "flushed (256 MB write) between timed P-builds; the arenas also exceed L2",
                    "parallelism": "replicas" if world > 1 else "single"},
         "tflops_dgemm_equiv": dgemm_equiv * steps_applied / (ms_per_step / 1e3) / 1e12,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp64_peak, "traffic": None,
-                     "kernel": "square_fp64_kernel",
-                     "peak_source": f"{src} bf16 burst {peaks['bf16_tflops']} TF/s x nominal fp64/bf16 "
-                                    f"{NOMINAL['fp64']}/{NOMINAL['bf16']}",
-                     "avg_launch_ms": avg_launch_ms, "share_of_step": share,
-                     "flops_per_launch": alg_flops},
+        "roofline": roof,
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(plan.nnz_h * 8),
                 "d2h_bytes_per_step": int(plan.nnz_p * 8)},
-        "gpu_launches": int(args.steps * (4 + plan.options.max_steps)),
+        "gpu_launches": int(args.steps * launches_per_build),
         "clocks": clk.summary(),
         "status": int(st), "wall_s": wall,
     }
+    plan.close()
+    del plan
+    torch.cuda.empty_cache()
+
+    # ---- low-precision paths on the same workload, against the FP64 result
+    if not args.no_mixed:
+        mixed = {}
+        tf32_peak = peaks["bf16_tflops"] * NOMINAL["tf32"] / NOMINAL["bf16"]
+        for prec in args.mixed.split(","):
+            mp = GSP2(s.n, s.rowptr, s.colind, s.nocc, s.part, s.nparts, s.g_rowptr, s.g_colind, device=dev,
+                      precision=prec, max_steps=args.max_steps, time_steps=1)
+            pm = torch.empty(mp.nnz_p, dtype=torch.float64, device=dev)
+            for _ in range(warm):
+                mp.density(h_dev, out=pm)
+            mst, mrep = mp.status()
+            with ClockSampler(local) as mclk:
+                mms, mstep = time_builds(mp, h_dev, pm, max(args.steps, 5), flush, stream)
+            mst, mrep = mp.status()
+            lp_steps = mrep["steps"] - mrep["fp64_steps"]
+            t_build = sum(mms) / len(mms) / 1e3
+            dp = float((pm - p_ref).abs().max().item())
+            k_ms, _ = kernel_avg_ms(mstep, lp_steps)
+            nprod = 3 if prec.endswith("x3") else 1
+            entry = {"value": 1.0 / t_build, "unit": UNIT, "ms_per_build": 1e3 * t_build,
+                     "speedup_vs_fp64": (1.0 / t_build) / value, "lowprec_steps": int(lp_steps),
+                     "fp64_tail_steps": int(mrep["fp64_steps"]), "max_abs_dP_vs_fp64": dp,
+                     "gate_max_dP_1e-6": dp <= 1e-6, "trace_minus_nocc": mrep["trace"] - s.nocc,
+                     "status": int(mst), "clocks": mclk.summary(),
+                     "square_kernel_ms": k_ms,
+                     "tflops_dgemm_equiv": dgemm_equiv * lp_steps / t_build / 1e12}
+            if prec != "fp32":
+                # executed tensor flops of one launch: every 128x128 upper tile, K rounded to the stage
+                nt = np.ceil(sizes / 128.0)
+                kst = 64 if prec.startswith("bf16") else 32
+                kk = np.ceil(sizes / kst) * kst
+                exec_flops = float(np.sum(nt * (nt + 1) / 2 * 2 * 128 * 128 * kk)) * nprod
+                ach = exec_flops / (k_ms / 1e3) / 1e12
+                entry["roofline"] = {"bound": "tensor", "achieved": ach, "peak": tf32_peak if "tf32" in prec
+                                     else peaks["bf16_tflops"], "unit": "TFLOP/s",
+                                     "kernel": f"square_tc_kernel<{'tf32' if 'tf32' in prec else 'bf16'},{nprod}>",
+                                     "flops": "executed tensor flops per launch (all upper 128-tiles, all products)"}
+                entry["roofline"]["frac"] = ach / entry["roofline"]["peak"]
+            mixed[prec] = entry
+            mp.close()
+            del mp
+            torch.cuda.empty_cache()
+        line["mixed"] = mixed
+        line["mixed_note"] = ("max_abs_dP_vs_fp64 compares every P value with the FP64 GPU path, which the parity "
+                              "tests hold to the FP64 oracle within 1e-10")
+
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t_cpu, _ = oracle_build_seconds(s, args.max_steps)
         line["cpu_baseline"] = {"value": 1.0 / t_cpu, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
@@ -307,6 +368,8 @@ def main():
     ap.add_argument("--max-steps", dest="max_steps", type=int, default=45)
     ap.add_argument("--ref-stride", dest="ref_stride", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", dest="no_cpu_baseline", action="store_true")
+    ap.add_argument("--no-mixed", dest="no_mixed", action="store_true")
+    ap.add_argument("--mixed", default="tf32x3,bf16x3,tf32,bf16,fp32")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -54,8 +54,8 @@ typedef enum {
 /* Arithmetic of the purification steps.  Traces, bounds and branch decisions are
  * always FP64.  The low-precision modes keep an FP32 master copy of every X_k, run
  * the squarings in that precision (TF32/BF16: tcgen05 tensor cores, FP32 accumulation
- * in TMEM; FP32: CUDA cores), stop when the idempotency error e no longer falls below
- * max(idem_tol, 16 N u) (u: unit roundoff of one product), and finish with
+ * in TMEM; FP32: CUDA cores), stop when |e| <= max(idem_tol, 16 N u) (u: unit roundoff
+ * of one product) and e < 0 or e no longer falls over two steps, and finish with
  * `fp64_tail_steps` FP64 steps: the first takes its branch from the trace rule, each
  * further one the opposite branch, so eigenvalues near 0 and near 1 are both purified.
  * The low-precision modes support RECORD only and have no adjoint. */
@@ -75,7 +75,9 @@ typedef enum {
 
 typedef struct {
   int32_t max_steps;       /* cap on purification steps (default 45), 1..1024 */
-  double idem_tol;         /* stopping gate on e = Tr X - Tr X^2 (default 1e-3) */
+  double idem_tol;         /* stopping gate on e = Tr X - Tr X^2 (default 1e-3): after step i
+                              the loop stops when |e_{i-1}| <= idem_tol and e_{i-1} < 0 or
+                              e_{i-1} >= e_{i-2} (idempotency no longer improves) */
   double trace_tol;        /* replay check on |Tr P - Nocc| (default 1e-2) */
   int32_t precision;       /* gsp2_precision (default FP64) */
   int32_t fp64_tail_steps; /* low-precision modes: FP64 steps at the end, 0..8 (default 2) */

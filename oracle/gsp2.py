@@ -31,11 +31,15 @@ Readings where the paper is silent or garbled (each also listed in the design no
   entries of each part's iterate (part order, then core order);
 * stopping (the paper asks for idempotency "within given error bounds" after Eq. 3):
   with e_i = Tr[X_i] - Tr[X_i^2] (core entries only in G-SP2), step i computes
-  e_{i-1} alongside X_i, and the iteration stops after step i when i >= 3,
-  e_{i-1} <= idem_tol and e_{i-1} >= e_{i-3}: the error is small and no longer falls,
-  so only rounding is left.  Continuing past that point is harmful, because 0 is an
-  unstable fixed point of 2x - x^2 and 1 of x^2, and rounding noise doubles each
-  step.  max_steps caps the count.  A replayed alpha sequence runs exactly its length.
+  e_{i-1} alongside X_i, and the iteration stops after step i when i >= 2,
+  |e_{i-1}| <= idem_tol and either e_{i-1} < 0 or e_{i-1} >= e_{i-2}.  In exact
+  arithmetic e >= 0 (the spectrum of X0 lies in [0, 1], which both maps keep) and, once
+  every eigenvalue is close to 0 or 1, e falls at every step; so a small e that is
+  negative or no longer falls marks the point where only rounding (or, in G-SP2, the
+  drift caused by a core trace that cannot reach Nocc exactly) is left.  Continuing
+  past that point is harmful: 0 is an unstable fixed point of 2x - x^2 and 1 of x^2,
+  so each further step doubles such errors.  max_steps caps the count.  A replayed
+  alpha sequence runs exactly its length.
 
 The adjoint functions (reverse mode through the recorded alpha sequence, the
 Daleckii-Krein form and the finite-difference probe) differentiate
@@ -98,9 +102,10 @@ def branch_alpha(trace, nocc):
 # --------------------------------------------------------------------------------------
 
 def stop_now(idem, i, idem_tol):
-    """Stopping test after step i (see the module notes): i >= 3, e_{i-1} <= idem_tol and
-    e_{i-1} >= e_{i-3}.  `idem` holds e_0 .. e_{i-1}."""
-    return i >= 3 and idem[i - 1] <= idem_tol and idem[i - 1] >= idem[i - 3]
+    """Stopping test after step i (see the module notes): i >= 2, |e_{i-1}| <= idem_tol
+    and (e_{i-1} < 0 or e_{i-1} >= e_{i-2}).  `idem` holds e_0 .. e_{i-1}."""
+    e = idem[i - 1]
+    return i >= 2 and abs(e) <= idem_tol and (e < 0 or e >= idem[i - 2])
 
 
 def sp2_dense(H, nocc, max_steps=45, bounds=None, alphas=None, keep_iterates=False,

@@ -558,7 +558,7 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
   auto alpha = (int8_t*)(w + L.alpha);
   auto A = [&](int i) { return (double*)(w + h->step_arena_off[i]); };
   StepCtl ctl{st, alpha, (double*)(w + L.traces), (double*)(w + L.idem), h->nocc, h->opt.idem_tol,
-              h->opt.trace_tol, mode, mode == MODE_REPLAY ? nsteps : h->opt.max_steps};
+              h->opt.trace_tol, mode, mode == MODE_REPLAY ? nsteps : h->opt.max_steps, 1};
   CU(h, launch_reset(st, alpha, mode == MODE_REPLAY ? alpha_user : nullptr, nsteps, h->opt.max_steps + HIST_EXTRA, s));
   CU(h, launch_bounds(h->n, rp, ci, hv, slots, BOUNDS_BLOCKS, st, s));
   const int prec = h->opt.precision;
@@ -567,6 +567,7 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
     const int kind = prec_kind(prec), nprod = prec_nprod(prec);
     StepCtl lp = ctl;
     lp.idem_tol = std::max(h->opt.idem_tol, 16.0 * (double)h->n * prec_unit(prec));
+    lp.stop_lag = 2;
     float* mf[2] = {(float*)(w + L.mf[0]), (float*)(w + L.mf[1])};
     void* oh[2] = {w + L.op_hi[0], w + L.op_hi[1]};
     void* ol[2] = {w + L.op_lo[0], w + L.op_lo[1]};
@@ -748,7 +749,7 @@ static gsp2_status enqueue_backward(gsp2_plan* h, const double* pbar, double* hb
   const int k = h->opt.ckpt_every, M = h->opt.max_steps;
   const int nt = (int)h->tiles.size();
   StepCtl ctl{st, alpha, (double*)(w + L.traces), (double*)(w + L.idem), h->nocc, h->opt.idem_tol,
-              h->opt.trace_tol, MODE_REPLAY, M};
+              h->opt.trace_tol, MODE_REPLAY, M, 1};
   CU(h, launch_adj_seed(parts, gbl, (int)h->gblocks.size(), Sall, (const int32_t*)(w + L.invperm),
                         (const int64_t*)(w + L.pcolptr), pbar, xb0, s));
   for (int c0 = (M / k) * k; c0 >= 0; c0 -= k) {

@@ -64,6 +64,7 @@ struct StepCtl {
   double trace_tol;
   int32_t mode;
   int32_t last_step;  // max_steps (RECORD) or nsteps (REPLAY)
+  int32_t stop_lag;   // stopping test compares e_{i-1} with e_{i-1-stop_lag}
 };
 
 // Arguments of one tensor-core purification step (k_tc.cu).
@@ -158,6 +159,12 @@ __device__ __forceinline__ double2 block_sum2(double a, double b) {
 //   tN = Tr_core[X_step], tY = Tr_core[X_{step-1}^2] (unused for step 0).
 // Records T_step and e_{step-1}, applies the stopping test, and in RECORD mode
 // chooses the branch of the next step: alpha = +1 iff T_step <= Nocc.
+// Stopping test (RECORD): |e| <= idem_tol and (e < 0 or e >= e_{step-1-stop_lag});
+// e >= 0 in exact arithmetic and falls once all eigenvalues are near 0 or 1, so a
+// small e that is negative or no longer falls leaves only rounding (or the G-SP2
+// drift of a core trace that cannot reach Nocc) to iterate on.  The FP64 path uses
+// lag 1; the low-precision phase lag 2, as its larger tolerance also covers the early
+// iterations where e may rise for a single step.
 __device__ __forceinline__ void finish_step(const StepCtl& c, int step, double tN, double tY) {
   DevState* st = c.st;
   c.traces[step] = tN;
@@ -166,7 +173,9 @@ __device__ __forceinline__ void finish_step(const StepCtl& c, int step, double t
   if (step > 0) {
     const double e = c.traces[step - 1] - tY;
     c.idem[step - 1] = e;
-    if (c.mode == MODE_RECORD && step >= 3 && e <= c.idem_tol && e >= c.idem[step - 3]) stop = true;
+    if (c.mode == MODE_RECORD && step >= 1 + c.stop_lag && fabs(e) <= c.idem_tol &&
+        (e < 0.0 || e >= c.idem[step - 1 - c.stop_lag]))
+      stop = true;
     if (!isfinite(e)) st->nonfinite = 1;
   }
   if (!isfinite(tN)) st->nonfinite = 1;
@@ -176,7 +185,7 @@ __device__ __forceinline__ void finish_step(const StepCtl& c, int step, double t
   }
   if (!stop && step >= c.last_step) {
     stop = true;
-    if (c.mode == MODE_RECORD && step > 0 && !(c.idem[step - 1] <= c.idem_tol)) st->status = ST_NOT_CONVERGED;
+    if (c.mode == MODE_RECORD && step > 0 && !(fabs(c.idem[step - 1]) <= c.idem_tol)) st->status = ST_NOT_CONVERGED;
   }
   if (stop) {
     st->stopped = 1;

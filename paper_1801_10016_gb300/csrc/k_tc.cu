@@ -7,9 +7,9 @@
 // the same per-part TMA tensor map (128-byte swizzle).  Accumulation is FP32 in TMEM.
 // With NPROD = 3 the operand is split X = hi + lo and Y = hi hi + hi lo + lo hi.
 //
-// Roles (128 threads): warp 0 lane 0 issues TMA loads into a ring of stages, warp 1
-// allocates TMEM and its lane 0 issues tcgen05.mma, then all four warps drain TMEM
-// (warp w owns rows 32w..32w+31), form X_new = Y or 2X - Y against the FP32 master
+// Roles (256 threads): warp 0 lane 0 issues TMA loads into a ring of stages, warp 1
+// allocates TMEM and its lane 0 issues tcgen05.mma, then all eight warps drain TMEM
+// (warp w owns rows 32 (w % 4) .. + 31 and column half w / 4), form X_new = Y or 2X - Y against the FP32 master
 // copy, write X_new (master and next operands) to (I, J) and mirrored to (J, I), and
 // add the core-diagonal traces of Y and X_new in FP64.  The last block runs the same
 // FP64 trace/branch/stopping bookkeeping as the FP64 path.
@@ -160,8 +160,49 @@ __device__ __forceinline__ void store_operands(void* hi, void* lo, int64_t e, fl
   }
 }
 
+// Store the operand(s) of 32 consecutive elements x[0..31] starting at element e
+// (16-byte aligned) with vector stores.
 template <int KIND, int NPROD>
-__global__ void __launch_bounds__(128, 1) square_tc_kernel(TcStepArgs a) {
+__device__ __forceinline__ void store_operand_row(void* hi, void* lo, int64_t e, const float (&x)[32]) {
+  if (KIND == 0) {
+    uint32_t hw[16], lw[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const uint16_t h0 = Operand<0>::bits(x[2 * q]), h1 = Operand<0>::bits(x[2 * q + 1]);
+      hw[q] = (uint32_t)h0 | ((uint32_t)h1 << 16);
+      if (NPROD == 3) {
+        const uint16_t l0 = Operand<0>::bits(x[2 * q] - Operand<0>::value(h0));
+        const uint16_t l1 = Operand<0>::bits(x[2 * q + 1] - Operand<0>::value(h1));
+        lw[q] = (uint32_t)l0 | ((uint32_t)l1 << 16);
+      }
+    }
+    uint4* dh = reinterpret_cast<uint4*>(reinterpret_cast<uint16_t*>(hi) + e);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dh[q] = make_uint4(hw[4 * q], hw[4 * q + 1], hw[4 * q + 2], hw[4 * q + 3]);
+    if (NPROD == 3) {
+      uint4* dl = reinterpret_cast<uint4*>(reinterpret_cast<uint16_t*>(lo) + e);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) dl[q] = make_uint4(lw[4 * q], lw[4 * q + 1], lw[4 * q + 2], lw[4 * q + 3]);
+    }
+  } else {
+    uint4* dh = reinterpret_cast<uint4*>(reinterpret_cast<uint32_t*>(hi) + e);
+    uint4* dl = reinterpret_cast<uint4*>(reinterpret_cast<uint32_t*>(lo) + e);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      uint32_t h[4], l[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        h[u] = Operand<1>::bits(x[4 * q + u]);
+        if (NPROD == 3) l[u] = Operand<1>::bits(x[4 * q + u] - Operand<1>::value(h[u]));
+      }
+      dh[q] = make_uint4(h[0], h[1], h[2], h[3]);
+      if (NPROD == 3) dl[q] = make_uint4(l[0], l[1], l[2], l[3]);
+    }
+  }
+}
+
+template <int KIND, int NPROD>
+__global__ void __launch_bounds__(256, 2) square_tc_kernel(TcStepArgs a) {
   constexpr int NOPS = NPROD == 3 ? 4 : 2;
   constexpr int STAGES = NPROD == 3 ? 2 : 3;
   constexpr uint32_t STAGE_B = NOPS * kTileBytes;
@@ -263,7 +304,8 @@ __global__ void __launch_bounds__(128, 1) square_tc_kernel(TcStepArgs a) {
   }
   __syncwarp();
 
-  // epilogue
+  // epilogue: 8 warps; warp w drains TMEM lanes 32 (w % 4) .. + 31 (its rows) and the
+  // column half w / 4, in chunks of 32 columns
   const bool ok = mbar_wait(done, 0, abort_flag);
   if (!ok) *s_err = 1;
   tc_fence_after();
@@ -271,38 +313,43 @@ __global__ void __launch_bounds__(128, 1) square_tc_kernel(TcStepArgs a) {
   const float* Xi = a.xin + p.off;
   float* Xo = a.xout + p.off;
   const int64_t ld = p.ld;
-  const int m = warp * 32 + lane;
+  const int quarter = warp & 3, half = warp >> 2;
+  const int m = quarter * 32 + lane;
   const int r = r0 + m;
   const bool diag = t.slot >= 0;
   double tY = 0.0, tN = 0.0;
   if (ok) {
 #pragma unroll 1
-    for (int cb = 0; cb < 4; ++cb) {
+    for (int cc = 0; cc < 2; ++cc) {
+      const int cb = half * 2 + cc;
+      const int cbase = c0 + cb * 32;
       uint32_t v[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cb * 32), v);
-      float xn[32];
+      tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(cb * 32), v);
+      float x[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) x[j] = Xi[(int64_t)(cbase + j) * ld + r];
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
-        const int c = c0 + cb * 32 + j;
-        const int64_t e = (int64_t)c * ld + r;
         const float y = __uint_as_float(v[j]);
-        const float x = Xi[e];
-        const float z = (al > 0) ? (2.0f * x - y) : y;
-        xn[j] = z;
-        Xo[e] = z;
-        store_operands<KIND, NPROD>(a.op_hi_out, a.op_lo_out, p.off + e, z);
-        if (diag && c == r && r < p.c) {
+        const float z = (al > 0) ? (2.0f * x[j] - y) : y;
+        if (diag && cbase + j == r && r < p.c) {
           tY += (double)y;
           tN += (double)z;
         }
+        x[j] = z;
+      }
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int64_t e = (int64_t)(cbase + j) * ld + r;
+        Xo[e] = x[j];
+        store_operands<KIND, NPROD>(a.op_hi_out, a.op_lo_out, p.off + e, x[j]);
       }
       if (t.ti != t.tj) {
-        const int64_t e0 = (int64_t)r * ld + c0 + cb * 32;
+        const int64_t e0 = (int64_t)r * ld + cbase;
         float4* dst = reinterpret_cast<float4*>(Xo + e0);
 #pragma unroll
-        for (int q = 0; q < 8; ++q) dst[q] = make_float4(xn[4 * q], xn[4 * q + 1], xn[4 * q + 2], xn[4 * q + 3]);
-#pragma unroll
-        for (int j = 0; j < 32; ++j) store_operands<KIND, NPROD>(a.op_hi_out, a.op_lo_out, p.off + e0 + j, xn[j]);
+        for (int q = 0; q < 8; ++q) dst[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+        store_operand_row<KIND, NPROD>(a.op_hi_out, a.op_lo_out, p.off + e0, x);
       }
     }
   }
@@ -341,7 +388,7 @@ static cudaError_t launch_tc(const TcStepArgs& a, int ntiles, cudaStream_t s) {
   const int smem = STAGES * NOPS * (int)kTileBytes + 1024 + 8 * (2 * STAGES + 1) + 16;
   cudaError_t e = cudaFuncSetAttribute(square_tc_kernel<KIND, NPROD>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  square_tc_kernel<KIND, NPROD><<<ntiles, 128, smem, s>>>(a);
+  square_tc_kernel<KIND, NPROD><<<ntiles, 256, smem, s>>>(a);
   return cudaGetLastError();
 }
 
