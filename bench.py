@@ -303,9 +303,13 @@ def run_ours(args):
     if not args.no_mixed:
         mixed = {}
         tf32_peak = peaks["bf16_tflops"] * NOMINAL["tf32"] / NOMINAL["bf16"]
-        for prec in args.mixed.split(","):
+        for spec in args.mixed.split(","):
+            # "prec" = FP64 tail of 2 steps; "prec:lpN" = N alternating tail steps in prec, no FP64 step
+            prec, _, tail = spec.partition(":")
+            lp_tail = int(tail[2:]) if tail.startswith("lp") else 0
             mp = GSP2(s.n, s.rowptr, s.colind, s.nocc, s.part, s.nparts, s.g_rowptr, s.g_colind, device=dev,
-                      precision=prec, max_steps=args.max_steps, time_steps=1)
+                      precision=prec, max_steps=args.max_steps, time_steps=1, lp_tail_steps=lp_tail,
+                      fp64_tail_steps=0 if lp_tail else 2)
             pm = torch.empty(mp.nnz_p, dtype=torch.float64, device=dev)
             for _ in range(warm):
                 mp.density(h_dev, out=pm)
@@ -313,7 +317,7 @@ def run_ours(args):
             with ClockSampler(local) as mclk:
                 mms, mstep = time_builds(mp, h_dev, pm, max(args.steps, 5), flush, stream)
             mst, mrep = mp.status()
-            lp_steps = mrep["steps"] - mrep["fp64_steps"]
+            lp_steps = mrep["steps"] - mrep["fp64_steps"] - lp_tail
             t_build = sum(mms) / len(mms) / 1e3
             dp = float((pm - p_ref).abs().max().item())
             k_ms, _ = kernel_avg_ms(mstep, lp_steps)
@@ -337,7 +341,8 @@ def run_ours(args):
                                      "kernel": f"square_tc_kernel<{'tf32' if 'tf32' in prec else 'bf16'},{nprod}>",
                                      "flops": "executed tensor flops per launch (all upper 128-tiles, all products)"}
                 entry["roofline"]["frac"] = ach / entry["roofline"]["peak"]
-            mixed[prec] = entry
+            entry["lp_tail_steps"] = lp_tail
+            mixed[spec] = entry
             mp.close()
             del mp
             torch.cuda.empty_cache()
@@ -369,7 +374,7 @@ def main():
     ap.add_argument("--ref-stride", dest="ref_stride", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", dest="no_cpu_baseline", action="store_true")
     ap.add_argument("--no-mixed", dest="no_mixed", action="store_true")
-    ap.add_argument("--mixed", default="tf32x3,bf16x3,tf32,bf16,fp32")
+    ap.add_argument("--mixed", default="tf32x3,tf32x3:lp2,bf16x3,bf16x3:lp2,tf32,bf16,fp32")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -85,7 +85,13 @@ typedef struct {
   int32_t use_graph;       /* 1 (default): capture the whole step sequence in a CUDA graph */
   int32_t time_steps;      /* 1: record CUDA events around every purification-step launch
                               (read with gsp2_step_times); default 0 */
-  int32_t reserved[7];
+  int32_t lp_tail_steps;   /* tensor-core precisions: alternating steps in that precision
+                              after its loop stops, before the FP64 tail (default 0);
+                              lp_tail_steps + fp64_tail_steps <= 8 */
+  int32_t tc_schedule;     /* tensor-core steps: 0 (default) persistent, one CTA per SM with two
+                              TMEM accumulators so the epilogue of one tile overlaps the
+                              next tile's MMAs; 1 = one CTA per tile */
+  int32_t reserved[5];
 } gsp2_options;
 
 /* Per-call report, read back by gsp2_sync_status. */

@@ -73,6 +73,7 @@ struct gsp2_plan {
   char* ws = nullptr;
   size_t ws_size = 0;
   int device = -1;
+  int num_sms = 0;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t exec = nullptr;
   GraphKey key{};
@@ -200,7 +201,7 @@ static void build_layout(gsp2_plan* h) {
   L.traces = take(((size_t)h->opt.max_steps + HIST_EXTRA) * sizeof(double));
   L.idem = take(((size_t)h->opt.max_steps + HIST_EXTRA) * sizeof(double));
   L.step_arena = take(((size_t)h->opt.max_steps + 1) * sizeof(double*));
-  L.master_of_step = take(((size_t)h->opt.max_steps + 1) * sizeof(float*));
+  L.master_of_step = take(((size_t)h->opt.max_steps + 1 + MAX_TAIL) * sizeof(float*));
   const size_t ab = (size_t)h->arena_elems * sizeof(double);
   const int prec = h->opt.precision;
   if (prec != GSP2_PREC_FP64) {
@@ -276,6 +277,11 @@ extern "C" gsp2_status gsp2_create(int64_t n, const int64_t* rowptr, const int32
     if (o.precision < GSP2_PREC_FP64 || o.precision > GSP2_PREC_TF32X3) return bail(GSP2_E_ARG, "unknown precision");
     if (o.fp64_tail_steps < 0 || o.fp64_tail_steps > MAX_TAIL)
       return bail(GSP2_E_ARG, "fp64_tail_steps must be in [0, 8]");
+    if (o.lp_tail_steps < 0 || o.fp64_tail_steps + o.lp_tail_steps > MAX_TAIL)
+      return bail(GSP2_E_ARG, "lp_tail_steps must be >= 0 with lp_tail_steps + fp64_tail_steps <= 8");
+    if (o.tc_schedule < 0 || o.tc_schedule > 1) return bail(GSP2_E_ARG, "tc_schedule must be 0 or 1");
+    if (o.lp_tail_steps > 0 && (o.precision == GSP2_PREC_FP64 || o.precision == GSP2_PREC_FP32))
+      return bail(GSP2_E_ARG, "lp_tail_steps needs a tensor-core precision");
     if (o.ckpt_every < 0) return bail(GSP2_E_ARG, "ckpt_every must be >= 0");
     if ((g_rowptr == nullptr) != (g_colind == nullptr)) return bail(GSP2_E_ARG, "graph: give both arrays or neither");
     std::string m = check_csr(n, rowptr, colind, true, "H");
@@ -474,6 +480,7 @@ extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t byt
     return fail(h, GSP2_E_WORKSPACE, "workspace is not device memory");
   int dev = 0;
   CU(h, cudaGetDevice(&dev));
+  CU(h, cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev));
   cudaStream_t s = (cudaStream_t)stream;
   drop_graph(h);
   h->ws = (char*)d_ws;
@@ -504,7 +511,7 @@ extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t byt
   CU(h, up(L.tc_tiles, h->tc_tiles.data(), h->tc_tiles.size() * sizeof(Tile)));
   CU(h, up(L.gblocks_ld, h->gblocks_ld.data(), h->gblocks_ld.size() * sizeof(ColBlock)));
   if (h->opt.precision != GSP2_PREC_FP64) {
-    std::vector<const float*> mt((size_t)h->opt.max_steps + 1);
+    std::vector<const float*> mt((size_t)h->opt.max_steps + 1 + MAX_TAIL);
     for (size_t i = 0; i < mt.size(); ++i) mt[i] = (const float*)(h->ws + L.mf[i & 1]);
     CU(h, up(L.master_of_step, mt.data(), mt.size() * sizeof(float*)));
     const int kind = prec_kind(h->opt.precision), nprod = prec_nprod(h->opt.precision);
@@ -575,28 +582,42 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
                            rp, ci, hv, mf[0], kind >= 0 ? oh[0] : nullptr, nprod == 3 ? ol[0] : nullptr,
                            (double*)slots, lp, s));
     const size_t np = h->parts.size();
+    // tensor-core schedule: persistent (one CTA per SM, overlapped epilogue) or one CTA per tile
+    const int pgrid = h->opt.tc_schedule == 0 ? h->num_sms : 0;
+    TcStepArgs tc_args{};
+    if (kind >= 0) {
+      tc_args.parts = parts;
+      tc_args.tiles = (const Tile*)(w + L.tc_tiles);
+      for (int b = 0; b < 2; ++b) {
+        tc_args.map_hi[b] = w + L.maps + (size_t)(2 * b + 0) * np * 128;
+        tc_args.map_lo[b] = w + L.maps + (size_t)(2 * b + 1) * np * 128;
+        tc_args.master[b] = mf[b];
+        tc_args.op_hi[b] = oh[b];
+        tc_args.op_lo[b] = nprod == 3 ? ol[b] : nullptr;
+      }
+      tc_args.slots = slots;
+      tc_args.nslots = h->nslots_tc;
+      tc_args.ntiles = (int)h->tc_tiles.size();
+      tc_args.ctl = lp;
+      tc_args.tail = 0;
+    }
     for (int i = 1; i <= lp.last_step; ++i) {
       const int bi = (i - 1) & 1, bo = i & 1;
       if (!h->ev.empty()) CU(h, cudaEventRecordWithFlags(h->ev[2 * (i - 1)], s, cudaEventRecordExternal));
       if (kind < 0) {
         CU(h, launch_square_fp32(parts, tiles, (int)h->tiles.size(), mf[bi], mf[bo], slots, h->nslots, lp, i, s));
       } else {
-        TcStepArgs a{};
-        a.parts = parts;
-        a.tiles = (const Tile*)(w + L.tc_tiles);
-        a.map_hi = w + L.maps + (size_t)(2 * bi + 0) * np * 128;
-        a.map_lo = w + L.maps + (size_t)(2 * bi + 1) * np * 128;
-        a.xin = mf[bi];
-        a.xout = mf[bo];
-        a.op_hi_out = oh[bo];
-        a.op_lo_out = nprod == 3 ? ol[bo] : nullptr;
-        a.slots = slots;
-        a.nslots = h->nslots_tc;
-        a.ctl = lp;
+        TcStepArgs a = tc_args;
         a.step = i;
-        CU(h, launch_square_tc(kind, nprod, a, (int)h->tc_tiles.size(), s));
+        CU(h, launch_square_tc(kind, nprod, a, (int)h->tc_tiles.size(), pgrid, s));
       }
       if (!h->ev.empty()) CU(h, cudaEventRecordWithFlags(h->ev[2 * (i - 1) + 1], s, cudaEventRecordExternal));
+    }
+    // alternating tail steps in the low precision
+    for (int t = 0; t < h->opt.lp_tail_steps; ++t) {
+      TcStepArgs a = tc_args;
+      a.tail = t == 0 ? 1 : 2;
+      CU(h, launch_square_tc(kind, nprod, a, (int)h->tc_tiles.size(), pgrid, s));
     }
     // FP64 tail: convert the last FP32 iterate, then purification steps in FP64
     double* d[2] = {(double*)(w + L.d[0]), (double*)(w + L.d[1])};
@@ -604,7 +625,7 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
     const int T = h->opt.fp64_tail_steps;
     for (int t = 0; t < T; ++t)
       CU(h, launch_square_fp64(parts, tiles, (int)h->tiles.size(), d[t & 1], d[(t + 1) & 1], slots, h->nslots, ctl, 0,
-                               t == 0 ? SQ_TAIL_FIRST : SQ_TAIL_NEXT, s));
+                               (t == 0 && h->opt.lp_tail_steps == 0) ? SQ_TAIL_FIRST : SQ_TAIL_NEXT, s));
     CU(h, launch_scatter(parts, sbl, (int)h->sblocks.size(), Sall, perm, pcol, nullptr, d[T & 1], pv, st, s));
     if (alpha_user)
       CU(h, cudaMemcpyAsync(alpha_user, alpha + 1, (size_t)h->opt.max_steps, cudaMemcpyDeviceToDevice, s));

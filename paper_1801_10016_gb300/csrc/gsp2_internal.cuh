@@ -68,19 +68,22 @@ struct StepCtl {
 };
 
 // Arguments of one tensor-core purification step (k_tc.cu).
+// Buffers alternate with the step parity: X_{step-1} is read from buffer (step-1)&1 and
+// X_step written to buffer step&1.
 struct TcStepArgs {
   const PartDesc* parts;
   const Tile* tiles;       // 128x128 upper tiles
-  const void* map_hi;      // CUtensorMap[nparts] over the input operand arena (hi part)
-  const void* map_lo;      // CUtensorMap[nparts] over the input lo arena (split mode)
-  const float* xin;        // FP32 master of X_{step-1}
-  float* xout;             // FP32 master of X_step
-  void* op_hi_out;         // operand arenas of X_step
-  void* op_lo_out;
+  const void* map_hi[2];   // CUtensorMap[nparts] over each operand arena (hi part)
+  const void* map_lo[2];   // CUtensorMap[nparts] over each lo arena (split mode)
+  float* master[2];        // FP32 master copies of X
+  void* op_hi[2];          // operand arenas
+  void* op_lo[2];
   double2* slots;
   int nslots;
+  int ntiles;
   StepCtl ctl;
-  int step;
+  int step;                // ignored in tail mode (step = steps applied + 1)
+  int tail;                // 0: loop step; 1: first alternating tail step; 2: further ones
 };
 
 // ------------------------------------------------------------------ device helpers
@@ -198,14 +201,15 @@ __device__ __forceinline__ void finish_step(const StepCtl& c, int step, double t
   }
 }
 
-// Bookkeeping of an FP64 tail step of a low-precision run: records T_step, e_{step-1}
-// and the step count; no stopping test and no branch choice.
-__device__ __forceinline__ void finish_tail(const StepCtl& c, int step, double tN, double tY) {
+// Bookkeeping of a tail step of a low-precision run (FP64, or alternating steps in the
+// low precision): records T_step, e_{step-1} and the step count; no stopping test and
+// no branch choice.
+__device__ __forceinline__ void finish_tail(const StepCtl& c, int step, double tN, double tY, bool fp64) {
   DevState* st = c.st;
   c.traces[step] = tN;
   c.idem[step - 1] = c.traces[step - 1] - tY;
   st->steps = step;
-  st->fp64_steps += 1;
+  if (fp64) st->fp64_steps += 1;
   if (!isfinite(tN) || !isfinite(c.idem[step - 1])) {
     st->nonfinite = 1;
     st->status = ST_NONFINITE;

@@ -22,7 +22,8 @@ cudaError_t launch_scatter(const PartDesc* parts, const ColBlock* blocks, int nb
                            const double* fixed_arena, double* pvals, const DevState* st, cudaStream_t s);
 
 // low-precision paths (k_tc.cu)
-cudaError_t launch_square_tc(int kind, int nprod, const TcStepArgs& a, int ntiles, cudaStream_t s);
+cudaError_t launch_square_tc(int kind, int nprod, const TcStepArgs& a, int ntiles, int persistent_grid,
+                             cudaStream_t s);
 cudaError_t launch_gather_lp(int kind, int nprod, const PartDesc* parts, const ColBlock* blocks, int nblocks,
                              const int32_t* Sall, const int64_t* rowptr, const int32_t* colind, const double* vals,
                              float* master, void* op_hi, void* op_lo, double* slots, const StepCtl& ctl,

@@ -297,7 +297,7 @@ __global__ void __launch_bounds__(256, 2) square_simt_kernel(const PartDesc* __r
         finish_step(ctl, step, s.y, s.x);
       } else {
         ctl.alpha[step] = al;
-        finish_tail(ctl, step, s.y, s.x);
+        finish_tail(ctl, step, s.y, s.x, true);
       }
       ctl.st->counter = 0;
     }

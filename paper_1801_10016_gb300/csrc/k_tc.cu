@@ -214,7 +214,15 @@ __global__ void __launch_bounds__(256, 2) square_tc_kernel(TcStepArgs a) {
   constexpr uint32_t FMT = KIND == 0 ? 1u : 2u;
   constexpr uint32_t IDESC = (1u << 4) | (FMT << 7) | (FMT << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
 
-  if (*(volatile int32_t*)&a.ctl.st->stopped) return;
+  int step = a.step;
+  if (a.tail) {
+    const int32_t stt = *(volatile int32_t*)&a.ctl.st->status;
+    if (stt == ST_NONFINITE || stt == ST_TIMEOUT) return;
+    step = *(volatile int32_t*)&a.ctl.st->steps + 1;
+  } else if (*(volatile int32_t*)&a.ctl.st->stopped) {
+    return;
+  }
+  const int bi = (step - 1) & 1, bo = step & 1;
 
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -255,8 +263,8 @@ __global__ void __launch_bounds__(256, 2) square_tc_kernel(TcStepArgs a) {
 
   if (warp == 0 && lane == 0) {
     // producer
-    const CUtensorMap* mhi = reinterpret_cast<const CUtensorMap*>(a.map_hi) + t.part;
-    const CUtensorMap* mlo = reinterpret_cast<const CUtensorMap*>(a.map_lo) + t.part;
+    const CUtensorMap* mhi = reinterpret_cast<const CUtensorMap*>(a.map_hi[bi]) + t.part;
+    const CUtensorMap* mlo = reinterpret_cast<const CUtensorMap*>(a.map_lo[bi]) + t.part;
     int issued = 0;
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % STAGES;
@@ -306,12 +314,18 @@ __global__ void __launch_bounds__(256, 2) square_tc_kernel(TcStepArgs a) {
 
   // epilogue: 8 warps; warp w drains TMEM lanes 32 (w % 4) .. + 31 (its rows) and the
   // column half w / 4, in chunks of 32 columns
-  const bool ok = mbar_wait(done, 0, abort_flag);
+  // warp-uniform outcome: tcgen05.ld is a warp-collective instruction
+  const bool ok = __all_sync(0xffffffffu, mbar_wait(done, 0, abort_flag));
   if (!ok) *s_err = 1;
   tc_fence_after();
-  const int8_t al = a.ctl.alpha[a.step];
-  const float* Xi = a.xin + p.off;
-  float* Xo = a.xout + p.off;
+  int8_t al;
+  if (a.tail == 1) al = (a.ctl.traces[step - 1] <= (double)a.ctl.nocc) ? (int8_t)1 : (int8_t)-1;
+  else if (a.tail == 2) al = (int8_t)(-a.ctl.alpha[step - 1]);
+  else al = a.ctl.alpha[step];
+  const float* Xi = a.master[bi] + p.off;
+  float* Xo = a.master[bo] + p.off;
+  void* ohi = a.op_hi[bo];
+  void* olo = a.op_lo[bo];
   const int64_t ld = p.ld;
   const int quarter = warp & 3, half = warp >> 2;
   const int m = quarter * 32 + lane;
@@ -342,14 +356,14 @@ __global__ void __launch_bounds__(256, 2) square_tc_kernel(TcStepArgs a) {
       for (int j = 0; j < 32; ++j) {
         const int64_t e = (int64_t)(cbase + j) * ld + r;
         Xo[e] = x[j];
-        store_operands<KIND, NPROD>(a.op_hi_out, a.op_lo_out, p.off + e, x[j]);
+        store_operands<KIND, NPROD>(ohi, olo, p.off + e, x[j]);
       }
       if (t.ti != t.tj) {
         const int64_t e0 = (int64_t)r * ld + cbase;
         float4* dst = reinterpret_cast<float4*>(Xo + e0);
 #pragma unroll
         for (int q = 0; q < 8; ++q) dst[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
-        store_operand_row<KIND, NPROD>(a.op_hi_out, a.op_lo_out, p.off + e0, x);
+        store_operand_row<KIND, NPROD>(ohi, olo, p.off + e0, x);
       }
     }
   }
@@ -373,12 +387,279 @@ __global__ void __launch_bounds__(256, 2) square_tc_kernel(TcStepArgs a) {
       if (a.ctl.st->timeout) {
         a.ctl.st->status = ST_TIMEOUT;
         a.ctl.st->stopped = 1;
+      } else if (a.tail) {
+        a.ctl.alpha[step] = al;
+        finish_tail(a.ctl, step, sum.y, sum.x, false);
       } else {
-        finish_step(a.ctl, a.step, sum.y, sum.x);
+        finish_step(a.ctl, step, sum.y, sum.x);
       }
       a.ctl.st->counter = 0;
     }
   }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(bar) : "memory");
+}
+
+// Persistent variant: one CTA per SM walks the tiles blockIdx.x, blockIdx.x + gridDim.x,
+// ... (largest parts first).  Two TMEM accumulators let the epilogue of one tile run
+// while the tensor cores work on the next.  12 warps: warp 0 lane 0 issues TMA loads,
+// warp 1 owns TMEM and its lane 0 issues tcgen05.mma, warps 4..11 drain TMEM (warp w:
+// lanes 32 (w % 4) .. + 31, column half (w - 4) / 4).  Same arithmetic and the same
+// bookkeeping as square_tc_kernel.
+template <int KIND, int NPROD>
+__global__ void __launch_bounds__(384, 1) square_tc_persistent_kernel(TcStepArgs a) {
+  constexpr int NOPS = NPROD == 3 ? 4 : 2;
+  constexpr int STAGES = NPROD == 3 ? 3 : 4;
+  constexpr uint32_t STAGE_B = NOPS * kTileBytes;
+  constexpr int ES = KIND == 0 ? 2 : 4;
+  constexpr int BKE = 128 / ES;
+  constexpr int KMMA = KIND == 0 ? 16 : 8;
+  constexpr int NMMA = BKE / KMMA;
+  constexpr uint32_t FMT = KIND == 0 ? 1u : 2u;
+  constexpr uint32_t IDESC = (1u << 4) | (FMT << 7) | (FMT << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+
+  int step = a.step;
+  if (a.tail) {
+    const int32_t stt = *(volatile int32_t*)&a.ctl.st->status;
+    if (stt == ST_NONFINITE || stt == ST_TIMEOUT) return;
+    step = *(volatile int32_t*)&a.ctl.st->steps + 1;
+  } else if (*(volatile int32_t*)&a.ctl.st->stopped) {
+    return;
+  }
+  const int bi = (step - 1) & 1, bo = step & 1;
+
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* sb = smem_raw + (base - raw);
+  const uint32_t bars = base + STAGES * STAGE_B;  // full[S], empty[S], tfull[2], tempty[2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sb + STAGES * STAGE_B + 8 * (2 * STAGES + 4));
+  int* s_err = reinterpret_cast<int*>(tmem_slot + 1);
+  double2* red = reinterpret_cast<double2*>(sb + STAGES * STAGE_B + 8 * (2 * STAGES + 4) + 16);
+  auto full = [&](int s) { return bars + 8u * s; };
+  auto empty = [&](int s) { return bars + 8u * (STAGES + s); };
+  auto tfull = [&](int b) { return bars + 8u * (2 * STAGES + b); };
+  auto tempty = [&](int b) { return bars + 8u * (2 * STAGES + 2 + b); };
+  auto tile_addr = [&](int s, int op) { return base + (uint32_t)s * STAGE_B + (uint32_t)op * kTileBytes; };
+  int32_t* abort_flag = &a.ctl.st->timeout;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(empty(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull(b), 1);
+      mbar_init(tempty(b), 8);
+    }
+    *s_err = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;\n" ::"r"(smem_u32(tmem_slot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // producer: one ring of stages across all tiles of this CTA
+    uint32_t g = 0;
+    bool bad = false;
+    for (int ti = blockIdx.x; ti < a.ntiles && !bad; ti += gridDim.x) {
+      const Tile t = a.tiles[ti];
+      const PartDesc p = a.parts[t.part];
+      const CUtensorMap* mhi = reinterpret_cast<const CUtensorMap*>(a.map_hi[bi]) + t.part;
+      const CUtensorMap* mlo = reinterpret_cast<const CUtensorMap*>(a.map_lo[bi]) + t.part;
+      const int nk = (p.s + BKE - 1) / BKE;
+      for (int kb = 0; kb < nk; ++kb, ++g) {
+        const int s = g % STAGES;
+        if (g >= STAGES && !mbar_wait(empty(s), ((g / STAGES) - 1) & 1, abort_flag)) {
+          bad = true;
+          break;
+        }
+        mbar_expect_tx(full(s), STAGE_B);
+        const int k0 = kb * BKE;
+        tma_load_2d(tile_addr(s, 0), mhi, k0, t.ti * 128, full(s));
+        tma_load_2d(tile_addr(s, 1), mhi, k0, t.tj * 128, full(s));
+        if (NPROD == 3) {
+          tma_load_2d(tile_addr(s, 2), mlo, k0, t.ti * 128, full(s));
+          tma_load_2d(tile_addr(s, 3), mlo, k0, t.tj * 128, full(s));
+        }
+      }
+    }
+    if (bad) {
+      *s_err = 1;
+      // do not leave while copies are in flight: bounded wait for the last stages issued
+      const uint32_t first = g > STAGES ? g - STAGES : 0;
+      for (uint32_t q = first; q < g; ++q) (void)mbar_wait(full(q % STAGES), (q / STAGES) & 1, abort_flag);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer: tile i accumulates in TMEM columns [128 (i & 1), + 128)
+    uint32_t g = 0;
+    int i = 0;
+    bool bad = false;
+    for (int ti = blockIdx.x; ti < a.ntiles && !bad; ti += gridDim.x, ++i) {
+      const Tile t = a.tiles[ti];
+      const PartDesc p = a.parts[t.part];
+      const int nk = (p.s + BKE - 1) / BKE;
+      const int b = i & 1, u = i >> 1;
+      if (u >= 1 && !mbar_wait(tempty(b), (u - 1) & 1, abort_flag)) {
+        bad = true;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t d = tmem + (uint32_t)(b * 128);
+      for (int kb = 0; kb < nk; ++kb, ++g) {
+        const int s = g % STAGES;
+        if (!mbar_wait(full(s), (g / STAGES) & 1, abort_flag)) {
+          bad = true;
+          break;
+        }
+        tc_fence_after();
+        const uint64_t ah = smem_desc(tile_addr(s, 0)), bh = smem_desc(tile_addr(s, 1));
+        const uint64_t al = smem_desc(tile_addr(s, 2)), bl = smem_desc(tile_addr(s, 3));
+#pragma unroll
+        for (int kk = 0; kk < NMMA; ++kk) {
+          const uint64_t adv = (uint64_t)((kk * KMMA * ES) >> 4);
+          mma<KIND>(d, ah + adv, bh + adv, IDESC, (kb > 0 || kk > 0) ? 1u : 0u);
+          if (NPROD == 3) {
+            mma<KIND>(d, ah + adv, bl + adv, IDESC, 1u);
+            mma<KIND>(d, al + adv, bh + adv, IDESC, 1u);
+          }
+        }
+        mma_commit(empty(s));
+      }
+      mma_commit(tfull(b));
+    }
+    if (bad) *s_err = 1;
+  } else if (warp >= 4) {
+    // epilogue
+    const int quarter = warp & 3, half = (warp - 4) >> 2;
+    const int m = quarter * 32 + lane;
+    int i = 0;
+    for (int ti = blockIdx.x; ti < a.ntiles; ti += gridDim.x, ++i) {
+      const int b = i & 1, u = i >> 1;
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(tfull(b), u & 1, abort_flag));
+      tc_fence_after();
+      const Tile t = a.tiles[ti];
+      const PartDesc p = a.parts[t.part];
+      int8_t alf;
+      if (a.tail == 1) alf = (a.ctl.traces[step - 1] <= (double)a.ctl.nocc) ? (int8_t)1 : (int8_t)-1;
+      else if (a.tail == 2) alf = (int8_t)(-a.ctl.alpha[step - 1]);
+      else alf = a.ctl.alpha[step];
+      const float* Xi = a.master[bi] + p.off;
+      float* Xo = a.master[bo] + p.off;
+      void* ohi = a.op_hi[bo];
+      void* olo = a.op_lo[bo];
+      const int64_t ld = p.ld;
+      const int r0 = t.ti * 128, c0 = t.tj * 128;
+      const int r = r0 + m;
+      const bool diag = t.slot >= 0;
+      double tY = 0.0, tN = 0.0;
+      if (ok) {
+#pragma unroll 1
+        for (int cc = 0; cc < 2; ++cc) {
+          const int cb = half * 2 + cc;
+          const int cbase = c0 + cb * 32;
+          uint32_t v[32];
+          tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 128 + cb * 32), v);
+          float x[32];
+#pragma unroll
+          for (int j = 0; j < 32; ++j) x[j] = Xi[(int64_t)(cbase + j) * ld + r];
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const float y = __uint_as_float(v[j]);
+            const float z = (alf > 0) ? (2.0f * x[j] - y) : y;
+            if (diag && cbase + j == r && r < p.c) {
+              tY += (double)y;
+              tN += (double)z;
+            }
+            x[j] = z;
+          }
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const int64_t e = (int64_t)(cbase + j) * ld + r;
+            Xo[e] = x[j];
+            store_operands<KIND, NPROD>(ohi, olo, p.off + e, x[j]);
+          }
+          if (t.ti != t.tj) {
+            const int64_t e0 = (int64_t)r * ld + cbase;
+            float4* dst = reinterpret_cast<float4*>(Xo + e0);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) dst[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+            store_operand_row<KIND, NPROD>(ohi, olo, p.off + e0, x);
+          }
+        }
+      } else {
+        *s_err = 1;
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty(b));
+      if (diag) {
+        // fixed-order reduction over the 8 epilogue warps (named barrier 1, 256 threads)
+        tY = warp_sum(tY);
+        tN = warp_sum(tN);
+        if (lane == 0) red[warp - 4] = make_double2(tY, tN);
+        asm volatile("bar.sync 1, 256;\n" ::: "memory");
+        if (warp == 4 && lane == 0) {
+          double2 acc = make_double2(0.0, 0.0);
+          for (int w = 0; w < 8; ++w) {
+            acc.x += red[w].x;
+            acc.y += red[w].y;
+          }
+          a.slots[t.slot] = acc;
+        }
+        asm volatile("bar.sync 1, 256;\n" ::: "memory");
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;\n" ::"r"(tmem));
+  if (threadIdx.x == 0 && *s_err) a.ctl.st->timeout = 1;
+
+  if (last_block_ticket(&a.ctl.st->counter)) {
+    double u = 0.0, w = 0.0;
+    for (int k = threadIdx.x; k < a.nslots; k += blockDim.x) {
+      u += ld_cg(&a.slots[k].x);
+      w += ld_cg(&a.slots[k].y);
+    }
+    const double2 sum = block_sum2(u, w);
+    if (threadIdx.x == 0) {
+      if (a.ctl.st->timeout) {
+        a.ctl.st->status = ST_TIMEOUT;
+        a.ctl.st->stopped = 1;
+      } else if (a.tail) {
+        int8_t alf;
+        if (a.tail == 1) alf = (a.ctl.traces[step - 1] <= (double)a.ctl.nocc) ? (int8_t)1 : (int8_t)-1;
+        else alf = (int8_t)(-a.ctl.alpha[step - 1]);
+        a.ctl.alpha[step] = alf;
+        finish_tail(a.ctl, step, sum.y, sum.x, false);
+      } else {
+        finish_step(a.ctl, step, sum.y, sum.x);
+      }
+      a.ctl.st->counter = 0;
+    }
+  }
+}
+
+template <int KIND, int NPROD>
+static cudaError_t launch_tc_persistent(const TcStepArgs& a, int grid, cudaStream_t s) {
+  constexpr int NOPS = NPROD == 3 ? 4 : 2;
+  constexpr int STAGES = NPROD == 3 ? 3 : 4;
+  const int smem = STAGES * NOPS * (int)kTileBytes + 1024 + 8 * (2 * STAGES + 4) + 16 + 8 * 16;
+  cudaError_t e = cudaFuncSetAttribute(square_tc_persistent_kernel<KIND, NPROD>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  square_tc_persistent_kernel<KIND, NPROD><<<grid, 384, smem, s>>>(a);
+  return cudaGetLastError();
 }
 
 template <int KIND, int NPROD>
@@ -392,7 +673,16 @@ static cudaError_t launch_tc(const TcStepArgs& a, int ntiles, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_square_tc(int kind, int nprod, const TcStepArgs& a, int ntiles, cudaStream_t s) {
+cudaError_t launch_square_tc(int kind, int nprod, const TcStepArgs& a, int ntiles, int persistent_grid,
+                             cudaStream_t s) {
+  if (persistent_grid > 0) {
+    const int g = persistent_grid < ntiles ? persistent_grid : ntiles;
+    if (kind == 0 && nprod == 1) return launch_tc_persistent<0, 1>(a, g, s);
+    if (kind == 0 && nprod == 3) return launch_tc_persistent<0, 3>(a, g, s);
+    if (kind == 1 && nprod == 1) return launch_tc_persistent<1, 1>(a, g, s);
+    if (kind == 1 && nprod == 3) return launch_tc_persistent<1, 3>(a, g, s);
+    return cudaErrorInvalidValue;
+  }
   if (kind == 0 && nprod == 1) return launch_tc<0, 1>(a, ntiles, s);
   if (kind == 0 && nprod == 3) return launch_tc<0, 3>(a, ntiles, s);
   if (kind == 1 && nprod == 1) return launch_tc<1, 1>(a, ntiles, s);

@@ -84,3 +84,41 @@ def test_full_run_against_fp64_oracle(g, prec, max_dp):
           f"|trP-N|={abs(rep['trace'] - s.nocc):.3e} status={hist['status']}")
     assert rep["fp64_steps"] == 2
     assert err <= max_dp, err
+
+
+@pytest.mark.parametrize("prec,max_dp", [("tf32x3", 5e-6), ("bf16x3", 3e-5)])
+def test_low_precision_alternating_tail(g, prec, max_dp):
+    """Tail steps in the low precision instead of FP64: same alternation, no FP64 step."""
+    s = make_workload("tb512")
+    plan, p, hist = run(g, s, prec, fp64_tail_steps=0, lp_tail_steps=2)
+    rep = hist["report"]
+    assert hist["status"] == 0 and rep["fp64_steps"] == 0
+    k = rep["steps"]
+    assert hist["alphas"][k - 1] == -hist["alphas"][k - 2]
+    ref = oracle.gsp2(s.n, s.rowptr, s.colind, s.vals, s.nocc, s.part, s.nparts, s.g_rowptr, s.g_colind)
+    want = ref.p_on_pattern(plan.p_colptr, plan.p_rowind)
+    err = float(np.max(np.abs(p - want)))
+    print(f"{prec} low-precision tail: steps={k} max|dP|={err:.3e}")
+    assert err <= max_dp, err
+
+
+def test_tail_options_rejected_where_meaningless(g):
+    s = make_workload("tb512")
+    for kw in (dict(precision="fp64", lp_tail_steps=2), dict(precision="fp32", lp_tail_steps=1),
+               dict(precision="tf32x3", lp_tail_steps=5, fp64_tail_steps=5)):
+        with pytest.raises(g.GSP2Error):
+            g.GSP2(s.n, s.rowptr, s.colind, s.nocc, s.part, s.nparts, s.g_rowptr, s.g_colind, bind=False, **kw)
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "tf32", "bf16"])
+@pytest.mark.parametrize("case", ["tb512", "tb30k"])
+def test_persistent_schedule_matches_one_cta_per_tile(g, prec, case):
+    """The persistent tensor-core kernel (two TMEM accumulators, epilogue overlapped with
+    the next tile) computes every tile exactly as the one-CTA-per-tile kernel."""
+    if case == "tb30k" and prec not in ("tf32x3", "bf16"):
+        pytest.skip("one large case per kind")
+    s = make_workload(case)
+    _, p0, h0 = run(g, s, prec, tc_schedule=0, max_steps=6)
+    _, p1, h1 = run(g, s, prec, tc_schedule=1, max_steps=6)
+    assert h0["alphas"] == h1["alphas"]
+    assert np.array_equal(p0, p1)
