@@ -55,7 +55,7 @@ typedef enum {
  * always FP64.  The low-precision modes keep an FP32 master copy of every X_k, run
  * the squarings in that precision (TF32/BF16: tcgen05 tensor cores, FP32 accumulation
  * in TMEM; FP32: CUDA cores), stop when |e| <= max(idem_tol, 16 N u) (u: unit roundoff
- * of one product) and e < 0 or e no longer falls over two steps, and finish with
+ * of one product) and e < 0 or e no longer falls, and finish with
  * `fp64_tail_steps` FP64 steps: the first takes its branch from the trace rule, each
  * further one the opposite branch, so eigenvalues near 0 and near 1 are both purified.
  * The low-precision modes support RECORD only and have no adjoint. */

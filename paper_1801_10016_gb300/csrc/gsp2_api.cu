@@ -574,7 +574,7 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
     const int kind = prec_kind(prec), nprod = prec_nprod(prec);
     StepCtl lp = ctl;
     lp.idem_tol = std::max(h->opt.idem_tol, 16.0 * (double)h->n * prec_unit(prec));
-    lp.stop_lag = 2;
+    lp.stop_lag = 1;
     float* mf[2] = {(float*)(w + L.mf[0]), (float*)(w + L.mf[1])};
     void* oh[2] = {w + L.op_hi[0], w + L.op_hi[1]};
     void* ol[2] = {w + L.op_lo[0], w + L.op_lo[1]};

@@ -165,9 +165,8 @@ __device__ __forceinline__ double2 block_sum2(double a, double b) {
 // Stopping test (RECORD): |e| <= idem_tol and (e < 0 or e >= e_{step-1-stop_lag});
 // e >= 0 in exact arithmetic and falls once all eigenvalues are near 0 or 1, so a
 // small e that is negative or no longer falls leaves only rounding (or the G-SP2
-// drift of a core trace that cannot reach Nocc) to iterate on.  The FP64 path uses
-// lag 1; the low-precision phase lag 2, as its larger tolerance also covers the early
-// iterations where e may rise for a single step.
+// drift of a core trace that cannot reach Nocc) to iterate on.  Every path uses lag 1
+// (the field is kept for experiments with longer lags).
 __device__ __forceinline__ void finish_step(const StepCtl& c, int step, double tN, double tY) {
   DevState* st = c.st;
   c.traces[step] = tN;
