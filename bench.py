@@ -276,7 +276,7 @@ def run_ours(args):
                            f"{NOMINAL['fp64']}/{NOMINAL['bf16']} (of measured)",
             "avg_launch_ms": avg_launch_ms, "share_of_step": work_ms / (sum(dev_ms) + 1e-30),
             "flops_per_launch": alg_flops}
-    launches_per_build = 4 + plan.options.max_steps
+    launches_per_build = 4 + plan.info.step_launches
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": warm, "ms_per_step": ms_per_step, "higher_is_better": True,

@@ -80,7 +80,9 @@ typedef struct {
                               e_{i-1} >= e_{i-2} (idempotency no longer improves) */
   double trace_tol;        /* replay check on |Tr P - Nocc| (default 1e-2) */
   int32_t precision;       /* gsp2_precision (default FP64) */
-  int32_t fp64_tail_steps; /* low-precision modes: FP64 steps at the end, 0..8 (default 2) */
+  int32_t fp64_tail_steps; /* FP64 steps after the stopping test, -1..8 (default -1: 0 for the
+                              FP64 precision, 2 for the low-precision modes); their first
+                              branch follows the trace rule, each further one the opposite */
   int32_t ckpt_every;      /* adjoint: keep every k-th iterate (default 8); 0 = no adjoint */
   int32_t use_graph;       /* 1 (default): capture the whole step sequence in a CUDA graph */
   int32_t time_steps;      /* 1: record CUDA events around every purification-step launch
@@ -91,7 +93,9 @@ typedef struct {
   int32_t tc_schedule;     /* tensor-core steps: 0 (default) persistent, one CTA per SM with two
                               TMEM accumulators so the epilogue of one tile overlaps the
                               next tile's MMAs; 1 = one CTA per tile */
-  int32_t reserved[5];
+  int32_t report_idem;     /* 1: after each density call, one extra FP64 pass over the final
+                              iterates computes the idempotency report idem_fro (default 0) */
+  int32_t reserved[4];
 } gsp2_options;
 
 /* Per-call report, read back by gsp2_sync_status. */
@@ -104,6 +108,8 @@ typedef struct {
   double eps_max;
   double trace;         /* Tr P = sum of core diagonal entries of the final iterates */
   double idem;          /* last idempotency error e computed */
+  double idem_fro;      /* report_idem = 1: sqrt(sum_k ||(X_k^2 - X_k)[:, cores of k]||_F^2 / N),
+                           the idempotency of P column by column (Eq. 3's check); else -1 */
 } gsp2_report;
 
 /* Plan sizes, for accounting (flops from the real part sizes). */
@@ -121,6 +127,8 @@ typedef struct {
   int64_t ntiles;       /* upper-triangular square tiles per step */
   int32_t tile;         /* square tile edge */
   int32_t ld_pad;       /* padding multiple of ld_k */
+  int32_t step_launches;   /* purification-step launches per density call (the loop's) */
+  int32_t fp64_tail_steps; /* resolved value of the option */
 } gsp2_plan_info;
 
 /* Fill `opt` with the defaults listed above. */
@@ -171,11 +179,11 @@ gsp2_status gsp2_plan_query(gsp2_handle h, gsp2_plan_info* info, int32_t* s, int
  *  d_hvals  device double[nnz_h]: values of H on the pattern given to gsp2_create
  *           (symmetric values expected; a new SCF/MD H reuses the plan, Section 1.1)
  *  d_pvals  device double[nnz_p]: output, P on the pattern of gsp2_p_pattern
- *  d_alpha  device int8[max_steps] or NULL.  RECORD: receives the branch sequence
- *           (+1: 2X - X^2, -1: X^2) of the applied steps, zeros after the last.
- *           REPLAY: the sequence to apply; its length is `nsteps`.
+ *  d_alpha  device int8[max_steps + 8] or NULL.  RECORD: receives the branch sequence
+ *           (+1: 2X - X^2, -1: X^2) of the applied steps (tail steps included), zeros
+ *           after the last.  REPLAY: the sequence to apply; its length is `nsteps`.
  *  mode     gsp2_mode
- *  nsteps   REPLAY: number of steps to apply (1..max_steps); RECORD: ignored
+ *  nsteps   REPLAY: number of steps to apply (1..max_steps + fp64_tail_steps); RECORD: ignored
  * Host-visible errors are argument/state errors only; numerical outcomes
  * (convergence, trace check, non-finite values) are read with gsp2_sync_status.
  */

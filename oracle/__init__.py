@@ -16,6 +16,7 @@ from .gsp2 import (  # noqa: F401
     core_halo,
     ch_cost,
     stop_now,
+    tail_alpha,
     gsp2,
     GSP2Result,
     eig_projector,

@@ -40,6 +40,11 @@ Readings where the paper is silent or garbled (each also listed in the design no
   past that point is harmful: 0 is an unstable fixed point of 2x - x^2 and 1 of x^2,
   so each further step doubles such errors.  max_steps caps the count.  A replayed
   alpha sequence runs exactly its length.
+* optional tail (not in the paper): after the stopping test, `tail_steps` more steps
+  whose first branch follows the trace rule and each further one the opposite.  A pair
+  X^2, 2X - X^2 (either order) maps 1 - d to 1 - O(d^2) and d to O(d^2), so the pair
+  purifies the eigenvalues the trace rule leaves drifting when the G-SP2 core trace
+  cannot reach Nocc.
 
 The adjoint functions (reverse mode through the recorded alpha sequence, the
 Daleckii-Krein form and the finite-difference probe) differentiate
@@ -108,11 +113,19 @@ def stop_now(idem, i, idem_tol):
     return i >= 2 and abs(e) <= idem_tol and (e < 0 or e >= idem[i - 2])
 
 
+def tail_alpha(t, trace, prev_alpha, nocc):
+    """Branch of the t-th purification step after the stopping test (t = 0, 1, ...):
+    the first follows the trace rule, each further one is the opposite of the previous,
+    so that eigenvalues near 0 and near 1 are both purified (see the module notes)."""
+    return branch_alpha(trace, nocc) if t == 0 else -prev_alpha
+
+
 def sp2_dense(H, nocc, max_steps=45, bounds=None, alphas=None, keep_iterates=False,
-              idem_tol=1e-3):
+              idem_tol=1e-3, tail_steps=0):
     """Plain SP2 on a dense symmetric H.  Returns (X_final, record) where record holds
     the alpha sequence, the traces T_0..T_n of the iterates and the idempotency
-    errors e_i = Tr[X_i] - Tr[X_i^2] (Eq. 3's convergence check)."""
+    errors e_i = Tr[X_i] - Tr[X_i^2] (Eq. 3's convergence check).  `tail_steps`
+    alternating steps follow the stopping test (not with a replayed sequence)."""
     H = np.asarray(H, dtype=np.float64)
     n = H.shape[0]
     if bounds is None:
@@ -125,16 +138,29 @@ def sp2_dense(H, nocc, max_steps=45, bounds=None, alphas=None, keep_iterates=Fal
     rec = dict(alphas=[], traces=[float(np.trace(X))], idem=[], bounds=(eps_min, eps_max))
     its = [X] if keep_iterates else None
     nsteps = max_steps if alphas is None else len(alphas)
-    for i in range(1, nsteps + 1):
-        a = branch_alpha(rec["traces"][-1], nocc) if alphas is None else int(alphas[i - 1])
+    tail = 0 if alphas is not None else tail_steps
+    t = -1  # index of the current tail step, -1 before the stopping test
+    i = 0
+    while True:
+        i += 1
+        if t >= 0:
+            a = tail_alpha(t, rec["traces"][-1], rec["alphas"][-1], nocc)
+        else:
+            a = branch_alpha(rec["traces"][-1], nocc) if alphas is None else int(alphas[i - 1])
         rec["idem"].append(float(np.trace(X) - np.trace(X @ X)))
         X = sp2_step(X, a)
         rec["alphas"].append(a)
         rec["traces"].append(float(np.trace(X)))
         if keep_iterates:
             its.append(X)
-        if alphas is None and stop_now(rec["idem"], i, idem_tol):
-            break
+        if t >= 0:
+            t += 1
+            if t == tail:
+                break
+        elif (alphas is None and stop_now(rec["idem"], i, idem_tol)) or i == nsteps:
+            if tail == 0:
+                break
+            t = 0
     if keep_iterates:
         rec["iterates"] = its
     return X, rec
@@ -208,7 +234,7 @@ def _h_sparse(n, rowptr, colind, vals):
 
 
 def gsp2(n, rowptr, colind, vals, nocc, part, nparts, g_rowptr=None, g_colind=None,
-         max_steps=45, alphas=None, bounds=None, keep_iterates=False, idem_tol=1e-3):
+         max_steps=45, alphas=None, bounds=None, keep_iterates=False, idem_tol=1e-3, tail_steps=0):
     """Graph-partitioned SP2 (Section 1.1, Fig. 1; Section 2.2).
 
     Each part k gets the dense submatrix H[S_k, S_k], is mapped by Eq. 1 with the
@@ -216,8 +242,8 @@ def gsp2(n, rowptr, colind, vals, nocc, part, nparts, g_rowptr=None, g_colind=No
     for all parts, from the global trace T = sum_k sum_{j core} X_k[j, j] of the
     iterates the step acts on.  Passing `alphas` replays a recorded sequence
     (Section 2.1's reuse of the multiplication sequence) for exactly its length;
-    otherwise the stopping test of the module notes ends the loop.  Without a graph,
-    the pattern of H is used as G_tau."""
+    otherwise the stopping test of the module notes ends the loop, followed by
+    `tail_steps` alternating steps.  Without a graph, the pattern of H is used as G_tau."""
     if g_rowptr is None:
         g_rowptr, g_colind = rowptr, colind
     if bounds is None:
@@ -240,8 +266,15 @@ def gsp2(n, rowptr, colind, vals, nocc, part, nparts, g_rowptr=None, g_colind=No
     traces = [core_trace(X)]
     idem, used = [], []
     nsteps = max_steps if alphas is None else len(alphas)
-    for i in range(1, nsteps + 1):
-        a = branch_alpha(traces[-1], nocc) if alphas is None else int(alphas[i - 1])
+    tail = 0 if alphas is not None else tail_steps
+    t = -1  # index of the current tail step, -1 before the stopping test
+    i = 0
+    while True:
+        i += 1
+        if t >= 0:
+            a = tail_alpha(t, traces[-1], used[-1], nocc)
+        else:
+            a = branch_alpha(traces[-1], nocc) if alphas is None else int(alphas[i - 1])
         idem.append(traces[-1] - core_trace_sq(X))
         X = [sp2_step(x, a) for x in X]
         used.append(a)
@@ -249,8 +282,14 @@ def gsp2(n, rowptr, colind, vals, nocc, part, nparts, g_rowptr=None, g_colind=No
         if keep_iterates:
             for lst, x in zip(its, X):
                 lst.append(x)
-        if alphas is None and stop_now(idem, i, idem_tol):
-            break
+        if t >= 0:
+            t += 1
+            if t == tail:
+                break
+        elif (alphas is None and stop_now(idem, i, idem_tol)) or i == nsteps:
+            if tail == 0:
+                break
+            t = 0
     return GSP2Result(n=n, S=S, ncore=ncore, X=X, alphas=used, traces=traces, idem=idem,
                       bounds=(eps_min, eps_max), iterates=its)
 

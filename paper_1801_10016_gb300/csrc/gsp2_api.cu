@@ -29,7 +29,7 @@ struct WsLayout {
   size_t maps;         // CUtensorMap[2 buffers][hi, lo][nparts]
   size_t master_of_step;
   size_t d[2];         // FP64 arenas of the tail steps
-  size_t slots, state, alpha, traces, idem, step_arena;
+  size_t slots, rslots, state, alpha, traces, idem, step_arena;
   size_t arena0, arena1;       // ping-pong iterates
   std::vector<size_t> ckpt;    // X_0, X_k, X_2k, ... (adjoint checkpoints)
   std::vector<size_t> seg;     // seg[j] = X_{c0+j}, j = 1..k-1, recomputed in the adjoint
@@ -64,6 +64,7 @@ struct gsp2_plan {
   std::vector<ColBlock> gblocks, sblocks;  // gather (to nt*64) and scatter (cores) columns
   std::vector<ColBlock> gblocks_ld;        // low-precision gather: every column up to ld
   int32_t nslots_tc = 0;
+  int32_t total_steps = 0;  // FP64 path: max_steps + tail steps (static launches of a call)
   std::vector<int64_t> pcolptr;
   std::vector<int32_t> prowind;
   int32_t nslots = 0, max_s = 0;
@@ -163,7 +164,7 @@ extern "C" void gsp2_default_options(gsp2_options* o) {
   o->idem_tol = 1e-3;
   o->trace_tol = 1e-2;
   o->precision = GSP2_PREC_FP64;
-  o->fp64_tail_steps = 2;
+  o->fp64_tail_steps = -1;
   o->ckpt_every = 8;
   o->use_graph = 1;
 }
@@ -172,6 +173,7 @@ extern "C" const char* gsp2_last_error(gsp2_handle h) { return h ? h->err.c_str(
 
 static void build_layout(gsp2_plan* h) {
   WsLayout& L = h->L;
+  h->total_steps = h->opt.max_steps + (h->opt.precision == GSP2_PREC_FP64 ? h->opt.fp64_tail_steps : 0);
   size_t o = 0;
   auto take = [&](size_t bytes) {
     const size_t at = o;
@@ -196,11 +198,12 @@ static void build_layout(gsp2_plan* h) {
   const size_t nsl = std::max<size_t>({(size_t)h->nslots, (size_t)h->nslots_tc, h->gblocks.size(),
                                         h->gblocks_ld.size(), (size_t)BOUNDS_BLOCKS, 1});
   L.slots = take(nsl * sizeof(double2));
+  L.rslots = take(std::max<size_t>(h->tiles.size(), 1) * sizeof(double));
   L.state = take(sizeof(DevState));
   L.alpha = take((size_t)h->opt.max_steps + HIST_EXTRA);
   L.traces = take(((size_t)h->opt.max_steps + HIST_EXTRA) * sizeof(double));
   L.idem = take(((size_t)h->opt.max_steps + HIST_EXTRA) * sizeof(double));
-  L.step_arena = take(((size_t)h->opt.max_steps + 1) * sizeof(double*));
+  L.step_arena = take(((size_t)h->total_steps + 1) * sizeof(double*));
   L.master_of_step = take(((size_t)h->opt.max_steps + 1 + MAX_TAIL) * sizeof(float*));
   const size_t ab = (size_t)h->arena_elems * sizeof(double);
   const int prec = h->opt.precision;
@@ -239,15 +242,15 @@ static void build_layout(gsp2_plan* h) {
   L.seg.clear();
   L.xb0 = L.xb1 = 0;
   if (k > 0) {
-    for (int c = 0; c <= h->opt.max_steps / k; ++c) L.ckpt.push_back(take(ab));
+    for (int c = 0; c <= h->total_steps / k; ++c) L.ckpt.push_back(take(ab));
     for (int j = 1; j < k; ++j) L.seg.push_back(take(ab));
     L.xb0 = take(ab);
     L.xb1 = take(ab);
   }
   L.total = o;
   // arena of each iterate X_i: checkpoints where i is a multiple of k, else ping-pong
-  h->step_arena_off.assign((size_t)h->opt.max_steps + 1, 0);
-  for (int i = 0; i <= h->opt.max_steps; ++i) {
+  h->step_arena_off.assign((size_t)h->total_steps + 1, 0);
+  for (int i = 0; i <= h->total_steps; ++i) {
     if (k > 0 && i % k == 0) h->step_arena_off[i] = L.ckpt[i / k];
     else h->step_arena_off[i] = (i & 1) ? L.arena1 : L.arena0;
   }
@@ -275,8 +278,9 @@ extern "C" gsp2_status gsp2_create(int64_t n, const int64_t* rowptr, const int32
     if (o.max_steps < 1 || o.max_steps > 1024) return bail(GSP2_E_ARG, "max_steps must be in [1, 1024]");
     if (!(o.idem_tol >= 0.0) || !(o.trace_tol >= 0.0)) return bail(GSP2_E_ARG, "tolerances must be >= 0");
     if (o.precision < GSP2_PREC_FP64 || o.precision > GSP2_PREC_TF32X3) return bail(GSP2_E_ARG, "unknown precision");
-    if (o.fp64_tail_steps < 0 || o.fp64_tail_steps > MAX_TAIL)
-      return bail(GSP2_E_ARG, "fp64_tail_steps must be in [0, 8]");
+    if (o.fp64_tail_steps < -1 || o.fp64_tail_steps > MAX_TAIL)
+      return bail(GSP2_E_ARG, "fp64_tail_steps must be in [-1, 8]");
+    if (h->opt.fp64_tail_steps < 0) h->opt.fp64_tail_steps = o.precision == GSP2_PREC_FP64 ? 0 : 2;
     if (o.lp_tail_steps < 0 || o.fp64_tail_steps + o.lp_tail_steps > MAX_TAIL)
       return bail(GSP2_E_ARG, "lp_tail_steps must be >= 0 with lp_tail_steps + fp64_tail_steps <= 8");
     if (o.tc_schedule < 0 || o.tc_schedule > 1) return bail(GSP2_E_ARG, "tc_schedule must be 0 or 1");
@@ -444,6 +448,8 @@ extern "C" gsp2_status gsp2_plan_query(gsp2_handle h, gsp2_plan_info* info, int3
     info->ntiles = (int64_t)h->tiles.size();
     info->tile = SQ_TILE;
     info->ld_pad = LD_PAD;
+    info->step_launches = (int32_t)(h->ev.empty() ? std::max(h->total_steps, h->opt.max_steps) : h->ev.size() / 2);
+    info->fp64_tail_steps = h->opt.fp64_tail_steps;
   }
   for (int32_t k = 0; k < h->nparts; ++k) {
     if (s) s[k] = h->parts[k].s;
@@ -489,7 +495,7 @@ extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t byt
   h->have_forward = false;
   if (!h->cap_stream) CU(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
   if (h->opt.time_steps && h->ev.empty()) {
-    h->ev.resize(2 * (size_t)h->opt.max_steps);
+    h->ev.resize(2 * (size_t)std::max(h->total_steps, h->opt.max_steps));
     for (auto& e : h->ev) CU(h, cudaEventCreate(&e));
   }
   const WsLayout& L = h->L;
@@ -564,8 +570,18 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
   auto st = (DevState*)(w + L.state);
   auto alpha = (int8_t*)(w + L.alpha);
   auto A = [&](int i) { return (double*)(w + h->step_arena_off[i]); };
-  StepCtl ctl{st, alpha, (double*)(w + L.traces), (double*)(w + L.idem), h->nocc, h->opt.idem_tol,
-              h->opt.trace_tol, mode, mode == MODE_REPLAY ? nsteps : h->opt.max_steps, 1};
+  const bool fp64 = h->opt.precision == GSP2_PREC_FP64;
+  StepCtl ctl{st,
+              alpha,
+              (double*)(w + L.traces),
+              (double*)(w + L.idem),
+              h->nocc,
+              h->opt.idem_tol,
+              h->opt.trace_tol,
+              mode,
+              mode == MODE_REPLAY ? nsteps : (fp64 ? h->total_steps : h->opt.max_steps),
+              1,
+              (mode == MODE_RECORD && fp64) ? h->opt.fp64_tail_steps : 0};
   CU(h, launch_reset(st, alpha, mode == MODE_REPLAY ? alpha_user : nullptr, nsteps, h->opt.max_steps + HIST_EXTRA, s));
   CU(h, launch_bounds(h->n, rp, ci, hv, slots, BOUNDS_BLOCKS, st, s));
   const int prec = h->opt.precision;
@@ -627,8 +643,11 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
       CU(h, launch_square_fp64(parts, tiles, (int)h->tiles.size(), d[t & 1], d[(t + 1) & 1], slots, h->nslots, ctl, 0,
                                (t == 0 && h->opt.lp_tail_steps == 0) ? SQ_TAIL_FIRST : SQ_TAIL_NEXT, s));
     CU(h, launch_scatter(parts, sbl, (int)h->sblocks.size(), Sall, perm, pcol, nullptr, d[T & 1], pv, st, s));
+    if (h->opt.report_idem)
+      CU(h, launch_residual_fp64(parts, tiles, (int)h->tiles.size(), d[T & 1], nullptr, (double*)(w + L.rslots),
+                                 h->n, ctl, s));
     if (alpha_user)
-      CU(h, cudaMemcpyAsync(alpha_user, alpha + 1, (size_t)h->opt.max_steps, cudaMemcpyDeviceToDevice, s));
+      CU(h, cudaMemcpyAsync(alpha_user, alpha + 1, (size_t)h->opt.max_steps + MAX_TAIL, cudaMemcpyDeviceToDevice, s));
     return GSP2_OK;
   }
   CU(h, launch_gather(parts, gbl, (int)h->gblocks.size(), Sall, rp, ci, hv, A(0), (double*)slots, ctl, s));
@@ -641,8 +660,11 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
   }
   CU(h, launch_scatter(parts, sbl, (int)h->sblocks.size(), Sall, perm, pcol, (const double* const*)(w + L.step_arena),
                        nullptr, pv, st, s));
+  if (h->opt.report_idem)
+    CU(h, launch_residual_fp64(parts, tiles, (int)h->tiles.size(), nullptr, (const double* const*)(w + L.step_arena),
+                               (double*)(w + L.rslots), h->n, ctl, s));
   if (mode == MODE_RECORD && alpha_user)
-    CU(h, cudaMemcpyAsync(alpha_user, alpha + 1, (size_t)h->opt.max_steps, cudaMemcpyDeviceToDevice, s));
+    CU(h, cudaMemcpyAsync(alpha_user, alpha + 1, (size_t)h->opt.max_steps + MAX_TAIL, cudaMemcpyDeviceToDevice, s));
   return GSP2_OK;
 }
 
@@ -652,8 +674,8 @@ extern "C" gsp2_status gsp2_density(gsp2_handle h, const double* d_hvals, double
   if (!h->ws) return fail(h, GSP2_E_STATE, "no workspace bound");
   if (!d_hvals || !d_pvals) return fail(h, GSP2_E_ARG, "NULL H or P buffer");
   if (mode != MODE_RECORD && mode != MODE_REPLAY) return fail(h, GSP2_E_ARG, "mode must be RECORD or REPLAY");
-  if (mode == MODE_REPLAY && (!d_alpha || nsteps < 1 || nsteps > h->opt.max_steps))
-    return fail(h, GSP2_E_ARG, "REPLAY needs d_alpha and 1 <= nsteps <= max_steps");
+  if (mode == MODE_REPLAY && (!d_alpha || nsteps < 1 || nsteps > h->total_steps))
+    return fail(h, GSP2_E_ARG, "REPLAY needs d_alpha and 1 <= nsteps <= max_steps + fp64_tail_steps");
   if (mode == MODE_REPLAY && h->opt.precision != GSP2_PREC_FP64)
     return fail(h, GSP2_E_ARG, "REPLAY is available for the FP64 precision only");
   if (mode == MODE_RECORD) nsteps = 0;
@@ -711,6 +733,7 @@ extern "C" gsp2_status gsp2_sync_status(gsp2_handle h, gsp2_report* r) {
     r->eps_max = st.eps_max;
     r->trace = tr;
     r->idem = e;
+    r->idem_fro = st.idem_fro;
   }
   if (st.status != 0) {
     const char* what = st.status == ST_NOT_CONVERGED ? "not converged within max_steps"
@@ -739,7 +762,7 @@ extern "C" gsp2_status gsp2_step_times(gsp2_handle h, float* ms, int32_t cap) {
   if (!usable(h) || !ms) return fail(h, GSP2_E_ARG, "invalid handle or NULL output");
   if (h->ev.empty() || !h->have_forward) return fail(h, GSP2_E_STATE, "time_steps not set or no density call");
   CU(h, cudaDeviceSynchronize());
-  const int32_t m = std::min<int32_t>(cap, h->opt.max_steps);
+  const int32_t m = std::min<int32_t>(cap, (int32_t)(h->ev.size() / 2));
   for (int32_t i = 0; i < m; ++i) {
     ms[i] = 0.0f;
     cudaError_t e = cudaEventElapsedTime(&ms[i], h->ev[2 * i], h->ev[2 * i + 1]);
@@ -767,10 +790,10 @@ static gsp2_status enqueue_backward(gsp2_plan* h, const double* pbar, double* hb
   auto alpha = (int8_t*)(w + L.alpha);
   double* xb0 = (double*)(w + L.xb0);
   double* xb1 = (double*)(w + L.xb1);
-  const int k = h->opt.ckpt_every, M = h->opt.max_steps;
+  const int k = h->opt.ckpt_every, M = h->total_steps;
   const int nt = (int)h->tiles.size();
   StepCtl ctl{st, alpha, (double*)(w + L.traces), (double*)(w + L.idem), h->nocc, h->opt.idem_tol,
-              h->opt.trace_tol, MODE_REPLAY, M, 1};
+              h->opt.trace_tol, MODE_REPLAY, M, 1, 0};
   CU(h, launch_adj_seed(parts, gbl, (int)h->gblocks.size(), Sall, (const int32_t*)(w + L.invperm),
                         (const int64_t*)(w + L.pcolptr), pbar, xb0, s));
   for (int c0 = (M / k) * k; c0 >= 0; c0 -= k) {

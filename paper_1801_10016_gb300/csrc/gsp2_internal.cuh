@@ -39,6 +39,7 @@ struct ColBlock {  // COLS_PER_BLOCK consecutive local columns of one part
 // reductions; the block that finishes a reduction sets it back to zero.
 struct DevState {
   double eps_min, eps_max;
+  double idem_fro;     // idempotency report of the final P (core columns), -1 if not run
   unsigned int counter;
   int32_t stopped;     // 1: no further purification steps this call
   int32_t steps;       // purification steps applied so far
@@ -46,12 +47,13 @@ struct DevState {
   int32_t nonfinite;   // set by any block that meets NaN/Inf
   int32_t fp64_steps;
   int32_t timeout;     // a bounded device wait gave up
-  int32_t pad[5];
+  int32_t tail_left;   // FP64 path: alternating tail steps still to run (0: none)
+  int32_t pad[4];
 };
 
 enum : int32_t { ST_OK = 0, ST_NOT_CONVERGED = 5, ST_TRACE = 6, ST_NONFINITE = 7, ST_TIMEOUT = 9 };
 enum : int32_t { MODE_RECORD = 0, MODE_REPLAY = 1 };
-enum : int32_t { SQ_FORWARD = 0, SQ_RECOMPUTE = 1, SQ_TAIL_FIRST = 2, SQ_TAIL_NEXT = 3 };
+enum : int32_t { SQ_FORWARD = 0, SQ_RECOMPUTE = 1, SQ_TAIL_FIRST = 2, SQ_TAIL_NEXT = 3, SQ_RESIDUAL = 4 };
 
 // Arguments of the per-step trace bookkeeping done by the last block of a step.
 struct StepCtl {
@@ -65,6 +67,7 @@ struct StepCtl {
   int32_t mode;
   int32_t last_step;  // max_steps (RECORD) or nsteps (REPLAY)
   int32_t stop_lag;   // stopping test compares e_{i-1} with e_{i-1-stop_lag}
+  int32_t tail_steps; // RECORD: alternating steps after the stopping test (last_step includes them)
 };
 
 // Arguments of one tensor-core purification step (k_tc.cu).
@@ -171,23 +174,42 @@ __device__ __forceinline__ void finish_step(const StepCtl& c, int step, double t
   DevState* st = c.st;
   c.traces[step] = tN;
   st->steps = step;
-  bool stop = false;
+  bool stop = false, fire = false;
   if (step > 0) {
     const double e = c.traces[step - 1] - tY;
     c.idem[step - 1] = e;
     if (c.mode == MODE_RECORD && step >= 1 + c.stop_lag && fabs(e) <= c.idem_tol &&
         (e < 0.0 || e >= c.idem[step - 1 - c.stop_lag]))
-      stop = true;
+      fire = true;
     if (!isfinite(e)) st->nonfinite = 1;
   }
   if (!isfinite(tN)) st->nonfinite = 1;
   if (st->nonfinite) {
     st->status = ST_NONFINITE;
-    stop = true;
+    st->stopped = 1;
+    return;
   }
-  if (!stop && step >= c.last_step) {
+  if (c.mode == MODE_RECORD && st->tail_left > 0) {
+    // this step was one of the alternating tail steps
+    st->tail_left -= 1;
+    if (st->tail_left == 0) {
+      st->stopped = 1;
+    } else {
+      c.alpha[step + 1] = (int8_t)(-c.alpha[step]);
+    }
+    return;
+  }
+  const bool cap = step >= c.last_step - (c.mode == MODE_RECORD ? c.tail_steps : 0);
+  if (fire) stop = true;
+  if (!stop && cap) {
     stop = true;
     if (c.mode == MODE_RECORD && step > 0 && !(fabs(c.idem[step - 1]) <= c.idem_tol)) st->status = ST_NOT_CONVERGED;
+  }
+  if (stop && c.mode == MODE_RECORD && c.tail_steps > 0) {
+    // start the tail: first branch from the trace rule, then alternating
+    st->tail_left = c.tail_steps;
+    c.alpha[step + 1] = (tN <= (double)c.nocc) ? (int8_t)1 : (int8_t)-1;
+    return;
   }
   if (stop) {
     st->stopped = 1;

@@ -15,6 +15,9 @@ cudaError_t launch_gather(const PartDesc* parts, const ColBlock* blocks, int nbl
 cudaError_t launch_square_fp64(const PartDesc* parts, const Tile* tiles, int ntiles, const double* xin,
                                double* xout, double2* slots, int nslots, const StepCtl& ctl, int step, int mode,
                                cudaStream_t s);
+cudaError_t launch_residual_fp64(const PartDesc* parts, const Tile* tiles, int ntiles, const double* x,
+                                 const double* const* x_of_step, double* rslots, int64_t n, const StepCtl& ctl,
+                                 cudaStream_t s);
 cudaError_t launch_square_fp32(const PartDesc* parts, const Tile* tiles, int ntiles, const float* xin, float* xout,
                                double2* slots, int nslots, const StepCtl& ctl, int step, cudaStream_t s);
 cudaError_t launch_scatter(const PartDesc* parts, const ColBlock* blocks, int nblocks, const int32_t* Sall,

@@ -68,6 +68,8 @@ __global__ void reset_kernel(DevState* st, int8_t* alpha, const int8_t* alpha_in
     st->nonfinite = 0;
     st->fp64_steps = 0;
     st->timeout = 0;
+    st->tail_left = 0;
+    st->idem_fro = -1.0;
     st->counter = 0;
   }
   for (int i = threadIdx.x; i < n_alpha; i += blockDim.x)
@@ -163,12 +165,18 @@ struct Vec2<float> {
   using V = float2;
 };
 
+//
+// SQ_RESIDUAL - idempotency report of the final iterate X (from `xin_table[steps]` when
+//               given, else `xin`): no write; the block adds sum (X^2 - X)_ij^2 over the
+//               core columns j of its tile (and of the mirrored tile) to rslots, and the
+//               last block stores sqrt(sum / N) in the state.
 template <typename T>
 __global__ void __launch_bounds__(256, 2) square_simt_kernel(const PartDesc* __restrict__ parts,
                                                              const Tile* __restrict__ tiles,
                                                              const T* __restrict__ xin, T* __restrict__ xout,
                                                              double2* __restrict__ slots, int nslots, StepCtl ctl,
-                                                             int step, int mode) {
+                                                             int step, int mode, const T* const* xin_table,
+                                                             double* __restrict__ rslots, int64_t n) {
   using V2 = typename Vec2<T>::V;
   if (mode == SQ_RECOMPUTE) {
     if (step >= *(volatile int32_t*)&ctl.st->steps) return;
@@ -183,7 +191,8 @@ __global__ void __launch_bounds__(256, 2) square_simt_kernel(const PartDesc* __r
   __shared__ __align__(16) T Bs[2][BK][SQ_TILE];
   const Tile t = tiles[blockIdx.x];
   const PartDesc p = parts[t.part];
-  const T* X = xin + p.off;
+  const T* xbase = (mode == SQ_RESIDUAL && xin_table) ? xin_table[step - 1] : xin;
+  const T* X = xbase + p.off;
   const int64_t ld = p.ld;
   const int r0 = t.ti * SQ_TILE, c0 = t.tj * SQ_TILE;
   const int kend = (p.s + BK - 1) / BK * BK;
@@ -235,6 +244,34 @@ __global__ void __launch_bounds__(256, 2) square_simt_kernel(const PartDesc* __r
         for (int jj = 0; jj < 4; ++jj) acc[i][jj] = fma(a[i], b[jj], acc[i][jj]);
     }
     __syncthreads();
+  }
+
+  if (mode == SQ_RESIDUAL) {
+    double res = 0.0;
+    const int rb = r0 + tx * 4, cb = c0 + ty * 4;
+#pragma unroll
+    for (int jj = 0; jj < 4; ++jj) {
+      const int c = cb + jj;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int r = rb + i;
+        const double d = (double)acc[i][jj] - (double)X[(int64_t)c * ld + r];
+        if (c < p.c) res += d * d;
+        if (t.ti != t.tj && r < p.c) res += d * d;
+      }
+    }
+    const double2 sr = block_sum2(res, 0.0);
+    if (tid == 0) rslots[blockIdx.x] = sr.x;
+    if (last_block_ticket(&ctl.st->counter)) {
+      double a = 0.0;
+      for (unsigned int k = tid; k < gridDim.x; k += blockDim.x) a += ld_cg(&rslots[k]);
+      const double2 sum = block_sum2(a, 0.0);
+      if (tid == 0) {
+        ctl.st->idem_fro = sqrt(sum.x / (double)n);
+        ctl.st->counter = 0;
+      }
+    }
+    return;
   }
 
   // branch of this step
@@ -356,13 +393,23 @@ cudaError_t launch_gather(const PartDesc* parts, const ColBlock* blocks, int nbl
 cudaError_t launch_square_fp64(const PartDesc* parts, const Tile* tiles, int ntiles, const double* xin,
                                double* xout, double2* slots, int nslots, const StepCtl& ctl, int step, int mode,
                                cudaStream_t s) {
-  square_simt_kernel<double><<<ntiles, 256, 0, s>>>(parts, tiles, xin, xout, slots, nslots, ctl, step, mode);
+  square_simt_kernel<double><<<ntiles, 256, 0, s>>>(parts, tiles, xin, xout, slots, nslots, ctl, step, mode,
+                                                    nullptr, nullptr, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual_fp64(const PartDesc* parts, const Tile* tiles, int ntiles, const double* x,
+                                 const double* const* x_of_step, double* rslots, int64_t n, const StepCtl& ctl,
+                                 cudaStream_t s) {
+  square_simt_kernel<double><<<ntiles, 256, 0, s>>>(parts, tiles, x, nullptr, nullptr, 0, ctl, 0, SQ_RESIDUAL,
+                                                    x_of_step, rslots, n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_square_fp32(const PartDesc* parts, const Tile* tiles, int ntiles, const float* xin, float* xout,
                                double2* slots, int nslots, const StepCtl& ctl, int step, cudaStream_t s) {
-  square_simt_kernel<float><<<ntiles, 256, 0, s>>>(parts, tiles, xin, xout, slots, nslots, ctl, step, SQ_FORWARD);
+  square_simt_kernel<float><<<ntiles, 256, 0, s>>>(parts, tiles, xin, xout, slots, nslots, ctl, step, SQ_FORWARD,
+                                                   nullptr, nullptr, 0);
   return cudaGetLastError();
 }
 

@@ -36,19 +36,20 @@ class Options(C.Structure):
     _fields_ = [("max_steps", C.c_int32), ("idem_tol", C.c_double), ("trace_tol", C.c_double),
                 ("precision", C.c_int32), ("fp64_tail_steps", C.c_int32), ("ckpt_every", C.c_int32),
                 ("use_graph", C.c_int32), ("time_steps", C.c_int32), ("lp_tail_steps", C.c_int32),
-                ("tc_schedule", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("tc_schedule", C.c_int32), ("report_idem", C.c_int32), ("reserved", C.c_int32 * 4)]
 
 
 class Report(C.Structure):
     _fields_ = [("status", C.c_int32), ("steps", C.c_int32), ("stopped", C.c_int32), ("fp64_steps", C.c_int32),
-                ("eps_min", C.c_double), ("eps_max", C.c_double), ("trace", C.c_double), ("idem", C.c_double)]
+                ("eps_min", C.c_double), ("eps_max", C.c_double), ("trace", C.c_double), ("idem", C.c_double),
+                ("idem_fro", C.c_double)]
 
 
 class PlanInfo(C.Structure):
     _fields_ = [("n", C.c_int64), ("nocc", C.c_int64), ("nparts", C.c_int32), ("max_s", C.c_int32),
                 ("sum_s", C.c_int64), ("sum_s2", C.c_double), ("sum_s3", C.c_double), ("nnz_h", C.c_int64),
                 ("nnz_p", C.c_int64), ("arena_elems", C.c_int64), ("ntiles", C.c_int64), ("tile", C.c_int32),
-                ("ld_pad", C.c_int32)]
+                ("ld_pad", C.c_int32), ("step_launches", C.c_int32), ("fp64_tail_steps", C.c_int32)]
 
 
 _lib = None
@@ -225,9 +226,14 @@ class GSP2:
         k = rep["steps"]
         return dict(traces=tr[:k + 1], idem=e[:k], alphas=a[:k].astype(int).tolist(), report=rep, status=st)
 
+    @property
+    def alpha_len(self):
+        """Length of the branch-sequence buffer a density call may fill (max_steps + 8)."""
+        return self.options.max_steps + 8
+
     def step_times(self):
         """Per-step device milliseconds of the last density call (needs time_steps=1)."""
-        ms = np.zeros(self.options.max_steps, np.float32)
+        ms = np.zeros(self.info.step_launches, np.float32)
         self._check(self._lib.gsp2_step_times(self._h, _ptr(ms), len(ms)))
         return ms
 

@@ -95,3 +95,14 @@ def test_backward_state_errors(g):
     with pytest.raises(g.GSP2Error) as e:
         plan0.backward(torch.zeros(plan0.nnz_p, dtype=torch.float64, device="cuda:0"))
     assert e.value.status == g.E_STATE
+
+
+def test_adjoint_through_tail_steps(g):
+    s = make_tb_system(48, 4, 3.0, seed=21)
+    plan, h, hist, pb, Pbar, hb = run_adjoint(g, s, fp64_tail_steps=2, ckpt_every=3)
+    ref = oracle.gsp2(s.n, s.rowptr, s.colind, s.vals, s.nocc, s.part, s.nparts, s.g_rowptr, s.g_colind,
+                      tail_steps=2)
+    assert hist["alphas"] == ref.alphas
+    want = oracle.gsp2_adjoint(s.n, s.rowptr, s.colind, s.vals, ref, Pbar)
+    got = hb.cpu().numpy()
+    assert np.max(np.abs(got - want)) <= 1e-9 * max(1.0, np.max(np.abs(want)))

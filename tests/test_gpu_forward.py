@@ -30,7 +30,7 @@ def run_gpu(g, s_or_args, **opt):
     s = s_or_args
     plan = g.GSP2(s.n, s.rowptr, s.colind, s.nocc, s.part, s.nparts, s.g_rowptr, s.g_colind, device="cuda:0", **opt)
     h = torch.from_numpy(s.vals).to("cuda:0")
-    alpha = torch.zeros(plan.options.max_steps, dtype=torch.int8, device="cuda:0")
+    alpha = torch.zeros(plan.alpha_len, dtype=torch.int8, device="cuda:0")
     p = plan.density(h, alpha=alpha)
     hist = plan.history()
     return plan, h, p, alpha, hist
@@ -178,3 +178,33 @@ def test_step_times_recorded_in_graph_mode(g):
     k = hist["report"]["steps"]
     assert np.all(ms[:k] > 0.0)
     assert np.all(np.isfinite(ms))
+
+
+def test_idempotency_report_matches_oracle(g):
+    """report_idem: sqrt(sum_k ||(X_k^2 - X_k)[:, cores]||_F^2 / N) of the final iterates."""
+    s = make_workload("tb512")
+    plan, h, p, alpha, hist = run_gpu(g, s, report_idem=1)
+    ref = oracle.gsp2(s.n, s.rowptr, s.colind, s.vals, s.nocc, s.part, s.nparts, s.g_rowptr, s.g_colind)
+    want = np.sqrt(sum(np.linalg.norm((X @ X - X)[:, :c]) ** 2 for X, c in zip(ref.X, ref.ncore)) / s.n)
+    got = hist["report"]["idem_fro"]
+    assert got == pytest.approx(want, rel=1e-6, abs=1e-15)
+    plan2, _, _, _, hist2 = run_gpu(g, s)
+    assert hist2["report"]["idem_fro"] == -1.0
+
+
+def test_fp64_tail_matches_oracle_tail(g):
+    """fp64_tail_steps = 2 on the FP64 path: the loop continues past the stopping test
+    with two alternating steps, as the oracle's tail."""
+    s = make_workload("tb512")
+    plan, h, p, alpha, hist = run_gpu(g, s, fp64_tail_steps=2, report_idem=1)
+    assert hist["status"] == 0
+    ref = oracle.gsp2(s.n, s.rowptr, s.colind, s.vals, s.nocc, s.part, s.nparts, s.g_rowptr, s.g_colind,
+                      tail_steps=2)
+    check_against_oracle(plan, p, hist, s, ref=ref)
+    assert hist["alphas"] == ref.alphas and hist["alphas"][-1] == -hist["alphas"][-2]
+    assert hist["report"]["idem_fro"] < 1e-10
+    # replaying the recorded sequence (tail included) reproduces P bitwise
+    import torch
+    k = hist["report"]["steps"]
+    p2 = plan.density(h, alpha=alpha, mode="replay", nsteps=k)
+    assert plan.status()[0] == 0 and torch.equal(p, p2)

@@ -122,3 +122,21 @@ def test_persistent_schedule_matches_one_cta_per_tile(g, prec, case):
     _, p1, h1 = run(g, s, prec, tc_schedule=1, max_steps=6)
     assert h0["alphas"] == h1["alphas"]
     assert np.array_equal(p0, p1)
+
+
+@pytest.mark.parametrize("case", ["tb512", "tb30k"])
+def test_tf32x3_meets_the_gates_against_the_oracle_with_the_same_tail(g, case):
+    """Mixed precision (tf32x3 squarings, FP64 traces, two FP64 tail steps) against the FP64
+    oracle with the same two tail steps: max|dP| <= 1e-6 and the column idempotency
+    ||P^2 - P||_F / sqrt(N) (part by part) <= 1e-8."""
+    s = make_workload(case)
+    plan, p, hist = run(g, s, "tf32x3", fp64_tail_steps=2, report_idem=1)
+    assert hist["status"] == 0
+    ref = oracle.gsp2(s.n, s.rowptr, s.colind, s.vals, s.nocc, s.part, s.nparts, s.g_rowptr, s.g_colind,
+                      tail_steps=2)
+    want = ref.p_on_pattern(plan.p_colptr, plan.p_rowind)
+    err = float(np.max(np.abs(p - want)))
+    idem = hist["report"]["idem_fro"]
+    print(f"{case} tf32x3 + 2 FP64 tail vs oracle + 2 tail: max|dP|={err:.3e} idem_fro={idem:.3e}")
+    assert err <= 1e-6, err
+    assert 0.0 <= idem <= 1e-8, idem

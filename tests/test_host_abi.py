@@ -38,7 +38,12 @@ def _plan(g, s, **kw):
 def test_default_options(g):
     o = g.default_options()
     assert o.max_steps == 45 and o.precision == 0 and o.use_graph == 1 and o.ckpt_every == 8
-    assert o.idem_tol == 1e-3
+    assert o.idem_tol == 1e-3 and o.fp64_tail_steps == -1 and o.lp_tail_steps == 0 and o.tc_schedule == 0
+    # "-1" resolves to no tail for FP64 (the paper's method) and two FP64 steps otherwise
+    s = make_workload("tb512")
+    assert _plan(g, s).info.fp64_tail_steps == 0
+    assert _plan(g, s, precision="tf32x3").info.fp64_tail_steps == 2
+    assert _plan(g, s, fp64_tail_steps=3).info.fp64_tail_steps == 3
 
 
 def test_halos_and_p_pattern_match_section_2_2(g):

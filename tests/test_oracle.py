@@ -287,3 +287,30 @@ def test_gsp2_assembles_core_columns(tb512):
             np.testing.assert_array_equal(P[S, g], X[:, j])
     # halos are non-empty, so some entries of P lie outside the diagonal blocks
     assert any(len(S) > c for S, c in zip(r.S, r.ncore))
+
+
+# ---------------------------------------------------------------- optional tail
+
+def test_tail_steps_alternate_and_purify(tb512, tb512_dense):
+    """Plain SP2 with a tail stays on the exact projector; in G-SP2 the alternating tail
+    removes the drift left by a core trace that cannot reach Nocc."""
+    P0, r0 = oracle.sp2_dense(tb512_dense, tb512.nocc, 45)
+    P2, r2 = oracle.sp2_dense(tb512_dense, tb512.nocc, 45, tail_steps=2)
+    assert r2["alphas"][:len(r0["alphas"])] == r0["alphas"] and len(r2["alphas"]) == len(r0["alphas"]) + 2
+    assert r2["alphas"][-1] == -r2["alphas"][-2]
+    assert np.max(np.abs(P2 - oracle.eig_projector(tb512_dense, tb512.nocc))) <= 1e-10
+    # the recorded sequence, tail included, is one SP2 polynomial
+    assert np.max(np.abs(P2 - oracle.sp2_map_on_spectrum(tb512_dense, r2["alphas"], r2["bounds"]))) <= 1e-11
+    kw = dict(max_steps=45)
+    args = (tb512.n, tb512.rowptr, tb512.colind, tb512.vals, tb512.nocc, tb512.part, tb512.nparts,
+            tb512.g_rowptr, tb512.g_colind)
+    g0 = oracle.gsp2(*args, **kw)
+    g2 = oracle.gsp2(*args, tail_steps=2, **kw)
+    assert g2.alphas[:len(g0.alphas)] == g0.alphas and g2.alphas[-1] == -g2.alphas[-2]
+
+    def part_idem(r):
+        return np.sqrt(sum(np.linalg.norm(X @ X - X) ** 2 for X in r.X) / tb512.n)
+    assert part_idem(g0) > 1e-8 and part_idem(g2) < 1e-10
+    # a replayed sequence runs exactly its length (the tail is part of it)
+    g3 = oracle.gsp2(*args, alphas=g2.alphas, tail_steps=5)
+    assert g3.alphas == g2.alphas and np.array_equal(g3.dense_p(), g2.dense_p())
