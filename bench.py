@@ -167,6 +167,18 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def aggregate(local_seconds, units_per_rank, world, device):
+    """Whole-job throughput of N replicas: every rank processed `units_per_rank` units in
+    `local_seconds`; the job took the slowest rank's time (max over ranks)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(local_seconds)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        local_seconds = float(t.item())
+    return world * units_per_rank / local_seconds, local_seconds
+
+
 def time_builds(plan, h_dev, p_dev, steps, flush, stream):
     """Device time (ms) of `steps` P-builds, L2 flushed before each, plus the per-step
     kernel times of each build."""
@@ -232,13 +244,8 @@ def run_ours(args):
         dev_ms, step_ms = time_builds(plan, h_dev, p_dev, args.steps, flush, stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
-    tot = sum(dev_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([tot], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        tot = float(t.item())
+    value, tot = aggregate(sum(dev_ms) / 1e3, args.steps, world, dev)
     st, rep = plan.status()
-    value = world * args.steps / tot
     ms_per_step = 1e3 * tot / args.steps
 
     # ---- end to end through the public API: pinned host H in, P back to pinned host
@@ -255,12 +262,7 @@ def run_ours(args):
         p_host.copy_(p_dev, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_s = e0.elapsed_time(e1) / 1e3
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = world * e_steps / e2e_s
+    e2e, _ = aggregate(e0.elapsed_time(e1) / 1e3, e_steps, world, dev)
 
     # ---- roofline of the dominant kernel (the purification step)
     peaks, src = load_peaks()

@@ -65,7 +65,10 @@ typedef enum {
   GSP2_PREC_TF32 = 2,
   GSP2_PREC_BF16 = 3,
   GSP2_PREC_BF16X3 = 4, /* split operands hi+lo in BF16, three products, FP32 accumulate */
-  GSP2_PREC_TF32X3 = 5  /* split operands hi+lo in TF32, three products, FP32 accumulate */
+  GSP2_PREC_TF32X3 = 5, /* split operands hi+lo in TF32, three products, FP32 accumulate */
+  GSP2_PREC_FP64_EMU = 6 /* FP64 results; every product X X rebuilt from 8 base-2^7 digits of X
+                            held in BF16 (36 exact BF16 tensor-core products per tile, groups
+                            summed as 64-bit fixed point), FP64 master copy and epilogue */
 } gsp2_precision;
 
 typedef enum {

@@ -29,6 +29,10 @@ struct WsLayout {
   size_t maps;         // CUtensorMap[2 buffers][hi, lo][nparts]
   size_t master_of_step;
   size_t d[2];         // FP64 arenas of the tail steps
+  // FP64 products from BF16 digits
+  size_t oz_slice[OZ_SLICES];  // BF16 digit arenas of the current iterate
+  size_t oz_acc;               // 64-bit fixed-point accumulator of X X
+  size_t oz_maps;              // CUtensorMap[OZ_SLICES][nparts]
   size_t slots, rslots, state, alpha, traces, idem, step_arena;
   size_t arena0, arena1;       // ping-pong iterates
   std::vector<size_t> ckpt;    // X_0, X_k, X_2k, ... (adjoint checkpoints)
@@ -111,6 +115,9 @@ static size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr int HIST_EXTRA = 16;
 constexpr int MAX_TAIL = 8;
 
+// FP64 results: native FP64 steps or FP64 products rebuilt from BF16 digits
+static bool fp64_like(int prec) { return prec == GSP2_PREC_FP64 || prec == GSP2_PREC_FP64_EMU; }
+
 // tensor-core operand kind (-1: FP32 CUDA cores, 0: BF16, 1: TF32) and products per tile
 static int prec_kind(int prec) {
   return prec == GSP2_PREC_FP32 ? -1 : (prec == GSP2_PREC_BF16 || prec == GSP2_PREC_BF16X3) ? 0 : 1;
@@ -173,7 +180,7 @@ extern "C" const char* gsp2_last_error(gsp2_handle h) { return h ? h->err.c_str(
 
 static void build_layout(gsp2_plan* h) {
   WsLayout& L = h->L;
-  h->total_steps = h->opt.max_steps + (h->opt.precision == GSP2_PREC_FP64 ? h->opt.fp64_tail_steps : 0);
+  h->total_steps = h->opt.max_steps + (fp64_like(h->opt.precision) ? h->opt.fp64_tail_steps : 0);
   size_t o = 0;
   auto take = [&](size_t bytes) {
     const size_t at = o;
@@ -207,7 +214,7 @@ static void build_layout(gsp2_plan* h) {
   L.master_of_step = take(((size_t)h->opt.max_steps + 1 + MAX_TAIL) * sizeof(float*));
   const size_t ab = (size_t)h->arena_elems * sizeof(double);
   const int prec = h->opt.precision;
-  if (prec != GSP2_PREC_FP64) {
+  if (!fp64_like(prec)) {
     // low precision: FP32 masters, operands, tensor maps, FP64 tail arenas; no adjoint
     const size_t af = (size_t)h->arena_elems * sizeof(float);
     L.mf[0] = take(af);
@@ -247,6 +254,11 @@ static void build_layout(gsp2_plan* h) {
     L.xb0 = take(ab);
     L.xb1 = take(ab);
   }
+  if (prec == GSP2_PREC_FP64_EMU) {
+    for (int t = 0; t < OZ_SLICES; ++t) L.oz_slice[t] = take((size_t)h->arena_elems * 2);
+    L.oz_acc = take(ab);
+    L.oz_maps = take((size_t)OZ_SLICES * h->parts.size() * 128);
+  }
   L.total = o;
   // arena of each iterate X_i: checkpoints where i is a multiple of k, else ping-pong
   h->step_arena_off.assign((size_t)h->total_steps + 1, 0);
@@ -277,14 +289,14 @@ extern "C" gsp2_status gsp2_create(int64_t n, const int64_t* rowptr, const int32
     if (!part) return bail(GSP2_E_ARG, "part is NULL");
     if (o.max_steps < 1 || o.max_steps > 1024) return bail(GSP2_E_ARG, "max_steps must be in [1, 1024]");
     if (!(o.idem_tol >= 0.0) || !(o.trace_tol >= 0.0)) return bail(GSP2_E_ARG, "tolerances must be >= 0");
-    if (o.precision < GSP2_PREC_FP64 || o.precision > GSP2_PREC_TF32X3) return bail(GSP2_E_ARG, "unknown precision");
+    if (o.precision < GSP2_PREC_FP64 || o.precision > GSP2_PREC_FP64_EMU) return bail(GSP2_E_ARG, "unknown precision");
     if (o.fp64_tail_steps < -1 || o.fp64_tail_steps > MAX_TAIL)
       return bail(GSP2_E_ARG, "fp64_tail_steps must be in [-1, 8]");
-    if (h->opt.fp64_tail_steps < 0) h->opt.fp64_tail_steps = o.precision == GSP2_PREC_FP64 ? 0 : 2;
+    if (h->opt.fp64_tail_steps < 0) h->opt.fp64_tail_steps = fp64_like(o.precision) ? 0 : 2;
     if (o.lp_tail_steps < 0 || o.fp64_tail_steps + o.lp_tail_steps > MAX_TAIL)
       return bail(GSP2_E_ARG, "lp_tail_steps must be >= 0 with lp_tail_steps + fp64_tail_steps <= 8");
     if (o.tc_schedule < 0 || o.tc_schedule > 1) return bail(GSP2_E_ARG, "tc_schedule must be 0 or 1");
-    if (o.lp_tail_steps > 0 && (o.precision == GSP2_PREC_FP64 || o.precision == GSP2_PREC_FP32))
+    if (o.lp_tail_steps > 0 && (fp64_like(o.precision) || o.precision == GSP2_PREC_FP32))
       return bail(GSP2_E_ARG, "lp_tail_steps needs a tensor-core precision");
     if (o.ckpt_every < 0) return bail(GSP2_E_ARG, "ckpt_every must be >= 0");
     if ((g_rowptr == nullptr) != (g_colind == nullptr)) return bail(GSP2_E_ARG, "graph: give both arrays or neither");
@@ -516,7 +528,22 @@ extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t byt
   CU(h, up(L.tiles, h->tiles.data(), h->tiles.size() * sizeof(Tile)));
   CU(h, up(L.tc_tiles, h->tc_tiles.data(), h->tc_tiles.size() * sizeof(Tile)));
   CU(h, up(L.gblocks_ld, h->gblocks_ld.data(), h->gblocks_ld.size() * sizeof(ColBlock)));
-  if (h->opt.precision != GSP2_PREC_FP64) {
+  if (h->opt.precision == GSP2_PREC_FP64_EMU) {
+    void* enc = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    CU(h, cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &enc, 12000, cudaEnableDefault, &q));
+    if (!enc || q != cudaDriverEntryPointSuccess)
+      return fail(h, GSP2_E_CUDA, "cuTensorMapEncodeTiled not available from the driver");
+    const size_t np = h->parts.size();
+    std::vector<unsigned char> maps((size_t)OZ_SLICES * np * 128, 0);
+    for (int t = 0; t < OZ_SLICES; ++t) {
+      const int r = encode_part_maps(enc, maps.data() + (size_t)t * np * 128, h->parts.data(), (int)np,
+                                     h->ws + L.oz_slice[t], 0);
+      if (r != 0) return fail(h, GSP2_E_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string(r));
+    }
+    CU(h, up(L.oz_maps, maps.data(), maps.size()));
+  }
+  if (!fp64_like(h->opt.precision)) {
     std::vector<const float*> mt((size_t)h->opt.max_steps + 1 + MAX_TAIL);
     for (size_t i = 0; i < mt.size(); ++i) mt[i] = (const float*)(h->ws + L.mf[i & 1]);
     CU(h, up(L.master_of_step, mt.data(), mt.size() * sizeof(float*)));
@@ -570,7 +597,7 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
   auto st = (DevState*)(w + L.state);
   auto alpha = (int8_t*)(w + L.alpha);
   auto A = [&](int i) { return (double*)(w + h->step_arena_off[i]); };
-  const bool fp64 = h->opt.precision == GSP2_PREC_FP64;
+  const bool fp64 = fp64_like(h->opt.precision);
   StepCtl ctl{st,
               alpha,
               (double*)(w + L.traces),
@@ -585,7 +612,7 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
   CU(h, launch_reset(st, alpha, mode == MODE_REPLAY ? alpha_user : nullptr, nsteps, h->opt.max_steps + HIST_EXTRA, s));
   CU(h, launch_bounds(h->n, rp, ci, hv, slots, BOUNDS_BLOCKS, st, s));
   const int prec = h->opt.precision;
-  if (prec != GSP2_PREC_FP64) {
+  if (!fp64_like(prec)) {
     // low-precision phase, stopping test gated at max(idem_tol, 16 N u)
     const int kind = prec_kind(prec), nprod = prec_nprod(prec);
     StepCtl lp = ctl;
@@ -651,11 +678,30 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
     return GSP2_OK;
   }
   CU(h, launch_gather(parts, gbl, (int)h->gblocks.size(), Sall, rp, ci, hv, A(0), (double*)slots, ctl, s));
+  const bool emu = prec == GSP2_PREC_FP64_EMU;
+  OzSlices sl{};
+  OzGroupArgs oz{};
+  if (emu) {
+    for (int t = 0; t < OZ_SLICES; ++t) sl.s[t] = (uint16_t*)(w + L.oz_slice[t]);
+    oz.parts = parts;
+    oz.tiles = (const Tile*)(w + L.tc_tiles);
+    oz.ntiles = (int)h->tc_tiles.size();
+    oz.maps = w + L.oz_maps;
+    oz.nparts = (int)h->parts.size();
+    oz.acc = (long long*)(w + L.oz_acc);
+    oz.st = st;
+    CU(h, launch_oz_slice(parts, (const ColBlock*)(w + L.gblocks_ld), (int)h->gblocks_ld.size(), A(0), sl, s));
+  }
   for (int i = 1; i <= ctl.last_step; ++i) {
     const double* xin = A(i - 1);
     double* xout = A(i);
     if (!h->ev.empty()) CU(h, cudaEventRecordWithFlags(h->ev[2 * (i - 1)], s, cudaEventRecordExternal));
-    CU(h, launch_square_fp64(parts, tiles, (int)h->tiles.size(), xin, xout, slots, h->nslots, ctl, i, SQ_FORWARD, s));
+    if (emu)
+      CU(h, launch_oz_step(oz, h->num_sms, (const ColBlock*)(w + L.gblocks_ld), (int)h->gblocks_ld.size(), xin, xout,
+                           sl, slots, ctl, i, SQ_FORWARD, s));
+    else
+      CU(h, launch_square_fp64(parts, tiles, (int)h->tiles.size(), xin, xout, slots, h->nslots, ctl, i, SQ_FORWARD,
+                               s));
     if (!h->ev.empty()) CU(h, cudaEventRecordWithFlags(h->ev[2 * (i - 1) + 1], s, cudaEventRecordExternal));
   }
   CU(h, launch_scatter(parts, sbl, (int)h->sblocks.size(), Sall, perm, pcol, (const double* const*)(w + L.step_arena),
@@ -676,7 +722,7 @@ extern "C" gsp2_status gsp2_density(gsp2_handle h, const double* d_hvals, double
   if (mode != MODE_RECORD && mode != MODE_REPLAY) return fail(h, GSP2_E_ARG, "mode must be RECORD or REPLAY");
   if (mode == MODE_REPLAY && (!d_alpha || nsteps < 1 || nsteps > h->total_steps))
     return fail(h, GSP2_E_ARG, "REPLAY needs d_alpha and 1 <= nsteps <= max_steps + fp64_tail_steps");
-  if (mode == MODE_REPLAY && h->opt.precision != GSP2_PREC_FP64)
+  if (mode == MODE_REPLAY && !fp64_like(h->opt.precision))
     return fail(h, GSP2_E_ARG, "REPLAY is available for the FP64 precision only");
   if (mode == MODE_RECORD) nsteps = 0;
   int dev = 0;
@@ -816,7 +862,7 @@ static gsp2_status enqueue_backward(gsp2_plan* h, const double* pbar, double* hb
 
 extern "C" gsp2_status gsp2_backward(gsp2_handle h, const double* d_pbar, double* d_hbar, void* stream) {
   if (!usable(h)) return fail(h, GSP2_E_ARG, "invalid handle");
-  if (h->opt.ckpt_every <= 0 || h->opt.precision != GSP2_PREC_FP64)
+  if (h->opt.ckpt_every <= 0 || !fp64_like(h->opt.precision))
     return fail(h, GSP2_E_STATE, "the adjoint needs an FP64 plan built with ckpt_every > 0");
   if (!h->ws || !h->have_forward) return fail(h, GSP2_E_STATE, "gsp2_backward needs a completed density call");
   if (!d_pbar || !d_hbar) return fail(h, GSP2_E_ARG, "NULL Pbar or Hbar buffer");

@@ -89,6 +89,26 @@ struct TcStepArgs {
   int tail;                // 0: loop step; 1: first alternating tail step; 2: further ones
 };
 
+// FP64 products rebuilt from BF16 digits (k_oz.cu)
+constexpr int OZ_SLICES = 8;  // base-2^7 digits per entry
+
+struct OzSlices {
+  uint16_t* s[OZ_SLICES];  // BF16 digit arenas (same element indexing as the arenas)
+};
+
+struct OzGroupArgs {
+  const PartDesc* parts;
+  const Tile* tiles;  // 128x128 upper tiles
+  int ntiles;
+  const void* maps;   // CUtensorMap[OZ_SLICES][nparts] over the digit arenas
+  int nparts;
+  long long* acc;     // 64-bit fixed-point accumulator, resolution 2^-56
+  DevState* st;
+  int group;          // d: this launch adds 2^{-7(d+2)} sum_{a+b=d} S_a S_b
+  int first;          // 1: store instead of add
+  int mode;           // SQ_FORWARD or a tail mode (skip rules)
+};
+
 // ------------------------------------------------------------------ device helpers
 
 __device__ __forceinline__ double ld_cg(const double* p) { return __ldcg(p); }

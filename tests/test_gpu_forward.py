@@ -208,3 +208,31 @@ def test_fp64_tail_matches_oracle_tail(g):
     k = hist["report"]["steps"]
     p2 = plan.density(h, alpha=alpha, mode="replay", nsteps=k)
     assert plan.status()[0] == 0 and torch.equal(p, p2)
+
+
+# ---------------------------------------------------------------- FP64 from BF16 digits
+
+@pytest.mark.parametrize("case", ["tb512", "ragged36", "ragged132", "ragged280", "tb30k"])
+def test_fp64_emulated_matches_oracle(g, case):
+    """precision fp64e: X X rebuilt from 8 BF16 digits on the tensor cores, FP64 master and
+    bookkeeping; held to the FP64 parity bar (1e-10) against the oracle."""
+    s = {"tb512": lambda: make_workload("tb512"), "ragged36": lambda: make_tb_system(9, 3, 3.0, seed=109),
+         "ragged132": lambda: make_tb_system(33, 1, 3.0, seed=9), "ragged280": lambda: make_tb_system(70, 4, 4.0, seed=170),
+         "tb30k": lambda: make_workload("tb30k")}[case]()
+    plan, h, p, alpha, hist = run_gpu(g, s, precision="fp64e")
+    assert hist["status"] == 0
+    err = check_against_oracle(plan, p, hist, s)
+    print(f"fp64e {case}: steps={hist['report']['steps']} max|dP|={err:.3e}")
+
+
+def test_fp64_emulated_one_step_error(g):
+    """One emulated step against the FP64 product, element by element: the digit expansion
+    truncates below 2^-56 and drops products of order 2^{-7 (d+2)} for d >= 8."""
+    s = make_workload("tb512")
+    plan, h, p, alpha, hist = run_gpu(g, s, precision="fp64e", max_steps=1)
+    ref = oracle.gsp2(s.n, s.rowptr, s.colind, s.vals, s.nocc, s.part, s.nparts, s.g_rowptr, s.g_colind,
+                      max_steps=1)
+    want = ref.p_on_pattern(plan.p_colptr, plan.p_rowind)
+    err = float(np.max(np.abs(p.cpu().numpy() - want)))
+    print(f"fp64e one step: max|dY|={err:.3e}")
+    assert err <= 1e-13
