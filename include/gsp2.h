@@ -98,7 +98,10 @@ typedef struct {
                               next tile's MMAs; 1 = one CTA per tile */
   int32_t report_idem;     /* 1: after each density call, one extra FP64 pass over the final
                               iterates computes the idempotency report idem_fro (default 0) */
-  int32_t reserved[4];
+  int32_t fp64_tail_emulated; /* low-precision modes: 1 (default) runs the FP64 tail steps with
+                                 the products rebuilt from BF16 digits (as GSP2_PREC_FP64_EMU),
+                                 0 on the FP64 units */
+  int32_t reserved[3];
 } gsp2_options;
 
 /* Per-call report, read back by gsp2_sync_status. */

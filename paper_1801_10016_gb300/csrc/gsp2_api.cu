@@ -69,6 +69,7 @@ struct gsp2_plan {
   std::vector<ColBlock> gblocks_ld;        // low-precision gather: every column up to ld
   int32_t nslots_tc = 0;
   int32_t total_steps = 0;  // FP64 path: max_steps + tail steps (static launches of a call)
+  bool use_oz = false;      // FP64 products from BF16 digits (fp64e steps or emulated tail steps)
   std::vector<int64_t> pcolptr;
   std::vector<int32_t> prowind;
   int32_t nslots = 0, max_s = 0;
@@ -174,12 +175,15 @@ extern "C" void gsp2_default_options(gsp2_options* o) {
   o->fp64_tail_steps = -1;
   o->ckpt_every = 8;
   o->use_graph = 1;
+  o->fp64_tail_emulated = 1;
 }
 
 extern "C" const char* gsp2_last_error(gsp2_handle h) { return h ? h->err.c_str() : t_create_err.c_str(); }
 
 static void build_layout(gsp2_plan* h) {
   WsLayout& L = h->L;
+  h->use_oz = h->opt.precision == GSP2_PREC_FP64_EMU ||
+              (!fp64_like(h->opt.precision) && h->opt.fp64_tail_steps > 0 && h->opt.fp64_tail_emulated);
   h->total_steps = h->opt.max_steps + (fp64_like(h->opt.precision) ? h->opt.fp64_tail_steps : 0);
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -233,6 +237,11 @@ static void build_layout(gsp2_plan* h) {
     }
     L.d[0] = take(ab);
     L.d[1] = take(ab);
+    if (h->use_oz) {
+      for (int t = 0; t < OZ_SLICES; ++t) L.oz_slice[t] = take((size_t)h->arena_elems * 2);
+      L.oz_acc = take(ab);
+      L.oz_maps = take((size_t)OZ_SLICES * h->parts.size() * 128);
+    }
     L.ckpt.clear();
     L.seg.clear();
     L.arena0 = L.d[0];
@@ -254,7 +263,7 @@ static void build_layout(gsp2_plan* h) {
     L.xb0 = take(ab);
     L.xb1 = take(ab);
   }
-  if (prec == GSP2_PREC_FP64_EMU) {
+  if (h->use_oz) {
     for (int t = 0; t < OZ_SLICES; ++t) L.oz_slice[t] = take((size_t)h->arena_elems * 2);
     L.oz_acc = take(ab);
     L.oz_maps = take((size_t)OZ_SLICES * h->parts.size() * 128);
@@ -528,7 +537,7 @@ extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t byt
   CU(h, up(L.tiles, h->tiles.data(), h->tiles.size() * sizeof(Tile)));
   CU(h, up(L.tc_tiles, h->tc_tiles.data(), h->tc_tiles.size() * sizeof(Tile)));
   CU(h, up(L.gblocks_ld, h->gblocks_ld.data(), h->gblocks_ld.size() * sizeof(ColBlock)));
-  if (h->opt.precision == GSP2_PREC_FP64_EMU) {
+  if (h->use_oz) {
     void* enc = nullptr;
     cudaDriverEntryPointQueryResult q{};
     CU(h, cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &enc, 12000, cudaEnableDefault, &q));
@@ -662,13 +671,33 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
       a.tail = t == 0 ? 1 : 2;
       CU(h, launch_square_tc(kind, nprod, a, (int)h->tc_tiles.size(), pgrid, s));
     }
-    // FP64 tail: convert the last FP32 iterate, then purification steps in FP64
+    // FP64 tail: convert the last FP32 iterate, then purification steps in FP64 (native, or
+    // with the products rebuilt from BF16 digits)
     double* d[2] = {(double*)(w + L.d[0]), (double*)(w + L.d[1])};
     CU(h, launch_convert((const float* const*)(w + L.master_of_step), d[0], h->arena_elems, st, s));
     const int T = h->opt.fp64_tail_steps;
-    for (int t = 0; t < T; ++t)
-      CU(h, launch_square_fp64(parts, tiles, (int)h->tiles.size(), d[t & 1], d[(t + 1) & 1], slots, h->nslots, ctl, 0,
-                               (t == 0 && h->opt.lp_tail_steps == 0) ? SQ_TAIL_FIRST : SQ_TAIL_NEXT, s));
+    OzSlices tsl{};
+    OzGroupArgs toz{};
+    if (h->use_oz) {
+      for (int t = 0; t < OZ_SLICES; ++t) tsl.s[t] = (uint16_t*)(w + L.oz_slice[t]);
+      toz.parts = parts;
+      toz.tiles = (const Tile*)(w + L.tc_tiles);
+      toz.ntiles = (int)h->tc_tiles.size();
+      toz.maps = w + L.oz_maps;
+      toz.nparts = (int)h->parts.size();
+      toz.acc = (long long*)(w + L.oz_acc);
+      toz.st = st;
+      CU(h, launch_oz_slice(parts, (const ColBlock*)(w + L.gblocks_ld), (int)h->gblocks_ld.size(), d[0], tsl, s));
+    }
+    for (int t = 0; t < T; ++t) {
+      const int tmode = (t == 0 && h->opt.lp_tail_steps == 0) ? SQ_TAIL_FIRST : SQ_TAIL_NEXT;
+      if (h->use_oz)
+        CU(h, launch_oz_step(toz, h->num_sms, (const ColBlock*)(w + L.gblocks_ld), (int)h->gblocks_ld.size(),
+                             d[t & 1], d[(t + 1) & 1], tsl, slots, ctl, 0, tmode, s));
+      else
+        CU(h, launch_square_fp64(parts, tiles, (int)h->tiles.size(), d[t & 1], d[(t + 1) & 1], slots, h->nslots, ctl,
+                                 0, tmode, s));
+    }
     CU(h, launch_scatter(parts, sbl, (int)h->sblocks.size(), Sall, perm, pcol, nullptr, d[T & 1], pv, st, s));
     if (h->opt.report_idem)
       CU(h, launch_residual_fp64(parts, tiles, (int)h->tiles.size(), d[T & 1], nullptr, (double*)(w + L.rslots),

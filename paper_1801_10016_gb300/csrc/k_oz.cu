@@ -215,12 +215,20 @@ __global__ void __launch_bounds__(384, 1) oz_group_kernel(OzGroupArgs a) {
             const float f = __uint_as_float(v[j]);
             z[j] = shift >= 0 ? __float2ll_rn(f) * (1ll << shift) : __float2ll_rn(f * 0.0078125f);
           }
+          // diagonal tiles: upper triangle (c >= r) mirrored, so the sum stays exactly symmetric
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
+            if (t.ti == t.tj && cbase + j < r) continue;
             long long* y = Y + (int64_t)(cbase + j) * ld + r;
             *y = a.first ? z[j] : *y + z[j];
           }
-          if (t.ti != t.tj) {
+          if (t.ti == t.tj) {
+            for (int j = 0; j < 32; ++j) {
+              if (cbase + j <= r) continue;
+              long long* y = Y + (int64_t)r * ld + cbase + j;
+              *y = a.first ? z[j] : *y + z[j];
+            }
+          } else {
             longlong2* ym = reinterpret_cast<longlong2*>(Y + (int64_t)r * ld + cbase);
 #pragma unroll
             for (int q = 0; q < 16; ++q) {

@@ -231,12 +231,22 @@ __global__ void __launch_bounds__(256, 2) square_tc_kernel(TcStepArgs a) {
         x[j] = z;
       }
 #pragma unroll
+      // diagonal tiles: keep the upper triangle (c >= r) and mirror it, so X stays exactly
+      // symmetric whatever order the tensor cores sum the split products in
       for (int j = 0; j < 32; ++j) {
+        if (t.ti == t.tj && cbase + j < r) continue;
         const int64_t e = (int64_t)(cbase + j) * ld + r;
         Xo[e] = x[j];
         store_operands<KIND, NPROD>(ohi, olo, p.off + e, x[j]);
       }
-      if (t.ti != t.tj) {
+      if (t.ti == t.tj) {
+        for (int j = 0; j < 32; ++j) {
+          if (cbase + j <= r) continue;
+          const int64_t e = (int64_t)r * ld + cbase + j;
+          Xo[e] = x[j];
+          store_operands<KIND, NPROD>(ohi, olo, p.off + e, x[j]);
+        }
+      } else {
         const int64_t e0 = (int64_t)r * ld + cbase;
         float4* dst = reinterpret_cast<float4*>(Xo + e0);
 #pragma unroll
@@ -457,12 +467,22 @@ __global__ void __launch_bounds__(384, 1) square_tc_persistent_kernel(TcStepArgs
             x[j] = z;
           }
 #pragma unroll
+          // diagonal tiles: keep the upper triangle (c >= r) and mirror it, so X stays exactly
+          // symmetric whatever order the tensor cores sum the split products in
           for (int j = 0; j < 32; ++j) {
+            if (t.ti == t.tj && cbase + j < r) continue;
             const int64_t e = (int64_t)(cbase + j) * ld + r;
             Xo[e] = x[j];
             store_operands<KIND, NPROD>(ohi, olo, p.off + e, x[j]);
           }
-          if (t.ti != t.tj) {
+          if (t.ti == t.tj) {
+            for (int j = 0; j < 32; ++j) {
+              if (cbase + j <= r) continue;
+              const int64_t e = (int64_t)r * ld + cbase + j;
+              Xo[e] = x[j];
+              store_operands<KIND, NPROD>(ohi, olo, p.off + e, x[j]);
+            }
+          } else {
             const int64_t e0 = (int64_t)r * ld + cbase;
             float4* dst = reinterpret_cast<float4*>(Xo + e0);
 #pragma unroll

@@ -36,7 +36,8 @@ class Options(C.Structure):
     _fields_ = [("max_steps", C.c_int32), ("idem_tol", C.c_double), ("trace_tol", C.c_double),
                 ("precision", C.c_int32), ("fp64_tail_steps", C.c_int32), ("ckpt_every", C.c_int32),
                 ("use_graph", C.c_int32), ("time_steps", C.c_int32), ("lp_tail_steps", C.c_int32),
-                ("tc_schedule", C.c_int32), ("report_idem", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("tc_schedule", C.c_int32), ("report_idem", C.c_int32), ("fp64_tail_emulated", C.c_int32),
+                ("reserved", C.c_int32 * 3)]
 
 
 class Report(C.Structure):

@@ -140,3 +140,13 @@ def test_tf32x3_meets_the_gates_against_the_oracle_with_the_same_tail(g, case):
     print(f"{case} tf32x3 + 2 FP64 tail vs oracle + 2 tail: max|dP|={err:.3e} idem_fro={idem:.3e}")
     assert err <= 1e-6, err
     assert 0.0 <= idem <= 1e-8, idem
+
+
+def test_emulated_and_native_fp64_tail_agree(g):
+    """The FP64 tail steps of a low-precision run, with the products on the FP64 units or
+    rebuilt from BF16 digits, give the same P to FP64 accuracy."""
+    s = make_workload("tb512")
+    _, pe, he = run(g, s, "tf32x3", fp64_tail_steps=2, fp64_tail_emulated=1)
+    _, pn, hn = run(g, s, "tf32x3", fp64_tail_steps=2, fp64_tail_emulated=0)
+    assert he["alphas"] == hn["alphas"] and he["report"]["fp64_steps"] == 2
+    assert float(np.max(np.abs(pe - pn))) <= 1e-12
