@@ -90,7 +90,7 @@ struct TcStepArgs {
 };
 
 // FP64 products rebuilt from BF16 digits (k_oz.cu)
-constexpr int OZ_SLICES = 8;  // base-2^7 digits per entry
+constexpr int OZ_SLICES = 7;  // base-2^7 digits per entry
 
 struct OzSlices {
   uint16_t* s[OZ_SLICES];  // BF16 digit arenas (same element indexing as the arenas)

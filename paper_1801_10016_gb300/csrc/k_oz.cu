@@ -2,11 +2,12 @@
 //
 // GB300 runs FP64 at 1/1800 of its BF16 rate, so the FP64 product X X is rebuilt from
 // exact BF16 products, in the spirit of the Ozaki splitting (Ozaki, Ogita, Oishi and
-// Rump, 2012):
+// Rump, 2012).  With T = OZ_SLICES digits:
 //
 //   every entry of X (|x| <= 1: the spectrum of X stays in [0, 1]) is written in base 2^7
 //   with rounded signed digits, x = sum_{t<T} S_t 2^{-7(t+1)} + r, |S_0| <= 2^7 + 1,
-//   |S_t| <= 2^6 (t >= 1), |r| <= 2^{-7T-1}; every S_t is an integer exact in BF16;
+//   |S_t| <= 2^6 (t >= 1), |r| <= 2^{-7T-1} (+ 2^-57 from the fixed point); every S_t is an
+//   integer exact in BF16;
 //
 //   X X = sum_{d<T} 2^{-7(d+2)} G_d + (terms below 2^{-7(T+2)}), G_d = sum_{a+b=d} S_a S_b.
 //
@@ -16,9 +17,9 @@
 // scaled by 2^{-49} or less.  The groups are added as integers into a 64-bit fixed-point
 // accumulator (resolution 2^-56), and a final elementwise pass forms X_new = Y or 2X - Y on
 // that grid (kept as FP64 master copy), the core traces in FP64, and the digits of X_new for
-// the next step by integer arithmetic.  With T = 8 (36 BF16
-// products per tile) the error of Y is about 1e-14, far below the 1e-10 parity of the FP64
-// path.
+// the next step by integer arithmetic.  With T = 7 (28 BF16
+// products per tile) the digits hold x to 2^-49 and the dropped products are of order
+// 2^-63 K 2^12; the error of Y is about 1e-13, far below the 1e-10 parity of the FP64 path.
 #include <cuda.h>
 
 #include "gsp2_internal.cuh"
@@ -27,18 +28,21 @@
 
 namespace gsp2 {
 
-// Digits of a value held in 64-bit fixed point v = x 2^56 (|x| <= 1 + small): balanced
-// base-2^7 digits from the least significant up, S_t in [-64, 63] for t >= 1 and the rest in
-// S_0, so that v = sum_t S_t 2^{7(7-t)} exactly; written as BF16 to the digit arenas.
+// Digits of a value held in 64-bit fixed point v = x 2^56 (|x| <= 1 + small): rounded to
+// w = x 2^{7T}, then balanced base-2^7 digits from the least significant up, S_t in
+// [-64, 63] for t >= 1 and the rest in S_0, so that w = sum_t S_t 2^{7(T-1-t)} exactly;
+// written as BF16 to the digit arenas (digit t weighs 2^{-7(t+1)}).
 __device__ __forceinline__ void store_digits(uint16_t* const* slices, int64_t e, long long v) {
+  constexpr int drop = 56 - 7 * OZ_SLICES;
+  long long w = drop > 0 ? ((v + (1ll << (drop - 1))) >> drop) : v;
 #pragma unroll
   for (int t = OZ_SLICES - 1; t >= 0; --t) {
     long long dgt;
     if (t > 0) {
-      dgt = ((v + 64) & 127) - 64;
-      v = (v - dgt) >> 7;
+      dgt = ((w + 64) & 127) - 64;
+      w = (w - dgt) >> 7;
     } else {
-      dgt = v;
+      dgt = w;
     }
     uint16_t h;
     asm("cvt.rn.bf16.f32 %0, %1;\n" : "=h"(h) : "f"((float)dgt));
@@ -46,8 +50,46 @@ __device__ __forceinline__ void store_digits(uint16_t* const* slices, int64_t e,
   }
 }
 
-__device__ __forceinline__ long long to_fixed(double x) { return __double2ll_rn(x * 0x1p56); }
-__device__ __forceinline__ double from_fixed(long long v) { return (double)v * 0x1p-56; }
+// Conversions between FP64 and the 2^-56 fixed point done with integer instructions (the
+// FP64 pipe of GB300 is 64x slower than its integer pipe), rounding to nearest even.
+__device__ __forceinline__ long long to_fixed(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  if (ex == 0) return 0;                                    // zero and subnormals (< 2^-1022)
+  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int sh = ex - 1023 - 52 + 56;                       // value * 2^56 = m * 2^sh
+  unsigned long long a;
+  if (sh >= 0) {
+    a = m << sh;                                            // |x| < 2^7 keeps this below 2^63
+  } else if (sh > -64) {
+    const int k = -sh;
+    const unsigned long long q = m >> k, rem = m & ((1ull << k) - 1), half = 1ull << (k - 1);
+    a = q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull);
+  } else {
+    a = 0;
+  }
+  return (b >> 63) ? -(long long)a : (long long)a;
+}
+
+__device__ __forceinline__ double from_fixed(long long v) {
+  if (v == 0) return 0.0;
+  const unsigned long long sgn = v < 0 ? (1ull << 63) : 0ull;
+  const unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+  const int lz = __clzll(a);
+  const unsigned long long m = a << lz;                     // top bit at 63
+  unsigned long long mant = m >> 11;                        // 53 bits with the leading one
+  const unsigned long long rem = m & 0x7FFull;
+  int e = 63 - lz - 56;                                     // value = 1.f x 2^e
+  if (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) {
+    mant += 1;
+    if (mant >> 53) {
+      mant >>= 1;
+      e += 1;
+    }
+  }
+  const unsigned long long bits = sgn | ((unsigned long long)(e + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFull);
+  return __longlong_as_double((long long)bits);
+}
 
 // Digits of an FP64 arena (X0 after the gather): one warp per column up to ld.
 __global__ void __launch_bounds__(256) oz_slice_kernel(const PartDesc* __restrict__ parts,
