@@ -157,7 +157,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * per_build, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "n": int(s.n), "nocc": int(s.nocc), "parts": int(s.nparts),
-                       "part_size_min": int(sizes.min()), "part_size_max": int(sizes.max()), "precision": "fp64",
+                       "part_size_min": int(sizes.min()), "part_size_max": int(sizes.max()),
+                       "result_precision": "fp64", "arith": "fp64 (numpy/BLAS dgemm)",
                        "sp2_steps": len(ref.alphas), "l2": "host CPU caches (no GPU)", "parallelism": "single"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"oracle replay of its own {len(ref.alphas)}-step sequence on every "
@@ -165,6 +166,55 @@ def run_reference(args):
                                        f"scaled to a full P-build; full oracle build took {t_full:.1f} s"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+OZ_DIGITS = 7  # base-2^7 digits of the fp64e step
+OZ_PRODUCTS = OZ_DIGITS * (OZ_DIGITS + 1) // 2  # BF16 digit products per tile (28)
+
+
+def tc_exec_flops(sizes, kstage, products):
+    """Executed tensor flops of one step: every upper 128x128 tile, K rounded to the stage."""
+    import numpy as np
+    nt = np.ceil(sizes / 128.0)
+    kk = np.ceil(sizes / kstage) * kstage
+    return float(np.sum(nt * (nt + 1) / 2 * 2 * 128 * 128 * kk)) * products
+
+
+def fp64_roofline(precision, sizes, avg_launch_ms, peaks, src, workload):
+    """Roofline of one FP64-result step: native (FP64 pipe, algorithmic flops s^2 (s+1)) or
+    rebuilt from BF16 digits (tensor pipe, executed BF16 flops of all digit products)."""
+    import numpy as np
+    if precision == "fp64e":
+        flops = tc_exec_flops(sizes, 64, OZ_PRODUCTS)
+        achieved = flops / (avg_launch_ms / 1e3) / 1e12
+        peak = peaks["bf16_tflops"]
+        return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": TRAFFIC.get((workload, precision)),
+                "kernel": "oz_group_kernel x7 + oz_finalize_kernel (one FP64-accurate step)",
+                "peak_source": f"{src}: bf16 burst (of measured)", "avg_launch_ms": avg_launch_ms,
+                "flops_per_launch": flops,
+                "flops": f"executed BF16 tensor flops of the {OZ_PRODUCTS} digit products per upper 128-tile"}
+    flops = float(np.sum(sizes * sizes * (sizes + 1.0)))
+    achieved = flops / (avg_launch_ms / 1e3) / 1e12
+    peak = peaks["bf16_tflops"] * NOMINAL["fp64"] / NOMINAL["bf16"]
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": TRAFFIC.get((workload, precision)), "kernel": "square_simt_kernel<double>",
+            "peak_source": f"{src}: bf16 burst {peaks['bf16_tflops']} TF/s x nominal fp64/bf16 "
+                           f"{NOMINAL['fp64']}/{NOMINAL['bf16']} (of measured)",
+            "avg_launch_ms": avg_launch_ms, "flops_per_launch": flops,
+            "flops": "algorithmic s^2 (s+1) per part (upper triangle of X^2)"}
+
+
+def kernels_per_build(precision, info, lp_tail=0, report_idem=0):
+    """Kernel launches of one density call (all launched, including the step launches that
+    return at once after the stopping test)."""
+    n = 4 + report_idem  # reset, bounds, gather, scatter (+ idempotency report)
+    if precision == "fp64":
+        return n + info.step_launches
+    if precision == "fp64e":
+        return n + 1 + info.step_launches * (OZ_DIGITS + 1)  # digit groups + final pass per step
+    tail = info.fp64_tail_steps
+    return n + info.step_launches + lp_tail + 1 + (1 + tail * 8 if tail > 0 else 0)
 
 
 def aggregate(local_seconds, units_per_rank, world, device):
@@ -270,24 +320,19 @@ def run_ours(args):
     alg_flops = float(np.sum(sizes * sizes * (sizes + 1.0)))  # upper triangle incl. diagonal: s(s+1)/2 * 2s
     dgemm_equiv = 2.0 * float(np.sum(sizes ** 3))
     avg_launch_ms, work_ms = kernel_avg_ms(step_ms, steps_applied)
-    fp64_peak = peaks["bf16_tflops"] * NOMINAL["fp64"] / NOMINAL["bf16"]
-    achieved = alg_flops / (avg_launch_ms / 1e3) / 1e12
-    roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-            "frac": achieved / fp64_peak, "traffic": TRAFFIC.get((args.workload, args.precision)),
-            "kernel": "square_simt_kernel<double>",
-            "peak_source": f"{src}: bf16 burst {peaks['bf16_tflops']} TF/s x nominal fp64/bf16 "
-                           f"{NOMINAL['fp64']}/{NOMINAL['bf16']} (of measured)",
-            "avg_launch_ms": avg_launch_ms, "share_of_step": work_ms / (sum(dev_ms) + 1e-30),
-            "flops_per_launch": alg_flops}
-    launches_per_build = 4 + plan.info.step_launches
+    roof = fp64_roofline(args.precision, sizes, avg_launch_ms, peaks, src, args.workload)
+    roof["share_of_step"] = work_ms / (sum(dev_ms) + 1e-30)
+    launches_per_build = kernels_per_build(args.precision, plan.info)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": warm, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else args.precision,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64", "fp64e": "f64 (bf16 digit products, int64 sums)"}.get(args.precision, args.precision),
         "data": "synthetic",
         "config": {"workload": args.workload, "n": int(s.n), "nocc": int(s.nocc), "parts": int(s.nparts),
                    "part_size_min": int(sizes.min()), "part_size_max": int(sizes.max()),
-                   "precision": args.precision, "sp2_steps": int(steps_applied),
+                   "result_precision": "fp64" if args.precision in ("fp64", "fp64e") else args.precision,
+                   "arith": args.precision, "sp2_steps": int(steps_applied),
                    "l2": "flushed (256 MB write) between timed P-builds; the arenas also exceed L2",
                    "parallelism": "replicas" if world > 1 else "single"},
         "tflops_dgemm_equiv": dgemm_equiv * steps_applied / (ms_per_step / 1e3) / 1e12,
@@ -302,6 +347,26 @@ def run_ours(args):
     del plan
     torch.cuda.empty_cache()
 
+    # ---- the native FP64 path (FP64 pipe) on the same workload, for comparison
+    if args.precision != "fp64" and not args.no_native:
+        npn = GSP2(s.n, s.rowptr, s.colind, s.nocc, s.part, s.nparts, s.g_rowptr, s.g_colind, device=dev,
+                   precision="fp64", max_steps=args.max_steps, time_steps=1, ckpt_every=0)
+        pn = torch.empty(npn.nnz_p, dtype=torch.float64, device=dev)
+        npn.density(h_dev, out=pn)
+        with ClockSampler(local) as nclk:
+            nms, nstep = time_builds(npn, h_dev, pn, 2, flush, stream)
+        nst, nrep = npn.status()
+        npn.close()
+        del npn
+        torch.cuda.empty_cache()
+        n_ms, _ = kernel_avg_ms(nstep, nrep["steps"])
+        nroof = fp64_roofline("fp64", sizes, n_ms, peaks, src, args.workload)
+        line["fp64_native"] = {"value": 2.0 / (sum(nms) / 1e3), "unit": UNIT, "ms_per_build": sum(nms) / 2,
+                               "sp2_steps": int(nrep["steps"]), "status": int(nst),
+                               "max_abs_dP_vs_value": float((pn - p_ref).abs().max().item()),
+                               "roofline": nroof, "clocks": nclk.summary()}
+        line["speedup_vs_fp64_native"] = value / line["fp64_native"]["value"]
+
     # ---- low-precision paths on the same workload, against the FP64 result
     if not args.no_mixed:
         mixed = {}
@@ -309,7 +374,7 @@ def run_ours(args):
         # FP64 with the same two alternating tail steps (untimed): the like-for-like reference
         # for the accuracy gates of the runs that end with two tail steps
         rp = GSP2(s.n, s.rowptr, s.colind, s.nocc, s.part, s.nparts, s.g_rowptr, s.g_colind, device=dev,
-                  max_steps=args.max_steps, fp64_tail_steps=2, ckpt_every=0, report_idem=1)
+                  precision="fp64e", max_steps=args.max_steps, fp64_tail_steps=2, ckpt_every=0, report_idem=1)
         p_ref_tail = rp.density(h_dev).clone()
         _, rrep = rp.status()
         line["fp64_tail2_idem_fro"] = rrep["idem_fro"]
@@ -377,10 +442,11 @@ def run_ours(args):
                 entry["roofline"]["frac"] = ach / entry["roofline"]["peak"]
             mixed[spec] = entry
         line["mixed"] = mixed
-        line["mixed_note"] = ("max_abs_dP_vs_fp64: against the FP64 GPU path (the paper's method, no tail), which "
-                              "the parity tests hold to the FP64 oracle within 1e-10; max_abs_dP_vs_fp64_tail2: "
-                              "against FP64 with the same two alternating tail steps; idem_fro: "
-                              "sqrt(sum_k ||(X_k^2 - X_k)[:, cores]||^2 / N) from the library's FP64 report pass")
+        line["mixed_note"] = ("max_abs_dP_vs_fp64: against the FP64-result path of `value` (the paper's method, no "
+                              "tail), which the parity tests hold to the FP64 oracle within 1e-10; "
+                              "max_abs_dP_vs_fp64_tail2: against the same with two alternating tail steps; "
+                              "idem_fro: sqrt(sum_k ||(X_k^2 - X_k)[:, cores]||^2 / N) from the library's FP64 "
+                              "report pass")
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t_cpu, _ = oracle_build_seconds(s, args.max_steps)
@@ -401,7 +467,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="tb30k")
-    ap.add_argument("--precision", default="fp64")
+    ap.add_argument("--precision", default="fp64e")
+    ap.add_argument("--no-native", dest="no_native", action="store_true")
     ap.add_argument("--max-steps", dest="max_steps", type=int, default=45)
     ap.add_argument("--ref-stride", dest="ref_stride", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", dest="no_cpu_baseline", action="store_true")
