@@ -30,9 +30,8 @@ struct WsLayout {
   size_t master_of_step;
   size_t d[2];         // FP64 arenas of the tail steps
   // FP64 products from BF16 digits
-  size_t oz_slice[OZ_SLICES];  // BF16 digit arenas of the current iterate
-  size_t oz_acc;               // 64-bit fixed-point accumulator of X X
-  size_t oz_maps;              // CUtensorMap[OZ_SLICES][nparts]
+  size_t oz_slice[2][OZ_SLICES];  // BF16 digit arenas, two buffers (read / written by a step)
+  size_t oz_maps;                 // CUtensorMap[2][OZ_SLICES][nparts]
   size_t slots, rslots, state, alpha, traces, idem, step_arena;
   size_t arena0, arena1;       // ping-pong iterates
   std::vector<size_t> ckpt;    // X_0, X_k, X_2k, ... (adjoint checkpoints)
@@ -238,9 +237,9 @@ static void build_layout(gsp2_plan* h) {
     L.d[0] = take(ab);
     L.d[1] = take(ab);
     if (h->use_oz) {
-      for (int t = 0; t < OZ_SLICES; ++t) L.oz_slice[t] = take((size_t)h->arena_elems * 2);
-      L.oz_acc = take(ab);
-      L.oz_maps = take((size_t)OZ_SLICES * h->parts.size() * 128);
+      for (int b = 0; b < 2; ++b)
+        for (int t = 0; t < OZ_SLICES; ++t) L.oz_slice[b][t] = take((size_t)h->arena_elems * 2);
+      L.oz_maps = take((size_t)2 * OZ_SLICES * h->parts.size() * 128);
     }
     L.ckpt.clear();
     L.seg.clear();
@@ -264,9 +263,9 @@ static void build_layout(gsp2_plan* h) {
     L.xb1 = take(ab);
   }
   if (h->use_oz) {
-    for (int t = 0; t < OZ_SLICES; ++t) L.oz_slice[t] = take((size_t)h->arena_elems * 2);
-    L.oz_acc = take(ab);
-    L.oz_maps = take((size_t)OZ_SLICES * h->parts.size() * 128);
+    for (int b = 0; b < 2; ++b)
+      for (int t = 0; t < OZ_SLICES; ++t) L.oz_slice[b][t] = take((size_t)h->arena_elems * 2);
+    L.oz_maps = take((size_t)2 * OZ_SLICES * h->parts.size() * 128);
   }
   L.total = o;
   // arena of each iterate X_i: checkpoints where i is a multiple of k, else ping-pong
@@ -544,12 +543,13 @@ extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t byt
     if (!enc || q != cudaDriverEntryPointSuccess)
       return fail(h, GSP2_E_CUDA, "cuTensorMapEncodeTiled not available from the driver");
     const size_t np = h->parts.size();
-    std::vector<unsigned char> maps((size_t)OZ_SLICES * np * 128, 0);
-    for (int t = 0; t < OZ_SLICES; ++t) {
-      const int r = encode_part_maps(enc, maps.data() + (size_t)t * np * 128, h->parts.data(), (int)np,
-                                     h->ws + L.oz_slice[t], 0);
-      if (r != 0) return fail(h, GSP2_E_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string(r));
-    }
+    std::vector<unsigned char> maps((size_t)2 * OZ_SLICES * np * 128, 0);
+    for (int b = 0; b < 2; ++b)
+      for (int t = 0; t < OZ_SLICES; ++t) {
+        const int r = encode_part_maps(enc, maps.data() + ((size_t)b * OZ_SLICES + t) * np * 128, h->parts.data(),
+                                       (int)np, h->ws + L.oz_slice[b][t], 0);
+        if (r != 0) return fail(h, GSP2_E_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string(r));
+      }
     CU(h, up(L.oz_maps, maps.data(), maps.size()));
   }
   if (!fp64_like(h->opt.precision)) {
@@ -586,6 +586,25 @@ extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t byt
   // the uploads read pageable host vectors; finish them before the call returns
   CU(h, cudaStreamSynchronize(s));
   return GSP2_OK;
+}
+
+// Arguments of the emulated FP64 step common to all its launches of a call.
+static OzStepArgs oz_args(gsp2_plan* h, const StepCtl& ctl) {
+  const WsLayout& L = h->L;
+  char* w = h->ws;
+  OzStepArgs a{};
+  if (!h->use_oz) return a;
+  a.parts = (const PartDesc*)(w + L.parts);
+  a.tiles = (const Tile*)(w + L.tc_tiles);
+  a.ntiles = (int)h->tc_tiles.size();
+  a.maps = w + L.oz_maps;
+  a.nparts = (int)h->parts.size();
+  for (int b = 0; b < 2; ++b)
+    for (int t = 0; t < OZ_SLICES; ++t) a.digits[b].s[t] = (uint16_t*)(w + L.oz_slice[b][t]);
+  a.slots = (double2*)(w + L.slots);
+  a.nslots = h->nslots_tc;
+  a.ctl = ctl;
+  return a;
 }
 
 // Queue the whole forward pass on `s`.
@@ -676,25 +695,19 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
     double* d[2] = {(double*)(w + L.d[0]), (double*)(w + L.d[1])};
     CU(h, launch_convert((const float* const*)(w + L.master_of_step), d[0], h->arena_elems, st, s));
     const int T = h->opt.fp64_tail_steps;
-    OzSlices tsl{};
-    OzGroupArgs toz{};
-    if (h->use_oz) {
-      for (int t = 0; t < OZ_SLICES; ++t) tsl.s[t] = (uint16_t*)(w + L.oz_slice[t]);
-      toz.parts = parts;
-      toz.tiles = (const Tile*)(w + L.tc_tiles);
-      toz.ntiles = (int)h->tc_tiles.size();
-      toz.maps = w + L.oz_maps;
-      toz.nparts = (int)h->parts.size();
-      toz.acc = (long long*)(w + L.oz_acc);
-      toz.st = st;
-      CU(h, launch_oz_slice(parts, (const ColBlock*)(w + L.gblocks_ld), (int)h->gblocks_ld.size(), d[0], tsl, s));
-    }
+    OzStepArgs toz = oz_args(h, ctl);
+    if (h->use_oz)
+      CU(h, launch_oz_slice(parts, (const ColBlock*)(w + L.gblocks_ld), (int)h->gblocks_ld.size(), d[0], toz.digits,
+                            st, s));
     for (int t = 0; t < T; ++t) {
       const int tmode = (t == 0 && h->opt.lp_tail_steps == 0) ? SQ_TAIL_FIRST : SQ_TAIL_NEXT;
-      if (h->use_oz)
-        CU(h, launch_oz_step(toz, h->num_sms, (const ColBlock*)(w + L.gblocks_ld), (int)h->gblocks_ld.size(),
-                             d[t & 1], d[(t + 1) & 1], tsl, slots, ctl, 0, tmode, s));
-      else
+      if (h->use_oz) {
+        OzStepArgs a = toz;
+        a.xin = d[t & 1];
+        a.xout = d[(t + 1) & 1];
+        a.mode = tmode;
+        CU(h, launch_oz_step(a, h->num_sms, s));
+      } else
         CU(h, launch_square_fp64(parts, tiles, (int)h->tiles.size(), d[t & 1], d[(t + 1) & 1], slots, h->nslots, ctl,
                                  0, tmode, s));
     }
@@ -708,27 +721,24 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
   }
   CU(h, launch_gather(parts, gbl, (int)h->gblocks.size(), Sall, rp, ci, hv, A(0), (double*)slots, ctl, s));
   const bool emu = prec == GSP2_PREC_FP64_EMU;
-  OzSlices sl{};
-  OzGroupArgs oz{};
+  OzStepArgs oz{};
   if (emu) {
-    for (int t = 0; t < OZ_SLICES; ++t) sl.s[t] = (uint16_t*)(w + L.oz_slice[t]);
-    oz.parts = parts;
-    oz.tiles = (const Tile*)(w + L.tc_tiles);
-    oz.ntiles = (int)h->tc_tiles.size();
-    oz.maps = w + L.oz_maps;
-    oz.nparts = (int)h->parts.size();
-    oz.acc = (long long*)(w + L.oz_acc);
-    oz.st = st;
-    CU(h, launch_oz_slice(parts, (const ColBlock*)(w + L.gblocks_ld), (int)h->gblocks_ld.size(), A(0), sl, s));
+    oz = oz_args(h, ctl);
+    CU(h, launch_oz_slice(parts, (const ColBlock*)(w + L.gblocks_ld), (int)h->gblocks_ld.size(), A(0), oz.digits, st,
+                          s));
   }
   for (int i = 1; i <= ctl.last_step; ++i) {
     const double* xin = A(i - 1);
     double* xout = A(i);
     if (!h->ev.empty()) CU(h, cudaEventRecordWithFlags(h->ev[2 * (i - 1)], s, cudaEventRecordExternal));
-    if (emu)
-      CU(h, launch_oz_step(oz, h->num_sms, (const ColBlock*)(w + L.gblocks_ld), (int)h->gblocks_ld.size(), xin, xout,
-                           sl, slots, ctl, i, SQ_FORWARD, s));
-    else
+    if (emu) {
+      OzStepArgs a = oz;
+      a.xin = xin;
+      a.xout = xout;
+      a.step = i;
+      a.mode = SQ_FORWARD;
+      CU(h, launch_oz_step(a, h->num_sms, s));
+    } else
       CU(h, launch_square_fp64(parts, tiles, (int)h->tiles.size(), xin, xout, slots, h->nslots, ctl, i, SQ_FORWARD,
                                s));
     if (!h->ev.empty()) CU(h, cudaEventRecordWithFlags(h->ev[2 * (i - 1) + 1], s, cudaEventRecordExternal));

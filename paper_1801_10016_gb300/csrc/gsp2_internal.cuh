@@ -96,17 +96,22 @@ struct OzSlices {
   uint16_t* s[OZ_SLICES];  // BF16 digit arenas (same element indexing as the arenas)
 };
 
-struct OzGroupArgs {
+// One emulated step: digits of X_{step-1} are read from buffer (step-1)&1 and the digits
+// of X_step written to buffer step&1.
+struct OzStepArgs {
   const PartDesc* parts;
-  const Tile* tiles;  // 128x128 upper tiles
+  const Tile* tiles;   // 128x128 upper tiles
   int ntiles;
-  const void* maps;   // CUtensorMap[OZ_SLICES][nparts] over the digit arenas
+  const void* maps;    // CUtensorMap[2 buffers][OZ_SLICES][nparts] over the digit arenas
   int nparts;
-  long long* acc;     // 64-bit fixed-point accumulator, resolution 2^-56
-  DevState* st;
-  int group;          // d: this launch adds 2^{-7(d+2)} sum_{a+b=d} S_a S_b
-  int first;          // 1: store instead of add
-  int mode;           // SQ_FORWARD or a tail mode (skip rules)
+  OzSlices digits[2];
+  const double* xin;   // FP64 master of X_{step-1}
+  double* xout;        // FP64 master of X_step
+  double2* slots;      // diagonal-tile trace slots
+  int nslots;
+  StepCtl ctl;
+  int step;            // ignored in tail modes (step = steps applied + 1)
+  int mode;            // SQ_FORWARD, SQ_TAIL_FIRST or SQ_TAIL_NEXT
 };
 
 // ------------------------------------------------------------------ device helpers

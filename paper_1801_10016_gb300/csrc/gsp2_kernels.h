@@ -35,10 +35,8 @@ cudaError_t launch_convert(const float* const* master_of_step, double* out, int6
                            cudaStream_t s);
 // FP64 products from BF16 digits (k_oz.cu)
 cudaError_t launch_oz_slice(const PartDesc* parts, const ColBlock* blocks, int nblocks, const double* X,
-                            const OzSlices& sl, cudaStream_t s);
-cudaError_t launch_oz_step(const OzGroupArgs& g0, int grid, const ColBlock* blocks, int nblocks, const double* xin,
-                           double* xout, const OzSlices& sl, double2* slots, const StepCtl& ctl, int step, int mode,
-                           cudaStream_t s);
+                            const OzSlices* digits, const DevState* st, cudaStream_t s);
+cudaError_t launch_oz_step(const OzStepArgs& a, int grid, cudaStream_t s);
 int encode_part_maps(void* enc_fn, void* out_maps, const PartDesc* parts, int nparts, void* arena, int kind);
 
 // adjoint (k_adjoint.cu)
