@@ -76,6 +76,18 @@ __device__ __forceinline__ long long to_fixed(double x) {
   return (b >> 63) ? -(long long)a : (long long)a;
 }
 
+// An integer-valued FP32 number (|f| < 2^31) times 2^shift as a 64-bit integer, with integer
+// instructions only (a 64-bit conversion would run on the FP64 pipe).
+__device__ __forceinline__ long long fint_shl(float f, int shift) {
+  const uint32_t b = __float_as_uint(f);
+  const int ex = (int)((b >> 23) & 0xFF) - 127;  // f = 1.m 2^ex
+  if (ex < 0) return 0;                          // f == 0 (|f| >= 1 otherwise)
+  const long long m = (long long)((b & 0x7FFFFFu) | 0x800000u);
+  const int sh = ex - 23 + shift;
+  const long long a = sh >= 0 ? (m << sh) : (m >> (-sh));  // exact: f is an integer, shift >= 0
+  return (b >> 31) ? -a : a;
+}
+
 __device__ __forceinline__ double from_fixed(long long v) {
   if (v == 0) return 0.0;
   const unsigned long long sgn = v < 0 ? (1ull << 63) : 0ull;
@@ -298,7 +310,7 @@ __global__ void __launch_bounds__(384, 1) oz_step_kernel(OzStepArgs a) {
           }
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
-            long long z = __float2ll_rn(__uint_as_float(v[j])) * (1ll << shift);
+            long long z = fint_shl(__uint_as_float(v[j]), shift);
             if (d > 0) z += (long long)(((unsigned long long)hi[j] << 32) | lo[j]);
             lo[j] = (uint32_t)((unsigned long long)z & 0xFFFFFFFFull);
             hi[j] = (uint32_t)((unsigned long long)z >> 32);
