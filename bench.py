@@ -190,7 +190,7 @@ def fp64_roofline(precision, sizes, avg_launch_ms, peaks, src, workload):
         peak = peaks["bf16_tflops"]
         return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": TRAFFIC.get((workload, precision)),
-                "kernel": "oz_group_kernel x7 + oz_finalize_kernel (one FP64-accurate step)",
+                "kernel": "oz_step_kernel (one FP64-accurate step: 28 BF16 digit products per upper tile, fused)",
                 "peak_source": f"{src}: bf16 burst (of measured)", "avg_launch_ms": avg_launch_ms,
                 "flops_per_launch": flops,
                 "flops": f"executed BF16 tensor flops of the {OZ_PRODUCTS} digit products per upper 128-tile"}
@@ -205,16 +205,17 @@ def fp64_roofline(precision, sizes, avg_launch_ms, peaks, src, workload):
             "flops": "algorithmic s^2 (s+1) per part (upper triangle of X^2)"}
 
 
-def kernels_per_build(precision, info, lp_tail=0, report_idem=0):
+def kernels_per_build(precision, info, lp_tail=0, report_idem=0, emulated_tail=True):
     """Kernel launches of one density call (all launched, including the step launches that
     return at once after the stopping test)."""
     n = 4 + report_idem  # reset, bounds, gather, scatter (+ idempotency report)
     if precision == "fp64":
         return n + info.step_launches
     if precision == "fp64e":
-        return n + 1 + info.step_launches * (OZ_DIGITS + 1)  # digit groups + final pass per step
+        return n + 1 + info.step_launches  # digits of X0, then one fused launch per step
     tail = info.fp64_tail_steps
-    return n + info.step_launches + lp_tail + 1 + (1 + tail * 8 if tail > 0 else 0)
+    # low-precision steps, low-precision tail, conversion, digits of the converted iterate
+    return n + info.step_launches + lp_tail + 1 + (1 if (tail > 0 and emulated_tail) else 0) + tail
 
 
 def aggregate(local_seconds, units_per_rank, world, device):
