@@ -32,6 +32,7 @@ struct WsLayout {
   // FP64 products from BF16 digits
   size_t oz_slice[2][OZ_SLICES];  // BF16 digit arenas, two buffers (read / written by a step)
   size_t oz_maps;                 // CUtensorMap[2][OZ_SLICES][nparts]
+  size_t oz_acc;                  // int64[OZ_MAX_GRID][128 * 128] partial sums of the emulated step
   size_t slots, rslots, state, alpha, traces, idem, step_arena;
   size_t arena0, arena1;       // ping-pong iterates
   std::vector<size_t> ckpt;    // X_0, X_k, X_2k, ... (adjoint checkpoints)
@@ -240,6 +241,7 @@ static void build_layout(gsp2_plan* h) {
       for (int b = 0; b < 2; ++b)
         for (int t = 0; t < OZ_SLICES; ++t) L.oz_slice[b][t] = take((size_t)h->arena_elems * 2);
       L.oz_maps = take((size_t)2 * OZ_SLICES * h->parts.size() * 128);
+      L.oz_acc = take((size_t)OZ_MAX_GRID * 128 * 128 * 8);
     }
     L.ckpt.clear();
     L.seg.clear();
@@ -266,6 +268,7 @@ static void build_layout(gsp2_plan* h) {
     for (int b = 0; b < 2; ++b)
       for (int t = 0; t < OZ_SLICES; ++t) L.oz_slice[b][t] = take((size_t)h->arena_elems * 2);
     L.oz_maps = take((size_t)2 * OZ_SLICES * h->parts.size() * 128);
+    L.oz_acc = take((size_t)OZ_MAX_GRID * 128 * 128 * 8);
   }
   L.total = o;
   // arena of each iterate X_i: checkpoints where i is a multiple of k, else ping-pong
@@ -547,7 +550,7 @@ extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t byt
     for (int b = 0; b < 2; ++b)
       for (int t = 0; t < OZ_SLICES; ++t) {
         const int r = encode_part_maps(enc, maps.data() + ((size_t)b * OZ_SLICES + t) * np * 128, h->parts.data(),
-                                       (int)np, h->ws + L.oz_slice[b][t], 0);
+                                       (int)np, h->ws + L.oz_slice[b][t], 0, 2 * OZ_BK);
         if (r != 0) return fail(h, GSP2_E_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string(r));
       }
     CU(h, up(L.oz_maps, maps.data(), maps.size()));
@@ -603,6 +606,7 @@ static OzStepArgs oz_args(gsp2_plan* h, const StepCtl& ctl) {
     for (int t = 0; t < OZ_SLICES; ++t) a.digits[b].s[t] = (uint16_t*)(w + L.oz_slice[b][t]);
   a.slots = (double2*)(w + L.slots);
   a.nslots = h->nslots_tc;
+  a.acc = (long long*)(w + L.oz_acc);
   a.ctl = ctl;
   return a;
 }

@@ -91,6 +91,9 @@ struct TcStepArgs {
 
 // FP64 products rebuilt from BF16 digits (k_oz.cu)
 constexpr int OZ_SLICES = 7;  // base-2^7 digits per entry
+constexpr int OZ_SPLIT = 3;   // digit groups d < OZ_SPLIT form the second pass of a tile
+constexpr int OZ_MAX_GRID = 256;  // CTAs of the emulated step (one 128x128 int64 scratch each)
+constexpr int OZ_BK = 32;         // K per pipeline stage of the emulated step (64-byte rows)
 
 struct OzSlices {
   uint16_t* s[OZ_SLICES];  // BF16 digit arenas (same element indexing as the arenas)
@@ -109,6 +112,7 @@ struct OzStepArgs {
   double* xout;        // FP64 master of X_step
   double2* slots;      // diagonal-tile trace slots
   int nslots;
+  long long* acc;      // OZ_MAX_GRID x 128 x 128 fixed-point partial sums, one tile per CTA
   StepCtl ctl;
   int step;            // ignored in tail modes (step = steps applied + 1)
   int mode;            // SQ_FORWARD, SQ_TAIL_FIRST or SQ_TAIL_NEXT

@@ -37,7 +37,8 @@ cudaError_t launch_convert(const float* const* master_of_step, double* out, int6
 cudaError_t launch_oz_slice(const PartDesc* parts, const ColBlock* blocks, int nblocks, const double* X,
                             const OzSlices* digits, const DevState* st, cudaStream_t s);
 cudaError_t launch_oz_step(const OzStepArgs& a, int grid, cudaStream_t s);
-int encode_part_maps(void* enc_fn, void* out_maps, const PartDesc* parts, int nparts, void* arena, int kind);
+int encode_part_maps(void* enc_fn, void* out_maps, const PartDesc* parts, int nparts, void* arena, int kind,
+                     int box_bytes = 128);
 
 // adjoint (k_adjoint.cu)
 cudaError_t launch_adj_seed(const PartDesc* parts, const ColBlock* blocks, int nblocks, const int32_t* Sall,

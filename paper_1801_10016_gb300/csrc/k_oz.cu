@@ -28,31 +28,32 @@
 
 namespace gsp2 {
 
-// Digits of a value held in 64-bit fixed point v = x 2^56 (|x| <= 1 + small): rounded to
-// w = x 2^{7T}, then balanced base-2^7 digits from the least significant up, S_t in
-// [-64, 63] for t >= 1 and the rest in S_0, so that w = sum_t S_t 2^{7(T-1-t)} exactly;
-// written as BF16 to the digit arenas (digit t weighs 2^{-7(t+1)}).
-__device__ __forceinline__ void digits_of(long long v, uint16_t (&dg)[OZ_SLICES]) {
+// Digits of a value held in 64-bit fixed point v = x 2^56 (|x| < 1.5): rounded to
+// w = x 2^{7T}, then written as balanced base-2^7 digits, S_t in [-64, 63] for t >= 1 and
+// the rest in S_0 (|S_0| <= 2^7 + 1 for |x| <= 1), w = sum_t S_t 2^{7(T-1-t)} exactly.
+// The balanced digits of w are the plain base-2^7 digits of w + 64 (1 + 2^7 + ... +
+// 2^{7(T-2)}) less 64, so each is one shift-and-mask; the small integer becomes exact BF16
+// bits through the FP32 magic-number form (2^23 + u, then subtracting 2^23 + 64 is exact).
+// Returned are the FP32 bit patterns whose upper halves are the BF16 digits (digit t
+// weighs 2^{-7(t+1)}).
+__device__ __forceinline__ void digit_words(long long v, uint32_t (&fw)[OZ_SLICES]) {
   constexpr int drop = 56 - 7 * OZ_SLICES;
-  long long w = drop > 0 ? ((v + (1ll << (drop - 1))) >> drop) : v;
+  constexpr long long bias = 64ll * (((1ll << (7 * (OZ_SLICES - 1))) - 1) / 127);
+  const long long w = (drop > 0 ? ((v + (1ll << (drop - 1))) >> drop) : v) + bias;
 #pragma unroll
-  for (int t = OZ_SLICES - 1; t >= 0; --t) {
-    long long dgt;
-    if (t > 0) {
-      dgt = ((w + 64) & 127) - 64;
-      w = (w - dgt) >> 7;
-    } else {
-      dgt = w;
-    }
-    asm("cvt.rn.bf16.f32 %0, %1;\n" : "=h"(dg[t]) : "f"((float)dgt));
+  for (int t = OZ_SLICES - 1; t >= 1; --t) {
+    const uint32_t u = (uint32_t)(w >> (7 * (OZ_SLICES - 1 - t))) & 127u;
+    fw[t] = __float_as_uint(__fsub_rn(__uint_as_float(0x4B000000u | u), 8388672.0f));  // 2^23 + 64
   }
+  const int s0 = (int)(w >> (7 * (OZ_SLICES - 1)));  // |s0| < 256
+  fw[0] = __float_as_uint(__fsub_rn(__uint_as_float(0x4B000000u | (uint32_t)(s0 + 256)), 8388864.0f));
 }
 
 __device__ __forceinline__ void store_digits(uint16_t* const* slices, int64_t e, long long v) {
-  uint16_t dg[OZ_SLICES];
-  digits_of(v, dg);
+  uint32_t fw[OZ_SLICES];
+  digit_words(v, fw);
 #pragma unroll
-  for (int t = 0; t < OZ_SLICES; ++t) slices[t][e] = dg[t];
+  for (int t = 0; t < OZ_SLICES; ++t) slices[t][e] = (uint16_t)(fw[t] >> 16);
 }
 
 // Conversions between FP64 and the 2^-56 fixed point done with integer instructions (the
@@ -140,27 +141,61 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32
 // One FP64-accurate purification step for every part, in one persistent launch (one CTA
 // per SM walks the upper 128x128 tiles blockIdx.x, blockIdx.x + gridDim.x, ...).
 //
-// For each tile, the digit groups d = 0 .. T-1 are computed one after the other; a unit
-// (tile, d) is the K loop over the pairs (a, d - a), each item loading the A tile from digit
-// a (rows I) and the B tile from digit d - a (rows J) by TMA into a ring of stages, with
-// four K = 16 BF16 MMAs per item into one of two FP32 TMEM accumulators (columns 0-255,
-// alternating between units so the drain of one unit overlaps the next unit's MMAs).  The
-// epilogue warps turn each unit's integer-valued sums into 64-bit fixed point (2^-56) and
-// add them into a 64-bit accumulator that lives in TMEM columns 256-511 (low and high
-// words).  After the last group they form X_new = Y or 2X - Y, write the FP64 master copy
-// and the digits of X_new (into the other digit buffer) at (I, J) and mirrored at (J, I)
-// (diagonal tiles from their upper triangle), and add the core traces; the last block runs
-// the step bookkeeping.
+// The T(T+1)/2 digit products of a tile need one FP32 accumulator per group d = a + b
+// (T x 128 TMEM columns), more than the 512 columns of an SM, so a tile takes two passes
+// over K: first the high groups d >= OZ_SPLIT (all seven digits; 22 of the 28 products),
+// then the low groups d < OZ_SPLIT (digits below OZ_SPLIT).  A stage of the TMA ring holds
+// one K = OZ_BK slice of
+// every digit the pass needs, for rows I (A) and rows J (B; diagonal tiles reuse A), so each
+// distinct digit tile is loaded once per slice and feeds all its products (one K = 16 BF16
+// MMA each).  The epilogue warps turn the high groups' integer-valued sums into 64-bit
+// fixed point (2^-56) and park them in a per-CTA scratch tile (L2-resident), which frees
+// the columns for the low pass; after the low pass they add the low groups, form
+// X_new = Y or 2X - Y, write the FP64 master copy and the digits of X_new (into the other
+// digit buffer) at (I, J) and mirrored at (J, I) (diagonal tiles from their upper triangle),
+// and add the core traces, while the MMAs of the next tile's high pass run.  The new
+// iterate is written with evict-first stores: the next step reads it after this launch,
+// and keeping it out of L2 leaves room for the digit panels the running tiles share.  The last block
+// runs the step bookkeeping.
 //
-// 12 warps: warp 0 lane 0 TMA, warp 1 TMEM owner and MMA issuer, warps 4..11 epilogue
-// (warp w: TMEM lanes 32 (w % 4) .. + 31, column half (w - 4) / 4).
-__global__ void __launch_bounds__(384, 1) oz_step_kernel(OzStepArgs a) {
-  constexpr int STAGES = 6;
-  constexpr uint32_t STAGE_B = 2 * kTileBytes;
-  constexpr int BKE = 64;
+// 20 warps: warp 0 lane 0 TMA, warp 1 TMEM owner and MMA issuer, warps 4..19 epilogue
+// (warp w: TMEM lanes 32 (w % 4) .. + 31, columns 32 ((w - 4) / 4) .. + 31 of each group,
+// in two chunks of 16), sized so that four epilogue warps per scheduler hide latency.
+constexpr int OZ_STAGES = 2;
+constexpr uint32_t OZ_DTILE = 128u * OZ_BK * 2u;                 // one digit tile: 128 rows x 64 B
+constexpr uint32_t OZ_STAGE_B = 2u * OZ_SLICES * OZ_DTILE;       // all A and B digit tiles
+constexpr int OZ_EPI_WARPS = 16;                                 // 4 per TMEM lane quarter
+constexpr int OZ_THREADS = 32 * (4 + OZ_EPI_WARPS);
+constexpr int OZ_SMEM = OZ_STAGES * (int)OZ_STAGE_B + 1024 + 8 * (2 * OZ_STAGES + 4) + 16 + 16 * OZ_EPI_WARPS;
+static_assert(OZ_SLICES - OZ_SPLIT <= 4 && OZ_SPLIT <= 4, "groups of one pass must fit in 512 TMEM columns");
+static_assert(OZ_SMEM <= 232448, "shared memory of the emulated step");
+
+__device__ __forceinline__ uint32_t oz_group_col(int d) {
+  return (uint32_t)(d >= OZ_SPLIT ? 128 * (d - OZ_SPLIT + 4 - (OZ_SLICES - OZ_SPLIT)) : 128 * d);
+}
+
+// The MMAs of one stage for the groups d0 <= d < d1, fully unrolled: every pair (q, d - q)
+// of a group into the group's accumulator, descriptors formed by adding compile-time
+// offsets to the stage's base descriptors (the 14-bit address field cannot carry: shared
+// addresses stay below 2^18).
+template <int D0, int D1>
+__device__ __forceinline__ void oz_issue_stage(uint32_t tmem, uint64_t da, uint64_t db, bool first_k) {
   constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+  constexpr uint64_t step = OZ_DTILE >> 4;
+#pragma unroll
+  for (int kk = 0; kk < OZ_BK / 16; ++kk) {  // K = 16 slices inside the swizzled rows (32 B each)
+#pragma unroll
+    for (int d = D0; d < D1; ++d) {
+#pragma unroll
+      for (int q = 0; q <= d; ++q)
+        mma<0>(tmem + oz_group_col(d), da + (uint64_t)q * step + 2u * kk, db + (uint64_t)(d - q) * step + 2u * kk,
+               IDESC, (q > 0 || kk > 0 || !first_k) ? 1u : 0u);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
   constexpr int T = OZ_SLICES;
-  constexpr uint32_t ACC_LO = 256, ACC_HI = 384;  // TMEM columns of the 64-bit accumulator
 
   int step = a.step;
   if (a.mode == SQ_FORWARD) {
@@ -176,27 +211,29 @@ __global__ void __launch_bounds__(384, 1) oz_step_kernel(OzStepArgs a) {
   const uint32_t raw = smem_u32(smem_raw);
   const uint32_t base = (raw + 1023u) & ~1023u;
   uint8_t* sb = smem_raw + (base - raw);
-  const uint32_t bars = base + STAGES * STAGE_B;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sb + STAGES * STAGE_B + 8 * (2 * STAGES + 4));
+  const uint32_t bars = base + OZ_STAGES * OZ_STAGE_B;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sb + OZ_STAGES * OZ_STAGE_B + 8 * (2 * OZ_STAGES + 4));
   int* s_err = reinterpret_cast<int*>(tmem_slot + 1);
-  double2* red = reinterpret_cast<double2*>(sb + STAGES * STAGE_B + 8 * (2 * STAGES + 4) + 16);
+  double2* red = reinterpret_cast<double2*>(sb + OZ_STAGES * OZ_STAGE_B + 8 * (2 * OZ_STAGES + 4) + 16);
   auto full = [&](int s) { return bars + 8u * s; };
-  auto empty = [&](int s) { return bars + 8u * (STAGES + s); };
-  auto tfull = [&](int b) { return bars + 8u * (2 * STAGES + b); };
-  auto tempty = [&](int b) { return bars + 8u * (2 * STAGES + 2 + b); };
-  auto tile_addr = [&](int s, int op) { return base + (uint32_t)s * STAGE_B + (uint32_t)op * kTileBytes; };
+  auto empty = [&](int s) { return bars + 8u * (OZ_STAGES + s); };
+  // accumulator barriers: [0] high groups, [1] low groups
+  auto afull = [&](int pass) { return bars + 8u * (2 * OZ_STAGES + pass); };
+  auto aempty = [&](int pass) { return bars + 8u * (2 * OZ_STAGES + 2 + pass); };
+  auto tileA = [&](int s, int q) { return base + (uint32_t)s * OZ_STAGE_B + (uint32_t)q * OZ_DTILE; };
+  auto tileB = [&](int s, int q) { return base + (uint32_t)s * OZ_STAGE_B + (uint32_t)(OZ_SLICES + q) * OZ_DTILE; };
   int32_t* abort_flag = &a.ctl.st->timeout;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const CUtensorMap* maps = reinterpret_cast<const CUtensorMap*>(a.maps) + (size_t)dbi * T * a.nparts;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < OZ_STAGES; ++s) {
       mbar_init(full(s), 1);
       mbar_init(empty(s), 1);
     }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(tfull(b), 1);
-      mbar_init(tempty(b), 8);
+    for (int q = 0; q < 2; ++q) {
+      mbar_init(afull(q), 1);
+      mbar_init(aempty(q), OZ_EPI_WARPS);
     }
     *s_err = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -215,184 +252,198 @@ __global__ void __launch_bounds__(384, 1) oz_step_kernel(OzStepArgs a) {
     bool bad = false;
     for (int ti = blockIdx.x; ti < a.ntiles && !bad; ti += gridDim.x) {
       const Tile t = a.tiles[ti];
-      const PartDesc p = a.parts[t.part];
-      const int nk = (p.s + BKE - 1) / BKE;
-      for (int d = 0; d < T && !bad; ++d) {
-        for (int kb = 0; kb < nk && !bad; ++kb) {
-          for (int q = 0; q <= d; ++q, ++g) {
-            const int s = g % STAGES;
-            if (g >= STAGES && !mbar_wait(empty(s), ((g / STAGES) - 1) & 1, abort_flag)) {
-              bad = true;
-              break;
-            }
-            mbar_expect_tx(full(s), STAGE_B);
-            tma_load_2d(tile_addr(s, 0), maps + (size_t)q * a.nparts + t.part, kb * BKE, t.ti * 128, full(s));
-            tma_load_2d(tile_addr(s, 1), maps + (size_t)(d - q) * a.nparts + t.part, kb * BKE, t.tj * 128, full(s));
+      const int nk = (a.parts[t.part].s + OZ_BK - 1) / OZ_BK;
+      const bool dg = t.ti == t.tj;
+      for (int pass = 0; pass < 2 && !bad; ++pass) {
+        const int nd = pass == 0 ? T : OZ_SPLIT;  // digits the pass multiplies
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const int s = g % OZ_STAGES;
+          if (g >= OZ_STAGES && !mbar_wait(empty(s), ((g / OZ_STAGES) - 1) & 1, abort_flag)) {
+            bad = true;
+            break;
+          }
+          mbar_expect_tx(full(s), (uint32_t)(dg ? nd : 2 * nd) * OZ_DTILE);
+          for (int q = 0; q < nd; ++q) {
+            const CUtensorMap* m = maps + (size_t)q * a.nparts + t.part;
+            tma_load_2d(tileA(s, q), m, kb * OZ_BK, t.ti * 128, full(s));
+            if (!dg) tma_load_2d(tileB(s, q), m, kb * OZ_BK, t.tj * 128, full(s));
           }
         }
       }
     }
     if (bad) {
       *s_err = 1;
-      const uint32_t first = g > STAGES ? g - STAGES : 0;
-      for (uint32_t q = first; q < g; ++q) (void)mbar_wait(full(q % STAGES), (q / STAGES) & 1, abort_flag);
+      const uint32_t first = g > OZ_STAGES ? g - OZ_STAGES : 0;
+      for (uint32_t q = first; q < g; ++q) (void)mbar_wait(full(q % OZ_STAGES), (q / OZ_STAGES) & 1, abort_flag);
     }
   } else if (warp == 1 && lane == 0) {
     uint32_t g = 0;
-    int i = 0;  // unit counter (tile, group)
+    int u = 0;  // tiles done by this CTA
     bool bad = false;
-    for (int ti = blockIdx.x; ti < a.ntiles && !bad; ti += gridDim.x) {
+    for (int ti = blockIdx.x; ti < a.ntiles && !bad; ti += gridDim.x, ++u) {
       const Tile t = a.tiles[ti];
-      const PartDesc p = a.parts[t.part];
-      const int nk = (p.s + BKE - 1) / BKE;
-      for (int d = 0; d < T && !bad; ++d, ++i) {
-        const int b = i & 1, u = i >> 1;
-        if (u >= 1 && !mbar_wait(tempty(b), (u - 1) & 1, abort_flag)) {
+      const int nk = (a.parts[t.part].s + OZ_BK - 1) / OZ_BK;
+      const bool dg = t.ti == t.tj;
+      for (int pass = 0; pass < 2 && !bad; ++pass) {
+        // the high pass reuses the columns of the previous tile's low groups, the low pass
+        // those of this tile's high groups: wait until the epilogue has read them
+        const bool ready = pass == 0 ? (u == 0 || mbar_wait(aempty(1), (u - 1) & 1, abort_flag))
+                                     : mbar_wait(aempty(0), u & 1, abort_flag);
+        if (!ready) {
           bad = true;
           break;
         }
         tc_fence_after();
-        const uint32_t dt = tmem + (uint32_t)(b * 128);
-        bool first = true;
-        for (int kb = 0; kb < nk && !bad; ++kb) {
-          for (int q = 0; q <= d; ++q, ++g) {
-            const int s = g % STAGES;
-            if (!mbar_wait(full(s), (g / STAGES) & 1, abort_flag)) {
-              bad = true;
-              break;
-            }
-            tc_fence_after();
-            const uint64_t ad = smem_desc(tile_addr(s, 0)), bd = smem_desc(tile_addr(s, 1));
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-              const uint64_t adv = (uint64_t)((kk * 16 * 2) >> 4);
-              mma<0>(dt, ad + adv, bd + adv, IDESC, first ? 0u : 1u);
-              first = false;
-            }
-            mma_commit(empty(s));
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const int s = g % OZ_STAGES;
+          if (!mbar_wait(full(s), (g / OZ_STAGES) & 1, abort_flag)) {
+            bad = true;
+            break;
           }
+          tc_fence_after();
+          // pairs (q, d - q) of every group of the pass; both digits are < d1 <= T
+          const uint64_t da = smem_desc_sw<2 * OZ_BK>(tileA(s, 0));
+          const uint64_t db = dg ? da : smem_desc_sw<2 * OZ_BK>(tileB(s, 0));
+          if (pass == 0) oz_issue_stage<OZ_SPLIT, T>(tmem, da, db, kb == 0);
+          else oz_issue_stage<0, OZ_SPLIT>(tmem, da, db, kb == 0);
+          mma_commit(empty(s));
         }
-        mma_commit(tfull(b));
+        if (!bad) mma_commit(afull(pass));
       }
     }
     if (bad) *s_err = 1;
   } else if (warp >= 4) {
-    const int quarter = warp & 3, half = (warp - 4) >> 2;
+    const int quarter = warp & 3, colq = (warp - 4) >> 2;
     const int m = quarter * 32 + lane;
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+    long long* acc = a.acc + (size_t)blockIdx.x * (128 * 128);
     int8_t alf;
     if (a.mode == SQ_TAIL_FIRST) alf = (a.ctl.traces[step - 1] <= (double)a.ctl.nocc) ? (int8_t)1 : (int8_t)-1;
     else if (a.mode == SQ_TAIL_NEXT) alf = (int8_t)(-a.ctl.alpha[step - 1]);
     else alf = a.ctl.alpha[step];
-    int i = 0;
-    for (int ti = blockIdx.x; ti < a.ntiles; ti += gridDim.x) {
+    int u = 0;
+    for (int ti = blockIdx.x; ti < a.ntiles; ti += gridDim.x, ++u) {
       const Tile t = a.tiles[ti];
       const PartDesc p = a.parts[t.part];
       const int64_t ld = p.ld;
       const int r = t.ti * 128 + m, c0 = t.tj * 128;
       const bool diag = t.slot >= 0;
       double tY = 0.0, tN = 0.0;
-      bool okall = true;
-      for (int d = 0; d < T; ++d, ++i) {
-        const int b = i & 1, u = i >> 1;
-        const bool ok = __all_sync(0xffffffffu, mbar_wait(tfull(b), u & 1, abort_flag));
+      bool ok = true;
+      // the two passes: read the groups' sums (integers held exactly in FP32), add them as
+      // 64-bit integers into the scratch tile (thread-private entries: column cl, row m),
+      // then hand the columns back
+      for (int pass = 0; pass < 2; ++pass) {
+        ok = __all_sync(0xffffffffu, mbar_wait(afull(pass), u & 1, abort_flag)) && ok;
         tc_fence_after();
-        okall = okall && ok;
-        const int shift = 7 * (6 - d) + 7 * (7 - T);  // 2^{-7(d+2)} in units of 2^-56
+        const int d0 = pass == 0 ? OZ_SPLIT : 0, d1 = pass == 0 ? T : OZ_SPLIT;
 #pragma unroll 1
         for (int cc = 0; cc < 2 && ok; ++cc) {
-          const int cb = half * 2 + cc;
-          uint32_t v[32], lo[32], hi[32];
-          tmem_ld32(tmem + lane_off + (uint32_t)(b * 128 + cb * 32), v);
-          if (d > 0) {
-            tmem_ld32(tmem + lane_off + ACC_LO + (uint32_t)(cb * 32), lo);
-            tmem_ld32(tmem + lane_off + ACC_HI + (uint32_t)(cb * 32), hi);
-          }
+          const int cl = colq * 32 + cc * 16;
+          long long z[16];
+          long long* zp = acc + (size_t)cl * 128 + m;
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
-            long long z = fint_shl(__uint_as_float(v[j]), shift);
-            if (d > 0) z += (long long)(((unsigned long long)hi[j] << 32) | lo[j]);
-            lo[j] = (uint32_t)((unsigned long long)z & 0xFFFFFFFFull);
-            hi[j] = (uint32_t)((unsigned long long)z >> 32);
-          }
-          if (d < T - 1) {
-            tmem_st32(tmem + lane_off + ACC_LO + (uint32_t)(cb * 32), lo);
-            tmem_st32(tmem + lane_off + ACC_HI + (uint32_t)(cb * 32), hi);
-          } else {
-            // final pass of the tile: X_new on the 2^-56 grid, FP64 master, digits, traces;
-            // column writes are coalesced across the warp, the mirrored row segment of each
-            // thread goes out in groups of 8 as 16-byte vectors
-            const int cbase = c0 + cb * 32;
-            const bool offd = t.ti != t.tj;
+          for (int j = 0; j < 16; ++j) z[j] = pass == 0 ? 0ll : zp[(size_t)j * 128];
+#pragma unroll 1
+          for (int d = d0; d < d1; ++d) {
+            uint32_t v[16];
+            tmem_ld16(tmem + lane_off + oz_group_col(d) + (uint32_t)cl, v);
+            const int shift = 56 - 7 * (d + 2);  // group weight 2^{-7(d+2)} in units of 2^-56
 #pragma unroll
-            for (int sub = 0; sub < 4; ++sub) {
-              double xn8[8];
-              uint16_t dg8[8][OZ_SLICES];
-#pragma unroll
-              for (int u = 0; u < 8; ++u) {
-                const int j = sub * 8 + u;
-                const int c = cbase + j;
-                const long long yf = (long long)(((unsigned long long)hi[j] << 32) | lo[j]);
-                const int64_t e = (int64_t)c * ld + r;
-                const bool upper = offd || c >= r;  // diagonal tiles: upper triangle only
-                const long long xf = (alf > 0 && upper) ? 2 * to_fixed(a.xin[p.off + e]) - yf : yf;
-                xn8[u] = from_fixed(xf);
-                digits_of(xf, dg8[u]);
-                if (upper) {
-                  a.xout[p.off + e] = xn8[u];
-#pragma unroll
-                  for (int q = 0; q < OZ_SLICES; ++q) a.digits[dbo].s[q][p.off + e] = dg8[u][q];
-                  if (c == r && diag && r < p.c) {
-                    tY += from_fixed(yf);
-                    tN += xn8[u];
-                  }
-                }
-              }
-              const int64_t em = p.off + (int64_t)r * ld + cbase + sub * 8;
-              if (offd) {
-                double2* xm = reinterpret_cast<double2*>(a.xout + em);
-#pragma unroll
-                for (int u = 0; u < 4; ++u) xm[u] = make_double2(xn8[2 * u], xn8[2 * u + 1]);
-#pragma unroll
-                for (int q = 0; q < OZ_SLICES; ++q) {
-                  uint4 pk;
-                  pk.x = (uint32_t)dg8[0][q] | ((uint32_t)dg8[1][q] << 16);
-                  pk.y = (uint32_t)dg8[2][q] | ((uint32_t)dg8[3][q] << 16);
-                  pk.z = (uint32_t)dg8[4][q] | ((uint32_t)dg8[5][q] << 16);
-                  pk.w = (uint32_t)dg8[6][q] | ((uint32_t)dg8[7][q] << 16);
-                  *reinterpret_cast<uint4*>(a.digits[dbo].s[q] + em) = pk;
-                }
-              } else {
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                  if (cbase + sub * 8 + u <= r) continue;
-                  a.xout[em + u] = xn8[u];
-#pragma unroll
-                  for (int q = 0; q < OZ_SLICES; ++q) a.digits[dbo].s[q][em + u] = dg8[u][q];
-                }
-              }
+            for (int j = 0; j < 16; ++j) {
+              const long long g = (long long)__float2int_rn(__uint_as_float(v[j]));  // exact: |sum| < 2^31
+              z[j] += (long long)((unsigned long long)g << shift);
             }
           }
+#pragma unroll
+          for (int j = 0; j < 16; ++j) zp[(size_t)j * 128] = z[j];
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(tempty(b));
+        if (lane == 0) mbar_arrive(aempty(pass));
       }
-      if (!okall) *s_err = 1;
+      if (!ok) *s_err = 1;
+      // final pass of the tile: X_new on the 2^-56 grid, FP64 master, digits, traces; column
+      // writes are coalesced across the warp, the mirrored row segment of each thread goes
+      // out in groups of 4 as 32-byte (FP64) and 8-byte (digit) vectors
+      const bool offd = t.ti != t.tj;
+#pragma unroll 1
+      for (int cc = 0; cc < 2 && ok; ++cc) {
+        const int cl = colq * 32 + cc * 16;
+        const int cbase = c0 + cl;
+        const long long* zp = acc + (size_t)cl * 128 + m;
+#pragma unroll
+        for (int sub = 0; sub < 4; ++sub) {
+          // loads of the group first (xin is not written by this launch), so that they are
+          // in flight together rather than each behind the previous group's stores
+          long long yv[4];
+          double xv[4];
+#pragma unroll
+          for (int w = 0; w < 4; ++w) {
+            const int j = sub * 4 + w;
+            yv[w] = zp[(size_t)j * 128];
+            xv[w] = alf > 0 ? __ldg(a.xin + p.off + (int64_t)(cbase + j) * ld + r) : 0.0;
+          }
+          double xn4[4];
+          uint32_t dw4[4][OZ_SLICES];
+#pragma unroll
+          for (int w = 0; w < 4; ++w) {
+            const int c = cbase + sub * 4 + w;
+            const long long yf = yv[w];
+            const int64_t e = (int64_t)c * ld + r;
+            const bool upper = offd || c >= r;  // diagonal tiles: upper triangle only
+            const long long xf = (alf > 0 && upper) ? 2 * to_fixed(xv[w]) - yf : yf;
+            xn4[w] = from_fixed(xf);
+            digit_words(xf, dw4[w]);
+            if (upper) {
+              __stcs(a.xout + p.off + e, xn4[w]);
+#pragma unroll
+              for (int q = 0; q < OZ_SLICES; ++q)
+                __stcs(a.digits[dbo].s[q] + p.off + e, (unsigned short)(dw4[w][q] >> 16));
+              if (c == r && diag && r < p.c) {
+                tY += from_fixed(yf);
+                tN += xn4[w];
+              }
+            }
+          }
+          const int64_t em = p.off + (int64_t)r * ld + cbase + sub * 4;
+          if (offd) {
+            double2* xm = reinterpret_cast<double2*>(a.xout + em);
+            __stcs(xm, make_double2(xn4[0], xn4[1]));
+            __stcs(xm + 1, make_double2(xn4[2], xn4[3]));
+#pragma unroll
+            for (int q = 0; q < OZ_SLICES; ++q) {
+              uint2 pk;  // upper halves of two words per 32 bits
+              pk.x = __byte_perm(dw4[0][q], dw4[1][q], 0x7632);
+              pk.y = __byte_perm(dw4[2][q], dw4[3][q], 0x7632);
+              __stcs(reinterpret_cast<uint2*>(a.digits[dbo].s[q] + em), pk);
+            }
+          } else {
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+              if (cbase + sub * 4 + w <= r) continue;
+              __stcs(a.xout + em + w, xn4[w]);
+#pragma unroll
+              for (int q = 0; q < OZ_SLICES; ++q)
+                __stcs(a.digits[dbo].s[q] + em + w, (unsigned short)(dw4[w][q] >> 16));
+            }
+          }
+        }
+      }
       if (diag) {
         tY = warp_sum(tY);
         tN = warp_sum(tN);
         if (lane == 0) red[warp - 4] = make_double2(tY, tN);
-        asm volatile("bar.sync 1, 256;\n" ::: "memory");
+        asm volatile("bar.sync 1, %0;\n" ::"n"(32 * OZ_EPI_WARPS) : "memory");
         if (warp == 4 && lane == 0) {
-          double2 acc = make_double2(0.0, 0.0);
-          for (int w = 0; w < 8; ++w) {
-            acc.x += red[w].x;
-            acc.y += red[w].y;
+          double2 sum = make_double2(0.0, 0.0);
+          for (int w = 0; w < OZ_EPI_WARPS; ++w) {
+            sum.x += red[w].x;
+            sum.y += red[w].y;
           }
-          a.slots[t.slot] = acc;
+          a.slots[t.slot] = sum;
         }
-        asm volatile("bar.sync 1, 256;\n" ::: "memory");
+        asm volatile("bar.sync 1, %0;\n" ::"n"(32 * OZ_EPI_WARPS) : "memory");
       }
     }
   }
@@ -433,12 +484,11 @@ cudaError_t launch_oz_slice(const PartDesc* parts, const ColBlock* blocks, int n
 }
 
 cudaError_t launch_oz_step(const OzStepArgs& a, int grid, cudaStream_t s) {
-  constexpr int STAGES = 6;
-  const int smem = STAGES * 2 * (int)kTileBytes + 1024 + 8 * (2 * STAGES + 4) + 16 + 8 * 16;
-  cudaError_t e = cudaFuncSetAttribute(oz_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = cudaFuncSetAttribute(oz_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
   if (e != cudaSuccess) return e;
-  const int gr = grid < a.ntiles ? grid : a.ntiles;
-  oz_step_kernel<<<gr, 384, smem, s>>>(a);
+  int gr = grid < a.ntiles ? grid : a.ntiles;
+  if (gr > OZ_MAX_GRID) gr = OZ_MAX_GRID;  // one scratch tile per CTA
+  oz_step_kernel<<<gr, OZ_THREADS, OZ_SMEM, s>>>(a);
   return cudaGetLastError();
 }
 

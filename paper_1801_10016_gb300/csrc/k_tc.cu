@@ -677,7 +677,10 @@ cudaError_t launch_convert(const float* const* master_of_step, double* out, int6
 // Encode one tensor map per part over an operand arena: 2-D, inner dimension = rows
 // of a column (contiguous), outer = columns, box = 128 bytes x 128 columns, 128-byte
 // swizzle.  `enc` is cuTensorMapEncodeTiled obtained from the driver.
-int encode_part_maps(void* enc_fn, void* out_maps, const PartDesc* parts, int nparts, void* arena, int kind) {
+// One 2-D tensor map per part over an arena (x = row within a column, y = column), box
+// box_bytes x 128 columns with the swizzle of the same width (128, 64 or 32 bytes).
+int encode_part_maps(void* enc_fn, void* out_maps, const PartDesc* parts, int nparts, void* arena, int kind,
+                     int box_bytes) {
   CUtensorMap* out = reinterpret_cast<CUtensorMap*>(out_maps);
   using Enc = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*, const cuuint64_t*,
                            const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -688,11 +691,14 @@ int encode_part_maps(void* enc_fn, void* out_maps, const PartDesc* parts, int np
     const PartDesc& p = parts[k];
     cuuint64_t dims[2] = {(cuuint64_t)p.ld, (cuuint64_t)p.ld};
     cuuint64_t strides[1] = {(cuuint64_t)p.ld * es};
-    cuuint32_t box[2] = {(cuuint32_t)(128 / es), 128u};
+    cuuint32_t box[2] = {(cuuint32_t)(box_bytes / es), 128u};
     cuuint32_t estr[2] = {1u, 1u};
     void* addr = (char*)arena + (size_t)p.off * es;
     CUresult r = enc(&out[k], kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, addr,
-                     dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     box_bytes == 32   ? CU_TENSOR_MAP_SWIZZLE_32B
+                     : box_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                       : CU_TENSOR_MAP_SWIZZLE_128B,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return (int)r;
   }

@@ -239,6 +239,9 @@ WORKLOADS = {
     "tb30k": dict(n_sites=7500, nparts=256, graph_radius=5.0),
     # 4,096 orbitals, 32 parts, sizes ~200-500 (adjoint workload)
     "tb4k": dict(n_sites=1024, nparts=32, graph_radius=3.0),
+    # 8,000 orbitals, 64 parts, the part sizes of tb30k on a quarter of the volume (arenas
+    # still larger than L2): the case kernel profiles are taken on
+    "tb8k": dict(n_sites=2000, nparts=64, graph_radius=5.0),
     # 120,000 orbitals, 1,024 parts, sizes ~200-2,000
     "tb120k": dict(n_sites=30000, nparts=1024, graph_radius=5.0),
 }
