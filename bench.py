@@ -32,7 +32,8 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 NOMINAL = {"bf16": 2250.0, "tf32": 1100.0, "fp64": 1.25}
 # DRAM bytes per launch of the dominant kernel from one ncu capture (workload, precision);
 # entries are removed when the kernel changes
-TRAFFIC = {("tb30k", "fp64"): 2.80e9}
+# (fp64e: tb8k capture scaled to tb30k by arena elements, 3.66 GB x 4.98)
+TRAFFIC = {("tb30k", "fp64"): 2.80e9, ("tb30k", "fp64e"): 18.2e9}
 
 
 def dist_env():
@@ -185,7 +186,7 @@ def fp64_roofline(precision, sizes, avg_launch_ms, peaks, src, workload):
     rebuilt from BF16 digits (tensor pipe, executed BF16 flops of all digit products)."""
     import numpy as np
     if precision == "fp64e":
-        flops = tc_exec_flops(sizes, 64, OZ_PRODUCTS)
+        flops = tc_exec_flops(sizes, 32, OZ_PRODUCTS)
         achieved = flops / (avg_launch_ms / 1e3) / 1e12
         peak = peaks["bf16_tflops"]
         return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
