@@ -278,6 +278,8 @@ def run_ours(args):
     h_dev = torch.from_numpy(s.vals).to(dev)
     p_dev = torch.empty(plan.nnz_p, dtype=torch.float64, device=dev)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
+    # schedule autotuner (untimed): keeps the fastest schedule / tile order for this plan
+    tune = None if args.no_autotune else plan.autotune(h_dev, trials=2)
     stream = torch.cuda.current_stream()
     warm = max(3, args.warmup)
 
@@ -336,7 +338,9 @@ def run_ours(args):
                    "result_precision": "fp64" if args.precision in ("fp64", "fp64e") else args.precision,
                    "arith": args.precision, "sp2_steps": int(steps_applied),
                    "l2": "flushed (256 MB write) between timed P-builds; the arenas also exceed L2",
-                   "parallelism": "replicas" if world > 1 else "single"},
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "schedule": {"tc_schedule": int(plan.info.tc_schedule), "tile_order": int(plan.info.tile_order),
+                                "autotuned": tune is not None}},
         "tflops_dgemm_equiv": dgemm_equiv * steps_applied / (ms_per_step / 1e3) / 1e12,
         "roofline": roof,
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(plan.nnz_h * 8),
@@ -392,6 +396,7 @@ def run_ours(args):
             kw = dict(precision=prec, max_steps=args.max_steps, lp_tail_steps=lp_tail, fp64_tail_steps=fp_tail)
             mp = GSP2(s.n, s.rowptr, s.colind, s.nocc, s.part, s.nparts, s.g_rowptr, s.g_colind, device=dev,
                       time_steps=1, **kw)
+            mtune = None if args.no_autotune else mp.autotune(h_dev, trials=2)
             pm = torch.empty(mp.nnz_p, dtype=torch.float64, device=dev)
             for _ in range(warm):
                 mp.density(h_dev, out=pm)
@@ -426,7 +431,8 @@ def run_ours(args):
                      "trace_minus_nocc": mrep["trace"] - s.nocc,
                      "status": int(mst), "clocks": mclk.summary(),
                      "square_kernel_ms": k_ms,
-                     "tflops_dgemm_equiv": dgemm_equiv * lp_steps / t_build / 1e12}
+                     "tflops_dgemm_equiv": dgemm_equiv * lp_steps / t_build / 1e12,
+                     "schedule": None if mtune is None else mtune["candidates"][mtune["chosen"]]}
             if prec != "fp32":
                 # executed tensor flops of one launch: every 128x128 upper tile, K rounded to the stage
                 nt = np.ceil(sizes / 128.0)
@@ -475,6 +481,7 @@ def main():
     ap.add_argument("--ref-stride", dest="ref_stride", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", dest="no_cpu_baseline", action="store_true")
     ap.add_argument("--no-mixed", dest="no_mixed", action="store_true")
+    ap.add_argument("--no-autotune", dest="no_autotune", action="store_true")
     ap.add_argument("--mixed", default="tf32x3,tf32x3:lp1:fp1,tf32x3:lp2,bf16x3,bf16x3:lp2,tf32,bf16,fp32")
     args = ap.parse_args()
     if args.impl == "reference":

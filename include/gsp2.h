@@ -66,8 +66,8 @@ typedef enum {
   GSP2_PREC_BF16 = 3,
   GSP2_PREC_BF16X3 = 4, /* split operands hi+lo in BF16, three products, FP32 accumulate */
   GSP2_PREC_TF32X3 = 5, /* split operands hi+lo in TF32, three products, FP32 accumulate */
-  GSP2_PREC_FP64_EMU = 6 /* FP64 results; every product X X rebuilt from 8 base-2^7 digits of X
-                            held in BF16 (36 exact BF16 tensor-core products per tile, groups
+  GSP2_PREC_FP64_EMU = 6 /* FP64 results; every product X X rebuilt from 7 base-2^7 digits of X
+                            held in BF16 (28 exact BF16 tensor-core products per tile, groups
                             summed as 64-bit fixed point), FP64 master copy and epilogue */
 } gsp2_precision;
 
@@ -101,7 +101,13 @@ typedef struct {
   int32_t fp64_tail_emulated; /* low-precision modes: 1 (default) runs the FP64 tail steps with
                                  the products rebuilt from BF16 digits (as GSP2_PREC_FP64_EMU),
                                  0 on the FP64 units */
-  int32_t reserved[3];
+  int32_t tile_order;      /* order of the 128x128 tiles walked by the persistent kernels
+                              (tensor-core steps with tc_schedule = 0, FP64_EMU steps): 0 (default)
+                              parts by descending size, tile t to CTA t mod (number of SMs);
+                              1 = the same list reversed in every other round of SMs, so that
+                              each SM's share of the uneven tiles evens out; set by
+                              gsp2_autotune */
+  int32_t reserved[2];
 } gsp2_options;
 
 /* Per-call report, read back by gsp2_sync_status. */
@@ -135,6 +141,8 @@ typedef struct {
   int32_t ld_pad;       /* padding multiple of ld_k */
   int32_t step_launches;   /* purification-step launches per density call (the loop's) */
   int32_t fp64_tail_steps; /* resolved value of the option */
+  int32_t tc_schedule;     /* schedule and tile order in use (options, or gsp2_autotune's choice) */
+  int32_t tile_order;
 } gsp2_plan_info;
 
 /* Fill `opt` with the defaults listed above. */
@@ -209,6 +217,31 @@ gsp2_status gsp2_history(gsp2_handle h, double* traces, double* idem, int8_t* al
  * milliseconds, ms[i-1] for step i (1..max_steps); needs time_steps = 1.  Steps after
  * the stopping test return at once and show a few microseconds.  Waits for the call. */
 gsp2_status gsp2_step_times(gsp2_handle h, float* ms, int32_t cap);
+
+/* Outcome of gsp2_autotune: the candidates tried and their times. */
+typedef struct {
+  int32_t ncand;        /* candidates timed (1 when the precision has no choice) */
+  int32_t chosen;       /* index of the fastest, now in use */
+  int32_t tc_schedule[4];
+  int32_t tile_order[4];
+  double ms[4];         /* median device time of one density call, milliseconds */
+} gsp2_tune_report;
+
+/*
+ * Autotuner of the step schedule (batching of uneven parts, not in the paper): times whole
+ * density calls (RECORD mode, `trials` >= 1 each after one untimed call) with every candidate
+ * that applies to the plan's precision -- tensor-core steps: persistent with either tile
+ * order, and one CTA per tile; FP64_EMU steps: either tile order; FP64 and FP32: the only
+ * schedule -- and keeps the fastest in the plan (gsp2_plan_query reports it).  Every
+ * candidate computes bitwise the same P (a tile's arithmetic does not depend on the CTA
+ * that runs it).
+ *  d_hvals, d_pvals  as for gsp2_density; d_pvals is overwritten
+ *  rep               optional output
+ * Synchronises `stream`.  Errors: GSP2_E_ARG, GSP2_E_STATE (no workspace), GSP2_E_CUDA, or
+ * the device status of a timed call (the plan then keeps the candidate that failed).
+ */
+gsp2_status gsp2_autotune(gsp2_handle h, const double* d_hvals, double* d_pvals, int32_t trials, void* stream,
+                          gsp2_tune_report* rep);
 
 /*
  * Adjoint of P(H): given Pbar = dL/dP on the pattern of P, write Hbar = dL/dH on the

@@ -65,6 +65,7 @@ struct gsp2_plan {
   std::vector<int32_t> mempart, memloc;  // part id, local index in S_part
   std::vector<Tile> tiles;                 // 64x64 upper tiles (CUDA-core steps)
   std::vector<Tile> tc_tiles;              // 128x128 upper tiles (tensor-core steps)
+  std::vector<Tile> tc_order;              // tc_tiles in the order of opt.tile_order (uploaded)
   std::vector<ColBlock> gblocks, sblocks;  // gather (to nt*64) and scatter (cores) columns
   std::vector<ColBlock> gblocks_ld;        // low-precision gather: every column up to ld
   int32_t nslots_tc = 0;
@@ -307,6 +308,7 @@ extern "C" gsp2_status gsp2_create(int64_t n, const int64_t* rowptr, const int32
     if (o.lp_tail_steps < 0 || o.fp64_tail_steps + o.lp_tail_steps > MAX_TAIL)
       return bail(GSP2_E_ARG, "lp_tail_steps must be >= 0 with lp_tail_steps + fp64_tail_steps <= 8");
     if (o.tc_schedule < 0 || o.tc_schedule > 1) return bail(GSP2_E_ARG, "tc_schedule must be 0 or 1");
+    if (o.tile_order < 0 || o.tile_order > 1) return bail(GSP2_E_ARG, "tile_order must be 0 or 1");
     if (o.lp_tail_steps > 0 && (fp64_like(o.precision) || o.precision == GSP2_PREC_FP32))
       return bail(GSP2_E_ARG, "lp_tail_steps needs a tensor-core precision");
     if (o.ckpt_every < 0) return bail(GSP2_E_ARG, "ckpt_every must be >= 0");
@@ -473,6 +475,8 @@ extern "C" gsp2_status gsp2_plan_query(gsp2_handle h, gsp2_plan_info* info, int3
     info->ld_pad = LD_PAD;
     info->step_launches = (int32_t)(h->ev.empty() ? std::max(h->total_steps, h->opt.max_steps) : h->ev.size() / 2);
     info->fp64_tail_steps = h->opt.fp64_tail_steps;
+    info->tc_schedule = h->opt.tc_schedule;
+    info->tile_order = h->opt.tile_order;
   }
   for (int32_t k = 0; k < h->nparts; ++k) {
     if (s) s[k] = h->parts[k].s;
@@ -497,6 +501,21 @@ static void drop_graph(gsp2_plan* h) {
   h->bexec = nullptr;
   h->bkey_pbar = nullptr;
   h->bkey_hbar = nullptr;
+}
+
+// The 128x128 tile list in the order of opt.tile_order for a grid of `grid` persistent CTAs
+// (CTA b takes entries b, b + grid, ...): 0 keeps parts by descending size; 1 reverses every
+// other round of `grid` entries, so that the CTA that took the largest tile of one round
+// takes the smallest of the next.
+static void order_tc_tiles(gsp2_plan* h, int grid) {
+  h->tc_order = h->tc_tiles;
+  if (h->opt.tile_order != 1 || grid < 2) return;
+  const size_t g = (size_t)grid;
+  for (size_t r = 0; r * g < h->tc_order.size(); ++r)
+    if (r & 1) {
+      const size_t b = r * g, e = std::min(b + g, h->tc_order.size());
+      std::reverse(h->tc_order.begin() + b, h->tc_order.begin() + e);
+    }
 }
 
 extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t bytes, void* stream) {
@@ -537,7 +556,8 @@ extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t byt
   for (size_t i = 0; i < tab.size(); ++i) tab[i] = (const double*)(h->ws + h->step_arena_off[i]);
   CU(h, up(L.step_arena, tab.data(), tab.size() * sizeof(double*)));
   CU(h, up(L.tiles, h->tiles.data(), h->tiles.size() * sizeof(Tile)));
-  CU(h, up(L.tc_tiles, h->tc_tiles.data(), h->tc_tiles.size() * sizeof(Tile)));
+  order_tc_tiles(h, h->num_sms);
+  CU(h, up(L.tc_tiles, h->tc_order.data(), h->tc_order.size() * sizeof(Tile)));
   CU(h, up(L.gblocks_ld, h->gblocks_ld.data(), h->gblocks_ld.size() * sizeof(ColBlock)));
   if (h->use_oz) {
     void* enc = nullptr;
@@ -800,6 +820,83 @@ extern "C" gsp2_status gsp2_density(gsp2_handle h, const double* d_hvals, double
   }
   h->have_forward = true;
   return GSP2_OK;
+}
+
+extern "C" gsp2_status gsp2_autotune(gsp2_handle h, const double* d_hvals, double* d_pvals, int32_t trials,
+                                     void* stream, gsp2_tune_report* rep) {
+  if (!usable(h)) return fail(h, GSP2_E_ARG, "invalid handle");
+  if (!h->ws) return fail(h, GSP2_E_STATE, "no workspace bound");
+  if (!d_hvals || !d_pvals || trials < 1 || trials > 100) return fail(h, GSP2_E_ARG, "NULL buffer or trials not in 1..100");
+  cudaStream_t s = (cudaStream_t)stream;
+  // candidates (tc_schedule, tile_order) that change something for this precision
+  std::vector<std::pair<int, int>> cand;
+  const int prec = h->opt.precision;
+  if (!fp64_like(prec) && prec_kind(prec) >= 0) cand = {{0, 0}, {0, 1}, {1, 0}};
+  else if (prec == GSP2_PREC_FP64_EMU) cand = {{0, 0}, {0, 1}};
+  else cand = {{h->opt.tc_schedule, h->opt.tile_order}};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CU(h, cudaEventCreate(&e0));
+  CU(h, cudaEventCreate(&e1));
+  auto apply = [&](int sched, int order) -> cudaError_t {
+    if (sched != h->opt.tc_schedule) drop_graph(h);  // the schedule is part of the captured launches
+    h->opt.tc_schedule = sched;
+    h->opt.tile_order = order;
+    order_tc_tiles(h, h->num_sms);
+    if (h->tc_order.empty()) return cudaSuccess;
+    cudaError_t e = cudaMemcpyAsync(h->ws + h->L.tc_tiles, h->tc_order.data(), h->tc_order.size() * sizeof(Tile),
+                                    cudaMemcpyHostToDevice, s);
+    return e != cudaSuccess ? e : cudaStreamSynchronize(s);  // the host vector may change next round
+  };
+  std::vector<double> med(cand.size(), 0.0);
+  gsp2_status out = GSP2_OK;
+  for (size_t c = 0; c < cand.size() && out == GSP2_OK; ++c) {
+    cudaError_t e = apply(cand[c].first, cand[c].second);
+    if (e != cudaSuccess) {
+      out = cuda_fail(h, e, "autotune: tile list upload");
+      break;
+    }
+    std::vector<float> t;
+    for (int k = 0; k <= trials && out == GSP2_OK; ++k) {
+      if (k > 0 && (e = cudaEventRecord(e0, s)) != cudaSuccess) out = cuda_fail(h, e, "cudaEventRecord");
+      if (out == GSP2_OK) out = gsp2_density(h, d_hvals, d_pvals, nullptr, MODE_RECORD, 0, stream);
+      if (out == GSP2_OK && k > 0) {
+        float ms = 0.f;
+        if ((e = cudaEventRecord(e1, s)) != cudaSuccess || (e = cudaEventSynchronize(e1)) != cudaSuccess ||
+            (e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess)
+          out = cuda_fail(h, e, "autotune timing");
+        t.push_back(ms);
+      }
+      if (out == GSP2_OK) {
+        gsp2_report r{};
+        const gsp2_status st = gsp2_sync_status(h, &r);
+        if (st != GSP2_OK && st != GSP2_E_NOT_CONVERGED) out = st;
+      }
+    }
+    if (out == GSP2_OK) {
+      std::sort(t.begin(), t.end());
+      med[c] = t[t.size() / 2];
+    }
+  }
+  size_t best = 0;
+  if (out == GSP2_OK) {
+    for (size_t c = 1; c < cand.size(); ++c)
+      if (med[c] < med[best]) best = c;
+    const cudaError_t e = apply(cand[best].first, cand[best].second);
+    if (e != cudaSuccess) out = cuda_fail(h, e, "autotune: tile list upload");
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rep) {
+    std::memset(rep, 0, sizeof(*rep));
+    rep->ncand = (int32_t)cand.size();
+    rep->chosen = (int32_t)best;
+    for (size_t c = 0; c < cand.size(); ++c) {
+      rep->tc_schedule[c] = cand[c].first;
+      rep->tile_order[c] = cand[c].second;
+      rep->ms[c] = med[c];
+    }
+  }
+  return out;
 }
 
 extern "C" gsp2_status gsp2_sync_status(gsp2_handle h, gsp2_report* r) {

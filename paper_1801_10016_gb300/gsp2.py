@@ -37,7 +37,7 @@ class Options(C.Structure):
                 ("precision", C.c_int32), ("fp64_tail_steps", C.c_int32), ("ckpt_every", C.c_int32),
                 ("use_graph", C.c_int32), ("time_steps", C.c_int32), ("lp_tail_steps", C.c_int32),
                 ("tc_schedule", C.c_int32), ("report_idem", C.c_int32), ("fp64_tail_emulated", C.c_int32),
-                ("reserved", C.c_int32 * 3)]
+                ("tile_order", C.c_int32), ("reserved", C.c_int32 * 2)]
 
 
 class Report(C.Structure):
@@ -50,7 +50,13 @@ class PlanInfo(C.Structure):
     _fields_ = [("n", C.c_int64), ("nocc", C.c_int64), ("nparts", C.c_int32), ("max_s", C.c_int32),
                 ("sum_s", C.c_int64), ("sum_s2", C.c_double), ("sum_s3", C.c_double), ("nnz_h", C.c_int64),
                 ("nnz_p", C.c_int64), ("arena_elems", C.c_int64), ("ntiles", C.c_int64), ("tile", C.c_int32),
-                ("ld_pad", C.c_int32), ("step_launches", C.c_int32), ("fp64_tail_steps", C.c_int32)]
+                ("ld_pad", C.c_int32), ("step_launches", C.c_int32), ("fp64_tail_steps", C.c_int32),
+                ("tc_schedule", C.c_int32), ("tile_order", C.c_int32)]
+
+
+class TuneReport(C.Structure):
+    _fields_ = [("ncand", C.c_int32), ("chosen", C.c_int32), ("tc_schedule", C.c_int32 * 4),
+                ("tile_order", C.c_int32 * 4), ("ms", C.c_double * 4)]
 
 
 _lib = None
@@ -86,6 +92,7 @@ def load(path: str = LIB_PATH):
         "gsp2_history": (C.c_int, [_P, _P, _P, _P, C.c_int32]),
         "gsp2_step_times": (C.c_int, [_P, _P, C.c_int32]),
         "gsp2_backward": (C.c_int, [_P, _P, _P, _P]),
+        "gsp2_autotune": (C.c_int, [_P, _P, _P, C.c_int32, _P, C.POINTER(TuneReport)]),
         "gsp2_last_error": (C.c_char_p, [_P]),
         "gsp2_destroy": (None, [_P]),
     }
@@ -208,6 +215,27 @@ class GSP2:
         self._check(self._lib.gsp2_density(self._h, _tptr(h_vals), _tptr(out), _tptr(alpha), MODES[mode],
                                            int(nsteps), _stream_ptr(stream)))
         return out
+
+    def autotune(self, h_vals, trials=3, stream=None):
+        """Time every schedule candidate of the plan's precision on whole density calls and
+        keep the fastest (gsp2_autotune); returns the candidates and their median times."""
+        import torch
+        if h_vals.dtype != torch.float64 or not h_vals.is_cuda or h_vals.numel() != self.nnz_h:
+            raise ValueError("h_vals must be a CUDA float64 tensor of nnz(H) values")
+        out = torch.empty(self.nnz_p, dtype=torch.float64, device=h_vals.device)
+        r = TuneReport()
+        self._check(self._lib.gsp2_autotune(self._h, _tptr(h_vals.contiguous()), _tptr(out), int(trials),
+                                            _stream_ptr(stream), C.byref(r)))
+        self._refresh_info()
+        cands = [dict(tc_schedule=r.tc_schedule[i], tile_order=r.tile_order[i], ms=r.ms[i]) for i in range(r.ncand)]
+        return dict(chosen=r.chosen, candidates=cands)
+
+    def _refresh_info(self):
+        info = PlanInfo()
+        self._check(self._lib.gsp2_plan_query(self._h, C.byref(info), None, None))
+        self.info = info
+        self.options.tc_schedule = info.tc_schedule
+        self.options.tile_order = info.tile_order
 
     def status(self):
         """(status code, report dict) of the last density call; waits for it."""

@@ -1,0 +1,56 @@
+"""The schedule autotuner and the tile orders it chooses between: every candidate computes
+bitwise the same P (a tile's arithmetic does not depend on the CTA that runs it), and the
+autotuner keeps a candidate it timed."""
+
+import numpy as np
+import pytest
+
+from synth import make_workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1801_10016_gb300 import gsp2
+    return gsp2
+
+
+def run(g, s, **opt):
+    import torch
+    plan = g.GSP2(s.n, s.rowptr, s.colind, s.nocc, s.part, s.nparts, s.g_rowptr, s.g_colind, device="cuda:0",
+                  ckpt_every=0, **opt)
+    h = torch.from_numpy(s.vals).to("cuda:0")
+    p = plan.density(h)
+    st, _ = plan.status()
+    assert st == 0
+    return plan, h, p.cpu().numpy()
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "fp64e"])
+def test_tile_orders_give_bitwise_equal_p(g, prec):
+    s = make_workload("tb4k")  # more 128-tiles than SMs: the second order differs
+    _, _, p0 = run(g, s, precision=prec, tile_order=0)
+    _, _, p1 = run(g, s, precision=prec, tile_order=1)
+    assert np.array_equal(p0, p1)
+
+
+@pytest.mark.parametrize("prec", ["tf32x3", "fp64e", "fp64"])
+def test_autotune_keeps_a_timed_candidate(g, prec):
+    s = make_workload("tb4k")
+    plan, h, p0 = run(g, s, precision=prec)
+    rep = plan.autotune(h, trials=2)
+    cands = rep["candidates"]
+    assert len(cands) == {"tf32x3": 3, "fp64e": 2, "fp64": 1}[prec]
+    assert all(c["ms"] > 0 for c in cands)
+    best = cands[rep["chosen"]]
+    assert best["ms"] == min(c["ms"] for c in cands)
+    assert (plan.info.tc_schedule, plan.info.tile_order) == (best["tc_schedule"], best["tile_order"])
+    p1 = plan.density(h).cpu().numpy()
+    assert np.array_equal(p0, p1)
+    print(prec, rep)

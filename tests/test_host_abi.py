@@ -132,3 +132,13 @@ def test_workspace_size_covers_two_arenas(g):
     # padded leading dimensions: every part padded to the 128 multiple
     ld = -(-plan.part_sizes // 128) * 128
     assert plan.info.arena_elems == int(np.sum(ld.astype(np.int64) ** 2))
+
+
+def test_tile_order_option(g):
+    s = make_tb_system(16, 2, 3.0, seed=5)
+    assert g.default_options().tile_order == 0
+    for bad in (-1, 2):
+        with pytest.raises(g.GSP2Error):
+            _plan(g, s, tile_order=bad)
+    p = _plan(g, s, precision="tf32x3", tile_order=1, tc_schedule=1)
+    assert p.info.tile_order == 1 and p.info.tc_schedule == 1
