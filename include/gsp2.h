@@ -86,7 +86,10 @@ typedef struct {
   int32_t fp64_tail_steps; /* FP64 steps after the stopping test, -1..8 (default -1: 0 for the
                               FP64 precision, 2 for the low-precision modes); their first
                               branch follows the trace rule, each further one the opposite */
-  int32_t ckpt_every;      /* adjoint: keep every k-th iterate (default 8); 0 = no adjoint */
+  int32_t ckpt_every;      /* adjoint: keep every k-th iterate; 0 = no adjoint; -1 (default) =
+                              8 for FP64 and FP64_EMU, 0 for the low-precision modes, whose
+                              adjoint (k > 0, lp_tail_steps = 0) runs in FP32 on CUDA cores from
+                              FP32 checkpoints, the FP64 tail steps reversed in FP32 too */
   int32_t use_graph;       /* 1 (default): capture the whole step sequence in a CUDA graph */
   int32_t time_steps;      /* 1: record CUDA events around every purification-step launch
                               (read with gsp2_step_times); default 0 */

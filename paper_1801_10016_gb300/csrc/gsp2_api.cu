@@ -33,6 +33,7 @@ struct WsLayout {
   size_t oz_slice[2][OZ_SLICES];  // BF16 digit arenas, two buffers (read / written by a step)
   size_t oz_maps;                 // CUtensorMap[2][OZ_SLICES][nparts]
   size_t oz_acc;                  // int64[OZ_MAX_GRID][128 * 128] partial sums of the emulated step
+  std::vector<size_t> tailf;      // low-precision adjoint: FP32 iterates of the FP64 tail, recomputed
   size_t slots, rslots, state, alpha, traces, idem, step_arena;
   size_t arena0, arena1;       // ping-pong iterates
   std::vector<size_t> ckpt;    // X_0, X_k, X_2k, ... (adjoint checkpoints)
@@ -66,6 +67,7 @@ struct gsp2_plan {
   std::vector<Tile> tiles;                 // 64x64 upper tiles (CUDA-core steps)
   std::vector<Tile> tc_tiles;              // 128x128 upper tiles (tensor-core steps)
   std::vector<Tile> tc_order;              // tc_tiles in the order of opt.tile_order (uploaded)
+  std::vector<size_t> mf_of_step;          // low precision: FP32 arena of iterate i (checkpoints or ping-pong)
   std::vector<ColBlock> gblocks, sblocks;  // gather (to nt*64) and scatter (cores) columns
   std::vector<ColBlock> gblocks_ld;        // low-precision gather: every column up to ld
   int32_t nslots_tc = 0;
@@ -174,7 +176,7 @@ extern "C" void gsp2_default_options(gsp2_options* o) {
   o->trace_tol = 1e-2;
   o->precision = GSP2_PREC_FP64;
   o->fp64_tail_steps = -1;
-  o->ckpt_every = 8;
+  o->ckpt_every = -1;
   o->use_graph = 1;
   o->fp64_tail_emulated = 1;
 }
@@ -220,10 +222,27 @@ static void build_layout(gsp2_plan* h) {
   const size_t ab = (size_t)h->arena_elems * sizeof(double);
   const int prec = h->opt.precision;
   if (!fp64_like(prec)) {
-    // low precision: FP32 masters, operands, tensor maps, FP64 tail arenas; no adjoint
+    // low precision: FP32 masters, operands, tensor maps, FP64 tail arenas; for the FP32
+    // adjoint, FP32 checkpoints every k steps, k - 1 segment arenas, two Xbar arenas and the
+    // recomputed tail iterates
     const size_t af = (size_t)h->arena_elems * sizeof(float);
     L.mf[0] = take(af);
     L.mf[1] = take(af);
+    const int k = h->opt.ckpt_every;
+    L.ckpt.clear();
+    L.seg.clear();
+    L.tailf.clear();
+    L.xb0 = L.xb1 = 0;
+    if (k > 0) {
+      for (int c = 0; c <= h->opt.max_steps / k; ++c) L.ckpt.push_back(take(af));
+      for (int j = 1; j < k; ++j) L.seg.push_back(take(af));
+      L.xb0 = take(af);
+      L.xb1 = take(af);
+      for (int t = 0; t < h->opt.fp64_tail_steps; ++t) L.tailf.push_back(take(af));
+    }
+    h->mf_of_step.assign((size_t)h->opt.max_steps + 1 + MAX_TAIL, 0);
+    for (size_t i = 0; i < h->mf_of_step.size(); ++i)
+      h->mf_of_step[i] = (k > 0 && (int)i <= h->opt.max_steps && i % (size_t)k == 0) ? L.ckpt[i / k] : L.mf[i & 1];
     const int kind = prec_kind(prec), nprod = prec_nprod(prec);
     const size_t es = kind == 0 ? 2 : 4;
     L.op_hi[0] = L.op_hi[1] = L.op_lo[0] = L.op_lo[1] = 0;
@@ -244,11 +263,8 @@ static void build_layout(gsp2_plan* h) {
       L.oz_maps = take((size_t)2 * OZ_SLICES * h->parts.size() * 128);
       L.oz_acc = take((size_t)OZ_MAX_GRID * 128 * 128 * 8);
     }
-    L.ckpt.clear();
-    L.seg.clear();
     L.arena0 = L.d[0];
     L.arena1 = L.d[1];
-    L.xb0 = L.xb1 = 0;
     L.total = o;
     h->step_arena_off.assign((size_t)h->opt.max_steps + 1, L.d[0]);
     return;
@@ -311,7 +327,10 @@ extern "C" gsp2_status gsp2_create(int64_t n, const int64_t* rowptr, const int32
     if (o.tile_order < 0 || o.tile_order > 1) return bail(GSP2_E_ARG, "tile_order must be 0 or 1");
     if (o.lp_tail_steps > 0 && (fp64_like(o.precision) || o.precision == GSP2_PREC_FP32))
       return bail(GSP2_E_ARG, "lp_tail_steps needs a tensor-core precision");
-    if (o.ckpt_every < 0) return bail(GSP2_E_ARG, "ckpt_every must be >= 0");
+    if (o.ckpt_every < -1) return bail(GSP2_E_ARG, "ckpt_every must be >= -1");
+    if (h->opt.ckpt_every < 0) h->opt.ckpt_every = fp64_like(o.precision) ? 8 : 0;
+    if (!fp64_like(o.precision) && o.ckpt_every > 0 && o.lp_tail_steps > 0)
+      return bail(GSP2_E_ARG, "the low-precision adjoint (ckpt_every > 0) needs lp_tail_steps = 0");
     if ((g_rowptr == nullptr) != (g_colind == nullptr)) return bail(GSP2_E_ARG, "graph: give both arrays or neither");
     std::string m = check_csr(n, rowptr, colind, true, "H");
     if (!m.empty()) return bail(GSP2_E_ARG, m);
@@ -576,8 +595,8 @@ extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t byt
     CU(h, up(L.oz_maps, maps.data(), maps.size()));
   }
   if (!fp64_like(h->opt.precision)) {
-    std::vector<const float*> mt((size_t)h->opt.max_steps + 1 + MAX_TAIL);
-    for (size_t i = 0; i < mt.size(); ++i) mt[i] = (const float*)(h->ws + L.mf[i & 1]);
+    std::vector<const float*> mt(h->mf_of_step.size());
+    for (size_t i = 0; i < mt.size(); ++i) mt[i] = (const float*)(h->ws + h->mf_of_step[i]);
     CU(h, up(L.master_of_step, mt.data(), mt.size() * sizeof(float*)));
     const int kind = prec_kind(h->opt.precision), nprod = prec_nprod(h->opt.precision);
     if (kind >= 0) {
@@ -671,10 +690,12 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
     lp.idem_tol = std::max(h->opt.idem_tol, 16.0 * (double)h->n * prec_unit(prec));
     lp.stop_lag = 1;
     float* mf[2] = {(float*)(w + L.mf[0]), (float*)(w + L.mf[1])};
+    // FP32 iterate i of the loop: a checkpoint arena when the adjoint keeps it, else ping-pong
+    auto mfs = [&](int i) { return (float*)(w + h->mf_of_step[(size_t)i]); };
     void* oh[2] = {w + L.op_hi[0], w + L.op_hi[1]};
     void* ol[2] = {w + L.op_lo[0], w + L.op_lo[1]};
     CU(h, launch_gather_lp(kind, nprod, parts, (const ColBlock*)(w + L.gblocks_ld), (int)h->gblocks_ld.size(), Sall,
-                           rp, ci, hv, mf[0], kind >= 0 ? oh[0] : nullptr, nprod == 3 ? ol[0] : nullptr,
+                           rp, ci, hv, mfs(0), kind >= 0 ? oh[0] : nullptr, nprod == 3 ? ol[0] : nullptr,
                            (double*)slots, lp, s));
     const size_t np = h->parts.size();
     // tensor-core schedule: persistent (one CTA per SM, overlapped epilogue) or one CTA per tile
@@ -700,10 +721,12 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
       const int bi = (i - 1) & 1, bo = i & 1;
       if (!h->ev.empty()) CU(h, cudaEventRecordWithFlags(h->ev[2 * (i - 1)], s, cudaEventRecordExternal));
       if (kind < 0) {
-        CU(h, launch_square_fp32(parts, tiles, (int)h->tiles.size(), mf[bi], mf[bo], slots, h->nslots, lp, i, s));
+        CU(h, launch_square_fp32(parts, tiles, (int)h->tiles.size(), mfs(i - 1), mfs(i), slots, h->nslots, lp, i, s));
       } else {
         TcStepArgs a = tc_args;
         a.step = i;
+        a.master[bi] = mfs(i - 1);
+        a.master[bo] = mfs(i);
         CU(h, launch_square_tc(kind, nprod, a, (int)h->tc_tiles.size(), pgrid, s));
       }
       if (!h->ev.empty()) CU(h, cudaEventRecordWithFlags(h->ev[2 * (i - 1) + 1], s, cudaEventRecordExternal));
@@ -980,8 +1003,8 @@ static gsp2_status enqueue_backward(gsp2_plan* h, const double* pbar, double* hb
   const int nt = (int)h->tiles.size();
   StepCtl ctl{st, alpha, (double*)(w + L.traces), (double*)(w + L.idem), h->nocc, h->opt.idem_tol,
               h->opt.trace_tol, MODE_REPLAY, M, 1, 0};
-  CU(h, launch_adj_seed(parts, gbl, (int)h->gblocks.size(), Sall, (const int32_t*)(w + L.invperm),
-                        (const int64_t*)(w + L.pcolptr), pbar, xb0, s));
+  CU(h, launch_adj_seed<double>(parts, gbl, (int)h->gblocks.size(), Sall, (const int32_t*)(w + L.invperm),
+                                (const int64_t*)(w + L.pcolptr), pbar, xb0, s));
   for (int c0 = (M / k) * k; c0 >= 0; c0 -= k) {
     const double* ck = (const double*)(w + L.ckpt[c0 / k]);
     for (int j = 1; j < k && c0 + j < M; ++j) {
@@ -991,19 +1014,62 @@ static gsp2_status enqueue_backward(gsp2_plan* h, const double* pbar, double* hb
     }
     for (int i = std::min(c0 + k, M); i >= c0 + 1; --i) {
       const double* X = (i - 1 == c0) ? ck : (const double*)(w + L.seg[i - 1 - c0 - 1]);
-      CU(h, launch_adj_step_fp64(parts, tiles, nt, X, xb0, xb1, alpha, st, i, s));
+      CU(h, launch_adj_step<double>(parts, tiles, nt, X, xb0, xb1, alpha, st, i, 0, s));
     }
   }
-  CU(h, launch_adj_hbar(h->n, (const int64_t*)(w + L.rowptr), (const int32_t*)(w + L.colind),
-                        (const int64_t*)(w + L.memptr), (const int32_t*)(w + L.mempart),
-                        (const int32_t*)(w + L.memloc), parts, Sall, xb0, xb1, hbar, st, s));
+  CU(h, launch_adj_hbar<double>(h->n, (const int64_t*)(w + L.rowptr), (const int32_t*)(w + L.colind),
+                                (const int64_t*)(w + L.memptr), (const int32_t*)(w + L.mempart),
+                                (const int32_t*)(w + L.memloc), parts, Sall, xb0, xb1, hbar, st, s));
+  return GSP2_OK;
+}
+
+// Adjoint of a low-precision plan, in FP32 on the CUDA cores: the T FP64 tail steps came
+// last, so they are reversed first, on FP32 iterates rebuilt from the loop's last iterate
+// X_L (L = n - T is known only on the device: these launches count back from n); then the
+// loop's steps, from the FP32 checkpoints the forward kept every k steps.
+static gsp2_status enqueue_backward_lp(gsp2_plan* h, const double* pbar, double* hbar, cudaStream_t s) {
+  const WsLayout& L = h->L;
+  char* w = h->ws;
+  auto parts = (const PartDesc*)(w + L.parts);
+  auto Sall = (const int32_t*)(w + L.S);
+  auto tiles = (const Tile*)(w + L.tiles);
+  auto gbl = (const ColBlock*)(w + L.gblocks);
+  auto st = (DevState*)(w + L.state);
+  auto alpha = (int8_t*)(w + L.alpha);
+  float* xb0 = (float*)(w + L.xb0);
+  float* xb1 = (float*)(w + L.xb1);
+  const int k = h->opt.ckpt_every, M = h->opt.max_steps, T = h->opt.fp64_tail_steps;
+  const int nt = (int)h->tiles.size();
+  StepCtl ctl{st, alpha, (double*)(w + L.traces), (double*)(w + L.idem), h->nocc, h->opt.idem_tol,
+              h->opt.trace_tol, MODE_REPLAY, M, 1, T};
+  auto tf = [&](int t) { return (float*)(w + L.tailf[(size_t)t]); };
+  CU(h, launch_adj_seed<float>(parts, gbl, (int)h->gblocks.size(), Sall, (const int32_t*)(w + L.invperm),
+                               (const int64_t*)(w + L.pcolptr), pbar, xb0, s));
+  if (T > 0) {
+    CU(h, launch_copy_iterate((const float* const*)(w + L.master_of_step), tf(0), h->arena_elems, st, T, s));
+    for (int t = 1; t < T; ++t) CU(h, launch_recompute_fp32(parts, tiles, nt, tf(t - 1), tf(t), ctl, t - T, s));
+    for (int t = T; t >= 1; --t) CU(h, launch_adj_step<float>(parts, tiles, nt, tf(t - 1), xb0, xb1, alpha, st, t - T, T, s));
+  }
+  for (int c0 = (M / k) * k; c0 >= 0; c0 -= k) {
+    const float* ck = (const float*)(w + L.ckpt[c0 / k]);
+    for (int j = 1; j < k && c0 + j < M; ++j) {
+      const float* xin = (j == 1) ? ck : (const float*)(w + L.seg[j - 2]);
+      CU(h, launch_recompute_fp32(parts, tiles, nt, xin, (float*)(w + L.seg[j - 1]), ctl, c0 + j, s));
+    }
+    for (int i = std::min(c0 + k, M); i >= c0 + 1; --i) {
+      const float* X = (i - 1 == c0) ? ck : (const float*)(w + L.seg[i - 1 - c0 - 1]);
+      CU(h, launch_adj_step<float>(parts, tiles, nt, X, xb0, xb1, alpha, st, i, T, s));
+    }
+  }
+  CU(h, launch_adj_hbar<float>(h->n, (const int64_t*)(w + L.rowptr), (const int32_t*)(w + L.colind),
+                               (const int64_t*)(w + L.memptr), (const int32_t*)(w + L.mempart),
+                               (const int32_t*)(w + L.memloc), parts, Sall, xb0, xb1, hbar, st, s));
   return GSP2_OK;
 }
 
 extern "C" gsp2_status gsp2_backward(gsp2_handle h, const double* d_pbar, double* d_hbar, void* stream) {
   if (!usable(h)) return fail(h, GSP2_E_ARG, "invalid handle");
-  if (h->opt.ckpt_every <= 0 || !fp64_like(h->opt.precision))
-    return fail(h, GSP2_E_STATE, "the adjoint needs an FP64 plan built with ckpt_every > 0");
+  if (h->opt.ckpt_every <= 0) return fail(h, GSP2_E_STATE, "the adjoint needs a plan built with ckpt_every > 0");
   if (!h->ws || !h->have_forward) return fail(h, GSP2_E_STATE, "gsp2_backward needs a completed density call");
   if (!d_pbar || !d_hbar) return fail(h, GSP2_E_ARG, "NULL Pbar or Hbar buffer");
   int dev = 0;
@@ -1016,7 +1082,8 @@ extern "C" gsp2_status gsp2_backward(gsp2_handle h, const double* d_pbar, double
       h->bexec = nullptr;
       cudaGraph_t g = nullptr;
       CU(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
-      gsp2_status st = enqueue_backward(h, d_pbar, d_hbar, h->cap_stream);
+      gsp2_status st = fp64_like(h->opt.precision) ? enqueue_backward(h, d_pbar, d_hbar, h->cap_stream)
+                                                   : enqueue_backward_lp(h, d_pbar, d_hbar, h->cap_stream);
       cudaError_t e = cudaStreamEndCapture(h->cap_stream, &g);
       if (st != GSP2_OK) {
         if (g) cudaGraphDestroy(g);
@@ -1035,7 +1102,7 @@ extern "C" gsp2_status gsp2_backward(gsp2_handle h, const double* d_pbar, double
     CU(h, cudaGraphLaunch(h->bexec, s));
     return GSP2_OK;
   }
-  return enqueue_backward(h, d_pbar, d_hbar, s);
+  return fp64_like(h->opt.precision) ? enqueue_backward(h, d_pbar, d_hbar, s) : enqueue_backward_lp(h, d_pbar, d_hbar, s);
 }
 
 extern "C" void gsp2_destroy(gsp2_handle h) {

@@ -18,6 +18,8 @@ cudaError_t launch_square_fp64(const PartDesc* parts, const Tile* tiles, int nti
 cudaError_t launch_residual_fp64(const PartDesc* parts, const Tile* tiles, int ntiles, const double* x,
                                  const double* const* x_of_step, double* rslots, int64_t n, const StepCtl& ctl,
                                  cudaStream_t s);
+cudaError_t launch_recompute_fp32(const PartDesc* parts, const Tile* tiles, int ntiles, const float* xin,
+                                  float* xout, const StepCtl& ctl, int step, cudaStream_t s);
 cudaError_t launch_square_fp32(const PartDesc* parts, const Tile* tiles, int ntiles, const float* xin, float* xout,
                                double2* slots, int nslots, const StepCtl& ctl, int step, cudaStream_t s);
 cudaError_t launch_scatter(const PartDesc* parts, const ColBlock* blocks, int nblocks, const int32_t* Sall,
@@ -31,6 +33,8 @@ cudaError_t launch_gather_lp(int kind, int nprod, const PartDesc* parts, const C
                              const int32_t* Sall, const int64_t* rowptr, const int32_t* colind, const double* vals,
                              float* master, void* op_hi, void* op_lo, double* slots, const StepCtl& ctl,
                              cudaStream_t s);
+cudaError_t launch_copy_iterate(const float* const* master_of_step, float* out, int64_t n, const DevState* st,
+                                int back, cudaStream_t s);
 cudaError_t launch_convert(const float* const* master_of_step, double* out, int64_t n, const DevState* st,
                            cudaStream_t s);
 // FP64 products from BF16 digits (k_oz.cu)
@@ -41,15 +45,17 @@ int encode_part_maps(void* enc_fn, void* out_maps, const PartDesc* parts, int np
                      int box_bytes = 128);
 
 // adjoint (k_adjoint.cu)
+template <typename T>
 cudaError_t launch_adj_seed(const PartDesc* parts, const ColBlock* blocks, int nblocks, const int32_t* Sall,
-                            const int32_t* invperm, const int64_t* pcolptr, const double* pbar, double* xbar,
+                            const int32_t* invperm, const int64_t* pcolptr, const double* pbar, T* xbar,
                             cudaStream_t s);
-cudaError_t launch_adj_step_fp64(const PartDesc* parts, const Tile* tiles, int ntiles, const double* X,
-                                 double* xb0, double* xb1, const int8_t* alpha, const DevState* st, int step,
-                                 cudaStream_t s);
+template <typename T>
+cudaError_t launch_adj_step(const PartDesc* parts, const Tile* tiles, int ntiles, const T* X, T* xb0, T* xb1,
+                            const int8_t* alpha, const DevState* st, int step, int tail, cudaStream_t s);
+template <typename T>
 cudaError_t launch_adj_hbar(int64_t n, const int64_t* rowptr, const int32_t* colind, const int64_t* memptr,
                             const int32_t* mempart, const int32_t* memloc, const PartDesc* parts,
-                            const int32_t* Sall, const double* xb0, const double* xb1, double* hbar,
-                            const DevState* st, cudaStream_t s);
+                            const int32_t* Sall, const T* xb0, const T* xb1, double* hbar, const DevState* st,
+                            cudaStream_t s);
 
 }  // namespace gsp2

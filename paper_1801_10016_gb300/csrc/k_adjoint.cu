@@ -1,5 +1,5 @@
-// Adjoint of the G-SP2 density matrix, FP64: seed, reverse purification steps and the
-// scatter-add onto the pattern of H.
+// Adjoint of the G-SP2 density matrix (FP64, or FP32 for the low-precision plans): seed,
+// reverse purification steps and the scatter-add onto the pattern of H.
 //
 // With L = sum Pbar .* P and the branch sequence alpha_1..alpha_n fixed:
 //   seed:   Xbar_n = sym(M_k), M_k[:, j] = Pbar[S_k, g_j] for core j, 0 for halo columns
@@ -15,12 +15,13 @@
 namespace gsp2 {
 
 // Seed: one warp per local column b (including the zero padding up to nt*TILE).
+template <typename T>
 __global__ void __launch_bounds__(256) adj_seed_kernel(const PartDesc* __restrict__ parts,
                                                        const ColBlock* __restrict__ blocks,
                                                        const int32_t* __restrict__ Sall,
                                                        const int32_t* __restrict__ invperm,
                                                        const int64_t* __restrict__ pcolptr,
-                                                       const double* __restrict__ pbar, double* __restrict__ xbar) {
+                                                       const double* __restrict__ pbar, T* __restrict__ xbar) {
   const ColBlock bl = blocks[blockIdx.x];
   const PartDesc p = parts[bl.part];
   const int lane = threadIdx.x & 31;
@@ -28,7 +29,7 @@ __global__ void __launch_bounds__(256) adj_seed_kernel(const PartDesc* __restric
   if (b >= p.nt * SQ_TILE) return;
   const int32_t* S = Sall + p.soff;
   const int32_t* ip = invperm + p.soff;
-  double* col = xbar + p.off + (int64_t)b * p.ld;
+  T* col = xbar + p.off + (int64_t)b * p.ld;
   const bool bin = b < p.s;
   const int64_t colb = (bin && b < p.c) ? pcolptr[S[b]] : -1;  // column g_b of P if b is a core
   const int ipb = bin ? ip[b] : 0;
@@ -39,35 +40,56 @@ __global__ void __launch_bounds__(256) adj_seed_kernel(const PartDesc* __restric
       const double mba = (a < p.c) ? pbar[pcolptr[S[a]] + ipb] : 0.0;       // M(b, a)
       v = 0.5 * (mab + mba);
     }
-    col[a] = v;
+    col[a] = (T)v;
   }
 }
 
-// One reverse step for every part, FP64.  Work item = one upper tile (ti <= tj);
+// One reverse step for every part.  Work item = one upper tile (ti <= tj);
 // Z_IJ = sum_k Xbar[I,k] X[k,J] + X[I,k] Xbar[k,J] with all four slices streamed from
 // columns k of the symmetric Xbar and X.  Result mirrored to (J, I).
-// The Xbar buffers alternate with (n - step) so that skipped steps (step > n) keep
-// the parity: input xb[(n - step) & 1], output xb[(n - step + 1) & 1].
-constexpr int ABK = 8;
+// The Xbar buffers alternate with (n - step) so that skipped steps keep the parity: input
+// xb[(n - step) & 1], output xb[(n - step + 1) & 1], n the steps applied by the forward.
+// `step` > 0 is a step of the loop, done if step <= n - tail (the FP64 tail steps of a
+// low-precision plan come last and are reversed first); `step` <= 0 names step n + step
+// (the tail steps, whose numbers are only known on the device).
+// Four consecutive elements (16-byte aligned for FP32, 32 for FP64) in vector stores.
+__device__ __forceinline__ void store4(double* p, double a, double b, double c, double d) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(a, b);
+  reinterpret_cast<double2*>(p)[1] = make_double2(c, d);
+}
+__device__ __forceinline__ void store4(float* p, float a, float b, float c, float d) {
+  *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+}
 
-__global__ void __launch_bounds__(256, 2) adj_step_fp64_kernel(const PartDesc* __restrict__ parts,
-                                                               const Tile* __restrict__ tiles,
-                                                               const double* __restrict__ Xall,
-                                                               double* __restrict__ xb0, double* __restrict__ xb1,
-                                                               const int8_t* __restrict__ alpha,
-                                                               const DevState* st, int step) {
+template <typename T>
+struct AdjBK {
+  static constexpr int v = 64 / (int)sizeof(T);  // K slice: 8 (FP64) or 16 (FP32) = 16 B per thread
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256, 2) adj_step_kernel(const PartDesc* __restrict__ parts,
+                                                          const Tile* __restrict__ tiles, const T* __restrict__ Xall,
+                                                          T* __restrict__ xb0, T* __restrict__ xb1,
+                                                          const int8_t* __restrict__ alpha, const DevState* st,
+                                                          int step, int tail) {
+  constexpr int ABK = AdjBK<T>::v;
   const int n = *(volatile const int32_t*)&st->steps;
-  if (step > n) return;
-  const double* XBin = ((n - step) & 1) ? xb1 : xb0;
-  double* XBout = ((n - step) & 1) ? xb0 : xb1;
-  __shared__ __align__(16) double S1[2][ABK][SQ_TILE];  // Xbar rows I
-  __shared__ __align__(16) double S2[2][ABK][SQ_TILE];  // X    rows J
-  __shared__ __align__(16) double S3[2][ABK][SQ_TILE];  // X    rows I
-  __shared__ __align__(16) double S4[2][ABK][SQ_TILE];  // Xbar rows J
+  if (step <= 0) {
+    step += n;
+    if (step < 1) return;
+  } else if (step > n - tail) {
+    return;
+  }
+  const T* XBin = ((n - step) & 1) ? xb1 : xb0;
+  T* XBout = ((n - step) & 1) ? xb0 : xb1;
+  __shared__ __align__(16) T S1[2][ABK][SQ_TILE];  // Xbar rows I
+  __shared__ __align__(16) T S2[2][ABK][SQ_TILE];  // X    rows J
+  __shared__ __align__(16) T S3[2][ABK][SQ_TILE];  // X    rows I
+  __shared__ __align__(16) T S4[2][ABK][SQ_TILE];  // Xbar rows J
   const Tile t = tiles[blockIdx.x];
   const PartDesc p = parts[t.part];
-  const double* X = Xall + p.off;
-  const double* B = XBin + p.off;
+  const T* X = Xall + p.off;
+  const T* B = XBin + p.off;
   const int64_t ld = p.ld;
   const int r0 = t.ti * SQ_TILE, c0 = t.tj * SQ_TILE;
   const int kend = (p.s + ABK - 1) / ABK * ABK;
@@ -75,8 +97,9 @@ __global__ void __launch_bounds__(256, 2) adj_step_fp64_kernel(const PartDesc* _
   const int tx = tid & 15, ty = tid >> 4;
 
   auto load_slice = [&](int buf, int k0) {
-    // 8 x 64 doubles per operand = 256 16-byte chunks: one per thread per operand
-    const int kr = tid >> 5, c2 = (tid & 31) * 2;
+    // ABK x 64 elements per operand = 256 16-byte chunks: one per thread per operand
+    constexpr int EPC = 16 / (int)sizeof(T);
+    const int kr = tid / (SQ_TILE / EPC), c2 = (tid % (SQ_TILE / EPC)) * EPC;
     const int64_t co = (int64_t)(k0 + kr) * ld;
     cp_async16(&S1[buf][kr][c2], B + co + r0 + c2);
     cp_async16(&S2[buf][kr][c2], X + co + c0 + c2);
@@ -85,11 +108,11 @@ __global__ void __launch_bounds__(256, 2) adj_step_fp64_kernel(const PartDesc* _
     cp_async_commit();
   };
 
-  double acc[4][4];
+  T acc[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
 
   const int nk = kend / ABK;
   load_slice(0, 0);
@@ -104,7 +127,7 @@ __global__ void __launch_bounds__(256, 2) adj_step_fp64_kernel(const PartDesc* _
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < ABK; ++kk) {
-      double a1[4], b1[4], a2[4], b2[4];
+      T a1[4], b1[4], a2[4], b2[4];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         a1[q] = S1[buf][kk][tx * 4 + q];
@@ -121,25 +144,23 @@ __global__ void __launch_bounds__(256, 2) adj_step_fp64_kernel(const PartDesc* _
   }
 
   const int8_t al = alpha[step];
-  double* O = XBout + p.off;
+  T* O = XBout + p.off;
   const int rb = r0 + tx * 4, cb = c0 + ty * 4;
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const int c = cb + j;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const double z = acc[i][j];
-      acc[i][j] = (al > 0) ? (2.0 * B[(int64_t)c * ld + rb + i] - z) : z;
+      const T z = acc[i][j];
+      acc[i][j] = (al > 0) ? (T(2) * B[(int64_t)c * ld + rb + i] - z) : z;
     }
-    *reinterpret_cast<double2*>(O + (int64_t)c * ld + rb) = make_double2(acc[0][j], acc[1][j]);
-    *reinterpret_cast<double2*>(O + (int64_t)c * ld + rb + 2) = make_double2(acc[2][j], acc[3][j]);
+    store4(O + (int64_t)c * ld + rb, acc[0][j], acc[1][j], acc[2][j], acc[3][j]);
   }
   if (t.ti != t.tj) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int r = rb + i;
-      *reinterpret_cast<double2*>(O + (int64_t)r * ld + cb) = make_double2(acc[i][0], acc[i][1]);
-      *reinterpret_cast<double2*>(O + (int64_t)r * ld + cb + 2) = make_double2(acc[i][2], acc[i][3]);
+      store4(O + (int64_t)r * ld + cb, acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
     }
   }
 }
@@ -147,6 +168,7 @@ __global__ void __launch_bounds__(256, 2) adj_step_fp64_kernel(const PartDesc* _
 // dL/dH on the CSR pattern: for every stored (r, col), the sum over the parts k that
 // hold r (membership list of r) and col of -Xbar0_k[col, r] / (eps_max - eps_min), in
 // the fixed membership order.  One warp per row, lanes over the row's entries.
+template <typename T>
 __global__ void __launch_bounds__(256) adj_hbar_kernel(int64_t n, const int64_t* __restrict__ rowptr,
                                                        const int32_t* __restrict__ colind,
                                                        const int64_t* __restrict__ memptr,
@@ -154,11 +176,10 @@ __global__ void __launch_bounds__(256) adj_hbar_kernel(int64_t n, const int64_t*
                                                        const int32_t* __restrict__ memloc,
                                                        const PartDesc* __restrict__ parts,
                                                        const int32_t* __restrict__ Sall,
-                                                       const double* __restrict__ xb0,
-                                                       const double* __restrict__ xb1,
+                                                       const T* __restrict__ xb0, const T* __restrict__ xb1,
                                                        double* __restrict__ hbar, const DevState* st) {
   const int nsteps = st->steps;
-  const double* XB = (nsteps & 1) ? xb1 : xb0;
+  const T* XB = (nsteps & 1) ? xb1 : xb0;
   const double scale = -1.0 / (st->eps_max - st->eps_min);
   const int lane = threadIdx.x & 31;
   const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -171,33 +192,46 @@ __global__ void __launch_bounds__(256) adj_hbar_kernel(int64_t n, const int64_t*
       for (int64_t m = m0; m < m1; ++m) {
         const PartDesc p = parts[mempart[m]];
         const int lc = find_local(Sall + p.soff, p.c, p.s, col);
-        if (lc >= 0) sum += XB[p.off + (int64_t)memloc[m] * p.ld + lc];
+        if (lc >= 0) sum += (double)XB[p.off + (int64_t)memloc[m] * p.ld + lc];
       }
       hbar[q] = scale * sum;
     }
   }
 }
 
+template <typename T>
 cudaError_t launch_adj_seed(const PartDesc* parts, const ColBlock* blocks, int nblocks, const int32_t* Sall,
-                            const int32_t* invperm, const int64_t* pcolptr, const double* pbar, double* xbar,
+                            const int32_t* invperm, const int64_t* pcolptr, const double* pbar, T* xbar,
                             cudaStream_t s) {
-  adj_seed_kernel<<<nblocks, 32 * COLS_PER_BLOCK, 0, s>>>(parts, blocks, Sall, invperm, pcolptr, pbar, xbar);
+  adj_seed_kernel<T><<<nblocks, 32 * COLS_PER_BLOCK, 0, s>>>(parts, blocks, Sall, invperm, pcolptr, pbar, xbar);
   return cudaGetLastError();
 }
 
-cudaError_t launch_adj_step_fp64(const PartDesc* parts, const Tile* tiles, int ntiles, const double* X,
-                                 double* xb0, double* xb1, const int8_t* alpha, const DevState* st, int step,
-                                 cudaStream_t s) {
-  adj_step_fp64_kernel<<<ntiles, 256, 0, s>>>(parts, tiles, X, xb0, xb1, alpha, st, step);
+template <typename T>
+cudaError_t launch_adj_step(const PartDesc* parts, const Tile* tiles, int ntiles, const T* X, T* xb0, T* xb1,
+                            const int8_t* alpha, const DevState* st, int step, int tail, cudaStream_t s) {
+  adj_step_kernel<T><<<ntiles, 256, 0, s>>>(parts, tiles, X, xb0, xb1, alpha, st, step, tail);
   return cudaGetLastError();
 }
 
+template <typename T>
 cudaError_t launch_adj_hbar(int64_t n, const int64_t* rowptr, const int32_t* colind, const int64_t* memptr,
                             const int32_t* mempart, const int32_t* memloc, const PartDesc* parts,
-                            const int32_t* Sall, const double* xb0, const double* xb1, double* hbar,
-                            const DevState* st, cudaStream_t s) {
-  adj_hbar_kernel<<<608, 256, 0, s>>>(n, rowptr, colind, memptr, mempart, memloc, parts, Sall, xb0, xb1, hbar, st);
+                            const int32_t* Sall, const T* xb0, const T* xb1, double* hbar, const DevState* st,
+                            cudaStream_t s) {
+  adj_hbar_kernel<T><<<608, 256, 0, s>>>(n, rowptr, colind, memptr, mempart, memloc, parts, Sall, xb0, xb1, hbar, st);
   return cudaGetLastError();
 }
+
+#define GSP2_ADJ_INSTANTIATE(T)                                                                                     \
+  template cudaError_t launch_adj_seed<T>(const PartDesc*, const ColBlock*, int, const int32_t*, const int32_t*,   \
+                                          const int64_t*, const double*, T*, cudaStream_t);                        \
+  template cudaError_t launch_adj_step<T>(const PartDesc*, const Tile*, int, const T*, T*, T*, const int8_t*,      \
+                                          const DevState*, int, int, cudaStream_t);                                \
+  template cudaError_t launch_adj_hbar<T>(int64_t, const int64_t*, const int32_t*, const int64_t*, const int32_t*, \
+                                          const int32_t*, const PartDesc*, const int32_t*, const T*, const T*,     \
+                                          double*, const DevState*, cudaStream_t);
+GSP2_ADJ_INSTANTIATE(double)
+GSP2_ADJ_INSTANTIATE(float)
 
 }  // namespace gsp2

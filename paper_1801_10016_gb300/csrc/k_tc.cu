@@ -674,6 +674,22 @@ cudaError_t launch_convert(const float* const* master_of_step, double* out, int6
   return cudaGetLastError();
 }
 
+// Adjoint of a low-precision run: copy the FP32 iterate n - back (n = steps applied,
+// found on the device) out of the per-step table, the start of the tail's recomputation.
+__global__ void copy_iterate_kernel(const float* const* __restrict__ master_of_step, float* __restrict__ out,
+                                    int64_t n, const DevState* st, int back) {
+  const int i = st->steps - back;
+  const float* in = master_of_step[i < 0 ? 0 : i];
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = in[e];
+}
+
+cudaError_t launch_copy_iterate(const float* const* master_of_step, float* out, int64_t n, const DevState* st,
+                                int back, cudaStream_t s) {
+  copy_iterate_kernel<<<152 * 8, 256, 0, s>>>(master_of_step, out, n, st, back);
+  return cudaGetLastError();
+}
+
 // Encode one tensor map per part over an operand arena: 2-D, inner dimension = rows
 // of a column (contiguous), outer = columns, box = 128 bytes x 128 columns, 128-byte
 // swizzle.  `enc` is cuTensorMapEncodeTiled obtained from the driver.

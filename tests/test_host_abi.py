@@ -37,7 +37,7 @@ def _plan(g, s, **kw):
 
 def test_default_options(g):
     o = g.default_options()
-    assert o.max_steps == 45 and o.precision == 0 and o.use_graph == 1 and o.ckpt_every == 8
+    assert o.max_steps == 45 and o.precision == 0 and o.use_graph == 1 and o.ckpt_every == -1
     assert o.idem_tol == 1e-3 and o.fp64_tail_steps == -1 and o.lp_tail_steps == 0 and o.tc_schedule == 0
     # "-1" resolves to no tail for FP64 (the paper's method) and two FP64 steps otherwise
     s = make_workload("tb512")
@@ -120,7 +120,7 @@ def test_create_rejects_bad_input(g, bad):
 
 def test_options_rejected(g):
     s = make_tb_system(16, 2, 3.0, seed=5)
-    for kw in (dict(max_steps=0), dict(max_steps=5000), dict(idem_tol=-1.0), dict(ckpt_every=-1)):
+    for kw in (dict(max_steps=0), dict(max_steps=5000), dict(idem_tol=-1.0), dict(ckpt_every=-2)):
         with pytest.raises(g.GSP2Error):
             _plan(g, s, **kw)
 
@@ -142,3 +142,18 @@ def test_tile_order_option(g):
             _plan(g, s, tile_order=bad)
     p = _plan(g, s, precision="tf32x3", tile_order=1, tc_schedule=1)
     assert p.info.tile_order == 1 and p.info.tc_schedule == 1
+
+
+def test_low_precision_adjoint_layout(g):
+    """ckpt_every = -1 keeps FP64 iterates every 8 steps for FP64 plans and none for the
+    low-precision ones; an explicit k adds FP32 checkpoints, and excludes low-precision
+    tail steps."""
+    s = make_workload("tb512")
+    base = _plan(g, s, precision="tf32x3").workspace_bytes
+    k4 = _plan(g, s, precision="tf32x3", ckpt_every=4).workspace_bytes
+    af = 4 * _plan(g, s).info.arena_elems
+    # 45 // 4 + 1 checkpoints, 3 segments, 2 Xbar, 2 tail iterates, FP32 each
+    assert k4 - base >= (45 // 4 + 1 + 3 + 2 + 2) * af
+    assert _plan(g, s).workspace_bytes > _plan(g, s, ckpt_every=0).workspace_bytes
+    with pytest.raises(g.GSP2Error):
+        _plan(g, s, precision="tf32x3", ckpt_every=4, lp_tail_steps=2, fp64_tail_steps=0)
