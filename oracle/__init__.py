@@ -22,6 +22,8 @@ from .gsp2 import (  # noqa: F401
     eig_projector,
     sp2_map_on_spectrum,
     gsp2_adjoint,
+    part_adjoint,
+    seed_on_pattern,
     dk_adjoint,
     fd_directional,
 )

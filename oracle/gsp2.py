@@ -170,13 +170,14 @@ def sp2_dense(H, nocc, max_steps=45, bounds=None, alphas=None, keep_iterates=Fal
 # Section 2.2: core and halo vertices, Eq. 5
 # --------------------------------------------------------------------------------------
 
-def core_halo(g_rowptr, g_colind, part, nparts):
+def core_halo(g_rowptr, g_colind, part, nparts, which=None):
     """Per part k: (core_k, halo_k).  core_k = vertices with part == k, ascending;
     halo_k = vertices outside part k adjacent in G_tau to some core vertex, ascending
-    (Section 2.2).  The subproblem's vertex list is S_k = core_k followed by halo_k."""
+    (Section 2.2).  The subproblem's vertex list is S_k = core_k followed by halo_k.
+    `which` lists the parts to build (default all, in order)."""
     part = np.asarray(part)
     out = []
-    for k in range(nparts):
+    for k in (range(nparts) if which is None else which):
         core = np.nonzero(part == k)[0]
         if core.size == 0:
             raise ValueError(f"part {k} is empty")
@@ -340,29 +341,47 @@ def _hbar_on_pattern(n, rowptr, colind, parts_grad):
     return G[rows, np.asarray(colind)]
 
 
+def seed_on_pattern(S, c, pbar, colptr, rowind):
+    """The seed of _seed from dL/dP given on P's core-column pattern (values `pbar`,
+    column g holding rows rowind[colptr[g]:colptr[g+1]]) instead of a dense N x N array."""
+    s = len(S)
+    loc = {int(g): t for t, g in enumerate(S)}
+    M = np.zeros((s, s))
+    for j in range(c):
+        g = int(S[j])
+        rows = rowind[colptr[g]:colptr[g + 1]]
+        M[[loc[int(r)] for r in rows], j] = pbar[colptr[g]:colptr[g + 1]]
+    return 0.5 * (M + M.T)
+
+
+def part_adjoint(Hk, alphas, bounds, Xbar):
+    """One part's reverse mode through the recorded alpha sequence (parts are independent
+    once alpha is fixed), from the symmetric seed Xbar = dL/dX_n.  For the step X_i = X^2
+    the adjoint is Xbar <- Xbar X + X Xbar; for X_i = 2X - X^2 it is
+    Xbar <- 2 Xbar - Xbar X - X Xbar, with X the iterate the step acted on.  Finally
+    dX0/dH = -1/(eps_max - eps_min) (Eq. 1).  Returns dL/dH[S_k, S_k]."""
+    eps_min, eps_max = bounds
+    X = initial_guess(Hk, eps_min, eps_max)
+    its = [X]
+    for a in alphas:
+        X = sp2_step(X, a)
+        its.append(X)
+    Xb = Xbar
+    for i in range(len(alphas), 0, -1):
+        Xp = its[i - 1]
+        if alphas[i - 1] == -1:
+            Xb = Xb @ Xp + Xp @ Xb
+        else:
+            Xb = 2.0 * Xb - Xb @ Xp - Xp @ Xb
+    return -Xb / (eps_max - eps_min)
+
+
 def gsp2_adjoint(n, rowptr, colind, vals, res: GSP2Result, Pbar_dense):
-    """Reverse mode through the recorded alpha sequence, part by part (parts are
-    independent once alpha is fixed).  For the step X_i = X^2 the adjoint is
-    Xbar <- Xbar X + X Xbar; for X_i = 2X - X^2 it is Xbar <- 2 Xbar - Xbar X - X Xbar,
-    with X the iterate the step acted on.  Finally dX0/dH = -1/(eps_max - eps_min)
-    (Eq. 1).  Returns dL/dH on H's CSR pattern (a symmetric array of values)."""
-    eps_min, eps_max = res.bounds
+    """Reverse mode through the recorded alpha sequence (part_adjoint for every part),
+    summed onto H's CSR pattern (a symmetric array of values)."""
     Hs = _h_sparse(n, rowptr, colind, vals)
-    grads = []
-    for S, c in zip(res.S, res.ncore):
-        X = initial_guess(Hs[S][:, S].toarray(), eps_min, eps_max)
-        its = [X]
-        for a in res.alphas:
-            X = sp2_step(X, a)
-            its.append(X)
-        Xb = _seed(Pbar_dense, S, c)
-        for i in range(len(res.alphas), 0, -1):
-            Xp = its[i - 1]
-            if res.alphas[i - 1] == -1:
-                Xb = Xb @ Xp + Xp @ Xb
-            else:
-                Xb = 2.0 * Xb - Xb @ Xp - Xp @ Xb
-        grads.append((S, -Xb / (eps_max - eps_min)))
+    grads = [(S, part_adjoint(Hs[S][:, S].toarray(), res.alphas, res.bounds, _seed(Pbar_dense, S, c)))
+             for S, c in zip(res.S, res.ncore)]
     return _hbar_on_pattern(n, rowptr, colind, grads)
 
 

@@ -314,3 +314,32 @@ def test_tail_steps_alternate_and_purify(tb512, tb512_dense):
     # a replayed sequence runs exactly its length (the tail is part of it)
     g3 = oracle.gsp2(*args, alphas=g2.alphas, tail_steps=5)
     assert g3.alphas == g2.alphas and np.array_equal(g3.dense_p(), g2.dense_p())
+
+
+def test_seed_on_pattern_and_core_halo_subset_agree_with_the_dense_forms():
+    """The pattern-based seed equals the dense-Pbar seed, and core_halo for a subset of
+    parts equals those entries of the full list (the forms the large-size checks use)."""
+    from oracle.gsp2 import _seed
+    s = make_workload("tb512")
+    res = oracle.gsp2(s.n, s.rowptr, s.colind, s.vals, s.nocc, s.part, s.nparts, s.g_rowptr, s.g_colind)
+    # pattern of P from the oracle's own lists (sorted rows S_part(g) per core column g)
+    colptr = np.zeros(s.n + 1, np.int64)
+    rows_of = {}
+    for S, c in zip(res.S, res.ncore):
+        for j in range(c):
+            rows_of[int(S[j])] = np.sort(S)
+    for g in range(s.n):
+        colptr[g + 1] = colptr[g] + len(rows_of[g])
+    rowind = np.concatenate([rows_of[g] for g in range(s.n)])
+    rng = np.random.default_rng(3)
+    pbar = rng.standard_normal(int(colptr[-1]))
+    dense = np.zeros((s.n, s.n))
+    cols = np.repeat(np.arange(s.n), np.diff(colptr))
+    dense[rowind, cols] = pbar
+    for S, c in zip(res.S, res.ncore):
+        np.testing.assert_array_equal(oracle.seed_on_pattern(S, c, pbar, colptr, rowind), _seed(dense, S, c))
+    full = oracle.core_halo(s.g_rowptr, s.g_colind, s.part, s.nparts)
+    sub = oracle.core_halo(s.g_rowptr, s.g_colind, s.part, s.nparts, which=[5, 2])
+    for k, (c, h) in zip([5, 2], sub):
+        np.testing.assert_array_equal(c, full[k][0])
+        np.testing.assert_array_equal(h, full[k][1])
