@@ -221,6 +221,35 @@ gsp2_status gsp2_history(gsp2_handle h, double* traces, double* idem, int8_t* al
  * the stopping test return at once and show a few microseconds.  Waits for the call. */
 gsp2_status gsp2_step_times(gsp2_handle h, float* ms, int32_t cap);
 
+/*
+ * Density for the next H of a sequence (SCF iterations or MD steps): Section 2.1 reuses the
+ * recorded sequence of multiplications as long as it still gives the right trace.  With
+ * *nsteps > 0 the call replays d_alpha[0 .. *nsteps) (GSP2_MODE_REPLAY) and checks Tr P; when
+ * the replayed sequence gives the wrong trace (|Tr P - Nocc| > trace_tol) or *nsteps == 0, it
+ * runs GSP2_MODE_RECORD, which chooses the branches afresh and writes them to d_alpha, and
+ * sets *nsteps to the steps applied and *recomputed to 1 (else 0).
+ *  d_alpha   device int8[max_steps + 8], the sequence carried from call to call
+ *  nsteps    in/out, host; 0 on the first call
+ * FP64 and FP64_EMU plans only (the branch replay of the low-precision modes is not
+ * available).  Synchronises `stream`; returns the device status of the call that produced P.
+ */
+gsp2_status gsp2_density_reuse(gsp2_handle h, const double* d_hvals, double* d_pvals, int8_t* d_alpha,
+                               int32_t* nsteps, void* stream, int32_t* recomputed);
+
+/*
+ * Dependency graph G_tau from a density matrix (Section 2.2: vertices i and j are adjacent
+ * when |P_ij| > tau), for re-planning between SCF or MD steps: the pattern of `d_pvals`
+ * (the core-column layout of gsp2_p_pattern) thresholded on the device, symmetrised (an
+ * edge when either of P_ij, P_ji is stored and above tau), with every diagonal entry, as a
+ * CSR graph with sorted columns that gsp2_create accepts.
+ *  g_rowptr  host int64[n + 1], always written
+ *  g_colind  host int32[cap]; written when cap >= the number of entries, which is returned
+ *            in *nnz either way (call once with cap = 0 to size the buffer)
+ * Synchronises `stream`.  Errors: GSP2_E_ARG (tau < 0, NULL outputs), GSP2_E_STATE, GSP2_E_CUDA.
+ */
+gsp2_status gsp2_threshold_graph(gsp2_handle h, const double* d_pvals, double tau, void* stream, int64_t* g_rowptr,
+                                 int32_t* g_colind, int64_t cap, int64_t* nnz);
+
 /* Outcome of gsp2_autotune: the candidates tried and their times. */
 typedef struct {
   int32_t ncand;        /* candidates timed (1 when the precision has no choice) */

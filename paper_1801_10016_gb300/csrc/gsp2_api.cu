@@ -33,6 +33,7 @@ struct WsLayout {
   size_t oz_slice[2][OZ_SLICES];  // BF16 digit arenas, two buffers (read / written by a step)
   size_t oz_maps;                 // CUtensorMap[2][OZ_SLICES][nparts]
   size_t oz_acc;                  // int64[OZ_MAX_GRID][128 * 128] partial sums of the emulated step
+  size_t mask;                    // uint8[nnz_p]: |P| > tau flags of gsp2_threshold_graph
   std::vector<size_t> tailf;      // low-precision adjoint: FP32 iterates of the FP64 tail, recomputed
   size_t slots, rslots, state, alpha, traces, idem, step_arena;
   size_t arena0, arena1;       // ping-pong iterates
@@ -219,6 +220,7 @@ static void build_layout(gsp2_plan* h) {
   L.idem = take(((size_t)h->opt.max_steps + HIST_EXTRA) * sizeof(double));
   L.step_arena = take(((size_t)h->total_steps + 1) * sizeof(double*));
   L.master_of_step = take(((size_t)h->opt.max_steps + 1 + MAX_TAIL) * sizeof(float*));
+  L.mask = take((size_t)h->pcolptr[(size_t)h->n]);
   const size_t ab = (size_t)h->arena_elems * sizeof(double);
   const int prec = h->opt.precision;
   if (!fp64_like(prec)) {
@@ -920,6 +922,85 @@ extern "C" gsp2_status gsp2_autotune(gsp2_handle h, const double* d_hvals, doubl
     }
   }
   return out;
+}
+
+extern "C" gsp2_status gsp2_density_reuse(gsp2_handle h, const double* d_hvals, double* d_pvals, int8_t* d_alpha,
+                                          int32_t* nsteps, void* stream, int32_t* recomputed) {
+  if (!usable(h)) return fail(h, GSP2_E_ARG, "invalid handle");
+  if (!nsteps || !d_alpha || *nsteps < 0) return fail(h, GSP2_E_ARG, "NULL d_alpha or nsteps, or nsteps < 0");
+  if (!fp64_like(h->opt.precision)) return fail(h, GSP2_E_STATE, "sequence reuse needs an FP64 or FP64_EMU plan");
+  if (recomputed) *recomputed = 0;
+  gsp2_report r{};
+  if (*nsteps > 0) {
+    gsp2_status st = gsp2_density(h, d_hvals, d_pvals, d_alpha, MODE_REPLAY, *nsteps, stream);
+    if (st != GSP2_OK) return st;
+    st = gsp2_sync_status(h, &r);
+    if (st != GSP2_E_TRACE) return st;  // the sequence still holds (or another outcome to report)
+  }
+  gsp2_status st = gsp2_density(h, d_hvals, d_pvals, d_alpha, MODE_RECORD, 0, stream);
+  if (st != GSP2_OK) return st;
+  st = gsp2_sync_status(h, &r);
+  *nsteps = r.steps;
+  if (recomputed) *recomputed = 1;
+  return st;
+}
+
+extern "C" gsp2_status gsp2_threshold_graph(gsp2_handle h, const double* d_pvals, double tau, void* stream,
+                                            int64_t* g_rowptr, int32_t* g_colind, int64_t cap, int64_t* nnz) {
+  if (!usable(h)) return fail(h, GSP2_E_ARG, "invalid handle");
+  if (!d_pvals || !g_rowptr || !nnz || !(tau >= 0.0) || cap < 0) return fail(h, GSP2_E_ARG, "NULL argument or tau < 0");
+  if (!h->ws) return fail(h, GSP2_E_STATE, "no workspace bound");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t np = h->pcolptr[h->n];
+  std::vector<uint8_t> mask((size_t)np);
+  uint8_t* dmask = (uint8_t*)(h->ws + h->L.mask);
+  CU(h, launch_threshold(d_pvals, np, tau, dmask, s));
+  CU(h, cudaMemcpyAsync(mask.data(), dmask, (size_t)np, cudaMemcpyDeviceToHost, s));
+  CU(h, cudaStreamSynchronize(s));
+  const int64_t n = h->n;
+  // edges (r, g) and (g, r) for every stored P_rg above tau, plus the diagonal
+  std::vector<int64_t> deg((size_t)n + 1, 0);
+  for (int64_t g = 0; g < n; ++g) {
+    ++deg[(size_t)g];
+    for (int64_t e = h->pcolptr[g]; e < h->pcolptr[g + 1]; ++e) {
+      const int32_t r = h->prowind[(size_t)e];
+      if (mask[(size_t)e] && r != g) {
+        ++deg[(size_t)r];
+        ++deg[(size_t)g];
+      }
+    }
+  }
+  std::vector<int64_t> rp((size_t)n + 1, 0);
+  for (int64_t i = 0; i < n; ++i) rp[(size_t)i + 1] = rp[(size_t)i] + deg[(size_t)i];
+  std::vector<int32_t> ci((size_t)rp[(size_t)n]);
+  std::vector<int64_t> fill(rp.begin(), rp.end() - 1);
+  for (int64_t g = 0; g < n; ++g) {
+    ci[(size_t)fill[(size_t)g]++] = (int32_t)g;
+    for (int64_t e = h->pcolptr[g]; e < h->pcolptr[g + 1]; ++e) {
+      const int32_t r = h->prowind[(size_t)e];
+      if (mask[(size_t)e] && r != g) {
+        ci[(size_t)fill[(size_t)r]++] = (int32_t)g;
+        ci[(size_t)fill[(size_t)g]++] = r;
+      }
+    }
+  }
+  // sort and deduplicate every row (an edge can come from both P_rg and P_gr), compacting
+  // the rows to the front of ci
+  int64_t out = 0;
+  g_rowptr[0] = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    auto b = ci.begin() + rp[(size_t)i], e = ci.begin() + rp[(size_t)i + 1];
+    std::sort(b, e);
+    const int64_t m = std::unique(b, e) - b;
+    if (ci.begin() + out != b) std::copy(b, b + m, ci.begin() + out);  // out < rp[i]: moves left
+    out += m;
+    g_rowptr[i + 1] = out;
+  }
+  *nnz = out;
+  if (!g_colind) return GSP2_OK;
+  if (cap < out) return fail(h, GSP2_E_ARG, "g_colind smaller than the graph (see *nnz)");
+  std::copy(ci.begin(), ci.begin() + out, g_colind);
+  return GSP2_OK;
 }
 
 extern "C" gsp2_status gsp2_sync_status(gsp2_handle h, gsp2_report* r) {

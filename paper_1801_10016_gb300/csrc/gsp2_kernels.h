@@ -18,6 +18,7 @@ cudaError_t launch_square_fp64(const PartDesc* parts, const Tile* tiles, int nti
 cudaError_t launch_residual_fp64(const PartDesc* parts, const Tile* tiles, int ntiles, const double* x,
                                  const double* const* x_of_step, double* rslots, int64_t n, const StepCtl& ctl,
                                  cudaStream_t s);
+cudaError_t launch_threshold(const double* p, int64_t n, double tau, uint8_t* mask, cudaStream_t s);
 cudaError_t launch_recompute_fp32(const PartDesc* parts, const Tile* tiles, int ntiles, const float* xin,
                                   float* xout, const StepCtl& ctl, int step, cudaStream_t s);
 cudaError_t launch_square_fp32(const PartDesc* parts, const Tile* tiles, int ntiles, const float* xin, float* xout,

@@ -429,6 +429,17 @@ cudaError_t launch_recompute_fp32(const PartDesc* parts, const Tile* tiles, int 
   return cudaGetLastError();
 }
 
+// |P_e| > tau over the stored values of P (graph refresh of Section 2.2).
+__global__ void threshold_kernel(const double* __restrict__ p, int64_t n, double tau, uint8_t* __restrict__ mask) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    mask[e] = fabs(p[e]) > tau ? 1 : 0;
+}
+
+cudaError_t launch_threshold(const double* p, int64_t n, double tau, uint8_t* mask, cudaStream_t s) {
+  threshold_kernel<<<152 * 8, 256, 0, s>>>(p, n, tau, mask);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_scatter(const PartDesc* parts, const ColBlock* blocks, int nblocks, const int32_t* Sall,
                            const int32_t* perm, const int64_t* pcolptr, const double* const* arena_of_step,
                            const double* fixed_arena, double* pvals, const DevState* st, cudaStream_t s) {

@@ -93,6 +93,8 @@ def load(path: str = LIB_PATH):
         "gsp2_step_times": (C.c_int, [_P, _P, C.c_int32]),
         "gsp2_backward": (C.c_int, [_P, _P, _P, _P]),
         "gsp2_autotune": (C.c_int, [_P, _P, _P, C.c_int32, _P, C.POINTER(TuneReport)]),
+        "gsp2_density_reuse": (C.c_int, [_P, _P, _P, _P, C.POINTER(C.c_int32), _P, C.POINTER(C.c_int32)]),
+        "gsp2_threshold_graph": (C.c_int, [_P, _P, C.c_double, _P, _P, _P, C.c_int64, C.POINTER(C.c_int64)]),
         "gsp2_last_error": (C.c_char_p, [_P]),
         "gsp2_destroy": (None, [_P]),
     }
@@ -229,6 +231,37 @@ class GSP2:
         self._refresh_info()
         cands = [dict(tc_schedule=r.tc_schedule[i], tile_order=r.tile_order[i], ms=r.ms[i]) for i in range(r.ncand)]
         return dict(chosen=r.chosen, candidates=cands)
+
+    def density_reuse(self, h_vals, alpha, nsteps, out=None, stream=None):
+        """Density for the next H of an SCF/MD sequence (gsp2_density_reuse): replays the
+        `nsteps` branches in `alpha` (int8 CUDA tensor of alpha_len) and records a new
+        sequence when they give the wrong trace.  Returns (P, nsteps, recomputed, status)."""
+        import torch
+        if h_vals.dtype != torch.float64 or not h_vals.is_cuda or h_vals.numel() != self.nnz_h:
+            raise ValueError("h_vals must be a CUDA float64 tensor of nnz(H) values")
+        if alpha.dtype != torch.int8 or not alpha.is_cuda or alpha.numel() < self.alpha_len:
+            raise ValueError("alpha must be a CUDA int8 tensor of alpha_len entries")
+        if out is None:
+            out = torch.empty(self.nnz_p, dtype=torch.float64, device=h_vals.device)
+        n = C.c_int32(int(nsteps))
+        rec = C.c_int32(0)
+        st = self._lib.gsp2_density_reuse(self._h, _tptr(h_vals.contiguous()), _tptr(out), _tptr(alpha), C.byref(n),
+                                          _stream_ptr(stream), C.byref(rec))
+        if st in (E_ARG, E_STATE, E_CUDA, E_TIMEOUT):
+            self._check(st)
+        return out, n.value, bool(rec.value), st
+
+    def threshold_graph(self, p_vals, tau, stream=None):
+        """G_tau from P (gsp2_threshold_graph): (g_rowptr int64[n+1], g_colind int32[nnz]),
+        symmetric with the diagonal, ready for a new plan."""
+        rp = np.empty(self.n + 1, np.int64)
+        nnz = C.c_int64(0)
+        self._check(self._lib.gsp2_threshold_graph(self._h, _tptr(p_vals), float(tau), _stream_ptr(stream), _ptr(rp),
+                                                   None, 0, C.byref(nnz)))
+        ci = np.empty(nnz.value, np.int32)
+        self._check(self._lib.gsp2_threshold_graph(self._h, _tptr(p_vals), float(tau), _stream_ptr(stream), _ptr(rp),
+                                                   _ptr(ci), nnz.value, C.byref(nnz)))
+        return rp, ci
 
     def _refresh_info(self):
         info = PlanInfo()
