@@ -242,14 +242,19 @@ WORKLOADS = {
     # 8,000 orbitals, 64 parts, the part sizes of tb30k on a quarter of the volume (arenas
     # still larger than L2): the case kernel profiles are taken on
     "tb8k": dict(n_sites=2000, nparts=64, graph_radius=5.0),
+    # dense molecular crystal (the paper's urea case stands behind it): sites twice as dense,
+    # so each core carries a halo about twice as large; 8,000 orbitals, 64 parts
+    "crystal8k": dict(n_sites=2000, nparts=64, graph_radius=5.0, density=0.2),
+    # the same at 512 orbitals, for the oracle
+    "crystal512": dict(n_sites=128, nparts=8, graph_radius=3.5, density=0.2),
     # 120,000 orbitals, 1,024 parts, sizes ~200-2,000
     "tb120k": dict(n_sites=30000, nparts=1024, graph_radius=5.0),
 }
 
 
 def make_tb_system(n_sites: int, nparts: int, graph_radius: float, seed: int = 1234,
-                   name: str = "custom") -> TBSystem:
-    coords, rowptr, colind, vals = make_hamiltonian(n_sites, seed=seed)
+                   name: str = "custom", density: float = 0.1) -> TBSystem:
+    coords, rowptr, colind, vals = make_hamiltonian(n_sites, seed=seed, density=density)
     site_part = rcb_partition(coords, nparts)
     part = np.repeat(site_part, ORBS_PER_SITE).astype(np.int32)
     g_rowptr, g_colind = locality_graph(coords, graph_radius)
@@ -257,9 +262,10 @@ def make_tb_system(n_sites: int, nparts: int, graph_radius: float, seed: int = 1
     return TBSystem(name=name, n_sites=n_sites, n=n, nocc=2 * n_sites, rowptr=rowptr,
                     colind=colind, vals=vals, coords=coords, part=part, nparts=nparts,
                     g_rowptr=g_rowptr, g_colind=g_colind,
-                    meta=dict(seed=seed, graph_radius=graph_radius))
+                    meta=dict(seed=seed, graph_radius=graph_radius, density=density))
 
 
 def make_workload(name: str, seed: int = 1234) -> TBSystem:
     w = WORKLOADS[name]
-    return make_tb_system(w["n_sites"], w["nparts"], w["graph_radius"], seed=seed, name=name)
+    return make_tb_system(w["n_sites"], w["nparts"], w["graph_radius"], seed=seed, name=name,
+                          density=w.get("density", 0.1))
