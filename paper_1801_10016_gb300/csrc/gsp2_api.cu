@@ -31,7 +31,8 @@ struct WsLayout {
   size_t d[2];         // FP64 arenas of the tail steps
   // FP64 products from BF16 digits
   size_t oz_slice[2][OZ_SLICES];  // BF16 digit arenas, two buffers (read / written by a step)
-  size_t oz_maps;                 // CUtensorMap[2][OZ_SLICES][nparts]
+  size_t oz_maps;                 // CUtensorMap[2][OZ_SLICES][nparts], K-major boxes
+  size_t oz_maps_mn;              // the same, MN-major boxes
   size_t oz_acc;                  // int64[OZ_MAX_GRID][128 * 128] partial sums of the emulated step
   size_t mask;                    // uint8[nnz_p]: |P| > tau flags of gsp2_threshold_graph
   std::vector<size_t> tailf;      // low-precision adjoint: FP32 iterates of the FP64 tail, recomputed
@@ -263,6 +264,7 @@ static void build_layout(gsp2_plan* h) {
       for (int b = 0; b < 2; ++b)
         for (int t = 0; t < OZ_SLICES; ++t) L.oz_slice[b][t] = take((size_t)h->arena_elems * 2);
       L.oz_maps = take((size_t)2 * OZ_SLICES * h->parts.size() * 128);
+      L.oz_maps_mn = take((size_t)2 * OZ_SLICES * h->parts.size() * 128);
       L.oz_acc = take((size_t)OZ_MAX_GRID * 128 * 128 * 8);
     }
     L.arena0 = L.d[0];
@@ -287,6 +289,7 @@ static void build_layout(gsp2_plan* h) {
     for (int b = 0; b < 2; ++b)
       for (int t = 0; t < OZ_SLICES; ++t) L.oz_slice[b][t] = take((size_t)h->arena_elems * 2);
     L.oz_maps = take((size_t)2 * OZ_SLICES * h->parts.size() * 128);
+    L.oz_maps_mn = take((size_t)2 * OZ_SLICES * h->parts.size() * 128);
     L.oz_acc = take((size_t)OZ_MAX_GRID * 128 * 128 * 8);
   }
   L.total = o;
@@ -587,14 +590,20 @@ extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t byt
     if (!enc || q != cudaDriverEntryPointSuccess)
       return fail(h, GSP2_E_CUDA, "cuTensorMapEncodeTiled not available from the driver");
     const size_t np = h->parts.size();
-    std::vector<unsigned char> maps((size_t)2 * OZ_SLICES * np * 128, 0);
+    // K-major boxes (OZ_BK rows of 128 columns) and MN-major boxes (64 rows of OZ_BK columns)
+    std::vector<unsigned char> maps((size_t)2 * OZ_SLICES * np * 128, 0), maps_mn(maps.size(), 0);
     for (int b = 0; b < 2; ++b)
       for (int t = 0; t < OZ_SLICES; ++t) {
-        const int r = encode_part_maps(enc, maps.data() + ((size_t)b * OZ_SLICES + t) * np * 128, h->parts.data(),
-                                       (int)np, h->ws + L.oz_slice[b][t], 0, 2 * OZ_BK);
+        const size_t at = ((size_t)b * OZ_SLICES + t) * np * 128;
+        int r = encode_part_maps(enc, maps.data() + at, h->parts.data(), (int)np, h->ws + L.oz_slice[b][t], 0,
+                                 2 * OZ_BK, 128);
+        if (r == 0)
+          r = encode_part_maps(enc, maps_mn.data() + at, h->parts.data(), (int)np, h->ws + L.oz_slice[b][t], 0, 128,
+                               OZ_BK);
         if (r != 0) return fail(h, GSP2_E_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string(r));
       }
     CU(h, up(L.oz_maps, maps.data(), maps.size()));
+    CU(h, up(L.oz_maps_mn, maps_mn.data(), maps_mn.size()));
   }
   if (!fp64_like(h->opt.precision)) {
     std::vector<const float*> mt(h->mf_of_step.size());
@@ -642,6 +651,10 @@ static OzStepArgs oz_args(gsp2_plan* h, const StepCtl& ctl) {
   a.tiles = (const Tile*)(w + L.tc_tiles);
   a.ntiles = (int)h->tc_tiles.size();
   a.maps = w + L.oz_maps;
+  a.maps_mn = w + L.oz_maps_mn;
+  // the emulated steps keep the upper tiles only, and the lower ones too where an iterate is
+  // a checkpoint of the FP64 adjoint (the low-precision adjoint keeps FP32 iterates instead)
+  a.lower_every = fp64_like(h->opt.precision) ? h->opt.ckpt_every : 0;
   a.nparts = (int)h->parts.size();
   for (int b = 0; b < 2; ++b)
     for (int t = 0; t < OZ_SLICES; ++t) a.digits[b].s[t] = (uint16_t*)(w + L.oz_slice[b][t]);
@@ -760,10 +773,15 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
         CU(h, launch_square_fp64(parts, tiles, (int)h->tiles.size(), d[t & 1], d[(t + 1) & 1], slots, h->nslots, ctl,
                                  0, tmode, s));
     }
-    CU(h, launch_scatter(parts, sbl, (int)h->sblocks.size(), Sall, perm, pcol, nullptr, d[T & 1], pv, st, s));
-    if (h->opt.report_idem)
+    // emulated tail steps leave the upper 128-tiles only
+    const int ub = (h->use_oz && T > 0) ? TC_TILE : 0;
+    CU(h, launch_scatter(parts, sbl, (int)h->sblocks.size(), Sall, perm, pcol, nullptr, d[T & 1], pv, st, s, ub));
+    if (h->opt.report_idem) {
+      if (ub) CU(h, launch_symmetrize(parts, (const Tile*)(w + L.tc_tiles), (int)h->tc_tiles.size(), nullptr, d[T & 1],
+                                      st, s));
       CU(h, launch_residual_fp64(parts, tiles, (int)h->tiles.size(), d[T & 1], nullptr, (double*)(w + L.rslots),
                                  h->n, ctl, s));
+    }
     if (alpha_user)
       CU(h, cudaMemcpyAsync(alpha_user, alpha + 1, (size_t)h->opt.max_steps + MAX_TAIL, cudaMemcpyDeviceToDevice, s));
     return GSP2_OK;
@@ -793,10 +811,14 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
     if (!h->ev.empty()) CU(h, cudaEventRecordWithFlags(h->ev[2 * (i - 1) + 1], s, cudaEventRecordExternal));
   }
   CU(h, launch_scatter(parts, sbl, (int)h->sblocks.size(), Sall, perm, pcol, (const double* const*)(w + L.step_arena),
-                       nullptr, pv, st, s));
-  if (h->opt.report_idem)
+                       nullptr, pv, st, s, emu ? TC_TILE : 0));
+  if (h->opt.report_idem) {
+    if (emu)
+      CU(h, launch_symmetrize(parts, (const Tile*)(w + L.tc_tiles), (int)h->tc_tiles.size(),
+                              (const double* const*)(w + L.step_arena), nullptr, st, s));
     CU(h, launch_residual_fp64(parts, tiles, (int)h->tiles.size(), nullptr, (const double* const*)(w + L.step_arena),
                                (double*)(w + L.rslots), h->n, ctl, s));
+  }
   if (mode == MODE_RECORD && alpha_user)
     CU(h, cudaMemcpyAsync(alpha_user, alpha + 1, (size_t)h->opt.max_steps + MAX_TAIL, cudaMemcpyDeviceToDevice, s));
   return GSP2_OK;

@@ -105,7 +105,8 @@ struct OzStepArgs {
   const PartDesc* parts;
   const Tile* tiles;   // 128x128 upper tiles
   int ntiles;
-  const void* maps;    // CUtensorMap[2 buffers][OZ_SLICES][nparts] over the digit arenas
+  const void* maps;    // CUtensorMap[2 buffers][OZ_SLICES][nparts] over the digit arenas, K-major boxes
+  const void* maps_mn; // the same with MN-major boxes (64 rows x OZ_BK columns, 128-byte swizzle)
   int nparts;
   OzSlices digits[2];
   const double* xin;   // FP64 master of X_{step-1}
@@ -113,6 +114,7 @@ struct OzStepArgs {
   double2* slots;      // diagonal-tile trace slots
   int nslots;
   long long* acc;      // OZ_MAX_GRID x 128 x 128 fixed-point partial sums, one tile per CTA
+  int lower_every;     // also write the lower tiles when k divides the step (k > 0): checkpoints
   StepCtl ctl;
   int step;            // ignored in tail modes (step = steps applied + 1)
   int mode;            // SQ_FORWARD, SQ_TAIL_FIRST or SQ_TAIL_NEXT

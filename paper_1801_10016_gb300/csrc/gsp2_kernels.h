@@ -25,7 +25,10 @@ cudaError_t launch_square_fp32(const PartDesc* parts, const Tile* tiles, int nti
                                double2* slots, int nslots, const StepCtl& ctl, int step, cudaStream_t s);
 cudaError_t launch_scatter(const PartDesc* parts, const ColBlock* blocks, int nblocks, const int32_t* Sall,
                            const int32_t* perm, const int64_t* pcolptr, const double* const* arena_of_step,
-                           const double* fixed_arena, double* pvals, const DevState* st, cudaStream_t s);
+                           const double* fixed_arena, double* pvals, const DevState* st, cudaStream_t s,
+                           int upper_block = 0);
+cudaError_t launch_symmetrize(const PartDesc* parts, const Tile* tiles, int ntiles, const double* const* arena_of_step,
+                              double* fixed_arena, const DevState* st, cudaStream_t s);
 
 // low-precision paths (k_tc.cu)
 cudaError_t launch_square_tc(int kind, int nprod, const TcStepArgs& a, int ntiles, int persistent_grid,
@@ -43,7 +46,7 @@ cudaError_t launch_oz_slice(const PartDesc* parts, const ColBlock* blocks, int n
                             const OzSlices* digits, const DevState* st, cudaStream_t s);
 cudaError_t launch_oz_step(const OzStepArgs& a, int grid, cudaStream_t s);
 int encode_part_maps(void* enc_fn, void* out_maps, const PartDesc* parts, int nparts, void* arena, int kind,
-                     int box_bytes = 128);
+                     int box_bytes = 128, int box_cols = 128);
 
 // adjoint (k_adjoint.cu)
 template <typename T>

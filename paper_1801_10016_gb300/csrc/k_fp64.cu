@@ -362,18 +362,48 @@ __global__ void __launch_bounds__(256) scatter_kernel(const PartDesc* __restrict
                                                       const int64_t* __restrict__ pcolptr,
                                                       const double* const* __restrict__ arena_of_step,
                                                       const double* __restrict__ fixed_arena,
-                                                      double* __restrict__ pvals, const DevState* st) {
+                                                      double* __restrict__ pvals, const DevState* st,
+                                                      int upper_block) {
   const ColBlock b = blocks[blockIdx.x];
   const PartDesc p = parts[b.part];
   const int j = b.j0 + (threadIdx.x >> 5);
   if (j >= p.c) return;
   const int lane = threadIdx.x & 31;
-  const double* A = fixed_arena ? fixed_arena : arena_of_step[st->steps];
-  const double* X = A + p.off + (int64_t)j * p.ld;
+  const double* A = (fixed_arena ? fixed_arena : arena_of_step[st->steps]) + p.off;
+  const double* X = A + (int64_t)j * p.ld;
   const int32_t g = Sall[p.soff + j];
   const int32_t* pm = perm + p.soff;
   double* out = pvals + pcolptr[g];
-  for (int t = lane; t < p.s; t += 32) out[t] = X[pm[t]];
+  // upper_block > 0: only the tiles of that edge on or above the diagonal are stored (the
+  // matrix is symmetric), so X[a, j] below them is read as X[j, a]
+  const int jb = upper_block > 0 ? j / upper_block : 0;
+  for (int t = lane; t < p.s; t += 32) {
+    const int a = pm[t];
+    out[t] = (upper_block > 0 && a / upper_block > jb) ? A[(int64_t)a * p.ld + j] : X[a];
+  }
+}
+
+// Fill the lower tiles of arenas that hold only the upper 128-tiles (emulated FP64 steps
+// without mirrored writes), for consumers that read whole columns: one block per upper
+// off-diagonal tile, 32 x 32 blocks transposed through shared memory.
+__global__ void __launch_bounds__(256) symmetrize_kernel(const PartDesc* __restrict__ parts,
+                                                         const Tile* __restrict__ tiles,
+                                                         const double* const* __restrict__ arena_of_step,
+                                                         double* __restrict__ fixed_arena, const DevState* st) {
+  const Tile t = tiles[blockIdx.x];
+  if (t.ti == t.tj) return;
+  const PartDesc p = parts[t.part];
+  double* A = (fixed_arena ? fixed_arena : const_cast<double*>(arena_of_step[st->steps])) + p.off;
+  __shared__ double buf[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  for (int bi = 0; bi < 4; ++bi)
+    for (int bj = 0; bj < 4; ++bj) {
+      const int r0 = t.ti * 128 + bi * 32, c0 = t.tj * 128 + bj * 32;
+      for (int y = ty; y < 32; y += 8) buf[y][tx] = A[(int64_t)(c0 + y) * p.ld + r0 + tx];  // column c0+y
+      __syncthreads();
+      for (int y = ty; y < 32; y += 8) A[(int64_t)(r0 + y) * p.ld + c0 + tx] = buf[tx][y];   // column r0+y
+      __syncthreads();
+    }
 }
 
 // ------------------------------------------------------------------------------------
@@ -442,9 +472,15 @@ cudaError_t launch_threshold(const double* p, int64_t n, double tau, uint8_t* ma
 
 cudaError_t launch_scatter(const PartDesc* parts, const ColBlock* blocks, int nblocks, const int32_t* Sall,
                            const int32_t* perm, const int64_t* pcolptr, const double* const* arena_of_step,
-                           const double* fixed_arena, double* pvals, const DevState* st, cudaStream_t s) {
+                           const double* fixed_arena, double* pvals, const DevState* st, cudaStream_t s, int upper_block) {
   scatter_kernel<<<nblocks, 32 * COLS_PER_BLOCK, 0, s>>>(parts, blocks, Sall, perm, pcolptr, arena_of_step,
-                                                        fixed_arena, pvals, st);
+                                                        fixed_arena, pvals, st, upper_block);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_symmetrize(const PartDesc* parts, const Tile* tiles, int ntiles, const double* const* arena_of_step,
+                              double* fixed_arena, const DevState* st, cudaStream_t s) {
+  symmetrize_kernel<<<ntiles, 256, 0, s>>>(parts, tiles, arena_of_step, fixed_arena, st);
   return cudaGetLastError();
 }
 

@@ -179,23 +179,24 @@ __device__ __forceinline__ uint32_t oz_group_col(int d) {
 // offsets to the stage's base descriptors (the 14-bit address field cannot carry: shared
 // addresses stay below 2^18).
 template <int D0, int D1>
-__device__ __forceinline__ void oz_issue_stage(uint32_t tmem, uint64_t da, uint64_t db, bool first_k) {
-  constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+__device__ __forceinline__ void oz_issue_stage(uint32_t tmem, uint64_t da, uint64_t db, uint32_t adv_a,
+                                               uint32_t adv_b, uint32_t idesc, bool first_k) {
   constexpr uint64_t step = OZ_DTILE >> 4;
 #pragma unroll
-  for (int kk = 0; kk < OZ_BK / 16; ++kk) {  // K = 16 slices inside the swizzled rows (32 B each)
+  for (int kk = 0; kk < OZ_BK / 16; ++kk) {  // K = 16 slices of the stage
 #pragma unroll
     for (int d = D0; d < D1; ++d) {
 #pragma unroll
       for (int q = 0; q <= d; ++q)
-        mma<0>(tmem + oz_group_col(d), da + (uint64_t)q * step + 2u * kk, db + (uint64_t)(d - q) * step + 2u * kk,
-               IDESC, (q > 0 || kk > 0 || !first_k) ? 1u : 0u);
+        mma<0>(tmem + oz_group_col(d), da + (uint64_t)q * step + (uint64_t)(adv_a * kk),
+               db + (uint64_t)(d - q) * step + (uint64_t)(adv_b * kk), idesc, (q > 0 || kk > 0 || !first_k) ? 1u : 0u);
     }
   }
 }
 
 __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
   constexpr int T = OZ_SLICES;
+  constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
 
   int step = a.step;
   if (a.mode == SQ_FORWARD) {
@@ -225,6 +226,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
   int32_t* abort_flag = &a.ctl.st->timeout;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const CUtensorMap* maps = reinterpret_cast<const CUtensorMap*>(a.maps) + (size_t)dbi * T * a.nparts;
+  const CUtensorMap* maps_mn = reinterpret_cast<const CUtensorMap*>(a.maps_mn) + (size_t)dbi * T * a.nparts;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < OZ_STAGES; ++s) {
@@ -263,10 +265,25 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
             break;
           }
           mbar_expect_tx(full(s), (uint32_t)(dg ? nd : 2 * nd) * OZ_DTILE);
+          // rows I over the K slice: K-major from columns I of the tiles on or above the
+          // diagonal (slice block <= I's block), else MN-major from rows I of tile (I, slice)
+          const int kt = kb * OZ_BK / 128;
           for (int q = 0; q < nd; ++q) {
             const CUtensorMap* m = maps + (size_t)q * a.nparts + t.part;
-            tma_load_2d(tileA(s, q), m, kb * OZ_BK, t.ti * 128, full(s));
-            if (!dg) tma_load_2d(tileB(s, q), m, kb * OZ_BK, t.tj * 128, full(s));
+            const CUtensorMap* mm = maps_mn + (size_t)q * a.nparts + t.part;
+            if (kt <= t.ti) {
+              tma_load_2d(tileA(s, q), m, kb * OZ_BK, t.ti * 128, full(s));
+            } else {
+              tma_load_2d(tileA(s, q), mm, t.ti * 128, kb * OZ_BK, full(s));
+              tma_load_2d(tileA(s, q) + OZ_DTILE / 2, mm, t.ti * 128 + 64, kb * OZ_BK, full(s));
+            }
+            if (dg) continue;
+            if (kt <= t.tj) {
+              tma_load_2d(tileB(s, q), m, kb * OZ_BK, t.tj * 128, full(s));
+            } else {
+              tma_load_2d(tileB(s, q), mm, t.tj * 128, kb * OZ_BK, full(s));
+              tma_load_2d(tileB(s, q) + OZ_DTILE / 2, mm, t.tj * 128 + 64, kb * OZ_BK, full(s));
+            }
           }
         }
       }
@@ -301,11 +318,19 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
             break;
           }
           tc_fence_after();
-          // pairs (q, d - q) of every group of the pass; both digits are < d1 <= T
-          const uint64_t da = smem_desc_sw<2 * OZ_BK>(tileA(s, 0));
-          const uint64_t db = dg ? da : smem_desc_sw<2 * OZ_BK>(tileB(s, 0));
-          if (pass == 0) oz_issue_stage<OZ_SPLIT, T>(tmem, da, db, kb == 0);
-          else oz_issue_stage<0, OZ_SPLIT>(tmem, da, db, kb == 0);
+          // pairs (q, d - q) of every group of the pass; both digits are < d1 <= T.  Operands
+          // right of the tile's own block came in MN-major (transpose bits 15 / 16); a K = 16
+          // step advances 32 B in a K-major row, 2 KB (16 K values) in an MN-major tile
+          const int kt = kb * OZ_BK / 128;
+          const bool amn = kt > t.ti, bmn = kt > t.tj;
+          const uint64_t da = amn ? smem_desc_mn128(tileA(s, 0), OZ_DTILE / 2) : smem_desc_sw<2 * OZ_BK>(tileA(s, 0));
+          const uint64_t db = dg ? da
+                                 : (bmn ? smem_desc_mn128(tileB(s, 0), OZ_DTILE / 2)
+                                        : smem_desc_sw<2 * OZ_BK>(tileB(s, 0)));
+          const uint32_t adv_a = amn ? (2048u >> 4) : (32u >> 4), adv_b = bmn ? (2048u >> 4) : (32u >> 4);
+          const uint32_t idesc = IDESC | ((amn ? 1u : 0u) << 15) | ((bmn ? 1u : 0u) << 16);
+          if (pass == 0) oz_issue_stage<OZ_SPLIT, T>(tmem, da, db, adv_a, adv_b, idesc, kb == 0);
+          else oz_issue_stage<0, OZ_SPLIT>(tmem, da, db, adv_a, adv_b, idesc, kb == 0);
           mma_commit(empty(s));
         }
         if (!bad) mma_commit(afull(pass));
@@ -317,6 +342,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
     const int m = quarter * 32 + lane;
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
     long long* acc = a.acc + (size_t)blockIdx.x * (128 * 128);
+    const bool mirror = a.lower_every > 0 && step % a.lower_every == 0;
     int8_t alf;
     if (a.mode == SQ_TAIL_FIRST) alf = (a.ctl.traces[step - 1] <= (double)a.ctl.nocc) ? (int8_t)1 : (int8_t)-1;
     else if (a.mode == SQ_TAIL_NEXT) alf = (int8_t)(-a.ctl.alpha[step - 1]);
@@ -364,8 +390,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
       }
       if (!ok) *s_err = 1;
       // final pass of the tile: X_new on the 2^-56 grid, FP64 master, digits, traces; column
-      // writes are coalesced across the warp, the mirrored row segment of each thread goes
-      // out in groups of 4 as 32-byte (FP64) and 8-byte (digit) vectors
+      // writes are coalesced across the warp.  Only tiles on or above the diagonal are kept
+      // (the next step reads the rest MN-major from them); where the lower tiles are wanted
+      // (checkpoints of the adjoint), the mirrored row segment of each thread goes out in
+      // groups of 4 as 32-byte (FP64) and 8-byte (digit) vectors
       const bool offd = t.ti != t.tj;
 #pragma unroll 1
       for (int cc = 0; cc < 2 && ok; ++cc) {
@@ -408,6 +436,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
           }
           const int64_t em = p.off + (int64_t)r * ld + cbase + sub * 4;
           if (offd) {
+            if (!mirror) continue;
             double2* xm = reinterpret_cast<double2*>(a.xout + em);
             __stcs(xm, make_double2(xn4[0], xn4[1]));
             __stcs(xm + 1, make_double2(xn4[2], xn4[3]));

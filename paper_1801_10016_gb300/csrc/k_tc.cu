@@ -694,9 +694,9 @@ cudaError_t launch_copy_iterate(const float* const* master_of_step, float* out, 
 // of a column (contiguous), outer = columns, box = 128 bytes x 128 columns, 128-byte
 // swizzle.  `enc` is cuTensorMapEncodeTiled obtained from the driver.
 // One 2-D tensor map per part over an arena (x = row within a column, y = column), box
-// box_bytes x 128 columns with the swizzle of the same width (128, 64 or 32 bytes).
+// box_bytes x box_cols columns with the swizzle of the box's width (128, 64 or 32 bytes).
 int encode_part_maps(void* enc_fn, void* out_maps, const PartDesc* parts, int nparts, void* arena, int kind,
-                     int box_bytes) {
+                     int box_bytes, int box_cols) {
   CUtensorMap* out = reinterpret_cast<CUtensorMap*>(out_maps);
   using Enc = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*, const cuuint64_t*,
                            const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -707,7 +707,7 @@ int encode_part_maps(void* enc_fn, void* out_maps, const PartDesc* parts, int np
     const PartDesc& p = parts[k];
     cuuint64_t dims[2] = {(cuuint64_t)p.ld, (cuuint64_t)p.ld};
     cuuint64_t strides[1] = {(cuuint64_t)p.ld * es};
-    cuuint32_t box[2] = {(cuuint32_t)(box_bytes / es), 128u};
+    cuuint32_t box[2] = {(cuuint32_t)(box_bytes / es), (cuuint32_t)box_cols};
     cuuint32_t estr[2] = {1u, 1u};
     void* addr = (char*)arena + (size_t)p.off * es;
     CUresult r = enc(&out[k], kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, addr,

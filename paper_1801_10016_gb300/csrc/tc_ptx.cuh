@@ -84,6 +84,19 @@ __device__ __forceinline__ uint64_t smem_desc_sw(uint32_t addr) {
   return d;
 }
 
+// MN-major tile of 16-bit elements with 128-byte swizzle: atoms of 64 MN-consecutive
+// elements x 8 K values (1 KB); `lbo` bytes between the atoms along MN, 1 KB between the
+// groups of 8 K values.
+__device__ __forceinline__ uint64_t smem_desc_mn128(uint32_t addr, uint32_t lbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;  // leading byte offset: next 64 MN elements
+  d |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset: next 8 K values
+  d |= (uint64_t)1 << 46;                      // descriptor version
+  d |= (uint64_t)2 << 61;                      // 128-byte swizzle
+  return d;
+}
+
 template <int KIND>
 __device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   if (KIND == 0) {

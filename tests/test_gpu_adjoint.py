@@ -135,3 +135,17 @@ def test_fp32_checkpoint_interval_does_not_change_the_gradient(g, k):
     _, _, _, _, _, hb4 = run_adjoint(g, s, precision="fp32", fp64_tail_steps=0, ckpt_every=4)
     _, _, _, _, _, hbk = run_adjoint(g, s, precision="fp32", fp64_tail_steps=0, ckpt_every=k)
     assert torch.equal(hb4, hbk)
+
+
+@pytest.mark.parametrize("k", [3, 8])
+def test_adjoint_of_the_emulated_fp64_forward(g, k):
+    """FP64 adjoint behind the emulated FP64 forward: the emulated steps keep only upper
+    tiles except at checkpoints, which the reverse sweep rebuilds from."""
+    s = make_workload("tb4k")
+    plan, h, hist, pb, Pbar, hb = run_adjoint(g, s, precision="fp64e", ckpt_every=k)
+    assert hist["status"] == 0
+    ref = oracle.gsp2(s.n, s.rowptr, s.colind, s.vals, s.nocc, s.part, s.nparts, s.g_rowptr, s.g_colind)
+    assert hist["alphas"] == ref.alphas
+    want = oracle.gsp2_adjoint(s.n, s.rowptr, s.colind, s.vals, ref, Pbar)
+    err = float(np.max(np.abs(hb.cpu().numpy() - want)))
+    assert err <= 1e-9 * max(1.0, float(np.max(np.abs(want)))), err
