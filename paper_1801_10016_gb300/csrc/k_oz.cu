@@ -435,8 +435,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
             }
           }
           const int64_t em = p.off + (int64_t)r * ld + cbase + sub * 4;
-          if (offd) {
-            if (!mirror) continue;
+          if (offd ? mirror : cbase + sub * 4 > r) {
+            // the four mirrored elements are contiguous in column r: vector stores (in a
+            // diagonal tile, whenever all four lie right of the diagonal)
             double2* xm = reinterpret_cast<double2*>(a.xout + em);
             __stcs(xm, make_double2(xn4[0], xn4[1]));
             __stcs(xm + 1, make_double2(xn4[2], xn4[3]));
@@ -447,7 +448,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
               pk.y = __byte_perm(dw4[2][q], dw4[3][q], 0x7632);
               __stcs(reinterpret_cast<uint2*>(a.digits[dbo].s[q] + em), pk);
             }
-          } else {
+          } else if (!offd) {
 #pragma unroll
             for (int w = 0; w < 4; ++w) {
               if (cbase + sub * 4 + w <= r) continue;
