@@ -239,7 +239,7 @@ __global__ void __launch_bounds__(256, 2) square_tc_kernel(TcStepArgs a) {
         Xo[e] = x[j];
         store_operands<KIND, NPROD>(ohi, olo, p.off + e, x[j]);
       }
-      if (t.ti == t.tj) {
+      if (t.ti == t.tj && cbase <= r) {
         for (int j = 0; j < 32; ++j) {
           if (cbase + j <= r) continue;
           const int64_t e = (int64_t)r * ld + cbase + j;
@@ -475,7 +475,8 @@ __global__ void __launch_bounds__(384, 1) square_tc_persistent_kernel(TcStepArgs
             Xo[e] = x[j];
             store_operands<KIND, NPROD>(ohi, olo, p.off + e, x[j]);
           }
-          if (t.ti == t.tj) {
+          if (t.ti == t.tj && cbase <= r) {
+            // the 32 x 32 blocks of a diagonal tile that straddle the diagonal: element stores
             for (int j = 0; j < 32; ++j) {
               if (cbase + j <= r) continue;
               const int64_t e = (int64_t)r * ld + cbase + j;
@@ -483,6 +484,7 @@ __global__ void __launch_bounds__(384, 1) square_tc_persistent_kernel(TcStepArgs
               store_operands<KIND, NPROD>(ohi, olo, p.off + e, x[j]);
             }
           } else {
+            // the mirrored row segment (all of it right of the diagonal): vector stores
             const int64_t e0 = (int64_t)r * ld + cbase;
             float4* dst = reinterpret_cast<float4*>(Xo + e0);
 #pragma unroll
