@@ -17,9 +17,9 @@
 // scaled by 2^{-49} or less.  The groups are added as integers into a 64-bit fixed-point
 // accumulator (resolution 2^-56), and a final elementwise pass forms X_new = Y or 2X - Y on
 // that grid (kept as FP64 master copy), the core traces in FP64, and the digits of X_new for
-// the next step by integer arithmetic.  With T = 7 (28 BF16
-// products per tile) the digits hold x to 2^-49 and the dropped products are of order
-// 2^-63 K 2^12; the error of Y is about 1e-13, far below the 1e-10 parity of the FP64 path.
+// the next step by integer arithmetic.  With T = 7 (28 BF16 products per tile) the digits
+// hold x to 2^-49 and the dropped products are of order 2^-63 K 2^12; the error of Y is
+// about 1e-13, far below the 1e-10 parity of the FP64 path.
 #include <cuda.h>
 
 #include "gsp2_internal.cuh"
@@ -77,18 +77,6 @@ __device__ __forceinline__ long long to_fixed(double x) {
   return (b >> 63) ? -(long long)a : (long long)a;
 }
 
-// An integer-valued FP32 number (|f| < 2^31) times 2^shift as a 64-bit integer, with integer
-// instructions only (a 64-bit conversion would run on the FP64 pipe).
-__device__ __forceinline__ long long fint_shl(float f, int shift) {
-  const uint32_t b = __float_as_uint(f);
-  const int ex = (int)((b >> 23) & 0xFF) - 127;  // f = 1.m 2^ex
-  if (ex < 0) return 0;                          // f == 0 (|f| >= 1 otherwise)
-  const long long m = (long long)((b & 0x7FFFFFu) | 0x800000u);
-  const int sh = ex - 23 + shift;
-  const long long a = sh >= 0 ? (m << sh) : (m >> (-sh));  // exact: f is an integer, shift >= 0
-  return (b >> 31) ? -a : a;
-}
-
 __device__ __forceinline__ double from_fixed(long long v) {
   if (v == 0) return 0.0;
   const unsigned long long sgn = v < 0 ? (1ull << 63) : 0ull;
@@ -124,18 +112,6 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const PartDesc* __restric
   if (j >= p.ld) return;
   const int64_t cbase = p.off + (int64_t)j * p.ld;
   for (int r = lane; r < p.ld; r += 32) store_digits(sl.s, cbase + r, to_fixed(X[cbase + r]));
-}
-
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
-      "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};\n" ::"r"(taddr),
-      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
-      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]),
-      "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]),
-      "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
-      : "memory");
-  asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
 }
 
 // One FP64-accurate purification step for every part, in one persistent launch (one CTA
