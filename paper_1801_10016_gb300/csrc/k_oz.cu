@@ -138,6 +138,7 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const PartDesc* __restric
 // (warp w: TMEM lanes 32 (w % 4) .. + 31, columns 32 ((w - 4) / 4) .. + 31 of each group,
 // in two chunks of 16), sized so that four epilogue warps per scheduler hide latency.
 constexpr int OZ_STAGES = 2;
+constexpr int OZ_LOW_SUB = 2;  // K slices per stage of the low-group pass (it needs OZ_SPLIT digits)
 constexpr uint32_t OZ_DTILE = 128u * OZ_BK * 2u;                 // one digit tile: 128 rows x 64 B
 constexpr uint32_t OZ_STAGE_B = 2u * OZ_SLICES * OZ_DTILE;       // all A and B digit tiles
 constexpr int OZ_EPI_WARPS = 16;                                 // 4 per TMEM lane quarter
@@ -145,6 +146,8 @@ constexpr int OZ_THREADS = 32 * (4 + OZ_EPI_WARPS);
 constexpr int OZ_SMEM = OZ_STAGES * (int)OZ_STAGE_B + 1024 + 8 * (2 * OZ_STAGES + 4) + 16 + 16 * OZ_EPI_WARPS;
 static_assert(OZ_SLICES - OZ_SPLIT <= 4 && OZ_SPLIT <= 4, "groups of one pass must fit in 512 TMEM columns");
 static_assert(OZ_SMEM <= 232448, "shared memory of the emulated step");
+static_assert(2 * OZ_LOW_SUB * OZ_SPLIT <= 2 * OZ_SLICES && OZ_LOW_SUB * OZ_BK <= 128,
+              "low-pass stage: its tiles fit a stage and its slices one 128-block of K");
 
 __device__ __forceinline__ uint32_t oz_group_col(int d) {
   return (uint32_t)(d >= OZ_SPLIT ? 128 * (d - OZ_SPLIT + 4 - (OZ_SLICES - OZ_SPLIT)) : 128 * d);
@@ -230,35 +233,41 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
     bool bad = false;
     for (int ti = blockIdx.x; ti < a.ntiles && !bad; ti += gridDim.x) {
       const Tile t = a.tiles[ti];
-      const int nk = (a.parts[t.part].s + OZ_BK - 1) / OZ_BK;
+      const int sz = a.parts[t.part].s;
       const bool dg = t.ti == t.tj;
       for (int pass = 0; pass < 2 && !bad; ++pass) {
         const int nd = pass == 0 ? T : OZ_SPLIT;  // digits the pass multiplies
+        const int sub = pass == 0 ? 1 : OZ_LOW_SUB; // K slices per stage
+        const int nk = (sz + sub * OZ_BK - 1) / (sub * OZ_BK);
         for (int kb = 0; kb < nk; ++kb, ++g) {
           const int s = g % OZ_STAGES;
           if (g >= OZ_STAGES && !mbar_wait(empty(s), ((g / OZ_STAGES) - 1) & 1, abort_flag)) {
             bad = true;
             break;
           }
-          mbar_expect_tx(full(s), (uint32_t)(dg ? nd : 2 * nd) * OZ_DTILE);
+          mbar_expect_tx(full(s), (uint32_t)(sub * (dg ? nd : 2 * nd)) * OZ_DTILE);
           // rows I over the K slice: K-major from columns I of the tiles on or above the
-          // diagonal (slice block <= I's block), else MN-major from rows I of tile (I, slice)
-          const int kt = kb * OZ_BK / 128;
-          for (int q = 0; q < nd; ++q) {
+          // diagonal (slice block <= I's block), else MN-major from rows I of tile (I, slice);
+          // the slices of one stage lie in one 128-block of K
+          for (int u = 0; u < sub; ++u)
+          for (int qq = 0; qq < nd; ++qq) {
+            const int k0 = (kb * sub + u) * OZ_BK;
+            const int kt = k0 / 128;
+            const int q = qq, slot = u * nd + qq;  // digit, tile slot within the stage
             const CUtensorMap* m = maps + (size_t)q * a.nparts + t.part;
             const CUtensorMap* mm = maps_mn + (size_t)q * a.nparts + t.part;
             if (kt <= t.ti) {
-              tma_load_2d(tileA(s, q), m, kb * OZ_BK, t.ti * 128, full(s));
+              tma_load_2d(tileA(s, slot), m, k0, t.ti * 128, full(s));
             } else {
-              tma_load_2d(tileA(s, q), mm, t.ti * 128, kb * OZ_BK, full(s));
-              tma_load_2d(tileA(s, q) + OZ_DTILE / 2, mm, t.ti * 128 + 64, kb * OZ_BK, full(s));
+              tma_load_2d(tileA(s, slot), mm, t.ti * 128, k0, full(s));
+              tma_load_2d(tileA(s, slot) + OZ_DTILE / 2, mm, t.ti * 128 + 64, k0, full(s));
             }
             if (dg) continue;
             if (kt <= t.tj) {
-              tma_load_2d(tileB(s, q), m, kb * OZ_BK, t.tj * 128, full(s));
+              tma_load_2d(tileB(s, slot), m, k0, t.tj * 128, full(s));
             } else {
-              tma_load_2d(tileB(s, q), mm, t.tj * 128, kb * OZ_BK, full(s));
-              tma_load_2d(tileB(s, q) + OZ_DTILE / 2, mm, t.tj * 128 + 64, kb * OZ_BK, full(s));
+              tma_load_2d(tileB(s, slot), mm, t.tj * 128, k0, full(s));
+              tma_load_2d(tileB(s, slot) + OZ_DTILE / 2, mm, t.tj * 128 + 64, k0, full(s));
             }
           }
         }
@@ -275,9 +284,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
     bool bad = false;
     for (int ti = blockIdx.x; ti < a.ntiles && !bad; ti += gridDim.x, ++u) {
       const Tile t = a.tiles[ti];
-      const int nk = (a.parts[t.part].s + OZ_BK - 1) / OZ_BK;
+      const int sz = a.parts[t.part].s;
       const bool dg = t.ti == t.tj;
       for (int pass = 0; pass < 2 && !bad; ++pass) {
+        const int sub = pass == 0 ? 1 : OZ_LOW_SUB;
+        const int nk = (sz + sub * OZ_BK - 1) / (sub * OZ_BK);
         // the high pass reuses the columns of the previous tile's low groups, the low pass
         // those of this tile's high groups: wait until the epilogue has read them
         const bool ready = pass == 0 ? (u == 0 || mbar_wait(aempty(1), (u - 1) & 1, abort_flag))
@@ -297,7 +308,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
           // pairs (q, d - q) of every group of the pass; both digits are < d1 <= T.  Operands
           // right of the tile's own block came in MN-major (transpose bits 15 / 16); a K = 16
           // step advances 32 B in a K-major row, 2 KB (16 K values) in an MN-major tile
-          const int kt = kb * OZ_BK / 128;
+          const int kt = kb * sub * OZ_BK / 128;
           const bool amn = kt > t.ti, bmn = kt > t.tj;
           const uint64_t da = amn ? smem_desc_mn128(tileA(s, 0), OZ_DTILE / 2) : smem_desc_sw<2 * OZ_BK>(tileA(s, 0));
           const uint64_t db = dg ? da
@@ -305,8 +316,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
                                         : smem_desc_sw<2 * OZ_BK>(tileB(s, 0)));
           const uint32_t adv_a = amn ? (2048u >> 4) : (32u >> 4), adv_b = bmn ? (2048u >> 4) : (32u >> 4);
           const uint32_t idesc = IDESC | ((amn ? 1u : 0u) << 15) | ((bmn ? 1u : 0u) << 16);
-          if (pass == 0) oz_issue_stage<OZ_SPLIT, T>(tmem, da, db, adv_a, adv_b, idesc, kb == 0);
-          else oz_issue_stage<0, OZ_SPLIT>(tmem, da, db, adv_a, adv_b, idesc, kb == 0);
+          if (pass == 0) {
+            oz_issue_stage<OZ_SPLIT, T>(tmem, da, db, adv_a, adv_b, idesc, kb == 0);
+          } else {
+#pragma unroll
+            for (int u = 0; u < OZ_LOW_SUB; ++u) {  // the stage's K slices, OZ_SPLIT tiles apart
+              const uint64_t off = (uint64_t)(u * OZ_SPLIT) * (OZ_DTILE >> 4);
+              oz_issue_stage<0, OZ_SPLIT>(tmem, da + off, db + off, adv_a, adv_b, idesc, kb == 0 && u == 0);
+            }
+          }
           mma_commit(empty(s));
         }
         if (!bad) mma_commit(afull(pass));
