@@ -674,7 +674,7 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
   auto Sall = (const int32_t*)(w + L.S);
   auto perm = (const int32_t*)(w + L.perm);
   auto tiles = (const Tile*)(w + L.tiles);
-  auto gbl = (const ColBlock*)(w + L.gblocks);
+  auto gbl = (const ColBlock*)(w + L.gblocks_ld);  // every column up to ld, padding zeroed
   auto sbl = (const ColBlock*)(w + L.sblocks);
   auto pcol = (const int64_t*)(w + L.pcolptr);
   auto rp = (const int64_t*)(w + L.rowptr);
@@ -786,7 +786,7 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
       CU(h, cudaMemcpyAsync(alpha_user, alpha + 1, (size_t)h->opt.max_steps + MAX_TAIL, cudaMemcpyDeviceToDevice, s));
     return GSP2_OK;
   }
-  CU(h, launch_gather(parts, gbl, (int)h->gblocks.size(), Sall, rp, ci, hv, A(0), (double*)slots, ctl, s));
+  CU(h, launch_gather(parts, gbl, (int)h->gblocks_ld.size(), Sall, rp, ci, hv, A(0), (double*)slots, ctl, s));
   const bool emu = prec == GSP2_PREC_FP64_EMU;
   OzStepArgs oz{};
   if (emu) {

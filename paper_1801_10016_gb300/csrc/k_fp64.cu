@@ -99,8 +99,9 @@ __global__ void __launch_bounds__(256) gather_kernel(const PartDesc* __restrict_
   const double emax = ctl.st->eps_max, emin = ctl.st->eps_min;
   const double den = emax - emin;
   double tr = 0.0;
-  const int jend = p.nt * SQ_TILE;  // columns [s, nt*TILE) are zero padding read by the squares
-  if (j < jend) {
+  // columns [s, ld) are zero padding: the squares read it up to the tile edge, and the
+  // emulated steps up to ld (their K slices are packed within 128-blocks)
+  if (j < p.ld) {
     double* col = arena + p.off + (int64_t)j * p.ld;
     for (int r = lane; r < p.ld; r += 32) col[r] = 0.0;
     __syncwarp();

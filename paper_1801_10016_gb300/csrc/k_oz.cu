@@ -138,7 +138,6 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const PartDesc* __restric
 // (warp w: TMEM lanes 32 (w % 4) .. + 31, columns 32 ((w - 4) / 4) .. + 31 of each group,
 // in two chunks of 16), sized so that four epilogue warps per scheduler hide latency.
 constexpr int OZ_STAGES = 2;
-constexpr int OZ_LOW_SUB = 2;  // K slices per stage of the low-group pass (it needs OZ_SPLIT digits)
 constexpr uint32_t OZ_DTILE = 128u * OZ_BK * 2u;                 // one digit tile: 128 rows x 64 B
 constexpr uint32_t OZ_STAGE_B = 2u * OZ_SLICES * OZ_DTILE;       // all A and B digit tiles
 constexpr int OZ_EPI_WARPS = 16;                                 // 4 per TMEM lane quarter
@@ -146,8 +145,16 @@ constexpr int OZ_THREADS = 32 * (4 + OZ_EPI_WARPS);
 constexpr int OZ_SMEM = OZ_STAGES * (int)OZ_STAGE_B + 1024 + 8 * (2 * OZ_STAGES + 4) + 16 + 16 * OZ_EPI_WARPS;
 static_assert(OZ_SLICES - OZ_SPLIT <= 4 && OZ_SPLIT <= 4, "groups of one pass must fit in 512 TMEM columns");
 static_assert(OZ_SMEM <= 232448, "shared memory of the emulated step");
-static_assert(2 * OZ_LOW_SUB * OZ_SPLIT <= 2 * OZ_SLICES && OZ_LOW_SUB * OZ_BK <= 128,
-              "low-pass stage: its tiles fit a stage and its slices one 128-block of K");
+
+// K slices per stage: as many as the stage's 2 T tile slots hold (a slice needs nd digit tiles
+// of A, and as many of B unless the tile is diagonal), at most one 128-block of K, a power of 2
+// so that the slices of a stage never cross a 128-block.
+__host__ __device__ constexpr int oz_slices_per_stage(int nd, bool diag) {
+  const int fit = (2 * OZ_SLICES) / ((diag ? 1 : 2) * nd), cap = 128 / OZ_BK;
+  const int m = fit < cap ? fit : cap;
+  return m >= 4 ? 4 : (m >= 2 ? 2 : 1);
+}
+static_assert(oz_slices_per_stage(OZ_SLICES, false) >= 1, "a high-pass slice fits a stage");
 
 __device__ __forceinline__ uint32_t oz_group_col(int d) {
   return (uint32_t)(d >= OZ_SPLIT ? 128 * (d - OZ_SPLIT + 4 - (OZ_SLICES - OZ_SPLIT)) : 128 * d);
@@ -237,7 +244,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
       const bool dg = t.ti == t.tj;
       for (int pass = 0; pass < 2 && !bad; ++pass) {
         const int nd = pass == 0 ? T : OZ_SPLIT;  // digits the pass multiplies
-        const int sub = pass == 0 ? 1 : OZ_LOW_SUB; // K slices per stage
+        const int sub = oz_slices_per_stage(nd, dg);
         const int nk = (sz + sub * OZ_BK - 1) / (sub * OZ_BK);
         for (int kb = 0; kb < nk; ++kb, ++g) {
           const int s = g % OZ_STAGES;
@@ -287,7 +294,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
       const int sz = a.parts[t.part].s;
       const bool dg = t.ti == t.tj;
       for (int pass = 0; pass < 2 && !bad; ++pass) {
-        const int sub = pass == 0 ? 1 : OZ_LOW_SUB;
+        const int nd = pass == 0 ? T : OZ_SPLIT;
+        const int sub = oz_slices_per_stage(nd, dg);
         const int nk = (sz + sub * OZ_BK - 1) / (sub * OZ_BK);
         // the high pass reuses the columns of the previous tile's low groups, the low pass
         // those of this tile's high groups: wait until the epilogue has read them
@@ -316,14 +324,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
                                         : smem_desc_sw<2 * OZ_BK>(tileB(s, 0)));
           const uint32_t adv_a = amn ? (2048u >> 4) : (32u >> 4), adv_b = bmn ? (2048u >> 4) : (32u >> 4);
           const uint32_t idesc = IDESC | ((amn ? 1u : 0u) << 15) | ((bmn ? 1u : 0u) << 16);
-          if (pass == 0) {
-            oz_issue_stage<OZ_SPLIT, T>(tmem, da, db, adv_a, adv_b, idesc, kb == 0);
-          } else {
-#pragma unroll
-            for (int u = 0; u < OZ_LOW_SUB; ++u) {  // the stage's K slices, OZ_SPLIT tiles apart
-              const uint64_t off = (uint64_t)(u * OZ_SPLIT) * (OZ_DTILE >> 4);
-              oz_issue_stage<0, OZ_SPLIT>(tmem, da + off, db + off, adv_a, adv_b, idesc, kb == 0 && u == 0);
-            }
+          for (int u = 0; u < sub; ++u) {  // the stage's K slices, nd tiles apart
+            const uint64_t off = (uint64_t)(u * nd) * (OZ_DTILE >> 4);
+            if (pass == 0) oz_issue_stage<OZ_SPLIT, T>(tmem, da + off, db + off, adv_a, adv_b, idesc, kb == 0 && u == 0);
+            else oz_issue_stage<0, OZ_SPLIT>(tmem, da + off, db + off, adv_a, adv_b, idesc, kb == 0 && u == 0);
           }
           mma_commit(empty(s));
         }
