@@ -360,7 +360,10 @@ __global__ void __launch_bounds__(384, 1) square_tc_persistent_kernel(TcStepArgs
       const PartDesc p = a.parts[t.part];
       const CUtensorMap* mhi = reinterpret_cast<const CUtensorMap*>(a.map_hi[bi]) + t.part;
       const CUtensorMap* mlo = reinterpret_cast<const CUtensorMap*>(a.map_lo[bi]) + t.part;
-      const int nk = (p.s + BKE - 1) / BKE;
+      // a diagonal tile needs rows I only (B = A): two K blocks per stage
+      const bool dg = t.ti == t.tj;
+      const int sub = dg ? 2 : 1;
+      const int nk = (p.s + sub * BKE - 1) / (sub * BKE);
       for (int kb = 0; kb < nk; ++kb, ++g) {
         const int s = g % STAGES;
         if (g >= STAGES && !mbar_wait(empty(s), ((g / STAGES) - 1) & 1, abort_flag)) {
@@ -368,12 +371,20 @@ __global__ void __launch_bounds__(384, 1) square_tc_persistent_kernel(TcStepArgs
           break;
         }
         mbar_expect_tx(full(s), STAGE_B);
-        const int k0 = kb * BKE;
-        tma_load_2d(tile_addr(s, 0), mhi, k0, t.ti * 128, full(s));
-        tma_load_2d(tile_addr(s, 1), mhi, k0, t.tj * 128, full(s));
-        if (NPROD == 3) {
-          tma_load_2d(tile_addr(s, 2), mlo, k0, t.ti * 128, full(s));
-          tma_load_2d(tile_addr(s, 3), mlo, k0, t.tj * 128, full(s));
+        if (dg) {
+          for (int u = 0; u < 2; ++u) {
+            const int k0 = (2 * kb + u) * BKE;
+            tma_load_2d(tile_addr(s, u * (NOPS / 2)), mhi, k0, t.ti * 128, full(s));
+            if (NPROD == 3) tma_load_2d(tile_addr(s, u * 2 + 1), mlo, k0, t.ti * 128, full(s));
+          }
+        } else {
+          const int k0 = kb * BKE;
+          tma_load_2d(tile_addr(s, 0), mhi, k0, t.ti * 128, full(s));
+          tma_load_2d(tile_addr(s, 1), mhi, k0, t.tj * 128, full(s));
+          if (NPROD == 3) {
+            tma_load_2d(tile_addr(s, 2), mlo, k0, t.ti * 128, full(s));
+            tma_load_2d(tile_addr(s, 3), mlo, k0, t.tj * 128, full(s));
+          }
         }
       }
     }
@@ -391,7 +402,8 @@ __global__ void __launch_bounds__(384, 1) square_tc_persistent_kernel(TcStepArgs
     for (int ti = blockIdx.x; ti < a.ntiles && !bad; ti += gridDim.x, ++i) {
       const Tile t = a.tiles[ti];
       const PartDesc p = a.parts[t.part];
-      const int nk = (p.s + BKE - 1) / BKE;
+      const bool dg = t.ti == t.tj;
+      const int nk = (p.s + (dg ? 2 : 1) * BKE - 1) / ((dg ? 2 : 1) * BKE);
       const int b = i & 1, u = i >> 1;
       if (u >= 1 && !mbar_wait(tempty(b), (u - 1) & 1, abort_flag)) {
         bad = true;
@@ -406,15 +418,25 @@ __global__ void __launch_bounds__(384, 1) square_tc_persistent_kernel(TcStepArgs
           break;
         }
         tc_fence_after();
-        const uint64_t ah = smem_desc(tile_addr(s, 0)), bh = smem_desc(tile_addr(s, 1));
-        const uint64_t al = smem_desc(tile_addr(s, 2)), bl = smem_desc(tile_addr(s, 3));
+        for (int v = 0; v < (dg ? 2 : 1); ++v) {  // K blocks of the stage, in K order
+          uint64_t ah, bh, al, bl;
+          if (dg) {
+            ah = bh = smem_desc(tile_addr(s, v * (NOPS / 2)));
+            al = bl = smem_desc(tile_addr(s, v * 2 + 1));
+          } else {
+            ah = smem_desc(tile_addr(s, 0));
+            bh = smem_desc(tile_addr(s, 1));
+            al = smem_desc(tile_addr(s, 2));
+            bl = smem_desc(tile_addr(s, 3));
+          }
 #pragma unroll
-        for (int kk = 0; kk < NMMA; ++kk) {
-          const uint64_t adv = (uint64_t)((kk * KMMA * ES) >> 4);
-          mma<KIND>(d, ah + adv, bh + adv, IDESC, (kb > 0 || kk > 0) ? 1u : 0u);
-          if (NPROD == 3) {
-            mma<KIND>(d, ah + adv, bl + adv, IDESC, 1u);
-            mma<KIND>(d, al + adv, bh + adv, IDESC, 1u);
+          for (int kk = 0; kk < NMMA; ++kk) {
+            const uint64_t adv = (uint64_t)((kk * KMMA * ES) >> 4);
+            mma<KIND>(d, ah + adv, bh + adv, IDESC, (kb > 0 || v > 0 || kk > 0) ? 1u : 0u);
+            if (NPROD == 3) {
+              mma<KIND>(d, ah + adv, bl + adv, IDESC, 1u);
+              mma<KIND>(d, al + adv, bh + adv, IDESC, 1u);
+            }
           }
         }
         mma_commit(empty(s));
