@@ -38,14 +38,15 @@ __device__ __forceinline__ void store_operands(void* hi, void* lo, int64_t e, fl
   }
 }
 
-// Store the operand(s) of 32 consecutive elements x[0..31] starting at element e
-// (16-byte aligned) with vector stores.
-template <int KIND, int NPROD>
-__device__ __forceinline__ void store_operand_row(void* hi, void* lo, int64_t e, const float (&x)[32]) {
+// Store the operand(s) of N consecutive elements x[0..N-1] (N a multiple of 8) starting at
+// element e (16-byte aligned) with vector stores.
+template <int KIND, int NPROD, int N>
+__device__ __forceinline__ void store_operand_row(void* hi, void* lo, int64_t e, const float (&x)[N]) {
+  static_assert(N % 8 == 0, "whole 16-byte vectors");
   if (KIND == 0) {
-    uint32_t hw[16], lw[16];
+    uint32_t hw[N / 2], lw[N / 2];
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
+    for (int q = 0; q < N / 2; ++q) {
       const uint16_t h0 = Operand<0>::bits(x[2 * q]), h1 = Operand<0>::bits(x[2 * q + 1]);
       hw[q] = (uint32_t)h0 | ((uint32_t)h1 << 16);
       if (NPROD == 3) {
@@ -56,17 +57,17 @@ __device__ __forceinline__ void store_operand_row(void* hi, void* lo, int64_t e,
     }
     uint4* dh = reinterpret_cast<uint4*>(reinterpret_cast<uint16_t*>(hi) + e);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) dh[q] = make_uint4(hw[4 * q], hw[4 * q + 1], hw[4 * q + 2], hw[4 * q + 3]);
+    for (int q = 0; q < N / 8; ++q) dh[q] = make_uint4(hw[4 * q], hw[4 * q + 1], hw[4 * q + 2], hw[4 * q + 3]);
     if (NPROD == 3) {
       uint4* dl = reinterpret_cast<uint4*>(reinterpret_cast<uint16_t*>(lo) + e);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) dl[q] = make_uint4(lw[4 * q], lw[4 * q + 1], lw[4 * q + 2], lw[4 * q + 3]);
+      for (int q = 0; q < N / 8; ++q) dl[q] = make_uint4(lw[4 * q], lw[4 * q + 1], lw[4 * q + 2], lw[4 * q + 3]);
     }
   } else {
     uint4* dh = reinterpret_cast<uint4*>(reinterpret_cast<uint32_t*>(hi) + e);
     uint4* dl = reinterpret_cast<uint4*>(reinterpret_cast<uint32_t*>(lo) + e);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
+    for (int q = 0; q < N / 4; ++q) {
       uint32_t h[4], l[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
@@ -251,7 +252,7 @@ __global__ void __launch_bounds__(256, 2) square_tc_kernel(TcStepArgs a) {
         float4* dst = reinterpret_cast<float4*>(Xo + e0);
 #pragma unroll
         for (int q = 0; q < 8; ++q) dst[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
-        store_operand_row<KIND, NPROD>(ohi, olo, p.off + e0, x);
+        store_operand_row<KIND, NPROD, 32>(ohi, olo, p.off + e0, x);
       }
     }
   }
@@ -288,12 +289,16 @@ __global__ void __launch_bounds__(256, 2) square_tc_kernel(TcStepArgs a) {
 
 // Persistent variant: one CTA per SM walks the tiles blockIdx.x, blockIdx.x + gridDim.x,
 // ... (largest parts first).  Two TMEM accumulators let the epilogue of one tile run
-// while the tensor cores work on the next.  12 warps: warp 0 lane 0 issues TMA loads,
-// warp 1 owns TMEM and its lane 0 issues tcgen05.mma, warps 4..11 drain TMEM (warp w:
-// lanes 32 (w % 4) .. + 31, column half (w - 4) / 4).  Same arithmetic and the same
+// while the tensor cores work on the next.  20 warps: warp 0 lane 0 issues TMA loads,
+// warp 1 owns TMEM and its lane 0 issues tcgen05.mma, warps 4..19 drain TMEM (four per
+// lane quarter, so that the epilogue, which writes the master and operand copies of the
+// tile and its mirror, keeps up with the tensor cores).  Same arithmetic and the same
 // bookkeeping as square_tc_kernel.
+constexpr int TC_EPI_WARPS = 16;  // 4 per TMEM lane quarter, 32 columns each
+constexpr int TC_THREADS = 32 * (4 + TC_EPI_WARPS);
+
 template <int KIND, int NPROD>
-__global__ void __launch_bounds__(384, 1) square_tc_persistent_kernel(TcStepArgs a) {
+__global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcStepArgs a) {
   constexpr int NOPS = NPROD == 3 ? 4 : 2;
   constexpr int STAGES = NPROD == 3 ? 3 : 4;
   constexpr uint32_t STAGE_B = NOPS * kTileBytes;
@@ -337,7 +342,7 @@ __global__ void __launch_bounds__(384, 1) square_tc_persistent_kernel(TcStepArgs
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull(b), 1);
-      mbar_init(tempty(b), 8);
+      mbar_init(tempty(b), TC_EPI_WARPS);
     }
     *s_err = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -445,8 +450,9 @@ __global__ void __launch_bounds__(384, 1) square_tc_persistent_kernel(TcStepArgs
     }
     if (bad) *s_err = 1;
   } else if (warp >= 4) {
-    // epilogue
-    const int quarter = warp & 3, half = (warp - 4) >> 2;
+    // epilogue: warp w drains TMEM lanes 32 (w % 4) .. + 31, columns 32 ((w - 4) / 4) .. + 31,
+    // in two halves of 16
+    const int quarter = warp & 3, colq = (warp - 4) >> 2;
     const int m = quarter * 32 + lane;
     int i = 0;
     for (int ti = blockIdx.x; ti < a.ntiles; ti += gridDim.x, ++i) {
@@ -470,16 +476,16 @@ __global__ void __launch_bounds__(384, 1) square_tc_persistent_kernel(TcStepArgs
       double tY = 0.0, tN = 0.0;
       if (ok) {
 #pragma unroll 1
-        for (int cc = 0; cc < 2; ++cc) {
-          const int cb = half * 2 + cc;
-          const int cbase = c0 + cb * 32;
-          uint32_t v[32];
-          tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 128 + cb * 32), v);
-          float x[32];
+        for (int h = 0; h < 2; ++h) {
+          const int cl = colq * 32 + h * 16;
+          const int cbase = c0 + cl;
+          uint32_t v[16];
+          tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 128 + cl), v);
+          float x[16];
 #pragma unroll
-          for (int j = 0; j < 32; ++j) x[j] = Xi[(int64_t)(cbase + j) * ld + r];
+          for (int j = 0; j < 16; ++j) x[j] = Xi[(int64_t)(cbase + j) * ld + r];
 #pragma unroll
-          for (int j = 0; j < 32; ++j) {
+          for (int j = 0; j < 16; ++j) {
             const float y = __uint_as_float(v[j]);
             const float z = (alf > 0) ? (2.0f * x[j] - y) : y;
             if (diag && cbase + j == r && r < p.c) {
@@ -488,18 +494,18 @@ __global__ void __launch_bounds__(384, 1) square_tc_persistent_kernel(TcStepArgs
             }
             x[j] = z;
           }
-#pragma unroll
           // diagonal tiles: keep the upper triangle (c >= r) and mirror it, so X stays exactly
           // symmetric whatever order the tensor cores sum the split products in
-          for (int j = 0; j < 32; ++j) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
             if (t.ti == t.tj && cbase + j < r) continue;
             const int64_t e = (int64_t)(cbase + j) * ld + r;
             Xo[e] = x[j];
             store_operands<KIND, NPROD>(ohi, olo, p.off + e, x[j]);
           }
           if (t.ti == t.tj && cbase <= r) {
-            // the 32 x 32 blocks of a diagonal tile that straddle the diagonal: element stores
-            for (int j = 0; j < 32; ++j) {
+            // the 16 x 16 blocks of a diagonal tile that straddle the diagonal: element stores
+            for (int j = 0; j < 16; ++j) {
               if (cbase + j <= r) continue;
               const int64_t e = (int64_t)r * ld + cbase + j;
               Xo[e] = x[j];
@@ -510,8 +516,8 @@ __global__ void __launch_bounds__(384, 1) square_tc_persistent_kernel(TcStepArgs
             const int64_t e0 = (int64_t)r * ld + cbase;
             float4* dst = reinterpret_cast<float4*>(Xo + e0);
 #pragma unroll
-            for (int q = 0; q < 8; ++q) dst[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
-            store_operand_row<KIND, NPROD>(ohi, olo, p.off + e0, x);
+            for (int q = 0; q < 4; ++q) dst[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+            store_operand_row<KIND, NPROD, 16>(ohi, olo, p.off + e0, x);
           }
         }
       } else {
@@ -521,20 +527,20 @@ __global__ void __launch_bounds__(384, 1) square_tc_persistent_kernel(TcStepArgs
       __syncwarp();
       if (lane == 0) mbar_arrive(tempty(b));
       if (diag) {
-        // fixed-order reduction over the 8 epilogue warps (named barrier 1, 256 threads)
+        // fixed-order reduction over the epilogue warps (named barrier 1)
         tY = warp_sum(tY);
         tN = warp_sum(tN);
         if (lane == 0) red[warp - 4] = make_double2(tY, tN);
-        asm volatile("bar.sync 1, 256;\n" ::: "memory");
+        asm volatile("bar.sync 1, %0;\n" ::"n"(32 * TC_EPI_WARPS) : "memory");
         if (warp == 4 && lane == 0) {
           double2 acc = make_double2(0.0, 0.0);
-          for (int w = 0; w < 8; ++w) {
+          for (int w = 0; w < TC_EPI_WARPS; ++w) {
             acc.x += red[w].x;
             acc.y += red[w].y;
           }
           a.slots[t.slot] = acc;
         }
-        asm volatile("bar.sync 1, 256;\n" ::: "memory");
+        asm volatile("bar.sync 1, %0;\n" ::"n"(32 * TC_EPI_WARPS) : "memory");
       }
     }
   }
@@ -572,11 +578,11 @@ template <int KIND, int NPROD>
 static cudaError_t launch_tc_persistent(const TcStepArgs& a, int grid, cudaStream_t s) {
   constexpr int NOPS = NPROD == 3 ? 4 : 2;
   constexpr int STAGES = NPROD == 3 ? 3 : 4;
-  const int smem = STAGES * NOPS * (int)kTileBytes + 1024 + 8 * (2 * STAGES + 4) + 16 + 8 * 16;
+  const int smem = STAGES * NOPS * (int)kTileBytes + 1024 + 8 * (2 * STAGES + 4) + 16 + 16 * TC_EPI_WARPS;
   cudaError_t e = cudaFuncSetAttribute(square_tc_persistent_kernel<KIND, NPROD>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  square_tc_persistent_kernel<KIND, NPROD><<<grid, 384, smem, s>>>(a);
+  square_tc_persistent_kernel<KIND, NPROD><<<grid, TC_THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
 
