@@ -294,6 +294,11 @@ __global__ void __launch_bounds__(256, 2) square_simt_kernel(const PartDesc* __r
   T* Y = xout + p.off;
   double tY = 0.0, tN = 0.0;
   const int rb = r0 + tx * 4, cb = c0 + ty * 4;
+  // rb and cb are multiples of 4: a thread's block meets the diagonal only when rb == cb,
+  // at (i, i); its entries are added in FP64 outside the unrolled loop
+  T yd[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) yd[i] = acc[i][i];
 #pragma unroll
   for (int jj = 0; jj < 4; ++jj) {
     const int c = cb + jj;
@@ -304,10 +309,6 @@ __global__ void __launch_bounds__(256, 2) square_simt_kernel(const PartDesc* __r
     for (int i = 0; i < 4; ++i) {
       const T y = acc[i][jj];
       const T xn = (al > 0) ? (T(2) * xv[i] - y) : y;
-      if (book && t.slot >= 0 && rb + i == c && c < p.c) {
-        tY += (double)y;
-        tN += (double)xn;
-      }
       acc[i][jj] = xn;
     }
     V2 v;
@@ -315,6 +316,13 @@ __global__ void __launch_bounds__(256, 2) square_simt_kernel(const PartDesc* __r
     *reinterpret_cast<V2*>(Y + (int64_t)c * ld + rb) = v;
     v.x = acc[2][jj]; v.y = acc[3][jj];
     *reinterpret_cast<V2*>(Y + (int64_t)c * ld + rb + 2) = v;
+  }
+  if (book && t.slot >= 0 && rb == cb) {
+    for (int i = 0; i < 4; ++i) {
+      if (cb + i >= p.c) break;
+      tY += (double)yd[i];
+      tN += (double)acc[i][i];
+    }
   }
   if (t.ti != t.tj) {
 #pragma unroll

@@ -222,14 +222,19 @@ __global__ void __launch_bounds__(256, 2) square_tc_kernel(TcStepArgs a) {
 #pragma unroll
       for (int j = 0; j < 32; ++j) x[j] = Xi[(int64_t)(cbase + j) * ld + r];
 #pragma unroll
+      // the one diagonal entry of this row segment, if any, picked out in FP32 and added in
+      // FP64 once (an FP64 add in the unrolled loop would be issued for every element)
+      float yd = 0.0f, zd = 0.0f;
       for (int j = 0; j < 32; ++j) {
         const float y = __uint_as_float(v[j]);
         const float z = (al > 0) ? (2.0f * x[j] - y) : y;
-        if (diag && cbase + j == r && r < p.c) {
-          tY += (double)y;
-          tN += (double)z;
-        }
+        yd = (cbase + j == r) ? y : yd;
+        zd = (cbase + j == r) ? z : zd;
         x[j] = z;
+      }
+      if (diag && r >= cbase && r < cbase + 32 && r < p.c) {
+        tY += (double)yd;
+        tN += (double)zd;
       }
 #pragma unroll
       // diagonal tiles: keep the upper triangle (c >= r) and mirror it, so X stays exactly
@@ -484,15 +489,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
           float x[16];
 #pragma unroll
           for (int j = 0; j < 16; ++j) x[j] = Xi[(int64_t)(cbase + j) * ld + r];
+          // the one diagonal entry of this half row, if any, picked out in FP32 and added in
+          // FP64 once (an FP64 add in the unrolled loop would be issued for every element)
+          float yd = 0.0f, zd = 0.0f;
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
             const float y = __uint_as_float(v[j]);
             const float z = (alf > 0) ? (2.0f * x[j] - y) : y;
-            if (diag && cbase + j == r && r < p.c) {
-              tY += (double)y;
-              tN += (double)z;
-            }
+            yd = (cbase + j == r) ? y : yd;
+            zd = (cbase + j == r) ? z : zd;
             x[j] = z;
+          }
+          if (diag && r >= cbase && r < cbase + 16 && r < p.c) {
+            tY += (double)yd;
+            tN += (double)zd;
           }
           // diagonal tiles: keep the upper triangle (c >= r) and mirror it, so X stays exactly
           // symmetric whatever order the tensor cores sum the split products in

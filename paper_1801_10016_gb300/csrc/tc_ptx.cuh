@@ -155,10 +155,14 @@ struct Operand<0> {
 };
 template <>
 struct Operand<1> {
+  // TF32 (10 fraction bits), round to nearest with ties away from zero, in two integer
+  // instructions: adding half of the 13 dropped bits to the sign-magnitude pattern and
+  // clearing them rounds the magnitude up exactly when the dropped part is at least half.
+  // Non-finite values pass unchanged.
   static __device__ __forceinline__ uint32_t bits(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
-    return r;
+    const uint32_t u = __float_as_uint(x);
+    if ((u & 0x7F800000u) == 0x7F800000u) return u;
+    return (u + 0x1000u) & 0xFFFFE000u;
   }
   static __device__ __forceinline__ float value(uint32_t b) { return __uint_as_float(b); }
 };
