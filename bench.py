@@ -253,6 +253,53 @@ def kernel_avg_ms(step_ms, nwork):
     return sum(work) / max(1, len(work)), sum(work)
 
 
+def adjoint_block(dev, peaks, src, workload="tb4k", reps=3):
+    """gsp2_backward of L = sum Pbar .* P on the 4,096-orbital, 32-part workload, FP64 and
+    FP32, checkpoints every 8 steps: device time per backward (after a density call) and the
+    reverse sweep's algorithmic flops (every reverse step 2 s^2 (s+1) per part, every rebuilt
+    iterate s^2 (s+1)) against the FP64 / FP32 CUDA-core peak."""
+    import numpy as np
+    import torch
+    from paper_1801_10016_gb300.gsp2 import GSP2
+    s = make_system(workload)
+    h = torch.from_numpy(s.vals).to(dev)
+    out = {"workload": workload, "checkpoint_every": 8}
+    for prec in ("fp64", "fp32"):
+        plan = GSP2(s.n, s.rowptr, s.colind, s.nocc, s.part, s.nparts, s.g_rowptr, s.g_colind, device=dev,
+                    precision=prec, ckpt_every=8, fp64_tail_steps=0)
+        rng = np.random.default_rng(5678)
+        pbar = torch.from_numpy(rng.standard_normal(plan.nnz_p)).to(dev)
+        ms = []
+        for r in range(reps + 2):
+            plan.density(h)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            plan.backward(pbar)
+            e1.record()
+            torch.cuda.synchronize()
+            if r >= 2:
+                ms.append(e0.elapsed_time(e1))
+        _, rep = plan.status()
+        n = int(rep["steps"])
+        plan.close()
+        sz = plan.part_sizes.astype(np.float64)
+        w = float(np.sum(sz * sz * (sz + 1.0)))
+        rebuilt = sum(1 for i in range(1, n) if i % 8 != 0)
+        flops = (2.0 * n + rebuilt) * w
+        t = statistics.median(ms) / 1e3
+        if prec == "fp64":
+            peak, psrc = peaks["bf16_tflops"] * NOMINAL["fp64"] / NOMINAL["bf16"], f"{src} bf16 x nominal fp64/bf16"
+        else:
+            peak, psrc = 152 * 128 * 2 * 2.07e9 / 1e12, "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"
+        out[prec] = {"ms_per_backward": 1e3 * t, "steps": n, "rebuilt_iterates": rebuilt,
+                     "roofline": {"bound": "alu", "achieved": flops / t / 1e12, "peak": peak, "unit": "TFLOP/s",
+                                  "frac": flops / t / 1e12 / peak, "peak_source": psrc,
+                                  "kernel": f"adj_step_kernel<{'double' if prec == 'fp64' else 'float'}> + "
+                                            f"square_simt_kernel recompute",
+                                  "flops": "reverse steps 2 s^2 (s+1) + rebuilt iterates s^2 (s+1), per part"}}
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -458,6 +505,9 @@ def run_ours(args):
                               "idem_fro: sqrt(sum_k ||(X_k^2 - X_k)[:, cores]||^2 / N) from the library's FP64 "
                               "report pass")
 
+    if rank == 0 and not args.no_adjoint:
+        line["adjoint"] = adjoint_block(dev, peaks, src)
+
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t_cpu, _ = oracle_build_seconds(s, args.max_steps)
         line["cpu_baseline"] = {"value": 1.0 / t_cpu, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
@@ -484,6 +534,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="no_cpu_baseline", action="store_true")
     ap.add_argument("--no-mixed", dest="no_mixed", action="store_true")
     ap.add_argument("--no-autotune", dest="no_autotune", action="store_true")
+    ap.add_argument("--no-adjoint", dest="no_adjoint", action="store_true")
     ap.add_argument("--mixed", default="tf32x3,tf32x3:lp1:fp1,tf32x3:lp2,bf16x3,bf16x3:lp2,tf32,bf16,fp32")
     args = ap.parse_args()
     if args.impl == "reference":
