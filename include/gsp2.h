@@ -110,7 +110,11 @@ typedef struct {
                               1 = the same list reversed in every other round of SMs, so that
                               each SM's share of the uneven tiles evens out; set by
                               gsp2_autotune */
-  int32_t reserved[2];
+  int32_t tile_shape;      /* output tiles of the persistent tensor-core steps: 0 (default)
+                              128 x 128; 1 = 128 x 256 (two upper tiles of a row block per
+                              MMA, N = 256, halving the loads of the A operand); set by
+                              gsp2_autotune */
+  int32_t reserved[1];
 } gsp2_options;
 
 /* Per-call report, read back by gsp2_sync_status. */
@@ -144,8 +148,9 @@ typedef struct {
   int32_t ld_pad;       /* padding multiple of ld_k */
   int32_t step_launches;   /* purification-step launches per density call (the loop's) */
   int32_t fp64_tail_steps; /* resolved value of the option */
-  int32_t tc_schedule;     /* schedule and tile order in use (options, or gsp2_autotune's choice) */
+  int32_t tc_schedule;     /* schedule, tile order and tile shape in use (options, or gsp2_autotune's choice) */
   int32_t tile_order;
+  int32_t tile_shape;
 } gsp2_plan_info;
 
 /* Fill `opt` with the defaults listed above. */
@@ -254,17 +259,19 @@ gsp2_status gsp2_threshold_graph(gsp2_handle h, const double* d_pvals, double ta
 typedef struct {
   int32_t ncand;        /* candidates timed (1 when the precision has no choice) */
   int32_t chosen;       /* index of the fastest, now in use */
-  int32_t tc_schedule[4];
-  int32_t tile_order[4];
-  double ms[4];         /* median device time of one density call, milliseconds */
+  int32_t tc_schedule[8];
+  int32_t tile_order[8];
+  int32_t tile_shape[8];
+  double ms[8];         /* median device time of one density call, milliseconds */
 } gsp2_tune_report;
 
 /*
  * Autotuner of the step schedule (batching of uneven parts, not in the paper): times whole
  * density calls (RECORD mode, `trials` >= 1 each after one untimed call) with every candidate
  * that applies to the plan's precision -- tensor-core steps: persistent with either tile
- * order, and one CTA per tile; FP64_EMU steps: either tile order; FP64 and FP32: the only
- * schedule -- and keeps the fastest in the plan (gsp2_plan_query reports it).  Every
+ * order and either tile shape, and one CTA per tile; FP64_EMU steps: either tile order;
+ * FP64 and FP32: the only schedule -- and keeps the fastest in the plan (gsp2_plan_query
+ * reports it).  Every
  * candidate computes bitwise the same P (a tile's arithmetic does not depend on the CTA
  * that runs it).
  *  d_hvals, d_pvals  as for gsp2_density; d_pvals is overwritten

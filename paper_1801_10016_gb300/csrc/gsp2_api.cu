@@ -20,7 +20,8 @@ namespace {
 constexpr int BOUNDS_BLOCKS = 608;  // 152 SMs x 4
 
 struct WsLayout {
-  size_t parts, S, perm, invperm, tiles, tc_tiles, gblocks, gblocks_ld, sblocks, pcolptr, rowptr, colind;
+  size_t parts, S, perm, invperm, tiles, tc_tiles, tc_wide, tc_wide_nb, gblocks, gblocks_ld, sblocks, pcolptr, rowptr,
+      colind;
   size_t memptr, mempart, memloc;
   // low-precision paths
   size_t mf[2];        // FP32 master copies of X (ping-pong)
@@ -69,6 +70,10 @@ struct gsp2_plan {
   std::vector<Tile> tiles;                 // 64x64 upper tiles (CUDA-core steps)
   std::vector<Tile> tc_tiles;              // 128x128 upper tiles (tensor-core steps)
   std::vector<Tile> tc_order;              // tc_tiles in the order of opt.tile_order (uploaded)
+  std::vector<Tile> tc_wide;               // tile_shape 1: one or two column blocks per tile
+  std::vector<int8_t> tc_wide_nb;
+  std::vector<Tile> tcw_order;             // tc_wide / tc_wide_nb in the order of opt.tile_order
+  std::vector<int8_t> tcw_nb_order;
   std::vector<size_t> mf_of_step;          // low precision: FP32 arena of iterate i (checkpoints or ping-pong)
   std::vector<ColBlock> gblocks, sblocks;  // gather (to nt*64) and scatter (cores) columns
   std::vector<ColBlock> gblocks_ld;        // low-precision gather: every column up to ld
@@ -205,6 +210,8 @@ static void build_layout(gsp2_plan* h) {
   L.memloc = take(h->memloc.size() * sizeof(int32_t));
   L.tiles = take(h->tiles.size() * sizeof(Tile));
   L.tc_tiles = take(h->tc_tiles.size() * sizeof(Tile));
+  L.tc_wide = take(h->tc_wide.size() * sizeof(Tile));
+  L.tc_wide_nb = take(h->tc_wide_nb.size());
   L.gblocks = take(h->gblocks.size() * sizeof(ColBlock));
   L.gblocks_ld = take(h->gblocks_ld.size() * sizeof(ColBlock));
   L.sblocks = take(h->sblocks.size() * sizeof(ColBlock));
@@ -330,6 +337,7 @@ extern "C" gsp2_status gsp2_create(int64_t n, const int64_t* rowptr, const int32
       return bail(GSP2_E_ARG, "lp_tail_steps must be >= 0 with lp_tail_steps + fp64_tail_steps <= 8");
     if (o.tc_schedule < 0 || o.tc_schedule > 1) return bail(GSP2_E_ARG, "tc_schedule must be 0 or 1");
     if (o.tile_order < 0 || o.tile_order > 1) return bail(GSP2_E_ARG, "tile_order must be 0 or 1");
+    if (o.tile_shape < 0 || o.tile_shape > 1) return bail(GSP2_E_ARG, "tile_shape must be 0 or 1");
     if (o.lp_tail_steps > 0 && (fp64_like(o.precision) || o.precision == GSP2_PREC_FP32))
       return bail(GSP2_E_ARG, "lp_tail_steps needs a tensor-core precision");
     if (o.ckpt_every < -1) return bail(GSP2_E_ARG, "ckpt_every must be >= -1");
@@ -455,9 +463,17 @@ extern "C" gsp2_status gsp2_create(int64_t n, const int64_t* rowptr, const int32
       for (int32_t j = 0; j < d.nt * SQ_TILE; j += COLS_PER_BLOCK) h->gblocks.push_back(ColBlock{k, j});
       for (int32_t j = 0; j < d.ld; j += COLS_PER_BLOCK) h->gblocks_ld.push_back(ColBlock{k, j});
       const int32_t nt128 = (d.s + TC_TILE - 1) / TC_TILE;
+      const int32_t slot0 = h->nslots_tc;  // diagonal tiles take slots slot0 + ti in both lists
       for (int32_t ti = 0; ti < nt128; ++ti)
         for (int32_t tj = ti; tj < nt128; ++tj)
           h->tc_tiles.push_back(Tile{k, ti, tj, ti == tj ? h->nslots_tc++ : -1});
+      // the same upper tiles two column blocks at a time along each row block (the last
+      // one alone when the row has an odd number)
+      for (int32_t ti = 0; ti < nt128; ++ti)
+        for (int32_t tj = ti; tj < nt128; tj += 2) {
+          h->tc_wide.push_back(Tile{k, ti, tj, ti == tj ? slot0 + ti : -1});
+          h->tc_wide_nb.push_back((int8_t)(tj + 1 < nt128 ? 2 : 1));
+        }
       for (int32_t j = 0; j < d.c; j += COLS_PER_BLOCK) h->sblocks.push_back(ColBlock{k, j});
     }
     h->nslots = slot;
@@ -501,6 +517,7 @@ extern "C" gsp2_status gsp2_plan_query(gsp2_handle h, gsp2_plan_info* info, int3
     info->fp64_tail_steps = h->opt.fp64_tail_steps;
     info->tc_schedule = h->opt.tc_schedule;
     info->tile_order = h->opt.tile_order;
+    info->tile_shape = h->opt.tile_shape;
   }
   for (int32_t k = 0; k < h->nparts; ++k) {
     if (s) s[k] = h->parts[k].s;
@@ -533,13 +550,20 @@ static void drop_graph(gsp2_plan* h) {
 // takes the smallest of the next.
 static void order_tc_tiles(gsp2_plan* h, int grid) {
   h->tc_order = h->tc_tiles;
+  h->tcw_order = h->tc_wide;
+  h->tcw_nb_order = h->tc_wide_nb;
   if (h->opt.tile_order != 1 || grid < 2) return;
   const size_t g = (size_t)grid;
-  for (size_t r = 0; r * g < h->tc_order.size(); ++r)
-    if (r & 1) {
-      const size_t b = r * g, e = std::min(b + g, h->tc_order.size());
-      std::reverse(h->tc_order.begin() + b, h->tc_order.begin() + e);
-    }
+  auto serpentine = [g](auto& v) {
+    for (size_t r = 0; r * g < v.size(); ++r)
+      if (r & 1) {
+        const size_t b = r * g, e = std::min(b + g, v.size());
+        std::reverse(v.begin() + b, v.begin() + e);
+      }
+  };
+  serpentine(h->tc_order);
+  serpentine(h->tcw_order);
+  serpentine(h->tcw_nb_order);
 }
 
 extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t bytes, void* stream) {
@@ -582,6 +606,8 @@ extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t byt
   CU(h, up(L.tiles, h->tiles.data(), h->tiles.size() * sizeof(Tile)));
   order_tc_tiles(h, h->num_sms);
   CU(h, up(L.tc_tiles, h->tc_order.data(), h->tc_order.size() * sizeof(Tile)));
+  CU(h, up(L.tc_wide, h->tcw_order.data(), h->tcw_order.size() * sizeof(Tile)));
+  CU(h, up(L.tc_wide_nb, h->tcw_nb_order.data(), h->tcw_nb_order.size()));
   CU(h, up(L.gblocks_ld, h->gblocks_ld.data(), h->gblocks_ld.size() * sizeof(ColBlock)));
   if (h->use_oz) {
     void* enc = nullptr;
@@ -716,9 +742,11 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
     // tensor-core schedule: persistent (one CTA per SM, overlapped epilogue) or one CTA per tile
     const int pgrid = h->opt.tc_schedule == 0 ? h->num_sms : 0;
     TcStepArgs tc_args{};
+    const bool wide = pgrid > 0 && h->opt.tile_shape == 1;
     if (kind >= 0) {
       tc_args.parts = parts;
-      tc_args.tiles = (const Tile*)(w + L.tc_tiles);
+      tc_args.tiles = (const Tile*)(w + (wide ? L.tc_wide : L.tc_tiles));
+      tc_args.nb = wide ? (const int8_t*)(w + L.tc_wide_nb) : nullptr;
       for (int b = 0; b < 2; ++b) {
         tc_args.map_hi[b] = w + L.maps + (size_t)(2 * b + 0) * np * 128;
         tc_args.map_lo[b] = w + L.maps + (size_t)(2 * b + 1) * np * 128;
@@ -728,7 +756,7 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
       }
       tc_args.slots = slots;
       tc_args.nslots = h->nslots_tc;
-      tc_args.ntiles = (int)h->tc_tiles.size();
+      tc_args.ntiles = (int)(wide ? h->tc_wide.size() : h->tc_tiles.size());
       tc_args.ctl = lp;
       tc_args.tail = 0;
     }
@@ -742,7 +770,7 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
         a.step = i;
         a.master[bi] = mfs(i - 1);
         a.master[bo] = mfs(i);
-        CU(h, launch_square_tc(kind, nprod, a, (int)h->tc_tiles.size(), pgrid, s));
+        CU(h, launch_square_tc(kind, nprod, a, a.ntiles, pgrid, s));
       }
       if (!h->ev.empty()) CU(h, cudaEventRecordWithFlags(h->ev[2 * (i - 1) + 1], s, cudaEventRecordExternal));
     }
@@ -750,7 +778,7 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
     for (int t = 0; t < h->opt.lp_tail_steps; ++t) {
       TcStepArgs a = tc_args;
       a.tail = t == 0 ? 1 : 2;
-      CU(h, launch_square_tc(kind, nprod, a, (int)h->tc_tiles.size(), pgrid, s));
+      CU(h, launch_square_tc(kind, nprod, a, a.ntiles, pgrid, s));
     }
     // FP64 tail: convert the last FP32 iterate, then purification steps in FP64 (native, or
     // with the products rebuilt from BF16 digits)
@@ -876,28 +904,39 @@ extern "C" gsp2_status gsp2_autotune(gsp2_handle h, const double* d_hvals, doubl
   if (!d_hvals || !d_pvals || trials < 1 || trials > 100) return fail(h, GSP2_E_ARG, "NULL buffer or trials not in 1..100");
   cudaStream_t s = (cudaStream_t)stream;
   // candidates (tc_schedule, tile_order) that change something for this precision
-  std::vector<std::pair<int, int>> cand;
+  struct Cand {
+    int sched, order, shape;
+  };
+  std::vector<Cand> cand;
   const int prec = h->opt.precision;
-  if (!fp64_like(prec) && prec_kind(prec) >= 0) cand = {{0, 0}, {0, 1}, {1, 0}};
-  else if (prec == GSP2_PREC_FP64_EMU) cand = {{0, 0}, {0, 1}};
-  else cand = {{h->opt.tc_schedule, h->opt.tile_order}};
+  if (!fp64_like(prec) && prec_kind(prec) >= 0) cand = {{0, 0, 0}, {0, 1, 0}, {0, 0, 1}, {0, 1, 1}, {1, 0, 0}};
+  else if (prec == GSP2_PREC_FP64_EMU) cand = {{0, 0, 0}, {0, 1, 0}};
+  else cand = {{h->opt.tc_schedule, h->opt.tile_order, h->opt.tile_shape}};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CU(h, cudaEventCreate(&e0));
   CU(h, cudaEventCreate(&e1));
-  auto apply = [&](int sched, int order) -> cudaError_t {
-    if (sched != h->opt.tc_schedule) drop_graph(h);  // the schedule is part of the captured launches
-    h->opt.tc_schedule = sched;
-    h->opt.tile_order = order;
+  auto apply = [&](const Cand& c) -> cudaError_t {
+    // schedule and shape are part of the captured launches; the order only of the tile lists
+    if (c.sched != h->opt.tc_schedule || c.shape != h->opt.tile_shape) drop_graph(h);
+    h->opt.tc_schedule = c.sched;
+    h->opt.tile_order = c.order;
+    h->opt.tile_shape = c.shape;
     order_tc_tiles(h, h->num_sms);
     if (h->tc_order.empty()) return cudaSuccess;
     cudaError_t e = cudaMemcpyAsync(h->ws + h->L.tc_tiles, h->tc_order.data(), h->tc_order.size() * sizeof(Tile),
                                     cudaMemcpyHostToDevice, s);
-    return e != cudaSuccess ? e : cudaStreamSynchronize(s);  // the host vector may change next round
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h->ws + h->L.tc_wide, h->tcw_order.data(), h->tcw_order.size() * sizeof(Tile),
+                          cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h->ws + h->L.tc_wide_nb, h->tcw_nb_order.data(), h->tcw_nb_order.size(),
+                          cudaMemcpyHostToDevice, s);
+    return e != cudaSuccess ? e : cudaStreamSynchronize(s);  // the host vectors may change next round
   };
   std::vector<double> med(cand.size(), 0.0);
   gsp2_status out = GSP2_OK;
   for (size_t c = 0; c < cand.size() && out == GSP2_OK; ++c) {
-    cudaError_t e = apply(cand[c].first, cand[c].second);
+    cudaError_t e = apply(cand[c]);
     if (e != cudaSuccess) {
       out = cuda_fail(h, e, "autotune: tile list upload");
       break;
@@ -928,7 +967,7 @@ extern "C" gsp2_status gsp2_autotune(gsp2_handle h, const double* d_hvals, doubl
   if (out == GSP2_OK) {
     for (size_t c = 1; c < cand.size(); ++c)
       if (med[c] < med[best]) best = c;
-    const cudaError_t e = apply(cand[best].first, cand[best].second);
+    const cudaError_t e = apply(cand[best]);
     if (e != cudaSuccess) out = cuda_fail(h, e, "autotune: tile list upload");
   }
   cudaEventDestroy(e0);
@@ -938,8 +977,9 @@ extern "C" gsp2_status gsp2_autotune(gsp2_handle h, const double* d_hvals, doubl
     rep->ncand = (int32_t)cand.size();
     rep->chosen = (int32_t)best;
     for (size_t c = 0; c < cand.size(); ++c) {
-      rep->tc_schedule[c] = cand[c].first;
-      rep->tile_order[c] = cand[c].second;
+      rep->tc_schedule[c] = cand[c].sched;
+      rep->tile_order[c] = cand[c].order;
+      rep->tile_shape[c] = cand[c].shape;
       rep->ms[c] = med[c];
     }
   }

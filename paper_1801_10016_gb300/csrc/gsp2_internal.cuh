@@ -75,7 +75,8 @@ struct StepCtl {
 // X_step written to buffer step&1.
 struct TcStepArgs {
   const PartDesc* parts;
-  const Tile* tiles;       // 128x128 upper tiles
+  const Tile* tiles;       // upper tiles: 128x128, or 128 x 128 nb[t] for the wide persistent kernel
+  const int8_t* nb;        // wide tiles: 128-column blocks of each tile (1 or 2); NULL: 128x128 tiles
   const void* map_hi[2];   // CUtensorMap[nparts] over each operand arena (hi part)
   const void* map_lo[2];   // CUtensorMap[nparts] over each lo arena (split mode)
   float* master[2];        // FP32 master copies of X

@@ -584,6 +584,295 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
   }
 }
 
+// Wide variant (tile_shape 1): each work item covers one or two 128-column blocks of a row
+// block of upper tiles (two tiles per MMA, N = 256), so every A tile feeds twice the MMA
+// work; two 256-column TMEM accumulators.  Stage: A hi (16 KB), A lo, then B hi and B lo of
+// up to 256 rows (32 KB each); a diagonal item takes its A from the first rows of B.  The
+// arithmetic of every output element is that of the 128 x 128 kernels.
+template <int NPROD>
+struct TcWideStage {
+  static constexpr uint32_t A_HI = 0, A_LO = kTileBytes;
+  static constexpr uint32_t B_HI = (NPROD == 3 ? 2 : 1) * kTileBytes;
+  static constexpr uint32_t B_LO = B_HI + 2 * kTileBytes;
+  static constexpr uint32_t BYTES = (NPROD == 3 ? 6 : 3) * kTileBytes;
+  static constexpr int STAGES = NPROD == 3 ? 2 : 4;
+};
+
+template <int KIND, int NPROD>
+__global__ void __launch_bounds__(TC_THREADS, 1) square_tc_wide_kernel(TcStepArgs a) {
+  using SL = TcWideStage<NPROD>;
+  constexpr int STAGES = SL::STAGES;
+  constexpr uint32_t STAGE_B = SL::BYTES;
+  constexpr int ES = KIND == 0 ? 2 : 4;
+  constexpr int BKE = 128 / ES;
+  constexpr int KMMA = KIND == 0 ? 16 : 8;
+  constexpr int NMMA = BKE / KMMA;
+  constexpr uint32_t FMT = KIND == 0 ? 1u : 2u;
+  constexpr uint32_t IDESC0 = (1u << 4) | (FMT << 7) | (FMT << 10) | ((128u >> 4) << 24);  // N set per item
+
+  int step = a.step;
+  if (a.tail) {
+    const int32_t stt = *(volatile int32_t*)&a.ctl.st->status;
+    if (stt == ST_NONFINITE || stt == ST_TIMEOUT) return;
+    step = *(volatile int32_t*)&a.ctl.st->steps + 1;
+  } else if (*(volatile int32_t*)&a.ctl.st->stopped) {
+    return;
+  }
+  const int bi = (step - 1) & 1, bo = step & 1;
+
+  extern __shared__ uint8_t smem_raw[];
+  const uint32_t raw = smem_u32(smem_raw);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  uint8_t* sb = smem_raw + (base - raw);
+  const uint32_t bars = base + STAGES * STAGE_B;  // full[S], empty[S], tfull[2], tempty[2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sb + STAGES * STAGE_B + 8 * (2 * STAGES + 4));
+  int* s_err = reinterpret_cast<int*>(tmem_slot + 1);
+  double2* red = reinterpret_cast<double2*>(sb + STAGES * STAGE_B + 8 * (2 * STAGES + 4) + 16);
+  auto full = [&](int s) { return bars + 8u * s; };
+  auto empty = [&](int s) { return bars + 8u * (STAGES + s); };
+  auto tfull = [&](int b) { return bars + 8u * (2 * STAGES + b); };
+  auto tempty = [&](int b) { return bars + 8u * (2 * STAGES + 2 + b); };
+  auto sa = [&](int s, uint32_t off) { return base + (uint32_t)s * STAGE_B + off; };
+  int32_t* abort_flag = &a.ctl.st->timeout;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full(s), 1);
+      mbar_init(empty(s), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull(b), 1);
+      mbar_init(tempty(b), TC_EPI_WARPS);
+    }
+    *s_err = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;\n" ::"r"(smem_u32(tmem_slot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    uint32_t g = 0;
+    bool bad = false;
+    for (int ti = blockIdx.x; ti < a.ntiles && !bad; ti += gridDim.x) {
+      const Tile t = a.tiles[ti];
+      const int nb = a.nb[ti];
+      const PartDesc p = a.parts[t.part];
+      const CUtensorMap* mhi = reinterpret_cast<const CUtensorMap*>(a.map_hi[bi]) + t.part;
+      const CUtensorMap* mlo = reinterpret_cast<const CUtensorMap*>(a.map_lo[bi]) + t.part;
+      const bool dg = t.ti == t.tj;  // rows I are the first rows of B
+      const uint32_t per = (uint32_t)(NPROD == 3 ? 2 : 1) * kTileBytes;  // one 128-row block, hi (+ lo)
+      const uint32_t bytes = (uint32_t)(nb + (dg ? 0 : 1)) * per;
+      const int nk = (p.s + BKE - 1) / BKE;
+      for (int kb = 0; kb < nk; ++kb, ++g) {
+        const int s = g % STAGES;
+        if (g >= STAGES && !mbar_wait(empty(s), ((g / STAGES) - 1) & 1, abort_flag)) {
+          bad = true;
+          break;
+        }
+        mbar_expect_tx(full(s), bytes);
+        const int k0 = kb * BKE;
+        if (!dg) {
+          tma_load_2d(sa(s, SL::A_HI), mhi, k0, t.ti * 128, full(s));
+          if (NPROD == 3) tma_load_2d(sa(s, SL::A_LO), mlo, k0, t.ti * 128, full(s));
+        }
+        for (int q = 0; q < nb; ++q) {
+          tma_load_2d(sa(s, SL::B_HI + q * kTileBytes), mhi, k0, (t.tj + q) * 128, full(s));
+          if (NPROD == 3) tma_load_2d(sa(s, SL::B_LO + q * kTileBytes), mlo, k0, (t.tj + q) * 128, full(s));
+        }
+      }
+    }
+    if (bad) {
+      *s_err = 1;
+      const uint32_t first = g > STAGES ? g - STAGES : 0;
+      for (uint32_t q = first; q < g; ++q) (void)mbar_wait(full(q % STAGES), (q / STAGES) & 1, abort_flag);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer: item i accumulates in TMEM columns [256 (i & 1), + 128 nb)
+    uint32_t g = 0;
+    int i = 0;
+    bool bad = false;
+    for (int ti = blockIdx.x; ti < a.ntiles && !bad; ti += gridDim.x, ++i) {
+      const Tile t = a.tiles[ti];
+      const int nb = a.nb[ti];
+      const PartDesc p = a.parts[t.part];
+      const bool dg = t.ti == t.tj;
+      const int nk = (p.s + BKE - 1) / BKE;
+      const uint32_t idesc = IDESC0 | ((uint32_t)(128 * nb) >> 3) << 17;
+      const int b = i & 1, u = i >> 1;
+      if (u >= 1 && !mbar_wait(tempty(b), (u - 1) & 1, abort_flag)) {
+        bad = true;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t d = tmem + (uint32_t)(b * 256);
+      for (int kb = 0; kb < nk; ++kb, ++g) {
+        const int s = g % STAGES;
+        if (!mbar_wait(full(s), (g / STAGES) & 1, abort_flag)) {
+          bad = true;
+          break;
+        }
+        tc_fence_after();
+        const uint64_t bh = smem_desc(sa(s, SL::B_HI)), bl = smem_desc(sa(s, SL::B_LO));
+        const uint64_t ah = dg ? bh : smem_desc(sa(s, SL::A_HI)), al = dg ? bl : smem_desc(sa(s, SL::A_LO));
+#pragma unroll
+        for (int kk = 0; kk < NMMA; ++kk) {
+          const uint64_t adv = (uint64_t)((kk * KMMA * ES) >> 4);
+          mma<KIND>(d, ah + adv, bh + adv, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+          if (NPROD == 3) {
+            mma<KIND>(d, ah + adv, bl + adv, idesc, 1u);
+            mma<KIND>(d, al + adv, bh + adv, idesc, 1u);
+          }
+        }
+        mma_commit(empty(s));
+      }
+      mma_commit(tfull(b));
+    }
+    if (bad) *s_err = 1;
+  } else if (warp >= 4) {
+    // epilogue: warp w drains TMEM lanes 32 (w % 4) .. + 31 and 32 nb columns, in 16-column
+    // pieces
+    const int quarter = warp & 3, colq = (warp - 4) >> 2;
+    const int m = quarter * 32 + lane;
+    int i = 0;
+    for (int ti = blockIdx.x; ti < a.ntiles; ti += gridDim.x, ++i) {
+      const int b = i & 1, u = i >> 1;
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(tfull(b), u & 1, abort_flag));
+      tc_fence_after();
+      const Tile t = a.tiles[ti];
+      const int nb = a.nb[ti];
+      const PartDesc p = a.parts[t.part];
+      int8_t alf;
+      if (a.tail == 1) alf = (a.ctl.traces[step - 1] <= (double)a.ctl.nocc) ? (int8_t)1 : (int8_t)-1;
+      else if (a.tail == 2) alf = (int8_t)(-a.ctl.alpha[step - 1]);
+      else alf = a.ctl.alpha[step];
+      const float* Xi = a.master[bi] + p.off;
+      float* Xo = a.master[bo] + p.off;
+      void* ohi = a.op_hi[bo];
+      void* olo = a.op_lo[bo];
+      const int64_t ld = p.ld;
+      const int r0 = t.ti * 128, c0 = t.tj * 128;
+      const int r = r0 + m;
+      const bool diag = t.slot >= 0;
+      double tY = 0.0, tN = 0.0;
+      if (ok) {
+#pragma unroll 1
+        for (int h = 0; h < 2 * nb; ++h) {
+          // columns colq * 32 nb + 16 h .. + 15 of the item; block 0 of a diagonal item is
+          // the diagonal tile
+          const int cl = colq * 32 * nb + h * 16;
+          const int cbase = c0 + cl;
+          const bool dblk = diag && cl < 128;
+          uint32_t v[16];
+          tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 256 + cl), v);
+          float x[16];
+#pragma unroll
+          for (int j = 0; j < 16; ++j) x[j] = Xi[(int64_t)(cbase + j) * ld + r];
+          float yd = 0.0f, zd = 0.0f;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const float y = __uint_as_float(v[j]);
+            const float z = (alf > 0) ? (2.0f * x[j] - y) : y;
+            yd = (cbase + j == r) ? y : yd;
+            zd = (cbase + j == r) ? z : zd;
+            x[j] = z;
+          }
+          if (dblk && r >= cbase && r < cbase + 16 && r < p.c) {
+            tY += (double)yd;
+            tN += (double)zd;
+          }
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            if (dblk && cbase + j < r) continue;
+            const int64_t e = (int64_t)(cbase + j) * ld + r;
+            Xo[e] = x[j];
+            store_operands<KIND, NPROD>(ohi, olo, p.off + e, x[j]);
+          }
+          if (dblk && cbase <= r) {
+            for (int j = 0; j < 16; ++j) {
+              if (cbase + j <= r) continue;
+              const int64_t e = (int64_t)r * ld + cbase + j;
+              Xo[e] = x[j];
+              store_operands<KIND, NPROD>(ohi, olo, p.off + e, x[j]);
+            }
+          } else {
+            const int64_t e0 = (int64_t)r * ld + cbase;
+            float4* dst = reinterpret_cast<float4*>(Xo + e0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) dst[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+            store_operand_row<KIND, NPROD, 16>(ohi, olo, p.off + e0, x);
+          }
+        }
+      } else {
+        *s_err = 1;
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tempty(b));
+      if (diag) {
+        tY = warp_sum(tY);
+        tN = warp_sum(tN);
+        if (lane == 0) red[warp - 4] = make_double2(tY, tN);
+        asm volatile("bar.sync 1, %0;\n" ::"n"(32 * TC_EPI_WARPS) : "memory");
+        if (warp == 4 && lane == 0) {
+          double2 acc = make_double2(0.0, 0.0);
+          for (int w = 0; w < TC_EPI_WARPS; ++w) {
+            acc.x += red[w].x;
+            acc.y += red[w].y;
+          }
+          a.slots[t.slot] = acc;
+        }
+        asm volatile("bar.sync 1, %0;\n" ::"n"(32 * TC_EPI_WARPS) : "memory");
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;\n" ::"r"(tmem));
+  if (threadIdx.x == 0 && *s_err) a.ctl.st->timeout = 1;
+
+  if (last_block_ticket(&a.ctl.st->counter)) {
+    double u = 0.0, w = 0.0;
+    for (int k = threadIdx.x; k < a.nslots; k += blockDim.x) {
+      u += ld_cg(&a.slots[k].x);
+      w += ld_cg(&a.slots[k].y);
+    }
+    const double2 sum = block_sum2(u, w);
+    if (threadIdx.x == 0) {
+      if (a.ctl.st->timeout) {
+        a.ctl.st->status = ST_TIMEOUT;
+        a.ctl.st->stopped = 1;
+      } else if (a.tail) {
+        int8_t alf;
+        if (a.tail == 1) alf = (a.ctl.traces[step - 1] <= (double)a.ctl.nocc) ? (int8_t)1 : (int8_t)-1;
+        else alf = (int8_t)(-a.ctl.alpha[step - 1]);
+        a.ctl.alpha[step] = alf;
+        finish_tail(a.ctl, step, sum.y, sum.x, false);
+      } else {
+        finish_step(a.ctl, step, sum.y, sum.x);
+      }
+      a.ctl.st->counter = 0;
+    }
+  }
+}
+
+template <int KIND, int NPROD>
+static cudaError_t launch_tc_wide(const TcStepArgs& a, int grid, cudaStream_t s) {
+  constexpr int STAGES = TcWideStage<NPROD>::STAGES;
+  const int smem = STAGES * (int)TcWideStage<NPROD>::BYTES + 1024 + 8 * (2 * STAGES + 4) + 16 + 16 * TC_EPI_WARPS;
+  cudaError_t e = cudaFuncSetAttribute(square_tc_wide_kernel<KIND, NPROD>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       smem);
+  if (e != cudaSuccess) return e;
+  square_tc_wide_kernel<KIND, NPROD><<<grid, TC_THREADS, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <int KIND, int NPROD>
 static cudaError_t launch_tc_persistent(const TcStepArgs& a, int grid, cudaStream_t s) {
   constexpr int NOPS = NPROD == 3 ? 4 : 2;
@@ -609,6 +898,14 @@ static cudaError_t launch_tc(const TcStepArgs& a, int ntiles, cudaStream_t s) {
 
 cudaError_t launch_square_tc(int kind, int nprod, const TcStepArgs& a, int ntiles, int persistent_grid,
                              cudaStream_t s) {
+  if (persistent_grid > 0 && a.nb) {  // 128 x 256 work items
+    const int g = persistent_grid < ntiles ? persistent_grid : ntiles;
+    if (kind == 0 && nprod == 1) return launch_tc_wide<0, 1>(a, g, s);
+    if (kind == 0 && nprod == 3) return launch_tc_wide<0, 3>(a, g, s);
+    if (kind == 1 && nprod == 1) return launch_tc_wide<1, 1>(a, g, s);
+    if (kind == 1 && nprod == 3) return launch_tc_wide<1, 3>(a, g, s);
+    return cudaErrorInvalidValue;
+  }
   if (persistent_grid > 0) {
     const int g = persistent_grid < ntiles ? persistent_grid : ntiles;
     if (kind == 0 && nprod == 1) return launch_tc_persistent<0, 1>(a, g, s);

@@ -37,7 +37,7 @@ class Options(C.Structure):
                 ("precision", C.c_int32), ("fp64_tail_steps", C.c_int32), ("ckpt_every", C.c_int32),
                 ("use_graph", C.c_int32), ("time_steps", C.c_int32), ("lp_tail_steps", C.c_int32),
                 ("tc_schedule", C.c_int32), ("report_idem", C.c_int32), ("fp64_tail_emulated", C.c_int32),
-                ("tile_order", C.c_int32), ("reserved", C.c_int32 * 2)]
+                ("tile_order", C.c_int32), ("tile_shape", C.c_int32), ("reserved", C.c_int32 * 1)]
 
 
 class Report(C.Structure):
@@ -51,12 +51,12 @@ class PlanInfo(C.Structure):
                 ("sum_s", C.c_int64), ("sum_s2", C.c_double), ("sum_s3", C.c_double), ("nnz_h", C.c_int64),
                 ("nnz_p", C.c_int64), ("arena_elems", C.c_int64), ("ntiles", C.c_int64), ("tile", C.c_int32),
                 ("ld_pad", C.c_int32), ("step_launches", C.c_int32), ("fp64_tail_steps", C.c_int32),
-                ("tc_schedule", C.c_int32), ("tile_order", C.c_int32)]
+                ("tc_schedule", C.c_int32), ("tile_order", C.c_int32), ("tile_shape", C.c_int32)]
 
 
 class TuneReport(C.Structure):
-    _fields_ = [("ncand", C.c_int32), ("chosen", C.c_int32), ("tc_schedule", C.c_int32 * 4),
-                ("tile_order", C.c_int32 * 4), ("ms", C.c_double * 4)]
+    _fields_ = [("ncand", C.c_int32), ("chosen", C.c_int32), ("tc_schedule", C.c_int32 * 8),
+                ("tile_order", C.c_int32 * 8), ("tile_shape", C.c_int32 * 8), ("ms", C.c_double * 8)]
 
 
 _lib = None
@@ -229,7 +229,8 @@ class GSP2:
         self._check(self._lib.gsp2_autotune(self._h, _tptr(h_vals.contiguous()), _tptr(out), int(trials),
                                             _stream_ptr(stream), C.byref(r)))
         self._refresh_info()
-        cands = [dict(tc_schedule=r.tc_schedule[i], tile_order=r.tile_order[i], ms=r.ms[i]) for i in range(r.ncand)]
+        cands = [dict(tc_schedule=r.tc_schedule[i], tile_order=r.tile_order[i], tile_shape=r.tile_shape[i], ms=r.ms[i])
+                 for i in range(r.ncand)]
         return dict(chosen=r.chosen, candidates=cands)
 
     def density_reuse(self, h_vals, alpha, nsteps, out=None, stream=None):
@@ -269,6 +270,7 @@ class GSP2:
         self.info = info
         self.options.tc_schedule = info.tc_schedule
         self.options.tile_order = info.tile_order
+        self.options.tile_shape = info.tile_shape
 
     def status(self):
         """(status code, report dict) of the last density call; waits for it."""

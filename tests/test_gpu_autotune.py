@@ -40,17 +40,29 @@ def test_tile_orders_give_bitwise_equal_p(g, prec):
     assert np.array_equal(p0, p1)
 
 
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "tf32", "bf16"])
+def test_tile_shapes_give_bitwise_equal_p(g, prec):
+    """128 x 256 work items (two upper tiles per N = 256 MMA) compute every element as the
+    128 x 128 tiles do."""
+    s = make_workload("tb4k")
+    _, _, p0 = run(g, s, precision=prec, tile_shape=0)
+    _, _, p1 = run(g, s, precision=prec, tile_shape=1)
+    _, _, p2 = run(g, s, precision=prec, tile_shape=1, tile_order=1)
+    assert np.array_equal(p0, p1) and np.array_equal(p0, p2)
+
+
 @pytest.mark.parametrize("prec", ["tf32x3", "fp64e", "fp64"])
 def test_autotune_keeps_a_timed_candidate(g, prec):
     s = make_workload("tb4k")
     plan, h, p0 = run(g, s, precision=prec)
     rep = plan.autotune(h, trials=2)
     cands = rep["candidates"]
-    assert len(cands) == {"tf32x3": 3, "fp64e": 2, "fp64": 1}[prec]
+    assert len(cands) == {"tf32x3": 5, "fp64e": 2, "fp64": 1}[prec]
     assert all(c["ms"] > 0 for c in cands)
     best = cands[rep["chosen"]]
     assert best["ms"] == min(c["ms"] for c in cands)
-    assert (plan.info.tc_schedule, plan.info.tile_order) == (best["tc_schedule"], best["tile_order"])
+    assert (plan.info.tc_schedule, plan.info.tile_order, plan.info.tile_shape) == (
+        best["tc_schedule"], best["tile_order"], best["tile_shape"])
     p1 = plan.density(h).cpu().numpy()
     assert np.array_equal(p0, p1)
     print(prec, rep)

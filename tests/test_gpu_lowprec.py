@@ -120,8 +120,9 @@ def test_persistent_schedule_matches_one_cta_per_tile(g, prec, case):
     s = make_workload(case)
     _, p0, h0 = run(g, s, prec, tc_schedule=0, max_steps=6)
     _, p1, h1 = run(g, s, prec, tc_schedule=1, max_steps=6)
-    assert h0["alphas"] == h1["alphas"]
-    assert np.array_equal(p0, p1)
+    _, p2, h2 = run(g, s, prec, tc_schedule=0, tile_shape=1, max_steps=6)
+    assert h0["alphas"] == h1["alphas"] == h2["alphas"]
+    assert np.array_equal(p0, p1) and np.array_equal(p0, p2)
 
 
 @pytest.mark.parametrize("case", ["tb512", "tb30k"])

@@ -142,6 +142,11 @@ def test_tile_order_option(g):
             _plan(g, s, tile_order=bad)
     p = _plan(g, s, precision="tf32x3", tile_order=1, tc_schedule=1)
     assert p.info.tile_order == 1 and p.info.tc_schedule == 1
+    assert g.default_options().tile_shape == 0
+    for bad in (-1, 2):
+        with pytest.raises(g.GSP2Error):
+            _plan(g, s, tile_shape=bad)
+    assert _plan(g, s, precision="tf32x3", tile_shape=1).info.tile_shape == 1
 
 
 def test_low_precision_adjoint_layout(g):
