@@ -254,17 +254,20 @@ def kernel_avg_ms(step_ms, nwork):
 
 
 def adjoint_block(dev, peaks, src, workload="tb4k", reps=3):
-    """gsp2_backward of L = sum Pbar .* P on the 4,096-orbital, 32-part workload, FP64 and
-    FP32, checkpoints every 8 steps: device time per backward (after a density call) and the
-    reverse sweep's algorithmic flops (every reverse step 2 s^2 (s+1) per part, every rebuilt
-    iterate s^2 (s+1)) against the FP64 / FP32 CUDA-core peak."""
+    """gsp2_backward of L = sum Pbar .* P on the 4,096-orbital, 32-part workload, checkpoints
+    every 8 steps, for the three plans with an adjoint: FP64 (CUDA cores), FP64 rebuilt from
+    BF16 digit products (tensor cores) and FP32 (CUDA cores).  Device time per backward (after
+    a density call) and the reverse sweep's flops against the peak of the pipe it runs on:
+    algorithmic flops on the CUDA cores (every reverse step 2 s^2 (s+1) per part, every
+    rebuilt iterate s^2 (s+1)); executed BF16 flops on the tensor cores (every reverse step
+    twice, every rebuilt iterate once, the digit products of all upper 128-tiles)."""
     import numpy as np
     import torch
     from paper_1801_10016_gb300.gsp2 import GSP2
     s = make_system(workload)
     h = torch.from_numpy(s.vals).to(dev)
     out = {"workload": workload, "checkpoint_every": 8}
-    for prec in ("fp64", "fp32"):
+    for prec in ("fp64", "fp64e", "fp32"):
         plan = GSP2(s.n, s.rowptr, s.colind, s.nocc, s.part, s.nparts, s.g_rowptr, s.g_colind, device=dev,
                     precision=prec, ckpt_every=8, fp64_tail_steps=0)
         rng = np.random.default_rng(5678)
@@ -283,20 +286,28 @@ def adjoint_block(dev, peaks, src, workload="tb4k", reps=3):
         n = int(rep["steps"])
         plan.close()
         sz = plan.part_sizes.astype(np.float64)
-        w = float(np.sum(sz * sz * (sz + 1.0)))
         rebuilt = sum(1 for i in range(1, n) if i % 8 != 0)
-        flops = (2.0 * n + rebuilt) * w
         t = statistics.median(ms) / 1e3
-        if prec == "fp64":
-            peak, psrc = peaks["bf16_tflops"] * NOMINAL["fp64"] / NOMINAL["bf16"], f"{src} bf16 x nominal fp64/bf16"
+        if prec == "fp64e":
+            flops = (2.0 * n + rebuilt) * tc_exec_flops(sz, 32, OZ_PRODUCTS)
+            peak, psrc = peaks["bf16_tflops"], f"{src}: bf16 burst (of measured)"
+            kern, fdesc = ("oz_step_kernel<adjoint> + oz_step_kernel recompute",
+                           f"executed BF16 tensor flops of the {OZ_PRODUCTS} digit products per upper 128-tile: "
+                           "reverse steps twice (K = 2s), rebuilt iterates once")
+            bound = "tensor"
         else:
-            peak, psrc = 152 * 128 * 2 * 2.07e9 / 1e12, "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"
+            flops = (2.0 * n + rebuilt) * float(np.sum(sz * sz * (sz + 1.0)))
+            if prec == "fp64":
+                peak, psrc = peaks["bf16_tflops"] * NOMINAL["fp64"] / NOMINAL["bf16"], f"{src} bf16 x nominal fp64/bf16"
+            else:
+                peak, psrc = 152 * 128 * 2 * 2.07e9 / 1e12, "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"
+            kern = f"adj_step_kernel<{'double' if prec == 'fp64' else 'float'}> + square_simt_kernel recompute"
+            fdesc = "reverse steps 2 s^2 (s+1) + rebuilt iterates s^2 (s+1), per part"
+            bound = "alu"
         out[prec] = {"ms_per_backward": 1e3 * t, "steps": n, "rebuilt_iterates": rebuilt,
-                     "roofline": {"bound": "alu", "achieved": flops / t / 1e12, "peak": peak, "unit": "TFLOP/s",
-                                  "frac": flops / t / 1e12 / peak, "peak_source": psrc,
-                                  "kernel": f"adj_step_kernel<{'double' if prec == 'fp64' else 'float'}> + "
-                                            f"square_simt_kernel recompute",
-                                  "flops": "reverse steps 2 s^2 (s+1) + rebuilt iterates s^2 (s+1), per part"}}
+                     "roofline": {"bound": bound, "achieved": flops / t / 1e12, "peak": peak, "unit": "TFLOP/s",
+                                  "frac": flops / t / 1e12 / peak, "peak_source": psrc, "kernel": kern,
+                                  "flops": fdesc}}
     return out
 
 

@@ -35,6 +35,11 @@ struct WsLayout {
   size_t oz_maps;                 // CUtensorMap[2][OZ_SLICES][nparts], K-major boxes
   size_t oz_maps_mn;              // the same, MN-major boxes
   size_t oz_acc;                  // int64[OZ_MAX_GRID][128 * 128] partial sums of the emulated step
+  // emulated FP64 adjoint: digit sets 0..k-1 hold X_{c0+j} of a checkpoint segment, set k
+  // holds Xbar / 2^sig; their tensor maps; row norms and per-part scales of Xbar
+  std::vector<size_t> adj_dig;    // adj_dig[set * OZ_SLICES + t]
+  size_t adj_maps, adj_maps_mn;   // CUtensorMap[k + 1][OZ_SLICES][nparts]
+  size_t adj_norm, adj_sig;       // double[sum of s], int32[nparts]
   size_t mask;                    // uint8[nnz_p]: |P| > tau flags of gsp2_threshold_graph
   std::vector<size_t> tailf;      // low-precision adjoint: FP32 iterates of the FP64 tail, recomputed
   size_t slots, rslots, state, alpha, traces, idem, step_arena;
@@ -298,6 +303,16 @@ static void build_layout(gsp2_plan* h) {
     L.oz_maps = take((size_t)2 * OZ_SLICES * h->parts.size() * 128);
     L.oz_maps_mn = take((size_t)2 * OZ_SLICES * h->parts.size() * 128);
     L.oz_acc = take((size_t)OZ_MAX_GRID * 128 * 128 * 8);
+  }
+  L.adj_dig.clear();
+  L.adj_maps = L.adj_maps_mn = L.adj_norm = L.adj_sig = 0;
+  if (h->use_oz && k > 0) {
+    for (int set = 0; set <= k; ++set)
+      for (int t = 0; t < OZ_SLICES; ++t) L.adj_dig.push_back(take((size_t)h->arena_elems * 2));
+    L.adj_maps = take((size_t)(k + 1) * OZ_SLICES * h->parts.size() * 128);
+    L.adj_maps_mn = take((size_t)(k + 1) * OZ_SLICES * h->parts.size() * 128);
+    L.adj_norm = take(h->S.size() * sizeof(double));
+    L.adj_sig = take(h->parts.size() * sizeof(int32_t));
   }
   L.total = o;
   // arena of each iterate X_i: checkpoints where i is a multiple of k, else ping-pong
@@ -630,6 +645,19 @@ extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t byt
       }
     CU(h, up(L.oz_maps, maps.data(), maps.size()));
     CU(h, up(L.oz_maps_mn, maps_mn.data(), maps_mn.size()));
+    if (!L.adj_dig.empty()) {
+      std::vector<unsigned char> amaps(L.adj_dig.size() * np * 128, 0), amaps_mn(amaps.size(), 0);
+      for (size_t i = 0; i < L.adj_dig.size(); ++i) {
+        int r = encode_part_maps(enc, amaps.data() + i * np * 128, h->parts.data(), (int)np, h->ws + L.adj_dig[i], 0,
+                                 2 * OZ_BK, 128);
+        if (r == 0)
+          r = encode_part_maps(enc, amaps_mn.data() + i * np * 128, h->parts.data(), (int)np, h->ws + L.adj_dig[i],
+                               0, 128, OZ_BK);
+        if (r != 0) return fail(h, GSP2_E_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string(r));
+      }
+      CU(h, up(L.adj_maps, amaps.data(), amaps.size()));
+      CU(h, up(L.adj_maps_mn, amaps_mn.data(), amaps_mn.size()));
+    }
   }
   if (!fp64_like(h->opt.precision)) {
     std::vector<const float*> mt(h->mf_of_step.size());
@@ -678,9 +706,6 @@ static OzStepArgs oz_args(gsp2_plan* h, const StepCtl& ctl) {
   a.ntiles = (int)h->tc_tiles.size();
   a.maps = w + L.oz_maps;
   a.maps_mn = w + L.oz_maps_mn;
-  // the emulated steps keep the upper tiles only, and the lower ones too where an iterate is
-  // a checkpoint of the FP64 adjoint (the low-precision adjoint keeps FP32 iterates instead)
-  a.lower_every = fp64_like(h->opt.precision) ? h->opt.ckpt_every : 0;
   a.nparts = (int)h->parts.size();
   for (int b = 0; b < 2; ++b)
     for (int t = 0; t < OZ_SLICES; ++t) a.digits[b].s[t] = (uint16_t*)(w + L.oz_slice[b][t]);
@@ -1131,7 +1156,82 @@ extern "C" gsp2_status gsp2_step_times(gsp2_handle h, float* ms, int32_t cap) {
 // Queue the adjoint on `s`: seed, then per checkpoint segment (last first) the
 // recomputed iterates and the reverse steps, then the scatter-add onto H.  The
 // schedule covers max_steps; kernels for steps beyond the applied count return at once.
+// Adjoint of an emulated-FP64 plan on the BF16 tensor cores.  For each checkpoint segment
+// the iterates X_{c0} .. X_{c0+k-1} are rebuilt as digit sets (digits of the checkpoint,
+// then emulated steps with the recorded branches); every reverse step multiplies the
+// digits of X_{i-1} with those of Xbar / 2^sig, and the row norms, scales and digits of the
+// new Xbar follow it.  Xbar is kept in its upper 128-tiles like the forward iterates.
+static gsp2_status enqueue_backward_emu(gsp2_plan* h, const double* pbar, double* hbar, cudaStream_t s) {
+  const WsLayout& L = h->L;
+  char* w = h->ws;
+  auto parts = (const PartDesc*)(w + L.parts);
+  auto Sall = (const int32_t*)(w + L.S);
+  auto gbl = (const ColBlock*)(w + L.gblocks);
+  auto gbl_ld = (const ColBlock*)(w + L.gblocks_ld);
+  const int ngb = (int)h->gblocks_ld.size();
+  auto tct = (const Tile*)(w + L.tc_tiles);
+  const int ntc = (int)h->tc_tiles.size();
+  auto st = (DevState*)(w + L.state);
+  auto alpha = (int8_t*)(w + L.alpha);
+  double* xb0 = (double*)(w + L.xb0);
+  double* xb1 = (double*)(w + L.xb1);
+  double* norm = (double*)(w + L.adj_norm);
+  int32_t* sig = (int32_t*)(w + L.adj_sig);
+  const int k = h->opt.ckpt_every, M = h->total_steps;
+  const int np = (int)h->parts.size();
+  StepCtl ctl{st, alpha, (double*)(w + L.traces), (double*)(w + L.idem), h->nocc, h->opt.idem_tol,
+              h->opt.trace_tol, MODE_REPLAY, M, 1, 0};
+  auto set = [&](int j) {
+    OzSlices o{};
+    for (int t = 0; t < OZ_SLICES; ++t) o.s[t] = (uint16_t*)(w + L.adj_dig[(size_t)j * OZ_SLICES + t]);
+    return o;
+  };
+  auto smaps = [&](size_t base, int j) { return (const void*)(w + base + (size_t)j * OZ_SLICES * np * 128); };
+  const OzStepArgs base = oz_args(h, ctl);
+  CU(h, cudaMemsetAsync(norm, 0, h->S.size() * sizeof(double), s));
+  CU(h, launch_adj_seed<double>(parts, gbl, (int)h->gblocks.size(), Sall, (const int32_t*)(w + L.invperm),
+                                (const int64_t*)(w + L.pcolptr), pbar, xb0, s));
+  CU(h, launch_oz_adj_scale(parts, np, tct, ntc, xb0, xb1, 0, norm, sig, st, s));
+  CU(h, launch_oz_digits(parts, gbl_ld, ngb, xb0, xb1, 0, 0, set(k), sig, st, s));
+  for (int c0 = (M / k) * k; c0 >= 0; c0 -= k) {
+    const double* ck = (const double*)(w + L.ckpt[c0 / k]);
+    CU(h, launch_oz_digits(parts, gbl_ld, ngb, ck, ck, 0, c0 + 1, set(0), nullptr, st, s));
+    for (int j = 1; j < k && c0 + j < M; ++j) {
+      OzStepArgs a = base;
+      a.maps = smaps(L.adj_maps, j - 1);
+      a.maps_mn = smaps(L.adj_maps_mn, j - 1);
+      a.digits[0] = a.digits[1] = set(j);
+      a.xin = (j == 1) ? ck : (const double*)(w + L.seg[j - 2]);
+      a.xout = (double*)(w + L.seg[j - 1]);
+      a.step = c0 + j;
+      a.mode = SQ_RECOMPUTE;
+      CU(h, launch_oz_step(a, h->num_sms, s));
+    }
+    for (int i = std::min(c0 + k, M); i >= c0 + 1; --i) {
+      OzStepArgs a = base;
+      a.maps = smaps(L.adj_maps, i - 1 - c0);
+      a.maps_mn = smaps(L.adj_maps_mn, i - 1 - c0);
+      a.maps_b = smaps(L.adj_maps, k);
+      a.maps_mn_b = smaps(L.adj_maps_mn, k);
+      a.sig = sig;
+      a.xin = xb0;
+      a.xout = xb1;
+      a.step = i;
+      CU(h, launch_oz_step(a, h->num_sms, s, true));
+      if (i > 1) {
+        CU(h, launch_oz_adj_scale(parts, np, tct, ntc, xb0, xb1, i, norm, sig, st, s));
+        CU(h, launch_oz_digits(parts, gbl_ld, ngb, xb0, xb1, i, 0, set(k), sig, st, s));
+      }
+    }
+  }
+  CU(h, launch_adj_hbar<double>(h->n, (const int64_t*)(w + L.rowptr), (const int32_t*)(w + L.colind),
+                                (const int64_t*)(w + L.memptr), (const int32_t*)(w + L.mempart),
+                                (const int32_t*)(w + L.memloc), parts, Sall, xb0, xb1, hbar, st, s, TC_TILE));
+  return GSP2_OK;
+}
+
 static gsp2_status enqueue_backward(gsp2_plan* h, const double* pbar, double* hbar, cudaStream_t s) {
+  if (h->opt.precision == GSP2_PREC_FP64_EMU) return enqueue_backward_emu(h, pbar, hbar, s);
   const WsLayout& L = h->L;
   char* w = h->ws;
   auto parts = (const PartDesc*)(w + L.parts);

@@ -101,13 +101,20 @@ struct OzSlices {
 };
 
 // One emulated step: digits of X_{step-1} are read from buffer (step-1)&1 and the digits
-// of X_step written to buffer step&1.
+// of X_step written to buffer step&1 (SQ_FORWARD and the tail modes).  SQ_RECOMPUTE (the
+// adjoint's rebuilt iterates) reads the digit set `maps` points at and writes digits[0],
+// with the recorded branch and no bookkeeping.  The adjoint instantiation reads the digits
+// of X (`maps`) and of Xbar / 2^sig (`maps_b`) and writes Xbar's FP64 ping-pong pair
+// (xin = Xbar buffer 0, xout = buffer 1, the roles swapped on the device by step parity).
 struct OzStepArgs {
   const PartDesc* parts;
   const Tile* tiles;   // 128x128 upper tiles
   int ntiles;
   const void* maps;    // CUtensorMap[2 buffers][OZ_SLICES][nparts] over the digit arenas, K-major boxes
   const void* maps_mn; // the same with MN-major boxes (64 rows x OZ_BK columns, 128-byte swizzle)
+  const void* maps_b;    // adjoint: CUtensorMap[OZ_SLICES][nparts] over the digits of Xbar / 2^sig
+  const void* maps_mn_b; // the same, MN-major
+  const int32_t* sig;    // adjoint: per-part scale exponent of Xbar's digits (OZ_SIG_NONFINITE: NaN)
   int nparts;
   OzSlices digits[2];
   const double* xin;   // FP64 master of X_{step-1}
@@ -115,11 +122,11 @@ struct OzStepArgs {
   double2* slots;      // diagonal-tile trace slots
   int nslots;
   long long* acc;      // OZ_MAX_GRID x 128 x 128 fixed-point partial sums, one tile per CTA
-  int lower_every;     // also write the lower tiles when k divides the step (k > 0): checkpoints
   StepCtl ctl;
   int step;            // ignored in tail modes (step = steps applied + 1)
-  int mode;            // SQ_FORWARD, SQ_TAIL_FIRST or SQ_TAIL_NEXT
+  int mode;            // SQ_FORWARD, SQ_RECOMPUTE, SQ_TAIL_FIRST or SQ_TAIL_NEXT
 };
+constexpr int32_t OZ_SIG_NONFINITE = 0x7FFF;  // scale of a part whose Xbar holds NaN or Inf
 
 // ------------------------------------------------------------------ device helpers
 

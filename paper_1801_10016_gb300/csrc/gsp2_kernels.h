@@ -44,7 +44,14 @@ cudaError_t launch_convert(const float* const* master_of_step, double* out, int6
 // FP64 products from BF16 digits (k_oz.cu)
 cudaError_t launch_oz_slice(const PartDesc* parts, const ColBlock* blocks, int nblocks, const double* X,
                             const OzSlices* digits, const DevState* st, cudaStream_t s);
-cudaError_t launch_oz_step(const OzStepArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_oz_step(const OzStepArgs& a, int grid, cudaStream_t s, bool adjoint = false);
+// the emulated adjoint's Xbar digits: row norms and per-part scales, then the digits
+cudaError_t launch_oz_adj_scale(const PartDesc* parts, int nparts, const Tile* tiles, int ntiles, const double* xb0,
+                                const double* xb1, int after, double* norm, int32_t* sig, const DevState* st,
+                                cudaStream_t s);
+cudaError_t launch_oz_digits(const PartDesc* parts, const ColBlock* blocks, int nblocks, const double* x0,
+                             const double* x1, int after, int need, const OzSlices& out, const int32_t* sig,
+                             const DevState* st, cudaStream_t s);
 int encode_part_maps(void* enc_fn, void* out_maps, const PartDesc* parts, int nparts, void* arena, int kind,
                      int box_bytes = 128, int box_cols = 128);
 
@@ -60,6 +67,6 @@ template <typename T>
 cudaError_t launch_adj_hbar(int64_t n, const int64_t* rowptr, const int32_t* colind, const int64_t* memptr,
                             const int32_t* mempart, const int32_t* memloc, const PartDesc* parts,
                             const int32_t* Sall, const T* xb0, const T* xb1, double* hbar, const DevState* st,
-                            cudaStream_t s);
+                            cudaStream_t s, int upper_block = 0);
 
 }  // namespace gsp2

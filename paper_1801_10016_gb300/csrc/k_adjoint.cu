@@ -167,7 +167,9 @@ __global__ void __launch_bounds__(256, 2) adj_step_kernel(const PartDesc* __rest
 
 // dL/dH on the CSR pattern: for every stored (r, col), the sum over the parts k that
 // hold r (membership list of r) and col of -Xbar0_k[col, r] / (eps_max - eps_min), in
-// the fixed membership order.  One warp per row, lanes over the row's entries.
+// the fixed membership order.  One warp per row, lanes over the row's entries.  With
+// upper_block > 0 only the tiles of that edge on or above the diagonal hold Xbar0 (the
+// emulated adjoint); the symmetric entry is read from there.
 template <typename T>
 __global__ void __launch_bounds__(256) adj_hbar_kernel(int64_t n, const int64_t* __restrict__ rowptr,
                                                        const int32_t* __restrict__ colind,
@@ -177,7 +179,8 @@ __global__ void __launch_bounds__(256) adj_hbar_kernel(int64_t n, const int64_t*
                                                        const PartDesc* __restrict__ parts,
                                                        const int32_t* __restrict__ Sall,
                                                        const T* __restrict__ xb0, const T* __restrict__ xb1,
-                                                       double* __restrict__ hbar, const DevState* st) {
+                                                       double* __restrict__ hbar, const DevState* st,
+                                                       int upper_block) {
   const int nsteps = st->steps;
   const T* XB = (nsteps & 1) ? xb1 : xb0;
   const double scale = -1.0 / (st->eps_max - st->eps_min);
@@ -192,7 +195,10 @@ __global__ void __launch_bounds__(256) adj_hbar_kernel(int64_t n, const int64_t*
       for (int64_t m = m0; m < m1; ++m) {
         const PartDesc p = parts[mempart[m]];
         const int lc = find_local(Sall + p.soff, p.c, p.s, col);
-        if (lc >= 0) sum += (double)XB[p.off + (int64_t)memloc[m] * p.ld + lc];
+        if (lc < 0) continue;
+        const int lr = memloc[m];
+        const bool swap = upper_block > 0 && lc / upper_block > lr / upper_block;
+        sum += (double)XB[p.off + (swap ? (int64_t)lc * p.ld + lr : (int64_t)lr * p.ld + lc)];
       }
       hbar[q] = scale * sum;
     }
@@ -218,8 +224,9 @@ template <typename T>
 cudaError_t launch_adj_hbar(int64_t n, const int64_t* rowptr, const int32_t* colind, const int64_t* memptr,
                             const int32_t* mempart, const int32_t* memloc, const PartDesc* parts,
                             const int32_t* Sall, const T* xb0, const T* xb1, double* hbar, const DevState* st,
-                            cudaStream_t s) {
-  adj_hbar_kernel<T><<<608, 256, 0, s>>>(n, rowptr, colind, memptr, mempart, memloc, parts, Sall, xb0, xb1, hbar, st);
+                            cudaStream_t s, int upper_block) {
+  adj_hbar_kernel<T><<<608, 256, 0, s>>>(n, rowptr, colind, memptr, mempart, memloc, parts, Sall, xb0, xb1, hbar, st,
+                                         upper_block);
   return cudaGetLastError();
 }
 
@@ -230,7 +237,7 @@ cudaError_t launch_adj_hbar(int64_t n, const int64_t* rowptr, const int32_t* col
                                           const DevState*, int, int, cudaStream_t);                                \
   template cudaError_t launch_adj_hbar<T>(int64_t, const int64_t*, const int32_t*, const int64_t*, const int32_t*, \
                                           const int32_t*, const PartDesc*, const int32_t*, const T*, const T*,     \
-                                          double*, const DevState*, cudaStream_t);
+                                          double*, const DevState*, cudaStream_t, int);
 GSP2_ADJ_INSTANTIATE(double)
 GSP2_ADJ_INSTANTIATE(float)
 

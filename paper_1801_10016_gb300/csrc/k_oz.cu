@@ -20,6 +20,16 @@
 // the next step by integer arithmetic.  With T = 7 (28 BF16 products per tile) the digits
 // hold x to 2^-49 and the dropped products are of order 2^-63 K 2^12; the error of Y is
 // about 1e-13, far below the 1e-10 parity of the FP64 path.
+//
+// The adjoint step Xbar <- Xbar X + X Xbar (or 2 Xbar minus that) runs on the same
+// machinery: an upper tile (I, J) of Xbar X + X Xbar is one product over K = 2s, rows I of
+// [Xbar | X] times columns J of [X ; Xbar], both symmetric and kept as upper tiles.  Xbar
+// has no a-priori bound, so its digits hold Xbar / 2^sig with one power-of-two scale per
+// part, chosen from the largest row 2-norm of Xbar so that every row of Xbar / 2^sig has
+// 2-norm <= 1/2.  With ||X||_2 <= 1, Cauchy-Schwarz gives
+// sum_k |xbar_ik x_kj| + |x_ik xbar_kj| <= 1/2 + 1/2, the bound the forward step rests on,
+// so the digit groups stay exact in the same way and the result carries an error of
+// order 2^-49 2^sig.
 #include <cuda.h>
 
 #include "gsp2_internal.cuh"
@@ -56,17 +66,20 @@ __device__ __forceinline__ void store_digits(uint16_t* const* slices, int64_t e,
   for (int t = 0; t < OZ_SLICES; ++t) slices[t][e] = (uint16_t)(fw[t] >> 16);
 }
 
-// Conversions between FP64 and the 2^-56 fixed point done with integer instructions (the
-// FP64 pipe of GB300 is 64x slower than its integer pipe), rounding to nearest even.
-__device__ __forceinline__ long long to_fixed(double x) {
+// Conversions between FP64 and the 2^-56 fixed point of x / 2^sig done with integer
+// instructions (the FP64 pipe of GB300 is 64x slower than its integer pipe), rounding to
+// nearest even.  |x| / 2^sig < 2^7; larger inputs saturate, results below 2^-1022 flush to 0.
+__device__ __forceinline__ long long to_fixed(double x, int sig = 0) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const int ex = (int)((b >> 52) & 0x7FF);
   if (ex == 0) return 0;                                    // zero and subnormals (< 2^-1022)
   const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-  const int sh = ex - 1023 - 52 + 56;                       // value * 2^56 = m * 2^sh
+  const int sh = ex - 1023 - 52 + 56 - sig;                 // (x / 2^sig) * 2^56 = m * 2^sh
   unsigned long long a;
-  if (sh >= 0) {
-    a = m << sh;                                            // |x| < 2^7 keeps this below 2^63
+  if (sh > 10) {
+    a = 1ull << 62;                                         // out of range: saturate
+  } else if (sh >= 0) {
+    a = m << sh;
   } else if (sh > -64) {
     const int k = -sh;
     const unsigned long long q = m >> k, rem = m & ((1ull << k) - 1), half = 1ull << (k - 1);
@@ -77,7 +90,7 @@ __device__ __forceinline__ long long to_fixed(double x) {
   return (b >> 63) ? -(long long)a : (long long)a;
 }
 
-__device__ __forceinline__ double from_fixed(long long v) {
+__device__ __forceinline__ double from_fixed(long long v, int sig = 0) {
   if (v == 0) return 0.0;
   const unsigned long long sgn = v < 0 ? (1ull << 63) : 0ull;
   const unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
@@ -85,7 +98,7 @@ __device__ __forceinline__ double from_fixed(long long v) {
   const unsigned long long m = a << lz;                     // top bit at 63
   unsigned long long mant = m >> 11;                        // 53 bits with the leading one
   const unsigned long long rem = m & 0x7FFull;
-  int e = 63 - lz - 56;                                     // value = 1.f x 2^e
+  int e = 63 - lz - 56 + sig;                               // value = 1.f x 2^e
   if (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) {
     mant += 1;
     if (mant >> 53) {
@@ -93,6 +106,7 @@ __device__ __forceinline__ double from_fixed(long long v) {
       e += 1;
     }
   }
+  if (e < -1022) return __longlong_as_double((long long)sgn);
   const unsigned long long bits = sgn | ((unsigned long long)(e + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFull);
   return __longlong_as_double((long long)bits);
 }
@@ -112,6 +126,115 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const PartDesc* __restric
   if (j >= p.ld) return;
   const int64_t cbase = p.off + (int64_t)j * p.ld;
   for (int r = lane; r < p.ld; r += 32) store_digits(sl.s, cbase + r, to_fixed(X[cbase + r]));
+}
+
+// The adjoint's operands.  `after` names the reverse step just run (0: the seed), whose
+// Xbar lies in buffer (n - after + 1) & 1 of the pair (x0, x1); kernels for a step that was
+// not run (after > n: the forward stopped earlier) return at once.
+
+// Squared row 2-norms of the symmetric Xbar held in its upper 128-tiles, FP64, added into
+// norm[soff + r] for rows r < s: the column sums of an upper tile (I, J) give the entries
+// of rows J within block I (a diagonal tile holds its whole block), and the row sums of an
+// off-diagonal tile the entries of rows I within block J.  One CTA per tile.
+__global__ void __launch_bounds__(256) oz_norm_kernel(const PartDesc* __restrict__ parts,
+                                                      const Tile* __restrict__ tiles, const double* xb0,
+                                                      const double* xb1, int after, double* __restrict__ norm,
+                                                      const DevState* st) {
+  const int n = *(volatile const int32_t*)&st->steps;
+  if (after > n) return;
+  const double* X = (after > 0 && ((n - after + 1) & 1)) ? xb1 : xb0;
+  const Tile t = tiles[blockIdx.x];
+  const PartDesc p = parts[t.part];
+  const double* x = X + p.off;
+  const int64_t ld = p.ld;
+  const int r0 = t.ti * 128, c0 = t.tj * 128;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int q = 0; q < 16; ++q) {  // warp w: columns c0 + 16 w .. + 15, lanes over the rows
+    const int c = c0 + warp * 16 + q;
+    if (c >= p.s) break;
+    double v = 0.0;
+    for (int i = lane; i < 128; i += 32) {
+      const int r = r0 + i;
+      if (r < p.s) {
+        const double d = x[(int64_t)c * ld + r];
+        v = fma(d, d, v);
+      }
+    }
+    v = warp_sum(v);
+    if (lane == 0) atomicAdd(&norm[p.soff + c], v);
+  }
+  if (t.ti != t.tj) {  // thread: row r0 + (tid % 128), half of the tile's columns
+    const int r = r0 + (threadIdx.x & 127), h = threadIdx.x >> 7;
+    if (r < p.s) {
+      double v = 0.0;
+      for (int q = 0; q < 64; ++q) {
+        const int c = c0 + h * 64 + q;
+        if (c >= p.s) break;
+        const double d = x[(int64_t)c * ld + r];
+        v = fma(d, d, v);
+      }
+      atomicAdd(&norm[p.soff + r], v);
+    }
+  }
+}
+
+// Scale of each part's Xbar digits: the smallest sig with 2^sig >= 2 max_r ||xbar_r||_2
+// (with a relative margin of 2^-20 over the rounding of the FP64 sums), 0 for a zero Xbar,
+// OZ_SIG_NONFINITE where a row norm is NaN or Inf.  Clears the norms for the next step.
+// One CTA per part.
+__global__ void __launch_bounds__(256) oz_scale_kernel(const PartDesc* __restrict__ parts, int after,
+                                                       double* __restrict__ norm, int32_t* __restrict__ sig,
+                                                       const DevState* st) {
+  const int n = *(volatile const int32_t*)&st->steps;
+  if (after > n) return;
+  const PartDesc p = parts[blockIdx.x];
+  __shared__ double smax[8];
+  double m = 0.0;
+  int bad = 0;
+  for (int r = threadIdx.x; r < p.s; r += blockDim.x) {
+    const double v = norm[p.soff + r];
+    norm[p.soff + r] = 0.0;
+    if (!(v <= 1.7976931348623157e308)) bad = 1;  // NaN or Inf
+    else m = fmax(m, v);
+  }
+  bad = __syncthreads_or(bad);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, smax[w]);
+    int e = 0;
+    if (bad) e = OZ_SIG_NONFINITE;
+    else if (m > 0.0) (void)frexp(2.0 * sqrt(m) * (1.0 + 9.5367431640625e-07), &e);  // 2^(e-1) <= v < 2^e
+    sig[blockIdx.x] = e;
+  }
+}
+
+// Digits of the upper 128-tiles of a symmetric FP64 arena, of x / 2^sig[part] (sig NULL:
+// unscaled), into `out`; entries outside the part (rows or columns >= s) get zero digits.
+// One warp per column up to ld.  Skipped where need > n (an iterate the adjoint does not
+// reach) or where `after` names a reverse step that was not run.
+__global__ void __launch_bounds__(256) oz_digits_kernel(const PartDesc* __restrict__ parts,
+                                                        const ColBlock* __restrict__ blocks, const double* x0,
+                                                        const double* x1, int after, int need, OzSlices out,
+                                                        const int32_t* __restrict__ sig, const DevState* st) {
+  const int n = *(volatile const int32_t*)&st->steps;
+  if (need > n || after > n) return;
+  const double* X = (after > 0 && ((n - after + 1) & 1)) ? x1 : x0;
+  const ColBlock b = blocks[blockIdx.x];
+  const PartDesc p = parts[b.part];
+  const int lane = threadIdx.x & 31;
+  const int j = b.j0 + (threadIdx.x >> 5);
+  if (j >= p.ld) return;
+  const int sg = sig ? sig[b.part] : 0;
+  const int rend = min(p.ld, (j / 128 + 1) * 128);
+  const int64_t cbase = p.off + (int64_t)j * p.ld;
+  for (int r = lane; r < rend; r += 32) {
+    long long v = 0;
+    if (r < p.s && j < p.s && sg != OZ_SIG_NONFINITE) v = to_fixed(X[cbase + r], sg);
+    store_digits(out.s, cbase + r, v);
+  }
 }
 
 // One FP64-accurate purification step for every part, in one persistent launch (one CTA
@@ -180,19 +303,30 @@ __device__ __forceinline__ void oz_issue_stage(uint32_t tmem, uint64_t da, uint6
   }
 }
 
+// ADJ: the adjoint step (see the top of the file): K runs over [Xbar | X] x [X ; Xbar],
+// diagonal tiles load both operands, the epilogue forms Xbar_new in FP64 without digits
+// or traces.
+template <bool ADJ>
 __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
   constexpr int T = OZ_SLICES;
   constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
 
   int step = a.step;
-  if (a.mode == SQ_FORWARD) {
+  const bool rec = !ADJ && a.mode == SQ_RECOMPUTE;
+  int n = 0;
+  if (ADJ || rec) {
+    // reverse step `step` exists iff step <= n; a rebuilt X_step is read iff step < n
+    n = *(volatile int32_t*)&a.ctl.st->steps;
+    if (ADJ ? step > n : step >= n) return;
+  } else if (a.mode == SQ_FORWARD) {
     if (*(volatile int32_t*)&a.ctl.st->stopped) return;
   } else {
     const int32_t stt = *(volatile int32_t*)&a.ctl.st->status;
     if (stt == ST_NONFINITE || stt == ST_TIMEOUT) return;
     step = *(volatile int32_t*)&a.ctl.st->steps + 1;
   }
-  const int dbi = (step - 1) & 1, dbo = step & 1;  // digit buffers read / written
+  // digit buffers read / written (the adjoint's sets are passed explicitly)
+  const int dbi = (ADJ || rec) ? 0 : (step - 1) & 1, dbo = (ADJ || rec) ? 0 : step & 1;
 
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -213,6 +347,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const CUtensorMap* maps = reinterpret_cast<const CUtensorMap*>(a.maps) + (size_t)dbi * T * a.nparts;
   const CUtensorMap* maps_mn = reinterpret_cast<const CUtensorMap*>(a.maps_mn) + (size_t)dbi * T * a.nparts;
+  const CUtensorMap* maps_b = reinterpret_cast<const CUtensorMap*>(a.maps_b);
+  const CUtensorMap* maps_mn_b = reinterpret_cast<const CUtensorMap*>(a.maps_mn_b);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < OZ_STAGES; ++s) {
@@ -241,12 +377,19 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
     for (int ti = blockIdx.x; ti < a.ntiles && !bad; ti += gridDim.x) {
       const Tile t = a.tiles[ti];
       const int sz = a.parts[t.part].s;
-      const bool dg = t.ti == t.tj;
+      const bool dg = !ADJ && t.ti == t.tj;  // X X on a diagonal tile: B is A
       for (int pass = 0; pass < 2 && !bad; ++pass) {
         const int nd = pass == 0 ? T : OZ_SPLIT;  // digits the pass multiplies
         const int sub = oz_slices_per_stage(nd, dg);
         const int nk = (sz + sub * OZ_BK - 1) / (sub * OZ_BK);
-        for (int kb = 0; kb < nk; ++kb, ++g) {
+        for (int kb = 0; kb < (ADJ ? 2 * nk : nk); ++kb, ++g) {
+          // the adjoint's first nk stages multiply Xbar (rows I) by X (rows J), the rest X by Xbar
+          const bool h2 = ADJ && kb >= nk;
+          const int kq = h2 ? kb - nk : kb;
+          const CUtensorMap* const mA = (ADJ && !h2) ? maps_b : maps;
+          const CUtensorMap* const mmA = (ADJ && !h2) ? maps_mn_b : maps_mn;
+          const CUtensorMap* const mB = h2 ? maps_b : maps;
+          const CUtensorMap* const mmB = h2 ? maps_mn_b : maps_mn;
           const int s = g % OZ_STAGES;
           if (g >= OZ_STAGES && !mbar_wait(empty(s), ((g / OZ_STAGES) - 1) & 1, abort_flag)) {
             bad = true;
@@ -258,23 +401,22 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
           // the slices of one stage lie in one 128-block of K
           for (int u = 0; u < sub; ++u)
           for (int qq = 0; qq < nd; ++qq) {
-            const int k0 = (kb * sub + u) * OZ_BK;
+            const int k0 = (kq * sub + u) * OZ_BK;
             const int kt = k0 / 128;
             const int q = qq, slot = u * nd + qq;  // digit, tile slot within the stage
-            const CUtensorMap* m = maps + (size_t)q * a.nparts + t.part;
-            const CUtensorMap* mm = maps_mn + (size_t)q * a.nparts + t.part;
+            const size_t at = (size_t)q * a.nparts + t.part;
             if (kt <= t.ti) {
-              tma_load_2d(tileA(s, slot), m, k0, t.ti * 128, full(s));
+              tma_load_2d(tileA(s, slot), mA + at, k0, t.ti * 128, full(s));
             } else {
-              tma_load_2d(tileA(s, slot), mm, t.ti * 128, k0, full(s));
-              tma_load_2d(tileA(s, slot) + OZ_DTILE / 2, mm, t.ti * 128 + 64, k0, full(s));
+              tma_load_2d(tileA(s, slot), mmA + at, t.ti * 128, k0, full(s));
+              tma_load_2d(tileA(s, slot) + OZ_DTILE / 2, mmA + at, t.ti * 128 + 64, k0, full(s));
             }
             if (dg) continue;
             if (kt <= t.tj) {
-              tma_load_2d(tileB(s, slot), m, k0, t.tj * 128, full(s));
+              tma_load_2d(tileB(s, slot), mB + at, k0, t.tj * 128, full(s));
             } else {
-              tma_load_2d(tileB(s, slot), mm, t.tj * 128, k0, full(s));
-              tma_load_2d(tileB(s, slot) + OZ_DTILE / 2, mm, t.tj * 128 + 64, k0, full(s));
+              tma_load_2d(tileB(s, slot), mmB + at, t.tj * 128, k0, full(s));
+              tma_load_2d(tileB(s, slot) + OZ_DTILE / 2, mmB + at, t.tj * 128 + 64, k0, full(s));
             }
           }
         }
@@ -292,7 +434,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
     for (int ti = blockIdx.x; ti < a.ntiles && !bad; ti += gridDim.x, ++u) {
       const Tile t = a.tiles[ti];
       const int sz = a.parts[t.part].s;
-      const bool dg = t.ti == t.tj;
+      const bool dg = !ADJ && t.ti == t.tj;
       for (int pass = 0; pass < 2 && !bad; ++pass) {
         const int nd = pass == 0 ? T : OZ_SPLIT;
         const int sub = oz_slices_per_stage(nd, dg);
@@ -306,7 +448,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
           break;
         }
         tc_fence_after();
-        for (int kb = 0; kb < nk; ++kb, ++g) {
+        for (int kb = 0; kb < (ADJ ? 2 * nk : nk); ++kb, ++g) {
+          const int kq = (ADJ && kb >= nk) ? kb - nk : kb;
           const int s = g % OZ_STAGES;
           if (!mbar_wait(full(s), (g / OZ_STAGES) & 1, abort_flag)) {
             bad = true;
@@ -316,7 +459,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
           // pairs (q, d - q) of every group of the pass; both digits are < d1 <= T.  Operands
           // right of the tile's own block came in MN-major (transpose bits 15 / 16); a K = 16
           // step advances 32 B in a K-major row, 2 KB (16 K values) in an MN-major tile
-          const int kt = kb * sub * OZ_BK / 128;
+          const int kt = kq * sub * OZ_BK / 128;
           const bool amn = kt > t.ti, bmn = kt > t.tj;
           const uint64_t da = amn ? smem_desc_mn128(tileA(s, 0), OZ_DTILE / 2) : smem_desc_sw<2 * OZ_BK>(tileA(s, 0));
           const uint64_t db = dg ? da
@@ -340,11 +483,18 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
     const int m = quarter * 32 + lane;
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
     long long* acc = a.acc + (size_t)blockIdx.x * (128 * 128);
-    const bool mirror = a.lower_every > 0 && step % a.lower_every == 0;
     int8_t alf;
-    if (a.mode == SQ_TAIL_FIRST) alf = (a.ctl.traces[step - 1] <= (double)a.ctl.nocc) ? (int8_t)1 : (int8_t)-1;
+    if (ADJ || rec) alf = a.ctl.alpha[step];  // the recorded branch of step `step`
+    else if (a.mode == SQ_TAIL_FIRST) alf = (a.ctl.traces[step - 1] <= (double)a.ctl.nocc) ? (int8_t)1 : (int8_t)-1;
     else if (a.mode == SQ_TAIL_NEXT) alf = (int8_t)(-a.ctl.alpha[step - 1]);
     else alf = a.ctl.alpha[step];
+    // the adjoint's Xbar ping-pong: in = buffer (n - step) & 1, out = the other
+    const double* xin = a.xin;
+    double* xout = a.xout;
+    if (ADJ && ((n - step) & 1)) {
+      xin = a.xout;
+      xout = const_cast<double*>(a.xin);
+    }
     int u = 0;
     for (int ti = blockIdx.x; ti < a.ntiles; ti += gridDim.x, ++u) {
       const Tile t = a.tiles[ti];
@@ -352,6 +502,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
       const int64_t ld = p.ld;
       const int r = t.ti * 128 + m, c0 = t.tj * 128;
       const bool diag = t.slot >= 0;
+      const int sg = ADJ ? a.sig[t.part] : 0;  // the adjoint's sums hold (Xbar X + X Xbar) / 2^sg
       double tY = 0.0, tN = 0.0;
       bool ok = true;
       // the two passes: read the groups' sums (integers held exactly in FP32), add them as
@@ -387,10 +538,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
         if (lane == 0) mbar_arrive(aempty(pass));
       }
       if (!ok) *s_err = 1;
-      // final pass of the tile: X_new on the 2^-56 grid, FP64 master, digits, traces; column
-      // writes are coalesced across the warp.  Only tiles on or above the diagonal are kept
-      // (the next step reads the rest MN-major from them); where the lower tiles are wanted
-      // (checkpoints of the adjoint), the mirrored row segment of each thread goes out in
+      // final pass of the tile: X_new on the 2^-56 grid, FP64 master, digits, traces (the
+      // adjoint: Xbar_new, FP64 only); column writes are coalesced across the warp.  Only
+      // tiles on or above the diagonal are kept (the next step reads the rest MN-major from
+      // them); a diagonal tile mirrors its upper triangle, each thread's row segment in
       // groups of 4 as 32-byte (FP64) and 8-byte (digit) vectors
       const bool offd = t.ti != t.tj;
 #pragma unroll 1
@@ -408,7 +559,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
           for (int w = 0; w < 4; ++w) {
             const int j = sub * 4 + w;
             yv[w] = zp[(size_t)j * 128];
-            xv[w] = alf > 0 ? __ldg(a.xin + p.off + (int64_t)(cbase + j) * ld + r) : 0.0;
+            xv[w] = alf > 0 ? __ldg(xin + p.off + (int64_t)(cbase + j) * ld + r) : 0.0;
           }
           double xn4[4];
           uint32_t dw4[4][OZ_SLICES];
@@ -418,47 +569,53 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
             const long long yf = yv[w];
             const int64_t e = (int64_t)c * ld + r;
             const bool upper = offd || c >= r;  // diagonal tiles: upper triangle only
-            const long long xf = (alf > 0 && upper) ? 2 * to_fixed(xv[w]) - yf : yf;
-            xn4[w] = from_fixed(xf);
-            digit_words(xf, dw4[w]);
+            const long long xf = (alf > 0 && upper) ? 2 * to_fixed(xv[w], sg) - yf : yf;
+            xn4[w] = (ADJ && sg == OZ_SIG_NONFINITE) ? __longlong_as_double(0x7FF8000000000000ll) : from_fixed(xf, sg);
+            if (!ADJ) digit_words(xf, dw4[w]);
             if (upper) {
-              __stcs(a.xout + p.off + e, xn4[w]);
+              __stcs(xout + p.off + e, xn4[w]);
+              if (!ADJ) {
 #pragma unroll
-              for (int q = 0; q < OZ_SLICES; ++q)
-                __stcs(a.digits[dbo].s[q] + p.off + e, (unsigned short)(dw4[w][q] >> 16));
-              if (c == r && diag && r < p.c) {
+                for (int q = 0; q < OZ_SLICES; ++q)
+                  __stcs(a.digits[dbo].s[q] + p.off + e, (unsigned short)(dw4[w][q] >> 16));
+              }
+              if (!ADJ && !rec && c == r && diag && r < p.c) {
                 tY += from_fixed(yf);
                 tN += xn4[w];
               }
             }
           }
           const int64_t em = p.off + (int64_t)r * ld + cbase + sub * 4;
-          if (offd ? mirror : cbase + sub * 4 > r) {
-            // the four mirrored elements are contiguous in column r: vector stores (in a
-            // diagonal tile, whenever all four lie right of the diagonal)
-            double2* xm = reinterpret_cast<double2*>(a.xout + em);
+          if (!offd && cbase + sub * 4 > r) {
+            // the four mirrored elements are contiguous in column r: vector stores whenever
+            // all four lie right of the diagonal
+            double2* xm = reinterpret_cast<double2*>(xout + em);
             __stcs(xm, make_double2(xn4[0], xn4[1]));
             __stcs(xm + 1, make_double2(xn4[2], xn4[3]));
+            if (!ADJ) {
 #pragma unroll
-            for (int q = 0; q < OZ_SLICES; ++q) {
-              uint2 pk;  // upper halves of two words per 32 bits
-              pk.x = __byte_perm(dw4[0][q], dw4[1][q], 0x7632);
-              pk.y = __byte_perm(dw4[2][q], dw4[3][q], 0x7632);
-              __stcs(reinterpret_cast<uint2*>(a.digits[dbo].s[q] + em), pk);
+              for (int q = 0; q < OZ_SLICES; ++q) {
+                uint2 pk;  // upper halves of two words per 32 bits
+                pk.x = __byte_perm(dw4[0][q], dw4[1][q], 0x7632);
+                pk.y = __byte_perm(dw4[2][q], dw4[3][q], 0x7632);
+                __stcs(reinterpret_cast<uint2*>(a.digits[dbo].s[q] + em), pk);
+              }
             }
           } else if (!offd) {
 #pragma unroll
             for (int w = 0; w < 4; ++w) {
               if (cbase + sub * 4 + w <= r) continue;
-              __stcs(a.xout + em + w, xn4[w]);
+              __stcs(xout + em + w, xn4[w]);
+              if (!ADJ) {
 #pragma unroll
-              for (int q = 0; q < OZ_SLICES; ++q)
-                __stcs(a.digits[dbo].s[q] + em + w, (unsigned short)(dw4[w][q] >> 16));
+                for (int q = 0; q < OZ_SLICES; ++q)
+                  __stcs(a.digits[dbo].s[q] + em + w, (unsigned short)(dw4[w][q] >> 16));
+              }
             }
           }
         }
       }
-      if (diag) {
+      if (!ADJ && !rec && diag) {
         tY = warp_sum(tY);
         tN = warp_sum(tN);
         if (lane == 0) red[warp - 4] = make_double2(tY, tN);
@@ -478,7 +635,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
   tc_fence_before();
   __syncthreads();
   if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;\n" ::"r"(tmem));
-  if (threadIdx.x == 0 && *s_err) a.ctl.st->timeout = 1;
+  if (threadIdx.x == 0 && *s_err) {
+    a.ctl.st->timeout = 1;
+    if (ADJ || rec) a.ctl.st->status = ST_TIMEOUT;  // no step bookkeeping follows
+  }
+  if (ADJ || rec) return;
 
   if (last_block_ticket(&a.ctl.st->counter)) {
     double u = 0.0, w = 0.0;
@@ -511,12 +672,30 @@ cudaError_t launch_oz_slice(const PartDesc* parts, const ColBlock* blocks, int n
   return cudaGetLastError();
 }
 
-cudaError_t launch_oz_step(const OzStepArgs& a, int grid, cudaStream_t s) {
-  cudaError_t e = cudaFuncSetAttribute(oz_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
+cudaError_t launch_oz_step(const OzStepArgs& a, int grid, cudaStream_t s, bool adjoint) {
+  auto kern = adjoint ? oz_step_kernel<true> : oz_step_kernel<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
   if (e != cudaSuccess) return e;
   int gr = grid < a.ntiles ? grid : a.ntiles;
   if (gr > OZ_MAX_GRID) gr = OZ_MAX_GRID;  // one scratch tile per CTA
-  oz_step_kernel<<<gr, OZ_THREADS, OZ_SMEM, s>>>(a);
+  kern<<<gr, OZ_THREADS, OZ_SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_oz_adj_scale(const PartDesc* parts, int nparts, const Tile* tiles, int ntiles, const double* xb0,
+                                const double* xb1, int after, double* norm, int32_t* sig, const DevState* st,
+                                cudaStream_t s) {
+  if (ntiles > 0) oz_norm_kernel<<<ntiles, 256, 0, s>>>(parts, tiles, xb0, xb1, after, norm, st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  oz_scale_kernel<<<nparts, 256, 0, s>>>(parts, after, norm, sig, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_oz_digits(const PartDesc* parts, const ColBlock* blocks, int nblocks, const double* x0,
+                             const double* x1, int after, int need, const OzSlices& out, const int32_t* sig,
+                             const DevState* st, cudaStream_t s) {
+  oz_digits_kernel<<<nblocks, 32 * COLS_PER_BLOCK, 0, s>>>(parts, blocks, x0, x1, after, need, out, sig, st);
   return cudaGetLastError();
 }
 

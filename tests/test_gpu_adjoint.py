@@ -137,11 +137,12 @@ def test_fp32_checkpoint_interval_does_not_change_the_gradient(g, k):
     assert torch.equal(hb4, hbk)
 
 
-@pytest.mark.parametrize("k", [3, 8])
-def test_adjoint_of_the_emulated_fp64_forward(g, k):
-    """FP64 adjoint behind the emulated FP64 forward: the emulated steps keep only upper
-    tiles except at checkpoints, which the reverse sweep rebuilds from."""
-    s = make_workload("tb4k")
+@pytest.mark.parametrize("case,k", [("small", 3), ("tb512", 8), ("tb4k", 3), ("tb4k", 8)])
+def test_adjoint_of_the_emulated_fp64_forward(g, case, k):
+    """Emulated FP64 adjoint (reverse steps and rebuilt iterates from BF16 digit products,
+    Xbar digits scaled per part) against the oracle's adjoint on the same branch sequence."""
+    s = {"small": lambda: make_tb_system(48, 4, 3.0, seed=21), "tb512": lambda: make_workload("tb512"),
+         "tb4k": lambda: make_workload("tb4k")}[case]()
     plan, h, hist, pb, Pbar, hb = run_adjoint(g, s, precision="fp64e", ckpt_every=k)
     assert hist["status"] == 0
     ref = oracle.gsp2(s.n, s.rowptr, s.colind, s.vals, s.nocc, s.part, s.nparts, s.g_rowptr, s.g_colind)
@@ -149,3 +150,42 @@ def test_adjoint_of_the_emulated_fp64_forward(g, k):
     want = oracle.gsp2_adjoint(s.n, s.rowptr, s.colind, s.vals, ref, Pbar)
     err = float(np.max(np.abs(hb.cpu().numpy() - want)))
     assert err <= 1e-9 * max(1.0, float(np.max(np.abs(want)))), err
+    st, _ = plan.status()
+    assert st == 0
+
+
+def test_emulated_adjoint_is_exact_under_power_of_two_scaling(g):
+    """Xbar's digits carry a per-part power-of-two scale taken from its row norms, so scaling
+    Pbar by 2^e scales every step's scale exponent by e and Hbar exactly by 2^e, far outside
+    the range a fixed scale would hold."""
+    import torch
+    s = make_workload("tb512")
+    plan = g.GSP2(s.n, s.rowptr, s.colind, s.nocc, s.part, s.nparts, s.g_rowptr, s.g_colind, device="cuda:0",
+                  precision="fp64e", ckpt_every=4)
+    plan.density(torch.from_numpy(s.vals).to("cuda:0"))
+    pb, _ = pbar_for_trace_loss(s, plan)
+    pbt = torch.from_numpy(pb).to("cuda:0")
+    hb = plan.backward(pbt).clone()
+    for e in (-300, -60, 60, 300):
+        hbe = plan.backward(pbt * 2.0 ** e)
+        assert torch.equal(hbe, hb * 2.0 ** e), e
+
+
+def test_emulated_adjoint_propagates_nonfinite_like_the_fp64_adjoint(g):
+    """A NaN in Pbar makes every Hbar entry that draws on its part NaN, in the emulated adjoint
+    (the part's scale marks it) as in the FP64 one (through the arithmetic)."""
+    import torch
+    s = make_workload("tb512")
+    out = {}
+    for prec in ("fp64", "fp64e"):
+        plan = g.GSP2(s.n, s.rowptr, s.colind, s.nocc, s.part, s.nparts, s.g_rowptr, s.g_colind, device="cuda:0",
+                      precision=prec, ckpt_every=8)
+        plan.density(torch.from_numpy(s.vals).to("cuda:0"))
+        pb, _ = pbar_for_trace_loss(s, plan)
+        pb[len(pb) // 3] = np.nan
+        out[prec] = plan.backward(torch.from_numpy(pb).to("cuda:0")).cpu().numpy()
+    nan64, nan_e = np.isnan(out["fp64"]), np.isnan(out["fp64e"])
+    assert nan64.any() and not nan64.all()
+    assert np.array_equal(nan64, nan_e)
+    ok = ~nan64
+    assert np.max(np.abs(out["fp64"][ok] - out["fp64e"][ok])) <= 1e-9 * max(1.0, np.max(np.abs(out["fp64"][ok])))
