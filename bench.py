@@ -255,12 +255,13 @@ def kernel_avg_ms(step_ms, nwork):
 
 def adjoint_block(dev, peaks, src, workload="tb4k", reps=3):
     """gsp2_backward of L = sum Pbar .* P on the 4,096-orbital, 32-part workload, checkpoints
-    every 8 steps, for the three plans with an adjoint: FP64 (CUDA cores), FP64 rebuilt from
-    BF16 digit products (tensor cores) and FP32 (CUDA cores).  Device time per backward (after
-    a density call) and the reverse sweep's flops against the peak of the pipe it runs on:
-    algorithmic flops on the CUDA cores (every reverse step 2 s^2 (s+1) per part, every
-    rebuilt iterate s^2 (s+1)); executed BF16 flops on the tensor cores (every reverse step
-    twice, every rebuilt iterate once, the digit products of all upper 128-tiles)."""
+    every 8 steps, for the three kinds of adjoint: FP64 (CUDA cores), FP64 rebuilt from BF16
+    digit products (tensor cores) and FP32 (TF32 hi + lo products on the tensor cores, behind
+    an FP32 forward).  Device time per backward (after a density call) and the reverse sweep's
+    flops against the peak of the pipe it runs on: algorithmic flops on the CUDA cores (every
+    reverse step 2 s^2 (s+1) per part, every rebuilt iterate s^2 (s+1)); executed flops on the
+    tensor cores (every reverse step twice, every rebuilt iterate once, all products of all
+    upper 128-tiles)."""
     import numpy as np
     import torch
     from paper_1801_10016_gb300.gsp2 import GSP2
@@ -295,13 +296,18 @@ def adjoint_block(dev, peaks, src, workload="tb4k", reps=3):
                            f"executed BF16 tensor flops of the {OZ_PRODUCTS} digit products per upper 128-tile: "
                            "reverse steps twice (K = 2s), rebuilt iterates once")
             bound = "tensor"
+        elif prec == "fp32":
+            flops = (2.0 * n + rebuilt) * tc_exec_flops(sz, 32, 3)
+            peak = peaks["bf16_tflops"] * NOMINAL["tf32"] / NOMINAL["bf16"]
+            psrc = f"{src} bf16 x nominal tf32/bf16 (of measured)"
+            kern, fdesc = ("square_tc_persistent_kernel<tf32,3,adjoint> + <tf32,3,rebuild>",
+                           "executed TF32 tensor flops of the 3 products per upper 128-tile: reverse steps twice "
+                           "(K = 2s), rebuilt iterates once")
+            bound = "tensor"
         else:
             flops = (2.0 * n + rebuilt) * float(np.sum(sz * sz * (sz + 1.0)))
-            if prec == "fp64":
-                peak, psrc = peaks["bf16_tflops"] * NOMINAL["fp64"] / NOMINAL["bf16"], f"{src} bf16 x nominal fp64/bf16"
-            else:
-                peak, psrc = 152 * 128 * 2 * 2.07e9 / 1e12, "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"
-            kern = f"adj_step_kernel<{'double' if prec == 'fp64' else 'float'}> + square_simt_kernel recompute"
+            peak, psrc = peaks["bf16_tflops"] * NOMINAL["fp64"] / NOMINAL["bf16"], f"{src} bf16 x nominal fp64/bf16"
+            kern = "adj_step_kernel<double> + square_simt_kernel recompute"
             fdesc = "reverse steps 2 s^2 (s+1) + rebuilt iterates s^2 (s+1), per part"
             bound = "alu"
         out[prec] = {"ms_per_backward": 1e3 * t, "steps": n, "rebuilt_iterates": rebuilt,

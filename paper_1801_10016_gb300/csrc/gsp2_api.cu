@@ -40,6 +40,11 @@ struct WsLayout {
   std::vector<size_t> adj_dig;    // adj_dig[set * OZ_SLICES + t]
   size_t adj_maps, adj_maps_mn;   // CUtensorMap[k + 1][OZ_SLICES][nparts]
   size_t adj_norm, adj_sig;       // double[sum of s], int32[nparts]
+  // FP32 adjoint of the low-precision plans: TF32 (hi, lo) operand arenas aop[2 set + lo],
+  // sets 0..S-1 for rebuilt iterates, S and S + 1 for Xbar's ping-pong (in the FP64 tail
+  // arenas d[0], d[1], which the backward does not need); their tensor maps
+  std::vector<size_t> aop;
+  size_t aop_maps;                // CUtensorMap[2 (S + 2)][nparts]
   size_t mask;                    // uint8[nnz_p]: |P| > tau flags of gsp2_threshold_graph
   std::vector<size_t> tailf;      // low-precision adjoint: FP32 iterates of the FP64 tail, recomputed
   size_t slots, rslots, state, alpha, traces, idem, step_arena;
@@ -247,13 +252,17 @@ static void build_layout(gsp2_plan* h) {
     L.ckpt.clear();
     L.seg.clear();
     L.tailf.clear();
-    L.xb0 = L.xb1 = 0;
+    L.aop.clear();
+    L.xb0 = L.xb1 = L.aop_maps = 0;
     if (k > 0) {
       for (int c = 0; c <= h->opt.max_steps / k; ++c) L.ckpt.push_back(take(af));
       for (int j = 1; j < k; ++j) L.seg.push_back(take(af));
       L.xb0 = take(af);
       L.xb1 = take(af);
       for (int t = 0; t < h->opt.fp64_tail_steps; ++t) L.tailf.push_back(take(af));
+      const int nsets = std::max(k, h->opt.fp64_tail_steps);
+      for (int q = 0; q < 2 * nsets; ++q) L.aop.push_back(take(af));
+      L.aop_maps = take((size_t)2 * (nsets + 2) * h->parts.size() * 128);
     }
     h->mf_of_step.assign((size_t)h->opt.max_steps + 1 + MAX_TAIL, 0);
     for (size_t i = 0; i < h->mf_of_step.size(); ++i)
@@ -272,6 +281,11 @@ static void build_layout(gsp2_plan* h) {
     }
     L.d[0] = take(ab);
     L.d[1] = take(ab);
+    if (k > 0)
+      for (int b = 0; b < 2; ++b) {
+        L.aop.push_back(L.d[b]);
+        L.aop.push_back(L.d[b] + af);
+      }
     if (h->use_oz) {
       for (int b = 0; b < 2; ++b)
         for (int t = 0; t < OZ_SLICES; ++t) L.oz_slice[b][t] = take((size_t)h->arena_elems * 2);
@@ -681,6 +695,29 @@ extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t byt
         if (r != 0) return fail(h, GSP2_E_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string(r));
       }
       CU(h, up(L.maps, maps.data(), maps.size()));
+    }
+    if (!L.aop.empty()) {
+      // the FP32 adjoint: maps over its TF32 operand arenas; its iterate arenas start zeroed,
+      // so that the padding columns the CUDA-core steps never write stay zero
+      void* enc = nullptr;
+      cudaDriverEntryPointQueryResult q{};
+      CU(h, cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &enc, 12000, cudaEnableDefault, &q));
+      if (!enc || q != cudaDriverEntryPointSuccess)
+        return fail(h, GSP2_E_CUDA, "cuTensorMapEncodeTiled not available from the driver");
+      const size_t np = h->parts.size();
+      std::vector<unsigned char> amaps(L.aop.size() * np * 128, 0);
+      for (size_t i = 0; i < L.aop.size(); ++i) {
+        const int r = encode_part_maps(enc, amaps.data() + i * np * 128, h->parts.data(), (int)np, h->ws + L.aop[i], 1);
+        if (r != 0) return fail(h, GSP2_E_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string(r));
+      }
+      CU(h, up(L.aop_maps, amaps.data(), amaps.size()));
+      const size_t af = (size_t)h->arena_elems * sizeof(float);
+      std::vector<size_t> zero(L.ckpt);
+      zero.insert(zero.end(), L.seg.begin(), L.seg.end());
+      zero.insert(zero.end(), L.tailf.begin(), L.tailf.end());
+      zero.push_back(L.xb0);
+      zero.push_back(L.xb1);
+      for (size_t off : zero) CU(h, cudaMemsetAsync(h->ws + off, 0, af, s));
     }
   }
   CU(h, up(L.gblocks, h->gblocks.data(), h->gblocks.size() * sizeof(ColBlock)));
@@ -1257,7 +1294,7 @@ static gsp2_status enqueue_backward(gsp2_plan* h, const double* pbar, double* hb
     }
     for (int i = std::min(c0 + k, M); i >= c0 + 1; --i) {
       const double* X = (i - 1 == c0) ? ck : (const double*)(w + L.seg[i - 1 - c0 - 1]);
-      CU(h, launch_adj_step<double>(parts, tiles, nt, X, xb0, xb1, alpha, st, i, 0, s));
+      CU(h, launch_adj_step<double>(parts, tiles, nt, X, xb0, xb1, alpha, st, i, s));
     }
   }
   CU(h, launch_adj_hbar<double>(h->n, (const int64_t*)(w + L.rowptr), (const int32_t*)(w + L.colind),
@@ -1266,43 +1303,80 @@ static gsp2_status enqueue_backward(gsp2_plan* h, const double* pbar, double* hb
   return GSP2_OK;
 }
 
-// Adjoint of a low-precision plan, in FP32 on the CUDA cores: the T FP64 tail steps came
-// last, so they are reversed first, on FP32 iterates rebuilt from the loop's last iterate
-// X_L (L = n - T is known only on the device: these launches count back from n); then the
-// loop's steps, from the FP32 checkpoints the forward kept every k steps.
+// Adjoint of a low-precision plan, in FP32 with TF32 hi + lo products on the tensor cores
+// (three products per K step, as the tf32x3 squaring): the T FP64 tail steps came last, so
+// they are reversed first, on FP32 iterates rebuilt from the loop's last iterate X_L
+// (L = n - T is known only on the device: these launches count back from n); then the
+// loop's steps, from the FP32 checkpoints the forward kept every k steps.  Every FP32
+// iterate the sweep reads gets its TF32 operand copies (a split of a stored iterate, or the
+// rebuild's own output); Xbar keeps its master and operands in a ping-pong pair.
 static gsp2_status enqueue_backward_lp(gsp2_plan* h, const double* pbar, double* hbar, cudaStream_t s) {
   const WsLayout& L = h->L;
   char* w = h->ws;
   auto parts = (const PartDesc*)(w + L.parts);
   auto Sall = (const int32_t*)(w + L.S);
-  auto tiles = (const Tile*)(w + L.tiles);
   auto gbl = (const ColBlock*)(w + L.gblocks);
   auto st = (DevState*)(w + L.state);
   auto alpha = (int8_t*)(w + L.alpha);
   float* xb0 = (float*)(w + L.xb0);
   float* xb1 = (float*)(w + L.xb1);
   const int k = h->opt.ckpt_every, M = h->opt.max_steps, T = h->opt.fp64_tail_steps;
-  const int nt = (int)h->tiles.size();
+  const int64_t ne = h->arena_elems;
+  const size_t np = h->parts.size();
+  const int nsets = (int)L.aop.size() / 2 - 2;  // operand sets of rebuilt iterates
   StepCtl ctl{st, alpha, (double*)(w + L.traces), (double*)(w + L.idem), h->nocc, h->opt.idem_tol,
               h->opt.trace_tol, MODE_REPLAY, M, 1, T};
   auto tf = [&](int t) { return (float*)(w + L.tailf[(size_t)t]); };
+  auto aop = [&](int set, int lo) { return (void*)(w + L.aop[(size_t)(2 * set + lo)]); };
+  auto amap = [&](int set, int lo) { return (const void*)(w + L.aop_maps + (size_t)(2 * set + lo) * np * 128); };
+  TcStepArgs base{};
+  base.parts = parts;
+  base.tiles = (const Tile*)(w + L.tc_tiles);
+  base.ntiles = (int)h->tc_tiles.size();
+  base.ctl = ctl;
+  base.adj_tail = T;
+  for (int b = 0; b < 2; ++b) {
+    base.map_hi[b] = amap(nsets + b, 0);
+    base.map_lo[b] = amap(nsets + b, 1);
+    base.master[b] = b ? xb1 : xb0;
+    base.op_hi[b] = aop(nsets + b, 0);
+    base.op_lo[b] = aop(nsets + b, 1);
+  }
+  // X_step rebuilt from X_{step-1} (operand set `in`, master xin) into set `out`, master xout
+  auto rebuild = [&](int in, const float* xin, int out, float* xout, int step) {
+    TcStepArgs a = base;
+    a.xmap_hi = amap(in, 0);
+    a.xmap_lo = amap(in, 1);
+    a.xin = xin;
+    a.xout = xout;
+    a.xo_hi = aop(out, 0);
+    a.xo_lo = aop(out, 1);
+    a.step = step;
+    return launch_tc_adjoint(a, h->num_sms, true, s);
+  };
+  // reverse step `step` with X_{step-1} in operand set `x`
+  auto reverse = [&](int x, int step) {
+    TcStepArgs a = base;
+    a.xmap_hi = amap(x, 0);
+    a.xmap_lo = amap(x, 1);
+    a.step = step;
+    return launch_tc_adjoint(a, h->num_sms, false, s);
+  };
   CU(h, launch_adj_seed<float>(parts, gbl, (int)h->gblocks.size(), Sall, (const int32_t*)(w + L.invperm),
                                (const int64_t*)(w + L.pcolptr), pbar, xb0, s));
+  CU(h, launch_split_tf32(xb0, aop(nsets, 0), aop(nsets, 1), ne, st, 0, 0, s));
   if (T > 0) {
-    CU(h, launch_copy_iterate((const float* const*)(w + L.master_of_step), tf(0), h->arena_elems, st, T, s));
-    for (int t = 1; t < T; ++t) CU(h, launch_recompute_fp32(parts, tiles, nt, tf(t - 1), tf(t), ctl, t - T, s));
-    for (int t = T; t >= 1; --t) CU(h, launch_adj_step<float>(parts, tiles, nt, tf(t - 1), xb0, xb1, alpha, st, t - T, T, s));
+    CU(h, launch_copy_iterate((const float* const*)(w + L.master_of_step), tf(0), ne, st, T, s));
+    CU(h, launch_split_tf32(tf(0), aop(0, 0), aop(0, 1), ne, st, 0, 0, s));
+    for (int t = 1; t < T; ++t) CU(h, rebuild(t - 1, tf(t - 1), t, tf(t), t - T));
+    for (int t = T; t >= 1; --t) CU(h, reverse(t - 1, t - T));
   }
   for (int c0 = (M / k) * k; c0 >= 0; c0 -= k) {
     const float* ck = (const float*)(w + L.ckpt[c0 / k]);
-    for (int j = 1; j < k && c0 + j < M; ++j) {
-      const float* xin = (j == 1) ? ck : (const float*)(w + L.seg[j - 2]);
-      CU(h, launch_recompute_fp32(parts, tiles, nt, xin, (float*)(w + L.seg[j - 1]), ctl, c0 + j, s));
-    }
-    for (int i = std::min(c0 + k, M); i >= c0 + 1; --i) {
-      const float* X = (i - 1 == c0) ? ck : (const float*)(w + L.seg[i - 1 - c0 - 1]);
-      CU(h, launch_adj_step<float>(parts, tiles, nt, X, xb0, xb1, alpha, st, i, T, s));
-    }
+    CU(h, launch_split_tf32(ck, aop(0, 0), aop(0, 1), ne, st, c0 + 1, T, s));
+    for (int j = 1; j < k && c0 + j < M; ++j)
+      CU(h, rebuild(j - 1, (j == 1) ? ck : (const float*)(w + L.seg[j - 2]), j, (float*)(w + L.seg[j - 1]), c0 + j));
+    for (int i = std::min(c0 + k, M); i >= c0 + 1; --i) CU(h, reverse(i - 1 - c0, i));
   }
   CU(h, launch_adj_hbar<float>(h->n, (const int64_t*)(w + L.rowptr), (const int32_t*)(w + L.colind),
                                (const int64_t*)(w + L.memptr), (const int32_t*)(w + L.mempart),

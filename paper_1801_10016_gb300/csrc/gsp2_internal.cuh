@@ -88,6 +88,20 @@ struct TcStepArgs {
   StepCtl ctl;
   int step;                // ignored in tail mode (step = steps applied + 1)
   int tail;                // 0: loop step; 1: first alternating tail step; 2: further ones
+  // FP32 adjoint of the low-precision plans (TF32 hi + lo operands, explicit buffers):
+  // the rebuilt iterate X_step reads the operands of X_{step-1} (xmap_*) and its master
+  // xin and writes master xout and operands xo_*; the reverse step `step` reads the
+  // operands of X_{step-1} (xmap_*) and Xbar's ping-pong (map_*, master, op_* [2], the
+  // roles chosen on the device by step parity).  `step` <= 0 names step n + step (the
+  // FP64 tail steps, counted back from the device's step count n); loop steps above
+  // n - adj_tail are skipped.
+  const void* xmap_hi;
+  const void* xmap_lo;
+  const float* xin;
+  float* xout;
+  void* xo_hi;
+  void* xo_lo;
+  int adj_tail;
 };
 
 // FP64 products rebuilt from BF16 digits (k_oz.cu)

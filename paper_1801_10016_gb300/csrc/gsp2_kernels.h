@@ -19,8 +19,6 @@ cudaError_t launch_residual_fp64(const PartDesc* parts, const Tile* tiles, int n
                                  const double* const* x_of_step, double* rslots, int64_t n, const StepCtl& ctl,
                                  cudaStream_t s);
 cudaError_t launch_threshold(const double* p, int64_t n, double tau, uint8_t* mask, cudaStream_t s);
-cudaError_t launch_recompute_fp32(const PartDesc* parts, const Tile* tiles, int ntiles, const float* xin,
-                                  float* xout, const StepCtl& ctl, int step, cudaStream_t s);
 cudaError_t launch_square_fp32(const PartDesc* parts, const Tile* tiles, int ntiles, const float* xin, float* xout,
                                double2* slots, int nslots, const StepCtl& ctl, int step, cudaStream_t s);
 cudaError_t launch_scatter(const PartDesc* parts, const ColBlock* blocks, int nblocks, const int32_t* Sall,
@@ -37,6 +35,10 @@ cudaError_t launch_gather_lp(int kind, int nprod, const PartDesc* parts, const C
                              const int32_t* Sall, const int64_t* rowptr, const int32_t* colind, const double* vals,
                              float* master, void* op_hi, void* op_lo, double* slots, const StepCtl& ctl,
                              cudaStream_t s);
+// FP32 adjoint of the low-precision plans on the tensor cores (TF32 hi + lo operands)
+cudaError_t launch_tc_adjoint(const TcStepArgs& a, int grid, bool rebuild, cudaStream_t s);
+cudaError_t launch_split_tf32(const float* x, void* hi, void* lo, int64_t n, const DevState* st, int need, int tail,
+                              cudaStream_t s);
 cudaError_t launch_copy_iterate(const float* const* master_of_step, float* out, int64_t n, const DevState* st,
                                 int back, cudaStream_t s);
 cudaError_t launch_convert(const float* const* master_of_step, double* out, int64_t n, const DevState* st,
@@ -62,7 +64,7 @@ cudaError_t launch_adj_seed(const PartDesc* parts, const ColBlock* blocks, int n
                             cudaStream_t s);
 template <typename T>
 cudaError_t launch_adj_step(const PartDesc* parts, const Tile* tiles, int ntiles, const T* X, T* xb0, T* xb1,
-                            const int8_t* alpha, const DevState* st, int step, int tail, cudaStream_t s);
+                            const int8_t* alpha, const DevState* st, int step, cudaStream_t s);
 template <typename T>
 cudaError_t launch_adj_hbar(int64_t n, const int64_t* rowptr, const int32_t* colind, const int64_t* memptr,
                             const int32_t* mempart, const int32_t* memloc, const PartDesc* parts,

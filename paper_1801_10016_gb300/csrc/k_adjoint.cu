@@ -1,5 +1,7 @@
-// Adjoint of the G-SP2 density matrix (FP64, or FP32 for the low-precision plans): seed,
-// reverse purification steps and the scatter-add onto the pattern of H.
+// Adjoint of the G-SP2 density matrix: seed (FP64, or FP32 for the low-precision plans),
+// the reverse purification steps of the native FP64 plans on the CUDA cores, and the
+// scatter-add onto the pattern of H.  (The emulated FP64 plans and the low-precision plans
+// run their reverse steps on the tensor cores: k_oz.cu, k_tc.cu.)
 //
 // With L = sum Pbar .* P and the branch sequence alpha_1..alpha_n fixed:
 //   seed:   Xbar_n = sym(M_k), M_k[:, j] = Pbar[S_k, g_j] for core j, 0 for halo columns
@@ -48,10 +50,8 @@ __global__ void __launch_bounds__(256) adj_seed_kernel(const PartDesc* __restric
 // Z_IJ = sum_k Xbar[I,k] X[k,J] + X[I,k] Xbar[k,J] with all four slices streamed from
 // columns k of the symmetric Xbar and X.  Result mirrored to (J, I).
 // The Xbar buffers alternate with (n - step) so that skipped steps keep the parity: input
-// xb[(n - step) & 1], output xb[(n - step + 1) & 1], n the steps applied by the forward.
-// `step` > 0 is a step of the loop, done if step <= n - tail (the FP64 tail steps of a
-// low-precision plan come last and are reversed first); `step` <= 0 names step n + step
-// (the tail steps, whose numbers are only known on the device).
+// xb[(n - step) & 1], output xb[(n - step + 1) & 1], n the steps applied by the forward;
+// steps above n are skipped.
 // Four consecutive elements (16-byte aligned for FP32, 32 for FP64) in vector stores.
 __device__ __forceinline__ void store4(double* p, double a, double b, double c, double d) {
   reinterpret_cast<double2*>(p)[0] = make_double2(a, b);
@@ -71,15 +71,10 @@ __global__ void __launch_bounds__(256, 2) adj_step_kernel(const PartDesc* __rest
                                                           const Tile* __restrict__ tiles, const T* __restrict__ Xall,
                                                           T* __restrict__ xb0, T* __restrict__ xb1,
                                                           const int8_t* __restrict__ alpha, const DevState* st,
-                                                          int step, int tail) {
+                                                          int step) {
   constexpr int ABK = AdjBK<T>::v;
   const int n = *(volatile const int32_t*)&st->steps;
-  if (step <= 0) {
-    step += n;
-    if (step < 1) return;
-  } else if (step > n - tail) {
-    return;
-  }
+  if (step > n) return;
   const T* XBin = ((n - step) & 1) ? xb1 : xb0;
   T* XBout = ((n - step) & 1) ? xb0 : xb1;
   __shared__ __align__(16) T S1[2][ABK][SQ_TILE];  // Xbar rows I
@@ -215,8 +210,8 @@ cudaError_t launch_adj_seed(const PartDesc* parts, const ColBlock* blocks, int n
 
 template <typename T>
 cudaError_t launch_adj_step(const PartDesc* parts, const Tile* tiles, int ntiles, const T* X, T* xb0, T* xb1,
-                            const int8_t* alpha, const DevState* st, int step, int tail, cudaStream_t s) {
-  adj_step_kernel<T><<<ntiles, 256, 0, s>>>(parts, tiles, X, xb0, xb1, alpha, st, step, tail);
+                            const int8_t* alpha, const DevState* st, int step, cudaStream_t s) {
+  adj_step_kernel<T><<<ntiles, 256, 0, s>>>(parts, tiles, X, xb0, xb1, alpha, st, step);
   return cudaGetLastError();
 }
 
@@ -233,12 +228,12 @@ cudaError_t launch_adj_hbar(int64_t n, const int64_t* rowptr, const int32_t* col
 #define GSP2_ADJ_INSTANTIATE(T)                                                                                     \
   template cudaError_t launch_adj_seed<T>(const PartDesc*, const ColBlock*, int, const int32_t*, const int32_t*,   \
                                           const int64_t*, const double*, T*, cudaStream_t);                        \
-  template cudaError_t launch_adj_step<T>(const PartDesc*, const Tile*, int, const T*, T*, T*, const int8_t*,      \
-                                          const DevState*, int, int, cudaStream_t);                                \
   template cudaError_t launch_adj_hbar<T>(int64_t, const int64_t*, const int32_t*, const int64_t*, const int32_t*, \
                                           const int32_t*, const PartDesc*, const int32_t*, const T*, const T*,     \
                                           double*, const DevState*, cudaStream_t, int);
 GSP2_ADJ_INSTANTIATE(double)
 GSP2_ADJ_INSTANTIATE(float)
+template cudaError_t launch_adj_step<double>(const PartDesc*, const Tile*, int, const double*, double*, double*,
+                                             const int8_t*, const DevState*, int, cudaStream_t);
 
 }  // namespace gsp2

@@ -146,9 +146,8 @@ __global__ void __launch_bounds__(256) gather_kernel(const PartDesc* __restrict_
 // slot.  The last block sums the slots in a fixed order and runs the bookkeeping.
 //
 // mode: SQ_FORWARD   - step `step`; nothing to do once the loop has stopped;
-//       SQ_RECOMPUTE - adjoint: rebuild X_step from X_{step-1} with the recorded branch
-//                      if step < steps applied (less ctl.tail_steps; step <= 0 counts
-//                      back from the steps applied); no bookkeeping;
+//       SQ_RECOMPUTE - FP64 adjoint: rebuild X_step from X_{step-1} with the recorded
+//                      branch if step < steps applied; no bookkeeping;
 //       SQ_TAIL_FIRST/SQ_TAIL_NEXT - FP64 tail of a low-precision run: step = steps+1;
 //                      the first tail step takes its branch from the trace rule, each
 //                      further one the opposite of the previous, so that eigenvalues
@@ -181,15 +180,7 @@ __global__ void __launch_bounds__(256, 2) square_simt_kernel(const PartDesc* __r
                                                              double* __restrict__ rslots, int64_t n) {
   using V2 = typename Vec2<T>::V;
   if (mode == SQ_RECOMPUTE) {
-    // step > 0: an iterate of the loop, needed when step < n - tail_steps (the last one of
-    // the loop, and the tail's, are rebuilt otherwise); step <= 0: iterate n + step
-    const int n = *(volatile int32_t*)&ctl.st->steps;
-    if (step <= 0) {
-      step += n;
-      if (step < 1) return;
-    } else if (step >= n - ctl.tail_steps) {
-      return;
-    }
+    if (step >= *(volatile int32_t*)&ctl.st->steps) return;  // the sweep never reads X_n
   } else if (mode == SQ_FORWARD) {
     if (*(volatile int32_t*)&ctl.st->stopped) return;
   } else {
@@ -457,13 +448,6 @@ cudaError_t launch_residual_fp64(const PartDesc* parts, const Tile* tiles, int n
 cudaError_t launch_square_fp32(const PartDesc* parts, const Tile* tiles, int ntiles, const float* xin, float* xout,
                                double2* slots, int nslots, const StepCtl& ctl, int step, cudaStream_t s) {
   square_simt_kernel<float><<<ntiles, 256, 0, s>>>(parts, tiles, xin, xout, slots, nslots, ctl, step, SQ_FORWARD,
-                                                   nullptr, nullptr, 0);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_recompute_fp32(const PartDesc* parts, const Tile* tiles, int ntiles, const float* xin,
-                                  float* xout, const StepCtl& ctl, int step, cudaStream_t s) {
-  square_simt_kernel<float><<<ntiles, 256, 0, s>>>(parts, tiles, xin, xout, nullptr, 0, ctl, step, SQ_RECOMPUTE,
                                                    nullptr, nullptr, 0);
   return cudaGetLastError();
 }

@@ -299,10 +299,17 @@ __global__ void __launch_bounds__(256, 2) square_tc_kernel(TcStepArgs a) {
 // lane quarter, so that the epilogue, which writes the master and operand copies of the
 // tile and its mirror, keeps up with the tensor cores).  Same arithmetic and the same
 // bookkeeping as square_tc_kernel.
+//
+// MODE 1 rebuilds iterate X_step of the FP32 adjoint from explicit buffers with the
+// recorded branch; MODE 2 is a reverse step of that adjoint: an upper tile (I, J) of
+// Xbar X + X Xbar is one product over K = 2s, rows I of [Xbar | X] times rows J of
+// [X | Xbar] (both symmetric and stored whole), and Xbar_new = that or 2 Xbar minus it.
+// Neither keeps traces or runs the step bookkeeping.
 constexpr int TC_EPI_WARPS = 16;  // 4 per TMEM lane quarter, 32 columns each
 constexpr int TC_THREADS = 32 * (4 + TC_EPI_WARPS);
+enum : int { TC_STEP = 0, TC_REBUILD = 1, TC_ADJOINT = 2 };
 
-template <int KIND, int NPROD>
+template <int KIND, int NPROD, int MODE = TC_STEP>
 __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcStepArgs a) {
   constexpr int NOPS = NPROD == 3 ? 4 : 2;
   constexpr int STAGES = NPROD == 3 ? 3 : 4;
@@ -313,16 +320,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
   constexpr int NMMA = BKE / KMMA;
   constexpr uint32_t FMT = KIND == 0 ? 1u : 2u;
   constexpr uint32_t IDESC = (1u << 4) | (FMT << 7) | (FMT << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+  static_assert(MODE == TC_STEP || (KIND == 1 && NPROD == 3), "the FP32 adjoint runs on TF32 hi + lo operands");
 
   int step = a.step;
-  if (a.tail) {
+  int n = 0;
+  if (MODE != TC_STEP) {
+    // steps <= 0 count back from n (the tail steps); loop steps end at n - adj_tail, and
+    // the sweep never reads the loop's last iterate from a rebuild
+    n = *(volatile int32_t*)&a.ctl.st->steps;
+    if (step <= 0) {
+      step += n;
+      if (step < 1) return;
+    } else if (step > n - a.adj_tail || (MODE == TC_REBUILD && step == n - a.adj_tail)) {
+      return;
+    }
+  } else if (a.tail) {
     const int32_t stt = *(volatile int32_t*)&a.ctl.st->status;
     if (stt == ST_NONFINITE || stt == ST_TIMEOUT) return;
     step = *(volatile int32_t*)&a.ctl.st->steps + 1;
   } else if (*(volatile int32_t*)&a.ctl.st->stopped) {
     return;
   }
-  const int bi = (step - 1) & 1, bo = step & 1;
+  // iterate buffers read / written; the adjoint's Xbar: in (n - step) & 1, out the other
+  const int bi = MODE == TC_ADJOINT ? (n - step) & 1 : (step - 1) & 1;
+  const int bo = MODE == TC_ADJOINT ? bi ^ 1 : step & 1;
 
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw = smem_u32(smem_raw);
@@ -368,20 +389,34 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
     for (int ti = blockIdx.x; ti < a.ntiles && !bad; ti += gridDim.x) {
       const Tile t = a.tiles[ti];
       const PartDesc p = a.parts[t.part];
-      const CUtensorMap* mhi = reinterpret_cast<const CUtensorMap*>(a.map_hi[bi]) + t.part;
-      const CUtensorMap* mlo = reinterpret_cast<const CUtensorMap*>(a.map_lo[bi]) + t.part;
-      // a diagonal tile needs rows I only (B = A): two K blocks per stage
-      const bool dg = t.ti == t.tj;
+      // operand maps: the step's input iterate (MODE 0: by parity; 1 and 2: the rebuilt X)
+      const CUtensorMap* mhi =
+          reinterpret_cast<const CUtensorMap*>(MODE == TC_STEP ? a.map_hi[bi] : a.xmap_hi) + t.part;
+      const CUtensorMap* mlo =
+          reinterpret_cast<const CUtensorMap*>(MODE == TC_STEP ? a.map_lo[bi] : a.xmap_lo) + t.part;
+      const CUtensorMap* bhi =  // Xbar (adjoint)
+          MODE == TC_ADJOINT ? reinterpret_cast<const CUtensorMap*>(a.map_hi[bi]) + t.part : nullptr;
+      const CUtensorMap* blo = MODE == TC_ADJOINT ? reinterpret_cast<const CUtensorMap*>(a.map_lo[bi]) + t.part : nullptr;
+      // a diagonal tile of X X needs rows I only (B = A): two K blocks per stage
+      const bool dg = MODE != TC_ADJOINT && t.ti == t.tj;
       const int sub = dg ? 2 : 1;
       const int nk = (p.s + sub * BKE - 1) / (sub * BKE);
-      for (int kb = 0; kb < nk; ++kb, ++g) {
+      for (int kb = 0; kb < (MODE == TC_ADJOINT ? 2 * nk : nk); ++kb, ++g) {
         const int s = g % STAGES;
         if (g >= STAGES && !mbar_wait(empty(s), ((g / STAGES) - 1) & 1, abort_flag)) {
           bad = true;
           break;
         }
         mbar_expect_tx(full(s), STAGE_B);
-        if (dg) {
+        if (MODE == TC_ADJOINT) {
+          // first nk blocks: Xbar (rows I) times X (rows J); then X (rows I) times Xbar (rows J)
+          const bool h2 = kb >= nk;
+          const int k0 = (h2 ? kb - nk : kb) * BKE;
+          tma_load_2d(tile_addr(s, 0), h2 ? mhi : bhi, k0, t.ti * 128, full(s));
+          tma_load_2d(tile_addr(s, 1), h2 ? bhi : mhi, k0, t.tj * 128, full(s));
+          tma_load_2d(tile_addr(s, 2), h2 ? mlo : blo, k0, t.ti * 128, full(s));
+          tma_load_2d(tile_addr(s, 3), h2 ? blo : mlo, k0, t.tj * 128, full(s));
+        } else if (dg) {
           for (int u = 0; u < 2; ++u) {
             const int k0 = (2 * kb + u) * BKE;
             tma_load_2d(tile_addr(s, u * (NOPS / 2)), mhi, k0, t.ti * 128, full(s));
@@ -412,8 +447,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
     for (int ti = blockIdx.x; ti < a.ntiles && !bad; ti += gridDim.x, ++i) {
       const Tile t = a.tiles[ti];
       const PartDesc p = a.parts[t.part];
-      const bool dg = t.ti == t.tj;
-      const int nk = (p.s + (dg ? 2 : 1) * BKE - 1) / ((dg ? 2 : 1) * BKE);
+      const bool dg = MODE != TC_ADJOINT && t.ti == t.tj;
+      const int nk = (MODE == TC_ADJOINT ? 2 : 1) * ((p.s + (dg ? 2 : 1) * BKE - 1) / ((dg ? 2 : 1) * BKE));
       const int b = i & 1, u = i >> 1;
       if (u >= 1 && !mbar_wait(tempty(b), (u - 1) & 1, abort_flag)) {
         bad = true;
@@ -467,13 +502,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
       const Tile t = a.tiles[ti];
       const PartDesc p = a.parts[t.part];
       int8_t alf;
-      if (a.tail == 1) alf = (a.ctl.traces[step - 1] <= (double)a.ctl.nocc) ? (int8_t)1 : (int8_t)-1;
+      if (MODE != TC_STEP) alf = a.ctl.alpha[step];  // the recorded branch
+      else if (a.tail == 1) alf = (a.ctl.traces[step - 1] <= (double)a.ctl.nocc) ? (int8_t)1 : (int8_t)-1;
       else if (a.tail == 2) alf = (int8_t)(-a.ctl.alpha[step - 1]);
       else alf = a.ctl.alpha[step];
-      const float* Xi = a.master[bi] + p.off;
-      float* Xo = a.master[bo] + p.off;
-      void* ohi = a.op_hi[bo];
-      void* olo = a.op_lo[bo];
+      const float* Xi = (MODE == TC_REBUILD ? a.xin : a.master[bi]) + p.off;
+      float* Xo = (MODE == TC_REBUILD ? a.xout : a.master[bo]) + p.off;
+      void* ohi = MODE == TC_REBUILD ? a.xo_hi : a.op_hi[bo];
+      void* olo = MODE == TC_REBUILD ? a.xo_lo : a.op_lo[bo];
       const int64_t ld = p.ld;
       const int r0 = t.ti * 128, c0 = t.tj * 128;
       const int r = r0 + m;
@@ -500,7 +536,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
             zd = (cbase + j == r) ? z : zd;
             x[j] = z;
           }
-          if (diag && r >= cbase && r < cbase + 16 && r < p.c) {
+          if (MODE == TC_STEP && diag && r >= cbase && r < cbase + 16 && r < p.c) {
             tY += (double)yd;
             tN += (double)zd;
           }
@@ -536,7 +572,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(tempty(b));
-      if (diag) {
+      if (MODE == TC_STEP && diag) {
         // fixed-order reduction over the epilogue warps (named barrier 1)
         tY = warp_sum(tY);
         tN = warp_sum(tN);
@@ -557,7 +593,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
   tc_fence_before();
   __syncthreads();
   if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;\n" ::"r"(tmem));
-  if (threadIdx.x == 0 && *s_err) a.ctl.st->timeout = 1;
+  if (threadIdx.x == 0 && *s_err) {
+    a.ctl.st->timeout = 1;
+    if (MODE != TC_STEP) a.ctl.st->status = ST_TIMEOUT;  // no step bookkeeping follows
+  }
+  if (MODE != TC_STEP) return;
 
   if (last_block_ticket(&a.ctl.st->counter)) {
     double u = 0.0, w = 0.0;
@@ -873,15 +913,37 @@ static cudaError_t launch_tc_wide(const TcStepArgs& a, int grid, cudaStream_t s)
   return cudaGetLastError();
 }
 
-template <int KIND, int NPROD>
+template <int KIND, int NPROD, int MODE = TC_STEP>
 static cudaError_t launch_tc_persistent(const TcStepArgs& a, int grid, cudaStream_t s) {
   constexpr int NOPS = NPROD == 3 ? 4 : 2;
   constexpr int STAGES = NPROD == 3 ? 3 : 4;
   const int smem = STAGES * NOPS * (int)kTileBytes + 1024 + 8 * (2 * STAGES + 4) + 16 + 16 * TC_EPI_WARPS;
-  cudaError_t e = cudaFuncSetAttribute(square_tc_persistent_kernel<KIND, NPROD>,
+  cudaError_t e = cudaFuncSetAttribute(square_tc_persistent_kernel<KIND, NPROD, MODE>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  square_tc_persistent_kernel<KIND, NPROD><<<grid, TC_THREADS, smem, s>>>(a);
+  square_tc_persistent_kernel<KIND, NPROD, MODE><<<grid, TC_THREADS, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_adjoint(const TcStepArgs& a, int grid, bool rebuild, cudaStream_t s) {
+  const int g = grid < a.ntiles ? grid : a.ntiles;
+  return rebuild ? launch_tc_persistent<1, 3, TC_REBUILD>(a, g, s) : launch_tc_persistent<1, 3, TC_ADJOINT>(a, g, s);
+}
+
+// TF32 hi + lo operands of an FP32 arena (n elements): the operand copies of a checkpoint
+// or of Xbar for the adjoint.  Skipped where need > n - tail (a checkpoint the reverse
+// sweep does not reach).
+__global__ void __launch_bounds__(256) split_tf32_kernel(const float* __restrict__ x, uint32_t* __restrict__ hi,
+                                                         uint32_t* __restrict__ lo, int64_t n, const DevState* st,
+                                                         int need, int tail) {
+  if (need > *(volatile const int32_t*)&st->steps - tail) return;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    store_operands<1, 3>(hi, lo, e, x[e]);
+}
+
+cudaError_t launch_split_tf32(const float* x, void* hi, void* lo, int64_t n, const DevState* st, int need, int tail,
+                              cudaStream_t s) {
+  split_tf32_kernel<<<152 * 8, 256, 0, s>>>(x, (uint32_t*)hi, (uint32_t*)lo, n, st, need, tail);
   return cudaGetLastError();
 }
 
