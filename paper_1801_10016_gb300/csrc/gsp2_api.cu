@@ -39,7 +39,8 @@ struct WsLayout {
   // holds Xbar / 2^sig; their tensor maps; row norms and per-part scales of Xbar
   std::vector<size_t> adj_dig;    // adj_dig[set * OZ_SLICES + t]
   size_t adj_maps, adj_maps_mn;   // CUtensorMap[k + 1][OZ_SLICES][nparts]
-  size_t adj_norm, adj_sig;       // double[sum of s], int32[nparts]
+  size_t adj_norm, adj_sig;       // double[sum of s] (the seed's row norms), int32[nparts]
+  size_t adj_normf;               // float[sum of s]: the reverse steps' row norms on their grid
   // FP32 adjoint of the low-precision plans: TF32 (hi, lo) operand arenas aop[2 set + lo],
   // sets 0..S-1 for rebuilt iterates, S and S + 1 for Xbar's ping-pong (in the FP64 tail
   // arenas d[0], d[1], which the backward does not need); their tensor maps
@@ -319,13 +320,14 @@ static void build_layout(gsp2_plan* h) {
     L.oz_acc = take((size_t)OZ_MAX_GRID * 128 * 128 * 8);
   }
   L.adj_dig.clear();
-  L.adj_maps = L.adj_maps_mn = L.adj_norm = L.adj_sig = 0;
+  L.adj_maps = L.adj_maps_mn = L.adj_norm = L.adj_sig = L.adj_normf = 0;
   if (h->use_oz && k > 0) {
     for (int set = 0; set <= k; ++set)
       for (int t = 0; t < OZ_SLICES; ++t) L.adj_dig.push_back(take((size_t)h->arena_elems * 2));
     L.adj_maps = take((size_t)(k + 1) * OZ_SLICES * h->parts.size() * 128);
     L.adj_maps_mn = take((size_t)(k + 1) * OZ_SLICES * h->parts.size() * 128);
     L.adj_norm = take(h->S.size() * sizeof(double));
+    L.adj_normf = take(h->S.size() * sizeof(float));
     L.adj_sig = take(h->parts.size() * sizeof(int32_t));
   }
   L.total = o;
@@ -671,6 +673,9 @@ extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t byt
       }
       CU(h, up(L.adj_maps, amaps.data(), amaps.size()));
       CU(h, up(L.adj_maps_mn, amaps_mn.data(), amaps_mn.size()));
+      // Xbar's arenas start zeroed, so that padding the seed does not write stays zero
+      CU(h, cudaMemsetAsync(h->ws + L.xb0, 0, (size_t)h->arena_elems * sizeof(double), s));
+      CU(h, cudaMemsetAsync(h->ws + L.xb1, 0, (size_t)h->arena_elems * sizeof(double), s));
     }
   }
   if (!fp64_like(h->opt.precision)) {
@@ -1196,8 +1201,10 @@ extern "C" gsp2_status gsp2_step_times(gsp2_handle h, float* ms, int32_t cap) {
 // Adjoint of an emulated-FP64 plan on the BF16 tensor cores.  For each checkpoint segment
 // the iterates X_{c0} .. X_{c0+k-1} are rebuilt as digit sets (digits of the checkpoint,
 // then emulated steps with the recorded branches); every reverse step multiplies the
-// digits of X_{i-1} with those of Xbar / 2^sig, and the row norms, scales and digits of the
-// new Xbar follow it.  Xbar is kept in its upper 128-tiles like the forward iterates.
+// digits of X_{i-1} with those of Xbar / 2^sig and leaves the new Xbar's per-part scales
+// (from its row norms, summed in the step's epilogue), and the new digits follow.  The
+// seed's scales come from a separate norm pass.  Xbar is kept in its upper 128-tiles like
+// the forward iterates.
 static gsp2_status enqueue_backward_emu(gsp2_plan* h, const double* pbar, double* hbar, cudaStream_t s) {
   const WsLayout& L = h->L;
   char* w = h->ws;
@@ -1213,6 +1220,7 @@ static gsp2_status enqueue_backward_emu(gsp2_plan* h, const double* pbar, double
   double* xb0 = (double*)(w + L.xb0);
   double* xb1 = (double*)(w + L.xb1);
   double* norm = (double*)(w + L.adj_norm);
+  float* normf = (float*)(w + L.adj_normf);
   int32_t* sig = (int32_t*)(w + L.adj_sig);
   const int k = h->opt.ckpt_every, M = h->total_steps;
   const int np = (int)h->parts.size();
@@ -1226,6 +1234,7 @@ static gsp2_status enqueue_backward_emu(gsp2_plan* h, const double* pbar, double
   auto smaps = [&](size_t base, int j) { return (const void*)(w + base + (size_t)j * OZ_SLICES * np * 128); };
   const OzStepArgs base = oz_args(h, ctl);
   CU(h, cudaMemsetAsync(norm, 0, h->S.size() * sizeof(double), s));
+  CU(h, cudaMemsetAsync(normf, 0, h->S.size() * sizeof(float), s));
   CU(h, launch_adj_seed<double>(parts, gbl, (int)h->gblocks.size(), Sall, (const int32_t*)(w + L.invperm),
                                 (const int64_t*)(w + L.pcolptr), pbar, xb0, s));
   CU(h, launch_oz_adj_scale(parts, np, tct, ntc, xb0, xb1, 0, norm, sig, st, s));
@@ -1251,14 +1260,12 @@ static gsp2_status enqueue_backward_emu(gsp2_plan* h, const double* pbar, double
       a.maps_b = smaps(L.adj_maps, k);
       a.maps_mn_b = smaps(L.adj_maps_mn, k);
       a.sig = sig;
+      a.normf = normf;
       a.xin = xb0;
       a.xout = xb1;
       a.step = i;
-      CU(h, launch_oz_step(a, h->num_sms, s, true));
-      if (i > 1) {
-        CU(h, launch_oz_adj_scale(parts, np, tct, ntc, xb0, xb1, i, norm, sig, st, s));
-        CU(h, launch_oz_digits(parts, gbl_ld, ngb, xb0, xb1, i, 0, set(k), sig, st, s));
-      }
+      CU(h, launch_oz_step(a, h->num_sms, s, true));  // also leaves the new Xbar's scales in sig
+      if (i > 1) CU(h, launch_oz_digits(parts, gbl_ld, ngb, xb0, xb1, i, 0, set(k), sig, st, s));
     }
   }
   CU(h, launch_adj_hbar<double>(h->n, (const int64_t*)(w + L.rowptr), (const int32_t*)(w + L.colind),

@@ -128,7 +128,9 @@ struct OzStepArgs {
   const void* maps_mn; // the same with MN-major boxes (64 rows x OZ_BK columns, 128-byte swizzle)
   const void* maps_b;    // adjoint: CUtensorMap[OZ_SLICES][nparts] over the digits of Xbar / 2^sig
   const void* maps_mn_b; // the same, MN-major
-  const int32_t* sig;    // adjoint: per-part scale exponent of Xbar's digits (OZ_SIG_NONFINITE: NaN)
+  int32_t* sig;          // adjoint: per-part scale exponent of Xbar's digits (OZ_SIG_NONFINITE: NaN),
+                         // replaced by the new Xbar's scale by the last block of the step
+  float* normf;          // adjoint: squared row norms of the new Xbar / 2^sig (zero between steps)
   int nparts;
   OzSlices digits[2];
   const double* xin;   // FP64 master of X_{step-1}

@@ -132,7 +132,8 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const PartDesc* __restric
 // Xbar lies in buffer (n - after + 1) & 1 of the pair (x0, x1); kernels for a step that was
 // not run (after > n: the forward stopped earlier) return at once.
 
-// Squared row 2-norms of the symmetric Xbar held in its upper 128-tiles, FP64, added into
+// Squared row 2-norms of the symmetric Xbar held in its upper 128-tiles (the seed; the
+// reverse steps sum theirs in their epilogue), FP64, added into
 // norm[soff + r] for rows r < s: the column sums of an upper tile (I, J) give the entries
 // of rows J within block I (a diagonal tile holds its whole block), and the row sums of an
 // off-diagonal tile the entries of rows I within block J.  One CTA per tile.
@@ -303,9 +304,41 @@ __device__ __forceinline__ void oz_issue_stage(uint32_t tmem, uint64_t da, uint6
   }
 }
 
+// |v| 2^-56 as FP32 (integer instructions, truncated: at most 2^-23 below), for the row
+// norms of the adjoint's new Xbar on its fixed-point grid.
+__device__ __forceinline__ float fixed_to_f32_abs(long long v) {
+  const unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+  if (a == 0) return 0.0f;
+  const int lz = __clzll(a);
+  const uint32_t mant = (uint32_t)((a << lz) >> 40) & 0x7FFFFFu;  // 23 bits below the leading one
+  return __uint_as_float(((uint32_t)(63 - lz - 56 + 127) << 23) | mant);
+}
+
+// Sum of v[j] (j < 16) over the 32 lanes of a warp in 16 shuffles (each step exchanges half
+// of the remaining columns with the partner lane); lanes 2q and 2q + 1 end with the sum of
+// column `col` = 8 b4 + 4 b3 + 2 b2 + b1 (b the lane's bits).
+__device__ __forceinline__ float warp_colsum16(const float (&v)[16], int lane, int& col) {
+  float a8[8], a4[4], a2[2];
+  const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4, h2 = lane & 2;
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    a8[j] = (h16 ? v[j + 8] : v[j]) + __shfl_xor_sync(0xffffffffu, h16 ? v[j] : v[j + 8], 16);
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    a4[j] = (h8 ? a8[j + 4] : a8[j]) + __shfl_xor_sync(0xffffffffu, h8 ? a8[j] : a8[j + 4], 8);
+#pragma unroll
+  for (int j = 0; j < 2; ++j)
+    a2[j] = (h4 ? a4[j + 2] : a4[j]) + __shfl_xor_sync(0xffffffffu, h4 ? a4[j] : a4[j + 2], 4);
+  float a1 = (h2 ? a2[1] : a2[0]) + __shfl_xor_sync(0xffffffffu, h2 ? a2[0] : a2[1], 2);
+  a1 += __shfl_xor_sync(0xffffffffu, a1, 1);
+  col = (h16 ? 8 : 0) + (h8 ? 4 : 0) + (h4 ? 2 : 0) + (h2 ? 1 : 0);
+  return a1;
+}
+
 // ADJ: the adjoint step (see the top of the file): K runs over [Xbar | X] x [X ; Xbar],
 // diagonal tiles load both operands, the epilogue forms Xbar_new in FP64 without digits
-// or traces.
+// or traces and adds its squared row norms (FP32, on the grid of the input scale); the last
+// block turns them into each part's new scale.
 template <bool ADJ>
 __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
   constexpr int T = OZ_SLICES;
@@ -544,11 +577,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
       // them); a diagonal tile mirrors its upper triangle, each thread's row segment in
       // groups of 4 as 32-byte (FP64) and 8-byte (digit) vectors
       const bool offd = t.ti != t.tj;
+      float rown = 0.0f;  // adjoint: squared norm of row r over this thread's upper entries
 #pragma unroll 1
       for (int cc = 0; cc < 2 && ok; ++cc) {
         const int cl = colq * 32 + cc * 16;
         const int cbase = c0 + cl;
         const long long* zp = acc + (size_t)cl * 128 + m;
+        float coln[16];  // adjoint: squares of the entries (r, c) for the norms of rows c
+#pragma unroll
+        for (int j = 0; j < 16; ++j) coln[j] = 0.0f;
 #pragma unroll
         for (int sub = 0; sub < 4; ++sub) {
           // loads of the group first (xin is not written by this launch), so that they are
@@ -572,6 +609,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
             const long long xf = (alf > 0 && upper) ? 2 * to_fixed(xv[w], sg) - yf : yf;
             xn4[w] = (ADJ && sg == OZ_SIG_NONFINITE) ? __longlong_as_double(0x7FF8000000000000ll) : from_fixed(xf, sg);
             if (!ADJ) digit_words(xf, dw4[w]);
+            if (ADJ && upper && r < p.s && c < p.s) {
+              // every stored entry (r, c) adds to the norm of row r, and of row c unless c = r
+              const float f = fixed_to_f32_abs(xf);
+              rown = fmaf(f, f, rown);
+              if (c != r) coln[sub * 4 + w] = f * f;
+            }
             if (upper) {
               __stcs(xout + p.off + e, xn4[w]);
               if (!ADJ) {
@@ -614,7 +657,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
             }
           }
         }
+        if (ADJ) {
+          int col;
+          const float cs = warp_colsum16(coln, lane, col);
+          if (!(lane & 1) && cbase + col < p.s && cs != 0.0f) atomicAdd(&a.normf[p.soff + cbase + col], cs);
+        }
       }
+      if (ADJ && ok && r < p.s && rown != 0.0f) atomicAdd(&a.normf[p.soff + r], rown);
       if (!ADJ && !rec && diag) {
         tY = warp_sum(tY);
         tN = warp_sum(tN);
@@ -639,7 +688,35 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
     a.ctl.st->timeout = 1;
     if (ADJ || rec) a.ctl.st->status = ST_TIMEOUT;  // no step bookkeeping follows
   }
-  if (ADJ || rec) return;
+  if (rec) return;
+  if (ADJ) {
+    // the last block: each part's new scale from the largest squared row norm m (on the grid
+    // of the old scale sg): the smallest e with 2^e >= 2 sqrt(m) (1 + 2^-10), the margin
+    // covering the truncated squares and the FP32 sums; the norms are cleared for the next step
+    if (last_block_ticket(&a.ctl.st->counter)) {
+      for (int k = warp; k < a.nparts; k += OZ_THREADS / 32) {
+        const PartDesc p = a.parts[k];
+        float mx = 0.0f;
+        for (int rr = lane; rr < p.s; rr += 32) {
+          float* q = a.normf + p.soff + rr;
+          mx = fmaxf(mx, __ldcg(q));
+          *q = 0.0f;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) {
+          const int sg = a.sig[k];
+          int e = 0;
+          if (sg != OZ_SIG_NONFINITE && mx > 0.0f) {
+            (void)frexpf(2.0f * sqrtf(mx) * (1.0f + 0.0009765625f), &e);
+            a.sig[k] = sg + e;
+          }
+        }
+      }
+      if (threadIdx.x == 0) a.ctl.st->counter = 0;
+    }
+    return;
+  }
 
   if (last_block_ticket(&a.ctl.st->counter)) {
     double u = 0.0, w = 0.0;

@@ -97,9 +97,10 @@ def test_backward_state_errors(g):
     assert e.value.status == g.E_STATE
 
 
-def test_adjoint_through_tail_steps(g):
+@pytest.mark.parametrize("prec", ["fp64", "fp64e"])
+def test_adjoint_through_tail_steps(g, prec):
     s = make_tb_system(48, 4, 3.0, seed=21)
-    plan, h, hist, pb, Pbar, hb = run_adjoint(g, s, fp64_tail_steps=2, ckpt_every=3)
+    plan, h, hist, pb, Pbar, hb = run_adjoint(g, s, precision=prec, fp64_tail_steps=2, ckpt_every=3)
     ref = oracle.gsp2(s.n, s.rowptr, s.colind, s.vals, s.nocc, s.part, s.nparts, s.g_rowptr, s.g_colind,
                       tail_steps=2)
     assert hist["alphas"] == ref.alphas
