@@ -502,17 +502,18 @@ def run_ours(args):
             if prec != "fp32":
                 # executed tensor flops of one launch: every 128x128 upper tile, K rounded to the stage
                 nt = np.ceil(sizes / 128.0)
-                kst = 64 if prec.startswith("bf16") else 32
+                kst = 32 if prec.startswith("tf32") else 64  # K per stage: 128-byte operand rows
                 kk = np.ceil(sizes / kst) * kst
                 exec_flops = float(np.sum(nt * (nt + 1) / 2 * 2 * 128 * 128 * kk)) * nprod
                 ach = exec_flops / (k_ms / 1e3) / 1e12
+                kname = "tf32" if "tf32" in prec else ("fp16" if "fp16" in prec else "bf16")
                 entry["roofline"] = {"bound": "tensor", "achieved": ach, "peak": tf32_peak if "tf32" in prec
                                      else peaks["bf16_tflops"], "unit": "TFLOP/s",
-                                     "kernel": f"square_tc_persistent_kernel<{'tf32' if 'tf32' in prec else 'bf16'},"
-                                               f"{nprod}>",
+                                     "kernel": f"square_tc_persistent_kernel<{kname},{nprod}>",
                                      "flops": "executed tensor flops per launch (all upper 128-tiles, all products)",
                                      "peak_source": ("measured bf16 burst x nominal tf32/bf16 1100/2250 (of measured)"
-                                                     if "tf32" in prec else "measured bf16 burst (of measured)")}
+                                                     if "tf32" in prec else "measured bf16 burst (of measured; "
+                                                     "fp16 and bf16 share the 16-bit dense rate)")}
                 entry["roofline"]["frac"] = ach / entry["roofline"]["peak"]
             mixed[spec] = entry
         line["mixed"] = mixed
@@ -552,7 +553,7 @@ def main():
     ap.add_argument("--no-mixed", dest="no_mixed", action="store_true")
     ap.add_argument("--no-autotune", dest="no_autotune", action="store_true")
     ap.add_argument("--no-adjoint", dest="no_adjoint", action="store_true")
-    ap.add_argument("--mixed", default="tf32x3,tf32x3:lp1:fp1,tf32x3:lp2,bf16x3,bf16x3:lp2,tf32,bf16,fp32")
+    ap.add_argument("--mixed", default="fp16x3,tf32x3,tf32x3:lp1:fp1,tf32x3:lp2,bf16x3,bf16x3:lp2,tf32,bf16,fp32")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -58,7 +58,7 @@ typedef enum {
  * of one product) and e < 0 or e no longer falls, and finish with
  * `fp64_tail_steps` FP64 steps: the first takes its branch from the trace rule, each
  * further one the opposite branch, so eigenvalues near 0 and near 1 are both purified.
- * The low-precision modes support RECORD only and have no adjoint. */
+ * The low-precision modes support RECORD only; their adjoint runs in FP32 (see ckpt_every). */
 typedef enum {
   GSP2_PREC_FP64 = 0,
   GSP2_PREC_FP32 = 1,   /* FP32 CUDA-core squarings (no tensor cores) */
@@ -66,9 +66,12 @@ typedef enum {
   GSP2_PREC_BF16 = 3,
   GSP2_PREC_BF16X3 = 4, /* split operands hi+lo in BF16, three products, FP32 accumulate */
   GSP2_PREC_TF32X3 = 5, /* split operands hi+lo in TF32, three products, FP32 accumulate */
-  GSP2_PREC_FP64_EMU = 6 /* FP64 results; every product X X rebuilt from 7 base-2^7 digits of X
-                            held in BF16 (28 exact BF16 tensor-core products per tile, groups
-                            summed as 64-bit fixed point), FP64 master copy and epilogue */
+  GSP2_PREC_FP64_EMU = 6, /* FP64 results; every product X X rebuilt from 7 base-2^7 digits of X
+                             held in BF16 (28 exact BF16 tensor-core products per tile, groups
+                             summed as 64-bit fixed point), FP64 master copy and epilogue */
+  GSP2_PREC_FP16X3 = 7  /* split operands hi+lo in FP16 of X 2^14 (22 bits like TF32X3, entries
+                           down to 2^-28 in FP16's normal range), three products at the
+                           16-bit tensor rate, FP32 accumulate, sums scaled back by 2^-28 */
 } gsp2_precision;
 
 typedef enum {
@@ -88,8 +91,9 @@ typedef struct {
                               branch follows the trace rule, each further one the opposite */
   int32_t ckpt_every;      /* adjoint: keep every k-th iterate; 0 = no adjoint; -1 (default) =
                               8 for FP64 and FP64_EMU, 0 for the low-precision modes, whose
-                              adjoint (k > 0, lp_tail_steps = 0) runs in FP32 on CUDA cores from
-                              FP32 checkpoints, the FP64 tail steps reversed in FP32 too */
+                              adjoint (k > 0, lp_tail_steps = 0) runs in FP32 from FP32
+                              checkpoints, products as TF32 hi + lo on the tensor cores, the
+                              FP64 tail steps reversed in FP32 too */
   int32_t use_graph;       /* 1 (default): capture the whole step sequence in a CUDA graph */
   int32_t time_steps;      /* 1: record CUDA events around every purification-step launch
                               (read with gsp2_step_times); default 0 */
@@ -287,7 +291,10 @@ gsp2_status gsp2_autotune(gsp2_handle h, const double* d_hvals, double* d_pvals,
  * pattern of H, through the branch sequence of the last density call (its bounds
  * held fixed).  X^2 steps map Xbar -> Xbar X + X Xbar, 2X - X^2 steps map
  * Xbar -> 2 Xbar - Xbar X - X Xbar; dX0/dH = -1/(eps_max - eps_min) (Eq. 1).
- * Iterates are recomputed from checkpoints kept every `ckpt_every` steps.
+ * Iterates are recomputed from checkpoints kept every `ckpt_every` steps.  FP64 plans
+ * run it on the FP64 pipe, FP64_EMU plans from BF16 digit products (Xbar's digits scaled
+ * by a power of two per part taken from its row norms), the low-precision plans in FP32
+ * with TF32 hi + lo products.
  *  d_pbar  device double[nnz_p]
  *  d_hbar  device double[nnz_h], overwritten; symmetric for a symmetric problem
  * Requires ckpt_every > 0 at create and a completed density call (GSP2_E_STATE).

@@ -140,11 +140,16 @@ constexpr int MAX_TAIL = 8;
 // FP64 results: native FP64 steps or FP64 products rebuilt from BF16 digits
 static bool fp64_like(int prec) { return prec == GSP2_PREC_FP64 || prec == GSP2_PREC_FP64_EMU; }
 
-// tensor-core operand kind (-1: FP32 CUDA cores, 0: BF16, 1: TF32) and products per tile
+// tensor-core operand kind (-1: FP32 CUDA cores, 0: BF16, 1: TF32, 2: FP16 of x 2^14) and
+// products per tile
 static int prec_kind(int prec) {
-  return prec == GSP2_PREC_FP32 ? -1 : (prec == GSP2_PREC_BF16 || prec == GSP2_PREC_BF16X3) ? 0 : 1;
+  if (prec == GSP2_PREC_FP32) return -1;
+  if (prec == GSP2_PREC_BF16 || prec == GSP2_PREC_BF16X3) return 0;
+  return prec == GSP2_PREC_FP16X3 ? 2 : 1;
 }
-static int prec_nprod(int prec) { return (prec == GSP2_PREC_BF16X3 || prec == GSP2_PREC_TF32X3) ? 3 : 1; }
+static int prec_nprod(int prec) {
+  return (prec == GSP2_PREC_BF16X3 || prec == GSP2_PREC_TF32X3 || prec == GSP2_PREC_FP16X3) ? 3 : 1;
+}
 // unit roundoff of one product of the low-precision phase
 static double prec_unit(int prec) {
   switch (prec) {
@@ -153,6 +158,7 @@ static double prec_unit(int prec) {
     case GSP2_PREC_BF16: return 0x1p-8;
     case GSP2_PREC_BF16X3: return 0x1p-16;
     case GSP2_PREC_TF32X3: return 0x1p-22;
+    case GSP2_PREC_FP16X3: return 0x1p-22;
     default: return 0x1p-53;
   }
 }
@@ -269,7 +275,7 @@ static void build_layout(gsp2_plan* h) {
     for (size_t i = 0; i < h->mf_of_step.size(); ++i)
       h->mf_of_step[i] = (k > 0 && (int)i <= h->opt.max_steps && i % (size_t)k == 0) ? L.ckpt[i / k] : L.mf[i & 1];
     const int kind = prec_kind(prec), nprod = prec_nprod(prec);
-    const size_t es = kind == 0 ? 2 : 4;
+    const size_t es = kind == 1 ? 4 : 2;
     L.op_hi[0] = L.op_hi[1] = L.op_lo[0] = L.op_lo[1] = 0;
     if (kind >= 0) {
       L.op_hi[0] = take((size_t)h->arena_elems * es);
@@ -360,7 +366,7 @@ extern "C" gsp2_status gsp2_create(int64_t n, const int64_t* rowptr, const int32
     if (!part) return bail(GSP2_E_ARG, "part is NULL");
     if (o.max_steps < 1 || o.max_steps > 1024) return bail(GSP2_E_ARG, "max_steps must be in [1, 1024]");
     if (!(o.idem_tol >= 0.0) || !(o.trace_tol >= 0.0)) return bail(GSP2_E_ARG, "tolerances must be >= 0");
-    if (o.precision < GSP2_PREC_FP64 || o.precision > GSP2_PREC_FP64_EMU) return bail(GSP2_E_ARG, "unknown precision");
+    if (o.precision < GSP2_PREC_FP64 || o.precision > GSP2_PREC_FP16X3) return bail(GSP2_E_ARG, "unknown precision");
     if (o.fp64_tail_steps < -1 || o.fp64_tail_steps > MAX_TAIL)
       return bail(GSP2_E_ARG, "fp64_tail_steps must be in [-1, 8]");
     if (h->opt.fp64_tail_steps < 0) h->opt.fp64_tail_steps = fp64_like(o.precision) ? 0 : 2;

@@ -27,10 +27,10 @@ namespace gsp2 {
 // Store the operand(s) of x at element index e of the operand arena(s).
 template <int KIND, int NPROD>
 __device__ __forceinline__ void store_operands(void* hi, void* lo, int64_t e, float x) {
-  if (KIND == 0) {
-    const uint16_t h = Operand<0>::bits(x);
+  if (KIND != 1) {
+    const uint16_t h = Operand<KIND>::bits(x);
     reinterpret_cast<uint16_t*>(hi)[e] = h;
-    if (NPROD == 3) reinterpret_cast<uint16_t*>(lo)[e] = Operand<0>::bits(x - Operand<0>::value(h));
+    if (NPROD == 3) reinterpret_cast<uint16_t*>(lo)[e] = Operand<KIND>::bits(x - Operand<KIND>::value(h));
   } else {
     const uint32_t h = Operand<1>::bits(x);
     reinterpret_cast<uint32_t*>(hi)[e] = h;
@@ -43,15 +43,15 @@ __device__ __forceinline__ void store_operands(void* hi, void* lo, int64_t e, fl
 template <int KIND, int NPROD, int N>
 __device__ __forceinline__ void store_operand_row(void* hi, void* lo, int64_t e, const float (&x)[N]) {
   static_assert(N % 8 == 0, "whole 16-byte vectors");
-  if (KIND == 0) {
+  if (KIND != 1) {
     uint32_t hw[N / 2], lw[N / 2];
 #pragma unroll
     for (int q = 0; q < N / 2; ++q) {
-      const uint16_t h0 = Operand<0>::bits(x[2 * q]), h1 = Operand<0>::bits(x[2 * q + 1]);
+      const uint16_t h0 = Operand<KIND>::bits(x[2 * q]), h1 = Operand<KIND>::bits(x[2 * q + 1]);
       hw[q] = (uint32_t)h0 | ((uint32_t)h1 << 16);
       if (NPROD == 3) {
-        const uint16_t l0 = Operand<0>::bits(x[2 * q] - Operand<0>::value(h0));
-        const uint16_t l1 = Operand<0>::bits(x[2 * q + 1] - Operand<0>::value(h1));
+        const uint16_t l0 = Operand<KIND>::bits(x[2 * q] - Operand<KIND>::value(h0));
+        const uint16_t l1 = Operand<KIND>::bits(x[2 * q + 1] - Operand<KIND>::value(h1));
         lw[q] = (uint32_t)l0 | ((uint32_t)l1 << 16);
       }
     }
@@ -85,12 +85,12 @@ __global__ void __launch_bounds__(256, 2) square_tc_kernel(TcStepArgs a) {
   constexpr int NOPS = NPROD == 3 ? 4 : 2;
   constexpr int STAGES = NPROD == 3 ? 2 : 3;
   constexpr uint32_t STAGE_B = NOPS * kTileBytes;
-  constexpr int ES = KIND == 0 ? 2 : 4;  // operand element bytes
+  constexpr int ES = Kind<KIND>::ES;  // operand element bytes
   constexpr int BKE = 128 / ES;          // K elements per stage (one 128-byte swizzle row)
-  constexpr int KMMA = KIND == 0 ? 16 : 8;
+  constexpr int KMMA = Kind<KIND>::KMMA;
   constexpr int NMMA = BKE / KMMA;       // MMAs per stage and product (4)
   // instruction descriptor: FP32 accumulate, A/B format, K-major A and B, N = 128, M = 128
-  constexpr uint32_t FMT = KIND == 0 ? 1u : 2u;
+  constexpr uint32_t FMT = Kind<KIND>::FMT;
   constexpr uint32_t IDESC = (1u << 4) | (FMT << 7) | (FMT << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
 
   int step = a.step;
@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(256, 2) square_tc_kernel(TcStepArgs a) {
       // FP64 once (an FP64 add in the unrolled loop would be issued for every element)
       float yd = 0.0f, zd = 0.0f;
       for (int j = 0; j < 32; ++j) {
-        const float y = __uint_as_float(v[j]);
+        const float y = __uint_as_float(v[j]) * Kind<KIND>::YSCALE;
         const float z = (al > 0) ? (2.0f * x[j] - y) : y;
         yd = (cbase + j == r) ? y : yd;
         zd = (cbase + j == r) ? z : zd;
@@ -314,11 +314,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
   constexpr int NOPS = NPROD == 3 ? 4 : 2;
   constexpr int STAGES = NPROD == 3 ? 3 : 4;
   constexpr uint32_t STAGE_B = NOPS * kTileBytes;
-  constexpr int ES = KIND == 0 ? 2 : 4;
+  constexpr int ES = Kind<KIND>::ES;
   constexpr int BKE = 128 / ES;
-  constexpr int KMMA = KIND == 0 ? 16 : 8;
+  constexpr int KMMA = Kind<KIND>::KMMA;
   constexpr int NMMA = BKE / KMMA;
-  constexpr uint32_t FMT = KIND == 0 ? 1u : 2u;
+  constexpr uint32_t FMT = Kind<KIND>::FMT;
   constexpr uint32_t IDESC = (1u << 4) | (FMT << 7) | (FMT << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
   static_assert(MODE == TC_STEP || (KIND == 1 && NPROD == 3), "the FP32 adjoint runs on TF32 hi + lo operands");
 
@@ -530,7 +530,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
           float yd = 0.0f, zd = 0.0f;
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
-            const float y = __uint_as_float(v[j]);
+            const float y = __uint_as_float(v[j]) * Kind<KIND>::YSCALE;
             const float z = (alf > 0) ? (2.0f * x[j] - y) : y;
             yd = (cbase + j == r) ? y : yd;
             zd = (cbase + j == r) ? z : zd;
@@ -643,11 +643,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_wide_kernel(TcStepArg
   using SL = TcWideStage<NPROD>;
   constexpr int STAGES = SL::STAGES;
   constexpr uint32_t STAGE_B = SL::BYTES;
-  constexpr int ES = KIND == 0 ? 2 : 4;
+  constexpr int ES = Kind<KIND>::ES;
   constexpr int BKE = 128 / ES;
-  constexpr int KMMA = KIND == 0 ? 16 : 8;
+  constexpr int KMMA = Kind<KIND>::KMMA;
   constexpr int NMMA = BKE / KMMA;
-  constexpr uint32_t FMT = KIND == 0 ? 1u : 2u;
+  constexpr uint32_t FMT = Kind<KIND>::FMT;
   constexpr uint32_t IDESC0 = (1u << 4) | (FMT << 7) | (FMT << 10) | ((128u >> 4) << 24);  // N set per item
 
   int step = a.step;
@@ -817,7 +817,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_wide_kernel(TcStepArg
           float yd = 0.0f, zd = 0.0f;
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
-            const float y = __uint_as_float(v[j]);
+            const float y = __uint_as_float(v[j]) * Kind<KIND>::YSCALE;
             const float z = (alf > 0) ? (2.0f * x[j] - y) : y;
             yd = (cbase + j == r) ? y : yd;
             zd = (cbase + j == r) ? z : zd;
@@ -966,6 +966,7 @@ cudaError_t launch_square_tc(int kind, int nprod, const TcStepArgs& a, int ntile
     if (kind == 0 && nprod == 3) return launch_tc_wide<0, 3>(a, g, s);
     if (kind == 1 && nprod == 1) return launch_tc_wide<1, 1>(a, g, s);
     if (kind == 1 && nprod == 3) return launch_tc_wide<1, 3>(a, g, s);
+    if (kind == 2 && nprod == 3) return launch_tc_wide<2, 3>(a, g, s);
     return cudaErrorInvalidValue;
   }
   if (persistent_grid > 0) {
@@ -974,12 +975,14 @@ cudaError_t launch_square_tc(int kind, int nprod, const TcStepArgs& a, int ntile
     if (kind == 0 && nprod == 3) return launch_tc_persistent<0, 3>(a, g, s);
     if (kind == 1 && nprod == 1) return launch_tc_persistent<1, 1>(a, g, s);
     if (kind == 1 && nprod == 3) return launch_tc_persistent<1, 3>(a, g, s);
+    if (kind == 2 && nprod == 3) return launch_tc_persistent<2, 3>(a, g, s);
     return cudaErrorInvalidValue;
   }
   if (kind == 0 && nprod == 1) return launch_tc<0, 1>(a, ntiles, s);
   if (kind == 0 && nprod == 3) return launch_tc<0, 3>(a, ntiles, s);
   if (kind == 1 && nprod == 1) return launch_tc<1, 1>(a, ntiles, s);
   if (kind == 1 && nprod == 3) return launch_tc<1, 3>(a, ntiles, s);
+  if (kind == 2 && nprod == 3) return launch_tc<2, 3>(a, ntiles, s);
   return cudaErrorInvalidValue;
 }
 
@@ -1054,6 +1057,8 @@ cudaError_t launch_gather_lp(int kind, int nprod, const PartDesc* parts, const C
     gather_lp_kernel<1, 1><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, colind, vals, master, op_hi, op_lo, slots, ctl);
   else if (kind == 1 && nprod == 3)
     gather_lp_kernel<1, 3><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, colind, vals, master, op_hi, op_lo, slots, ctl);
+  else if (kind == 2 && nprod == 3)
+    gather_lp_kernel<2, 3><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, colind, vals, master, op_hi, op_lo, slots, ctl);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();
@@ -1101,7 +1106,10 @@ int encode_part_maps(void* enc_fn, void* out_maps, const PartDesc* parts, int np
                            const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
                            CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
   Enc enc = reinterpret_cast<Enc>(enc_fn);
-  const int es = kind == 0 ? 2 : 4;
+  const int es = kind == 1 ? 4 : 2;
+  const CUtensorMapDataType dt = kind == 0   ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                 : kind == 1 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                             : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
   for (int k = 0; k < nparts; ++k) {
     const PartDesc& p = parts[k];
     cuuint64_t dims[2] = {(cuuint64_t)p.ld, (cuuint64_t)p.ld};
@@ -1109,7 +1117,7 @@ int encode_part_maps(void* enc_fn, void* out_maps, const PartDesc* parts, int np
     cuuint32_t box[2] = {(cuuint32_t)(box_bytes / es), (cuuint32_t)box_cols};
     cuuint32_t estr[2] = {1u, 1u};
     void* addr = (char*)arena + (size_t)p.off * es;
-    CUresult r = enc(&out[k], kind == 0 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, addr,
+    CUresult r = enc(&out[k], dt, 2, addr,
                      dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                      box_bytes == 32   ? CU_TENSOR_MAP_SWIZZLE_32B
                      : box_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B

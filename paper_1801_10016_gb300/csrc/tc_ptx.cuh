@@ -97,9 +97,20 @@ __device__ __forceinline__ uint64_t smem_desc_mn128(uint32_t addr, uint32_t lbo)
   return d;
 }
 
+// Operand kinds of the low-precision tensor-core steps: 0 BF16, 1 TF32, 2 FP16 of x 2^14.
+// Element bytes, K per MMA, the A/B format code of the instruction descriptor (kind::f16:
+// F16 0, BF16 1; kind::tf32: TF32 2) and the factor that scales a product sum back.
+template <int KIND>
+struct Kind {
+  static constexpr int ES = KIND == 1 ? 4 : 2;
+  static constexpr int KMMA = KIND == 1 ? 8 : 16;
+  static constexpr uint32_t FMT = KIND == 0 ? 1u : (KIND == 1 ? 2u : 0u);
+  static constexpr float YSCALE = KIND == 2 ? 3.7252902984619141e-09f : 1.0f;  // 2^-28 = (2^-14)^2
+};
+
 template <int KIND>
 __device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  if (KIND == 0) {
+  if (KIND != 1) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
@@ -141,7 +152,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
 
-// operand rounding: BF16 round-to-nearest-even, TF32 round-to-nearest (ties away)
+// operand rounding: BF16 round-to-nearest-even, TF32 round-to-nearest (ties away), FP16
+// round-to-nearest-even of x 2^14
 template <int KIND>
 struct Operand;
 template <>
@@ -165,6 +177,23 @@ struct Operand<1> {
     return (u + 0x1000u) & 0xFFFFE000u;
   }
   static __device__ __forceinline__ float value(uint32_t b) { return __uint_as_float(b); }
+};
+template <>
+struct Operand<2> {
+  // |x| <= 1 (the spectrum of X lies in [0, 1]) keeps x 2^14 inside FP16's range, and the
+  // scale moves entries down to 2^-28 into FP16's normal range (absolute spacing 2^-38
+  // below that); the scalings by powers of two are exact
+  static constexpr float kScale = 16384.0f;
+  static __device__ __forceinline__ uint16_t bits(float x) {
+    uint16_t h;
+    asm("cvt.rn.f16.f32 %0, %1;\n" : "=h"(h) : "f"(x * kScale));
+    return h;
+  }
+  static __device__ __forceinline__ float value(uint16_t h) {
+    float f;
+    asm("cvt.f32.f16 %0, %1;\n" : "=f"(f) : "h"(h));
+    return f * (1.0f / kScale);
+  }
 };
 
 

@@ -22,7 +22,7 @@ HEADER = os.path.join(os.path.dirname(_HERE), "include", "gsp2.h")
 OK, E_ARG, E_OOM, E_STATE, E_CUDA, E_NOT_CONVERGED, E_TRACE, E_NONFINITE, E_WORKSPACE, E_TIMEOUT = range(10)
 STATUS_NAMES = {0: "OK", 1: "E_ARG", 2: "E_OOM", 3: "E_STATE", 4: "E_CUDA", 5: "E_NOT_CONVERGED",
                 6: "E_TRACE", 7: "E_NONFINITE", 8: "E_WORKSPACE", 9: "E_TIMEOUT"}
-PRECISIONS = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3, "bf16x3": 4, "tf32x3": 5, "fp64e": 6}
+PRECISIONS = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16": 3, "bf16x3": 4, "tf32x3": 5, "fp64e": 6, "fp16x3": 7}
 MODES = {"record": 0, "replay": 1}
 
 

@@ -1,4 +1,4 @@
-"""GPU checks of the low-precision purification paths (TF32/BF16 on tcgen05 tensor
+"""GPU checks of the low-precision purification paths (TF32/BF16/FP16 on tcgen05 tensor
 cores, FP32 on CUDA cores) against the FP64 oracle.
 
 * one step, element by element, inside the rounding bound of the arithmetic:
@@ -18,7 +18,11 @@ from synth.tb import make_tb_system
 pytestmark = pytest.mark.gpu
 
 # unit roundoff of one operand, and of one product of the split (x3) forms
-U_OPERAND = {"tf32": 2.0 ** -11, "bf16": 2.0 ** -8, "tf32x3": 2.0 ** -21, "bf16x3": 2.0 ** -15, "fp32": 2.0 ** -24}
+U_OPERAND = {"tf32": 2.0 ** -11, "bf16": 2.0 ** -8, "tf32x3": 2.0 ** -21, "bf16x3": 2.0 ** -15, "fp32": 2.0 ** -24,
+             "fp16x3": 2.0 ** -21}
+# absolute error of one operand: fp16x3 splits x 2^14, whose low part is subnormal in FP16
+# (spacing 2^-24) below 2^-14, so each factor also carries up to 2^-25 2^-14
+ETA_OPERAND = {"fp16x3": 2.0 ** -39}
 U32 = 2.0 ** -24
 
 
@@ -41,7 +45,7 @@ def run(g, s, prec, **opt):
     return plan, p.cpu().numpy(), plan.history()
 
 
-@pytest.mark.parametrize("prec", ["tf32", "bf16", "tf32x3", "bf16x3", "fp32"])
+@pytest.mark.parametrize("prec", ["tf32", "bf16", "tf32x3", "bf16x3", "fp32", "fp16x3"])
 @pytest.mark.parametrize("case", ["tb512", "ragged132"])
 def test_one_step_within_rounding_bound(g, prec, case):
     s = make_workload("tb512") if case == "tb512" else make_tb_system(33, 1, 3.0, seed=9)
@@ -59,6 +63,8 @@ def test_one_step_within_rounding_bound(g, prec, case):
         scale = 2.0 if ref.alphas[0] == 1 else 1.0
         # operand rounding (both factors), the FP32 master of X0, FP32 accumulation, output rounding
         bound = (2.0 * U_OPERAND[prec] + 2.0 * U32 + (K + 2) * U32) * (A @ A) + scale * 2 * U32 * A + U32 * np.abs(X1)
+        eta = ETA_OPERAND.get(prec, 0.0)
+        bound = bound + eta * (A.sum(axis=1)[:, None] + A.sum(axis=0)[None, :])
         bound = 2.0 * bound + 1e-30
         got = np.empty_like(X1[:, :c])
         for j in range(c):
@@ -72,7 +78,7 @@ def test_one_step_within_rounding_bound(g, prec, case):
 
 
 @pytest.mark.parametrize("prec,max_dp", [("tf32x3", 3e-6), ("fp32", 3e-6), ("tf32", 3e-3), ("bf16", 5e-2),
-                                         ("bf16x3", 1e-3)])
+                                         ("bf16x3", 1e-3), ("fp16x3", 3e-6)])
 def test_full_run_against_fp64_oracle(g, prec, max_dp):
     s = make_workload("tb512")
     plan, p, hist = run(g, s, prec)
@@ -86,7 +92,7 @@ def test_full_run_against_fp64_oracle(g, prec, max_dp):
     assert err <= max_dp, err
 
 
-@pytest.mark.parametrize("prec,max_dp", [("tf32x3", 5e-6), ("bf16x3", 3e-5)])
+@pytest.mark.parametrize("prec,max_dp", [("tf32x3", 5e-6), ("bf16x3", 3e-5), ("fp16x3", 5e-6)])
 def test_low_precision_alternating_tail(g, prec, max_dp):
     """Tail steps in the low precision instead of FP64: same alternation, no FP64 step."""
     s = make_workload("tb512")
@@ -110,12 +116,12 @@ def test_tail_options_rejected_where_meaningless(g):
             g.GSP2(s.n, s.rowptr, s.colind, s.nocc, s.part, s.nparts, s.g_rowptr, s.g_colind, bind=False, **kw)
 
 
-@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "tf32", "bf16"])
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "tf32", "bf16", "fp16x3"])
 @pytest.mark.parametrize("case", ["tb512", "tb30k"])
 def test_persistent_schedule_matches_one_cta_per_tile(g, prec, case):
     """The persistent tensor-core kernel (two TMEM accumulators, epilogue overlapped with
     the next tile) computes every tile exactly as the one-CTA-per-tile kernel."""
-    if case == "tb30k" and prec not in ("tf32x3", "bf16"):
+    if case == "tb30k" and prec not in ("tf32x3", "bf16", "fp16x3"):
         pytest.skip("one large case per kind")
     s = make_workload(case)
     _, p0, h0 = run(g, s, prec, tc_schedule=0, max_steps=6)
@@ -125,20 +131,21 @@ def test_persistent_schedule_matches_one_cta_per_tile(g, prec, case):
     assert np.array_equal(p0, p1) and np.array_equal(p0, p2)
 
 
+@pytest.mark.parametrize("prec", ["tf32x3", "fp16x3"])
 @pytest.mark.parametrize("case", ["tb512", "tb30k"])
-def test_tf32x3_meets_the_gates_against_the_oracle_with_the_same_tail(g, case):
-    """Mixed precision (tf32x3 squarings, FP64 traces, two FP64 tail steps) against the FP64
-    oracle with the same two tail steps: max|dP| <= 1e-6 and the column idempotency
+def test_split_precisions_meet_the_gates_against_the_oracle_with_the_same_tail(g, prec, case):
+    """Mixed precision (tf32x3 or fp16x3 squarings, FP64 traces, two FP64 tail steps) against
+    the FP64 oracle with the same two tail steps: max|dP| <= 1e-6 and the column idempotency
     ||P^2 - P||_F / sqrt(N) (part by part) <= 1e-8."""
     s = make_workload(case)
-    plan, p, hist = run(g, s, "tf32x3", fp64_tail_steps=2, report_idem=1)
+    plan, p, hist = run(g, s, prec, fp64_tail_steps=2, report_idem=1)
     assert hist["status"] == 0
     ref = oracle.gsp2(s.n, s.rowptr, s.colind, s.vals, s.nocc, s.part, s.nparts, s.g_rowptr, s.g_colind,
                       tail_steps=2)
     want = ref.p_on_pattern(plan.p_colptr, plan.p_rowind)
     err = float(np.max(np.abs(p - want)))
     idem = hist["report"]["idem_fro"]
-    print(f"{case} tf32x3 + 2 FP64 tail vs oracle + 2 tail: max|dP|={err:.3e} idem_fro={idem:.3e}")
+    print(f"{case} {prec} + 2 FP64 tail vs oracle + 2 tail: max|dP|={err:.3e} idem_fro={idem:.3e}")
     assert err <= 1e-6, err
     assert 0.0 <= idem <= 1e-8, idem
 
