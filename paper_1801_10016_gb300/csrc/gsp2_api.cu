@@ -667,6 +667,20 @@ extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t byt
       }
     CU(h, up(L.oz_maps, maps.data(), maps.size()));
     CU(h, up(L.oz_maps_mn, maps_mn.data(), maps_mn.size()));
+    // the emulated steps never write the 16-column chunks of a part's padding: every arena
+    // and digit buffer they write starts zeroed here
+    {
+      const size_t ab = (size_t)h->arena_elems * sizeof(double), dbytes = (size_t)h->arena_elems * 2;
+      std::vector<size_t> fp64_arenas{L.arena0, L.arena1};
+      if (fp64_like(h->opt.precision)) {
+        fp64_arenas.insert(fp64_arenas.end(), L.ckpt.begin(), L.ckpt.end());
+        fp64_arenas.insert(fp64_arenas.end(), L.seg.begin(), L.seg.end());
+      }
+      for (size_t off : fp64_arenas) CU(h, cudaMemsetAsync(h->ws + off, 0, ab, s));
+      for (int b = 0; b < 2; ++b)
+        for (int t = 0; t < OZ_SLICES; ++t) CU(h, cudaMemsetAsync(h->ws + L.oz_slice[b][t], 0, dbytes, s));
+      for (size_t off : L.adj_dig) CU(h, cudaMemsetAsync(h->ws + off, 0, dbytes, s));
+    }
     if (!L.adj_dig.empty()) {
       std::vector<unsigned char> amaps(L.adj_dig.size() * np * 128, 0), amaps_mn(amaps.size(), 0);
       for (size_t i = 0; i < L.adj_dig.size(); ++i) {
@@ -707,9 +721,21 @@ extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t byt
       }
       CU(h, up(L.maps, maps.data(), maps.size()));
     }
+    {
+      // every FP32 iterate arena starts zeroed, so that the padding columns the CUDA-core
+      // steps never write (they work in 64-column tiles up to roundup(s, 64)) stay zero for
+      // the steps and conversions that read whole 128-column blocks
+      const size_t af = (size_t)h->arena_elems * sizeof(float);
+      std::vector<size_t> zero{L.mf[0], L.mf[1]};
+      zero.insert(zero.end(), L.ckpt.begin(), L.ckpt.end());
+      zero.insert(zero.end(), L.seg.begin(), L.seg.end());
+      zero.insert(zero.end(), L.tailf.begin(), L.tailf.end());
+      if (L.xb0) zero.push_back(L.xb0);
+      if (L.xb1) zero.push_back(L.xb1);
+      for (size_t off : zero) CU(h, cudaMemsetAsync(h->ws + off, 0, af, s));
+    }
     if (!L.aop.empty()) {
-      // the FP32 adjoint: maps over its TF32 operand arenas; its iterate arenas start zeroed,
-      // so that the padding columns the CUDA-core steps never write stay zero
+      // the FP32 adjoint: maps over its TF32 operand arenas
       void* enc = nullptr;
       cudaDriverEntryPointQueryResult q{};
       CU(h, cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &enc, 12000, cudaEnableDefault, &q));
@@ -722,13 +748,6 @@ extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t byt
         if (r != 0) return fail(h, GSP2_E_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string(r));
       }
       CU(h, up(L.aop_maps, amaps.data(), amaps.size()));
-      const size_t af = (size_t)h->arena_elems * sizeof(float);
-      std::vector<size_t> zero(L.ckpt);
-      zero.insert(zero.end(), L.seg.begin(), L.seg.end());
-      zero.insert(zero.end(), L.tailf.begin(), L.tailf.end());
-      zero.push_back(L.xb0);
-      zero.push_back(L.xb1);
-      for (size_t off : zero) CU(h, cudaMemsetAsync(h->ws + off, 0, af, s));
     }
   }
   CU(h, up(L.gblocks, h->gblocks.data(), h->gblocks.size() * sizeof(ColBlock)));

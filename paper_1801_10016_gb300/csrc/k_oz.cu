@@ -280,6 +280,12 @@ __host__ __device__ constexpr int oz_slices_per_stage(int nd, bool diag) {
 }
 static_assert(oz_slices_per_stage(OZ_SLICES, false) >= 1, "a high-pass slice fits a stage");
 
+// Columns of tile column block tj that an MMA must cover: those inside the part, rounded up
+// to 16 (N of an M = 128 MMA is a multiple of 16); the rest of the block is zero padding.
+__host__ __device__ constexpr int oz_tile_cols(int s, int tj) {
+  return s - tj * 128 >= 128 ? 128 : ((s - tj * 128 + 15) & ~15);
+}
+
 __device__ __forceinline__ uint32_t oz_group_col(int d) {
   return (uint32_t)(d >= OZ_SPLIT ? 128 * (d - OZ_SPLIT + 4 - (OZ_SLICES - OZ_SPLIT)) : 128 * d);
 }
@@ -342,7 +348,8 @@ __device__ __forceinline__ float warp_colsum16(const float (&v)[16], int lane, i
 template <bool ADJ>
 __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
   constexpr int T = OZ_SLICES;
-  constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+  // instruction descriptor without N (bits 17..22, N / 8): FP32 accumulate, BF16 A and B, M = 128
+  constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 4) << 24);
 
   int step = a.step;
   const bool rec = !ADJ && a.mode == SQ_RECOMPUTE;
@@ -499,7 +506,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
                                  : (bmn ? smem_desc_mn128(tileB(s, 0), OZ_DTILE / 2)
                                         : smem_desc_sw<2 * OZ_BK>(tileB(s, 0)));
           const uint32_t adv_a = amn ? (2048u >> 4) : (32u >> 4), adv_b = bmn ? (2048u >> 4) : (32u >> 4);
-          const uint32_t idesc = IDESC | ((amn ? 1u : 0u) << 15) | ((bmn ? 1u : 0u) << 16);
+          const uint32_t idesc =
+              IDESC | ((uint32_t)(oz_tile_cols(sz, t.tj) >> 3) << 17) | ((amn ? 1u : 0u) << 15) | ((bmn ? 1u : 0u) << 16);
           for (int u = 0; u < sub; ++u) {  // the stage's K slices, nd tiles apart
             const uint64_t off = (uint64_t)(u * nd) * (OZ_DTILE >> 4);
             if (pass == 0) oz_issue_stage<OZ_SPLIT, T>(tmem, da + off, db + off, adv_a, adv_b, idesc, kb == 0 && u == 0);
@@ -536,6 +544,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
       const int r = t.ti * 128 + m, c0 = t.tj * 128;
       const bool diag = t.slot >= 0;
       const int sg = ADJ ? a.sig[t.part] : 0;  // the adjoint's sums hold (Xbar X + X Xbar) / 2^sg
+      // columns the MMAs covered; the 16-column chunks beyond them lie in the part's zero
+      // padding, which no step writes (the arenas are zeroed when the workspace is bound)
+      const int ncols = oz_tile_cols(p.s, t.tj);
       double tY = 0.0, tN = 0.0;
       bool ok = true;
       // the two passes: read the groups' sums (integers held exactly in FP32), add them as
@@ -548,6 +559,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
 #pragma unroll 1
         for (int cc = 0; cc < 2 && ok; ++cc) {
           const int cl = colq * 32 + cc * 16;
+          if (cl >= ncols) continue;
           long long z[16];
           long long* zp = acc + (size_t)cl * 128 + m;
 #pragma unroll
@@ -581,6 +593,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
 #pragma unroll 1
       for (int cc = 0; cc < 2 && ok; ++cc) {
         const int cl = colq * 32 + cc * 16;
+        if (cl >= ncols) continue;
         const int cbase = c0 + cl;
         const long long* zp = acc + (size_t)cl * 128 + m;
         float coln[16];  // adjoint: squares of the entries (r, c) for the norms of rows c
