@@ -173,28 +173,50 @@ OZ_DIGITS = 7  # base-2^7 digits of the fp64e step
 OZ_PRODUCTS = OZ_DIGITS * (OZ_DIGITS + 1) // 2  # BF16 digit products per tile (28)
 
 
-def tc_exec_flops(sizes, kstage, products):
-    """Executed tensor flops of one step: every upper 128x128 tile, K rounded to the stage."""
+def tc_exec_flops(sizes, kstage, products, trim=False):
+    """Executed tensor flops of one step: every upper 128x128 tile, K rounded to the stage;
+    with `trim`, the last column block of a part at its columns rounded up to 16 (N of the
+    emulated step's MMAs there)."""
     import numpy as np
     nt = np.ceil(sizes / 128.0)
     kk = np.ceil(sizes / kstage) * kstage
-    return float(np.sum(nt * (nt + 1) / 2 * 2 * 128 * 128 * kk)) * products
+    full = nt * (nt + 1) / 2 * 128.0
+    if trim:
+        last = np.minimum(128.0, np.ceil((sizes - (nt - 1) * 128.0) / 16.0) * 16.0)
+        full = full - nt * (128.0 - last)  # the nt tiles of the last column block
+    return float(np.sum(full * 2 * 128 * kk)) * products
+
+
+def alg_flops(sizes, products=1):
+    """Algorithmic flops of one symmetric squaring of every part: the upper triangle with the
+    diagonal, s (s + 1) / 2 dot products of length s, 2 s flops each: s^2 (s + 1); the
+    tensor-core forms multiply it by their products per element (28 digit products, 3 for a
+    hi + lo split)."""
+    import numpy as np
+    return float(np.sum(sizes * sizes * (sizes + 1.0))) * products
 
 
 def fp64_roofline(precision, sizes, avg_launch_ms, peaks, src, workload):
-    """Roofline of one FP64-result step: native (FP64 pipe, algorithmic flops s^2 (s+1)) or
-    rebuilt from BF16 digits (tensor pipe, executed BF16 flops of all digit products)."""
+    """Roofline of one FP64-result step: native (FP64 pipe) or rebuilt from BF16 digits
+    (tensor pipe); `achieved` from the algorithmic flops s^2 (s+1) per part (times the 28
+    digit products for the emulated step), the emulated step's executed flops (128-tile
+    padding, whole diagonal tiles) beside it."""
     import numpy as np
     if precision == "fp64e":
-        flops = tc_exec_flops(sizes, 32, OZ_PRODUCTS)
-        achieved = flops / (avg_launch_ms / 1e3) / 1e12
+        flops = alg_flops(sizes, OZ_PRODUCTS)
+        exe = tc_exec_flops(sizes, 32, OZ_PRODUCTS, trim=True)
+        t = avg_launch_ms / 1e3
+        achieved = flops / t / 1e12
         peak = peaks["bf16_tflops"]
         return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": TRAFFIC.get((workload, precision)),
                 "kernel": "oz_step_kernel (one FP64-accurate step: 28 BF16 digit products per upper tile, fused)",
                 "peak_source": f"{src}: bf16 burst (of measured)", "avg_launch_ms": avg_launch_ms,
                 "flops_per_launch": flops,
-                "flops": f"executed BF16 tensor flops of the {OZ_PRODUCTS} digit products per upper 128-tile"}
+                "flops": f"algorithmic: {OZ_PRODUCTS} BF16 digit products x s^2 (s+1) per part (upper triangle "
+                         f"of X^2)",
+                "executed_flops_per_launch": exe, "executed_tflops": exe / t / 1e12,
+                "executed_frac": exe / t / 1e12 / peak}
     flops = float(np.sum(sizes * sizes * (sizes + 1.0)))
     achieved = flops / (avg_launch_ms / 1e3) / 1e12
     peak = peaks["bf16_tflops"] * NOMINAL["fp64"] / NOMINAL["bf16"]
@@ -258,10 +280,9 @@ def adjoint_block(dev, peaks, src, workload="tb4k", reps=3):
     every 8 steps, for the three kinds of adjoint: FP64 (CUDA cores), FP64 rebuilt from BF16
     digit products (tensor cores) and FP32 (TF32 hi + lo products on the tensor cores, behind
     an FP32 forward).  Device time per backward (after a density call) and the reverse sweep's
-    flops against the peak of the pipe it runs on: algorithmic flops on the CUDA cores (every
-    reverse step 2 s^2 (s+1) per part, every rebuilt iterate s^2 (s+1)); executed flops on the
-    tensor cores (every reverse step twice, every rebuilt iterate once, all products of all
-    upper 128-tiles)."""
+    algorithmic flops (every reverse step 2 s^2 (s+1) per part, every rebuilt iterate
+    s^2 (s+1), times the products per element on the tensor cores) against the peak of the
+    pipe it runs on."""
     import numpy as np
     import torch
     from paper_1801_10016_gb300.gsp2 import GSP2
@@ -290,19 +311,19 @@ def adjoint_block(dev, peaks, src, workload="tb4k", reps=3):
         rebuilt = sum(1 for i in range(1, n) if i % 8 != 0)
         t = statistics.median(ms) / 1e3
         if prec == "fp64e":
-            flops = (2.0 * n + rebuilt) * tc_exec_flops(sz, 32, OZ_PRODUCTS)
+            flops = (2.0 * n + rebuilt) * alg_flops(sz, OZ_PRODUCTS)
             peak, psrc = peaks["bf16_tflops"], f"{src}: bf16 burst (of measured)"
             kern, fdesc = ("oz_step_kernel<adjoint> + oz_step_kernel recompute",
-                           f"executed BF16 tensor flops of the {OZ_PRODUCTS} digit products per upper 128-tile: "
-                           "reverse steps twice (K = 2s), rebuilt iterates once")
+                           f"algorithmic BF16 flops of the {OZ_PRODUCTS} digit products: reverse steps 2 s^2 (s+1), "
+                           "rebuilt iterates s^2 (s+1), per part and product")
             bound = "tensor"
         elif prec == "fp32":
-            flops = (2.0 * n + rebuilt) * tc_exec_flops(sz, 32, 3)
+            flops = (2.0 * n + rebuilt) * alg_flops(sz, 3)
             peak = peaks["bf16_tflops"] * NOMINAL["tf32"] / NOMINAL["bf16"]
             psrc = f"{src} bf16 x nominal tf32/bf16 (of measured)"
             kern, fdesc = ("square_tc_persistent_kernel<tf32,3,adjoint> + <tf32,3,rebuild>",
-                           "executed TF32 tensor flops of the 3 products per upper 128-tile: reverse steps twice "
-                           "(K = 2s), rebuilt iterates once")
+                           "algorithmic TF32 flops of the 3 products: reverse steps 2 s^2 (s+1), rebuilt iterates "
+                           "s^2 (s+1), per part and product")
             bound = "tensor"
         else:
             flops = (2.0 * n + rebuilt) * float(np.sum(sz * sz * (sz + 1.0)))
@@ -500,21 +521,23 @@ def run_ours(args):
                      "tflops_dgemm_equiv": dgemm_equiv * lp_steps / t_build / 1e12,
                      "schedule": None if mtune is None else mtune["candidates"][mtune["chosen"]]}
             if prec != "fp32":
-                # executed tensor flops of one launch: every 128x128 upper tile, K rounded to the stage
-                nt = np.ceil(sizes / 128.0)
+                # algorithmic tensor flops of one launch (s^2 (s+1) per part and product) and the
+                # executed ones (every 128x128 upper tile, K rounded to the stage)
                 kst = 32 if prec.startswith("tf32") else 64  # K per stage: 128-byte operand rows
-                kk = np.ceil(sizes / kst) * kst
-                exec_flops = float(np.sum(nt * (nt + 1) / 2 * 2 * 128 * 128 * kk)) * nprod
-                ach = exec_flops / (k_ms / 1e3) / 1e12
+                alg = alg_flops(sizes, nprod)
+                exec_flops = tc_exec_flops(sizes, kst, nprod)
+                ach = alg / (k_ms / 1e3) / 1e12
                 kname = "tf32" if "tf32" in prec else ("fp16" if "fp16" in prec else "bf16")
                 entry["roofline"] = {"bound": "tensor", "achieved": ach, "peak": tf32_peak if "tf32" in prec
                                      else peaks["bf16_tflops"], "unit": "TFLOP/s",
                                      "kernel": f"square_tc_persistent_kernel<{kname},{nprod}>",
-                                     "flops": "executed tensor flops per launch (all upper 128-tiles, all products)",
+                                     "flops": "algorithmic tensor flops per launch (s^2 (s+1) per part and product)",
+                                     "executed_tflops": exec_flops / (k_ms / 1e3) / 1e12,
                                      "peak_source": ("measured bf16 burst x nominal tf32/bf16 1100/2250 (of measured)"
                                                      if "tf32" in prec else "measured bf16 burst (of measured; "
                                                      "fp16 and bf16 share the 16-bit dense rate)")}
                 entry["roofline"]["frac"] = ach / entry["roofline"]["peak"]
+                entry["roofline"]["executed_frac"] = entry["roofline"]["executed_tflops"] / entry["roofline"]["peak"]
             mixed[spec] = entry
         line["mixed"] = mixed
         line["mixed_note"] = ("max_abs_dP_vs_fp64: against the FP64-result path of `value` (the paper's method, no "
