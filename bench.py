@@ -407,7 +407,6 @@ def run_ours(args):
     # ---- roofline of the dominant kernel (the purification step)
     peaks, src = load_peaks()
     sizes = plan.part_sizes.astype(np.float64)
-    alg_flops = float(np.sum(sizes * sizes * (sizes + 1.0)))  # upper triangle incl. diagonal: s(s+1)/2 * 2s
     dgemm_equiv = 2.0 * float(np.sum(sizes ** 3))
     avg_launch_ms, work_ms = kernel_avg_ms(step_ms, steps_applied)
     roof = fp64_roofline(args.precision, sizes, avg_launch_ms, peaks, src, args.workload)
@@ -525,7 +524,11 @@ def run_ours(args):
                 # executed ones (every 128x128 upper tile, K rounded to the stage)
                 kst = 32 if prec.startswith("tf32") else 64  # K per stage: 128-byte operand rows
                 alg = alg_flops(sizes, nprod)
-                exec_flops = tc_exec_flops(sizes, kst, nprod)
+                # the persistent 128x128 kernel trims the last column block of each part (the
+                # per-tile and 128x256 kernels run whole tiles)
+                sched = None if mtune is None else mtune["candidates"][mtune["chosen"]]
+                trim = sched is None or (sched["tc_schedule"] == 0 and sched["tile_shape"] == 0)
+                exec_flops = tc_exec_flops(sizes, kst, nprod, trim=trim)
                 ach = alg / (k_ms / 1e3) / 1e12
                 kname = "tf32" if "tf32" in prec else ("fp16" if "fp16" in prec else "bf16")
                 entry["roofline"] = {"bound": "tensor", "achieved": ach, "peak": tf32_peak if "tf32" in prec

@@ -722,17 +722,25 @@ extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t byt
       CU(h, up(L.maps, maps.data(), maps.size()));
     }
     {
-      // every FP32 iterate arena starts zeroed, so that the padding columns the CUDA-core
-      // steps never write (they work in 64-column tiles up to roundup(s, 64)) stay zero for
-      // the steps and conversions that read whole 128-column blocks
+      // every iterate and operand arena starts zeroed, so that the padding no step writes
+      // stays zero for the steps and conversions that read whole 128-column blocks: the
+      // CUDA-core steps work in 64-column tiles up to roundup(s, 64), the tensor-core steps
+      // skip the 16-column chunks beyond roundup(s, 16)
       const size_t af = (size_t)h->arena_elems * sizeof(float);
-      std::vector<size_t> zero{L.mf[0], L.mf[1]};
-      zero.insert(zero.end(), L.ckpt.begin(), L.ckpt.end());
-      zero.insert(zero.end(), L.seg.begin(), L.seg.end());
-      zero.insert(zero.end(), L.tailf.begin(), L.tailf.end());
-      if (L.xb0) zero.push_back(L.xb0);
-      if (L.xb1) zero.push_back(L.xb1);
-      for (size_t off : zero) CU(h, cudaMemsetAsync(h->ws + off, 0, af, s));
+      const size_t ab = (size_t)h->arena_elems * sizeof(double);
+      const size_t es = kind == 1 ? 4 : 2;
+      std::vector<std::pair<size_t, size_t>> zero{{L.mf[0], af}, {L.mf[1], af}, {L.d[0], ab}, {L.d[1], ab}};
+      for (size_t off : L.ckpt) zero.push_back({off, af});
+      for (size_t off : L.seg) zero.push_back({off, af});
+      for (size_t off : L.tailf) zero.push_back({off, af});
+      for (size_t off : L.aop) zero.push_back({off, af});
+      if (L.xb0) zero.push_back({L.xb0, af});
+      if (L.xb1) zero.push_back({L.xb1, af});
+      for (int b = 0; b < 2; ++b) {
+        if (L.op_hi[b]) zero.push_back({L.op_hi[b], (size_t)h->arena_elems * es});
+        if (L.op_lo[b]) zero.push_back({L.op_lo[b], (size_t)h->arena_elems * es});
+      }
+      for (const auto& z : zero) CU(h, cudaMemsetAsync(h->ws + z.first, 0, z.second, s));
     }
     if (!L.aop.empty()) {
       // the FP32 adjoint: maps over its TF32 operand arenas
@@ -1394,6 +1402,12 @@ static gsp2_status enqueue_backward_lp(gsp2_plan* h, const double* pbar, double*
     a.step = step;
     return launch_tc_adjoint(a, h->num_sms, false, s);
   };
+  // Xbar's operands live in the FP64 tail arenas: zeroed first, so that the padding the
+  // reverse steps do not write reads as zero, and again at the end, so that the next
+  // forward's FP64 tail finds its padding zero
+  const size_t ab = (size_t)ne * sizeof(double);
+  CU(h, cudaMemsetAsync(w + L.d[0], 0, ab, s));
+  CU(h, cudaMemsetAsync(w + L.d[1], 0, ab, s));
   CU(h, launch_adj_seed<float>(parts, gbl, (int)h->gblocks.size(), Sall, (const int32_t*)(w + L.invperm),
                                (const int64_t*)(w + L.pcolptr), pbar, xb0, s));
   CU(h, launch_split_tf32(xb0, aop(nsets, 0), aop(nsets, 1), ne, st, 0, 0, s));
@@ -1413,6 +1427,8 @@ static gsp2_status enqueue_backward_lp(gsp2_plan* h, const double* pbar, double*
   CU(h, launch_adj_hbar<float>(h->n, (const int64_t*)(w + L.rowptr), (const int32_t*)(w + L.colind),
                                (const int64_t*)(w + L.memptr), (const int32_t*)(w + L.mempart),
                                (const int32_t*)(w + L.memloc), parts, Sall, xb0, xb1, hbar, st, s));
+  CU(h, cudaMemsetAsync(w + L.d[0], 0, ab, s));
+  CU(h, cudaMemsetAsync(w + L.d[1], 0, ab, s));
   return GSP2_OK;
 }
 

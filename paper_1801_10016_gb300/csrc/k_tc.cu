@@ -298,13 +298,21 @@ __global__ void __launch_bounds__(256, 2) square_tc_kernel(TcStepArgs a) {
 // warp 1 owns TMEM and its lane 0 issues tcgen05.mma, warps 4..19 drain TMEM (four per
 // lane quarter, so that the epilogue, which writes the master and operand copies of the
 // tile and its mirror, keeps up with the tensor cores).  Same arithmetic and the same
-// bookkeeping as square_tc_kernel.
+// bookkeeping as square_tc_kernel, bitwise; the MMAs of a part's last column block cover
+// only its columns, and the epilogue leaves the padding beyond them alone.
 //
 // MODE 1 rebuilds iterate X_step of the FP32 adjoint from explicit buffers with the
 // recorded branch; MODE 2 is a reverse step of that adjoint: an upper tile (I, J) of
 // Xbar X + X Xbar is one product over K = 2s, rows I of [Xbar | X] times rows J of
 // [X | Xbar] (both symmetric and stored whole), and Xbar_new = that or 2 Xbar minus it.
 // Neither keeps traces or runs the step bookkeeping.
+
+// Columns of tile column block tj that an MMA must cover: those inside the part, rounded up
+// to 16 (N of an M = 128 MMA is a multiple of 16); the rest of the block is zero padding.
+__host__ __device__ constexpr int tc_tile_cols(int s, int tj) {
+  return s - tj * 128 >= 128 ? 128 : ((s - tj * 128 + 15) & ~15);
+}
+
 constexpr int TC_EPI_WARPS = 16;  // 4 per TMEM lane quarter, 32 columns each
 constexpr int TC_THREADS = 32 * (4 + TC_EPI_WARPS);
 enum : int { TC_STEP = 0, TC_REBUILD = 1, TC_ADJOINT = 2 };
@@ -319,7 +327,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
   constexpr int KMMA = Kind<KIND>::KMMA;
   constexpr int NMMA = BKE / KMMA;
   constexpr uint32_t FMT = Kind<KIND>::FMT;
-  constexpr uint32_t IDESC = (1u << 4) | (FMT << 7) | (FMT << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+  // instruction descriptor without N (set per tile: the last column block of a part covers
+  // only the part's columns, rounded up to 16)
+  constexpr uint32_t IDESC0 = (1u << 4) | (FMT << 7) | (FMT << 10) | ((128u >> 4) << 24);
   static_assert(MODE == TC_STEP || (KIND == 1 && NPROD == 3), "the FP32 adjoint runs on TF32 hi + lo operands");
 
   int step = a.step;
@@ -456,6 +466,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
       }
       tc_fence_after();
       const uint32_t d = tmem + (uint32_t)(b * 128);
+      const uint32_t IDESC = IDESC0 | ((uint32_t)(tc_tile_cols(p.s, t.tj) >> 3) << 17);
       for (int kb = 0; kb < nk; ++kb, ++g) {
         const int s = g % STAGES;
         if (!mbar_wait(full(s), (g / STAGES) & 1, abort_flag)) {
@@ -519,6 +530,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
 #pragma unroll 1
         for (int h = 0; h < 2; ++h) {
           const int cl = colq * 32 + h * 16;
+          // 16-column chunks beyond the MMAs' columns lie in the part's zero padding, which
+          // no step writes (the iterate and operand arenas are zeroed when the workspace is bound)
+          if (cl >= tc_tile_cols(p.s, t.tj)) continue;
           const int cbase = c0 + cl;
           uint32_t v[16];
           tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 128 + cl), v);

@@ -131,6 +131,27 @@ def test_low_precision_adjoint_matches_oracle_on_the_same_sequence(g, prec, tail
     assert err <= tol, err
 
 
+@pytest.mark.parametrize("prec,tail", [("fp32", 2), ("tf32x3", 2), ("fp16x3", 2), ("fp64e", 2), ("fp64", 0)])
+def test_density_after_backward_is_unchanged(g, prec, tail):
+    """A backward shares scratch arenas with the forward (the FP32 adjoint keeps Xbar's
+    operands in the FP64 tail arenas): a density call after it gives bitwise the same P,
+    branch sequence and idempotency report as before it."""
+    import torch
+    s = make_tb_system(48, 4, 3.0, seed=21)
+    plan = g.GSP2(s.n, s.rowptr, s.colind, s.nocc, s.part, s.nparts, s.g_rowptr, s.g_colind, device="cuda:0",
+                  precision=prec, fp64_tail_steps=tail, ckpt_every=3, report_idem=1)
+    h = torch.from_numpy(s.vals).to("cuda:0")
+    p0 = plan.density(h).clone()
+    r0 = plan.history()
+    pb, _ = pbar_for_trace_loss(s, plan)
+    hb = plan.backward(torch.from_numpy(pb).to("cuda:0"))
+    assert torch.isfinite(hb).all()
+    p1 = plan.density(h)
+    r1 = plan.history()
+    assert torch.equal(p0, p1)
+    assert r0["alphas"] == r1["alphas"] and r0["report"]["idem_fro"] == r1["report"]["idem_fro"]
+
+
 @pytest.mark.parametrize("case,k", [("small", 1), ("small", 3), ("small", 45), ("tb512", 5)])
 def test_tf32x3_checkpoint_interval_does_not_change_the_gradient(g, case, k):
     """The FP32 adjoint rebuilds iterates with the tf32x3 step's own tensor-core arithmetic
