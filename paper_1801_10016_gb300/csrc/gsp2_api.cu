@@ -102,8 +102,14 @@ struct gsp2_plan {
   int device = -1;
   int num_sms = 0;
   cudaStream_t cap_stream = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  GraphKey key{};
+  // forward graphs, one per (H, P, alpha, mode, nsteps) key, the two most recent kept (a
+  // caller alternating two buffer pairs, e.g. to overlap copies with compute, replays both)
+  struct ForwardGraph {
+    GraphKey key{};
+    cudaGraphExec_t exec = nullptr;
+    uint64_t used = 0;
+  } fg[2];
+  uint64_t fg_clock = 0;
   cudaGraphExec_t bexec = nullptr;  // adjoint graph
   const void* bkey_pbar = nullptr;
   void* bkey_hbar = nullptr;
@@ -572,9 +578,10 @@ extern "C" gsp2_status gsp2_p_pattern(gsp2_handle h, int64_t* colptr, int32_t* r
 }
 
 static void drop_graph(gsp2_plan* h) {
-  if (h->exec) cudaGraphExecDestroy(h->exec);
-  h->exec = nullptr;
-  h->key = GraphKey{};
+  for (auto& f : h->fg) {
+    if (f.exec) cudaGraphExecDestroy(f.exec);
+    f = gsp2_plan::ForwardGraph{};
+  }
   if (h->bexec) cudaGraphExecDestroy(h->bexec);
   h->bexec = nullptr;
   h->bkey_pbar = nullptr;
@@ -969,8 +976,14 @@ extern "C" gsp2_status gsp2_density(gsp2_handle h, const double* d_hvals, double
   cudaStream_t s = (cudaStream_t)stream;
   if (h->opt.use_graph) {
     GraphKey k{d_hvals, d_pvals, d_alpha, mode, nsteps};
-    if (!h->exec || !(k == h->key)) {
-      drop_graph(h);
+    gsp2_plan::ForwardGraph* f = nullptr;
+    for (auto& c : h->fg)
+      if (c.exec && c.key == k) f = &c;
+    if (!f) {
+      // replace the empty or least recently used entry
+      f = (!h->fg[0].exec || (h->fg[1].exec && h->fg[0].used <= h->fg[1].used)) ? &h->fg[0] : &h->fg[1];
+      if (f->exec) cudaGraphExecDestroy(f->exec);
+      *f = gsp2_plan::ForwardGraph{};
       cudaGraph_t g = nullptr;
       CU(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
       gsp2_status st = enqueue_forward(h, d_hvals, d_pvals, d_alpha, mode, nsteps, h->cap_stream);
@@ -980,15 +993,16 @@ extern "C" gsp2_status gsp2_density(gsp2_handle h, const double* d_hvals, double
         return st;
       }
       if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
-      e = cudaGraphInstantiate(&h->exec, g, 0);
+      e = cudaGraphInstantiate(&f->exec, g, 0);
       cudaGraphDestroy(g);
       if (e != cudaSuccess) {
-        h->exec = nullptr;
+        f->exec = nullptr;
         return cuda_fail(h, e, "cudaGraphInstantiate");
       }
-      h->key = k;
+      f->key = k;
     }
-    CU(h, cudaGraphLaunch(h->exec, s));
+    f->used = ++h->fg_clock;
+    CU(h, cudaGraphLaunch(f->exec, s));
   } else {
     gsp2_status st = enqueue_forward(h, d_hvals, d_pvals, d_alpha, mode, nsteps, s);
     if (st != GSP2_OK) return st;

@@ -150,6 +150,24 @@ def test_graph_and_direct_launch_agree(g):
     assert torch.equal(p2, p1)
 
 
+@pytest.mark.parametrize("prec", ["fp64e", "fp16x3"])
+def test_alternating_buffer_pairs_replay_their_graphs(g, prec):
+    """The plan keeps a graph for each of the two most recent (H, P) buffer pairs: calls that
+    alternate two pairs (as a caller overlapping copies with compute does) and a third pair
+    that evicts one all give bitwise the same P."""
+    import torch
+    s = make_workload("tb512")
+    plan = g.GSP2(s.n, s.rowptr, s.colind, s.nocc, s.part, s.nparts, s.g_rowptr, s.g_colind, device="cuda:0",
+                  precision=prec)
+    hs = [torch.from_numpy(s.vals).to("cuda:0") for _ in range(3)]
+    ps = [torch.full((plan.nnz_p,), float("nan"), dtype=torch.float64, device="cuda:0") for _ in range(3)]
+    ref = plan.density(hs[0], out=ps[0]).clone()
+    for i in (1, 0, 1, 2, 0, 2, 1):
+        ps[i].fill_(float("nan"))
+        plan.density(hs[i], out=ps[i])
+        assert torch.equal(ps[i], ref), i
+
+
 def test_max_steps_cap_reports_not_converged(g):
     s = make_workload("tb512")
     plan, h, p, alpha, hist = run_gpu(g, s, max_steps=6)
