@@ -94,7 +94,9 @@ typedef struct {
                               adjoint (k > 0, lp_tail_steps = 0) runs in FP32 from FP32
                               checkpoints, products as TF32 hi + lo on the tensor cores, the
                               FP64 tail steps reversed in FP32 too */
-  int32_t use_graph;       /* 1 (default): capture the whole step sequence in a CUDA graph */
+  int32_t use_graph;       /* 1 (default): capture the whole step sequence in a CUDA graph, one
+                              per (H, P, alpha, mode, nsteps) of a density call, the two most
+                              recently used kept (two alternating buffer pairs replay theirs) */
   int32_t time_steps;      /* 1: record CUDA events around every purification-step launch
                               (read with gsp2_step_times); default 0 */
   int32_t lp_tail_steps;   /* tensor-core precisions: alternating steps in that precision
