@@ -32,8 +32,8 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 NOMINAL = {"bf16": 2250.0, "tf32": 1100.0, "fp64": 1.25}
 # DRAM bytes per launch of the dominant kernel from one ncu capture (workload, precision);
 # entries are removed when the kernel changes
-# (fp64e: tb8k capture scaled to tb30k by arena elements, 1.183 GB x 4.98)
-TRAFFIC = {("tb30k", "fp64"): 2.80e9, ("tb30k", "fp64e"): 5.89e9}
+# (fp64e: tb8k capture scaled to tb30k by arena elements, 1.075 GB x 4.98)
+TRAFFIC = {("tb30k", "fp64"): 2.80e9, ("tb30k", "fp64e"): 5.35e9}
 
 
 def dist_env():
