@@ -547,6 +547,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
       // columns the MMAs covered; the 16-column chunks beyond them lie in the part's zero
       // padding, which no step writes (the arenas are zeroed when the workspace is bound)
       const int ncols = oz_tile_cols(p.s, t.tj);
+      // a diagonal tile keeps its upper triangle and mirrors it: a chunk wholly left of the
+      // warp's first row (all its entries below the diagonal) is neither drained nor formed
+      const int cskip = (t.ti == t.tj) ? quarter * 32 : 0;
       double tY = 0.0, tN = 0.0;
       bool ok = true;
       // the two passes: read the groups' sums (integers held exactly in FP32), add them as
@@ -559,7 +562,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
 #pragma unroll 1
         for (int cc = 0; cc < 2 && ok; ++cc) {
           const int cl = colq * 32 + cc * 16;
-          if (cl >= ncols) continue;
+          if (cl >= ncols || cl + 16 <= cskip) continue;
           long long z[16];
           long long* zp = acc + (size_t)cl * 128 + m;
 #pragma unroll
@@ -593,7 +596,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
 #pragma unroll 1
       for (int cc = 0; cc < 2 && ok; ++cc) {
         const int cl = colq * 32 + cc * 16;
-        if (cl >= ncols) continue;
+        if (cl >= ncols || cl + 16 <= cskip) continue;
         const int cbase = c0 + cl;
         const long long* zp = acc + (size_t)cl * 128 + m;
         float coln[16];  // adjoint: squares of the entries (r, c) for the norms of rows c

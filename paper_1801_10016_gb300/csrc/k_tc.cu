@@ -531,8 +531,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
         for (int h = 0; h < 2; ++h) {
           const int cl = colq * 32 + h * 16;
           // 16-column chunks beyond the MMAs' columns lie in the part's zero padding, which
-          // no step writes (the iterate and operand arenas are zeroed when the workspace is bound)
-          if (cl >= tc_tile_cols(p.s, t.tj)) continue;
+          // no step writes (the iterate and operand arenas are zeroed when the workspace is
+          // bound); on a diagonal tile a chunk wholly left of the warp's first row holds only
+          // entries below the diagonal, which the mirror of the upper triangle writes
+          if (cl >= tc_tile_cols(p.s, t.tj) || (t.ti == t.tj && cl + 16 <= quarter * 32)) continue;
           const int cbase = c0 + cl;
           uint32_t v[16];
           tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(b * 128 + cl), v);
