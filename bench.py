@@ -235,7 +235,7 @@ def kernels_per_build(precision, info, lp_tail=0, report_idem=0, emulated_tail=T
     if precision == "fp64":
         return n + info.step_launches
     if precision == "fp64e":
-        return n + 1 + info.step_launches  # digits of X0, then one fused launch per step
+        return n + info.step_launches  # gather with the digits of X0, then one fused launch per step
     tail = info.fp64_tail_steps
     # low-precision steps, low-precision tail, conversion, digits of the converted iterate
     return n + info.step_launches + lp_tail + 1 + (1 if (tail > 0 and emulated_tail) else 0) + tail

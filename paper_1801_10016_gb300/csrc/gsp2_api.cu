@@ -921,13 +921,15 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
       CU(h, cudaMemcpyAsync(alpha_user, alpha + 1, (size_t)h->opt.max_steps + MAX_TAIL, cudaMemcpyDeviceToDevice, s));
     return GSP2_OK;
   }
-  CU(h, launch_gather(parts, gbl, (int)h->gblocks_ld.size(), Sall, rp, ci, hv, A(0), (double*)slots, ctl, s));
   const bool emu = prec == GSP2_PREC_FP64_EMU;
   OzStepArgs oz{};
   if (emu) {
+    // X0 and its digits in one pass (the digits to buffer 0, read by step 1)
     oz = oz_args(h, ctl);
-    CU(h, launch_oz_slice(parts, (const ColBlock*)(w + L.gblocks_ld), (int)h->gblocks_ld.size(), A(0), oz.digits, st,
-                          s));
+    CU(h, launch_oz_gather(parts, gbl, (int)h->gblocks_ld.size(), Sall, rp, ci, hv, A(0), oz.digits[0], (double*)slots,
+                           ctl, s));
+  } else {
+    CU(h, launch_gather(parts, gbl, (int)h->gblocks_ld.size(), Sall, rp, ci, hv, A(0), (double*)slots, ctl, s));
   }
   for (int i = 1; i <= ctl.last_step; ++i) {
     const double* xin = A(i - 1);

@@ -47,6 +47,10 @@ cudaError_t launch_convert(const float* const* master_of_step, double* out, int6
 cudaError_t launch_oz_slice(const PartDesc* parts, const ColBlock* blocks, int nblocks, const double* X,
                             const OzSlices* digits, const DevState* st, cudaStream_t s);
 cudaError_t launch_oz_step(const OzStepArgs& a, int grid, cudaStream_t s, bool adjoint = false);
+// gather with Eq. 1 and the digits of X0 in one pass (emulated path)
+cudaError_t launch_oz_gather(const PartDesc* parts, const ColBlock* blocks, int nblocks, const int32_t* Sall,
+                             const int64_t* rowptr, const int32_t* colind, const double* vals, double* arena,
+                             const OzSlices& dig, double* slots, const StepCtl& ctl, cudaStream_t s);
 // the emulated adjoint's Xbar digits: row norms and per-part scales, then the digits
 cudaError_t launch_oz_adj_scale(const PartDesc* parts, int nparts, const Tile* tiles, int ntiles, const double* xb0,
                                 const double* xb1, int after, double* norm, int32_t* sig, const DevState* st,

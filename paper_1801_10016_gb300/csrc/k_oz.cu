@@ -128,6 +128,59 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const PartDesc* __restric
   for (int r = lane; r < p.ld; r += 32) store_digits(sl.s, cbase + r, to_fixed(X[cbase + r]));
 }
 
+// Gather of the emulated path: Eq. 1 and the digits of X0 in one pass.  One warp per column
+// j < ld assembles the rows of column j of X0 on or above its diagonal block, the only ones
+// the emulated steps read (zeros, then the stored entries of row S_j of H that fall there,
+// located by binary search in the sorted core and halo lists), then reads them back from
+// L1/L2 and writes their digits, coalesced (rows outside the part are zero).  Blocks store
+// the core-diagonal sum of their columns; the last block forms T_0 and takes the first
+// branch.
+__global__ void __launch_bounds__(32 * COLS_PER_BLOCK) oz_gather_kernel(
+    const PartDesc* __restrict__ parts, const ColBlock* __restrict__ blocks, const int32_t* __restrict__ Sall,
+    const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colind, const double* __restrict__ vals,
+    double* __restrict__ arena, OzSlices dig, double* __restrict__ slots, StepCtl ctl) {
+  const ColBlock b = blocks[blockIdx.x];
+  const PartDesc p = parts[b.part];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int j = b.j0 + w;
+  const int32_t* S = Sall + p.soff;
+  double* col = arena + p.off + (int64_t)j * p.ld;
+  const double emax = ctl.st->eps_max, emin = ctl.st->eps_min;
+  const double den = emax - emin;
+  double tr = 0.0;
+  if (j < p.ld) {
+    const int rend = min(p.ld, (j / 128 + 1) * 128);
+    for (int r = lane; r < rend; r += 32) col[r] = 0.0;
+    __syncwarp();
+    if (j < p.s) {
+      const int32_t g = S[j];
+      for (int64_t q = rowptr[g] + lane; q < rowptr[g + 1]; q += 32) {
+        const int a = find_local(S, p.c, p.s, colind[q]);
+        if (a >= 0 && a < rend) {
+          const double x = (a == j) ? (emax - vals[q]) / den : (0.0 - vals[q]) / den;
+          col[a] = x;
+          if (a == j && j < p.c) tr = x;
+        }
+      }
+    }
+    __syncwarp();  // the lanes' stores to the column are visible to the whole warp
+    const int64_t cbase = p.off + (int64_t)j * p.ld;
+    for (int r = lane; r < rend; r += 32) store_digits(dig.s, cbase + r, to_fixed(col[r]));
+  }
+  const double2 t = block_sum2(tr, 0.0);
+  if (threadIdx.x == 0) slots[blockIdx.x] = t.x;
+  if (last_block_ticket(&ctl.st->counter)) {
+    double a = 0.0;
+    for (unsigned int k = threadIdx.x; k < gridDim.x; k += blockDim.x) a += ld_cg(&slots[k]);
+    const double2 acc = block_sum2(a, 0.0);
+    if (threadIdx.x == 0) {
+      if (ctl.st->nonfinite) ctl.st->status = ST_NONFINITE;
+      finish_step(ctl, 0, acc.x, 0.0);
+      ctl.st->counter = 0;
+    }
+  }
+}
+
 // The adjoint's operands.  `after` names the reverse step just run (0: the seed), whose
 // Xbar lies in buffer (n - after + 1) & 1 of the pair (x0, x1); kernels for a step that was
 // not run (after > n: the forward stopped earlier) return at once.
@@ -772,6 +825,14 @@ cudaError_t launch_oz_step(const OzStepArgs& a, int grid, cudaStream_t s, bool a
   int gr = grid < a.ntiles ? grid : a.ntiles;
   if (gr > OZ_MAX_GRID) gr = OZ_MAX_GRID;  // one scratch tile per CTA
   kern<<<gr, OZ_THREADS, OZ_SMEM, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_oz_gather(const PartDesc* parts, const ColBlock* blocks, int nblocks, const int32_t* Sall,
+                             const int64_t* rowptr, const int32_t* colind, const double* vals, double* arena,
+                             const OzSlices& dig, double* slots, const StepCtl& ctl, cudaStream_t s) {
+  oz_gather_kernel<<<nblocks, 32 * COLS_PER_BLOCK, 0, s>>>(parts, blocks, Sall, rowptr, colind, vals, arena, dig, slots,
+                                                            ctl);
   return cudaGetLastError();
 }
 
