@@ -32,8 +32,8 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 NOMINAL = {"bf16": 2250.0, "tf32": 1100.0, "fp64": 1.25}
 # DRAM bytes per launch of the dominant kernel from one ncu capture (workload, precision);
 # entries are removed when the kernel changes
-# (fp64e: tb8k capture scaled to tb30k by arena elements, 1.075 GB x 4.98)
-TRAFFIC = {("tb30k", "fp64"): 2.80e9, ("tb30k", "fp64e"): 5.35e9}
+# (fp64e: tb8k capture scaled to tb30k by arena elements, 1.029 GB x 4.98)
+TRAFFIC = {("tb30k", "fp64"): 2.80e9, ("tb30k", "fp64e"): 5.13e9}
 
 
 def dist_env():
@@ -278,7 +278,7 @@ def kernel_avg_ms(step_ms, nwork):
 def adjoint_block(dev, peaks, src, workload="tb4k", reps=3):
     """gsp2_backward of L = sum Pbar .* P on the 4,096-orbital, 32-part workload, checkpoints
     every 8 steps, for the three kinds of adjoint: FP64 (CUDA cores), FP64 rebuilt from BF16
-    digit products (tensor cores) and FP32 (TF32 hi + lo products on the tensor cores, behind
+    digit products (tensor cores) and FP32 (FP16 hi + lo products on the tensor cores, behind
     an FP32 forward).  Device time per backward (after a density call) and the reverse sweep's
     algorithmic flops (every reverse step 2 s^2 (s+1) per part, every rebuilt iterate
     s^2 (s+1), times the products per element on the tensor cores) against the peak of the
@@ -319,10 +319,10 @@ def adjoint_block(dev, peaks, src, workload="tb4k", reps=3):
             bound = "tensor"
         elif prec == "fp32":
             flops = (2.0 * n + rebuilt) * alg_flops(sz, 3)
-            peak = peaks["bf16_tflops"] * NOMINAL["tf32"] / NOMINAL["bf16"]
-            psrc = f"{src} bf16 x nominal tf32/bf16 (of measured)"
-            kern, fdesc = ("square_tc_persistent_kernel<tf32,3,adjoint> + <tf32,3,rebuild>",
-                           "algorithmic TF32 flops of the 3 products: reverse steps 2 s^2 (s+1), rebuilt iterates "
+            peak = peaks["bf16_tflops"]
+            psrc = f"{src}: bf16 burst (of measured; fp16 and bf16 share the 16-bit dense rate)"
+            kern, fdesc = ("square_tc_persistent_kernel<fp16,3,adjoint> + <fp16,3,rebuild>",
+                           "algorithmic FP16 flops of the 3 products: reverse steps 2 s^2 (s+1), rebuilt iterates "
                            "s^2 (s+1), per part and product")
             bound = "tensor"
         else:

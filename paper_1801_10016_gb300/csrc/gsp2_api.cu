@@ -41,11 +41,13 @@ struct WsLayout {
   size_t adj_maps, adj_maps_mn;   // CUtensorMap[k + 1][OZ_SLICES][nparts]
   size_t adj_norm, adj_sig;       // double[sum of s] (the seed's row norms), int32[nparts]
   size_t adj_normf;               // float[sum of s]: the reverse steps' row norms on their grid
-  // FP32 adjoint of the low-precision plans: TF32 (hi, lo) operand arenas aop[2 set + lo],
+  // FP32 adjoint of the low-precision plans: FP16 (hi, lo) operand arenas aop[2 set + lo],
   // sets 0..S-1 for rebuilt iterates, S and S + 1 for Xbar's ping-pong (in the FP64 tail
-  // arenas d[0], d[1], which the backward does not need); their tensor maps
+  // arenas d[0], d[1], which the backward does not need); their tensor maps; Xbar's
+  // per-part scale exponents and maxima
   std::vector<size_t> aop;
   size_t aop_maps;                // CUtensorMap[2 (S + 2)][nparts]
+  size_t xb_sig, xb_max;          // int32[nparts], uint32[nparts]
   size_t mask;                    // uint8[nnz_p]: |P| > tau flags of gsp2_threshold_graph
   std::vector<size_t> tailf;      // low-precision adjoint: FP32 iterates of the FP64 tail, recomputed
   size_t slots, rslots, state, alpha, traces, idem, step_arena;
@@ -266,7 +268,7 @@ static void build_layout(gsp2_plan* h) {
     L.seg.clear();
     L.tailf.clear();
     L.aop.clear();
-    L.xb0 = L.xb1 = L.aop_maps = 0;
+    L.xb0 = L.xb1 = L.aop_maps = L.xb_sig = L.xb_max = 0;
     if (k > 0) {
       for (int c = 0; c <= h->opt.max_steps / k; ++c) L.ckpt.push_back(take(af));
       for (int j = 1; j < k; ++j) L.seg.push_back(take(af));
@@ -274,8 +276,10 @@ static void build_layout(gsp2_plan* h) {
       L.xb1 = take(af);
       for (int t = 0; t < h->opt.fp64_tail_steps; ++t) L.tailf.push_back(take(af));
       const int nsets = std::max(k, h->opt.fp64_tail_steps);
-      for (int q = 0; q < 2 * nsets; ++q) L.aop.push_back(take(af));
+      for (int q = 0; q < 2 * nsets; ++q) L.aop.push_back(take((size_t)h->arena_elems * 2));
       L.aop_maps = take((size_t)2 * (nsets + 2) * h->parts.size() * 128);
+      L.xb_sig = take(h->parts.size() * sizeof(int32_t));
+      L.xb_max = take(h->parts.size() * sizeof(uint32_t));
     }
     h->mf_of_step.assign((size_t)h->opt.max_steps + 1 + MAX_TAIL, 0);
     for (size_t i = 0; i < h->mf_of_step.size(); ++i)
@@ -297,7 +301,7 @@ static void build_layout(gsp2_plan* h) {
     if (k > 0)
       for (int b = 0; b < 2; ++b) {
         L.aop.push_back(L.d[b]);
-        L.aop.push_back(L.d[b] + af);
+        L.aop.push_back(L.d[b] + (size_t)h->arena_elems * 2);
       }
     if (h->use_oz) {
       for (int b = 0; b < 2; ++b)
@@ -740,7 +744,8 @@ extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t byt
       for (size_t off : L.ckpt) zero.push_back({off, af});
       for (size_t off : L.seg) zero.push_back({off, af});
       for (size_t off : L.tailf) zero.push_back({off, af});
-      for (size_t off : L.aop) zero.push_back({off, af});
+      for (size_t off : L.aop) zero.push_back({off, (size_t)h->arena_elems * 2});
+      if (L.xb_max) zero.push_back({L.xb_max, h->parts.size() * sizeof(uint32_t)});
       if (L.xb0) zero.push_back({L.xb0, af});
       if (L.xb1) zero.push_back({L.xb1, af});
       for (int b = 0; b < 2; ++b) {
@@ -759,7 +764,7 @@ extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t byt
       const size_t np = h->parts.size();
       std::vector<unsigned char> amaps(L.aop.size() * np * 128, 0);
       for (size_t i = 0; i < L.aop.size(); ++i) {
-        const int r = encode_part_maps(enc, amaps.data() + i * np * 128, h->parts.data(), (int)np, h->ws + L.aop[i], 1);
+        const int r = encode_part_maps(enc, amaps.data() + i * np * 128, h->parts.data(), (int)np, h->ws + L.aop[i], 2);
         if (r != 0) return fail(h, GSP2_E_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string(r));
       }
       CU(h, up(L.aop_maps, amaps.data(), amaps.size()));
@@ -1359,23 +1364,30 @@ static gsp2_status enqueue_backward(gsp2_plan* h, const double* pbar, double* hb
   return GSP2_OK;
 }
 
-// Adjoint of a low-precision plan, in FP32 with TF32 hi + lo products on the tensor cores
-// (three products per K step, as the tf32x3 squaring): the T FP64 tail steps came last, so
+// Adjoint of a low-precision plan, in FP32 with FP16 hi + lo products on the tensor cores
+// (three products per K step, as the fp16x3 squaring): the T FP64 tail steps came last, so
 // they are reversed first, on FP32 iterates rebuilt from the loop's last iterate X_L
 // (L = n - T is known only on the device: these launches count back from n); then the
 // loop's steps, from the FP32 checkpoints the forward kept every k steps.  Every FP32
-// iterate the sweep reads gets its TF32 operand copies (a split of a stored iterate, or the
-// rebuild's own output); Xbar keeps its master and operands in a ping-pong pair.
+// iterate the sweep reads gets its FP16 operand copies of X 2^14 (a split of a stored
+// iterate, or the rebuild's own output).  Xbar keeps its FP32 master in a ping-pong pair;
+// its operands are FP16 of Xbar 2^(14 - sig) with one power-of-two scale per part, taken
+// from the part's largest |Xbar| (the seed's by a scan, each reverse step's by its
+// epilogue) and written by a scaled split after the step.
 static gsp2_status enqueue_backward_lp(gsp2_plan* h, const double* pbar, double* hbar, cudaStream_t s) {
   const WsLayout& L = h->L;
   char* w = h->ws;
   auto parts = (const PartDesc*)(w + L.parts);
   auto Sall = (const int32_t*)(w + L.S);
   auto gbl = (const ColBlock*)(w + L.gblocks);
+  auto gbl_ld = (const ColBlock*)(w + L.gblocks_ld);
+  const int ngb = (int)h->gblocks_ld.size();
   auto st = (DevState*)(w + L.state);
   auto alpha = (int8_t*)(w + L.alpha);
   float* xb0 = (float*)(w + L.xb0);
   float* xb1 = (float*)(w + L.xb1);
+  int32_t* xb_sig = (int32_t*)(w + L.xb_sig);
+  uint32_t* xb_max = (uint32_t*)(w + L.xb_max);
   const int k = h->opt.ckpt_every, M = h->opt.max_steps, T = h->opt.fp64_tail_steps;
   const int64_t ne = h->arena_elems;
   const size_t np = h->parts.size();
@@ -1391,6 +1403,9 @@ static gsp2_status enqueue_backward_lp(gsp2_plan* h, const double* pbar, double*
   base.ntiles = (int)h->tc_tiles.size();
   base.ctl = ctl;
   base.adj_tail = T;
+  base.xb_sig = xb_sig;
+  base.xb_max = xb_max;
+  base.nparts = (int)np;
   for (int b = 0; b < 2; ++b) {
     base.map_hi[b] = amap(nsets + b, 0);
     base.map_lo[b] = amap(nsets + b, 1);
@@ -1398,6 +1413,16 @@ static gsp2_status enqueue_backward_lp(gsp2_plan* h, const double* pbar, double*
     base.op_hi[b] = aop(nsets + b, 0);
     base.op_lo[b] = aop(nsets + b, 1);
   }
+  // operands of a stored iterate into set `set` (skipped where need > n - T)
+  auto split_x = [&](const float* x, int set, int need) {
+    return launch_split_f16(parts, gbl_ld, ngb, x, x, aop(set, 0), aop(set, 1), aop(set, 0), aop(set, 1), nullptr, 0,
+                            0, need, T, st, s);
+  };
+  // operands of Xbar after reverse step `step` (scaled per part)
+  auto split_xbar = [&](int step) {
+    return launch_split_f16(parts, gbl_ld, ngb, xb0, xb1, aop(nsets, 0), aop(nsets, 1), aop(nsets + 1, 0),
+                            aop(nsets + 1, 1), xb_sig, 1, step, 0, T, st, s);
+  };
   // X_step rebuilt from X_{step-1} (operand set `in`, master xin) into set `out`, master xout
   auto rebuild = [&](int in, const float* xin, int out, float* xout, int step) {
     TcStepArgs a = base;
@@ -1410,13 +1435,14 @@ static gsp2_status enqueue_backward_lp(gsp2_plan* h, const double* pbar, double*
     a.step = step;
     return launch_tc_adjoint(a, h->num_sms, true, s);
   };
-  // reverse step `step` with X_{step-1} in operand set `x`
+  // reverse step `step` with X_{step-1} in operand set `x`, then Xbar's new operands
   auto reverse = [&](int x, int step) {
     TcStepArgs a = base;
     a.xmap_hi = amap(x, 0);
     a.xmap_lo = amap(x, 1);
     a.step = step;
-    return launch_tc_adjoint(a, h->num_sms, false, s);
+    cudaError_t e = launch_tc_adjoint(a, h->num_sms, false, s);
+    return e != cudaSuccess ? e : split_xbar(step);
   };
   // Xbar's operands live in the FP64 tail arenas: zeroed first, so that the padding the
   // reverse steps do not write reads as zero, and again at the end, so that the next
@@ -1426,16 +1452,18 @@ static gsp2_status enqueue_backward_lp(gsp2_plan* h, const double* pbar, double*
   CU(h, cudaMemsetAsync(w + L.d[1], 0, ab, s));
   CU(h, launch_adj_seed<float>(parts, gbl, (int)h->gblocks.size(), Sall, (const int32_t*)(w + L.invperm),
                                (const int64_t*)(w + L.pcolptr), pbar, xb0, s));
-  CU(h, launch_split_tf32(xb0, aop(nsets, 0), aop(nsets, 1), ne, st, 0, 0, s));
+  CU(h, launch_xbar_seed_scale(parts, gbl_ld, ngb, xb0, xb_max, xb_sig, (int)np, st, s));
+  CU(h, launch_split_f16(parts, gbl_ld, ngb, xb0, xb0, aop(nsets, 0), aop(nsets, 1), aop(nsets, 0), aop(nsets, 1),
+                         xb_sig, 0, 0, 0, 0, st, s));
   if (T > 0) {
     CU(h, launch_copy_iterate((const float* const*)(w + L.master_of_step), tf(0), ne, st, T, s));
-    CU(h, launch_split_tf32(tf(0), aop(0, 0), aop(0, 1), ne, st, 0, 0, s));
+    CU(h, split_x(tf(0), 0, 0));
     for (int t = 1; t < T; ++t) CU(h, rebuild(t - 1, tf(t - 1), t, tf(t), t - T));
     for (int t = T; t >= 1; --t) CU(h, reverse(t - 1, t - T));
   }
   for (int c0 = (M / k) * k; c0 >= 0; c0 -= k) {
     const float* ck = (const float*)(w + L.ckpt[c0 / k]);
-    CU(h, launch_split_tf32(ck, aop(0, 0), aop(0, 1), ne, st, c0 + 1, T, s));
+    CU(h, split_x(ck, 0, c0 + 1));
     for (int j = 1; j < k && c0 + j < M; ++j)
       CU(h, rebuild(j - 1, (j == 1) ? ck : (const float*)(w + L.seg[j - 2]), j, (float*)(w + L.seg[j - 1]), c0 + j));
     for (int i = std::min(c0 + k, M); i >= c0 + 1; --i) CU(h, reverse(i - 1 - c0, i));

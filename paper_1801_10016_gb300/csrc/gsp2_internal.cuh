@@ -102,7 +102,15 @@ struct TcStepArgs {
   void* xo_hi;
   void* xo_lo;
   int adj_tail;
+  // FP16 operands (KIND 2) of the adjoint: Xbar's are FP16 of Xbar 2^(14 - sig) with one
+  // scale exponent per part; the reverse step writes Xbar's master only, records the
+  // largest |Xbar_new| of each part (FP32 bits) and its last block turns them into the
+  // parts' new scales (clearing the maxima); a scaled split then writes the operands
+  int32_t* xb_sig;
+  uint32_t* xb_max;
+  int nparts;
 };
+constexpr int TC_SIG_MIN = -98, TC_SIG_MAX = 126;  // range of the FP16 adjoint's scale exponents
 
 // FP64 products rebuilt from BF16 digits (k_oz.cu)
 constexpr int OZ_SLICES = 7;  // base-2^7 digits per entry

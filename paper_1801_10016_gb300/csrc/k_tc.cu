@@ -305,7 +305,11 @@ __global__ void __launch_bounds__(256, 2) square_tc_kernel(TcStepArgs a) {
 // recorded branch; MODE 2 is a reverse step of that adjoint: an upper tile (I, J) of
 // Xbar X + X Xbar is one product over K = 2s, rows I of [Xbar | X] times rows J of
 // [X | Xbar] (both symmetric and stored whole), and Xbar_new = that or 2 Xbar minus it.
-// Neither keeps traces or runs the step bookkeeping.
+// The adjoint runs on FP16 hi + lo operands (KIND 2); Xbar's carry a per-part scale.
+// Neither mode keeps traces or runs the step bookkeeping.
+
+// 2^e as FP32 for -126 <= e <= 127 (built from the exponent bits).
+__device__ __forceinline__ float pow2i(int e) { return __uint_as_float((uint32_t)(e + 127) << 23); }
 
 // Columns of tile column block tj that an MMA must cover: those inside the part, rounded up
 // to 16 (N of an M = 128 MMA is a multiple of 16); the rest of the block is zero padding.
@@ -330,7 +334,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
   // instruction descriptor without N (set per tile: the last column block of a part covers
   // only the part's columns, rounded up to 16)
   constexpr uint32_t IDESC0 = (1u << 4) | (FMT << 7) | (FMT << 10) | ((128u >> 4) << 24);
-  static_assert(MODE == TC_STEP || (KIND == 1 && NPROD == 3), "the FP32 adjoint runs on TF32 hi + lo operands");
+  static_assert(MODE == TC_STEP || (KIND == 2 && NPROD == 3), "the FP32 adjoint runs on FP16 hi + lo operands");
+  // the FP16 adjoint's reverse step: Xbar's operands carry a per-part scale, so the step
+  // writes Xbar's master only and records each part's largest |Xbar_new| for the next scale
+  constexpr bool XBAR16 = MODE == TC_ADJOINT && KIND == 2;
 
   int step = a.step;
   int n = 0;
@@ -525,6 +532,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
       const int r0 = t.ti * 128, c0 = t.tj * 128;
       const int r = r0 + m;
       const bool diag = t.slot >= 0;
+      // sums back to the unscaled product: 2^-28 for FP16 operands of X 2^14 on both sides,
+      // 2^(sig - 28) where the Xbar side is FP16 of Xbar 2^(14 - sig)
+      const float ysc = XBAR16 ? pow2i(a.xb_sig[t.part] - 28) : Kind<KIND>::YSCALE;
+      uint32_t amax = 0;  // FP16 adjoint: largest |Xbar_new| of the thread's entries (FP32 bits)
       double tY = 0.0, tN = 0.0;
       if (ok) {
 #pragma unroll 1
@@ -546,11 +557,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
           float yd = 0.0f, zd = 0.0f;
 #pragma unroll
           for (int j = 0; j < 16; ++j) {
-            const float y = __uint_as_float(v[j]) * Kind<KIND>::YSCALE;
+            const float y = __uint_as_float(v[j]) * ysc;
             const float z = (alf > 0) ? (2.0f * x[j] - y) : y;
             yd = (cbase + j == r) ? y : yd;
             zd = (cbase + j == r) ? z : zd;
             x[j] = z;
+            if (XBAR16) amax = max(amax, __float_as_uint(z) & 0x7FFFFFFFu);  // NaN bits exceed Inf
           }
           if (MODE == TC_STEP && diag && r >= cbase && r < cbase + 16 && r < p.c) {
             tY += (double)yd;
@@ -563,7 +575,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
             if (t.ti == t.tj && cbase + j < r) continue;
             const int64_t e = (int64_t)(cbase + j) * ld + r;
             Xo[e] = x[j];
-            store_operands<KIND, NPROD>(ohi, olo, p.off + e, x[j]);
+            if (!XBAR16) store_operands<KIND, NPROD>(ohi, olo, p.off + e, x[j]);
           }
           if (t.ti == t.tj && cbase <= r) {
             // the 16 x 16 blocks of a diagonal tile that straddle the diagonal: element stores
@@ -571,7 +583,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
               if (cbase + j <= r) continue;
               const int64_t e = (int64_t)r * ld + cbase + j;
               Xo[e] = x[j];
-              store_operands<KIND, NPROD>(ohi, olo, p.off + e, x[j]);
+              if (!XBAR16) store_operands<KIND, NPROD>(ohi, olo, p.off + e, x[j]);
             }
           } else {
             // the mirrored row segment (all of it right of the diagonal): vector stores
@@ -579,7 +591,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
             float4* dst = reinterpret_cast<float4*>(Xo + e0);
 #pragma unroll
             for (int q = 0; q < 4; ++q) dst[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
-            store_operand_row<KIND, NPROD, 16>(ohi, olo, p.off + e0, x);
+            if (!XBAR16) store_operand_row<KIND, NPROD, 16>(ohi, olo, p.off + e0, x);
           }
         }
       } else {
@@ -588,6 +600,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(tempty(b));
+      if (XBAR16) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) amax = max(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        if (lane == 0 && amax != 0) atomicMax(&a.xb_max[t.part], amax);
+      }
       if (MODE == TC_STEP && diag) {
         // fixed-order reduction over the epilogue warps (named barrier 1)
         tY = warp_sum(tY);
@@ -612,6 +629,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
   if (threadIdx.x == 0 && *s_err) {
     a.ctl.st->timeout = 1;
     if (MODE != TC_STEP) a.ctl.st->status = ST_TIMEOUT;  // no step bookkeeping follows
+  }
+  if (XBAR16 && last_block_ticket(&a.ctl.st->counter)) {
+    // each part's new scale: the smallest sig with 2^sig > max |Xbar_new| (0 for a zero or a
+    // non-finite Xbar, whose operands carry the NaN or Inf on), clamped to the FP32 range the
+    // scalings stay exact in; the maxima are cleared for the next step
+    for (int k = threadIdx.x; k < a.nparts; k += blockDim.x) {
+      const uint32_t mb = __ldcg(&a.xb_max[k]);
+      a.xb_max[k] = 0u;
+      int e = 0;
+      if (mb != 0u && mb < 0x7F800000u) (void)frexpf(__uint_as_float(mb), &e);
+      a.xb_sig[k] = e < TC_SIG_MIN ? TC_SIG_MIN : (e > TC_SIG_MAX ? TC_SIG_MAX : e);
+    }
+    if (threadIdx.x == 0) a.ctl.st->counter = 0;
   }
   if (MODE != TC_STEP) return;
 
@@ -943,25 +973,85 @@ static cudaError_t launch_tc_persistent(const TcStepArgs& a, int grid, cudaStrea
 
 cudaError_t launch_tc_adjoint(const TcStepArgs& a, int grid, bool rebuild, cudaStream_t s) {
   const int g = grid < a.ntiles ? grid : a.ntiles;
-  return rebuild ? launch_tc_persistent<1, 3, TC_REBUILD>(a, g, s) : launch_tc_persistent<1, 3, TC_ADJOINT>(a, g, s);
+  return rebuild ? launch_tc_persistent<2, 3, TC_REBUILD>(a, g, s) : launch_tc_persistent<2, 3, TC_ADJOINT>(a, g, s);
 }
 
-// TF32 hi + lo operands of an FP32 arena (n elements): the operand copies of a checkpoint
-// or of Xbar for the adjoint.  Skipped where need > n - tail (a checkpoint the reverse
-// sweep does not reach).
-__global__ void __launch_bounds__(256) split_tf32_kernel(const float* __restrict__ x, uint32_t* __restrict__ hi,
-                                                         uint32_t* __restrict__ lo, int64_t n, const DevState* st,
-                                                         int need, int tail) {
-  if (need > *(volatile const int32_t*)&st->steps - tail) return;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
-    store_operands<1, 3>(hi, lo, e, x[e]);
+// FP16 hi + lo operands of an FP32 arena, one warp per column up to ld: of x 2^-sig[part]
+// (the FP16 adjoint's Xbar; sig NULL: of x, an iterate), from x0 into (hi0, lo0).  With
+// `after`, the arena is Xbar after reverse step `step` (resolved as in the adjoint kernels:
+// step <= 0 counts back from n, loop steps above n - tail were not run), whose source and
+// destination follow the step parity; otherwise the call is skipped where need > n - tail.
+__global__ void __launch_bounds__(256) split_f16_kernel(const PartDesc* __restrict__ parts,
+                                                        const ColBlock* __restrict__ blocks, const float* x0,
+                                                        const float* x1, uint16_t* hi0, uint16_t* lo0, uint16_t* hi1,
+                                                        uint16_t* lo1, const int32_t* __restrict__ sig, int after,
+                                                        int step, int need, int tail, const DevState* st) {
+  const int n = *(volatile const int32_t*)&st->steps;
+  int buf = 0;
+  if (after) {  // Xbar after reverse step `step` lies in buffer (n - step + 1) & 1
+    if (step <= 0) step += n;
+    else if (step > n - tail) return;
+    if (step < 1) return;
+    buf = (n - step + 1) & 1;
+  } else if (need > n - tail) {
+    return;
+  }
+  const float* x = buf ? x1 : x0;
+  uint16_t* hi = buf ? hi1 : hi0;
+  uint16_t* lo = buf ? lo1 : lo0;
+  const ColBlock b = blocks[blockIdx.x];
+  const PartDesc p = parts[b.part];
+  const int lane = threadIdx.x & 31;
+  const int j = b.j0 + (threadIdx.x >> 5);
+  if (j >= p.ld) return;
+  const float f = sig ? pow2i(-sig[b.part]) : 1.0f;
+  const int64_t cbase = p.off + (int64_t)j * p.ld;
+  for (int r = lane; r < p.ld; r += 32) store_operands<2, 3>(hi, lo, cbase + r, x[cbase + r] * f);
 }
 
-cudaError_t launch_split_tf32(const float* x, void* hi, void* lo, int64_t n, const DevState* st, int need, int tail,
-                              cudaStream_t s) {
-  split_tf32_kernel<<<152 * 8, 256, 0, s>>>(x, (uint32_t*)hi, (uint32_t*)lo, n, st, need, tail);
+// Scale of the seed Xbar for its FP16 operands: each part's largest |x| into xb_max (one
+// warp per column), then, in the last block, the parts' scale exponents (maxima cleared).
+__global__ void __launch_bounds__(256) xbar_seed_scale_kernel(const PartDesc* __restrict__ parts,
+                                                              const ColBlock* __restrict__ blocks, const float* x,
+                                                              uint32_t* xb_max, int32_t* xb_sig, int nparts,
+                                                              DevState* st) {
+  const ColBlock b = blocks[blockIdx.x];
+  const PartDesc p = parts[b.part];
+  const int lane = threadIdx.x & 31;
+  const int j = b.j0 + (threadIdx.x >> 5);
+  uint32_t m = 0;
+  if (j < p.s)
+    for (int r = lane; r < p.s; r += 32) m = max(m, __float_as_uint(x[p.off + (int64_t)j * p.ld + r]) & 0x7FFFFFFFu);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0 && m != 0) atomicMax(&xb_max[b.part], m);
+  if (last_block_ticket(&st->counter)) {
+    for (int k = threadIdx.x; k < nparts; k += blockDim.x) {
+      const uint32_t mb = __ldcg(&xb_max[k]);
+      xb_max[k] = 0u;
+      int e = 0;
+      if (mb != 0u && mb < 0x7F800000u) (void)frexpf(__uint_as_float(mb), &e);
+      xb_sig[k] = e < TC_SIG_MIN ? TC_SIG_MIN : (e > TC_SIG_MAX ? TC_SIG_MAX : e);
+    }
+    if (threadIdx.x == 0) st->counter = 0;
+  }
+}
+
+cudaError_t launch_split_f16(const PartDesc* parts, const ColBlock* blocks, int nblocks, const float* x0,
+                             const float* x1, void* hi0, void* lo0, void* hi1, void* lo1, const int32_t* sig, int after,
+                             int step, int need, int tail, const DevState* st, cudaStream_t s) {
+  split_f16_kernel<<<nblocks, 32 * COLS_PER_BLOCK, 0, s>>>(parts, blocks, x0, x1, (uint16_t*)hi0, (uint16_t*)lo0,
+                                                            (uint16_t*)hi1, (uint16_t*)lo1, sig, after, step, need,
+                                                            tail, st);
   return cudaGetLastError();
 }
+
+cudaError_t launch_xbar_seed_scale(const PartDesc* parts, const ColBlock* blocks, int nblocks, const float* x,
+                                   uint32_t* xb_max, int32_t* xb_sig, int nparts, DevState* st, cudaStream_t s) {
+  xbar_seed_scale_kernel<<<nblocks, 32 * COLS_PER_BLOCK, 0, s>>>(parts, blocks, x, xb_max, xb_sig, nparts, st);
+  return cudaGetLastError();
+}
+
 
 template <int KIND, int NPROD>
 static cudaError_t launch_tc(const TcStepArgs& a, int ntiles, cudaStream_t s) {

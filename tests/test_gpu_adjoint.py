@@ -112,12 +112,13 @@ def test_adjoint_through_tail_steps(g, prec):
 @pytest.mark.parametrize("prec,tail,case,tol", [("fp32", 0, "small", 2e-5), ("fp32", 0, "tb4k", 2e-5),
                                                 ("fp32", 2, "tb4k", 2e-5), ("tf32x3", 2, "tb4k", 2e-5),
                                                 ("tf32x3", 2, "small", 2e-5), ("fp32", 3, "tb512", 2e-5),
-                                                ("bf16x3", 1, "tb512", 1e-4)])
+                                                ("fp16x3", 2, "tb4k", 2e-5), ("bf16x3", 1, "tb512", 1e-4)])
 def test_low_precision_adjoint_matches_oracle_on_the_same_sequence(g, prec, tail, case, tol):
-    """FP32 adjoint (TF32 hi + lo products on the tensor cores) of a low-precision forward
-    against the oracle's FP64 adjoint of the same polynomial (the GPU's own branch sequence,
-    tail steps included).  The sweep rebuilds its iterates from the forward's checkpoints,
-    so a bf16x3 forward (16-bit operands, outside the 1e-6 gate on P) bounds it at 1e-4."""
+    """FP32 adjoint (FP16 hi + lo products on the tensor cores, Xbar's scaled per part) of a
+    low-precision forward against the oracle's FP64 adjoint of the same polynomial (the
+    GPU's own branch sequence, tail steps included).  The sweep rebuilds its iterates from
+    the forward's checkpoints, so a bf16x3 forward (16-bit operands, outside the 1e-6 gate on
+    P) bounds it at 1e-4."""
     s = make_tb_system(48, 4, 3.0, seed=21) if case == "small" else make_workload(case)
     plan, h, hist, pb, Pbar, hb = run_adjoint(g, s, precision=prec, fp64_tail_steps=tail, ckpt_every=4)
     assert hist["status"] == 0 and hist["report"]["fp64_steps"] == tail
@@ -153,15 +154,31 @@ def test_density_after_backward_is_unchanged(g, prec, tail):
 
 
 @pytest.mark.parametrize("case,k", [("small", 1), ("small", 3), ("small", 45), ("tb512", 5)])
-def test_tf32x3_checkpoint_interval_does_not_change_the_gradient(g, case, k):
-    """The FP32 adjoint rebuilds iterates with the tf32x3 step's own tensor-core arithmetic
-    from the same TF32 operand split, so for tf32x3 plans every rebuilt iterate equals the
+def test_fp16x3_checkpoint_interval_does_not_change_the_gradient(g, case, k):
+    """The FP32 adjoint rebuilds iterates with the fp16x3 step's own tensor-core arithmetic
+    from the same FP16 operand split, so for fp16x3 plans every rebuilt iterate equals the
     forward's bit for bit: the same gradient whatever the checkpoint interval."""
     import torch
     s = make_tb_system(48, 4, 3.0, seed=21) if case == "small" else make_workload("tb512")
-    _, _, _, _, _, hb4 = run_adjoint(g, s, precision="tf32x3", fp64_tail_steps=0, ckpt_every=4)
-    _, _, _, _, _, hbk = run_adjoint(g, s, precision="tf32x3", fp64_tail_steps=0, ckpt_every=k)
+    _, _, _, _, _, hb4 = run_adjoint(g, s, precision="fp16x3", fp64_tail_steps=0, ckpt_every=4)
+    _, _, _, _, _, hbk = run_adjoint(g, s, precision="fp16x3", fp64_tail_steps=0, ckpt_every=k)
     assert torch.equal(hb4, hbk)
+
+
+def test_fp16_adjoint_is_exact_under_power_of_two_scaling(g):
+    """Xbar's FP16 operands carry a per-part power-of-two scale taken from its largest entry:
+    Pbar scaled by 2^e gives Hbar scaled by 2^e exactly, far beyond FP16's own range."""
+    import torch
+    s = make_workload("tb512")
+    plan = g.GSP2(s.n, s.rowptr, s.colind, s.nocc, s.part, s.nparts, s.g_rowptr, s.g_colind, device="cuda:0",
+                  precision="fp16x3", fp64_tail_steps=2, ckpt_every=4)
+    plan.density(torch.from_numpy(s.vals).to("cuda:0"))
+    pb, _ = pbar_for_trace_loss(s, plan)
+    pbt = torch.from_numpy(pb).to("cuda:0")
+    hb = plan.backward(pbt).clone()
+    assert torch.isfinite(hb).all()
+    for e in (-40, 40):
+        assert torch.equal(plan.backward(pbt * 2.0 ** e), hb * 2.0 ** e), e
 
 
 @pytest.mark.parametrize("case,k", [("small", 3), ("tb512", 8), ("tb4k", 3), ("tb4k", 8)])
