@@ -92,7 +92,7 @@ typedef struct {
   int32_t ckpt_every;      /* adjoint: keep every k-th iterate; 0 = no adjoint; -1 (default) =
                               8 for FP64 and FP64_EMU, 0 for the low-precision modes, whose
                               adjoint (k > 0, lp_tail_steps = 0) runs in FP32 from FP32
-                              checkpoints, products as TF32 hi + lo on the tensor cores, the
+                              checkpoints, products as FP16 hi + lo on the tensor cores, the
                               FP64 tail steps reversed in FP32 too */
   int32_t use_graph;       /* 1 (default): capture the whole step sequence in a CUDA graph, one
                               per (H, P, alpha, mode, nsteps) of a density call, the two most
@@ -296,7 +296,7 @@ gsp2_status gsp2_autotune(gsp2_handle h, const double* d_hvals, double* d_pvals,
  * Iterates are recomputed from checkpoints kept every `ckpt_every` steps.  FP64 plans
  * run it on the FP64 pipe, FP64_EMU plans from BF16 digit products (Xbar's digits scaled
  * by a power of two per part taken from its row norms), the low-precision plans in FP32
- * with TF32 hi + lo products.
+ * with FP16 hi + lo products (Xbar's operands scaled by a power of two per part).
  *  d_pbar  device double[nnz_p]
  *  d_hbar  device double[nnz_h], overwritten; symmetric for a symmetric problem
  * Requires ckpt_every > 0 at create and a completed density call (GSP2_E_STATE).
