@@ -755,7 +755,7 @@ extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t byt
       for (const auto& z : zero) CU(h, cudaMemsetAsync(h->ws + z.first, 0, z.second, s));
     }
     if (!L.aop.empty()) {
-      // the FP32 adjoint: maps over its TF32 operand arenas
+      // the FP32 adjoint: maps over its FP16 operand arenas
       void* enc = nullptr;
       cudaDriverEntryPointQueryResult q{};
       CU(h, cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &enc, 12000, cudaEnableDefault, &q));

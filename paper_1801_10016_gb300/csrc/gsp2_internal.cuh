@@ -88,7 +88,7 @@ struct TcStepArgs {
   StepCtl ctl;
   int step;                // ignored in tail mode (step = steps applied + 1)
   int tail;                // 0: loop step; 1: first alternating tail step; 2: further ones
-  // FP32 adjoint of the low-precision plans (TF32 hi + lo operands, explicit buffers):
+  // FP32 adjoint of the low-precision plans (FP16 hi + lo operands, explicit buffers):
   // the rebuilt iterate X_step reads the operands of X_{step-1} (xmap_*) and its master
   // xin and writes master xout and operands xo_*; the reverse step `step` reads the
   // operands of X_{step-1} (xmap_*) and Xbar's ping-pong (map_*, master, op_* [2], the
