@@ -2,6 +2,7 @@
 // padded layout, work lists, pattern of P), workspace binding, and the queued step
 // sequence of a density call, captured once into a CUDA graph and replayed.
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -47,7 +48,7 @@ struct WsLayout {
   // per-part scale exponents and maxima
   std::vector<size_t> aop;
   size_t aop_maps;                // CUtensorMap[2 (S + 2)][nparts]
-  size_t xb_sig, xb_max;          // int32[nparts], uint32[nparts]
+  size_t xb_sig, xb_max;          // int32[2][nparts] (scales read, written), uint32[nparts]
   size_t mask;                    // uint8[nnz_p]: |P| > tau flags of gsp2_threshold_graph
   std::vector<size_t> tailf;      // low-precision adjoint: FP32 iterates of the FP64 tail, recomputed
   size_t slots, rslots, state, alpha, traces, idem, step_arena;
@@ -278,7 +279,7 @@ static void build_layout(gsp2_plan* h) {
       const int nsets = std::max(k, h->opt.fp64_tail_steps);
       for (int q = 0; q < 2 * nsets; ++q) L.aop.push_back(take((size_t)h->arena_elems * 2));
       L.aop_maps = take((size_t)2 * (nsets + 2) * h->parts.size() * 128);
-      L.xb_sig = take(h->parts.size() * sizeof(int32_t));
+      L.xb_sig = take(2 * h->parts.size() * sizeof(int32_t));
       L.xb_max = take(h->parts.size() * sizeof(uint32_t));
     }
     h->mf_of_step.assign((size_t)h->opt.max_steps + 1 + MAX_TAIL, 0);
@@ -1370,10 +1371,10 @@ static gsp2_status enqueue_backward(gsp2_plan* h, const double* pbar, double* hb
 // (L = n - T is known only on the device: these launches count back from n); then the
 // loop's steps, from the FP32 checkpoints the forward kept every k steps.  Every FP32
 // iterate the sweep reads gets its FP16 operand copies of X 2^14 (a split of a stored
-// iterate, or the rebuild's own output).  Xbar keeps its FP32 master in a ping-pong pair;
-// its operands are FP16 of Xbar 2^(14 - sig) with one power-of-two scale per part, taken
-// from the part's largest |Xbar| (the seed's by a scan, each reverse step's by its
-// epilogue) and written by a scaled split after the step.
+// iterate, or the rebuild's own output).  Xbar keeps its FP32 master and its operands,
+// FP16 of Xbar 2^(14 - sig) with one power-of-two scale per part, in a ping-pong pair: the
+// seed's scale from a scan, each reverse step's output written at a scale fixed before the
+// step from the largest |Xbar| so far and the growth bound of one step.
 static gsp2_status enqueue_backward_lp(gsp2_plan* h, const double* pbar, double* hbar, cudaStream_t s) {
   const WsLayout& L = h->L;
   char* w = h->ws;
@@ -1406,6 +1407,11 @@ static gsp2_status enqueue_backward_lp(gsp2_plan* h, const double* pbar, double*
   base.xb_sig = xb_sig;
   base.xb_max = xb_max;
   base.nparts = (int)np;
+  // headroom of the written scale: one reverse step multiplies the largest |Xbar| by at most
+  // 2 + 2 sqrt(s) (Cauchy-Schwarz, ||X||_2 <= 1), one bit more for the rounding of X
+  int smax = 1;
+  for (const PartDesc& d : h->parts) smax = std::max(smax, (int)d.s);
+  base.xb_headroom = (int)std::ceil(std::log2(2.0 + 2.0 * std::sqrt((double)smax))) + 1;
   for (int b = 0; b < 2; ++b) {
     base.map_hi[b] = amap(nsets + b, 0);
     base.map_lo[b] = amap(nsets + b, 1);
@@ -1415,13 +1421,7 @@ static gsp2_status enqueue_backward_lp(gsp2_plan* h, const double* pbar, double*
   }
   // operands of a stored iterate into set `set` (skipped where need > n - T)
   auto split_x = [&](const float* x, int set, int need) {
-    return launch_split_f16(parts, gbl_ld, ngb, x, x, aop(set, 0), aop(set, 1), aop(set, 0), aop(set, 1), nullptr, 0,
-                            0, need, T, st, s);
-  };
-  // operands of Xbar after reverse step `step` (scaled per part)
-  auto split_xbar = [&](int step) {
-    return launch_split_f16(parts, gbl_ld, ngb, xb0, xb1, aop(nsets, 0), aop(nsets, 1), aop(nsets + 1, 0),
-                            aop(nsets + 1, 1), xb_sig, 1, step, 0, T, st, s);
+    return launch_split_f16(parts, gbl_ld, ngb, x, aop(set, 0), aop(set, 1), nullptr, need, T, st, s);
   };
   // X_step rebuilt from X_{step-1} (operand set `in`, master xin) into set `out`, master xout
   auto rebuild = [&](int in, const float* xin, int out, float* xout, int step) {
@@ -1435,14 +1435,13 @@ static gsp2_status enqueue_backward_lp(gsp2_plan* h, const double* pbar, double*
     a.step = step;
     return launch_tc_adjoint(a, h->num_sms, true, s);
   };
-  // reverse step `step` with X_{step-1} in operand set `x`, then Xbar's new operands
+  // reverse step `step` with X_{step-1} in operand set `x`
   auto reverse = [&](int x, int step) {
     TcStepArgs a = base;
     a.xmap_hi = amap(x, 0);
     a.xmap_lo = amap(x, 1);
     a.step = step;
-    cudaError_t e = launch_tc_adjoint(a, h->num_sms, false, s);
-    return e != cudaSuccess ? e : split_xbar(step);
+    return launch_tc_adjoint(a, h->num_sms, false, s);
   };
   // Xbar's operands live in the FP64 tail arenas: zeroed first, so that the padding the
   // reverse steps do not write reads as zero, and again at the end, so that the next
@@ -1452,9 +1451,8 @@ static gsp2_status enqueue_backward_lp(gsp2_plan* h, const double* pbar, double*
   CU(h, cudaMemsetAsync(w + L.d[1], 0, ab, s));
   CU(h, launch_adj_seed<float>(parts, gbl, (int)h->gblocks.size(), Sall, (const int32_t*)(w + L.invperm),
                                (const int64_t*)(w + L.pcolptr), pbar, xb0, s));
-  CU(h, launch_xbar_seed_scale(parts, gbl_ld, ngb, xb0, xb_max, xb_sig, (int)np, st, s));
-  CU(h, launch_split_f16(parts, gbl_ld, ngb, xb0, xb0, aop(nsets, 0), aop(nsets, 1), aop(nsets, 0), aop(nsets, 1),
-                         xb_sig, 0, 0, 0, 0, st, s));
+  CU(h, launch_xbar_seed_scale(parts, gbl_ld, ngb, xb0, xb_max, xb_sig, (int)np, base.xb_headroom, st, s));
+  CU(h, launch_split_f16(parts, gbl_ld, ngb, xb0, aop(nsets, 0), aop(nsets, 1), xb_sig, 0, 0, st, s));
   if (T > 0) {
     CU(h, launch_copy_iterate((const float* const*)(w + L.master_of_step), tf(0), ne, st, T, s));
     CU(h, split_x(tf(0), 0, 0));

@@ -103,12 +103,15 @@ struct TcStepArgs {
   void* xo_lo;
   int adj_tail;
   // FP16 operands (KIND 2) of the adjoint: Xbar's are FP16 of Xbar 2^(14 - sig) with one
-  // scale exponent per part; the reverse step writes Xbar's master only, records the
-  // largest |Xbar_new| of each part (FP32 bits) and its last block turns them into the
-  // parts' new scales (clearing the maxima); a scaled split then writes the operands
+  // scale exponent per part: xb_sig[k] that of the operands a reverse step reads,
+  // xb_sig[nparts + k] that of the operands it writes, chosen before the step from the
+  // largest |Xbar| so far plus xb_headroom bits (one step multiplies the largest entry by
+  // at most 2 + 2 sqrt(s), Cauchy-Schwarz with ||X||_2 <= 1).  The step records the largest
+  // |Xbar_new| of each part (FP32 bits, xb_max) and its last block moves the scales on
   int32_t* xb_sig;
   uint32_t* xb_max;
   int nparts;
+  int xb_headroom;
 };
 constexpr int TC_SIG_MIN = -98, TC_SIG_MAX = 126;  // range of the FP16 adjoint's scale exponents
 

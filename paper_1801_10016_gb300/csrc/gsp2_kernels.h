@@ -37,11 +37,11 @@ cudaError_t launch_gather_lp(int kind, int nprod, const PartDesc* parts, const C
                              cudaStream_t s);
 // FP32 adjoint of the low-precision plans on the tensor cores (FP16 hi + lo operands)
 cudaError_t launch_tc_adjoint(const TcStepArgs& a, int grid, bool rebuild, cudaStream_t s);
-cudaError_t launch_split_f16(const PartDesc* parts, const ColBlock* blocks, int nblocks, const float* x0,
-                             const float* x1, void* hi0, void* lo0, void* hi1, void* lo1, const int32_t* sig, int after,
-                             int step, int need, int tail, const DevState* st, cudaStream_t s);
+cudaError_t launch_split_f16(const PartDesc* parts, const ColBlock* blocks, int nblocks, const float* x, void* hi,
+                             void* lo, const int32_t* sig, int need, int tail, const DevState* st, cudaStream_t s);
 cudaError_t launch_xbar_seed_scale(const PartDesc* parts, const ColBlock* blocks, int nblocks, const float* x,
-                                   uint32_t* xb_max, int32_t* xb_sig, int nparts, DevState* st, cudaStream_t s);
+                                   uint32_t* xb_max, int32_t* xb_sig, int nparts, int headroom, DevState* st,
+                                   cudaStream_t s);
 cudaError_t launch_copy_iterate(const float* const* master_of_step, float* out, int64_t n, const DevState* st,
                                 int back, cudaStream_t s);
 cudaError_t launch_convert(const float* const* master_of_step, double* out, int64_t n, const DevState* st,

@@ -335,8 +335,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
   // only the part's columns, rounded up to 16)
   constexpr uint32_t IDESC0 = (1u << 4) | (FMT << 7) | (FMT << 10) | ((128u >> 4) << 24);
   static_assert(MODE == TC_STEP || (KIND == 2 && NPROD == 3), "the FP32 adjoint runs on FP16 hi + lo operands");
-  // the FP16 adjoint's reverse step: Xbar's operands carry a per-part scale, so the step
-  // writes Xbar's master only and records each part's largest |Xbar_new| for the next scale
+  // the FP16 adjoint's reverse step: Xbar's operands carry a per-part scale (read at one,
+  // written at the next) and the step records each part's largest |Xbar_new|
   constexpr bool XBAR16 = MODE == TC_ADJOINT && KIND == 2;
 
   int step = a.step;
@@ -535,6 +535,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
       // sums back to the unscaled product: 2^-28 for FP16 operands of X 2^14 on both sides,
       // 2^(sig - 28) where the Xbar side is FP16 of Xbar 2^(14 - sig)
       const float ysc = XBAR16 ? pow2i(a.xb_sig[t.part] - 28) : Kind<KIND>::YSCALE;
+      const float osc = XBAR16 ? pow2i(-a.xb_sig[a.nparts + t.part]) : 1.0f;  // Xbar_new's operand scale
       uint32_t amax = 0;  // FP16 adjoint: largest |Xbar_new| of the thread's entries (FP32 bits)
       double tY = 0.0, tN = 0.0;
       if (ok) {
@@ -575,7 +576,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
             if (t.ti == t.tj && cbase + j < r) continue;
             const int64_t e = (int64_t)(cbase + j) * ld + r;
             Xo[e] = x[j];
-            if (!XBAR16) store_operands<KIND, NPROD>(ohi, olo, p.off + e, x[j]);
+            store_operands<KIND, NPROD>(ohi, olo, p.off + e, XBAR16 ? x[j] * osc : x[j]);
           }
           if (t.ti == t.tj && cbase <= r) {
             // the 16 x 16 blocks of a diagonal tile that straddle the diagonal: element stores
@@ -583,7 +584,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
               if (cbase + j <= r) continue;
               const int64_t e = (int64_t)r * ld + cbase + j;
               Xo[e] = x[j];
-              if (!XBAR16) store_operands<KIND, NPROD>(ohi, olo, p.off + e, x[j]);
+              store_operands<KIND, NPROD>(ohi, olo, p.off + e, XBAR16 ? x[j] * osc : x[j]);
             }
           } else {
             // the mirrored row segment (all of it right of the diagonal): vector stores
@@ -591,7 +592,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
             float4* dst = reinterpret_cast<float4*>(Xo + e0);
 #pragma unroll
             for (int q = 0; q < 4; ++q) dst[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
-            if (!XBAR16) store_operand_row<KIND, NPROD, 16>(ohi, olo, p.off + e0, x);
+            if (XBAR16) {
+              float xs[16];
+#pragma unroll
+              for (int j = 0; j < 16; ++j) xs[j] = x[j] * osc;
+              store_operand_row<KIND, NPROD, 16>(ohi, olo, p.off + e0, xs);
+            } else {
+              store_operand_row<KIND, NPROD, 16>(ohi, olo, p.off + e0, x);
+            }
           }
         }
       } else {
@@ -631,15 +639,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
     if (MODE != TC_STEP) a.ctl.st->status = ST_TIMEOUT;  // no step bookkeeping follows
   }
   if (XBAR16 && last_block_ticket(&a.ctl.st->counter)) {
-    // each part's new scale: the smallest sig with 2^sig > max |Xbar_new| (0 for a zero or a
-    // non-finite Xbar, whose operands carry the NaN or Inf on), clamped to the FP32 range the
-    // scalings stay exact in; the maxima are cleared for the next step
+    // the scales move on: the next step reads the operands written at xb_sig[nparts + k] and
+    // writes at 2^e (the smallest power of two above max |Xbar_new|; e = 0 for a zero or a
+    // non-finite Xbar, whose operands carry the NaN or Inf on) times the headroom, clamped to
+    // the range the FP32 scalings stay exact in; the maxima are cleared for the next step
     for (int k = threadIdx.x; k < a.nparts; k += blockDim.x) {
       const uint32_t mb = __ldcg(&a.xb_max[k]);
       a.xb_max[k] = 0u;
       int e = 0;
       if (mb != 0u && mb < 0x7F800000u) (void)frexpf(__uint_as_float(mb), &e);
-      a.xb_sig[k] = e < TC_SIG_MIN ? TC_SIG_MIN : (e > TC_SIG_MAX ? TC_SIG_MAX : e);
+      e += a.xb_headroom;
+      a.xb_sig[k] = a.xb_sig[a.nparts + k];
+      a.xb_sig[a.nparts + k] = e < TC_SIG_MIN ? TC_SIG_MIN : (e > TC_SIG_MAX ? TC_SIG_MAX : e);
     }
     if (threadIdx.x == 0) a.ctl.st->counter = 0;
   }
@@ -977,28 +988,13 @@ cudaError_t launch_tc_adjoint(const TcStepArgs& a, int grid, bool rebuild, cudaS
 }
 
 // FP16 hi + lo operands of an FP32 arena, one warp per column up to ld: of x 2^-sig[part]
-// (the FP16 adjoint's Xbar; sig NULL: of x, an iterate), from x0 into (hi0, lo0).  With
-// `after`, the arena is Xbar after reverse step `step` (resolved as in the adjoint kernels:
-// step <= 0 counts back from n, loop steps above n - tail were not run), whose source and
-// destination follow the step parity; otherwise the call is skipped where need > n - tail.
+// (the FP16 adjoint's seed Xbar; sig NULL: of x, an iterate).  Skipped where need > n - tail
+// (a checkpoint the reverse sweep does not reach).
 __global__ void __launch_bounds__(256) split_f16_kernel(const PartDesc* __restrict__ parts,
-                                                        const ColBlock* __restrict__ blocks, const float* x0,
-                                                        const float* x1, uint16_t* hi0, uint16_t* lo0, uint16_t* hi1,
-                                                        uint16_t* lo1, const int32_t* __restrict__ sig, int after,
-                                                        int step, int need, int tail, const DevState* st) {
-  const int n = *(volatile const int32_t*)&st->steps;
-  int buf = 0;
-  if (after) {  // Xbar after reverse step `step` lies in buffer (n - step + 1) & 1
-    if (step <= 0) step += n;
-    else if (step > n - tail) return;
-    if (step < 1) return;
-    buf = (n - step + 1) & 1;
-  } else if (need > n - tail) {
-    return;
-  }
-  const float* x = buf ? x1 : x0;
-  uint16_t* hi = buf ? hi1 : hi0;
-  uint16_t* lo = buf ? lo1 : lo0;
+                                                        const ColBlock* __restrict__ blocks, const float* x,
+                                                        uint16_t* hi, uint16_t* lo, const int32_t* __restrict__ sig,
+                                                        int need, int tail, const DevState* st) {
+  if (need > *(volatile const int32_t*)&st->steps - tail) return;
   const ColBlock b = blocks[blockIdx.x];
   const PartDesc p = parts[b.part];
   const int lane = threadIdx.x & 31;
@@ -1009,12 +1005,14 @@ __global__ void __launch_bounds__(256) split_f16_kernel(const PartDesc* __restri
   for (int r = lane; r < p.ld; r += 32) store_operands<2, 3>(hi, lo, cbase + r, x[cbase + r] * f);
 }
 
-// Scale of the seed Xbar for its FP16 operands: each part's largest |x| into xb_max (one
-// warp per column), then, in the last block, the parts' scale exponents (maxima cleared).
+// Scales of the seed Xbar's FP16 operands: each part's largest |x| into xb_max (one warp
+// per column), then, in the last block, the exponent its operands are written at
+// (xb_sig[k]) and the one the first reverse step writes at (xb_sig[nparts + k], with the
+// headroom); maxima cleared.
 __global__ void __launch_bounds__(256) xbar_seed_scale_kernel(const PartDesc* __restrict__ parts,
                                                               const ColBlock* __restrict__ blocks, const float* x,
                                                               uint32_t* xb_max, int32_t* xb_sig, int nparts,
-                                                              DevState* st) {
+                                                              int headroom, DevState* st) {
   const ColBlock b = blocks[blockIdx.x];
   const PartDesc p = parts[b.part];
   const int lane = threadIdx.x & 31;
@@ -1031,24 +1029,26 @@ __global__ void __launch_bounds__(256) xbar_seed_scale_kernel(const PartDesc* __
       xb_max[k] = 0u;
       int e = 0;
       if (mb != 0u && mb < 0x7F800000u) (void)frexpf(__uint_as_float(mb), &e);
+      const int e2 = e + headroom;
       xb_sig[k] = e < TC_SIG_MIN ? TC_SIG_MIN : (e > TC_SIG_MAX ? TC_SIG_MAX : e);
+      xb_sig[nparts + k] = e2 < TC_SIG_MIN ? TC_SIG_MIN : (e2 > TC_SIG_MAX ? TC_SIG_MAX : e2);
     }
     if (threadIdx.x == 0) st->counter = 0;
   }
 }
 
-cudaError_t launch_split_f16(const PartDesc* parts, const ColBlock* blocks, int nblocks, const float* x0,
-                             const float* x1, void* hi0, void* lo0, void* hi1, void* lo1, const int32_t* sig, int after,
-                             int step, int need, int tail, const DevState* st, cudaStream_t s) {
-  split_f16_kernel<<<nblocks, 32 * COLS_PER_BLOCK, 0, s>>>(parts, blocks, x0, x1, (uint16_t*)hi0, (uint16_t*)lo0,
-                                                            (uint16_t*)hi1, (uint16_t*)lo1, sig, after, step, need,
+cudaError_t launch_split_f16(const PartDesc* parts, const ColBlock* blocks, int nblocks, const float* x, void* hi,
+                             void* lo, const int32_t* sig, int need, int tail, const DevState* st, cudaStream_t s) {
+  split_f16_kernel<<<nblocks, 32 * COLS_PER_BLOCK, 0, s>>>(parts, blocks, x, (uint16_t*)hi, (uint16_t*)lo, sig, need,
                                                             tail, st);
   return cudaGetLastError();
 }
 
 cudaError_t launch_xbar_seed_scale(const PartDesc* parts, const ColBlock* blocks, int nblocks, const float* x,
-                                   uint32_t* xb_max, int32_t* xb_sig, int nparts, DevState* st, cudaStream_t s) {
-  xbar_seed_scale_kernel<<<nblocks, 32 * COLS_PER_BLOCK, 0, s>>>(parts, blocks, x, xb_max, xb_sig, nparts, st);
+                                   uint32_t* xb_max, int32_t* xb_sig, int nparts, int headroom, DevState* st,
+                                   cudaStream_t s) {
+  xbar_seed_scale_kernel<<<nblocks, 32 * COLS_PER_BLOCK, 0, s>>>(parts, blocks, x, xb_max, xb_sig, nparts, headroom,
+                                                                  st);
   return cudaGetLastError();
 }
 
