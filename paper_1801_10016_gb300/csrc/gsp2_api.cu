@@ -29,6 +29,7 @@ struct WsLayout {
   size_t op_hi[2];     // operand arenas (BF16 or TF32), ping-pong
   size_t op_lo[2];     // split-mode low parts
   size_t maps;         // CUtensorMap[2 buffers][hi, lo][nparts]
+  size_t maps_mn;      // 16-bit kinds: the same with MN-major boxes (upper tiles only kept)
   size_t master_of_step;
   size_t d[2];         // FP64 arenas of the tail steps
   // FP64 products from BF16 digits
@@ -48,6 +49,7 @@ struct WsLayout {
   // per-part scale exponents and maxima
   std::vector<size_t> aop;
   size_t aop_maps;                // CUtensorMap[2 (S + 2)][nparts]
+  size_t aop_maps_mn;             // the same, MN-major boxes
   size_t xb_sig, xb_max;          // int32[2][nparts] (scales read, written), uint32[nparts]
   size_t mask;                    // uint8[nnz_p]: |P| > tau flags of gsp2_threshold_graph
   std::vector<size_t> tailf;      // low-precision adjoint: FP32 iterates of the FP64 tail, recomputed
@@ -269,7 +271,7 @@ static void build_layout(gsp2_plan* h) {
     L.seg.clear();
     L.tailf.clear();
     L.aop.clear();
-    L.xb0 = L.xb1 = L.aop_maps = L.xb_sig = L.xb_max = 0;
+    L.xb0 = L.xb1 = L.aop_maps = L.aop_maps_mn = L.xb_sig = L.xb_max = 0;
     if (k > 0) {
       for (int c = 0; c <= h->opt.max_steps / k; ++c) L.ckpt.push_back(take(af));
       for (int j = 1; j < k; ++j) L.seg.push_back(take(af));
@@ -279,6 +281,7 @@ static void build_layout(gsp2_plan* h) {
       const int nsets = std::max(k, h->opt.fp64_tail_steps);
       for (int q = 0; q < 2 * nsets; ++q) L.aop.push_back(take((size_t)h->arena_elems * 2));
       L.aop_maps = take((size_t)2 * (nsets + 2) * h->parts.size() * 128);
+      L.aop_maps_mn = take((size_t)2 * (nsets + 2) * h->parts.size() * 128);
       L.xb_sig = take(2 * h->parts.size() * sizeof(int32_t));
       L.xb_max = take(h->parts.size() * sizeof(uint32_t));
     }
@@ -296,6 +299,7 @@ static void build_layout(gsp2_plan* h) {
         L.op_lo[1] = take((size_t)h->arena_elems * es);
       }
       L.maps = take(4 * h->parts.size() * 128);
+      L.maps_mn = kind == 1 ? 0 : take(4 * h->parts.size() * 128);
     }
     L.d[0] = take(ab);
     L.d[1] = take(ab);
@@ -722,16 +726,20 @@ extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t byt
       if (!enc || q != cudaDriverEntryPointSuccess)
         return fail(h, GSP2_E_CUDA, "cuTensorMapEncodeTiled not available from the driver");
       const size_t np = h->parts.size();
-      std::vector<unsigned char> maps(4 * np * 128, 0);
-      for (int b = 0; b < 2; ++b) {
-        int r = encode_part_maps(enc, maps.data() + (size_t)(2 * b + 0) * np * 128, h->parts.data(), (int)np,
-                                 h->ws + L.op_hi[b], kind);
-        if (r == 0 && nprod == 3)
-          r = encode_part_maps(enc, maps.data() + (size_t)(2 * b + 1) * np * 128, h->parts.data(), (int)np,
-                               h->ws + L.op_lo[b], kind);
-        if (r != 0) return fail(h, GSP2_E_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string(r));
-      }
+      std::vector<unsigned char> maps(4 * np * 128, 0), maps_mn(maps.size(), 0);
+      // K-major boxes (one 128-byte row of K by 128 rows); for the 16-bit kinds also MN-major
+      // boxes (64 rows of 128 bytes by one K block of 64 elements)
+      for (int b = 0; b < 2; ++b)
+        for (int q = 0; q < (nprod == 3 ? 2 : 1); ++q) {
+          void* arena = h->ws + (q ? L.op_lo[b] : L.op_hi[b]);
+          const size_t at = (size_t)(2 * b + q) * np * 128;
+          int r = encode_part_maps(enc, maps.data() + at, h->parts.data(), (int)np, arena, kind);
+          if (r == 0 && L.maps_mn) r = encode_part_maps(enc, maps_mn.data() + at, h->parts.data(), (int)np, arena, kind,
+                                                        128, 64);
+          if (r != 0) return fail(h, GSP2_E_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string(r));
+        }
       CU(h, up(L.maps, maps.data(), maps.size()));
+      if (L.maps_mn) CU(h, up(L.maps_mn, maps_mn.data(), maps_mn.size()));
     }
     {
       // every iterate and operand arena starts zeroed, so that the padding no step writes
@@ -763,12 +771,16 @@ extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t byt
       if (!enc || q != cudaDriverEntryPointSuccess)
         return fail(h, GSP2_E_CUDA, "cuTensorMapEncodeTiled not available from the driver");
       const size_t np = h->parts.size();
-      std::vector<unsigned char> amaps(L.aop.size() * np * 128, 0);
+      std::vector<unsigned char> amaps(L.aop.size() * np * 128, 0), amaps_mn(amaps.size(), 0);
       for (size_t i = 0; i < L.aop.size(); ++i) {
-        const int r = encode_part_maps(enc, amaps.data() + i * np * 128, h->parts.data(), (int)np, h->ws + L.aop[i], 2);
+        int r = encode_part_maps(enc, amaps.data() + i * np * 128, h->parts.data(), (int)np, h->ws + L.aop[i], 2);
+        if (r == 0)
+          r = encode_part_maps(enc, amaps_mn.data() + i * np * 128, h->parts.data(), (int)np, h->ws + L.aop[i], 2, 128,
+                               64);
         if (r != 0) return fail(h, GSP2_E_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string(r));
       }
       CU(h, up(L.aop_maps, amaps.data(), amaps.size()));
+      CU(h, up(L.aop_maps_mn, amaps_mn.data(), amaps_mn.size()));
     }
   }
   CU(h, up(L.gblocks, h->gblocks.data(), h->gblocks.size() * sizeof(ColBlock)));
@@ -863,6 +875,10 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
       for (int b = 0; b < 2; ++b) {
         tc_args.map_hi[b] = w + L.maps + (size_t)(2 * b + 0) * np * 128;
         tc_args.map_lo[b] = w + L.maps + (size_t)(2 * b + 1) * np * 128;
+        if (L.maps_mn) {
+          tc_args.map_mn_hi[b] = w + L.maps_mn + (size_t)(2 * b + 0) * np * 128;
+          tc_args.map_mn_lo[b] = w + L.maps_mn + (size_t)(2 * b + 1) * np * 128;
+        }
         tc_args.master[b] = mf[b];
         tc_args.op_hi[b] = oh[b];
         tc_args.op_lo[b] = nprod == 3 ? ol[b] : nullptr;
@@ -898,6 +914,11 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
     double* d[2] = {(double*)(w + L.d[0]), (double*)(w + L.d[1])};
     CU(h, launch_convert((const float* const*)(w + L.master_of_step), d[0], h->arena_elems, st, s));
     const int T = h->opt.fp64_tail_steps;
+    // the persistent kernel of the 16-bit kinds keeps upper tiles only: the native FP64 tail
+    // reads whole 64-tiles, so it gets the lower ones first
+    const bool lp_upper = kind == 0 || kind == 2;
+    if (lp_upper && T > 0 && !h->use_oz)
+      CU(h, launch_symmetrize(parts, (const Tile*)(w + L.tc_tiles), (int)h->tc_tiles.size(), nullptr, d[0], st, s));
     OzStepArgs toz = oz_args(h, ctl);
     if (h->use_oz)
       CU(h, launch_oz_slice(parts, (const ColBlock*)(w + L.gblocks_ld), (int)h->gblocks_ld.size(), d[0], toz.digits,
@@ -914,8 +935,8 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
         CU(h, launch_square_fp64(parts, tiles, (int)h->tiles.size(), d[t & 1], d[(t + 1) & 1], slots, h->nslots, ctl,
                                  0, tmode, s));
     }
-    // emulated tail steps leave the upper 128-tiles only
-    const int ub = (h->use_oz && T > 0) ? TC_TILE : 0;
+    // emulated tail steps, and the 16-bit steps without a tail, leave the upper 128-tiles only
+    const int ub = ((h->use_oz && T > 0) || (lp_upper && T == 0)) ? TC_TILE : 0;
     CU(h, launch_scatter(parts, sbl, (int)h->sblocks.size(), Sall, perm, pcol, nullptr, d[T & 1], pv, st, s, ub));
     if (h->opt.report_idem) {
       if (ub) CU(h, launch_symmetrize(parts, (const Tile*)(w + L.tc_tiles), (int)h->tc_tiles.size(), nullptr, d[T & 1],
@@ -1398,6 +1419,9 @@ static gsp2_status enqueue_backward_lp(gsp2_plan* h, const double* pbar, double*
   auto tf = [&](int t) { return (float*)(w + L.tailf[(size_t)t]); };
   auto aop = [&](int set, int lo) { return (void*)(w + L.aop[(size_t)(2 * set + lo)]); };
   auto amap = [&](int set, int lo) { return (const void*)(w + L.aop_maps + (size_t)(2 * set + lo) * np * 128); };
+  auto amap_mn = [&](int set, int lo) {
+    return (const void*)(w + L.aop_maps_mn + (size_t)(2 * set + lo) * np * 128);
+  };
   TcStepArgs base{};
   base.parts = parts;
   base.tiles = (const Tile*)(w + L.tc_tiles);
@@ -1415,6 +1439,8 @@ static gsp2_status enqueue_backward_lp(gsp2_plan* h, const double* pbar, double*
   for (int b = 0; b < 2; ++b) {
     base.map_hi[b] = amap(nsets + b, 0);
     base.map_lo[b] = amap(nsets + b, 1);
+    base.map_mn_hi[b] = amap_mn(nsets + b, 0);
+    base.map_mn_lo[b] = amap_mn(nsets + b, 1);
     base.master[b] = b ? xb1 : xb0;
     base.op_hi[b] = aop(nsets + b, 0);
     base.op_lo[b] = aop(nsets + b, 1);
@@ -1428,6 +1454,8 @@ static gsp2_status enqueue_backward_lp(gsp2_plan* h, const double* pbar, double*
     TcStepArgs a = base;
     a.xmap_hi = amap(in, 0);
     a.xmap_lo = amap(in, 1);
+    a.xmap_mn_hi = amap_mn(in, 0);
+    a.xmap_mn_lo = amap_mn(in, 1);
     a.xin = xin;
     a.xout = xout;
     a.xo_hi = aop(out, 0);
@@ -1440,6 +1468,8 @@ static gsp2_status enqueue_backward_lp(gsp2_plan* h, const double* pbar, double*
     TcStepArgs a = base;
     a.xmap_hi = amap(x, 0);
     a.xmap_lo = amap(x, 1);
+    a.xmap_mn_hi = amap_mn(x, 0);
+    a.xmap_mn_lo = amap_mn(x, 1);
     a.step = step;
     return launch_tc_adjoint(a, h->num_sms, false, s);
   };
@@ -1468,7 +1498,7 @@ static gsp2_status enqueue_backward_lp(gsp2_plan* h, const double* pbar, double*
   }
   CU(h, launch_adj_hbar<float>(h->n, (const int64_t*)(w + L.rowptr), (const int32_t*)(w + L.colind),
                                (const int64_t*)(w + L.memptr), (const int32_t*)(w + L.mempart),
-                               (const int32_t*)(w + L.memloc), parts, Sall, xb0, xb1, hbar, st, s));
+                               (const int32_t*)(w + L.memloc), parts, Sall, xb0, xb1, hbar, st, s, TC_TILE));
   CU(h, cudaMemsetAsync(w + L.d[0], 0, ab, s));
   CU(h, cudaMemsetAsync(w + L.d[1], 0, ab, s));
   return GSP2_OK;

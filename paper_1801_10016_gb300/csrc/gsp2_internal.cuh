@@ -79,6 +79,11 @@ struct TcStepArgs {
   const int8_t* nb;        // wide tiles: 128-column blocks of each tile (1 or 2); NULL: 128x128 tiles
   const void* map_hi[2];   // CUtensorMap[nparts] over each operand arena (hi part)
   const void* map_lo[2];   // CUtensorMap[nparts] over each lo arena (split mode)
+  // 16-bit kinds: the persistent kernel keeps only the tiles on or above the diagonal and
+  // reads the operand panels right of a tile's block MN-major from them (boxes of 64 rows
+  // by one K block), through these maps over the same arenas
+  const void* map_mn_hi[2];
+  const void* map_mn_lo[2];
   float* master[2];        // FP32 master copies of X
   void* op_hi[2];          // operand arenas
   void* op_lo[2];
@@ -97,6 +102,8 @@ struct TcStepArgs {
   // n - adj_tail are skipped.
   const void* xmap_hi;
   const void* xmap_lo;
+  const void* xmap_mn_hi;
+  const void* xmap_mn_lo;
   const float* xin;
   float* xout;
   void* xo_hi;

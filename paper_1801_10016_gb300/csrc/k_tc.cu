@@ -338,6 +338,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
   // the FP16 adjoint's reverse step: Xbar's operands carry a per-part scale (read at one,
   // written at the next) and the step records each part's largest |Xbar_new|
   constexpr bool XBAR16 = MODE == TC_ADJOINT && KIND == 2;
+  // 16-bit kinds keep only the tiles on or above the diagonal (diagonal tiles whole): an
+  // operand slice in a K block right of the tile's own block is read MN-major from the
+  // upper tile (two boxes of 64 rows, 8 KB apart, 128-byte swizzle, transpose bit)
+  constexpr bool UPPER = KIND != 1;
 
   int step = a.step;
   int n = 0;
@@ -414,6 +418,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
       const CUtensorMap* bhi =  // Xbar (adjoint)
           MODE == TC_ADJOINT ? reinterpret_cast<const CUtensorMap*>(a.map_hi[bi]) + t.part : nullptr;
       const CUtensorMap* blo = MODE == TC_ADJOINT ? reinterpret_cast<const CUtensorMap*>(a.map_lo[bi]) + t.part : nullptr;
+      // the same arenas through MN-major boxes (16-bit kinds)
+      const CUtensorMap* mhi_mn =
+          UPPER ? reinterpret_cast<const CUtensorMap*>(MODE == TC_STEP ? a.map_mn_hi[bi] : a.xmap_mn_hi) + t.part
+                : nullptr;
+      const CUtensorMap* mlo_mn =
+          UPPER ? reinterpret_cast<const CUtensorMap*>(MODE == TC_STEP ? a.map_mn_lo[bi] : a.xmap_mn_lo) + t.part
+                : nullptr;
+      const CUtensorMap* bhi_mn =
+          (UPPER && MODE == TC_ADJOINT) ? reinterpret_cast<const CUtensorMap*>(a.map_mn_hi[bi]) + t.part : nullptr;
+      const CUtensorMap* blo_mn =
+          (UPPER && MODE == TC_ADJOINT) ? reinterpret_cast<const CUtensorMap*>(a.map_mn_lo[bi]) + t.part : nullptr;
       // a diagonal tile of X X needs rows I only (B = A): two K blocks per stage
       const bool dg = MODE != TC_ADJOINT && t.ti == t.tj;
       const int sub = dg ? 2 : 1;
@@ -425,27 +440,37 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
           break;
         }
         mbar_expect_tx(full(s), STAGE_B);
+        // rows `blk` of the K block at k0: K-major from the tile (k block, blk) where it is on
+        // or above the diagonal, else (16-bit kinds) MN-major from the upper tile (blk, k block)
+        auto load = [&](uint32_t dst, const CUtensorMap* mk, const CUtensorMap* mm, int k0, int blk) {
+          if (UPPER && k0 / 128 > blk) {
+            tma_load_2d(dst, mm, blk * 128, k0, full(s));
+            tma_load_2d(dst + kTileBytes / 2, mm, blk * 128 + 64, k0, full(s));
+          } else {
+            tma_load_2d(dst, mk, k0, blk * 128, full(s));
+          }
+        };
         if (MODE == TC_ADJOINT) {
           // first nk blocks: Xbar (rows I) times X (rows J); then X (rows I) times Xbar (rows J)
           const bool h2 = kb >= nk;
           const int k0 = (h2 ? kb - nk : kb) * BKE;
-          tma_load_2d(tile_addr(s, 0), h2 ? mhi : bhi, k0, t.ti * 128, full(s));
-          tma_load_2d(tile_addr(s, 1), h2 ? bhi : mhi, k0, t.tj * 128, full(s));
-          tma_load_2d(tile_addr(s, 2), h2 ? mlo : blo, k0, t.ti * 128, full(s));
-          tma_load_2d(tile_addr(s, 3), h2 ? blo : mlo, k0, t.tj * 128, full(s));
+          load(tile_addr(s, 0), h2 ? mhi : bhi, h2 ? mhi_mn : bhi_mn, k0, t.ti);
+          load(tile_addr(s, 1), h2 ? bhi : mhi, h2 ? bhi_mn : mhi_mn, k0, t.tj);
+          load(tile_addr(s, 2), h2 ? mlo : blo, h2 ? mlo_mn : blo_mn, k0, t.ti);
+          load(tile_addr(s, 3), h2 ? blo : mlo, h2 ? blo_mn : mlo_mn, k0, t.tj);
         } else if (dg) {
           for (int u = 0; u < 2; ++u) {
             const int k0 = (2 * kb + u) * BKE;
-            tma_load_2d(tile_addr(s, u * (NOPS / 2)), mhi, k0, t.ti * 128, full(s));
-            if (NPROD == 3) tma_load_2d(tile_addr(s, u * 2 + 1), mlo, k0, t.ti * 128, full(s));
+            load(tile_addr(s, u * (NOPS / 2)), mhi, mhi_mn, k0, t.ti);
+            if (NPROD == 3) load(tile_addr(s, u * 2 + 1), mlo, mlo_mn, k0, t.ti);
           }
         } else {
           const int k0 = kb * BKE;
-          tma_load_2d(tile_addr(s, 0), mhi, k0, t.ti * 128, full(s));
-          tma_load_2d(tile_addr(s, 1), mhi, k0, t.tj * 128, full(s));
+          load(tile_addr(s, 0), mhi, mhi_mn, k0, t.ti);
+          load(tile_addr(s, 1), mhi, mhi_mn, k0, t.tj);
           if (NPROD == 3) {
-            tma_load_2d(tile_addr(s, 2), mlo, k0, t.ti * 128, full(s));
-            tma_load_2d(tile_addr(s, 3), mlo, k0, t.tj * 128, full(s));
+            load(tile_addr(s, 2), mlo, mlo_mn, k0, t.ti);
+            load(tile_addr(s, 3), mlo, mlo_mn, k0, t.tj);
           }
         }
       }
@@ -482,23 +507,35 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
         }
         tc_fence_after();
         for (int v = 0; v < (dg ? 2 : 1); ++v) {  // K blocks of the stage, in K order
+          // the K block and how each operand came in (MN-major right of the tile's block)
+          const int kq = dg ? 2 * kb + v : (MODE == TC_ADJOINT && kb >= nk / 2 ? kb - nk / 2 : kb);
+          const int kt = kq * BKE / 128;
+          const bool amn = UPPER && kt > t.ti, bmn = UPPER && kt > t.tj;
+          auto desc = [&](uint32_t addr, bool mn) {
+            return mn ? smem_desc_mn128(addr, kTileBytes / 2) : smem_desc(addr);
+          };
           uint64_t ah, bh, al, bl;
           if (dg) {
-            ah = bh = smem_desc(tile_addr(s, v * (NOPS / 2)));
-            al = bl = smem_desc(tile_addr(s, v * 2 + 1));
+            ah = bh = desc(tile_addr(s, v * (NOPS / 2)), amn);
+            al = bl = desc(tile_addr(s, v * 2 + 1), amn);
           } else {
-            ah = smem_desc(tile_addr(s, 0));
-            bh = smem_desc(tile_addr(s, 1));
-            al = smem_desc(tile_addr(s, 2));
-            bl = smem_desc(tile_addr(s, 3));
+            ah = desc(tile_addr(s, 0), amn);
+            bh = desc(tile_addr(s, 1), bmn);
+            al = desc(tile_addr(s, 2), amn);
+            bl = desc(tile_addr(s, 3), bmn);
           }
+          // a K = KMMA step advances KMMA elements along a K-major row, KMMA rows of 128 B
+          // (64 MN elements) in an MN-major box
+          const uint32_t adv_a = amn ? (uint32_t)(KMMA * 128) >> 4 : (uint32_t)(KMMA * ES) >> 4;
+          const uint32_t adv_b = (dg ? amn : bmn) ? (uint32_t)(KMMA * 128) >> 4 : (uint32_t)(KMMA * ES) >> 4;
+          const uint32_t idesc = IDESC | ((amn ? 1u : 0u) << 15) | (((dg ? amn : bmn) ? 1u : 0u) << 16);
 #pragma unroll
           for (int kk = 0; kk < NMMA; ++kk) {
-            const uint64_t adv = (uint64_t)((kk * KMMA * ES) >> 4);
-            mma<KIND>(d, ah + adv, bh + adv, IDESC, (kb > 0 || v > 0 || kk > 0) ? 1u : 0u);
+            const uint64_t aa = (uint64_t)(adv_a * kk), ab = (uint64_t)(adv_b * kk);
+            mma<KIND>(d, ah + aa, bh + ab, idesc, (kb > 0 || v > 0 || kk > 0) ? 1u : 0u);
             if (NPROD == 3) {
-              mma<KIND>(d, ah + adv, bl + adv, IDESC, 1u);
-              mma<KIND>(d, al + adv, bh + adv, IDESC, 1u);
+              mma<KIND>(d, ah + aa, bl + ab, idesc, 1u);
+              mma<KIND>(d, al + aa, bh + ab, idesc, 1u);
             }
           }
         }
@@ -586,8 +623,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
               Xo[e] = x[j];
               store_operands<KIND, NPROD>(ohi, olo, p.off + e, XBAR16 ? x[j] * osc : x[j]);
             }
-          } else {
-            // the mirrored row segment (all of it right of the diagonal): vector stores
+          } else if (!UPPER || t.ti == t.tj) {
+            // the mirrored row segment (all of it right of the diagonal): vector stores (the
+            // 16-bit kinds keep off-diagonal tiles upper only and mirror diagonal tiles only)
             const int64_t e0 = (int64_t)r * ld + cbase;
             float4* dst = reinterpret_cast<float4*>(Xo + e0);
 #pragma unroll
