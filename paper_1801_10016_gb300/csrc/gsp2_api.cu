@@ -860,14 +860,17 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
     auto mfs = [&](int i) { return (float*)(w + h->mf_of_step[(size_t)i]); };
     void* oh[2] = {w + L.op_hi[0], w + L.op_hi[1]};
     void* ol[2] = {w + L.op_lo[0], w + L.op_lo[1]};
-    CU(h, launch_gather_lp(kind, nprod, parts, (const ColBlock*)(w + L.gblocks_ld), (int)h->gblocks_ld.size(), Sall,
-                           rp, ci, hv, mfs(0), kind >= 0 ? oh[0] : nullptr, nprod == 3 ? ol[0] : nullptr,
-                           (double*)slots, lp, s));
     const size_t np = h->parts.size();
     // tensor-core schedule: persistent (one CTA per SM, overlapped epilogue) or one CTA per tile
     const int pgrid = h->opt.tc_schedule == 0 ? h->num_sms : 0;
     TcStepArgs tc_args{};
     const bool wide = pgrid > 0 && h->opt.tile_shape == 1;
+    // the persistent 128x128 steps of the 16-bit kinds read the upper tiles only; the other
+    // schedules read whole columns
+    const bool upper_rows = (kind == 0 || kind == 2) && pgrid > 0 && !wide;
+    CU(h, launch_gather_lp(kind, nprod, parts, (const ColBlock*)(w + L.gblocks_ld), (int)h->gblocks_ld.size(), Sall,
+                           rp, ci, hv, mfs(0), kind >= 0 ? oh[0] : nullptr, nprod == 3 ? ol[0] : nullptr,
+                           (double*)slots, lp, s, upper_rows ? 1 : 0));
     if (kind >= 0) {
       tc_args.parts = parts;
       tc_args.tiles = (const Tile*)(w + (wide ? L.tc_wide : L.tc_tiles));

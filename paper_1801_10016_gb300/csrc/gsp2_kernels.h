@@ -34,7 +34,7 @@ cudaError_t launch_square_tc(int kind, int nprod, const TcStepArgs& a, int ntile
 cudaError_t launch_gather_lp(int kind, int nprod, const PartDesc* parts, const ColBlock* blocks, int nblocks,
                              const int32_t* Sall, const int64_t* rowptr, const int32_t* colind, const double* vals,
                              float* master, void* op_hi, void* op_lo, double* slots, const StepCtl& ctl,
-                             cudaStream_t s);
+                             cudaStream_t s, int upper_rows = 0);
 // FP32 adjoint of the low-precision plans on the tensor cores (FP16 hi + lo operands)
 cudaError_t launch_tc_adjoint(const TcStepArgs& a, int grid, bool rebuild, cudaStream_t s);
 cudaError_t launch_split_f16(const PartDesc* parts, const ColBlock* blocks, int nblocks, const float* x, void* hi,

@@ -1131,9 +1131,12 @@ cudaError_t launch_square_tc(int kind, int nprod, const TcStepArgs& a, int ntile
 }
 
 // Gather + Eq. 1 for the low-precision paths: like the FP64 gather, but X0 is stored
-// as the FP32 master copy and, for the tensor-core kinds, as the rounded operand(s);
-// every column of the padded part (up to ld) is written.  T_0 is summed in FP64 from
-// the stored FP32 values.  KIND = -1: FP32 master only (CUDA-core FP32 path).
+// as the FP32 master copy and, for the tensor-core kinds, as the rounded operand(s): the
+// warp assembles its column of the master (zeros, then the stored entries), then writes the
+// operands from it, coalesced.  Every column of the padded part (up to ld) is written, all
+// its rows, or with `upper_rows` only those on or above its diagonal block (the upper-only
+// 16-bit steps read no others).  T_0 is summed in FP64 from the stored FP32 values.
+// KIND = -1: FP32 master only (CUDA-core FP32 path).
 template <int KIND, int NPROD>
 __global__ void __launch_bounds__(256) gather_lp_kernel(const PartDesc* __restrict__ parts,
                                                         const ColBlock* __restrict__ blocks,
@@ -1142,7 +1145,7 @@ __global__ void __launch_bounds__(256) gather_lp_kernel(const PartDesc* __restri
                                                         const int32_t* __restrict__ colind,
                                                         const double* __restrict__ vals, float* __restrict__ master,
                                                         void* op_hi, void* op_lo, double* __restrict__ slots,
-                                                        StepCtl ctl) {
+                                                        StepCtl ctl, int upper_rows) {
   const ColBlock b = blocks[blockIdx.x];
   const PartDesc p = parts[b.part];
   const int lane = threadIdx.x & 31;
@@ -1153,23 +1156,26 @@ __global__ void __launch_bounds__(256) gather_lp_kernel(const PartDesc* __restri
   double tr = 0.0;
   if (j < p.ld) {
     const int64_t cbase = p.off + (int64_t)j * p.ld;
-    for (int r = lane; r < p.ld; r += 32) {
-      master[cbase + r] = 0.0f;
-      if (KIND >= 0) store_operands<(KIND < 0 ? 0 : KIND), NPROD>(op_hi, op_lo, cbase + r, 0.0f);
-    }
+    const int rend = upper_rows ? min(p.ld, (j / 128 + 1) * 128) : p.ld;
+    float* col = master + cbase;
+    for (int r = lane; r < rend; r += 32) col[r] = 0.0f;
     __syncwarp();
     if (j < p.s) {
       const int32_t g = S[j];
       for (int64_t q = rowptr[g] + lane; q < rowptr[g + 1]; q += 32) {
         const int a = find_local(S, p.c, p.s, colind[q]);
-        if (a >= 0) {
+        if (a >= 0 && a < rend) {
           const double x = (a == j) ? (emax - vals[q]) / den : (0.0 - vals[q]) / den;
           const float xf = (float)x;
-          master[cbase + a] = xf;
-          if (KIND >= 0) store_operands<(KIND < 0 ? 0 : KIND), NPROD>(op_hi, op_lo, cbase + a, xf);
+          col[a] = xf;
           if (a == j && j < p.c) tr = (double)xf;
         }
       }
+    }
+    if (KIND >= 0) {
+      __syncwarp();  // the lanes' stores to the column are visible to the whole warp
+      for (int r = lane; r < rend; r += 32)
+        store_operands<(KIND < 0 ? 0 : KIND), NPROD>(op_hi, op_lo, cbase + r, col[r]);
     }
   }
   const double2 t = block_sum2(tr, 0.0);
@@ -1189,20 +1195,26 @@ __global__ void __launch_bounds__(256) gather_lp_kernel(const PartDesc* __restri
 cudaError_t launch_gather_lp(int kind, int nprod, const PartDesc* parts, const ColBlock* blocks, int nblocks,
                              const int32_t* Sall, const int64_t* rowptr, const int32_t* colind, const double* vals,
                              float* master, void* op_hi, void* op_lo, double* slots, const StepCtl& ctl,
-                             cudaStream_t s) {
+                             cudaStream_t s, int upper_rows) {
   const dim3 g(nblocks), b(32 * COLS_PER_BLOCK);
   if (kind < 0)
-    gather_lp_kernel<-1, 1><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, colind, vals, master, op_hi, op_lo, slots, ctl);
+    gather_lp_kernel<-1, 1><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, colind, vals, master, op_hi, op_lo,
+                                            slots, ctl, upper_rows);
   else if (kind == 0 && nprod == 1)
-    gather_lp_kernel<0, 1><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, colind, vals, master, op_hi, op_lo, slots, ctl);
+    gather_lp_kernel<0, 1><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, colind, vals, master, op_hi, op_lo,
+                                           slots, ctl, upper_rows);
   else if (kind == 0 && nprod == 3)
-    gather_lp_kernel<0, 3><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, colind, vals, master, op_hi, op_lo, slots, ctl);
+    gather_lp_kernel<0, 3><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, colind, vals, master, op_hi, op_lo,
+                                           slots, ctl, upper_rows);
   else if (kind == 1 && nprod == 1)
-    gather_lp_kernel<1, 1><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, colind, vals, master, op_hi, op_lo, slots, ctl);
+    gather_lp_kernel<1, 1><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, colind, vals, master, op_hi, op_lo,
+                                           slots, ctl, upper_rows);
   else if (kind == 1 && nprod == 3)
-    gather_lp_kernel<1, 3><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, colind, vals, master, op_hi, op_lo, slots, ctl);
+    gather_lp_kernel<1, 3><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, colind, vals, master, op_hi, op_lo,
+                                           slots, ctl, upper_rows);
   else if (kind == 2 && nprod == 3)
-    gather_lp_kernel<2, 3><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, colind, vals, master, op_hi, op_lo, slots, ctl);
+    gather_lp_kernel<2, 3><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, colind, vals, master, op_hi, op_lo,
+                                           slots, ctl, upper_rows);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();
