@@ -221,10 +221,10 @@ __global__ void __launch_bounds__(256, 2) square_tc_kernel(TcStepArgs a) {
       float x[32];
 #pragma unroll
       for (int j = 0; j < 32; ++j) x[j] = Xi[(int64_t)(cbase + j) * ld + r];
-#pragma unroll
       // the one diagonal entry of this row segment, if any, picked out in FP32 and added in
       // FP64 once (an FP64 add in the unrolled loop would be issued for every element)
       float yd = 0.0f, zd = 0.0f;
+#pragma unroll
       for (int j = 0; j < 32; ++j) {
         const float y = __uint_as_float(v[j]) * Kind<KIND>::YSCALE;
         const float z = (al > 0) ? (2.0f * x[j] - y) : y;
