@@ -40,7 +40,7 @@ def test_tile_orders_give_bitwise_equal_p(g, prec):
     assert np.array_equal(p0, p1)
 
 
-@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "tf32", "bf16"])
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "tf32", "bf16", "fp16x3"])
 def test_tile_shapes_give_bitwise_equal_p(g, prec):
     """128 x 256 work items (two upper tiles per N = 256 MMA) compute every element as the
     128 x 128 tiles do."""
@@ -51,13 +51,13 @@ def test_tile_shapes_give_bitwise_equal_p(g, prec):
     assert np.array_equal(p0, p1) and np.array_equal(p0, p2)
 
 
-@pytest.mark.parametrize("prec", ["tf32x3", "fp64e", "fp64"])
+@pytest.mark.parametrize("prec", ["tf32x3", "fp16x3", "fp64e", "fp64"])
 def test_autotune_keeps_a_timed_candidate(g, prec):
     s = make_workload("tb4k")
     plan, h, p0 = run(g, s, precision=prec)
     rep = plan.autotune(h, trials=2)
     cands = rep["candidates"]
-    assert len(cands) == {"tf32x3": 5, "fp64e": 2, "fp64": 1}[prec]
+    assert len(cands) == {"tf32x3": 5, "fp16x3": 5, "fp64e": 2, "fp64": 1}[prec]
     assert all(c["ms"] > 0 for c in cands)
     best = cands[rep["chosen"]]
     assert best["ms"] == min(c["ms"] for c in cands)

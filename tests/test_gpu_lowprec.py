@@ -150,11 +150,13 @@ def test_split_precisions_meet_the_gates_against_the_oracle_with_the_same_tail(g
     assert 0.0 <= idem <= 1e-8, idem
 
 
-def test_emulated_and_native_fp64_tail_agree(g):
+@pytest.mark.parametrize("prec", ["tf32x3", "fp16x3"])
+def test_emulated_and_native_fp64_tail_agree(g, prec):
     """The FP64 tail steps of a low-precision run, with the products on the FP64 units or
-    rebuilt from BF16 digits, give the same P to FP64 accuracy."""
+    rebuilt from BF16 digits, give the same P to FP64 accuracy (fp16x3 keeps upper tiles
+    only, which the native tail gets mirrored first)."""
     s = make_workload("tb512")
-    _, pe, he = run(g, s, "tf32x3", fp64_tail_steps=2, fp64_tail_emulated=1)
-    _, pn, hn = run(g, s, "tf32x3", fp64_tail_steps=2, fp64_tail_emulated=0)
+    _, pe, he = run(g, s, prec, fp64_tail_steps=2, fp64_tail_emulated=1)
+    _, pn, hn = run(g, s, prec, fp64_tail_steps=2, fp64_tail_emulated=0)
     assert he["alphas"] == hn["alphas"] and he["report"]["fp64_steps"] == 2
     assert float(np.max(np.abs(pe - pn))) <= 1e-12
