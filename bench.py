@@ -228,6 +228,47 @@ def fp64_roofline(precision, sizes, avg_launch_ms, peaks, src, workload):
             "flops": "algorithmic s^2 (s+1) per part (upper triangle of X^2)"}
 
 
+FP32_LANES_PER_SM, SMS, SM_MAX_GHZ = 128, 152, 2.07  # CUDA-core FP32 peak: lanes x SMs x 2 (FMA) x clock
+
+
+def step_roofline(precision, sizes, avg_launch_ms, peaks, src, workload, sched=None):
+    """Roofline of one purification step in any precision: the FP64-result steps as above;
+    the tensor-core steps against the dense rate of their operand type (TF32, or the 16-bit
+    rate BF16 and FP16 share), in algorithmic flops s^2 (s+1) per part and product, executed
+    flops (128-tile padding, K rounded to the stage) beside them; FP32 on the CUDA cores
+    against FP32 lanes x SMs x 2 x the maximum clock."""
+    if precision in ("fp64", "fp64e"):
+        return fp64_roofline(precision, sizes, avg_launch_ms, peaks, src, workload)
+    t = avg_launch_ms / 1e3
+    if precision == "fp32":
+        flops = alg_flops(sizes)
+        peak = FP32_LANES_PER_SM * SMS * 2 * SM_MAX_GHZ / 1e3
+        return {"bound": "alu", "achieved": flops / t / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "frac": flops / t / 1e12 / peak, "traffic": None, "kernel": "square_simt_kernel<float>",
+                "peak_source": f"derived: {FP32_LANES_PER_SM} FP32 lanes x {SMS} SMs x 2 x {SM_MAX_GHZ} GHz",
+                "avg_launch_ms": avg_launch_ms, "flops_per_launch": flops,
+                "flops": "algorithmic s^2 (s+1) per part (upper triangle of X^2)"}
+    nprod = 3 if precision.endswith("x3") else 1
+    kst = 32 if precision.startswith("tf32") else 64  # K per stage: 128-byte operand rows
+    flops = alg_flops(sizes, nprod)
+    # the persistent 128x128 kernel trims the last column block of each part (the per-tile
+    # and 128x256 kernels run whole tiles)
+    trim = sched is None or (sched["tc_schedule"] == 0 and sched["tile_shape"] == 0)
+    exe = tc_exec_flops(sizes, kst, nprod, trim=trim)
+    tf32 = precision.startswith("tf32")
+    peak = peaks["bf16_tflops"] * NOMINAL["tf32"] / NOMINAL["bf16"] if tf32 else peaks["bf16_tflops"]
+    kname = "tf32" if tf32 else ("fp16" if precision.startswith("fp16") else "bf16")
+    return {"bound": "tensor", "achieved": flops / t / 1e12, "peak": peak, "unit": "TFLOP/s",
+            "frac": flops / t / 1e12 / peak, "traffic": None,
+            "kernel": f"square_tc_persistent_kernel<{kname},{nprod}>",
+            "peak_source": (f"{src}: bf16 burst x nominal tf32/bf16 {NOMINAL['tf32']}/{NOMINAL['bf16']} (of measured)"
+                            if tf32 else f"{src}: bf16 burst (of measured; fp16 and bf16 share the 16-bit dense rate)"),
+            "avg_launch_ms": avg_launch_ms, "flops_per_launch": flops,
+            "flops": "algorithmic tensor flops per launch (s^2 (s+1) per part and product)",
+            "executed_flops_per_launch": exe, "executed_tflops": exe / t / 1e12,
+            "executed_frac": exe / t / 1e12 / peak}
+
+
 def kernels_per_build(precision, info, lp_tail=0, report_idem=0, emulated_tail=True):
     """Kernel launches of one density call (all launched, including the step launches that
     return at once after the stopping test)."""
@@ -433,7 +474,8 @@ def run_ours(args):
     sizes = plan.part_sizes.astype(np.float64)
     dgemm_equiv = 2.0 * float(np.sum(sizes ** 3))
     avg_launch_ms, work_ms = kernel_avg_ms(step_ms, steps_applied)
-    roof = fp64_roofline(args.precision, sizes, avg_launch_ms, peaks, src, args.workload)
+    sched = None if tune is None else tune["candidates"][tune["chosen"]]
+    roof = step_roofline(args.precision, sizes, avg_launch_ms, peaks, src, args.workload, sched)
     roof["share_of_step"] = work_ms / (sum(dev_ms) + 1e-30)
     launches_per_build = kernels_per_build(args.precision, plan.info)
     line = {
@@ -486,7 +528,6 @@ def run_ours(args):
     # ---- low-precision paths on the same workload, against the FP64 result
     if not args.no_mixed:
         mixed = {}
-        tf32_peak = peaks["bf16_tflops"] * NOMINAL["tf32"] / NOMINAL["bf16"]
         # FP64 with the same two alternating tail steps (untimed): the like-for-like reference
         # for the accuracy gates of the runs that end with two tail steps
         rp = GSP2(s.n, s.rowptr, s.colind, s.nocc, s.part, s.nparts, s.g_rowptr, s.g_colind, device=dev,
@@ -528,7 +569,6 @@ def run_ours(args):
             del ip
             torch.cuda.empty_cache()
             k_ms, _ = kernel_avg_ms(mstep, lp_steps)
-            nprod = 3 if prec.endswith("x3") else 1
             tail_total = lp_tail + fp_tail
             entry = {"value": 1.0 / t_build, "unit": UNIT, "ms_per_build": 1e3 * t_build,
                      "speedup_vs_fp64": (1.0 / t_build) / value, "lowprec_steps": int(lp_steps),
@@ -543,28 +583,8 @@ def run_ours(args):
                      "square_kernel_ms": k_ms,
                      "tflops_dgemm_equiv": dgemm_equiv * lp_steps / t_build / 1e12,
                      "schedule": None if mtune is None else mtune["candidates"][mtune["chosen"]]}
-            if prec != "fp32":
-                # algorithmic tensor flops of one launch (s^2 (s+1) per part and product) and the
-                # executed ones (every 128x128 upper tile, K rounded to the stage)
-                kst = 32 if prec.startswith("tf32") else 64  # K per stage: 128-byte operand rows
-                alg = alg_flops(sizes, nprod)
-                # the persistent 128x128 kernel trims the last column block of each part (the
-                # per-tile and 128x256 kernels run whole tiles)
-                sched = None if mtune is None else mtune["candidates"][mtune["chosen"]]
-                trim = sched is None or (sched["tc_schedule"] == 0 and sched["tile_shape"] == 0)
-                exec_flops = tc_exec_flops(sizes, kst, nprod, trim=trim)
-                ach = alg / (k_ms / 1e3) / 1e12
-                kname = "tf32" if "tf32" in prec else ("fp16" if "fp16" in prec else "bf16")
-                entry["roofline"] = {"bound": "tensor", "achieved": ach, "peak": tf32_peak if "tf32" in prec
-                                     else peaks["bf16_tflops"], "unit": "TFLOP/s",
-                                     "kernel": f"square_tc_persistent_kernel<{kname},{nprod}>",
-                                     "flops": "algorithmic tensor flops per launch (s^2 (s+1) per part and product)",
-                                     "executed_tflops": exec_flops / (k_ms / 1e3) / 1e12,
-                                     "peak_source": ("measured bf16 burst x nominal tf32/bf16 1100/2250 (of measured)"
-                                                     if "tf32" in prec else "measured bf16 burst (of measured; "
-                                                     "fp16 and bf16 share the 16-bit dense rate)")}
-                entry["roofline"]["frac"] = ach / entry["roofline"]["peak"]
-                entry["roofline"]["executed_frac"] = entry["roofline"]["executed_tflops"] / entry["roofline"]["peak"]
+            sched = None if mtune is None else mtune["candidates"][mtune["chosen"]]
+            entry["roofline"] = step_roofline(prec, sizes, k_ms, peaks, src, args.workload, sched)
             mixed[spec] = entry
         line["mixed"] = mixed
         line["mixed_note"] = ("max_abs_dP_vs_fp64: against the FP64-result path of `value` (the paper's method, no "
