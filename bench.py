@@ -492,7 +492,8 @@ def run_ours(args):
                    "parallelism": "replicas" if world > 1 else "single",
                    "adjoint_checkpoints": "off (forward P-builds only)",
                    "schedule": {"tc_schedule": int(plan.info.tc_schedule), "tile_order": int(plan.info.tile_order),
-                                "autotuned": tune is not None}},
+                                "autotuned": tune is not None,
+                                "candidates_ms_per_build": None if tune is None else tune["candidates"]}},
         "tflops_dgemm_equiv": dgemm_equiv * steps_applied / (ms_per_step / 1e3) / 1e12,
         "roofline": roof,
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(plan.nnz_h * 8),
