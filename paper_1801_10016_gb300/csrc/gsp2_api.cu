@@ -669,7 +669,8 @@ extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t byt
     if (!enc || q != cudaDriverEntryPointSuccess)
       return fail(h, GSP2_E_CUDA, "cuTensorMapEncodeTiled not available from the driver");
     const size_t np = h->parts.size();
-    // K-major boxes (OZ_BK rows of 128 columns) and MN-major boxes (64 rows of OZ_BK columns)
+    // K-major boxes (OZ_BK rows of 128 columns) and MN-major boxes (128 rows of OZ_BK columns
+    // as two 64-row atoms, one request)
     std::vector<unsigned char> maps((size_t)2 * OZ_SLICES * np * 128, 0), maps_mn(maps.size(), 0);
     for (int b = 0; b < 2; ++b)
       for (int t = 0; t < OZ_SLICES; ++t) {
@@ -677,8 +678,8 @@ extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t byt
         int r = encode_part_maps(enc, maps.data() + at, h->parts.data(), (int)np, h->ws + L.oz_slice[b][t], 0,
                                  2 * OZ_BK, 128);
         if (r == 0)
-          r = encode_part_maps(enc, maps_mn.data() + at, h->parts.data(), (int)np, h->ws + L.oz_slice[b][t], 0, 128,
-                               OZ_BK);
+          r = encode_part_maps_mn128(enc, maps_mn.data() + at, h->parts.data(), (int)np, h->ws + L.oz_slice[b][t],
+                                     OZ_BK);
         if (r != 0) return fail(h, GSP2_E_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string(r));
       }
     CU(h, up(L.oz_maps, maps.data(), maps.size()));
@@ -703,8 +704,8 @@ extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t byt
         int r = encode_part_maps(enc, amaps.data() + i * np * 128, h->parts.data(), (int)np, h->ws + L.adj_dig[i], 0,
                                  2 * OZ_BK, 128);
         if (r == 0)
-          r = encode_part_maps(enc, amaps_mn.data() + i * np * 128, h->parts.data(), (int)np, h->ws + L.adj_dig[i],
-                               0, 128, OZ_BK);
+          r = encode_part_maps_mn128(enc, amaps_mn.data() + i * np * 128, h->parts.data(), (int)np,
+                                     h->ws + L.adj_dig[i], OZ_BK);
         if (r != 0) return fail(h, GSP2_E_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string(r));
       }
       CU(h, up(L.adj_maps, amaps.data(), amaps.size()));

@@ -143,7 +143,8 @@ struct OzStepArgs {
   const Tile* tiles;   // 128x128 upper tiles
   int ntiles;
   const void* maps;    // CUtensorMap[2 buffers][OZ_SLICES][nparts] over the digit arenas, K-major boxes
-  const void* maps_mn; // the same with MN-major boxes (64 rows x OZ_BK columns, 128-byte swizzle)
+  const void* maps_mn; // the same with MN-major boxes (128 rows x OZ_BK columns as two 64-row atoms,
+                       // 128-byte swizzle; 3-D maps, one request per digit tile)
   const void* maps_b;    // adjoint: CUtensorMap[OZ_SLICES][nparts] over the digits of Xbar / 2^sig
   const void* maps_mn_b; // the same, MN-major
   int32_t* sig;          // adjoint: per-part scale exponent of Xbar's digits (OZ_SIG_NONFINITE: NaN),

@@ -63,6 +63,7 @@ cudaError_t launch_oz_digits(const PartDesc* parts, const ColBlock* blocks, int 
                              const DevState* st, cudaStream_t s);
 int encode_part_maps(void* enc_fn, void* out_maps, const PartDesc* parts, int nparts, void* arena, int kind,
                      int box_bytes = 128, int box_cols = 128);
+int encode_part_maps_mn128(void* enc_fn, void* out_maps, const PartDesc* parts, int nparts, void* arena, int box_k);
 
 // adjoint (k_adjoint.cu)
 template <typename T>

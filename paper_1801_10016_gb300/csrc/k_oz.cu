@@ -501,15 +501,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
             if (kt <= t.ti) {
               tma_load_2d(tileA(s, slot), mA + at, k0, t.ti * 128, full(s));
             } else {
-              tma_load_2d(tileA(s, slot), mmA + at, t.ti * 128, k0, full(s));
-              tma_load_2d(tileA(s, slot) + OZ_DTILE / 2, mmA + at, t.ti * 128 + 64, k0, full(s));
+              tma_load_3d(tileA(s, slot), mmA + at, 0, k0, 2 * t.ti, full(s));  // both 64-row halves
             }
             if (dg) continue;
             if (kt <= t.tj) {
               tma_load_2d(tileB(s, slot), mB + at, k0, t.tj * 128, full(s));
             } else {
-              tma_load_2d(tileB(s, slot), mmB + at, t.tj * 128, k0, full(s));
-              tma_load_2d(tileB(s, slot) + OZ_DTILE / 2, mmB + at, t.tj * 128 + 64, k0, full(s));
+              tma_load_3d(tileB(s, slot), mmB + at, 0, k0, 2 * t.tj, full(s));
             }
           }
         }

@@ -1284,4 +1284,29 @@ int encode_part_maps(void* enc_fn, void* out_maps, const PartDesc* parts, int np
   return 0;
 }
 
+// MN-major boxes of 128 rows of a BF16 arena in one request: the part viewed as a 3-D tensor
+// (64 consecutive rows, the column, the 64-row block; strides 2 B, 2 ld B, 128 B) and a box of
+// 64 x box_k x 2, which lands as two 64-row atoms (box_k rows of 128 bytes each, 128-byte
+// swizzle) back to back, as the MN-major matrix descriptors expect them.
+int encode_part_maps_mn128(void* enc_fn, void* out_maps, const PartDesc* parts, int nparts, void* arena, int box_k) {
+  CUtensorMap* out = reinterpret_cast<CUtensorMap*>(out_maps);
+  using Enc = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*, const cuuint64_t*,
+                           const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                           CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+  Enc enc = reinterpret_cast<Enc>(enc_fn);
+  for (int k = 0; k < nparts; ++k) {
+    const PartDesc& p = parts[k];
+    cuuint64_t dims[3] = {64, (cuuint64_t)p.ld, (cuuint64_t)(p.ld / 64)};
+    cuuint64_t strides[2] = {(cuuint64_t)p.ld * 2, 128};
+    cuuint32_t box[3] = {64, (cuuint32_t)box_k, 2};
+    cuuint32_t estr[3] = {1u, 1u, 1u};
+    void* addr = (char*)arena + (size_t)p.off * 2;
+    CUresult r = enc(&out[k], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, addr, dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return (int)r;
+  }
+  return 0;
+}
+
 }  // namespace gsp2
