@@ -669,19 +669,26 @@ extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t byt
     if (!enc || q != cudaDriverEntryPointSuccess)
       return fail(h, GSP2_E_CUDA, "cuTensorMapEncodeTiled not available from the driver");
     const size_t np = h->parts.size();
-    // K-major boxes (OZ_BK rows of 128 columns) and MN-major boxes (128 rows of OZ_BK columns
-    // as two 64-row atoms, one request)
+    // per digit set, K-major and MN-major maps whose boxes take all OZ_SLICES digits (the
+    // high pass) or the first OZ_SPLIT (the low pass) of a tile slice in one request; a set's
+    // digit arenas lie one arena apart (consecutive equal allocations)
+    const size_t dstride = (size_t)h->arena_elems * 2;
+    auto encode_set = [&](unsigned char* mk, unsigned char* mm, const size_t* dig) -> int {
+      for (int t = 1; t < OZ_SLICES; ++t)
+        if (dig[t] != dig[0] + (size_t)t * dstride) return -1;
+      int r = encode_part_maps_digits(enc, mk, mm, h->parts.data(), (int)np, h->ws + dig[0], dstride, OZ_SLICES,
+                                      OZ_SLICES, OZ_BK);
+      if (r == 0)
+        r = encode_part_maps_digits(enc, mk + np * 128, mm + np * 128, h->parts.data(), (int)np, h->ws + dig[0],
+                                    dstride, OZ_SLICES, OZ_SPLIT, OZ_BK);
+      return r;
+    };
     std::vector<unsigned char> maps((size_t)2 * OZ_SLICES * np * 128, 0), maps_mn(maps.size(), 0);
-    for (int b = 0; b < 2; ++b)
-      for (int t = 0; t < OZ_SLICES; ++t) {
-        const size_t at = ((size_t)b * OZ_SLICES + t) * np * 128;
-        int r = encode_part_maps(enc, maps.data() + at, h->parts.data(), (int)np, h->ws + L.oz_slice[b][t], 0,
-                                 2 * OZ_BK, 128);
-        if (r == 0)
-          r = encode_part_maps_mn128(enc, maps_mn.data() + at, h->parts.data(), (int)np, h->ws + L.oz_slice[b][t],
-                                     OZ_BK);
-        if (r != 0) return fail(h, GSP2_E_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string(r));
-      }
+    for (int b = 0; b < 2; ++b) {
+      const size_t at = (size_t)b * OZ_SLICES * np * 128;
+      const int r = encode_set(maps.data() + at, maps_mn.data() + at, L.oz_slice[b]);
+      if (r != 0) return fail(h, GSP2_E_CUDA, "digit tensor maps failed: " + std::to_string(r));
+    }
     CU(h, up(L.oz_maps, maps.data(), maps.size()));
     CU(h, up(L.oz_maps_mn, maps_mn.data(), maps_mn.size()));
     // the emulated steps never write the 16-column chunks of a part's padding: every arena
@@ -700,13 +707,9 @@ extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t byt
     }
     if (!L.adj_dig.empty()) {
       std::vector<unsigned char> amaps(L.adj_dig.size() * np * 128, 0), amaps_mn(amaps.size(), 0);
-      for (size_t i = 0; i < L.adj_dig.size(); ++i) {
-        int r = encode_part_maps(enc, amaps.data() + i * np * 128, h->parts.data(), (int)np, h->ws + L.adj_dig[i], 0,
-                                 2 * OZ_BK, 128);
-        if (r == 0)
-          r = encode_part_maps_mn128(enc, amaps_mn.data() + i * np * 128, h->parts.data(), (int)np,
-                                     h->ws + L.adj_dig[i], OZ_BK);
-        if (r != 0) return fail(h, GSP2_E_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string(r));
+      for (size_t i = 0; i < L.adj_dig.size(); i += OZ_SLICES) {
+        const int r = encode_set(amaps.data() + i * np * 128, amaps_mn.data() + i * np * 128, &L.adj_dig[i]);
+        if (r != 0) return fail(h, GSP2_E_CUDA, "digit tensor maps failed: " + std::to_string(r));
       }
       CU(h, up(L.adj_maps, amaps.data(), amaps.size()));
       CU(h, up(L.adj_maps_mn, amaps_mn.data(), amaps_mn.size()));

@@ -142,10 +142,11 @@ struct OzStepArgs {
   const PartDesc* parts;
   const Tile* tiles;   // 128x128 upper tiles
   int ntiles;
-  const void* maps;    // CUtensorMap[2 buffers][OZ_SLICES][nparts] over the digit arenas, K-major boxes
-  const void* maps_mn; // the same with MN-major boxes (128 rows x OZ_BK columns as two 64-row atoms,
-                       // 128-byte swizzle; 3-D maps, one request per digit tile)
-  const void* maps_b;    // adjoint: CUtensorMap[OZ_SLICES][nparts] over the digits of Xbar / 2^sig
+  const void* maps;    // per digit buffer (OZ_SLICES x nparts maps apart): CUtensorMap[2][nparts], K-major
+                       // boxes of all OZ_SLICES digits ([0]) or the first OZ_SPLIT ([1]) of a tile slice
+  const void* maps_mn; // the same with MN-major boxes (each tile 128 rows x OZ_BK columns as two 64-row atoms,
+                       // 128-byte swizzle)
+  const void* maps_b;    // adjoint: the same two K-major map arrays over the digits of Xbar / 2^sig
   const void* maps_mn_b; // the same, MN-major
   int32_t* sig;          // adjoint: per-part scale exponent of Xbar's digits (OZ_SIG_NONFINITE: NaN),
                          // replaced by the new Xbar's scale by the last block of the step

@@ -63,7 +63,8 @@ cudaError_t launch_oz_digits(const PartDesc* parts, const ColBlock* blocks, int 
                              const DevState* st, cudaStream_t s);
 int encode_part_maps(void* enc_fn, void* out_maps, const PartDesc* parts, int nparts, void* arena, int kind,
                      int box_bytes = 128, int box_cols = 128);
-int encode_part_maps_mn128(void* enc_fn, void* out_maps, const PartDesc* parts, int nparts, void* arena, int box_k);
+int encode_part_maps_digits(void* enc_fn, void* out_k, void* out_mn, const PartDesc* parts, int nparts, void* arena0,
+                            size_t dstride, int ndig, int nbox, int box_k);
 
 // adjoint (k_adjoint.cu)
 template <typename T>

@@ -491,23 +491,24 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
           mbar_expect_tx(full(s), (uint32_t)(sub * (dg ? nd : 2 * nd)) * OZ_DTILE);
           // rows I over the K slice: K-major from columns I of the tiles on or above the
           // diagonal (slice block <= I's block), else MN-major from rows I of tile (I, slice);
-          // the slices of one stage lie in one 128-block of K
-          for (int u = 0; u < sub; ++u)
-          for (int qq = 0; qq < nd; ++qq) {
+          // the slices of one stage lie in one 128-block of K.  One request per slice and
+          // operand brings all nd digit tiles (slots u nd .. u nd + nd - 1): the maps of the
+          // high pass take OZ_SLICES digits per box, those of the low pass OZ_SPLIT
+          const size_t at = (size_t)(nd == T ? 0 : 1) * a.nparts + t.part;
+          for (int u = 0; u < sub; ++u) {
             const int k0 = (kq * sub + u) * OZ_BK;
             const int kt = k0 / 128;
-            const int q = qq, slot = u * nd + qq;  // digit, tile slot within the stage
-            const size_t at = (size_t)q * a.nparts + t.part;
+            const int slot = u * nd;
             if (kt <= t.ti) {
-              tma_load_2d(tileA(s, slot), mA + at, k0, t.ti * 128, full(s));
+              tma_load_3d(tileA(s, slot), mA + at, k0, t.ti * 128, 0, full(s));
             } else {
-              tma_load_3d(tileA(s, slot), mmA + at, 0, k0, 2 * t.ti, full(s));  // both 64-row halves
+              tma_load_4d(tileA(s, slot), mmA + at, 0, k0, 2 * t.ti, 0, full(s));  // 64-row atoms x digits
             }
             if (dg) continue;
             if (kt <= t.tj) {
-              tma_load_2d(tileB(s, slot), mB + at, k0, t.tj * 128, full(s));
+              tma_load_3d(tileB(s, slot), mB + at, k0, t.tj * 128, 0, full(s));
             } else {
-              tma_load_3d(tileB(s, slot), mmB + at, 0, k0, 2 * t.tj, full(s));
+              tma_load_4d(tileB(s, slot), mmB + at, 0, k0, 2 * t.tj, 0, full(s));
             }
           }
         }

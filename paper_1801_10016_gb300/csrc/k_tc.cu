@@ -1284,27 +1284,46 @@ int encode_part_maps(void* enc_fn, void* out_maps, const PartDesc* parts, int np
   return 0;
 }
 
-// MN-major boxes of 128 rows of a BF16 arena in one request: the part viewed as a 3-D tensor
-// (64 consecutive rows, the column, the 64-row block; strides 2 B, 2 ld B, 128 B) and a box of
-// 64 x box_k x 2, which lands as two 64-row atoms (box_k rows of 128 bytes each, 128-byte
-// swizzle) back to back, as the MN-major matrix descriptors expect them.
-int encode_part_maps_mn128(void* enc_fn, void* out_maps, const PartDesc* parts, int nparts, void* arena, int box_k) {
-  CUtensorMap* out = reinterpret_cast<CUtensorMap*>(out_maps);
+// Maps over the ndig consecutive BF16 digit arenas of the emulated step (digit t at
+// arena0 + t dstride bytes) whose boxes take `nbox` digits at once, so that one request
+// fills nbox consecutive 128 x box_k digit tiles of a stage.  K-major: (column, row, digit),
+// strides 2 ld B and dstride B, box box_k x 128 x nbox, 64-byte rows and swizzle.  MN-major:
+// (64 consecutive rows, column, 64-row block, digit), strides 2 ld B, 128 B and dstride B,
+// box 64 x box_k x 2 x nbox: each tile lands as two 128-byte-swizzled 64-row atoms back to
+// back, as the MN-major matrix descriptors expect them.
+int encode_part_maps_digits(void* enc_fn, void* out_k, void* out_mn, const PartDesc* parts, int nparts, void* arena0,
+                            size_t dstride, int ndig, int nbox, int box_k) {
+  CUtensorMap* ok = reinterpret_cast<CUtensorMap*>(out_k);
+  CUtensorMap* om = reinterpret_cast<CUtensorMap*>(out_mn);
   using Enc = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*, const cuuint64_t*,
                            const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
                            CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
   Enc enc = reinterpret_cast<Enc>(enc_fn);
   for (int k = 0; k < nparts; ++k) {
     const PartDesc& p = parts[k];
-    cuuint64_t dims[3] = {64, (cuuint64_t)p.ld, (cuuint64_t)(p.ld / 64)};
-    cuuint64_t strides[2] = {(cuuint64_t)p.ld * 2, 128};
-    cuuint32_t box[3] = {64, (cuuint32_t)box_k, 2};
-    cuuint32_t estr[3] = {1u, 1u, 1u};
-    void* addr = (char*)arena + (size_t)p.off * 2;
-    CUresult r = enc(&out[k], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, addr, dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return (int)r;
+    void* addr = (char*)arena0 + (size_t)p.off * 2;
+    const cuuint64_t ld = (cuuint64_t)p.ld;
+    {
+      cuuint64_t dims[3] = {ld, ld, (cuuint64_t)ndig};
+      cuuint64_t strides[2] = {ld * 2, (cuuint64_t)dstride};
+      cuuint32_t box[3] = {(cuuint32_t)box_k, 128, (cuuint32_t)nbox};
+      cuuint32_t estr[3] = {1u, 1u, 1u};
+      CUresult r = enc(&ok[k], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, addr, dims, strides, box, estr,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, box_k * 2 == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                                                       : CU_TENSOR_MAP_SWIZZLE_128B,
+                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return (int)r;
+    }
+    {
+      cuuint64_t dims[4] = {64, ld, ld / 64, (cuuint64_t)ndig};
+      cuuint64_t strides[3] = {ld * 2, 128, (cuuint64_t)dstride};
+      cuuint32_t box[4] = {64, (cuuint32_t)box_k, 2, (cuuint32_t)nbox};
+      cuuint32_t estr[4] = {1u, 1u, 1u, 1u};
+      CUresult r = enc(&om[k], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, addr, dims, strides, box, estr,
+                       CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) return (int)r;
+    }
   }
   return 0;
 }
