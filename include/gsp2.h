@@ -317,14 +317,17 @@ gsp2_status gsp2_backward(gsp2_handle h, const double* d_pbar, double* d_hbar, v
  *  d_bounds  device double[2], output
  *  stream    cudaStream_t as void*; the call is asynchronous
  * Returns GSP2_E_ARG for a bad size or a NULL pointer, GSP2_E_CUDA if a CUDA call fails
- * (no message is stored).  Non-finite values give non-finite bounds.
+ * (no message is stored).  A NaN anywhere in d_vals, or an Inf - Inf radius, gives NaN
+ * bounds; an infinite value otherwise gives infinite bounds.
  *
  * Its scratch (one 16-byte partial per block and a counter, about 64 KB) is a fixed
  * device array inside the library, held on every GPU that loads the library until
  * the process exits.  All calls on a device share that array: calls that can overlap
- * on the GPU (different streams without ordering) race and must not be issued.  The
- * first call on each device looks the array's device address up; make that first call
- * outside any CUDA stream capture.
+ * on the GPU (different streams without ordering) race and must not be issued.  Every
+ * call made outside a CUDA stream capture looks the array's device address up afresh
+ * (so a context re-created by cudaDeviceReset is followed); a call inside a capture uses
+ * the address an earlier call on the same device found, so make the first call on each
+ * device outside any capture.
  */
 gsp2_status gsp2_bounds_noalloc(int64_t n, const int64_t* d_rowptr, const int32_t* d_colind,
                                 const double* d_vals, double* d_bounds, void* stream);

@@ -517,7 +517,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
     if (bad) {
       *s_err = 1;
       const uint32_t first = g > OZ_STAGES ? g - OZ_STAGES : 0;
-      for (uint32_t q = first; q < g; ++q) (void)mbar_wait(full(q % OZ_STAGES), (q / OZ_STAGES) & 1, abort_flag);
+      for (uint32_t q = first; q < g; ++q) (void)mbar_wait_own(full(q % OZ_STAGES), (q / OZ_STAGES) & 1);
     }
   } else if (warp == 1 && lane == 0) {
     uint32_t g = 0;
@@ -570,7 +570,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
         if (!bad) mma_commit(afull(pass));
       }
     }
-    if (bad) *s_err = 1;
+    if (bad) {
+      *s_err = 1;
+      // MMAs already issued keep reading shared memory and writing TMEM: wait (on this
+      // thread's own limit) for the last commit, which covers all of them
+      if (g > 0) (void)mbar_wait_own(empty((g - 1) % OZ_STAGES), ((g - 1) / OZ_STAGES) & 1);
+    }
   } else if (warp >= 4) {
     const int quarter = warp & 3, colq = (warp - 4) >> 2;
     const int m = quarter * 32 + lane;

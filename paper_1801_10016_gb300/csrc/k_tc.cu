@@ -163,14 +163,16 @@ __global__ void __launch_bounds__(256, 2) square_tc_kernel(TcStepArgs a) {
     }
     // do not leave while copies are in flight: wait (bounded) for the last stages issued
     for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb) {
-      if (!mbar_wait(full(kb % STAGES), (kb / STAGES) & 1, abort_flag)) *s_err = 1;
+      if (!mbar_wait_own(full(kb % STAGES), (kb / STAGES) & 1)) *s_err = 1;
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
+    bool bad = false;
     for (int kb = 0; kb < nk; ++kb) {
       const int s = kb % STAGES;
       if (!mbar_wait(full(s), (kb / STAGES) & 1, abort_flag)) {
         *s_err = 1;
+        bad = true;
         break;
       }
       tc_fence_after();
@@ -188,6 +190,9 @@ __global__ void __launch_bounds__(256, 2) square_tc_kernel(TcStepArgs a) {
       mma_commit(empty(s));
     }
     mma_commit(done);
+    // after an abort the epilogue no longer waits for `done`: the MMAs issued must still
+    // finish before the block frees its TMEM
+    if (bad) (void)mbar_wait_own(done, 0);
   }
   __syncwarp();
 
@@ -479,7 +484,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
       *s_err = 1;
       // do not leave while copies are in flight: bounded wait for the last stages issued
       const uint32_t first = g > STAGES ? g - STAGES : 0;
-      for (uint32_t q = first; q < g; ++q) (void)mbar_wait(full(q % STAGES), (q / STAGES) & 1, abort_flag);
+      for (uint32_t q = first; q < g; ++q) (void)mbar_wait_own(full(q % STAGES), (q / STAGES) & 1);
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer: tile i accumulates in TMEM columns [128 (i & 1), + 128)
@@ -543,7 +548,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
       }
       mma_commit(tfull(b));
     }
-    if (bad) *s_err = 1;
+    if (bad) {
+      *s_err = 1;
+      // MMAs already issued keep reading shared memory and writing TMEM: wait (on this
+      // thread's own limit) for the last commit, which covers all of them
+      if (g > 0) (void)mbar_wait_own(empty((g - 1) % STAGES), ((g - 1) / STAGES) & 1);
+    }
   } else if (warp >= 4) {
     // epilogue: warp w drains TMEM lanes 32 (w % 4) .. + 31, columns 32 ((w - 4) / 4) .. + 31,
     // in two halves of 16
@@ -826,7 +836,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_wide_kernel(TcStepArg
     if (bad) {
       *s_err = 1;
       const uint32_t first = g > STAGES ? g - STAGES : 0;
-      for (uint32_t q = first; q < g; ++q) (void)mbar_wait(full(q % STAGES), (q / STAGES) & 1, abort_flag);
+      for (uint32_t q = first; q < g; ++q) (void)mbar_wait_own(full(q % STAGES), (q / STAGES) & 1);
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer: item i accumulates in TMEM columns [256 (i & 1), + 128 nb)
@@ -869,7 +879,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_wide_kernel(TcStepArg
       }
       mma_commit(tfull(b));
     }
-    if (bad) *s_err = 1;
+    if (bad) {
+      *s_err = 1;
+      // MMAs already issued keep reading shared memory and writing TMEM: wait (on this
+      // thread's own limit) for the last commit, which covers all of them
+      if (g > 0) (void)mbar_wait_own(empty((g - 1) % STAGES), ((g - 1) / STAGES) & 1);
+    }
   } else if (warp >= 4) {
     // epilogue: warp w drains TMEM lanes 32 (w % 4) .. + 31 and 32 nb columns, in 16-column
     // pieces

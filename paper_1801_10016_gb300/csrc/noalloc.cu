@@ -30,6 +30,11 @@ struct NoallocScratch {
 // Shared by every call on a device; a call leaves its partials behind.
 static __device__ __align__(256) NoallocScratch g_noalloc_scratch;
 
+// min / max that return NaN when either operand is NaN (fmin and fmax return the other
+// operand), so that a NaN in the matrix, or an Inf - Inf radius, reaches the bounds
+__device__ __forceinline__ double nan_min(double a, double b) { return (a != a || b != b) ? NAN : fmin(a, b); }
+__device__ __forceinline__ double nan_max(double a, double b) { return (a != a || b != b) ? NAN : fmax(a, b); }
+
 // Same per-row arithmetic as the bounds step of gsp2_density (one warp per row,
 // lanes striding over the row), with the scratch passed in explicitly.
 __global__ void __launch_bounds__(kThreads) bounds_noalloc_kernel(int64_t n, const int64_t* __restrict__ rowptr,
@@ -49,22 +54,22 @@ __global__ void __launch_bounds__(kThreads) bounds_noalloc_kernel(int64_t n, con
     }
     rad = gsp2::warp_sum(rad);
     dia = gsp2::warp_sum(dia);
-    lo = fmin(lo, dia - rad);
-    hi = fmax(hi, dia + rad);
+    lo = nan_min(lo, dia - rad);
+    hi = nan_max(hi, dia + rad);
   }
   __shared__ double s_lo[kThreads / 32], s_hi[kThreads / 32];
   if (lane == 0) { s_lo[w] = lo; s_hi[w] = hi; }
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int k = 1; k < kThreads / 32; ++k) { lo = fmin(lo, s_lo[k]); hi = fmax(hi, s_hi[k]); }
+    for (int k = 1; k < kThreads / 32; ++k) { lo = nan_min(lo, s_lo[k]); hi = nan_max(hi, s_hi[k]); }
     scratch->slots[blockIdx.x] = make_double2(lo, hi);
   }
   if (gsp2::last_block_ticket(&scratch->counter)) {
     if (threadIdx.x == 0) {
       double a = INFINITY, b = -INFINITY;
       for (unsigned int k = 0; k < gridDim.x; ++k) {
-        a = fmin(a, gsp2::ld_cg(&scratch->slots[k].x));
-        b = fmax(b, gsp2::ld_cg(&scratch->slots[k].y));
+        a = nan_min(a, gsp2::ld_cg(&scratch->slots[k].x));
+        b = nan_max(b, gsp2::ld_cg(&scratch->slots[k].y));
       }
       out[0] = a;
       out[1] = b;
@@ -84,19 +89,25 @@ extern "C" gsp2_status gsp2_bounds_noalloc(int64_t n, const int64_t* d_rowptr, c
   if (!d_rowptr || !d_colind || !d_vals || !d_bounds) return GSP2_E_ARG;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return GSP2_E_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
   NoallocScratch* scratch = nullptr;
   {
-    // one-time set-up per device, with that device current: the host-side name of the
-    // array is not a device address, so its device address is looked up here
+    // The host-side name of the array is not a device address: its address on this device
+    // is looked up with the device current.  Outside a stream capture the lookup is
+    // repeated on every call (it allocates nothing), so a context re-created after
+    // cudaDeviceReset is picked up; inside a capture the address found by an earlier call
+    // on this device is used, so the first call on a device must come before any capture.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return GSP2_E_CUDA;
     std::lock_guard<std::mutex> lock(g_addr_mutex);
-    if (!g_addr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
       void* p = nullptr;
       if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return GSP2_E_CUDA;
       g_addr[dev] = static_cast<NoallocScratch*>(p);
     }
     scratch = g_addr[dev];
+    if (!scratch) return GSP2_E_CUDA;
   }
-  cudaStream_t s = (cudaStream_t)stream;
   // the ticket counter must start at zero; the partials are overwritten
   if (cudaMemsetAsync(&scratch->counter, 0, sizeof(unsigned int), s) != cudaSuccess) return GSP2_E_CUDA;
   const int blocks = (int)((n + kRowsPerBlock - 1) / kRowsPerBlock);

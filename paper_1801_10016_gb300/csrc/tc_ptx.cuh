@@ -50,6 +50,19 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int32_t
   }
 }
 
+// Bounded wait on this thread's own time limit only, for the drains of an aborting CTA:
+// the copies and MMAs it has issued still complete whatever other blocks do, so the
+// shared abort flag must not cut this wait short (a CTA may not exit, nor free its
+// TMEM, while they are in flight).
+__device__ __forceinline__ bool mbar_wait_own(uint32_t bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t i = 1;; ++i) {
+    if (mbar_try(bar, parity)) return true;
+    if ((i & 255u) == 0u && global_ns() - t0 > kWaitNs) return false;
+  }
+}
+
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(

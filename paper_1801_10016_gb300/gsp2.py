@@ -171,6 +171,9 @@ class GSP2:
         self._check(L.gsp2_workspace_bytes(h, C.byref(b)))
         self.workspace_bytes = b.value
         self.workspace = None
+        # density calls made through this plan; gsp2_backward differentiates the last one,
+        # so the autograd function checks that no other call came in between
+        self.forward_count = 0
         if bind:
             self.bind(device)
 
@@ -216,6 +219,7 @@ class GSP2:
             raise ValueError("alpha must be a CUDA int8 tensor")
         self._check(self._lib.gsp2_density(self._h, _tptr(h_vals), _tptr(out), _tptr(alpha), MODES[mode],
                                            int(nsteps), _stream_ptr(stream)))
+        self.forward_count += 1
         return out
 
     def autotune(self, h_vals, trials=3, stream=None):
@@ -226,6 +230,7 @@ class GSP2:
             raise ValueError("h_vals must be a CUDA float64 tensor of nnz(H) values")
         out = torch.empty(self.nnz_p, dtype=torch.float64, device=h_vals.device)
         r = TuneReport()
+        self.forward_count += 1  # the candidates' density calls replace the last forward
         self._check(self._lib.gsp2_autotune(self._h, _tptr(h_vals.contiguous()), _tptr(out), int(trials),
                                             _stream_ptr(stream), C.byref(r)))
         self._refresh_info()
@@ -246,6 +251,7 @@ class GSP2:
             out = torch.empty(self.nnz_p, dtype=torch.float64, device=h_vals.device)
         n = C.c_int32(int(nsteps))
         rec = C.c_int32(0)
+        self.forward_count += 1
         st = self._lib.gsp2_density_reuse(self._h, _tptr(h_vals.contiguous()), _tptr(out), _tptr(alpha), C.byref(n),
                                           _stream_ptr(stream), C.byref(rec))
         if st in (E_ARG, E_STATE, E_CUDA, E_TIMEOUT):
@@ -333,10 +339,17 @@ def _make_function():
         @staticmethod
         def forward(ctx, h_vals, plan):
             ctx.plan = plan
-            return plan.density(h_vals)
+            p = plan.density(h_vals)
+            ctx.forward_id = plan.forward_count
+            return p
 
         @staticmethod
         def backward(ctx, p_bar):
+            # the library keeps the checkpoints and branch sequence of the plan's last density
+            # call only: a later call on the same plan has replaced this forward's
+            if ctx.plan.forward_count != ctx.forward_id:
+                raise RuntimeError("gsp2_density: the plan ran another density call after this forward; its "
+                                   "adjoint state is gone (use one plan per live forward)")
             return ctx.plan.backward(p_bar.contiguous()), None
 
     return GSP2Density

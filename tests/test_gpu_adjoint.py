@@ -82,6 +82,31 @@ def test_autograd_function_uses_the_adjoint(g):
     assert torch.equal(h.grad, direct)
 
 
+def test_autograd_refuses_a_forward_replaced_by_a_later_call(g):
+    """The library keeps the adjoint state of a plan's last density call only: a backward
+    through an earlier forward on the same plan must raise instead of returning the
+    gradient at the later H."""
+    import torch
+    s = make_tb_system(48, 4, 3.0, seed=21)
+    plan = g.GSP2(s.n, s.rowptr, s.colind, s.nocc, s.part, s.nparts, s.g_rowptr, s.g_colind, device="cuda:0")
+    pb, _ = pbar_for_trace_loss(s, plan)
+    pbt = torch.from_numpy(pb).to("cuda:0")
+    h1 = torch.from_numpy(s.vals).to("cuda:0").requires_grad_(True)
+    h2 = (torch.from_numpy(s.vals) * 1.01).to("cuda:0").requires_grad_(True)
+    P1 = g.gsp2_density(h1, plan)
+    P2 = g.gsp2_density(h2, plan)
+    with pytest.raises(RuntimeError, match="another density call"):
+        (P1 * pbt).sum().backward()
+    # the live (last) forward still differentiates, and a plain density call also
+    # invalidates it
+    (P2 * pbt).sum().backward()
+    assert torch.equal(h2.grad, plan.backward(pbt))
+    P3 = g.gsp2_density(h1.detach().requires_grad_(True), plan)
+    plan.density(h2.detach())
+    with pytest.raises(RuntimeError, match="another density call"):
+        (P3 * pbt).sum().backward()
+
+
 def test_backward_state_errors(g):
     import torch
     s = make_tb_system(20, 2, 3.0, seed=4)

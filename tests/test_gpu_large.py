@@ -41,7 +41,10 @@ def test_tb120k_forward_and_adjoint_on_samples(g):
     hist = plan.history()
     rep = hist["report"]
     assert hist["status"] == 0 and rep["fp64_steps"] == 2
-    bounds = (rep["eps_min"], rep["eps_max"])
+    # the Gershgorin bounds are the oracle's own (they are cheap at any size)
+    bounds = oracle.gershgorin_bounds(s.n, s.rowptr, s.colind, s.vals)
+    assert rep["eps_min"] == pytest.approx(bounds[0], rel=1e-13, abs=1e-13)
+    assert rep["eps_max"] == pytest.approx(bounds[1], rel=1e-13, abs=1e-13)
     alphas = hist["alphas"]
     Hs = sp.csr_matrix((s.vals, s.colind, s.rowptr), shape=(s.n, s.n))
     p_host = p.cpu().numpy()

@@ -343,3 +343,32 @@ def test_seed_on_pattern_and_core_halo_subset_agree_with_the_dense_forms():
     for k, (c, h) in zip([5, 2], sub):
         np.testing.assert_array_equal(c, full[k][0])
         np.testing.assert_array_equal(h, full[k][1])
+
+
+@pytest.mark.parametrize("case", ["tb512", "ragged"])
+def test_p_on_pattern_is_dense_p_read_on_the_pattern(case):
+    """Every GPU parity test reads the oracle's P through p_on_pattern: it must give, for
+    each stored (row, column) of a core-column pattern, the entry of the assembled P that
+    dense_p() holds there (dense_p itself is pinned by the core-column test above), in
+    whatever row order a column lists its rows."""
+    s = make_workload("tb512") if case == "tb512" else make_tb_system(33, 5, 3.2, seed=133)
+    res = oracle.gsp2(s.n, s.rowptr, s.colind, s.vals, s.nocc, s.part, s.nparts, s.g_rowptr, s.g_colind)
+    P = res.dense_p()
+    rows_of = {}
+    for S, c in zip(res.S, res.ncore):
+        for j in range(c):
+            rows_of[int(S[j])] = np.sort(S)
+    assert sorted(rows_of) == list(range(s.n))
+    rng = np.random.default_rng(7)
+    for order in ("ascending", "shuffled"):
+        lists = [rows_of[g] if order == "ascending" else rng.permutation(rows_of[g]) for g in range(s.n)]
+        colptr = np.zeros(s.n + 1, np.int64)
+        colptr[1:] = np.cumsum([len(r) for r in lists])
+        rowind = np.concatenate(lists).astype(np.int32)
+        cols = np.repeat(np.arange(s.n), np.diff(colptr))
+        got = res.p_on_pattern(colptr, rowind)
+        np.testing.assert_array_equal(got, P[rowind, cols])
+    # the pattern holds every nonzero of P (nothing of P lies off the core-column pattern)
+    mask = np.zeros((s.n, s.n), bool)
+    mask[rowind, cols] = True
+    assert not np.any(P[~mask])
