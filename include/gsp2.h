@@ -303,6 +303,80 @@ gsp2_status gsp2_autotune(gsp2_handle h, const double* d_hvals, double* d_pvals,
  */
 gsp2_status gsp2_backward(gsp2_handle h, const double* d_pbar, double* d_hbar, void* stream);
 
+/* ---------------------------------------------------------------- shard plans
+ *
+ * One problem's parts split over several GPUs, one process (and plan) per GPU.  Parts are
+ * independent except through the branch of every step, which Section 2.1 takes from the
+ * trace of the whole iterate, in G-SP2 the sum of all parts' core diagonals (Section 2.2).
+ * A shard plan holds the parts of one rank; each of its bookkeeping launches (the gather
+ * of X0, every purification step) leaves this rank's partial sums -- core trace of the new
+ * iterate and core trace of the square of the old one, 16 bytes -- for the caller to
+ * all-gather, and a decide launch adds every rank's partials in rank order and takes the
+ * branch, the stopping test and the history exactly as the fused step does.  Every rank
+ * sums the same numbers in the same order, so all take bitwise the same branches; with one
+ * rank the result is bitwise that of gsp2_density.  A call is:
+ *
+ *   gsp2_shard_exchanges(h, mode, nsteps, &count);
+ *   gsp2_shard_begin(h, H, P, alpha, mode, nsteps, send, s);     exchange 0 queued
+ *   for x in 0 .. count-1:
+ *     all-gather send (double[2]) of every rank into recv (double[nranks][2]), on s;
+ *     gsp2_shard_decide(h, x, recv, nranks, s);
+ *     if x + 1 < count: gsp2_shard_step(h, x + 1, send, s);
+ *   gsp2_shard_end(h, s);                                        scatter of this rank's P
+ *
+ * P of a shard plan holds the core columns of its parts (gsp2_p_pattern: the other columns
+ * are empty); the ranks' columns are disjoint and together are P.  gsp2_backward gives this
+ * rank's share of dL/dH (the parts it holds); the sum over ranks is dL/dH.  gsp2_density,
+ * gsp2_density_reuse and gsp2_autotune return GSP2_E_STATE on a shard plan.
+ */
+
+/* Parts to ranks by longest processing time first on the Eq. 5 cost s_k^3 (Section 2.2):
+ * parts in descending size (ties: lower id first), each to the rank with the least cost so
+ * far (ties: lower rank).  Host only, deterministic: every rank computes the same map.
+ *  sizes      host int32[nparts], s_k of every part (gsp2_plan_query of a plain plan), >= 1
+ *  nranks     1 .. nparts (every rank gets at least one part)
+ *  part_rank  host int32[nparts], output
+ *  rank_cost  host double[nranks] or NULL: sum of s_k^3 per rank */
+gsp2_status gsp2_assign_parts(const int32_t* sizes, int32_t nparts, int32_t nranks, int32_t* part_rank,
+                              double* rank_cost);
+
+/* A shard plan: as gsp2_create (same arguments, validation and halos from the whole
+ * problem), holding only the parts with part_rank[k] == rank (host int32[nparts], >= 0;
+ * the rank must own at least one part), numbered in ascending global order. */
+gsp2_status gsp2_create_shard(int64_t n, const int64_t* rowptr, const int32_t* colind, int64_t nocc,
+                              const int32_t* part, int32_t nparts, const int64_t* g_rowptr, const int32_t* g_colind,
+                              const int32_t* part_rank, int32_t rank, const gsp2_options* opt, gsp2_handle* out);
+
+/* Rank of a shard plan (0 for a plain one), the problem's part count, and the global id
+ * of each part the plan holds (host int32[gsp2_plan_info.nparts]); pointers may be NULL. */
+gsp2_status gsp2_shard_info(gsp2_handle h, int32_t* rank, int32_t* nparts_global, int32_t* part_ids);
+
+/* Number of exchanges of a shard density call: 1 (X0) + the step launches (RECORD: the
+ * loop's max_steps plus tail steps; REPLAY: nsteps, FP64 precisions only). */
+gsp2_status gsp2_shard_exchanges(gsp2_handle h, int32_t mode, int32_t nsteps, int32_t* count);
+
+/* Opens a shard density call (arguments as gsp2_density; the buffers must stay valid until
+ * gsp2_shard_end) and queues the bounds and the gather of X0; d_send (device double[2])
+ * receives this rank's partial of exchange 0.  A rank whose launches met NaN/Inf or a
+ * timed-out wait sends NaN, so that every rank's sum is non-finite and all stop. */
+gsp2_status gsp2_shard_begin(gsp2_handle h, const double* d_hvals, double* d_pvals, int8_t* d_alpha, int32_t mode,
+                             int32_t nsteps, double* d_send, void* stream);
+
+/* Bookkeeping of exchange x (0 .. count-1) from d_recv (device double[nranks][2], the
+ * partials of ranks 0 .. nranks-1 in order), summed in rank order.  Must follow
+ * gsp2_shard_begin (x = 0) or gsp2_shard_step(x); GSP2_E_STATE otherwise. */
+gsp2_status gsp2_shard_decide(gsp2_handle h, int32_t x, const double* d_recv, int32_t nranks, void* stream);
+
+/* Queues the launches up to the bookkeeping of exchange x (1 .. count-1), the purification
+ * step x and what prepares it; d_send receives this rank's partial.  Must follow
+ * gsp2_shard_decide(x - 1). */
+gsp2_status gsp2_shard_step(gsp2_handle h, int32_t x, double* d_send, void* stream);
+
+/* Closes the call after gsp2_shard_decide(count - 1): scatter of this rank's core columns
+ * into d_pvals, the branch sequence into d_alpha (RECORD).  Then gsp2_sync_status,
+ * gsp2_history and gsp2_backward apply as after gsp2_density. */
+gsp2_status gsp2_shard_end(gsp2_handle h, void* stream);
+
 /*
  * Allocation-free Gershgorin bounds (the paper has no counterpart: this entry point
  * exists for callers that may not allocate device memory, such as code running in

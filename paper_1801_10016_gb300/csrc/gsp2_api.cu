@@ -2,6 +2,7 @@
 // padded layout, work lists, pattern of P), workspace binding, and the queued step
 // sequence of a density call, captured once into a CUDA graph and replayed.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -54,6 +55,7 @@ struct WsLayout {
   size_t mask;                    // uint8[nnz_p]: |P| > tau flags of gsp2_threshold_graph
   std::vector<size_t> tailf;      // low-precision adjoint: FP32 iterates of the FP64 tail, recomputed
   size_t slots, rslots, state, alpha, traces, idem, step_arena;
+  size_t xchg;                 // ShardSlot of a shard plan's exchanges
   size_t arena0, arena1;       // ping-pong iterates
   std::vector<size_t> ckpt;    // X_0, X_k, X_2k, ... (adjoint checkpoints)
   std::vector<size_t> seg;     // seg[j] = X_{c0+j}, j = 1..k-1, recomputed in the adjoint
@@ -121,6 +123,20 @@ struct gsp2_plan {
   std::vector<size_t> step_arena_off;  // workspace offset of the arena holding X_i
   std::vector<cudaEvent_t> ev;  // 2 per step when time_steps is set
   bool have_forward = false;
+  // shard plans (gsp2_create_shard): the plan holds the parts one rank owns, numbered in
+  // ascending global order; part_global maps them back.  A plain plan owns every part.
+  bool shard = false;
+  int32_t shard_rank = 0, nparts_global = 0;
+  std::vector<int32_t> part_global;
+  // exchange sequence of the shard density call in progress: its buffers, and the next
+  // call expected (begin, then decide 0, step 1, decide 1, ..., end)
+  struct ShardCall {
+    const double* hv = nullptr;
+    double* pv = nullptr;
+    int8_t* alpha = nullptr;
+    int mode = 0, nsteps = 0, count = 0;
+    int next = -1;  // -1: no call open; 2x: decide x expected; 2x + 1: step x + 1 (or end)
+  } sx;
   std::string err;
 };
 
@@ -251,6 +267,7 @@ static void build_layout(gsp2_plan* h) {
   L.slots = take(nsl * sizeof(double2));
   L.rslots = take(std::max<size_t>(h->tiles.size(), 1) * sizeof(double));
   L.state = take(sizeof(DevState));
+  L.xchg = take(sizeof(ShardSlot));
   L.alpha = take((size_t)h->opt.max_steps + HIST_EXTRA);
   L.traces = take(((size_t)h->opt.max_steps + HIST_EXTRA) * sizeof(double));
   L.idem = take(((size_t)h->opt.max_steps + HIST_EXTRA) * sizeof(double));
@@ -360,9 +377,10 @@ static void build_layout(gsp2_plan* h) {
   }
 }
 
-extern "C" gsp2_status gsp2_create(int64_t n, const int64_t* rowptr, const int32_t* colind, int64_t nocc,
-                                   const int32_t* part, int32_t nparts, const int64_t* g_rowptr,
-                                   const int32_t* g_colind, const gsp2_options* opt, gsp2_handle* out) {
+// Plan over the parts that `part_rank` assigns to `rank` (every part when part_rank is NULL).
+static gsp2_status create_plan(int64_t n, const int64_t* rowptr, const int32_t* colind, int64_t nocc,
+                               const int32_t* part, int32_t nparts, const int64_t* g_rowptr, const int32_t* g_colind,
+                               const int32_t* part_rank, int32_t rank, const gsp2_options* opt, gsp2_handle* out) {
   if (!out) return GSP2_E_ARG;
   *out = nullptr;
   gsp2_plan* h = new (std::nothrow) gsp2_plan();
@@ -424,10 +442,32 @@ extern "C" gsp2_status gsp2_create(int64_t n, const int64_t* rowptr, const int32
       if (k < 0 || k >= nparts) return bail(GSP2_E_ARG, "part id out of range at vertex " + std::to_string(i));
       core[k].push_back((int32_t)i);
     }
+    for (int32_t k = 0; k < nparts; ++k)
+      if (core[k].empty()) return bail(GSP2_E_ARG, "part " + std::to_string(k) + " is empty");
+    // the parts this plan holds: all, or those of `rank` (local index = rank of the global id)
+    std::vector<int32_t> local(nparts, -1);
+    if (part_rank) {
+      for (int32_t k = 0; k < nparts; ++k) {
+        if (part_rank[k] < 0) return bail(GSP2_E_ARG, "part_rank[" + std::to_string(k) + "] is negative");
+        if (part_rank[k] == rank) {
+          local[k] = (int32_t)h->part_global.size();
+          h->part_global.push_back(k);
+        }
+      }
+      if (h->part_global.empty()) return bail(GSP2_E_ARG, "rank " + std::to_string(rank) + " owns no part");
+      h->shard = true;
+      h->shard_rank = rank;
+    } else {
+      for (int32_t k = 0; k < nparts; ++k) {
+        local[k] = k;
+        h->part_global.push_back(k);
+      }
+    }
+    h->nparts_global = nparts;
+    const int32_t nloc = (int32_t)h->part_global.size();
     // halo: vertices outside part k adjacent (out-edges of G_tau) to a core of k
     std::vector<int32_t> stamp(n, -1);
-    for (int32_t k = 0; k < nparts; ++k) {
-      if (core[k].empty()) return bail(GSP2_E_ARG, "part " + std::to_string(k) + " is empty");
+    for (int32_t k : h->part_global) {
       for (int32_t u : core[k])
         for (int64_t p = grp[u]; p < grp[u + 1]; ++p) {
           const int32_t v = gci[p];
@@ -439,10 +479,12 @@ extern "C" gsp2_status gsp2_create(int64_t n, const int64_t* rowptr, const int32
       std::sort(halo[k].begin(), halo[k].end());
     }
     // layout
-    h->parts.resize(nparts);
+    h->nparts = nloc;
+    h->parts.resize(nloc);
     int64_t off = 0, soff = 0;
-    for (int32_t k = 0; k < nparts; ++k) {
-      PartDesc& d = h->parts[k];
+    for (int32_t kl = 0; kl < nloc; ++kl) {
+      const int32_t k = h->part_global[kl];
+      PartDesc& d = h->parts[kl];
       d.c = (int32_t)core[k].size();
       d.s = d.c + (int32_t)halo[k].size();
       d.ld = (d.s + LD_PAD - 1) / LD_PAD * LD_PAD;
@@ -461,8 +503,7 @@ extern "C" gsp2_status gsp2_create(int64_t n, const int64_t* rowptr, const int32
     h->sum_s = soff;
     // scatter permutation and the pattern of P (rows of column g = sorted S_part(g))
     h->perm.resize(soff);
-    std::vector<int64_t> colstart(nparts);
-    for (int32_t k = 0; k < nparts; ++k) {
+    for (int32_t k = 0; k < nloc; ++k) {
       const PartDesc& d = h->parts[k];
       int32_t* pk = h->perm.data() + d.soff;
       std::iota(pk, pk + d.s, 0);
@@ -470,7 +511,7 @@ extern "C" gsp2_status gsp2_create(int64_t n, const int64_t* rowptr, const int32
       std::sort(pk, pk + d.s, [&](int32_t a, int32_t b) { return Sk[a] < Sk[b]; });
     }
     h->invperm.resize(soff);
-    for (int32_t k = 0; k < nparts; ++k) {
+    for (int32_t k = 0; k < nloc; ++k) {
       const PartDesc& d = h->parts[k];
       for (int32_t t = 0; t < d.s; ++t) h->invperm[d.soff + h->perm[d.soff + t]] = t;
     }
@@ -482,7 +523,7 @@ extern "C" gsp2_status gsp2_create(int64_t n, const int64_t* rowptr, const int32
     h->memloc.resize(soff);
     {
       std::vector<int64_t> fill(h->memptr.begin(), h->memptr.end() - 1);
-      for (int32_t k = 0; k < nparts; ++k) {
+      for (int32_t k = 0; k < nloc; ++k) {
         const PartDesc& d = h->parts[k];
         for (int32_t a = 0; a < d.s; ++a) {
           const int32_t v = h->S[d.soff + a];
@@ -492,18 +533,21 @@ extern "C" gsp2_status gsp2_create(int64_t n, const int64_t* rowptr, const int32
         }
       }
     }
+    // columns of parts held elsewhere (shard plans) are empty
     h->pcolptr.assign(n + 1, 0);
-    for (int64_t g = 0; g < n; ++g) h->pcolptr[g + 1] = h->pcolptr[g] + h->parts[part[g]].s;
+    for (int64_t g = 0; g < n; ++g)
+      h->pcolptr[g + 1] = h->pcolptr[g] + (local[part[g]] >= 0 ? h->parts[local[part[g]]].s : 0);
     h->prowind.resize(h->pcolptr[n]);
     for (int64_t g = 0; g < n; ++g) {
-      const PartDesc& d = h->parts[part[g]];
+      if (local[part[g]] < 0) continue;
+      const PartDesc& d = h->parts[local[part[g]]];
       const int32_t* Sk = h->S.data() + d.soff;
       const int32_t* pk = h->perm.data() + d.soff;
       int32_t* r = h->prowind.data() + h->pcolptr[g];
       for (int32_t t = 0; t < d.s; ++t) r[t] = Sk[pk[t]];
     }
     // work lists: parts in descending size, so the longest tiles start first
-    std::vector<int32_t> order(nparts);
+    std::vector<int32_t> order(nloc);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(),
                      [&](int32_t a, int32_t b) { return h->parts[a].s > h->parts[b].s; });
@@ -538,6 +582,48 @@ extern "C" gsp2_status gsp2_create(int64_t n, const int64_t* rowptr, const int32
     return GSP2_E_OOM;
   }
   *out = h;
+  return GSP2_OK;
+}
+
+extern "C" gsp2_status gsp2_create(int64_t n, const int64_t* rowptr, const int32_t* colind, int64_t nocc,
+                                   const int32_t* part, int32_t nparts, const int64_t* g_rowptr,
+                                   const int32_t* g_colind, const gsp2_options* opt, gsp2_handle* out) {
+  return create_plan(n, rowptr, colind, nocc, part, nparts, g_rowptr, g_colind, nullptr, 0, opt, out);
+}
+
+extern "C" gsp2_status gsp2_create_shard(int64_t n, const int64_t* rowptr, const int32_t* colind, int64_t nocc,
+                                         const int32_t* part, int32_t nparts, const int64_t* g_rowptr,
+                                         const int32_t* g_colind, const int32_t* part_rank, int32_t rank,
+                                         const gsp2_options* opt, gsp2_handle* out) {
+  if (!part_rank) {
+    t_create_err = "part_rank is NULL";
+    if (out) *out = nullptr;
+    return GSP2_E_ARG;
+  }
+  return create_plan(n, rowptr, colind, nocc, part, nparts, g_rowptr, g_colind, part_rank, rank, opt, out);
+}
+
+// Longest processing time first over the Eq. 5 cost s_k^3: parts in descending cost (ties by
+// id), each to the rank with the least cost so far (ties to the lowest rank).  Deterministic,
+// so every rank computes the same assignment from the same sizes.
+extern "C" gsp2_status gsp2_assign_parts(const int32_t* sizes, int32_t nparts, int32_t nranks, int32_t* part_rank,
+                                         double* rank_cost) {
+  if (!sizes || !part_rank || nparts < 1 || nranks < 1 || nranks > nparts) return GSP2_E_ARG;
+  for (int32_t k = 0; k < nparts; ++k)
+    if (sizes[k] < 1) return GSP2_E_ARG;
+  std::vector<int32_t> order(nparts);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return sizes[a] > sizes[b]; });
+  std::vector<double> load(nranks, 0.0);
+  for (int32_t k : order) {
+    int32_t r = 0;
+    for (int32_t q = 1; q < nranks; ++q)
+      if (load[q] < load[r]) r = q;
+    part_rank[k] = r;
+    load[r] += (double)sizes[k] * sizes[k] * sizes[k];
+  }
+  if (rank_cost)
+    for (int32_t r = 0; r < nranks; ++r) rank_cost[r] = load[r];
   return GSP2_OK;
 }
 
@@ -820,9 +906,60 @@ static OzStepArgs oz_args(gsp2_plan* h, const StepCtl& ctl) {
   return a;
 }
 
-// Queue the whole forward pass on `s`.
+// Bookkeeping arguments of a forward call: `ctl` for the FP64 steps, and for the
+// low-precision loop the same with its stopping test gated at max(idem_tol, 16 N u).
+static StepCtl forward_ctl(gsp2_plan* h, int mode, int nsteps) {
+  const WsLayout& L = h->L;
+  char* w = h->ws;
+  const bool fp64 = fp64_like(h->opt.precision);
+  StepCtl ctl{(DevState*)(w + L.state),
+              (int8_t*)(w + L.alpha),
+              (double*)(w + L.traces),
+              (double*)(w + L.idem),
+              h->nocc,
+              h->opt.idem_tol,
+              h->opt.trace_tol,
+              mode,
+              mode == MODE_REPLAY ? nsteps : (fp64 ? h->total_steps : h->opt.max_steps),
+              1,
+              (mode == MODE_RECORD && fp64) ? h->opt.fp64_tail_steps : 0,
+              h->shard ? (ShardSlot*)(w + L.xchg) : nullptr};
+  return ctl;
+}
+static StepCtl lowprec_ctl(gsp2_plan* h, const StepCtl& ctl) {
+  StepCtl lp = ctl;
+  lp.idem_tol = std::max(h->opt.idem_tol, 16.0 * (double)h->n * prec_unit(h->opt.precision));
+  lp.stop_lag = 1;
+  return lp;
+}
+
+// The forward pass is a sequence of segments.  Segment 0 resets the call state, takes the
+// bounds and gathers X0; every further segment ends with one purification-step launch (and
+// holds the launches that prepare it); each of those launches ends with the step's trace
+// bookkeeping in its last block.  The last segment (index = exchanges) scatters P and
+// writes the reports.  The number of bookkeeping launches, segments 0 .. exchanges - 1:
+static int forward_exchanges(gsp2_plan* h, int mode, int nsteps) {
+  if (fp64_like(h->opt.precision)) return 1 + (mode == MODE_REPLAY ? nsteps : h->total_steps);
+  return 1 + h->opt.max_steps + h->opt.lp_tail_steps + h->opt.fp64_tail_steps;
+}
+// The bookkeeping that exchange x completes (SHARD_*), and its arguments.
+static int exchange_kind(gsp2_plan* h, int x, int mode, int nsteps, StepCtl* c) {
+  const StepCtl ctl = forward_ctl(h, mode, nsteps);
+  if (fp64_like(h->opt.precision)) {
+    *c = ctl;
+    return x == 0 ? SHARD_GATHER : SHARD_LOOP;
+  }
+  const StepCtl lp = lowprec_ctl(h, ctl);
+  if (x == 0) { *c = lp; return SHARD_GATHER; }
+  if (x <= h->opt.max_steps) { *c = lp; return SHARD_LOOP; }
+  if (x <= h->opt.max_steps + h->opt.lp_tail_steps) { *c = lp; return SHARD_TAIL_LP; }
+  *c = ctl;
+  return SHARD_TAIL_FP64;
+}
+
+// Queue segments seg_lo .. seg_hi of the forward pass on `s` (the whole pass: 0 .. INT_MAX).
 static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, int8_t* alpha_user, int mode,
-                                   int nsteps, cudaStream_t s) {
+                                   int nsteps, cudaStream_t s, int seg_lo = 0, int seg_hi = INT_MAX) {
   const WsLayout& L = h->L;
   char* w = h->ws;
   auto parts = (const PartDesc*)(w + L.parts);
@@ -838,27 +975,19 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
   auto st = (DevState*)(w + L.state);
   auto alpha = (int8_t*)(w + L.alpha);
   auto A = [&](int i) { return (double*)(w + h->step_arena_off[i]); };
-  const bool fp64 = fp64_like(h->opt.precision);
-  StepCtl ctl{st,
-              alpha,
-              (double*)(w + L.traces),
-              (double*)(w + L.idem),
-              h->nocc,
-              h->opt.idem_tol,
-              h->opt.trace_tol,
-              mode,
-              mode == MODE_REPLAY ? nsteps : (fp64 ? h->total_steps : h->opt.max_steps),
-              1,
-              (mode == MODE_RECORD && fp64) ? h->opt.fp64_tail_steps : 0};
-  CU(h, launch_reset(st, alpha, mode == MODE_REPLAY ? alpha_user : nullptr, nsteps, h->opt.max_steps + HIST_EXTRA, s));
-  CU(h, launch_bounds(h->n, rp, ci, hv, slots, BOUNDS_BLOCKS, st, s));
+  const StepCtl ctl = forward_ctl(h, mode, nsteps);
+  int seg = 0;  // segment of the next launch; a bookkeeping launch closes it
+  auto on = [&]() { return seg >= seg_lo && seg <= seg_hi; };
+  if (on()) {
+    CU(h, launch_reset(st, alpha, mode == MODE_REPLAY ? alpha_user : nullptr, nsteps, h->opt.max_steps + HIST_EXTRA,
+                       s));
+    CU(h, launch_bounds(h->n, rp, ci, hv, slots, BOUNDS_BLOCKS, st, s));
+  }
   const int prec = h->opt.precision;
   if (!fp64_like(prec)) {
     // low-precision phase, stopping test gated at max(idem_tol, 16 N u)
     const int kind = prec_kind(prec), nprod = prec_nprod(prec);
-    StepCtl lp = ctl;
-    lp.idem_tol = std::max(h->opt.idem_tol, 16.0 * (double)h->n * prec_unit(prec));
-    lp.stop_lag = 1;
+    const StepCtl lp = lowprec_ctl(h, ctl);
     float* mf[2] = {(float*)(w + L.mf[0]), (float*)(w + L.mf[1])};
     // FP32 iterate i of the loop: a checkpoint arena when the adjoint keeps it, else ping-pong
     auto mfs = [&](int i) { return (float*)(w + h->mf_of_step[(size_t)i]); };
@@ -872,9 +1001,11 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
     // the persistent 128x128 steps of the 16-bit kinds read the upper tiles only; the other
     // schedules read whole columns
     const bool upper_rows = (kind == 0 || kind == 2) && pgrid > 0 && !wide;
-    CU(h, launch_gather_lp(kind, nprod, parts, (const ColBlock*)(w + L.gblocks_ld), (int)h->gblocks_ld.size(), Sall,
-                           rp, ci, hv, mfs(0), kind >= 0 ? oh[0] : nullptr, nprod == 3 ? ol[0] : nullptr,
-                           (double*)slots, lp, s, upper_rows ? 1 : 0));
+    if (on())
+      CU(h, launch_gather_lp(kind, nprod, parts, (const ColBlock*)(w + L.gblocks_ld), (int)h->gblocks_ld.size(), Sall,
+                             rp, ci, hv, mfs(0), kind >= 0 ? oh[0] : nullptr, nprod == 3 ? ol[0] : nullptr,
+                             (double*)slots, lp, s, upper_rows ? 1 : 0));
+    ++seg;
     if (kind >= 0) {
       tc_args.parts = parts;
       tc_args.tiles = (const Tile*)(w + (wide ? L.tc_wide : L.tc_tiles));
@@ -896,7 +1027,8 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
       tc_args.ctl = lp;
       tc_args.tail = 0;
     }
-    for (int i = 1; i <= lp.last_step; ++i) {
+    for (int i = 1; i <= lp.last_step; ++i, ++seg) {
+      if (!on()) continue;
       const int bi = (i - 1) & 1, bo = i & 1;
       if (!h->ev.empty()) CU(h, cudaEventRecordWithFlags(h->ev[2 * (i - 1)], s, cudaEventRecordExternal));
       if (kind < 0) {
@@ -911,26 +1043,31 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
       if (!h->ev.empty()) CU(h, cudaEventRecordWithFlags(h->ev[2 * (i - 1) + 1], s, cudaEventRecordExternal));
     }
     // alternating tail steps in the low precision
-    for (int t = 0; t < h->opt.lp_tail_steps; ++t) {
+    for (int t = 0; t < h->opt.lp_tail_steps; ++t, ++seg) {
+      if (!on()) continue;
       TcStepArgs a = tc_args;
       a.tail = t == 0 ? 1 : 2;
       CU(h, launch_square_tc(kind, nprod, a, a.ntiles, pgrid, s));
     }
     // FP64 tail: convert the last FP32 iterate, then purification steps in FP64 (native, or
-    // with the products rebuilt from BF16 digits)
+    // with the products rebuilt from BF16 digits); the conversions open the segment of the
+    // first tail step (or the last segment when there is no tail)
     double* d[2] = {(double*)(w + L.d[0]), (double*)(w + L.d[1])};
-    CU(h, launch_convert((const float* const*)(w + L.master_of_step), d[0], h->arena_elems, st, s));
     const int T = h->opt.fp64_tail_steps;
     // the persistent kernel of the 16-bit kinds keeps upper tiles only: the native FP64 tail
     // reads whole 64-tiles, so it gets the lower ones first
     const bool lp_upper = kind == 0 || kind == 2;
-    if (lp_upper && T > 0 && !h->use_oz)
-      CU(h, launch_symmetrize(parts, (const Tile*)(w + L.tc_tiles), (int)h->tc_tiles.size(), nullptr, d[0], st, s));
     OzStepArgs toz = oz_args(h, ctl);
-    if (h->use_oz)
-      CU(h, launch_oz_slice(parts, (const ColBlock*)(w + L.gblocks_ld), (int)h->gblocks_ld.size(), d[0], toz.digits,
-                            st, s));
-    for (int t = 0; t < T; ++t) {
+    if (on()) {
+      CU(h, launch_convert((const float* const*)(w + L.master_of_step), d[0], h->arena_elems, st, s));
+      if (lp_upper && T > 0 && !h->use_oz)
+        CU(h, launch_symmetrize(parts, (const Tile*)(w + L.tc_tiles), (int)h->tc_tiles.size(), nullptr, d[0], st, s));
+      if (h->use_oz)
+        CU(h, launch_oz_slice(parts, (const ColBlock*)(w + L.gblocks_ld), (int)h->gblocks_ld.size(), d[0], toz.digits,
+                              st, s));
+    }
+    for (int t = 0; t < T; ++t, ++seg) {
+      if (!on()) continue;
       const int tmode = (t == 0 && h->opt.lp_tail_steps == 0) ? SQ_TAIL_FIRST : SQ_TAIL_NEXT;
       if (h->use_oz) {
         OzStepArgs a = toz;
@@ -942,6 +1079,7 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
         CU(h, launch_square_fp64(parts, tiles, (int)h->tiles.size(), d[t & 1], d[(t + 1) & 1], slots, h->nslots, ctl,
                                  0, tmode, s));
     }
+    if (!on()) return GSP2_OK;
     // emulated tail steps, and the 16-bit steps without a tail, leave the upper 128-tiles only
     const int ub = ((h->use_oz && T > 0) || (lp_upper && T == 0)) ? TC_TILE : 0;
     CU(h, launch_scatter(parts, sbl, (int)h->sblocks.size(), Sall, perm, pcol, nullptr, d[T & 1], pv, st, s, ub));
@@ -957,15 +1095,19 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
   }
   const bool emu = prec == GSP2_PREC_FP64_EMU;
   OzStepArgs oz{};
-  if (emu) {
-    // X0 and its digits in one pass (the digits to buffer 0, read by step 1)
-    oz = oz_args(h, ctl);
-    CU(h, launch_oz_gather(parts, gbl, (int)h->gblocks_ld.size(), Sall, rp, ci, hv, A(0), oz.digits[0], (double*)slots,
-                           ctl, s));
-  } else {
-    CU(h, launch_gather(parts, gbl, (int)h->gblocks_ld.size(), Sall, rp, ci, hv, A(0), (double*)slots, ctl, s));
+  if (emu) oz = oz_args(h, ctl);
+  if (on()) {
+    if (emu) {
+      // X0 and its digits in one pass (the digits to buffer 0, read by step 1)
+      CU(h, launch_oz_gather(parts, gbl, (int)h->gblocks_ld.size(), Sall, rp, ci, hv, A(0), oz.digits[0],
+                             (double*)slots, ctl, s));
+    } else {
+      CU(h, launch_gather(parts, gbl, (int)h->gblocks_ld.size(), Sall, rp, ci, hv, A(0), (double*)slots, ctl, s));
+    }
   }
-  for (int i = 1; i <= ctl.last_step; ++i) {
+  ++seg;
+  for (int i = 1; i <= ctl.last_step; ++i, ++seg) {
+    if (!on()) continue;
     const double* xin = A(i - 1);
     double* xout = A(i);
     if (!h->ev.empty()) CU(h, cudaEventRecordWithFlags(h->ev[2 * (i - 1)], s, cudaEventRecordExternal));
@@ -981,6 +1123,7 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
                                s));
     if (!h->ev.empty()) CU(h, cudaEventRecordWithFlags(h->ev[2 * (i - 1) + 1], s, cudaEventRecordExternal));
   }
+  if (!on()) return GSP2_OK;
   CU(h, launch_scatter(parts, sbl, (int)h->sblocks.size(), Sall, perm, pcol, (const double* const*)(w + L.step_arena),
                        nullptr, pv, st, s, emu ? TC_TILE : 0));
   if (h->opt.report_idem) {
@@ -1006,6 +1149,7 @@ extern "C" gsp2_status gsp2_density(gsp2_handle h, const double* d_hvals, double
   if (mode == MODE_REPLAY && !fp64_like(h->opt.precision))
     return fail(h, GSP2_E_ARG, "REPLAY is available for the FP64 precision only");
   if (mode == MODE_RECORD) nsteps = 0;
+  if (h->shard) return fail(h, GSP2_E_STATE, "a shard plan computes P with the gsp2_shard_* calls");
   int dev = 0;
   CU(h, cudaGetDevice(&dev));
   if (dev != h->device) return fail(h, GSP2_E_STATE, "current device differs from the workspace's device");
@@ -1043,6 +1187,100 @@ extern "C" gsp2_status gsp2_density(gsp2_handle h, const double* d_hvals, double
     gsp2_status st = enqueue_forward(h, d_hvals, d_pvals, d_alpha, mode, nsteps, s);
     if (st != GSP2_OK) return st;
   }
+  h->have_forward = true;
+  return GSP2_OK;
+}
+
+// ------------------------------------------------------------------ shard plans
+
+extern "C" gsp2_status gsp2_shard_info(gsp2_handle h, int32_t* rank, int32_t* nparts_global, int32_t* part_ids) {
+  if (!usable(h)) return fail(h, GSP2_E_ARG, "invalid handle");
+  if (rank) *rank = h->shard ? h->shard_rank : 0;
+  if (nparts_global) *nparts_global = h->nparts_global;
+  if (part_ids) std::memcpy(part_ids, h->part_global.data(), h->part_global.size() * sizeof(int32_t));
+  return GSP2_OK;
+}
+
+extern "C" gsp2_status gsp2_shard_exchanges(gsp2_handle h, int32_t mode, int32_t nsteps, int32_t* count) {
+  if (!usable(h) || !count) return fail(h, GSP2_E_ARG, "invalid handle or NULL output");
+  if (mode != MODE_RECORD && mode != MODE_REPLAY) return fail(h, GSP2_E_ARG, "mode must be RECORD or REPLAY");
+  if (mode == MODE_REPLAY && (nsteps < 1 || nsteps > h->total_steps || !fp64_like(h->opt.precision)))
+    return fail(h, GSP2_E_ARG, "REPLAY needs the FP64 precision and 1 <= nsteps <= max_steps + fp64_tail_steps");
+  *count = forward_exchanges(h, mode, mode == MODE_REPLAY ? nsteps : 0);
+  return GSP2_OK;
+}
+
+static gsp2_status shard_ready(gsp2_plan* h) {
+  if (!usable(h)) return fail(h, GSP2_E_ARG, "invalid handle");
+  if (!h->shard) return fail(h, GSP2_E_STATE, "not a shard plan (gsp2_create_shard)");
+  if (!h->ws) return fail(h, GSP2_E_STATE, "no workspace bound");
+  int dev = 0;
+  CU(h, cudaGetDevice(&dev));
+  if (dev != h->device) return fail(h, GSP2_E_STATE, "current device differs from the workspace's device");
+  return GSP2_OK;
+}
+
+extern "C" gsp2_status gsp2_shard_begin(gsp2_handle h, const double* d_hvals, double* d_pvals, int8_t* d_alpha,
+                                        int32_t mode, int32_t nsteps, double* d_send, void* stream) {
+  gsp2_status r = shard_ready(h);
+  if (r != GSP2_OK) return r;
+  if (!d_hvals || !d_pvals || !d_send) return fail(h, GSP2_E_ARG, "NULL H, P or send buffer");
+  if (mode != MODE_RECORD && mode != MODE_REPLAY) return fail(h, GSP2_E_ARG, "mode must be RECORD or REPLAY");
+  if (mode == MODE_REPLAY && (!d_alpha || nsteps < 1 || nsteps > h->total_steps))
+    return fail(h, GSP2_E_ARG, "REPLAY needs d_alpha and 1 <= nsteps <= max_steps + fp64_tail_steps");
+  if (mode == MODE_REPLAY && !fp64_like(h->opt.precision))
+    return fail(h, GSP2_E_ARG, "REPLAY is available for the FP64 precision only");
+  if (mode == MODE_RECORD) nsteps = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  h->sx = gsp2_plan::ShardCall{};
+  h->have_forward = false;
+  r = enqueue_forward(h, d_hvals, d_pvals, d_alpha, mode, nsteps, s, 0, 0);
+  if (r != GSP2_OK) return r;
+  CU(h, launch_shard_partial((const DevState*)(h->ws + h->L.state), (const ShardSlot*)(h->ws + h->L.xchg), d_send, s));
+  h->sx.hv = d_hvals;
+  h->sx.pv = d_pvals;
+  h->sx.alpha = d_alpha;
+  h->sx.mode = mode;
+  h->sx.nsteps = nsteps;
+  h->sx.count = forward_exchanges(h, mode, nsteps);
+  h->sx.next = 0;
+  return GSP2_OK;
+}
+
+extern "C" gsp2_status gsp2_shard_decide(gsp2_handle h, int32_t x, const double* d_recv, int32_t nranks,
+                                         void* stream) {
+  gsp2_status r = shard_ready(h);
+  if (r != GSP2_OK) return r;
+  if (!d_recv || nranks < 1) return fail(h, GSP2_E_ARG, "NULL receive buffer or nranks < 1");
+  if (h->sx.next != 2 * x) return fail(h, GSP2_E_STATE, "gsp2_shard_decide out of order");
+  StepCtl c{};
+  const int kind = exchange_kind(h, x, h->sx.mode, h->sx.nsteps, &c);
+  CU(h, launch_shard_decide(c, d_recv, nranks, kind, (cudaStream_t)stream));
+  h->sx.next = 2 * x + 1;
+  return GSP2_OK;
+}
+
+extern "C" gsp2_status gsp2_shard_step(gsp2_handle h, int32_t x, double* d_send, void* stream) {
+  gsp2_status r = shard_ready(h);
+  if (r != GSP2_OK) return r;
+  if (!d_send) return fail(h, GSP2_E_ARG, "NULL send buffer");
+  if (x < 1 || x >= h->sx.count || h->sx.next != 2 * x - 1) return fail(h, GSP2_E_STATE, "gsp2_shard_step out of order");
+  cudaStream_t s = (cudaStream_t)stream;
+  r = enqueue_forward(h, h->sx.hv, h->sx.pv, h->sx.alpha, h->sx.mode, h->sx.nsteps, s, x, x);
+  if (r != GSP2_OK) return r;
+  CU(h, launch_shard_partial((const DevState*)(h->ws + h->L.state), (const ShardSlot*)(h->ws + h->L.xchg), d_send, s));
+  h->sx.next = 2 * x;
+  return GSP2_OK;
+}
+
+extern "C" gsp2_status gsp2_shard_end(gsp2_handle h, void* stream) {
+  gsp2_status r = shard_ready(h);
+  if (r != GSP2_OK) return r;
+  if (h->sx.count < 1 || h->sx.next != 2 * h->sx.count - 1) return fail(h, GSP2_E_STATE, "gsp2_shard_end out of order");
+  const int last = h->sx.count;
+  r = enqueue_forward(h, h->sx.hv, h->sx.pv, h->sx.alpha, h->sx.mode, h->sx.nsteps, (cudaStream_t)stream, last, last);
+  if (r != GSP2_OK) return r;
+  h->sx.next = -1;
   h->have_forward = true;
   return GSP2_OK;
 }

@@ -55,6 +55,20 @@ enum : int32_t { ST_OK = 0, ST_NOT_CONVERGED = 5, ST_TRACE = 6, ST_NONFINITE = 7
 enum : int32_t { MODE_RECORD = 0, MODE_REPLAY = 1 };
 enum : int32_t { SQ_FORWARD = 0, SQ_RECOMPUTE = 1, SQ_TAIL_FIRST = 2, SQ_TAIL_NEXT = 3, SQ_RESIDUAL = 4 };
 
+// Exchange slot of a shard plan (a plan over a subset of the parts, one per GPU): the
+// last block of a step leaves its partial core traces here instead of deciding, and the
+// decision is taken by a separate launch once every shard's partials are summed.
+struct ShardSlot {
+  double t;      // partial Tr_core[X_step] over this shard's parts
+  double y;      // partial Tr_core[X_{step-1}^2]
+  int32_t step;  // the step the partials belong to
+  int32_t pad;
+};
+
+// Which bookkeeping an exchange of a shard plan completes: the gather of X0, a step of
+// the purification loop, an alternating tail step in the low precision, an FP64 tail step.
+enum : int32_t { SHARD_GATHER = 0, SHARD_LOOP = 1, SHARD_TAIL_LP = 2, SHARD_TAIL_FP64 = 3 };
+
 // Arguments of the per-step trace bookkeeping done by the last block of a step.
 struct StepCtl {
   DevState* st;
@@ -68,6 +82,7 @@ struct StepCtl {
   int32_t last_step;  // max_steps (RECORD) or nsteps (REPLAY)
   int32_t stop_lag;   // stopping test compares e_{i-1} with e_{i-1-stop_lag}
   int32_t tail_steps; // RECORD: alternating steps after the stopping test (last_step includes them)
+  ShardSlot* xchg;    // shard plans: export the partial traces here instead of deciding (else NULL)
 };
 
 // Arguments of one tensor-core purification step (k_tc.cu).
@@ -246,6 +261,12 @@ __device__ __forceinline__ double2 block_sum2(double a, double b) {
 // drift of a core trace that cannot reach Nocc) to iterate on.  Every path uses lag 1
 // (the field is kept for experiments with longer lags).
 __device__ __forceinline__ void finish_step(const StepCtl& c, int step, double tN, double tY) {
+  if (c.xchg) {  // shard plan: the sums over all shards decide, in a later launch
+    c.xchg->t = tN;
+    c.xchg->y = tY;
+    c.xchg->step = step;
+    return;
+  }
   DevState* st = c.st;
   c.traces[step] = tN;
   st->steps = step;
@@ -301,6 +322,12 @@ __device__ __forceinline__ void finish_step(const StepCtl& c, int step, double t
 // low precision): records T_step, e_{step-1} and the step count; no stopping test and
 // no branch choice.
 __device__ __forceinline__ void finish_tail(const StepCtl& c, int step, double tN, double tY, bool fp64) {
+  if (c.xchg) {
+    c.xchg->t = tN;
+    c.xchg->y = tY;
+    c.xchg->step = step;
+    return;
+  }
   DevState* st = c.st;
   c.traces[step] = tN;
   c.idem[step - 1] = c.traces[step - 1] - tY;

@@ -66,6 +66,10 @@ int encode_part_maps(void* enc_fn, void* out_maps, const PartDesc* parts, int np
 int encode_part_maps_digits(void* enc_fn, void* out_k, void* out_mn, const PartDesc* parts, int nparts, void* arena0,
                             size_t dstride, int ndig, int nbox, int box_k);
 
+// shard plans (k_shard.cu): this shard's partial traces out, the summed decision in
+cudaError_t launch_shard_partial(const DevState* st, const ShardSlot* slot, double* send, cudaStream_t s);
+cudaError_t launch_shard_decide(const StepCtl& c, const double* recv, int nranks, int kind, cudaStream_t s);
+
 // adjoint (k_adjoint.cu)
 template <typename T>
 cudaError_t launch_adj_seed(const PartDesc* parts, const ColBlock* blocks, int nblocks, const int32_t* Sall,

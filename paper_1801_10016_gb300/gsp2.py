@@ -95,6 +95,15 @@ def load(path: str = LIB_PATH):
         "gsp2_autotune": (C.c_int, [_P, _P, _P, C.c_int32, _P, C.POINTER(TuneReport)]),
         "gsp2_density_reuse": (C.c_int, [_P, _P, _P, _P, C.POINTER(C.c_int32), _P, C.POINTER(C.c_int32)]),
         "gsp2_threshold_graph": (C.c_int, [_P, _P, C.c_double, _P, _P, _P, C.c_int64, C.POINTER(C.c_int64)]),
+        "gsp2_create_shard": (C.c_int, [C.c_int64, _P, _P, C.c_int64, _P, C.c_int32, _P, _P, _P, C.c_int32,
+                                        C.POINTER(Options), C.POINTER(_P)]),
+        "gsp2_assign_parts": (C.c_int, [_P, C.c_int32, C.c_int32, _P, _P]),
+        "gsp2_shard_info": (C.c_int, [_P, _P, _P, _P]),
+        "gsp2_shard_exchanges": (C.c_int, [_P, C.c_int32, C.c_int32, C.POINTER(C.c_int32)]),
+        "gsp2_shard_begin": (C.c_int, [_P, _P, _P, _P, C.c_int32, C.c_int32, _P, _P]),
+        "gsp2_shard_decide": (C.c_int, [_P, C.c_int32, _P, C.c_int32, _P]),
+        "gsp2_shard_step": (C.c_int, [_P, C.c_int32, _P, _P]),
+        "gsp2_shard_end": (C.c_int, [_P, _P]),
         "gsp2_last_error": (C.c_char_p, [_P]),
         "gsp2_destroy": (None, [_P]),
     }
@@ -149,15 +158,15 @@ class GSP2:
         grp = None if g_rowptr is None else np.ascontiguousarray(g_rowptr, np.int64)
         gci = None if g_colind is None else np.ascontiguousarray(g_colind, np.int32)
         h = _P()
-        st = L.gsp2_create(self.n, _ptr(self._keep[0]), _ptr(self._keep[1]), self.nocc, _ptr(self._keep[2]),
-                           self.nparts, _ptr(grp), _ptr(gci), C.byref(o), C.byref(h))
+        st = self._create(L, grp, gci, o, h)
         if st != OK:
             raise GSP2Error(st, L.gsp2_last_error(None).decode())
         self._h = h
         self.nnz_h = int(self._keep[0][-1])
         info = PlanInfo()
-        s = np.empty(self.nparts, np.int32)
-        c = np.empty(self.nparts, np.int32)
+        self._check(L.gsp2_plan_query(h, C.byref(info), None, None))
+        s = np.empty(info.nparts, np.int32)
+        c = np.empty(info.nparts, np.int32)
         self._check(L.gsp2_plan_query(h, C.byref(info), _ptr(s), _ptr(c)))
         self.info = info
         self.part_sizes, self.part_cores = s, c
@@ -178,6 +187,10 @@ class GSP2:
             self.bind(device)
 
     # -- plumbing
+    def _create(self, L, grp, gci, o, h):
+        return L.gsp2_create(self.n, _ptr(self._keep[0]), _ptr(self._keep[1]), self.nocc, _ptr(self._keep[2]),
+                             self.nparts, _ptr(grp), _ptr(gci), C.byref(o), C.byref(h))
+
     def _check(self, st):
         if st != OK:
             raise GSP2Error(st, self._lib.gsp2_last_error(self._h).decode())
