@@ -18,6 +18,7 @@ from .gsp2 import (  # noqa: F401
     stop_now,
     tail_alpha,
     gsp2,
+    gsp2_tail,
     GSP2Result,
     eig_projector,
     sp2_map_on_spectrum,

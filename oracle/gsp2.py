@@ -176,15 +176,15 @@ def core_halo(g_rowptr, g_colind, part, nparts, which=None):
     (Section 2.2).  The subproblem's vertex list is S_k = core_k followed by halo_k.
     `which` lists the parts to build (default all, in order)."""
     part = np.asarray(part)
+    g_colind = np.asarray(g_colind)
     out = []
     for k in (range(nparts) if which is None else which):
         core = np.nonzero(part == k)[0]
         if core.size == 0:
             raise ValueError(f"part {k} is empty")
-        nbrs = set()
-        for u in core:
-            nbrs.update(int(v) for v in g_colind[g_rowptr[u]:g_rowptr[u + 1]])
-        halo = np.array(sorted(v for v in nbrs if part[v] != k), dtype=np.int64)
+        # every neighbour of every core vertex, once (np.unique sorts them)
+        nbrs = np.unique(np.concatenate([g_colind[g_rowptr[u]:g_rowptr[u + 1]] for u in core]))
+        halo = nbrs[part[nbrs] != k].astype(np.int64)
         out.append((core.astype(np.int64), halo))
     return out
 
@@ -218,14 +218,20 @@ class GSP2Result:
         return P
 
     def p_on_pattern(self, colptr, rowind):
-        """P values in the core-column CSC layout given by (colptr, rowind)."""
+        """P values in the core-column CSC layout given by (colptr, rowind): column g = S_k[j]
+        (core j of part k) at stored row r holds X_k[t, j], t the position of r in S_k."""
         vals = np.empty(int(colptr[-1]))
+        rowind = np.asarray(rowind)
+        loc = np.full(self.n, -1, np.int64)  # global vertex -> position in the current S_k
         for S, c, X in zip(self.S, self.ncore, self.X):
-            loc = {int(g): t for t, g in enumerate(S)}
+            loc[S] = np.arange(len(S))
             for j in range(c):
                 g = int(S[j])
-                rows = rowind[colptr[g]:colptr[g + 1]]
-                vals[colptr[g]:colptr[g + 1]] = X[[loc[int(r)] for r in rows], j]
+                t = loc[rowind[colptr[g]:colptr[g + 1]]]
+                if np.any(t < 0):
+                    raise ValueError(f"column {g}: a stored row lies outside S_k")
+                vals[colptr[g]:colptr[g + 1]] = X[t, j]
+            loc[S] = -1
         return vals
 
 
@@ -293,6 +299,24 @@ def gsp2(n, rowptr, colind, vals, nocc, part, nparts, g_rowptr=None, g_colind=No
             t = 0
     return GSP2Result(n=n, S=S, ncore=ncore, X=X, alphas=used, traces=traces, idem=idem,
                       bounds=(eps_min, eps_max), iterates=its)
+
+
+def gsp2_tail(res: GSP2Result, nocc, tail_steps):
+    """The optional alternating tail (module notes) applied to a finished G-SP2 run without
+    one: `tail_steps` more steps on every part, the first branch from the trace rule on the
+    last global core trace, each further one the opposite.  Gives what gsp2(...,
+    tail_steps=tail_steps) gives, without repeating the loop; `res` is left unchanged."""
+    X = list(res.X)
+    traces, idem, used = list(res.traces), list(res.idem), list(res.alphas)
+    for t in range(tail_steps):
+        a = tail_alpha(t, traces[-1], used[-1], nocc)
+        idem.append(traces[-1] - float(sum(float(np.sum(np.einsum("ij,ji->i", m[:c, :], m[:, :c])))
+                                           for m, c in zip(X, res.ncore))))
+        X = [sp2_step(x, a) for x in X]
+        used.append(a)
+        traces.append(float(sum(float(np.sum(np.diag(m)[:c])) for m, c in zip(X, res.ncore))))
+    return GSP2Result(n=res.n, S=res.S, ncore=res.ncore, X=X, alphas=used, traces=traces, idem=idem,
+                      bounds=res.bounds)
 
 
 # --------------------------------------------------------------------------------------

@@ -11,7 +11,9 @@ Sections 3.1-3.2) are not available, so every workload here is synthetic:
   H_ab = -exp(-r / 1.5 Angstrom) * B_ab with B_ab = (R + R^T)/2, R ~ U[-1, 1]^{4x4},
   H_ba = H_ab^T; intra-site off-diagonal elements are zero;
 * recursive coordinate bisection of the sites into parts (all four orbitals of a
-  site share a part), standing in for the METIS partitions of Section 2.2;
+  site share a part), standing in for the METIS partitions of Section 2.2; median splits
+  give equal cores, weighted splits uneven ones (the spread of subproblem sizes Fig. 3
+  shows);
 * the dependency graph G_tau (Section 2.2) is built from locality: orbitals are
   adjacent when their sites are closer than a radius R_g, the localisation-radius
   construction mentioned at the end of Section 2.2.  R_g is chosen per workload so
@@ -134,12 +136,21 @@ def make_hamiltonian(n_sites: int, seed: int = 1234, density: float = 0.1,
     return coords, rowptr, colind, v
 
 
-def rcb_partition(coords: np.ndarray, nparts: int) -> np.ndarray:
+def rcb_partition(coords: np.ndarray, nparts: int, weights: np.ndarray | None = None) -> np.ndarray:
     """Recursive coordinate bisection of sites: split along the longest extent at the
-    (count-proportional) median, ties broken by site index.  Returns site -> part."""
+    (count-proportional) median, ties broken by site index.  With `weights` (one positive
+    number per part) each split gives the two sides sites in proportion to the summed
+    weights of their parts, so part k gets about weights[k] / sum(weights) of the sites
+    (uneven cores).  Returns site -> part."""
     n_sites = coords.shape[0]
     if nparts < 1 or nparts > n_sites:
         raise ValueError("nparts must be in [1, n_sites]")
+    wcum = None
+    if weights is not None:
+        w = np.asarray(weights, np.float64)
+        if w.shape != (nparts,) or np.any(~(w > 0)):
+            raise ValueError("weights must be nparts positive numbers")
+        wcum = np.concatenate([[0.0], np.cumsum(w)])
     site_part = np.empty(n_sites, np.int32)
     stack = [(np.arange(n_sites), 0, nparts)]
     while stack:
@@ -152,7 +163,8 @@ def rcb_partition(coords: np.ndarray, nparts: int) -> np.ndarray:
         ax = int(np.argmax(ext))
         order = np.lexsort((idx, pts[:, ax]))
         nl = npp // 2
-        nleft = int(round(len(idx) * nl / npp))
+        frac = nl / npp if wcum is None else (wcum[p0 + nl] - wcum[p0]) / (wcum[p0 + npp] - wcum[p0])
+        nleft = int(round(len(idx) * frac))
         nleft = min(max(nleft, nl), len(idx) - (npp - nl))
         stack.append((idx[order[nleft:]], p0 + nl, npp - nl))
         stack.append((idx[order[:nleft]], p0, nl))
@@ -247,25 +259,36 @@ WORKLOADS = {
     "crystal8k": dict(n_sites=2000, nparts=64, graph_radius=5.0, density=0.2),
     # the same at 512 orbitals, for the oracle
     "crystal512": dict(n_sites=128, nparts=8, graph_radius=3.5, density=0.2),
-    # 120,000 orbitals, 1,024 parts, sizes ~200-2,000
-    "tb120k": dict(n_sites=30000, nparts=1024, graph_radius=5.0),
+    # 120,000 orbitals, 1,024 parts of uneven cores (weights 4 + 76 u^2, u ~ U[0, 1]), sizes
+    # ~200-2,000 (152-1,960; 1st percentile 197)
+    "tb120k": dict(n_sites=30000, nparts=1024, graph_radius=5.0, core_weights=(4321, 4.0, 76.0)),
 }
 
 
+def core_weights(nparts: int, seed: int, lo: float, span: float) -> np.ndarray:
+    """Seeded part weights lo + span u^2, u ~ U[0, 1] (Philox): many small cores and a tail of
+    large ones, for the uneven-size workloads."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    return lo + span * rng.uniform(0.0, 1.0, nparts) ** 2
+
+
 def make_tb_system(n_sites: int, nparts: int, graph_radius: float, seed: int = 1234,
-                   name: str = "custom", density: float = 0.1) -> TBSystem:
+                   name: str = "custom", density: float = 0.1, weights: np.ndarray | None = None) -> TBSystem:
     coords, rowptr, colind, vals = make_hamiltonian(n_sites, seed=seed, density=density)
-    site_part = rcb_partition(coords, nparts)
+    site_part = rcb_partition(coords, nparts, weights)
     part = np.repeat(site_part, ORBS_PER_SITE).astype(np.int32)
     g_rowptr, g_colind = locality_graph(coords, graph_radius)
     n = n_sites * ORBS_PER_SITE
     return TBSystem(name=name, n_sites=n_sites, n=n, nocc=2 * n_sites, rowptr=rowptr,
                     colind=colind, vals=vals, coords=coords, part=part, nparts=nparts,
                     g_rowptr=g_rowptr, g_colind=g_colind,
-                    meta=dict(seed=seed, graph_radius=graph_radius, density=density))
+                    meta=dict(seed=seed, graph_radius=graph_radius, density=density,
+                              uneven=weights is not None))
 
 
 def make_workload(name: str, seed: int = 1234) -> TBSystem:
     w = WORKLOADS[name]
+    cw = w.get("core_weights")
+    weights = None if cw is None else core_weights(w["nparts"], *cw)
     return make_tb_system(w["n_sites"], w["nparts"], w["graph_radius"], seed=seed, name=name,
-                          density=w.get("density", 0.1))
+                          density=w.get("density", 0.1), weights=weights)

@@ -316,6 +316,22 @@ def test_tail_steps_alternate_and_purify(tb512, tb512_dense):
     assert g3.alphas == g2.alphas and np.array_equal(g3.dense_p(), g2.dense_p())
 
 
+def test_tail_continuation_equals_a_run_with_the_tail(tb512):
+    """gsp2_tail appends the alternating tail to a finished run: the same branches, traces,
+    idempotency history and iterates as one run with tail_steps (the large-size checks
+    use it to get both results from one loop)."""
+    args = (tb512.n, tb512.rowptr, tb512.colind, tb512.vals, tb512.nocc, tb512.part, tb512.nparts,
+            tb512.g_rowptr, tb512.g_colind)
+    g0 = oracle.gsp2(*args)
+    for tail in (1, 2, 3):
+        g2 = oracle.gsp2(*args, tail_steps=tail)
+        c2 = oracle.gsp2_tail(g0, tb512.nocc, tail)
+        assert c2.alphas == g2.alphas and c2.traces == g2.traces and c2.idem == g2.idem
+        for a, b in zip(c2.X, g2.X):
+            np.testing.assert_array_equal(a, b)
+    assert len(g0.alphas) == len(oracle.gsp2_tail(g0, tb512.nocc, 2).alphas) - 2  # g0 untouched
+
+
 def test_seed_on_pattern_and_core_halo_subset_agree_with_the_dense_forms():
     """The pattern-based seed equals the dense-Pbar seed, and core_halo for a subset of
     parts equals those entries of the full list (the forms the large-size checks use)."""
