@@ -303,6 +303,38 @@ gsp2_status gsp2_autotune(gsp2_handle h, const double* d_hvals, double* d_pvals,
  */
 gsp2_status gsp2_backward(gsp2_handle h, const double* d_pbar, double* d_hbar, void* stream);
 
+/* ---------------------------------------------------------------- re-partitioning
+ *
+ * Between SCF or MD steps the graph G_tau is refreshed from the new P (Section 1.1, Fig. 1;
+ * gsp2_threshold_graph) and may be re-partitioned before the next plan is built.  The cost
+ * Section 2.2 gives to a partition is Eq. 5, C = sum_i (c_i + h_i)^3 (core plus halo of
+ * every part: the dense work of one squaring).  Host only; no device memory. */
+typedef enum {
+  GSP2_PARTITION_AUTO = -1,       /* every method that applies; the smallest Eq. 5 cost wins
+                                     (ties: the lower method) */
+  GSP2_PARTITION_BLOCK = 0,       /* Section 2.3: consecutive indices, sizes differing by at
+                                     most one, the larger parts first */
+  GSP2_PARTITION_GRAPH_ORDER = 1, /* the same blocks over a breadth-first order of G_tau (each
+                                     component from a far vertex, neighbours ascending) */
+  GSP2_PARTITION_RCB = 2          /* recursive coordinate bisection over `coords` (longest
+                                     extent, count-proportional split, ties by index) */
+} gsp2_partition_method;
+
+/* Eq. 5 cost of a partition of G_tau (CSR as for gsp2_create; self loops ignored).
+ *  part     host int32[n] in [0, nparts)
+ *  cost     output, sum_i (c_i + h_i)^3
+ *  sizes    host int32[nparts] or NULL: c_i + h_i
+ * GSP2_E_ARG for a bad graph or part id. */
+gsp2_status gsp2_partition_cost(int64_t n, const int64_t* g_rowptr, const int32_t* g_colind, const int32_t* part,
+                                int32_t nparts, double* cost, int32_t* sizes);
+
+/* A partition of G_tau into nparts non-empty parts (1 <= nparts <= n) by `method`
+ * (gsp2_partition_method).  coords: host double[3 n] (x, y, z per vertex) or NULL; needed
+ * by GSP2_PARTITION_RCB, used by AUTO when given.  part: host int32[n], output; chosen and
+ * cost (may be NULL): the method used and its Eq. 5 cost.  Deterministic. */
+gsp2_status gsp2_partition(int64_t n, const int64_t* g_rowptr, const int32_t* g_colind, int32_t nparts,
+                           int32_t method, const double* coords, int32_t* part, int32_t* chosen, double* cost);
+
 /* ---------------------------------------------------------------- shard plans
  *
  * One problem's parts split over several GPUs, one process (and plan) per GPU.  Parts are

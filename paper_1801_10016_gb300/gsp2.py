@@ -104,6 +104,9 @@ def load(path: str = LIB_PATH):
         "gsp2_shard_decide": (C.c_int, [_P, C.c_int32, _P, C.c_int32, _P]),
         "gsp2_shard_step": (C.c_int, [_P, C.c_int32, _P, _P]),
         "gsp2_shard_end": (C.c_int, [_P, _P]),
+        "gsp2_partition_cost": (C.c_int, [C.c_int64, _P, _P, _P, C.c_int32, C.POINTER(C.c_double), _P]),
+        "gsp2_partition": (C.c_int, [C.c_int64, _P, _P, C.c_int32, C.c_int32, _P, _P, C.POINTER(C.c_int32),
+                                     C.POINTER(C.c_double)]),
         "gsp2_last_error": (C.c_char_p, [_P]),
         "gsp2_destroy": (None, [_P]),
     }
@@ -133,6 +136,44 @@ def _stream_ptr(stream=None):
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
     return C.c_void_p(s.cuda_stream)
+
+
+PARTITION_METHODS = {"auto": -1, "block": 0, "graph_order": 1, "rcb": 2}
+
+
+def partition_cost(g_rowptr, g_colind, part, nparts):
+    """Eq. 5 cost sum_i (c_i + h_i)^3 of a partition of G_tau, and the sizes c_i + h_i
+    (gsp2_partition_cost)."""
+    L = load()
+    rp = np.ascontiguousarray(g_rowptr, np.int64)
+    ci = np.ascontiguousarray(g_colind, np.int32)
+    pa = np.ascontiguousarray(part, np.int32)
+    sizes = np.empty(int(nparts), np.int32)
+    cost = C.c_double()
+    st = L.gsp2_partition_cost(rp.size - 1, _ptr(rp), _ptr(ci), _ptr(pa), int(nparts), C.byref(cost), _ptr(sizes))
+    if st != OK:
+        raise GSP2Error(st, "gsp2_partition_cost: bad graph or part ids")
+    return cost.value, sizes
+
+
+def partition(g_rowptr, g_colind, nparts, method="auto", coords=None):
+    """A partition of G_tau into nparts parts (gsp2_partition): block (Section 2.3), block over a
+    breadth-first graph order, or coordinate bisection (coords [n, 3]); "auto" keeps the one
+    with the smallest Eq. 5 cost.  Returns (part int32[n], method name, cost)."""
+    L = load()
+    rp = np.ascontiguousarray(g_rowptr, np.int64)
+    ci = np.ascontiguousarray(g_colind, np.int32)
+    n = rp.size - 1
+    xyz = None if coords is None else np.ascontiguousarray(coords, np.float64).reshape(n, 3)
+    part = np.empty(n, np.int32)
+    chosen = C.c_int32()
+    cost = C.c_double()
+    st = L.gsp2_partition(n, _ptr(rp), _ptr(ci), int(nparts), PARTITION_METHODS[method], _ptr(xyz), _ptr(part),
+                          C.byref(chosen), C.byref(cost))
+    if st != OK:
+        raise GSP2Error(st, "gsp2_partition: bad graph, nparts or coordinates")
+    names = {v: k for k, v in PARTITION_METHODS.items()}
+    return part, names[chosen.value], cost.value
 
 
 class GSP2:

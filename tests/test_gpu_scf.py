@@ -79,3 +79,34 @@ def test_threshold_graph_and_replan(g):
     print(f"refreshed graph: {len(ci)} entries (was {len(s.g_colind)}), sizes {nxt.part_sizes.min()}-"
           f"{nxt.part_sizes.max()}, max|dP| vs oracle {err:.3e}")
     assert err <= 1e-10
+
+
+def test_refresh_repartitions_by_the_eq5_cost_and_replans(g):
+    """Section 1.1 / Fig. 1: after P, G_tau is rebuilt from it and re-partitioned before the
+    next plan.  The partition is the one of smallest Eq. 5 cost among the block partition
+    of Section 2.3, blocks over a graph order and coordinate bisection; the plan built on
+    the refreshed graph and the new partition matches the oracle on the same graph and
+    partition."""
+    import torch
+    from synth.tb import ORBS_PER_SITE
+    s = make_workload("tb4k")
+    plan = plan_for(g, s)
+    h = torch.from_numpy(s.vals).to("cuda:0")
+    p = plan.density(h)
+    rp, ci = plan.threshold_graph(p, 1e-4)
+    xyz = np.repeat(s.coords, ORBS_PER_SITE, axis=0)
+    costs = {m: g.partition(rp, ci, s.nparts, m, coords=xyz)[2] for m in ("block", "graph_order", "rcb")}
+    part, method, cost = g.partition(rp, ci, s.nparts, "auto", coords=xyz)
+    assert cost == min(costs.values()) and costs[method] == cost
+    assert g.partition_cost(rp, ci, part, s.nparts)[0] == cost
+    assert np.bincount(part, minlength=s.nparts).min() >= 1
+    nxt = g.GSP2(s.n, s.rowptr, s.colind, s.nocc, part, s.nparts, rp, ci, device="cuda:0", ckpt_every=0,
+                 precision="fp64e")
+    pn = nxt.density(h).cpu().numpy()
+    st, _ = nxt.status()
+    assert st == 0
+    ref = oracle.gsp2(s.n, s.rowptr, s.colind, s.vals, s.nocc, part, s.nparts, rp, ci)
+    err = float(np.max(np.abs(pn - ref.p_on_pattern(nxt.p_colptr, nxt.p_rowind))))
+    print(f"re-partitioned ({method}): Eq. 5 costs {costs}, sizes {nxt.part_sizes.min()}-{nxt.part_sizes.max()}, "
+          f"max|dP| vs oracle {err:.3e}")
+    assert err <= 1e-10
