@@ -118,6 +118,16 @@ def oracle_build_seconds(s, max_steps):
     return time.perf_counter() - t0, r
 
 
+def workload_config(args, s, sizes, world):
+    """The `config` both arms print: the workload and how it is timed (identical keys and
+    values in the two arms; what differs between them is reported outside `config`)."""
+    return {"workload": args.workload, "n": int(s.n), "nocc": int(s.nocc), "parts": int(s.nparts),
+            "part_size_min": int(sizes.min()), "part_size_max": int(sizes.max()),
+            "result_precision": "fp64" if args.precision in ("fp64", "fp64e") else args.precision,
+            "l2": "flushed (256 MB write) between timed P-builds; the arenas also exceed L2",
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
 def run_reference(args):
     """Reference arm: the CPU oracle, as it stands, on the host cores."""
     rank, world, _ = dist_env()
@@ -130,20 +140,32 @@ def run_reference(args):
     t_full, ref = oracle_build_seconds(s, args.max_steps)
     ch = oracle.core_halo(s.g_rowptr, s.g_colind, s.part, s.nparts)
     sizes = np.array([len(c) + len(h) for c, h in ch], dtype=float)
-    # bounded sample per step: the oracle replays that sequence (Section 2.1) on every
-    # `stride`-th part; throughput is scaled by the sample's share of sum s^3
-    stride = max(1, int(args.ref_stride))
-    sample = np.arange(0, s.nparts, stride)
-    frac = float(np.sum(sizes[sample] ** 3) / np.sum(sizes ** 3))
     import scipy.sparse as sp
     H = sp.csr_matrix((s.vals, s.colind, s.rowptr), shape=(s.n, s.n))
 
+    def replay(k):
+        S = np.concatenate(ch[k])
+        X = oracle.initial_guess(H[S][:, S].toarray(), *ref.bounds)
+        for a in ref.alphas:
+            X = oracle.sp2_step(X, a)
+
+    # untimed calibration: every part's replay timed once, so that a sample's share of a
+    # whole P-build is its share of the measured time (not of sum s^3, which leaves out the
+    # per-part costs that weigh more on small parts)
+    t_part = np.empty(s.nparts)
+    for k in range(s.nparts):
+        t0 = time.perf_counter()
+        replay(k)
+        t_part[k] = time.perf_counter() - t0
+    # bounded sample per step: the oracle replays its sequence (Section 2.1) on every
+    # `stride`-th part; a step is that fraction of a P-build
+    stride = max(1, int(args.ref_stride))
+    sample = np.arange(0, s.nparts, stride)
+    frac = float(np.sum(t_part[sample]) / np.sum(t_part))
+
     def one_step():
         for k in sample:
-            S = np.concatenate(ch[k])
-            X = oracle.initial_guess(H[S][:, S].toarray(), *ref.bounds)
-            for a in ref.alphas:
-                X = oracle.sp2_step(X, a)
+            replay(k)
     for _ in range(args.warmup):
         one_step()
     times = []
@@ -151,20 +173,21 @@ def run_reference(args):
         t0 = time.perf_counter()
         one_step()
         times.append(time.perf_counter() - t0)
-    per_build = sum(times) / len(times) / frac
-    v = 1.0 / per_build
+    step_s = sum(times) / len(times)
+    v = frac / step_s  # P-builds per second
     cores = os.cpu_count()
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * per_build, "higher_is_better": True,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * step_s, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "n": int(s.n), "nocc": int(s.nocc), "parts": int(s.nparts),
-                       "part_size_min": int(sizes.min()), "part_size_max": int(sizes.max()),
-                       "result_precision": "fp64", "arith": "fp64 (numpy/BLAS dgemm)",
-                       "sp2_steps": len(ref.alphas), "l2": "host CPU caches (no GPU)", "parallelism": "single"},
+            "config": workload_config(args, s, sizes, world),
+            "arith": "fp64 (numpy/BLAS dgemm)", "sp2_steps": len(ref.alphas),
+            "units_per_step": frac,
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"oracle replay of its own {len(ref.alphas)}-step sequence on every "
-                                       f"{stride}-th part ({len(sample)} of {s.nparts}, {frac:.3f} of sum s^3), "
-                                       f"scaled to a full P-build; full oracle build took {t_full:.1f} s"},
+                             "sample": f"each step: the oracle's replay of its own {len(ref.alphas)}-step sequence "
+                                       f"on every {stride}-th part ({len(sample)} of {s.nparts}), {frac:.3f} of a "
+                                       f"P-build by the parts' measured times ({float(np.sum(sizes[sample] ** 3) / np.sum(sizes ** 3)):.3f} "
+                                       f"of sum s^3); one full oracle build took {t_full:.1f} s "
+                                       f"({1.0 / t_full:.4f} P-builds/s)"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -484,16 +507,12 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp64": "f64", "fp64e": "f64 (bf16 digit products, int64 sums)"}.get(args.precision, args.precision),
         "data": "synthetic",
-        "config": {"workload": args.workload, "n": int(s.n), "nocc": int(s.nocc), "parts": int(s.nparts),
-                   "part_size_min": int(sizes.min()), "part_size_max": int(sizes.max()),
-                   "result_precision": "fp64" if args.precision in ("fp64", "fp64e") else args.precision,
-                   "arith": args.precision, "sp2_steps": int(steps_applied),
-                   "l2": "flushed (256 MB write) between timed P-builds; the arenas also exceed L2",
-                   "parallelism": "replicas" if world > 1 else "single",
-                   "adjoint_checkpoints": "off (forward P-builds only)",
-                   "schedule": {"tc_schedule": int(plan.info.tc_schedule), "tile_order": int(plan.info.tile_order),
-                                "autotuned": tune is not None,
-                                "candidates_ms_per_build": None if tune is None else tune["candidates"]}},
+        "config": workload_config(args, s, sizes, world),
+        "arith": args.precision, "sp2_steps": int(steps_applied),
+        "adjoint_checkpoints": "off (forward P-builds only)",
+        "schedule": {"tc_schedule": int(plan.info.tc_schedule), "tile_order": int(plan.info.tile_order),
+                     "autotuned": tune is not None,
+                     "candidates_ms_per_build": None if tune is None else tune["candidates"]},
         "tflops_dgemm_equiv": dgemm_equiv * steps_applied / (ms_per_step / 1e3) / 1e12,
         "roofline": roof,
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(plan.nnz_h * 8),
