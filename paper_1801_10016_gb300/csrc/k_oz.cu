@@ -346,7 +346,11 @@ __device__ __forceinline__ uint32_t oz_group_col(int d) {
 // The MMAs of one stage for the groups d0 <= d < d1, fully unrolled: every pair (q, d - q)
 // of a group into the group's accumulator, descriptors formed by adding compile-time
 // offsets to the stage's base descriptors (the 14-bit address field cannot carry: shared
-// addresses stay below 2^18).
+// addresses stay below 2^18).  The products are issued A digit by A digit: the products of
+// A digit q (one per group d >= q) follow one another and share their A operand through the
+// collector buffer, so each A digit tile is read from shared memory once per K = 16 slice
+// instead of once per product (the MMAs' shared-memory reads, A and B, set the pace of the
+// tensor pipe otherwise).  Every accumulator's first product is the one with q = 0.
 template <int D0, int D1>
 __device__ __forceinline__ void oz_issue_stage(uint32_t tmem, uint64_t da, uint64_t db, uint32_t adv_a,
                                                uint32_t adv_b, uint32_t idesc, bool first_k) {
@@ -354,11 +358,15 @@ __device__ __forceinline__ void oz_issue_stage(uint32_t tmem, uint64_t da, uint6
 #pragma unroll
   for (int kk = 0; kk < OZ_BK / 16; ++kk) {  // K = 16 slices of the stage
 #pragma unroll
-    for (int d = D0; d < D1; ++d) {
+    for (int q = 0; q < D1; ++q) {
+      const int dlo = q > D0 ? q : D0;  // groups holding a product of A digit q
 #pragma unroll
-      for (int q = 0; q <= d; ++q)
-        mma<0>(tmem + oz_group_col(d), da + (uint64_t)q * step + (uint64_t)(adv_a * kk),
-               db + (uint64_t)(d - q) * step + (uint64_t)(adv_b * kk), idesc, (q > 0 || kk > 0 || !first_k) ? 1u : 0u);
+      for (int d = dlo; d < D1; ++d) {
+        const int op = (D1 - dlo == 1) ? 0 : (d == dlo ? 1 : (d == D1 - 1 ? 3 : 2));
+        mma_f16_col(op, tmem + oz_group_col(d), da + (uint64_t)q * step + (uint64_t)(adv_a * kk),
+                    db + (uint64_t)(d - q) * step + (uint64_t)(adv_b * kk), idesc,
+                    (q > 0 || kk > 0 || !first_k) ? 1u : 0u);
+      }
     }
   }
 }
