@@ -181,9 +181,10 @@ __global__ void __launch_bounds__(256, 2) square_tc_kernel(TcStepArgs a) {
 #pragma unroll
       for (int kk = 0; kk < NMMA; ++kk) {
         const uint64_t adv = (uint64_t)((kk * KMMA * ES) >> 4);
-        mma<KIND>(tmem, ah + adv, bh + adv, IDESC, (kb > 0 || kk > 0) ? 1u : 0u);
+        // hi x hi and hi x lo share their A operand (collector buffer)
+        mma_col<KIND>(NPROD == 3 ? 1 : 0, tmem, ah + adv, bh + adv, IDESC, (kb > 0 || kk > 0) ? 1u : 0u);
         if (NPROD == 3) {
-          mma<KIND>(tmem, ah + adv, bl + adv, IDESC, 1u);
+          mma_col<KIND>(3, tmem, ah + adv, bl + adv, IDESC, 1u);
           mma<KIND>(tmem, al + adv, bh + adv, IDESC, 1u);
         }
       }
@@ -537,9 +538,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
 #pragma unroll
           for (int kk = 0; kk < NMMA; ++kk) {
             const uint64_t aa = (uint64_t)(adv_a * kk), ab = (uint64_t)(adv_b * kk);
-            mma<KIND>(d, ah + aa, bh + ab, idesc, (kb > 0 || v > 0 || kk > 0) ? 1u : 0u);
+            // hi x hi and hi x lo share their A operand (collector buffer)
+            mma_col<KIND>(NPROD == 3 ? 1 : 0, d, ah + aa, bh + ab, idesc, (kb > 0 || v > 0 || kk > 0) ? 1u : 0u);
             if (NPROD == 3) {
-              mma<KIND>(d, ah + aa, bl + ab, idesc, 1u);
+              mma_col<KIND>(3, d, ah + aa, bl + ab, idesc, 1u);
               mma<KIND>(d, al + aa, bh + ab, idesc, 1u);
             }
           }
@@ -869,9 +871,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_wide_kernel(TcStepArg
 #pragma unroll
         for (int kk = 0; kk < NMMA; ++kk) {
           const uint64_t adv = (uint64_t)((kk * KMMA * ES) >> 4);
-          mma<KIND>(d, ah + adv, bh + adv, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+          // hi x hi and hi x lo share their A operand (collector buffer)
+          mma_col<KIND>(NPROD == 3 ? 1 : 0, d, ah + adv, bh + adv, idesc, (kb > 0 || kk > 0) ? 1u : 0u);
           if (NPROD == 3) {
-            mma<KIND>(d, ah + adv, bl + adv, idesc, 1u);
+            mma_col<KIND>(3, d, ah + adv, bl + adv, idesc, 1u);
             mma<KIND>(d, al + adv, bh + adv, idesc, 1u);
           }
         }

@@ -153,30 +153,33 @@ __device__ __forceinline__ void mma(uint32_t tmem, uint64_t a, uint64_t b, uint3
   }
 }
 
-// kind::f16 MMA that keeps its A operand in the tensor core's collector buffer for the next
-// MMAs with the same A: op 1 reads A from shared memory and keeps it (fill), 2 reuses the
-// kept A (use), 3 reuses it for the last time (lastuse); 0 reads A and does not keep it.
+// MMA that keeps its A operand in the tensor core's collector buffer for the next MMAs
+// with the same A: op 1 reads A from shared memory and keeps it (fill), 2 reuses the kept
+// A (use), 3 reuses it for the last time (lastuse); 0 reads A and does not keep it.
 // Consecutive MMAs that share A then read it from shared memory once.
+#define GSP2_MMA_COL(KINDSTR, OPSTR)                                                                  \
+  asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"                                       \
+               " tcgen05.mma.cta_group::1.kind::" KINDSTR ".collector::a::" OPSTR " [%0], %1, %2, %3, p;\n}\n" ::"r"( \
+                   tmem),                                                                           \
+               "l"(a), "l"(b), "r"(idesc), "r"(acc))
+template <int KIND>
+__device__ __forceinline__ void mma_col(int op, uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  if (op == 0) {
+    mma<KIND>(tmem, a, b, idesc, acc);
+  } else if (KIND != 1) {
+    if (op == 1) GSP2_MMA_COL("f16", "fill");
+    else if (op == 2) GSP2_MMA_COL("f16", "use");
+    else GSP2_MMA_COL("f16", "lastuse");
+  } else {
+    if (op == 1) GSP2_MMA_COL("tf32", "fill");
+    else if (op == 2) GSP2_MMA_COL("tf32", "use");
+    else GSP2_MMA_COL("tf32", "lastuse");
+  }
+}
+#undef GSP2_MMA_COL
 __device__ __forceinline__ void mma_f16_col(int op, uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc,
                                             uint32_t acc) {
-  if (op == 1) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc));
-  } else if (op == 2) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16.collector::a::use [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc));
-  } else if (op == 3) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(acc));
-  } else {
-    mma<0>(tmem, a, b, idesc, acc);
-  }
+  mma_col<0>(op, tmem, a, b, idesc, acc);
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
