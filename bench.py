@@ -33,7 +33,9 @@ NOMINAL = {"bf16": 2250.0, "tf32": 1100.0, "fp64": 1.25}
 # DRAM bytes per launch of the dominant kernel from one ncu capture (workload, precision);
 # entries are removed when the kernel changes (fp64e: the emulated step changed after its
 # last capture, so its traffic is reported as null)
-TRAFFIC = {("tb30k", "fp64"): 2.80e9}
+# DRAM bytes (read + write) per launch of the step kernel, from ncu captures (see profiles/):
+# the FP64 step on tb30k directly, the emulated step on tb8k scaled by arena elements (x 4.98)
+TRAFFIC = {("tb30k", "fp64"): 2.80e9, ("tb30k", "fp64e"): 1.058e9 * 191545344 / 38469632}
 
 
 def dist_env():
