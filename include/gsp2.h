@@ -120,7 +120,13 @@ typedef struct {
                               128 x 128; 1 = 128 x 256 (two upper tiles of a row block per
                               MMA, N = 256, halving the loads of the A operand); set by
                               gsp2_autotune */
-  int32_t reserved[1];
+  int32_t split_k;         /* adjoint reverse steps of FP64_EMU plans: 1 = each upper tile's product
+                              over K = 2s as two work items, one per half ([Xbar | X] x [X ; Xbar]:
+                              Xbar X and X Xbar), added as 64-bit integers by the second to finish
+                              (more, shorter items for small problems); 0 = one item per tile;
+                              -1 (default) = 1 when the plan has at most 512 upper 128-tiles.  Needs
+                              2 x 128 KB of workspace per tile.  The sum is exact: the result does
+                              not depend on the choice */
 } gsp2_options;
 
 /* Per-call report, read back by gsp2_sync_status. */
@@ -157,6 +163,7 @@ typedef struct {
   int32_t tc_schedule;     /* schedule, tile order and tile shape in use (options, or gsp2_autotune's choice) */
   int32_t tile_order;
   int32_t tile_shape;
+  int32_t split_k;         /* 1 if the emulated adjoint's reverse steps split K (resolved option) */
 } gsp2_plan_info;
 
 /* Fill `opt` with the defaults listed above. */

@@ -44,6 +44,7 @@ struct WsLayout {
   size_t adj_maps, adj_maps_mn;   // CUtensorMap[k + 1][OZ_SLICES][nparts]
   size_t adj_norm, adj_sig;       // double[sum of s] (the seed's row norms), int32[nparts]
   size_t adj_normf;               // float[sum of s]: the reverse steps' row norms on their grid
+  size_t split_acc, split_cnt;    // split-K reverse steps: int64[2 tiles][128 x 128], uint32[tiles]
   // FP32 adjoint of the low-precision plans: FP16 (hi, lo) operand arenas aop[2 set + lo],
   // sets 0..S-1 for rebuilt iterates, S and S + 1 for Xbar's ping-pong (in the FP64 tail
   // arenas d[0], d[1], which the backward does not need); their tensor maps; Xbar's
@@ -98,6 +99,7 @@ struct gsp2_plan {
   int32_t nslots_tc = 0;
   int32_t total_steps = 0;  // FP64 path: max_steps + tail steps (static launches of a call)
   bool use_oz = false;      // FP64 products from BF16 digits (fp64e steps or emulated tail steps)
+  bool adj_split = false;   // emulated adjoint: reverse steps split K into its two halves
   std::vector<int64_t> pcolptr;
   std::vector<int32_t> prowind;
   int32_t nslots = 0, max_s = 0;
@@ -230,6 +232,7 @@ extern "C" void gsp2_default_options(gsp2_options* o) {
   o->ckpt_every = -1;
   o->use_graph = 1;
   o->fp64_tail_emulated = 1;
+  o->split_k = -1;
 }
 
 extern "C" const char* gsp2_last_error(gsp2_handle h) { return h ? h->err.c_str() : t_create_err.c_str(); }
@@ -359,6 +362,13 @@ static void build_layout(gsp2_plan* h) {
   }
   L.adj_dig.clear();
   L.adj_maps = L.adj_maps_mn = L.adj_norm = L.adj_sig = L.adj_normf = 0;
+  L.split_acc = L.split_cnt = 0;
+  h->adj_split = h->opt.precision == GSP2_PREC_FP64_EMU && k > 0 &&
+                 (h->opt.split_k == 1 || (h->opt.split_k < 0 && h->tc_tiles.size() <= 512));
+  if (h->adj_split) {
+    L.split_acc = take(2 * h->tc_tiles.size() * 128 * 128 * sizeof(long long));
+    L.split_cnt = take(h->tc_tiles.size() * sizeof(uint32_t));
+  }
   if (h->use_oz && k > 0) {
     for (int set = 0; set <= k; ++set)
       for (int t = 0; t < OZ_SLICES; ++t) L.adj_dig.push_back(take((size_t)h->arena_elems * 2));
@@ -408,6 +418,7 @@ static gsp2_status create_plan(int64_t n, const int64_t* rowptr, const int32_t* 
     if (o.tc_schedule < 0 || o.tc_schedule > 1) return bail(GSP2_E_ARG, "tc_schedule must be 0 or 1");
     if (o.tile_order < 0 || o.tile_order > 1) return bail(GSP2_E_ARG, "tile_order must be 0 or 1");
     if (o.tile_shape < 0 || o.tile_shape > 1) return bail(GSP2_E_ARG, "tile_shape must be 0 or 1");
+    if (o.split_k < -1 || o.split_k > 1) return bail(GSP2_E_ARG, "split_k must be -1, 0 or 1");
     if (o.lp_tail_steps > 0 && (fp64_like(o.precision) || o.precision == GSP2_PREC_FP32))
       return bail(GSP2_E_ARG, "lp_tail_steps needs a tensor-core precision");
     if (o.ckpt_every < -1) return bail(GSP2_E_ARG, "ckpt_every must be >= -1");
@@ -656,6 +667,7 @@ extern "C" gsp2_status gsp2_plan_query(gsp2_handle h, gsp2_plan_info* info, int3
     info->tc_schedule = h->opt.tc_schedule;
     info->tile_order = h->opt.tile_order;
     info->tile_shape = h->opt.tile_shape;
+    info->split_k = h->adj_split ? 1 : 0;
   }
   for (int32_t k = 0; k < h->nparts; ++k) {
     if (s) s[k] = h->parts[k].s;
@@ -799,6 +811,8 @@ extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t byt
       }
       CU(h, up(L.adj_maps, amaps.data(), amaps.size()));
       CU(h, up(L.adj_maps_mn, amaps_mn.data(), amaps_mn.size()));
+      // the split reverse steps' per-tile counters start at zero (each step leaves them so)
+      if (L.split_cnt) CU(h, cudaMemsetAsync(h->ws + L.split_cnt, 0, h->tc_tiles.size() * sizeof(uint32_t), s));
       // Xbar's arenas start zeroed, so that padding the seed does not write stays zero
       CU(h, cudaMemsetAsync(h->ws + L.xb0, 0, (size_t)h->arena_elems * sizeof(double), s));
       CU(h, cudaMemsetAsync(h->ws + L.xb1, 0, (size_t)h->arena_elems * sizeof(double), s));
@@ -1585,6 +1599,11 @@ static gsp2_status enqueue_backward_emu(gsp2_plan* h, const double* pbar, double
       a.xin = xb0;
       a.xout = xb1;
       a.step = i;
+      if (h->adj_split) {
+        a.split = 1;
+        a.split_acc = (long long*)(w + L.split_acc);
+        a.split_cnt = (uint32_t*)(w + L.split_cnt);
+      }
       CU(h, launch_oz_step(a, h->num_sms, s, true));  // also leaves the new Xbar's scales in sig
       if (i > 1) CU(h, launch_oz_digits(parts, gbl_ld, ngb, xb0, xb1, i, 0, set(k), sig, st, s));
     }

@@ -436,6 +436,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
   const uint32_t bars = base + OZ_STAGES * OZ_STAGE_B;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sb + OZ_STAGES * OZ_STAGE_B + 8 * (2 * OZ_STAGES + 4));
   int* s_err = reinterpret_cast<int*>(tmem_slot + 1);
+  int* s_half = reinterpret_cast<int*>(tmem_slot + 2);  // split adjoint: halves of the tile done before
   double2* red = reinterpret_cast<double2*>(sb + OZ_STAGES * OZ_STAGE_B + 8 * (2 * OZ_STAGES + 4) + 16);
   auto full = [&](int s) { return bars + 8u * s; };
   auto empty = [&](int s) { return bars + 8u * (OZ_STAGES + s); };
@@ -450,6 +451,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
   const CUtensorMap* maps_mn = reinterpret_cast<const CUtensorMap*>(a.maps_mn) + (size_t)dbi * T * a.nparts;
   const CUtensorMap* maps_b = reinterpret_cast<const CUtensorMap*>(a.maps_b);
   const CUtensorMap* maps_mn_b = reinterpret_cast<const CUtensorMap*>(a.maps_mn_b);
+  // work items: the upper tiles, or (adjoint with split K) each tile's two K halves
+  const bool split = ADJ && a.split;
+  const int nitems = split ? 2 * a.ntiles : a.ntiles;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < OZ_STAGES; ++s) {
@@ -475,7 +479,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
   if (warp == 0 && lane == 0) {
     uint32_t g = 0;
     bool bad = false;
-    for (int ti = blockIdx.x; ti < a.ntiles && !bad; ti += gridDim.x) {
+    for (int it = blockIdx.x; it < nitems && !bad; it += gridDim.x) {
+      const int ti = split ? it >> 1 : it, half = split ? it & 1 : -1;
       const Tile t = a.tiles[ti];
       const int sz = a.parts[t.part].s;
       const bool dg = !ADJ && t.ti == t.tj;  // X X on a diagonal tile: B is A
@@ -483,7 +488,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
         const int nd = pass == 0 ? T : OZ_SPLIT;  // digits the pass multiplies
         const int sub = oz_slices_per_stage(nd, dg);
         const int nk = (sz + sub * OZ_BK - 1) / (sub * OZ_BK);
-        for (int kb = 0; kb < (ADJ ? 2 * nk : nk); ++kb, ++g) {
+        const int kb0 = half == 1 ? nk : 0, kb1 = ADJ ? (half == 0 ? nk : 2 * nk) : nk;
+        for (int kb = kb0; kb < kb1; ++kb, ++g) {
           // the adjoint's first nk stages multiply Xbar (rows I) by X (rows J), the rest X by Xbar
           const bool h2 = ADJ && kb >= nk;
           const int kq = h2 ? kb - nk : kb;
@@ -529,9 +535,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
     }
   } else if (warp == 1 && lane == 0) {
     uint32_t g = 0;
-    int u = 0;  // tiles done by this CTA
+    int u = 0;  // items done by this CTA
     bool bad = false;
-    for (int ti = blockIdx.x; ti < a.ntiles && !bad; ti += gridDim.x, ++u) {
+    for (int it = blockIdx.x; it < nitems && !bad; it += gridDim.x, ++u) {
+      const int ti = split ? it >> 1 : it, half = split ? it & 1 : -1;
       const Tile t = a.tiles[ti];
       const int sz = a.parts[t.part].s;
       const bool dg = !ADJ && t.ti == t.tj;
@@ -539,6 +546,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
         const int nd = pass == 0 ? T : OZ_SPLIT;
         const int sub = oz_slices_per_stage(nd, dg);
         const int nk = (sz + sub * OZ_BK - 1) / (sub * OZ_BK);
+        const int kb0 = half == 1 ? nk : 0, kb1 = ADJ ? (half == 0 ? nk : 2 * nk) : nk;
         // the high pass reuses the columns of the previous tile's low groups, the low pass
         // those of this tile's high groups: wait until the epilogue has read them
         const bool ready = pass == 0 ? (u == 0 || mbar_wait(aempty(1), (u - 1) & 1, abort_flag))
@@ -548,7 +556,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
           break;
         }
         tc_fence_after();
-        for (int kb = 0; kb < (ADJ ? 2 * nk : nk); ++kb, ++g) {
+        for (int kb = kb0; kb < kb1; ++kb, ++g) {
           const int kq = (ADJ && kb >= nk) ? kb - nk : kb;
           const int s = g % OZ_STAGES;
           if (!mbar_wait(full(s), (g / OZ_STAGES) & 1, abort_flag)) {
@@ -570,8 +578,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
               IDESC | ((uint32_t)(oz_tile_cols(sz, t.tj) >> 3) << 17) | ((amn ? 1u : 0u) << 15) | ((bmn ? 1u : 0u) << 16);
           for (int u = 0; u < sub; ++u) {  // the stage's K slices, nd tiles apart
             const uint64_t off = (uint64_t)(u * nd) * (OZ_DTILE >> 4);
-            if (pass == 0) oz_issue_stage<OZ_SPLIT, T>(tmem, da + off, db + off, adv_a, adv_b, idesc, kb == 0 && u == 0);
-            else oz_issue_stage<0, OZ_SPLIT>(tmem, da + off, db + off, adv_a, adv_b, idesc, kb == 0 && u == 0);
+            if (pass == 0) oz_issue_stage<OZ_SPLIT, T>(tmem, da + off, db + off, adv_a, adv_b, idesc, kb == kb0 && u == 0);
+            else oz_issue_stage<0, OZ_SPLIT>(tmem, da + off, db + off, adv_a, adv_b, idesc, kb == kb0 && u == 0);
           }
           mma_commit(empty(s));
         }
@@ -588,7 +596,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
     const int quarter = warp & 3, colq = (warp - 4) >> 2;
     const int m = quarter * 32 + lane;
     const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-    long long* acc = a.acc + (size_t)blockIdx.x * (128 * 128);
+    long long* const cta_acc = a.acc + (size_t)blockIdx.x * (128 * 128);
     int8_t alf;
     if (ADJ || rec) alf = a.ctl.alpha[step];  // the recorded branch of step `step`
     else if (a.mode == SQ_TAIL_FIRST) alf = (a.ctl.traces[step - 1] <= (double)a.ctl.nocc) ? (int8_t)1 : (int8_t)-1;
@@ -602,7 +610,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
       xout = const_cast<double*>(a.xin);
     }
     int u = 0;
-    for (int ti = blockIdx.x; ti < a.ntiles; ti += gridDim.x, ++u) {
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x, ++u) {
+      const int ti = split ? it >> 1 : it;
+      // a split item's 64-bit partial goes to its own tile of split_acc, which the item that
+      // finishes the tile reads; otherwise the sums wait in this CTA's scratch tile
+      long long* const acc = split ? a.split_acc + (size_t)it * (128 * 128) : cta_acc;
       const Tile t = a.tiles[ti];
       const PartDesc p = a.parts[t.part];
       const int64_t ld = p.ld;
@@ -651,6 +663,22 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
         if (lane == 0) mbar_arrive(aempty(pass));
       }
       if (!ok) *s_err = 1;
+      // split K: the first half to finish leaves its partial; the second adds the first's
+      // (64-bit integers: exact, so which one finishes first does not matter) and forms the tile
+      const long long* other = nullptr;
+      if (split) {
+        __threadfence();
+        asm volatile("bar.sync 1, %0;\n" ::"n"(32 * OZ_EPI_WARPS) : "memory");
+        if (warp == 4 && lane == 0) {
+          const unsigned int before = atomicAdd(&a.split_cnt[ti], 1u);
+          if (before == 1u) a.split_cnt[ti] = 0u;  // both halves in: clear for the next launch
+          *s_half = (int)before;
+        }
+        asm volatile("bar.sync 1, %0;\n" ::"n"(32 * OZ_EPI_WARPS) : "memory");
+        if (*s_half == 0) continue;
+        __threadfence();
+        other = a.split_acc + (size_t)(it ^ 1) * (128 * 128);
+      }
       // final pass of the tile: X_new on the 2^-56 grid, FP64 master, digits, traces (the
       // adjoint: Xbar_new, FP64 only); column writes are coalesced across the warp.  Only
       // tiles on or above the diagonal are kept (the next step reads the rest MN-major from
@@ -664,6 +692,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
         if (cl >= ncols || cl + 16 <= cskip) continue;
         const int cbase = c0 + cl;
         const long long* zp = acc + (size_t)cl * 128 + m;
+        const long long* zo = other ? other + (size_t)cl * 128 + m : nullptr;
         float coln[16];  // adjoint: squares of the entries (r, c) for the norms of rows c
 #pragma unroll
         for (int j = 0; j < 16; ++j) coln[j] = 0.0f;
@@ -676,7 +705,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
 #pragma unroll
           for (int w = 0; w < 4; ++w) {
             const int j = sub * 4 + w;
-            yv[w] = zp[(size_t)j * 128];
+            yv[w] = zp[(size_t)j * 128] + (zo ? __ldcg(zo + (size_t)j * 128) : 0ll);
             xv[w] = alf > 0 ? __ldg(xin + p.off + (int64_t)(cbase + j) * ld + r) : 0.0;
           }
           double xn4[4];
@@ -834,7 +863,8 @@ cudaError_t launch_oz_step(const OzStepArgs& a, int grid, cudaStream_t s, bool a
   auto kern = adjoint ? oz_step_kernel<true> : oz_step_kernel<false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
   if (e != cudaSuccess) return e;
-  int gr = grid < a.ntiles ? grid : a.ntiles;
+  const int nitems = (adjoint && a.split) ? 2 * a.ntiles : a.ntiles;
+  int gr = grid < nitems ? grid : nitems;
   if (gr > OZ_MAX_GRID) gr = OZ_MAX_GRID;  // one scratch tile per CTA
   kern<<<gr, OZ_THREADS, OZ_SMEM, s>>>(a);
   return cudaGetLastError();

@@ -37,7 +37,7 @@ class Options(C.Structure):
                 ("precision", C.c_int32), ("fp64_tail_steps", C.c_int32), ("ckpt_every", C.c_int32),
                 ("use_graph", C.c_int32), ("time_steps", C.c_int32), ("lp_tail_steps", C.c_int32),
                 ("tc_schedule", C.c_int32), ("report_idem", C.c_int32), ("fp64_tail_emulated", C.c_int32),
-                ("tile_order", C.c_int32), ("tile_shape", C.c_int32), ("reserved", C.c_int32 * 1)]
+                ("tile_order", C.c_int32), ("tile_shape", C.c_int32), ("split_k", C.c_int32)]
 
 
 class Report(C.Structure):
@@ -51,7 +51,8 @@ class PlanInfo(C.Structure):
                 ("sum_s", C.c_int64), ("sum_s2", C.c_double), ("sum_s3", C.c_double), ("nnz_h", C.c_int64),
                 ("nnz_p", C.c_int64), ("arena_elems", C.c_int64), ("ntiles", C.c_int64), ("tile", C.c_int32),
                 ("ld_pad", C.c_int32), ("step_launches", C.c_int32), ("fp64_tail_steps", C.c_int32),
-                ("tc_schedule", C.c_int32), ("tile_order", C.c_int32), ("tile_shape", C.c_int32)]
+                ("tc_schedule", C.c_int32), ("tile_order", C.c_int32), ("tile_shape", C.c_int32),
+                ("split_k", C.c_int32)]
 
 
 class TuneReport(C.Structure):
