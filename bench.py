@@ -511,6 +511,10 @@ def run_ours(args):
         "data": "synthetic",
         "config": workload_config(args, s, sizes, world),
         "arith": args.precision, "sp2_steps": int(steps_applied),
+        # the per-step figures carry over to workloads that need more purification steps
+        # (the paper quotes 40-50 multiplications per P; these gapped systems stop after fewer)
+        "ms_per_sp2_step": avg_launch_ms,
+        "sp2_steps_per_s": 1e3 / avg_launch_ms if avg_launch_ms else None,
         "adjoint_checkpoints": "off (forward P-builds only)",
         "schedule": {"tc_schedule": int(plan.info.tc_schedule), "tile_order": int(plan.info.tile_order),
                      "autotuned": tune is not None,
