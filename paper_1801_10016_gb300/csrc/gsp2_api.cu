@@ -1073,12 +1073,17 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
     const bool lp_upper = kind == 0 || kind == 2;
     OzStepArgs toz = oz_args(h, ctl);
     if (on()) {
-      CU(h, launch_convert((const float* const*)(w + L.master_of_step), d[0], h->arena_elems, st, s));
-      if (lp_upper && T > 0 && !h->use_oz)
-        CU(h, launch_symmetrize(parts, (const Tile*)(w + L.tc_tiles), (int)h->tc_tiles.size(), nullptr, d[0], st, s));
-      if (h->use_oz)
-        CU(h, launch_oz_slice(parts, (const ColBlock*)(w + L.gblocks_ld), (int)h->gblocks_ld.size(), d[0], toz.digits,
-                              st, s));
+      if (h->use_oz) {
+        // the emulated tail reads the rows on or above each diagonal block: conversion and
+        // digits of those rows in one pass
+        CU(h, launch_oz_convert_slice(parts, (const ColBlock*)(w + L.gblocks_ld), (int)h->gblocks_ld.size(),
+                                      (const float* const*)(w + L.master_of_step), d[0], toz.digits, st, s));
+      } else {
+        CU(h, launch_convert((const float* const*)(w + L.master_of_step), d[0], h->arena_elems, st, s));
+        if (lp_upper && T > 0)
+          CU(h, launch_symmetrize(parts, (const Tile*)(w + L.tc_tiles), (int)h->tc_tiles.size(), nullptr, d[0], st,
+                                  s));
+      }
     }
     for (int t = 0; t < T; ++t, ++seg) {
       if (!on()) continue;

@@ -50,6 +50,10 @@ cudaError_t launch_convert(const float* const* master_of_step, double* out, int6
 cudaError_t launch_oz_slice(const PartDesc* parts, const ColBlock* blocks, int nblocks, const double* X,
                             const OzSlices* digits, const DevState* st, cudaStream_t s);
 cudaError_t launch_oz_step(const OzStepArgs& a, int grid, cudaStream_t s, bool adjoint = false);
+// the last FP32 iterate of a low-precision run as FP64 master and digits (upper rows only)
+cudaError_t launch_oz_convert_slice(const PartDesc* parts, const ColBlock* blocks, int nblocks,
+                                    const float* const* master_of_step, double* X, const OzSlices* digits,
+                                    const DevState* st, cudaStream_t s);
 // gather with Eq. 1 and the digits of X0 in one pass (emulated path)
 cudaError_t launch_oz_gather(const PartDesc* parts, const ColBlock* blocks, int nblocks, const int32_t* Sall,
                              const int64_t* rowptr, const int32_t* colind, const double* vals, double* arena,

@@ -128,6 +128,32 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const PartDesc* __restric
   for (int r = lane; r < p.ld; r += 32) store_digits(sl.s, cbase + r, to_fixed(X[cbase + r]));
 }
 
+// Start of the emulated FP64 tail of a low-precision run: the last FP32 iterate (found on the
+// device from the step count) converted to the FP64 master and written as digits, in one pass
+// over the rows on or above each column's diagonal block, the only ones the emulated steps
+// read (and the scatter, which reads the upper tiles).  One warp per column up to ld.
+__global__ void __launch_bounds__(256) oz_convert_slice_kernel(const PartDesc* __restrict__ parts,
+                                                               const ColBlock* __restrict__ blocks,
+                                                               const float* const* __restrict__ master_of_step,
+                                                               double* __restrict__ X, OzSlices d0, OzSlices d1,
+                                                               const DevState* st) {
+  const int n = st->steps;
+  const OzSlices& sl = (n & 1) ? d1 : d0;
+  const float* __restrict__ in = master_of_step[n];
+  const ColBlock b = blocks[blockIdx.x];
+  const PartDesc p = parts[b.part];
+  const int lane = threadIdx.x & 31;
+  const int j = b.j0 + (threadIdx.x >> 5);
+  if (j >= p.ld) return;
+  const int rows = min(p.ld, (j / 128 + 1) * 128);
+  const int64_t cbase = p.off + (int64_t)j * p.ld;
+  for (int r = lane; r < rows; r += 32) {
+    const double x = (double)in[cbase + r];
+    X[cbase + r] = x;
+    store_digits(sl.s, cbase + r, to_fixed(x));
+  }
+}
+
 // Gather of the emulated path: Eq. 1 and the digits of X0 in one pass.  One warp per column
 // j < ld assembles the rows of column j of X0 on or above its diagonal block, the only ones
 // the emulated steps read (zeros, then the stored entries of row S_j of H that fall there,
@@ -851,6 +877,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
       a.ctl.st->counter = 0;
     }
   }
+}
+
+cudaError_t launch_oz_convert_slice(const PartDesc* parts, const ColBlock* blocks, int nblocks,
+                                    const float* const* master_of_step, double* X, const OzSlices* digits,
+                                    const DevState* st, cudaStream_t s) {
+  oz_convert_slice_kernel<<<nblocks, 256, 0, s>>>(parts, blocks, master_of_step, X, digits[0], digits[1], st);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_oz_slice(const PartDesc* parts, const ColBlock* blocks, int nblocks, const double* X,
