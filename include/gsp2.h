@@ -111,11 +111,12 @@ typedef struct {
                                  the products rebuilt from BF16 digits (as GSP2_PREC_FP64_EMU),
                                  0 on the FP64 units */
   int32_t tile_order;      /* order of the 128x128 tiles walked by the persistent kernels
-                              (tensor-core steps with tc_schedule = 0, FP64_EMU steps): 0 (default)
-                              parts by descending size, tile t to CTA t mod (number of SMs);
-                              1 = the same list reversed in every other round of SMs, so that
-                              each SM's share of the uneven tiles evens out; set by
-                              gsp2_autotune */
+                              (tensor-core steps with tc_schedule = 0, FP64_EMU steps): 0 = parts
+                              by descending size, tile t to CTA t mod (number of SMs); 1 (default)
+                              = the same list reversed in every other round of SMs, so that
+                              each SM's share of the uneven tiles evens out (with few tiles per
+                              SM, the CTA that took the largest tile of one round takes the
+                              smallest of the next); set by gsp2_autotune */
   int32_t tile_shape;      /* output tiles of the persistent tensor-core steps: 0 (default)
                               128 x 128; 1 = 128 x 256 (two upper tiles of a row block per
                               MMA, N = 256, halving the loads of the A operand); set by

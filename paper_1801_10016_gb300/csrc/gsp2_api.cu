@@ -45,6 +45,7 @@ struct WsLayout {
   size_t adj_norm, adj_sig;       // double[sum of s] (the seed's row norms), int32[nparts]
   size_t adj_normf;               // float[sum of s]: the reverse steps' row norms on their grid
   size_t split_acc, split_cnt;    // split-K reverse steps: int64[2 tiles][128 x 128], uint32[tiles]
+  size_t split_items;             // int32[2 tiles]: the order in which the CTAs take the items
   // FP32 adjoint of the low-precision plans: FP16 (hi, lo) operand arenas aop[2 set + lo],
   // sets 0..S-1 for rebuilt iterates, S and S + 1 for Xbar's ping-pong (in the FP64 tail
   // arenas d[0], d[1], which the backward does not need); their tensor maps; Xbar's
@@ -93,6 +94,7 @@ struct gsp2_plan {
   std::vector<int8_t> tc_wide_nb;
   std::vector<Tile> tcw_order;             // tc_wide / tc_wide_nb in the order of opt.tile_order
   std::vector<int8_t> tcw_nb_order;
+  std::vector<int32_t> split_items;        // split reverse steps: item codes 2 i + half (i into tc_order)
   std::vector<size_t> mf_of_step;          // low precision: FP32 arena of iterate i (checkpoints or ping-pong)
   std::vector<ColBlock> gblocks, sblocks;  // gather (to nt*64) and scatter (cores) columns
   std::vector<ColBlock> gblocks_ld;        // low-precision gather: every column up to ld
@@ -232,6 +234,7 @@ extern "C" void gsp2_default_options(gsp2_options* o) {
   o->ckpt_every = -1;
   o->use_graph = 1;
   o->fp64_tail_emulated = 1;
+  o->tile_order = 1;
   o->split_k = -1;
 }
 
@@ -362,12 +365,13 @@ static void build_layout(gsp2_plan* h) {
   }
   L.adj_dig.clear();
   L.adj_maps = L.adj_maps_mn = L.adj_norm = L.adj_sig = L.adj_normf = 0;
-  L.split_acc = L.split_cnt = 0;
+  L.split_acc = L.split_cnt = L.split_items = 0;
   h->adj_split = h->opt.precision == GSP2_PREC_FP64_EMU && k > 0 &&
                  (h->opt.split_k == 1 || (h->opt.split_k < 0 && h->tc_tiles.size() <= 512));
   if (h->adj_split) {
     L.split_acc = take(2 * h->tc_tiles.size() * 128 * 128 * sizeof(long long));
     L.split_cnt = take(h->tc_tiles.size() * sizeof(uint32_t));
+    L.split_items = take(2 * h->tc_tiles.size() * sizeof(int32_t));
   }
   if (h->use_oz && k > 0) {
     for (int set = 0; set <= k; ++set)
@@ -717,6 +721,34 @@ static void order_tc_tiles(gsp2_plan* h, int grid) {
   serpentine(h->tcw_nb_order);
 }
 
+// Work items of the split reverse steps (both K halves of every upper tile, codes 2 i + half
+// with i indexing tc_order): by descending cost (the tile's K = 2 s_k times its columns), in
+// rounds of `grid` items dealt like the tiles (tile_order 1: every other round reversed).
+static void order_split_items(gsp2_plan* h, int grid) {
+  const size_t nt = h->tc_order.size();
+  std::vector<int32_t> idx(nt);
+  std::iota(idx.begin(), idx.end(), 0);
+  auto cost = [&](int32_t i) {
+    const Tile& t = h->tc_order[i];
+    const int32_t s = h->parts[t.part].s;
+    return (double)s * (double)std::min(128, s - t.tj * 128);
+  };
+  std::stable_sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) { return cost(a) > cost(b); });
+  h->split_items.clear();
+  for (int32_t i : idx) {
+    h->split_items.push_back(2 * i);
+    h->split_items.push_back(2 * i + 1);
+  }
+  if (h->opt.tile_order == 1 && grid >= 2) {
+    const size_t g = (size_t)grid;
+    for (size_t r = 0; r * g < h->split_items.size(); ++r)
+      if (r & 1) {
+        const size_t b = r * g, e = std::min(b + g, h->split_items.size());
+        std::reverse(h->split_items.begin() + b, h->split_items.begin() + e);
+      }
+  }
+}
+
 extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t bytes, void* stream) {
   if (!usable(h)) return fail(h, GSP2_E_ARG, "invalid handle");
   if (!d_ws || ((uintptr_t)d_ws & 255)) return fail(h, GSP2_E_WORKSPACE, "workspace NULL or not 256-byte aligned");
@@ -759,6 +791,10 @@ extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t byt
   CU(h, up(L.tc_tiles, h->tc_order.data(), h->tc_order.size() * sizeof(Tile)));
   CU(h, up(L.tc_wide, h->tcw_order.data(), h->tcw_order.size() * sizeof(Tile)));
   CU(h, up(L.tc_wide_nb, h->tcw_nb_order.data(), h->tcw_nb_order.size()));
+  if (L.split_items) {
+    order_split_items(h, h->num_sms);
+    CU(h, up(L.split_items, h->split_items.data(), h->split_items.size() * sizeof(int32_t)));
+  }
   CU(h, up(L.gblocks_ld, h->gblocks_ld.data(), h->gblocks_ld.size() * sizeof(ColBlock)));
   if (h->use_oz) {
     void* enc = nullptr;
@@ -1338,6 +1374,11 @@ extern "C" gsp2_status gsp2_autotune(gsp2_handle h, const double* d_hvals, doubl
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(h->ws + h->L.tc_wide_nb, h->tcw_nb_order.data(), h->tcw_nb_order.size(),
                           cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && h->L.split_items) {
+      order_split_items(h, h->num_sms);
+      e = cudaMemcpyAsync(h->ws + h->L.split_items, h->split_items.data(), h->split_items.size() * sizeof(int32_t),
+                          cudaMemcpyHostToDevice, s);
+    }
     return e != cudaSuccess ? e : cudaStreamSynchronize(s);  // the host vectors may change next round
   };
   std::vector<double> med(cand.size(), 0.0);
@@ -1608,6 +1649,7 @@ static gsp2_status enqueue_backward_emu(gsp2_plan* h, const double* pbar, double
         a.split = 1;
         a.split_acc = (long long*)(w + L.split_acc);
         a.split_cnt = (uint32_t*)(w + L.split_cnt);
+        a.split_items = (const int32_t*)(w + L.split_items);
       }
       CU(h, launch_oz_step(a, h->num_sms, s, true));  // also leaves the new Xbar's scales in sig
       if (i > 1) CU(h, launch_oz_digits(parts, gbl_ld, ngb, xb0, xb1, i, 0, set(k), sig, st, s));

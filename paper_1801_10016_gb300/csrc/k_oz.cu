@@ -506,7 +506,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
     uint32_t g = 0;
     bool bad = false;
     for (int it = blockIdx.x; it < nitems && !bad; it += gridDim.x) {
-      const int ti = split ? it >> 1 : it, half = split ? it & 1 : -1;
+      const int code = split ? a.split_items[it] : it;
+      const int ti = split ? code >> 1 : it, half = split ? code & 1 : -1;
       const Tile t = a.tiles[ti];
       const int sz = a.parts[t.part].s;
       const bool dg = !ADJ && t.ti == t.tj;  // X X on a diagonal tile: B is A
@@ -564,7 +565,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
     int u = 0;  // items done by this CTA
     bool bad = false;
     for (int it = blockIdx.x; it < nitems && !bad; it += gridDim.x, ++u) {
-      const int ti = split ? it >> 1 : it, half = split ? it & 1 : -1;
+      const int code = split ? a.split_items[it] : it;
+      const int ti = split ? code >> 1 : it, half = split ? code & 1 : -1;
       const Tile t = a.tiles[ti];
       const int sz = a.parts[t.part].s;
       const bool dg = !ADJ && t.ti == t.tj;
@@ -637,10 +639,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
     }
     int u = 0;
     for (int it = blockIdx.x; it < nitems; it += gridDim.x, ++u) {
-      const int ti = split ? it >> 1 : it;
+      const int code = split ? a.split_items[it] : it;
+      const int ti = split ? code >> 1 : it;
       // a split item's 64-bit partial goes to its own tile of split_acc, which the item that
       // finishes the tile reads; otherwise the sums wait in this CTA's scratch tile
-      long long* const acc = split ? a.split_acc + (size_t)it * (128 * 128) : cta_acc;
+      long long* const acc = split ? a.split_acc + (size_t)code * (128 * 128) : cta_acc;
       const Tile t = a.tiles[ti];
       const PartDesc p = a.parts[t.part];
       const int64_t ld = p.ld;
@@ -703,7 +706,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
         asm volatile("bar.sync 1, %0;\n" ::"n"(32 * OZ_EPI_WARPS) : "memory");
         if (*s_half == 0) continue;
         __threadfence();
-        other = a.split_acc + (size_t)(it ^ 1) * (128 * 128);
+        other = a.split_acc + (size_t)(code ^ 1) * (128 * 128);
       }
       // final pass of the tile: X_new on the 2^-56 grid, FP64 master, digits, traces (the
       // adjoint: Xbar_new, FP64 only); column writes are coalesced across the warp.  Only

@@ -136,7 +136,7 @@ def test_workspace_size_covers_two_arenas(g):
 
 def test_tile_order_option(g):
     s = make_tb_system(16, 2, 3.0, seed=5)
-    assert g.default_options().tile_order == 0
+    assert g.default_options().tile_order == 1
     for bad in (-1, 2):
         with pytest.raises(g.GSP2Error):
             _plan(g, s, tile_order=bad)
