@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(256, 2) adj_step_kernel(const PartDesc* __rest
 
 // dL/dH on the CSR pattern: for every stored (r, col), the sum over the parts k that
 // hold r (membership list of r) and col of -Xbar0_k[col, r] / (eps_max - eps_min), in
-// the fixed membership order.  One warp per row, lanes over the row's entries.  With
+// the fixed membership order (ascending part id).  One warp per row, lanes over the row's entries.  With
 // upper_block > 0 only the tiles of that edge on or above the diagonal hold Xbar0 (the
 // emulated adjoint); the symmetric entry is read from there.
 template <typename T>
@@ -186,12 +186,18 @@ __global__ void __launch_bounds__(256) adj_hbar_kernel(int64_t n, const int64_t*
     const int64_t m0 = memptr[r], m1 = memptr[r + 1];
     for (int64_t q = rowptr[r] + lane; q < rowptr[r + 1]; q += 32) {
       const int32_t col = colind[q];
+      // the parts holding both r and col: the intersection of their membership lists, both
+      // in ascending part order, walked as a merge (the same parts in the same order as a
+      // search of col in every S_k of r's list, so the same sum)
+      int64_t mc = memptr[col];
+      const int64_t mc1 = memptr[col + 1];
       double sum = 0.0;
-      for (int64_t m = m0; m < m1; ++m) {
-        const PartDesc p = parts[mempart[m]];
-        const int lc = find_local(Sall + p.soff, p.c, p.s, col);
-        if (lc < 0) continue;
-        const int lr = memloc[m];
+      for (int64_t m = m0; m < m1 && mc < mc1; ++m) {
+        const int32_t k = mempart[m];
+        while (mc < mc1 && mempart[mc] < k) ++mc;
+        if (mc == mc1 || mempart[mc] != k) continue;
+        const PartDesc p = parts[k];
+        const int lc = memloc[mc], lr = memloc[m];
         const bool swap = upper_block > 0 && lc / upper_block > lr / upper_block;
         sum += (double)XB[p.off + (swap ? (int64_t)lc * p.ld + lr : (int64_t)lr * p.ld + lc)];
       }
