@@ -121,13 +121,16 @@ typedef struct {
                               128 x 128; 1 = 128 x 256 (two upper tiles of a row block per
                               MMA, N = 256, halving the loads of the A operand); set by
                               gsp2_autotune */
-  int32_t split_k;         /* adjoint reverse steps of FP64_EMU plans: 1 = each upper tile's product
-                              over K = 2s as two work items, one per half ([Xbar | X] x [X ; Xbar]:
-                              Xbar X and X Xbar), added as 64-bit integers by the second to finish
-                              (more, shorter items for small problems); 0 = one item per tile;
-                              -1 (default) = 1 when the plan has at most 512 upper 128-tiles.  Needs
-                              2 x 128 KB of workspace per tile.  The sum is exact: the result does
-                              not depend on the choice */
+  int32_t split_k;         /* FP64_EMU steps: 1 = each upper tile's product as two work items, one
+                              per half of its K (forward and rebuilt steps: the two halves of the
+                              K stages; adjoint reverse steps: Xbar X and X Xbar), their 64-bit
+                              partial sums added by the second to finish (more, shorter items for
+                              small problems); 0 = one item per tile; -1 (default) = 1 when the
+                              plan has at most 512 upper 128-tiles.  Needs every part above 128
+                              orbitals (else 0) and 2 x 128 KB of workspace per tile; gsp2_autotune
+                              may turn it off.  The 64-bit sums are exact; the group sums of each
+                              half are rounded in FP32 like the whole K's, so results agree to the
+                              last bits only */
 } gsp2_options;
 
 /* Per-call report, read back by gsp2_sync_status. */
@@ -164,7 +167,7 @@ typedef struct {
   int32_t tc_schedule;     /* schedule, tile order and tile shape in use (options, or gsp2_autotune's choice) */
   int32_t tile_order;
   int32_t tile_shape;
-  int32_t split_k;         /* 1 if the emulated adjoint's reverse steps split K (resolved option) */
+  int32_t split_k;         /* 1 if the emulated steps split K into two work items (in use now) */
 } gsp2_plan_info;
 
 /* Fill `opt` with the defaults listed above. */
@@ -277,6 +280,7 @@ typedef struct {
   int32_t tile_order[8];
   int32_t tile_shape[8];
   double ms[8];         /* median device time of one density call, milliseconds */
+  int32_t split_k[8];   /* FP64_EMU: 1 if the candidate splits each tile's K into two work items */
 } gsp2_tune_report;
 
 /*

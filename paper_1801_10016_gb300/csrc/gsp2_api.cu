@@ -101,10 +101,11 @@ struct gsp2_plan {
   int32_t nslots_tc = 0;
   int32_t total_steps = 0;  // FP64 path: max_steps + tail steps (static launches of a call)
   bool use_oz = false;      // FP64 products from BF16 digits (fp64e steps or emulated tail steps)
-  bool adj_split = false;   // emulated adjoint: reverse steps split K into its two halves
+  bool split_ok = false;    // emulated steps: buffers for split-K work items are in the workspace
+  bool split_on = false;    // emulated steps split each tile's K into two work items
   std::vector<int64_t> pcolptr;
   std::vector<int32_t> prowind;
-  int32_t nslots = 0, max_s = 0;
+  int32_t nslots = 0, max_s = 0, min_s = 0;
   int64_t arena_elems = 0, sum_s = 0;
   double sum_s2 = 0, sum_s3 = 0;
   WsLayout L{};
@@ -366,9 +367,12 @@ static void build_layout(gsp2_plan* h) {
   L.adj_dig.clear();
   L.adj_maps = L.adj_maps_mn = L.adj_norm = L.adj_sig = L.adj_normf = 0;
   L.split_acc = L.split_cnt = L.split_items = 0;
-  h->adj_split = h->opt.precision == GSP2_PREC_FP64_EMU && k > 0 &&
-                 (h->opt.split_k == 1 || (h->opt.split_k < 0 && h->tc_tiles.size() <= 512));
-  if (h->adj_split) {
+  // split-K work items: FP64_EMU plans whose parts all exceed 128 orbitals (so that both K
+  // halves of every pass hold at least one stage)
+  h->split_ok = h->opt.precision == GSP2_PREC_FP64_EMU && h->min_s > 128 &&
+                (h->opt.split_k == 1 || (h->opt.split_k < 0 && h->tc_tiles.size() <= 512));
+  h->split_on = h->split_ok;
+  if (h->split_ok) {
     L.split_acc = take(2 * h->tc_tiles.size() * 128 * 128 * sizeof(long long));
     L.split_cnt = take(h->tc_tiles.size() * sizeof(uint32_t));
     L.split_items = take(2 * h->tc_tiles.size() * sizeof(int32_t));
@@ -509,6 +513,7 @@ static gsp2_status create_plan(int64_t n, const int64_t* rowptr, const int32_t* 
       off += (int64_t)d.ld * d.ld;
       soff += d.s;
       h->max_s = std::max(h->max_s, d.s);
+      h->min_s = kl == 0 ? d.s : std::min(h->min_s, d.s);
       h->sum_s2 += (double)d.s * d.s;
       h->sum_s3 += (double)d.s * d.s * d.s;
       h->S.insert(h->S.end(), core[k].begin(), core[k].end());
@@ -671,7 +676,7 @@ extern "C" gsp2_status gsp2_plan_query(gsp2_handle h, gsp2_plan_info* info, int3
     info->tc_schedule = h->opt.tc_schedule;
     info->tile_order = h->opt.tile_order;
     info->tile_shape = h->opt.tile_shape;
-    info->split_k = h->adj_split ? 1 : 0;
+    info->split_k = h->split_on ? 1 : 0;
   }
   for (int32_t k = 0; k < h->nparts; ++k) {
     if (s) s[k] = h->parts[k].s;
@@ -794,6 +799,8 @@ extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t byt
   if (L.split_items) {
     order_split_items(h, h->num_sms);
     CU(h, up(L.split_items, h->split_items.data(), h->split_items.size() * sizeof(int32_t)));
+    // the per-tile counters of split items start at zero (every launch leaves them so)
+    CU(h, cudaMemsetAsync(h->ws + L.split_cnt, 0, h->tc_tiles.size() * sizeof(uint32_t), s));
   }
   CU(h, up(L.gblocks_ld, h->gblocks_ld.data(), h->gblocks_ld.size() * sizeof(ColBlock)));
   if (h->use_oz) {
@@ -847,8 +854,6 @@ extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t byt
       }
       CU(h, up(L.adj_maps, amaps.data(), amaps.size()));
       CU(h, up(L.adj_maps_mn, amaps_mn.data(), amaps_mn.size()));
-      // the split reverse steps' per-tile counters start at zero (each step leaves them so)
-      if (L.split_cnt) CU(h, cudaMemsetAsync(h->ws + L.split_cnt, 0, h->tc_tiles.size() * sizeof(uint32_t), s));
       // Xbar's arenas start zeroed, so that padding the seed does not write stays zero
       CU(h, cudaMemsetAsync(h->ws + L.xb0, 0, (size_t)h->arena_elems * sizeof(double), s));
       CU(h, cudaMemsetAsync(h->ws + L.xb1, 0, (size_t)h->arena_elems * sizeof(double), s));
@@ -953,6 +958,12 @@ static OzStepArgs oz_args(gsp2_plan* h, const StepCtl& ctl) {
   a.nslots = h->nslots_tc;
   a.acc = (long long*)(w + L.oz_acc);
   a.ctl = ctl;
+  if (h->split_on) {
+    a.split = 1;
+    a.split_acc = (long long*)(w + L.split_acc);
+    a.split_cnt = (uint32_t*)(w + L.split_cnt);
+    a.split_items = (const int32_t*)(w + L.split_items);
+  }
   return a;
 }
 
@@ -1348,22 +1359,28 @@ extern "C" gsp2_status gsp2_autotune(gsp2_handle h, const double* d_hvals, doubl
   cudaStream_t s = (cudaStream_t)stream;
   // candidates (tc_schedule, tile_order) that change something for this precision
   struct Cand {
-    int sched, order, shape;
+    int sched, order, shape, split;
   };
   std::vector<Cand> cand;
   const int prec = h->opt.precision;
-  if (!fp64_like(prec) && prec_kind(prec) >= 0) cand = {{0, 0, 0}, {0, 1, 0}, {0, 0, 1}, {0, 1, 1}, {1, 0, 0}};
-  else if (prec == GSP2_PREC_FP64_EMU) cand = {{0, 0, 0}, {0, 1, 0}};
-  else cand = {{h->opt.tc_schedule, h->opt.tile_order, h->opt.tile_shape}};
+  const int sp = h->split_on ? 1 : 0;
+  if (!fp64_like(prec) && prec_kind(prec) >= 0)
+    cand = {{0, 0, 0, 0}, {0, 1, 0, 0}, {0, 0, 1, 0}, {0, 1, 1, 0}, {1, 0, 0, 0}};
+  else if (prec == GSP2_PREC_FP64_EMU && h->split_ok)
+    cand = {{0, 0, 0, 0}, {0, 1, 0, 0}, {0, 0, 0, 1}, {0, 1, 0, 1}};
+  else if (prec == GSP2_PREC_FP64_EMU) cand = {{0, 0, 0, 0}, {0, 1, 0, 0}};
+  else cand = {{h->opt.tc_schedule, h->opt.tile_order, h->opt.tile_shape, sp}};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CU(h, cudaEventCreate(&e0));
   CU(h, cudaEventCreate(&e1));
   auto apply = [&](const Cand& c) -> cudaError_t {
     // schedule and shape are part of the captured launches; the order only of the tile lists
-    if (c.sched != h->opt.tc_schedule || c.shape != h->opt.tile_shape) drop_graph(h);
+    if (c.sched != h->opt.tc_schedule || c.shape != h->opt.tile_shape || (c.split != 0) != h->split_on)
+      drop_graph(h);
     h->opt.tc_schedule = c.sched;
     h->opt.tile_order = c.order;
     h->opt.tile_shape = c.shape;
+    h->split_on = c.split != 0 && h->split_ok;
     order_tc_tiles(h, h->num_sms);
     if (h->tc_order.empty()) return cudaSuccess;
     cudaError_t e = cudaMemcpyAsync(h->ws + h->L.tc_tiles, h->tc_order.data(), h->tc_order.size() * sizeof(Tile),
@@ -1428,6 +1445,7 @@ extern "C" gsp2_status gsp2_autotune(gsp2_handle h, const double* d_hvals, doubl
       rep->tc_schedule[c] = cand[c].sched;
       rep->tile_order[c] = cand[c].order;
       rep->tile_shape[c] = cand[c].shape;
+      rep->split_k[c] = cand[c].split;
       rep->ms[c] = med[c];
     }
   }
@@ -1645,12 +1663,6 @@ static gsp2_status enqueue_backward_emu(gsp2_plan* h, const double* pbar, double
       a.xin = xb0;
       a.xout = xb1;
       a.step = i;
-      if (h->adj_split) {
-        a.split = 1;
-        a.split_acc = (long long*)(w + L.split_acc);
-        a.split_cnt = (uint32_t*)(w + L.split_cnt);
-        a.split_items = (const int32_t*)(w + L.split_items);
-      }
       CU(h, launch_oz_step(a, h->num_sms, s, true));  // also leaves the new Xbar's scales in sig
       if (i > 1) CU(h, launch_oz_digits(parts, gbl_ld, ngb, xb0, xb1, i, 0, set(k), sig, st, s));
     }

@@ -176,9 +176,10 @@ struct OzStepArgs {
   StepCtl ctl;
   int step;            // ignored in tail modes (step = steps applied + 1)
   int mode;            // SQ_FORWARD, SQ_RECOMPUTE, SQ_TAIL_FIRST or SQ_TAIL_NEXT
-  // adjoint with split K: the work item of code 2 t + h is the half h of upper tile t (h = 0:
-  // Xbar X, h = 1: X Xbar); each writes its 64-bit partial tile to split_acc[2 t + h] and the
-  // second of the two to finish (split_cnt[t], left at zero) adds both and forms the tile
+  // split K: the work item of code 2 t + h is the half h of upper tile t's product (adjoint:
+  // h = 0 Xbar X, h = 1 X Xbar; forward: the two halves of each pass's K stages); each writes
+  // its 64-bit partial tile to split_acc[2 t + h] and the second of the two to finish
+  // (split_cnt[t], left at zero) adds both and forms the tile (X_new, digits, traces)
   int split;
   long long* split_acc;  // [2 ntiles][128 x 128], indexed by item code 2 t + h
   uint32_t* split_cnt;   // [ntiles]

@@ -477,8 +477,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
   const CUtensorMap* maps_mn = reinterpret_cast<const CUtensorMap*>(a.maps_mn) + (size_t)dbi * T * a.nparts;
   const CUtensorMap* maps_b = reinterpret_cast<const CUtensorMap*>(a.maps_b);
   const CUtensorMap* maps_mn_b = reinterpret_cast<const CUtensorMap*>(a.maps_mn_b);
-  // work items: the upper tiles, or (adjoint with split K) each tile's two K halves
-  const bool split = ADJ && a.split;
+  // work items: the upper tiles, or (split K) each tile's two K halves
+  const bool split = a.split != 0;
   const int nitems = split ? 2 * a.ntiles : a.ntiles;
 
   if (threadIdx.x == 0) {
@@ -515,7 +515,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
         const int nd = pass == 0 ? T : OZ_SPLIT;  // digits the pass multiplies
         const int sub = oz_slices_per_stage(nd, dg);
         const int nk = (sz + sub * OZ_BK - 1) / (sub * OZ_BK);
-        const int kb0 = half == 1 ? nk : 0, kb1 = ADJ ? (half == 0 ? nk : 2 * nk) : nk;
+        // K stages of the item: the adjoint's halves are Xbar X and X Xbar, the forward's the
+        // two halves of the stages of the pass
+        const int kb0 = half < 1 ? 0 : (ADJ ? nk : (nk + 1) / 2);
+        const int kb1 = ADJ ? (half == 0 ? nk : 2 * nk) : (half == 0 ? (nk + 1) / 2 : nk);
         for (int kb = kb0; kb < kb1; ++kb, ++g) {
           // the adjoint's first nk stages multiply Xbar (rows I) by X (rows J), the rest X by Xbar
           const bool h2 = ADJ && kb >= nk;
@@ -574,7 +577,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
         const int nd = pass == 0 ? T : OZ_SPLIT;
         const int sub = oz_slices_per_stage(nd, dg);
         const int nk = (sz + sub * OZ_BK - 1) / (sub * OZ_BK);
-        const int kb0 = half == 1 ? nk : 0, kb1 = ADJ ? (half == 0 ? nk : 2 * nk) : nk;
+        // K stages of the item: the adjoint's halves are Xbar X and X Xbar, the forward's the
+        // two halves of the stages of the pass
+        const int kb0 = half < 1 ? 0 : (ADJ ? nk : (nk + 1) / 2);
+        const int kb1 = ADJ ? (half == 0 ? nk : 2 * nk) : (half == 0 ? (nk + 1) / 2 : nk);
         // the high pass reuses the columns of the previous tile's low groups, the low pass
         // those of this tile's high groups: wait until the epilogue has read them
         const bool ready = pass == 0 ? (u == 0 || mbar_wait(aempty(1), (u - 1) & 1, abort_flag))
@@ -899,7 +905,7 @@ cudaError_t launch_oz_step(const OzStepArgs& a, int grid, cudaStream_t s, bool a
   auto kern = adjoint ? oz_step_kernel<true> : oz_step_kernel<false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM);
   if (e != cudaSuccess) return e;
-  const int nitems = (adjoint && a.split) ? 2 * a.ntiles : a.ntiles;
+  const int nitems = a.split ? 2 * a.ntiles : a.ntiles;
   int gr = grid < nitems ? grid : nitems;
   if (gr > OZ_MAX_GRID) gr = OZ_MAX_GRID;  // one scratch tile per CTA
   kern<<<gr, OZ_THREADS, OZ_SMEM, s>>>(a);

@@ -57,7 +57,8 @@ class PlanInfo(C.Structure):
 
 class TuneReport(C.Structure):
     _fields_ = [("ncand", C.c_int32), ("chosen", C.c_int32), ("tc_schedule", C.c_int32 * 8),
-                ("tile_order", C.c_int32 * 8), ("tile_shape", C.c_int32 * 8), ("ms", C.c_double * 8)]
+                ("tile_order", C.c_int32 * 8), ("tile_shape", C.c_int32 * 8), ("ms", C.c_double * 8),
+                ("split_k", C.c_int32 * 8)]
 
 
 _lib = None
@@ -289,8 +290,8 @@ class GSP2:
         self._check(self._lib.gsp2_autotune(self._h, _tptr(h_vals.contiguous()), _tptr(out), int(trials),
                                             _stream_ptr(stream), C.byref(r)))
         self._refresh_info()
-        cands = [dict(tc_schedule=r.tc_schedule[i], tile_order=r.tile_order[i], tile_shape=r.tile_shape[i], ms=r.ms[i])
-                 for i in range(r.ncand)]
+        cands = [dict(tc_schedule=r.tc_schedule[i], tile_order=r.tile_order[i], tile_shape=r.tile_shape[i],
+                      split_k=r.split_k[i], ms=r.ms[i]) for i in range(r.ncand)]
         return dict(chosen=r.chosen, candidates=cands)
 
     def density_reuse(self, h_vals, alpha, nsteps, out=None, stream=None):

@@ -1,6 +1,6 @@
-"""The schedule autotuner and the tile orders it chooses between: every candidate computes
-bitwise the same P (a tile's arithmetic does not depend on the CTA that runs it), and the
-autotuner keeps a candidate it timed."""
+"""The schedule autotuner and the tile orders it chooses between: every tile order computes
+bitwise the same P (a tile's arithmetic does not depend on the CTA that runs it), split-K
+work items the same P to the last bits, and the autotuner keeps a candidate it timed."""
 
 import numpy as np
 import pytest
@@ -57,12 +57,37 @@ def test_autotune_keeps_a_timed_candidate(g, prec):
     plan, h, p0 = run(g, s, precision=prec)
     rep = plan.autotune(h, trials=2)
     cands = rep["candidates"]
-    assert len(cands) == {"tf32x3": 5, "fp16x3": 5, "fp64e": 2, "fp64": 1}[prec]
+    # fp64e on this plan (193 tiles, parts above 128 orbitals): both tile orders with and
+    # without split-K work items
+    assert len(cands) == {"tf32x3": 5, "fp16x3": 5, "fp64e": 4, "fp64": 1}[prec]
     assert all(c["ms"] > 0 for c in cands)
     best = cands[rep["chosen"]]
     assert best["ms"] == min(c["ms"] for c in cands)
-    assert (plan.info.tc_schedule, plan.info.tile_order, plan.info.tile_shape) == (
-        best["tc_schedule"], best["tile_order"], best["tile_shape"])
+    assert (plan.info.tc_schedule, plan.info.tile_order, plan.info.tile_shape, plan.info.split_k) == (
+        best["tc_schedule"], best["tile_order"], best["tile_shape"], best["split_k"])
     p1 = plan.density(h).cpu().numpy()
-    assert np.array_equal(p0, p1)
+    if best["split_k"] == 1:  # the default of this plan: bitwise the same
+        assert np.array_equal(p0, p1)
+    else:
+        assert np.max(np.abs(p0 - p1)) <= 1e-14
     print(prec, rep)
+
+
+def test_split_k_items_of_the_emulated_steps(g):
+    """Split-K work items (each tile's K stages in two halves whose 64-bit partials the
+    second to finish adds) against one item per tile: the same branch sequence and P to the
+    last bits (only the FP32 rounding of the low-order digit groups can differ), both tile
+    orders bitwise equal within each setting; plans with a part of 128 orbitals or fewer
+    never split."""
+    s = make_workload("tb4k")
+    pa, _, p_split = run(g, s, precision="fp64e", split_k=1)
+    pb, _, p_one = run(g, s, precision="fp64e", split_k=0)
+    assert pa.info.split_k == 1 and pb.info.split_k == 0
+    assert pa.history()["alphas"] == pb.history()["alphas"]
+    assert np.max(np.abs(p_split - p_one)) <= 1e-14
+    _, _, p_split0 = run(g, s, precision="fp64e", split_k=1, tile_order=0)
+    assert np.array_equal(p_split, p_split0)
+    from synth.tb import make_tb_system
+    small = make_tb_system(33, 5, 3.2, seed=133)  # parts of fewer than 128 orbitals
+    pc, _, _ = run(g, small, precision="fp64e", split_k=1)
+    assert pc.info.split_k == 0
