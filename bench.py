@@ -341,7 +341,7 @@ def kernel_avg_ms(step_ms, nwork):
     return sum(work) / max(1, len(work)), sum(work)
 
 
-def adjoint_block(dev, peaks, src, workload="tb4k", reps=3):
+def adjoint_block(dev, peaks, src, workload="tb4k", reps=3, precisions=("fp64", "fp64e", "fp32")):
     """gsp2_backward of L = sum Pbar .* P on the 4,096-orbital, 32-part workload, checkpoints
     every 8 steps, for the three kinds of adjoint: FP64 (CUDA cores), FP64 rebuilt from BF16
     digit products (tensor cores) and FP32 (FP16 hi + lo products on the tensor cores, behind
@@ -355,7 +355,7 @@ def adjoint_block(dev, peaks, src, workload="tb4k", reps=3):
     s = make_system(workload)
     h = torch.from_numpy(s.vals).to(dev)
     out = {"workload": workload, "checkpoint_every": 8}
-    for prec in ("fp64", "fp64e", "fp32"):
+    for prec in precisions:
         plan = GSP2(s.n, s.rowptr, s.colind, s.nocc, s.part, s.nparts, s.g_rowptr, s.g_colind, device=dev,
                     precision=prec, ckpt_every=8, fp64_tail_steps=0)
         rng = np.random.default_rng(5678)
@@ -621,6 +621,10 @@ def run_ours(args):
 
     if rank == 0 and not args.no_adjoint:
         line["adjoint"] = adjoint_block(dev, peaks, src)
+        # the same sweeps on the 30,000-orbital workload, whose tiles fill the SMs (the 4,096-
+        # orbital case has 193 tiles for 152 SMs and is bound by launch latency and uneven ends)
+        line["adjoint_tb30k"] = adjoint_block(dev, peaks, src, workload="tb30k", reps=2,
+                                              precisions=("fp64e", "fp32"))
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t_cpu, _ = oracle_build_seconds(s, args.max_steps)
