@@ -61,6 +61,8 @@ struct WsLayout {
   size_t arena0, arena1;       // ping-pong iterates
   std::vector<size_t> ckpt;    // X_0, X_k, X_2k, ... (adjoint checkpoints)
   std::vector<size_t> seg;     // seg[j] = X_{c0+j}, j = 1..k-1, recomputed in the adjoint
+  std::vector<size_t> seg2;    // the same for the other checkpoint segment (overlapped adjoint)
+  size_t oz_acc2;              // the side stream's per-CTA scratch tiles (overlapped adjoint)
   size_t xb0, xb1;             // adjoint Xbar ping-pong
   size_t total;
 };
@@ -114,6 +116,11 @@ struct gsp2_plan {
   int device = -1;
   int num_sms = 0;
   cudaStream_t cap_stream = nullptr;
+  // emulated adjoint of small plans: the iterates of the next checkpoint segment are rebuilt
+  // on a side stream while the reverse steps of the current one run (two digit-set buffers)
+  bool adj_overlap = false;
+  cudaStream_t side_stream = nullptr;
+  std::vector<cudaEvent_t> bev;  // fork, per segment: rebuilt, reversed
   // forward graphs, one per (H, P, alpha, mode, nsteps) key, the two most recent kept (a
   // caller alternating two buffer pairs, e.g. to overlap copies with compute, replays both)
   struct ForwardGraph {
@@ -367,6 +374,9 @@ static void build_layout(gsp2_plan* h) {
   L.adj_dig.clear();
   L.adj_maps = L.adj_maps_mn = L.adj_norm = L.adj_sig = L.adj_normf = 0;
   L.split_acc = L.split_cnt = L.split_items = 0;
+  L.seg2.clear();
+  L.oz_acc2 = 0;
+  h->adj_overlap = h->opt.precision == GSP2_PREC_FP64_EMU && k > 1 && h->tc_tiles.size() <= 512;
   // split-K work items: FP64_EMU plans whose parts all exceed 128 orbitals (so that both K
   // halves of every pass hold at least one stage)
   h->split_ok = h->opt.precision == GSP2_PREC_FP64_EMU && h->min_s > 128 &&
@@ -378,10 +388,17 @@ static void build_layout(gsp2_plan* h) {
     L.split_items = take(2 * h->tc_tiles.size() * sizeof(int32_t));
   }
   if (h->use_oz && k > 0) {
-    for (int set = 0; set <= k; ++set)
+    // digit sets: the iterates of a checkpoint segment (k sets; two buffers of k when the
+    // rebuilds overlap the reverse steps), then Xbar / 2^sig
+    const int nsets = (h->adj_overlap ? 2 * k : k) + 1;
+    for (int set = 0; set < nsets; ++set)
       for (int t = 0; t < OZ_SLICES; ++t) L.adj_dig.push_back(take((size_t)h->arena_elems * 2));
-    L.adj_maps = take((size_t)(k + 1) * OZ_SLICES * h->parts.size() * 128);
-    L.adj_maps_mn = take((size_t)(k + 1) * OZ_SLICES * h->parts.size() * 128);
+    L.adj_maps = take((size_t)nsets * OZ_SLICES * h->parts.size() * 128);
+    L.adj_maps_mn = take((size_t)nsets * OZ_SLICES * h->parts.size() * 128);
+    if (h->adj_overlap) {
+      for (int j = 1; j < k; ++j) L.seg2.push_back(take(ab));
+      L.oz_acc2 = take((size_t)OZ_MAX_GRID * 128 * 128 * 8);
+    }
     L.adj_norm = take(h->S.size() * sizeof(double));
     L.adj_normf = take(h->S.size() * sizeof(float));
     L.adj_sig = take(h->parts.size() * sizeof(int32_t));
@@ -772,6 +789,11 @@ extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t byt
   h->device = dev;
   h->have_forward = false;
   if (!h->cap_stream) CU(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+  if (h->adj_overlap && !h->side_stream) {
+    CU(h, cudaStreamCreateWithFlags(&h->side_stream, cudaStreamNonBlocking));
+    h->bev.resize(1 + 2 * (size_t)(h->total_steps / h->opt.ckpt_every + 1));
+    for (auto& e : h->bev) CU(h, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
   if (h->opt.time_steps && h->ev.empty()) {
     h->ev.resize(2 * (size_t)std::max(h->total_steps, h->opt.max_steps));
     for (auto& e : h->ev) CU(h, cudaEventCreate(&e));
@@ -840,6 +862,7 @@ extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t byt
       if (fp64_like(h->opt.precision)) {
         fp64_arenas.insert(fp64_arenas.end(), L.ckpt.begin(), L.ckpt.end());
         fp64_arenas.insert(fp64_arenas.end(), L.seg.begin(), L.seg.end());
+        fp64_arenas.insert(fp64_arenas.end(), L.seg2.begin(), L.seg2.end());
       }
       for (size_t off : fp64_arenas) CU(h, cudaMemsetAsync(h->ws + off, 0, ab, s));
       for (int b = 0; b < 2; ++b)
@@ -1625,46 +1648,98 @@ static gsp2_status enqueue_backward_emu(gsp2_plan* h, const double* pbar, double
   const int np = (int)h->parts.size();
   StepCtl ctl{st, alpha, (double*)(w + L.traces), (double*)(w + L.idem), h->nocc, h->opt.idem_tol,
               h->opt.trace_tol, MODE_REPLAY, M, 1, 0};
-  auto set = [&](int j) {
+  // digit set j of buffer b (the iterates X_{c0+j} of a checkpoint segment), and Xbar's set
+  const int xset = h->adj_overlap ? 2 * k : k;
+  auto sidx = [&](int b, int j) { return (h->adj_overlap ? b * k : 0) + j; };
+  auto dset = [&](int idx) {
     OzSlices o{};
-    for (int t = 0; t < OZ_SLICES; ++t) o.s[t] = (uint16_t*)(w + L.adj_dig[(size_t)j * OZ_SLICES + t]);
+    for (int t = 0; t < OZ_SLICES; ++t) o.s[t] = (uint16_t*)(w + L.adj_dig[(size_t)idx * OZ_SLICES + t]);
     return o;
   };
-  auto smaps = [&](size_t base, int j) { return (const void*)(w + base + (size_t)j * OZ_SLICES * np * 128); };
+  auto smaps = [&](size_t base, int idx) { return (const void*)(w + base + (size_t)idx * OZ_SLICES * np * 128); };
+  auto seg = [&](int b, int j) { return (double*)(w + (b ? L.seg2[(size_t)j] : L.seg[(size_t)j])); };
   const OzStepArgs base = oz_args(h, ctl);
-  CU(h, cudaMemsetAsync(norm, 0, h->S.size() * sizeof(double), s));
-  CU(h, cudaMemsetAsync(normf, 0, h->S.size() * sizeof(float), s));
-  CU(h, launch_adj_seed<double>(parts, gbl, (int)h->gblocks.size(), Sall, (const int32_t*)(w + L.invperm),
-                                (const int64_t*)(w + L.pcolptr), pbar, xb0, s));
-  CU(h, launch_oz_adj_scale(parts, np, tct, ntc, xb0, xb1, 0, norm, sig, st, s));
-  CU(h, launch_oz_digits(parts, gbl_ld, ngb, xb0, xb1, 0, 0, set(k), sig, st, s));
-  for (int c0 = (M / k) * k; c0 >= 0; c0 -= k) {
-    const double* ck = (const double*)(w + L.ckpt[c0 / k]);
-    CU(h, launch_oz_digits(parts, gbl_ld, ngb, ck, ck, 0, c0 + 1, set(0), nullptr, st, s));
+  // segment q covers the steps c0 + 1 .. c0 + k, c0 = q k; its buffer alternates when overlapped
+  auto rebuild = [&](int q, cudaStream_t ss) -> gsp2_status {
+    const int c0 = q * k, b = h->adj_overlap ? (q & 1) : 0;
+    const double* ck = (const double*)(w + L.ckpt[(size_t)q]);
+    CU(h, launch_oz_digits(parts, gbl_ld, ngb, ck, ck, 0, c0 + 1, dset(sidx(b, 0)), nullptr, st, ss));
     for (int j = 1; j < k && c0 + j < M; ++j) {
       OzStepArgs a = base;
-      a.maps = smaps(L.adj_maps, j - 1);
-      a.maps_mn = smaps(L.adj_maps_mn, j - 1);
-      a.digits[0] = a.digits[1] = set(j);
-      a.xin = (j == 1) ? ck : (const double*)(w + L.seg[j - 2]);
-      a.xout = (double*)(w + L.seg[j - 1]);
+      a.maps = smaps(L.adj_maps, sidx(b, j - 1));
+      a.maps_mn = smaps(L.adj_maps_mn, sidx(b, j - 1));
+      a.digits[0] = a.digits[1] = dset(sidx(b, j));
+      a.xin = (j == 1) ? ck : seg(b, j - 2);
+      a.xout = seg(b, j - 1);
       a.step = c0 + j;
       a.mode = SQ_RECOMPUTE;
-      CU(h, launch_oz_step(a, h->num_sms, s));
+      if (h->adj_overlap) {
+        // beside the reverse steps: its own scratch tiles, no split items (their buffers are the
+        // reverse steps')
+        a.acc = (long long*)(w + L.oz_acc2);
+        a.split = 0;
+      }
+      CU(h, launch_oz_step(a, h->num_sms, ss));
     }
+    return GSP2_OK;
+  };
+  auto reverse = [&](int q, cudaStream_t ss) -> gsp2_status {
+    const int c0 = q * k, b = h->adj_overlap ? (q & 1) : 0;
     for (int i = std::min(c0 + k, M); i >= c0 + 1; --i) {
       OzStepArgs a = base;
-      a.maps = smaps(L.adj_maps, i - 1 - c0);
-      a.maps_mn = smaps(L.adj_maps_mn, i - 1 - c0);
-      a.maps_b = smaps(L.adj_maps, k);
-      a.maps_mn_b = smaps(L.adj_maps_mn, k);
+      a.maps = smaps(L.adj_maps, sidx(b, i - 1 - c0));
+      a.maps_mn = smaps(L.adj_maps_mn, sidx(b, i - 1 - c0));
+      a.maps_b = smaps(L.adj_maps, xset);
+      a.maps_mn_b = smaps(L.adj_maps_mn, xset);
       a.sig = sig;
       a.normf = normf;
       a.xin = xb0;
       a.xout = xb1;
       a.step = i;
-      CU(h, launch_oz_step(a, h->num_sms, s, true));  // also leaves the new Xbar's scales in sig
-      if (i > 1) CU(h, launch_oz_digits(parts, gbl_ld, ngb, xb0, xb1, i, 0, set(k), sig, st, s));
+      CU(h, launch_oz_step(a, h->num_sms, ss, true));  // also leaves the new Xbar's scales in sig
+      if (i > 1) CU(h, launch_oz_digits(parts, gbl_ld, ngb, xb0, xb1, i, 0, dset(xset), sig, st, ss));
+    }
+    return GSP2_OK;
+  };
+  auto seed = [&]() -> gsp2_status {
+    CU(h, cudaMemsetAsync(norm, 0, h->S.size() * sizeof(double), s));
+    CU(h, cudaMemsetAsync(normf, 0, h->S.size() * sizeof(float), s));
+    CU(h, launch_adj_seed<double>(parts, gbl, (int)h->gblocks.size(), Sall, (const int32_t*)(w + L.invperm),
+                                  (const int64_t*)(w + L.pcolptr), pbar, xb0, s));
+    CU(h, launch_oz_adj_scale(parts, np, tct, ntc, xb0, xb1, 0, norm, sig, st, s));
+    CU(h, launch_oz_digits(parts, gbl_ld, ngb, xb0, xb1, 0, 0, dset(xset), sig, st, s));
+    return GSP2_OK;
+  };
+  const int Q = M / k;  // the last segment
+  gsp2_status r;
+  if (!h->adj_overlap) {
+    if ((r = seed()) != GSP2_OK) return r;
+    for (int q = Q; q >= 0; --q) {
+      if ((r = rebuild(q, s)) != GSP2_OK) return r;
+      if ((r = reverse(q, s)) != GSP2_OK) return r;
+    }
+  } else {
+    // the side stream rebuilds segment q while the main stream reverses segment q + 1; the
+    // rebuild of q waits for the reverse of q + 2, which read the same buffer
+    cudaStream_t s2 = h->side_stream;
+    cudaEvent_t* ev_b = h->bev.data() + 1;            // segment q rebuilt
+    cudaEvent_t* ev_r = h->bev.data() + 1 + (Q + 1);  // segment q reversed
+    CU(h, cudaEventRecord(h->bev[0], s));
+    CU(h, cudaStreamWaitEvent(s2, h->bev[0], 0));
+    for (int q = Q; q >= std::max(0, Q - 1); --q) {
+      if ((r = rebuild(q, s2)) != GSP2_OK) return r;
+      CU(h, cudaEventRecord(ev_b[q], s2));
+    }
+    if ((r = seed()) != GSP2_OK) return r;
+    for (int q = Q; q >= 0; --q) {
+      CU(h, cudaStreamWaitEvent(s, ev_b[q], 0));
+      if ((r = reverse(q, s)) != GSP2_OK) return r;
+      CU(h, cudaEventRecord(ev_r[q], s));
+      if (q - 2 >= 0) {
+        CU(h, cudaStreamWaitEvent(s2, ev_r[q], 0));
+        if ((r = rebuild(q - 2, s2)) != GSP2_OK) return r;
+        CU(h, cudaEventRecord(ev_b[q - 2], s2));
+      }
     }
   }
   CU(h, launch_adj_hbar<double>(h->n, (const int64_t*)(w + L.rowptr), (const int32_t*)(w + L.colind),
@@ -1869,6 +1944,8 @@ extern "C" void gsp2_destroy(gsp2_handle h) {
   if (!h) return;
   drop_graph(h);
   for (auto& e : h->ev) cudaEventDestroy(e);
+  for (auto& e : h->bev) cudaEventDestroy(e);
+  if (h->side_stream) cudaStreamDestroy(h->side_stream);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
 }
