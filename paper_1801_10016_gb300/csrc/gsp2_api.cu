@@ -300,16 +300,22 @@ static void build_layout(gsp2_plan* h) {
     const int k = h->opt.ckpt_every;
     L.ckpt.clear();
     L.seg.clear();
+    L.seg2.clear();
     L.tailf.clear();
     L.aop.clear();
     L.xb0 = L.xb1 = L.aop_maps = L.aop_maps_mn = L.xb_sig = L.xb_max = 0;
+    // small plans rebuild the next checkpoint segment on a side stream during the reverse
+    // steps of the current one: a second buffer of k operand sets and k - 1 segment arenas
+    h->adj_overlap = k > 1 && h->tc_tiles.size() <= 512;
     if (k > 0) {
       for (int c = 0; c <= h->opt.max_steps / k; ++c) L.ckpt.push_back(take(af));
       for (int j = 1; j < k; ++j) L.seg.push_back(take(af));
+      if (h->adj_overlap)
+        for (int j = 1; j < k; ++j) L.seg2.push_back(take(af));
       L.xb0 = take(af);
       L.xb1 = take(af);
       for (int t = 0; t < h->opt.fp64_tail_steps; ++t) L.tailf.push_back(take(af));
-      const int nsets = std::max(k, h->opt.fp64_tail_steps);
+      const int nsets = std::max(k, h->opt.fp64_tail_steps) + (h->adj_overlap ? k : 0);
       for (int q = 0; q < 2 * nsets; ++q) L.aop.push_back(take((size_t)h->arena_elems * 2));
       L.aop_maps = take((size_t)2 * (nsets + 2) * h->parts.size() * 128);
       L.aop_maps_mn = take((size_t)2 * (nsets + 2) * h->parts.size() * 128);
@@ -920,6 +926,7 @@ extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t byt
       std::vector<std::pair<size_t, size_t>> zero{{L.mf[0], af}, {L.mf[1], af}, {L.d[0], ab}, {L.d[1], ab}};
       for (size_t off : L.ckpt) zero.push_back({off, af});
       for (size_t off : L.seg) zero.push_back({off, af});
+      for (size_t off : L.seg2) zero.push_back({off, af});
       for (size_t off : L.tailf) zero.push_back({off, af});
       for (size_t off : L.aop) zero.push_back({off, (size_t)h->arena_elems * 2});
       if (L.xb_max) zero.push_back({L.xb_max, h->parts.size() * sizeof(uint32_t)});
@@ -1811,7 +1818,8 @@ static gsp2_status enqueue_backward_lp(gsp2_plan* h, const double* pbar, double*
   const int k = h->opt.ckpt_every, M = h->opt.max_steps, T = h->opt.fp64_tail_steps;
   const int64_t ne = h->arena_elems;
   const size_t np = h->parts.size();
-  const int nsets = (int)L.aop.size() / 2 - 2;  // operand sets of rebuilt iterates
+  const int nsets = (int)L.aop.size() / 2 - 2;  // operand sets of rebuilt iterates (both buffers)
+  const int set1 = std::max(k, T);                // first set of the second buffer (overlap)
   StepCtl ctl{st, alpha, (double*)(w + L.traces), (double*)(w + L.idem), h->nocc, h->opt.idem_tol,
               h->opt.trace_tol, MODE_REPLAY, M, 1, T};
   auto tf = [&](int t) { return (float*)(w + L.tailf[(size_t)t]); };
@@ -1844,11 +1852,11 @@ static gsp2_status enqueue_backward_lp(gsp2_plan* h, const double* pbar, double*
     base.op_lo[b] = aop(nsets + b, 1);
   }
   // operands of a stored iterate into set `set` (skipped where need > n - T)
-  auto split_x = [&](const float* x, int set, int need) {
-    return launch_split_f16(parts, gbl_ld, ngb, x, aop(set, 0), aop(set, 1), nullptr, need, T, st, s);
+  auto split_x = [&](const float* x, int set, int need, cudaStream_t ss) {
+    return launch_split_f16(parts, gbl_ld, ngb, x, aop(set, 0), aop(set, 1), nullptr, need, T, st, ss);
   };
   // X_step rebuilt from X_{step-1} (operand set `in`, master xin) into set `out`, master xout
-  auto rebuild = [&](int in, const float* xin, int out, float* xout, int step) {
+  auto rebuild = [&](int in, const float* xin, int out, float* xout, int step, cudaStream_t ss) {
     TcStepArgs a = base;
     a.xmap_hi = amap(in, 0);
     a.xmap_lo = amap(in, 1);
@@ -1859,7 +1867,7 @@ static gsp2_status enqueue_backward_lp(gsp2_plan* h, const double* pbar, double*
     a.xo_hi = aop(out, 0);
     a.xo_lo = aop(out, 1);
     a.step = step;
-    return launch_tc_adjoint(a, h->num_sms, true, s);
+    return launch_tc_adjoint(a, h->num_sms, true, ss);
   };
   // reverse step `step` with X_{step-1} in operand set `x`
   auto reverse = [&](int x, int step) {
@@ -1883,16 +1891,56 @@ static gsp2_status enqueue_backward_lp(gsp2_plan* h, const double* pbar, double*
   CU(h, launch_split_f16(parts, gbl_ld, ngb, xb0, aop(nsets, 0), aop(nsets, 1), xb_sig, 0, 0, st, s));
   if (T > 0) {
     CU(h, launch_copy_iterate((const float* const*)(w + L.master_of_step), tf(0), ne, st, T, s));
-    CU(h, split_x(tf(0), 0, 0));
-    for (int t = 1; t < T; ++t) CU(h, rebuild(t - 1, tf(t - 1), t, tf(t), t - T));
+    CU(h, split_x(tf(0), 0, 0, s));
+    for (int t = 1; t < T; ++t) CU(h, rebuild(t - 1, tf(t - 1), t, tf(t), t - T, s));
     for (int t = T; t >= 1; --t) CU(h, reverse(t - 1, t - T));
   }
-  for (int c0 = (M / k) * k; c0 >= 0; c0 -= k) {
-    const float* ck = (const float*)(w + L.ckpt[c0 / k]);
-    CU(h, split_x(ck, 0, c0 + 1));
+  // segment q (steps c0 + 1 .. c0 + k, c0 = q k): its iterates' operands in buffer b (sets
+  // b set1 + j), masters in the segment arenas of b
+  auto segm = [&](int b, int j) { return (float*)(w + (b ? L.seg2[(size_t)j] : L.seg[(size_t)j])); };
+  auto build_segment = [&](int q, cudaStream_t ss) -> gsp2_status {
+    const int c0 = q * k, b = h->adj_overlap ? (q & 1) : 0, o = b * set1;
+    const float* ck = (const float*)(w + L.ckpt[(size_t)q]);
+    CU(h, split_x(ck, o, c0 + 1, ss));
     for (int j = 1; j < k && c0 + j < M; ++j)
-      CU(h, rebuild(j - 1, (j == 1) ? ck : (const float*)(w + L.seg[j - 2]), j, (float*)(w + L.seg[j - 1]), c0 + j));
-    for (int i = std::min(c0 + k, M); i >= c0 + 1; --i) CU(h, reverse(i - 1 - c0, i));
+      CU(h, rebuild(o + j - 1, (j == 1) ? ck : segm(b, j - 2), o + j, segm(b, j - 1), c0 + j, ss));
+    return GSP2_OK;
+  };
+  auto reverse_segment = [&](int q) -> gsp2_status {
+    const int c0 = q * k, o = (h->adj_overlap ? (q & 1) : 0) * set1;
+    for (int i = std::min(c0 + k, M); i >= c0 + 1; --i) CU(h, reverse(o + i - 1 - c0, i));
+    return GSP2_OK;
+  };
+  const int Q = M / k;
+  gsp2_status r;
+  if (!h->adj_overlap) {
+    for (int q = Q; q >= 0; --q) {
+      if ((r = build_segment(q, s)) != GSP2_OK) return r;
+      if ((r = reverse_segment(q)) != GSP2_OK) return r;
+    }
+  } else {
+    // the side stream rebuilds segment q while the main stream reverses segment q + 1; the
+    // rebuild of q waits for the reverse of q + 2, which read the same buffer (forked after
+    // the FP64 tail, which uses the first buffer's sets)
+    cudaStream_t s2 = h->side_stream;
+    cudaEvent_t* ev_b = h->bev.data() + 1;
+    cudaEvent_t* ev_r = h->bev.data() + 1 + (Q + 1);
+    CU(h, cudaEventRecord(h->bev[0], s));
+    CU(h, cudaStreamWaitEvent(s2, h->bev[0], 0));
+    for (int q = Q; q >= std::max(0, Q - 1); --q) {
+      if ((r = build_segment(q, s2)) != GSP2_OK) return r;
+      CU(h, cudaEventRecord(ev_b[q], s2));
+    }
+    for (int q = Q; q >= 0; --q) {
+      CU(h, cudaStreamWaitEvent(s, ev_b[q], 0));
+      if ((r = reverse_segment(q)) != GSP2_OK) return r;
+      CU(h, cudaEventRecord(ev_r[q], s));
+      if (q - 2 >= 0) {
+        CU(h, cudaStreamWaitEvent(s2, ev_r[q], 0));
+        if ((r = build_segment(q - 2, s2)) != GSP2_OK) return r;
+        CU(h, cudaEventRecord(ev_b[q - 2], s2));
+      }
+    }
   }
   CU(h, launch_adj_hbar<float>(h->n, (const int64_t*)(w + L.rowptr), (const int32_t*)(w + L.colind),
                                (const int64_t*)(w + L.memptr), (const int32_t*)(w + L.mempart),
