@@ -363,6 +363,7 @@ def adjoint_block(dev, peaks, src, workload="tb4k", reps=3, precisions=("fp64", 
         ms = []
         for r in range(reps + 2):
             plan.density(h)
+            plan.status()  # the applied step count: the adjoint then schedules only those steps
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             plan.backward(pbar)

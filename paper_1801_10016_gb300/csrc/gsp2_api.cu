@@ -135,6 +135,10 @@ struct gsp2_plan {
   std::vector<size_t> step_arena_off;  // workspace offset of the arena holding X_i
   std::vector<cudaEvent_t> ev;  // 2 per step when time_steps is set
   bool have_forward = false;
+  // steps the last density call applied, once gsp2_sync_status has read them (-1: unknown);
+  // the adjoint then schedules exactly those steps instead of max_steps
+  int32_t known_steps = -1;
+  int32_t bkey_m = -1;
   // shard plans (gsp2_create_shard): the plan holds the parts one rank owns, numbered in
   // ascending global order; part_global maps them back.  A plain plan owns every part.
   bool shard = false;
@@ -1284,6 +1288,7 @@ extern "C" gsp2_status gsp2_density(gsp2_handle h, const double* d_hvals, double
     if (st != GSP2_OK) return st;
   }
   h->have_forward = true;
+  h->known_steps = -1;
   return GSP2_OK;
 }
 
@@ -1330,6 +1335,7 @@ extern "C" gsp2_status gsp2_shard_begin(gsp2_handle h, const double* d_hvals, do
   cudaStream_t s = (cudaStream_t)stream;
   h->sx = gsp2_plan::ShardCall{};
   h->have_forward = false;
+  h->known_steps = -1;
   r = enqueue_forward(h, d_hvals, d_pvals, d_alpha, mode, nsteps, s, 0, 0);
   if (r != GSP2_OK) return r;
   CU(h, launch_shard_partial((const DevState*)(h->ws + h->L.state), (const ShardSlot*)(h->ws + h->L.xchg), d_send, s));
@@ -1572,6 +1578,8 @@ extern "C" gsp2_status gsp2_sync_status(gsp2_handle h, gsp2_report* r) {
   if (st.steps > 0)
     CU(h, cudaMemcpy(&e, h->ws + h->L.idem + sizeof(double) * (st.steps - 1), sizeof(double),
                      cudaMemcpyDeviceToHost));
+  // a finished call's step count lets the adjoint schedule exactly the applied steps
+  h->known_steps = (st.status == ST_OK || st.status == ST_NOT_CONVERGED || st.status == ST_TRACE) ? st.steps : -1;
   if (r) {
     r->status = st.status;
     r->steps = st.steps;
@@ -1634,6 +1642,17 @@ extern "C" gsp2_status gsp2_step_times(gsp2_handle h, float* ms, int32_t cap) {
 // (from its row norms, summed in the step's epilogue), and the new digits follow.  The
 // seed's scales come from a separate norm pass.  Xbar is kept in its upper 128-tiles like
 // the forward iterates.
+// Steps the adjoint schedules (launches for steps the forward did not apply return at once):
+// max_steps (FP64 plans: plus their tail steps), or the applied count once gsp2_sync_status
+// has read it (the loop's steps for the low-precision plans, whose FP64 tail steps are
+// reversed apart)
+static int backward_steps(gsp2_plan* h) {
+  if (fp64_like(h->opt.precision))
+    return h->known_steps >= 0 ? std::min(h->known_steps, h->total_steps) : h->total_steps;
+  const int T = h->opt.fp64_tail_steps;
+  return h->known_steps >= T ? std::min(h->known_steps - T, h->opt.max_steps) : h->opt.max_steps;
+}
+
 static gsp2_status enqueue_backward_emu(gsp2_plan* h, const double* pbar, double* hbar, cudaStream_t s) {
   const WsLayout& L = h->L;
   char* w = h->ws;
@@ -1651,7 +1670,7 @@ static gsp2_status enqueue_backward_emu(gsp2_plan* h, const double* pbar, double
   double* norm = (double*)(w + L.adj_norm);
   float* normf = (float*)(w + L.adj_normf);
   int32_t* sig = (int32_t*)(w + L.adj_sig);
-  const int k = h->opt.ckpt_every, M = h->total_steps;
+  const int k = h->opt.ckpt_every, M = backward_steps(h);
   const int np = (int)h->parts.size();
   StepCtl ctl{st, alpha, (double*)(w + L.traces), (double*)(w + L.idem), h->nocc, h->opt.idem_tol,
               h->opt.trace_tol, MODE_REPLAY, M, 1, 0};
@@ -1767,7 +1786,7 @@ static gsp2_status enqueue_backward(gsp2_plan* h, const double* pbar, double* hb
   auto alpha = (int8_t*)(w + L.alpha);
   double* xb0 = (double*)(w + L.xb0);
   double* xb1 = (double*)(w + L.xb1);
-  const int k = h->opt.ckpt_every, M = h->total_steps;
+  const int k = h->opt.ckpt_every, M = backward_steps(h);
   const int nt = (int)h->tiles.size();
   StepCtl ctl{st, alpha, (double*)(w + L.traces), (double*)(w + L.idem), h->nocc, h->opt.idem_tol,
               h->opt.trace_tol, MODE_REPLAY, M, 1, 0};
@@ -1815,7 +1834,7 @@ static gsp2_status enqueue_backward_lp(gsp2_plan* h, const double* pbar, double*
   float* xb1 = (float*)(w + L.xb1);
   int32_t* xb_sig = (int32_t*)(w + L.xb_sig);
   uint32_t* xb_max = (uint32_t*)(w + L.xb_max);
-  const int k = h->opt.ckpt_every, M = h->opt.max_steps, T = h->opt.fp64_tail_steps;
+  const int k = h->opt.ckpt_every, M = backward_steps(h), T = h->opt.fp64_tail_steps;
   const int64_t ne = h->arena_elems;
   const size_t np = h->parts.size();
   const int nsets = (int)L.aop.size() / 2 - 2;  // operand sets of rebuilt iterates (both buffers)
@@ -1960,7 +1979,7 @@ extern "C" gsp2_status gsp2_backward(gsp2_handle h, const double* d_pbar, double
   if (dev != h->device) return fail(h, GSP2_E_STATE, "current device differs from the workspace's device");
   cudaStream_t s = (cudaStream_t)stream;
   if (h->opt.use_graph) {
-    if (!h->bexec || h->bkey_pbar != d_pbar || h->bkey_hbar != d_hbar) {
+    if (!h->bexec || h->bkey_pbar != d_pbar || h->bkey_hbar != d_hbar || h->bkey_m != backward_steps(h)) {
       if (h->bexec) cudaGraphExecDestroy(h->bexec);
       h->bexec = nullptr;
       cudaGraph_t g = nullptr;
@@ -1981,6 +2000,7 @@ extern "C" gsp2_status gsp2_backward(gsp2_handle h, const double* d_pbar, double
       }
       h->bkey_pbar = d_pbar;
       h->bkey_hbar = d_hbar;
+      h->bkey_m = backward_steps(h);
     }
     CU(h, cudaGraphLaunch(h->bexec, s));
     return GSP2_OK;

@@ -284,3 +284,28 @@ def test_emulated_adjoint_split_k_matches_one_item_per_tile(g, case):
 def torch_from(x):
     import torch
     return torch.from_numpy(x).to("cuda:0")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp64e", "fp16x3"])
+def test_adjoint_after_a_status_read_is_the_same(g, prec):
+    """Once gsp2_sync_status has read the applied step count, the adjoint schedules only those
+    steps (the launches for steps beyond it return at once otherwise): bitwise the same Hbar,
+    and a later density call falls back to the full schedule until its status is read."""
+    import torch
+    s = make_tb_system(48, 4, 3.0, seed=21)
+    kw = dict(precision=prec, ckpt_every=3)
+    if prec == "fp16x3":
+        kw["fp64_tail_steps"] = 2
+    plan = g.GSP2(s.n, s.rowptr, s.colind, s.nocc, s.part, s.nparts, s.g_rowptr, s.g_colind, device="cuda:0", **kw)
+    h = torch.from_numpy(s.vals).to("cuda:0")
+    pb, _ = pbar_for_trace_loss(s, plan)
+    pbt = torch.from_numpy(pb).to("cuda:0")
+    plan.density(h)
+    full = plan.backward(pbt).clone()      # step count not read: every step launch scheduled
+    assert plan.status()[0] == 0
+    exact = plan.backward(pbt).clone()     # only the applied steps
+    assert torch.equal(full, exact)
+    plan.density(h * 1.001)
+    again = plan.backward(pbt)             # a new forward: the full schedule again
+    plan.status()
+    assert torch.equal(again, plan.backward(pbt))
