@@ -311,7 +311,10 @@ gsp2_status gsp2_autotune(gsp2_handle h, const double* d_hvals, double* d_pvals,
  * with FP16 hi + lo products (Xbar's operands scaled by a power of two per part).
  *  d_pbar  device double[nnz_p]
  *  d_hbar  device double[nnz_h], overwritten; symmetric for a symmetric problem
- * Requires ckpt_every > 0 at create and a completed density call (GSP2_E_STATE).
+ * Requires ckpt_every > 0 at create and a completed density call (GSP2_E_STATE).  The sweep
+ * covers max_steps (launches for steps the forward did not apply return at once) unless
+ * gsp2_sync_status has been called after the density call: then it covers exactly the steps
+ * applied, with bitwise the same result.
  */
 gsp2_status gsp2_backward(gsp2_handle h, const double* d_pbar, double* d_hbar, void* stream);
 
