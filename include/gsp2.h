@@ -116,7 +116,10 @@ typedef struct {
                               = the same list reversed in every other round of SMs, so that
                               each SM's share of the uneven tiles evens out (with few tiles per
                               SM, the CTA that took the largest tile of one round takes the
-                              smallest of the next); set by gsp2_autotune */
+                              smallest of the next); 2 = that order with the tiles of the last
+                              four rounds re-dealt, largest first, to the least loaded CTA of a
+                              cost model (columns x padded K), so that the CTAs finish together;
+                              set by gsp2_autotune */
   int32_t tile_shape;      /* output tiles of the persistent tensor-core steps: 0 (default)
                               128 x 128; 1 = 128 x 256 (two upper tiles of a row block per
                               MMA, N = 256, halving the loads of the A operand); set by
@@ -287,7 +290,8 @@ typedef struct {
  * Autotuner of the step schedule (batching of uneven parts, not in the paper): times whole
  * density calls (RECORD mode, `trials` >= 1 each after one untimed call) with every candidate
  * that applies to the plan's precision -- tensor-core steps: persistent with either tile
- * order and either tile shape, and one CTA per tile; FP64_EMU steps: either tile order;
+ * order and either tile shape, and one CTA per tile; FP64_EMU steps: the three tile orders,
+ * and for small plans split-K work items;
  * FP64 and FP32: the only schedule -- and keeps the fastest in the plan (gsp2_plan_query
  * reports it).  Every
  * candidate computes bitwise the same P (a tile's arithmetic does not depend on the CTA

@@ -451,7 +451,7 @@ static gsp2_status create_plan(int64_t n, const int64_t* rowptr, const int32_t* 
     if (o.lp_tail_steps < 0 || o.fp64_tail_steps + o.lp_tail_steps > MAX_TAIL)
       return bail(GSP2_E_ARG, "lp_tail_steps must be >= 0 with lp_tail_steps + fp64_tail_steps <= 8");
     if (o.tc_schedule < 0 || o.tc_schedule > 1) return bail(GSP2_E_ARG, "tc_schedule must be 0 or 1");
-    if (o.tile_order < 0 || o.tile_order > 1) return bail(GSP2_E_ARG, "tile_order must be 0 or 1");
+    if (o.tile_order < 0 || o.tile_order > 2) return bail(GSP2_E_ARG, "tile_order must be 0, 1 or 2");
     if (o.tile_shape < 0 || o.tile_shape > 1) return bail(GSP2_E_ARG, "tile_shape must be 0 or 1");
     if (o.split_k < -1 || o.split_k > 1) return bail(GSP2_E_ARG, "split_k must be -1, 0 or 1");
     if (o.lp_tail_steps > 0 && (fp64_like(o.precision) || o.precision == GSP2_PREC_FP32))
@@ -739,7 +739,7 @@ static void order_tc_tiles(gsp2_plan* h, int grid) {
   h->tc_order = h->tc_tiles;
   h->tcw_order = h->tc_wide;
   h->tcw_nb_order = h->tc_wide_nb;
-  if (h->opt.tile_order != 1 || grid < 2) return;
+  if (h->opt.tile_order == 0 || grid < 2) return;
   const size_t g = (size_t)grid;
   auto serpentine = [g](auto& v) {
     for (size_t r = 0; r * g < v.size(); ++r)
@@ -751,6 +751,35 @@ static void order_tc_tiles(gsp2_plan* h, int grid) {
   serpentine(h->tc_order);
   serpentine(h->tcw_order);
   serpentine(h->tcw_nb_order);
+  if (h->opt.tile_order != 2) return;
+  // tile_order 2: the serpentine deal, then the tiles of the last rounds re-dealt so that the
+  // CTAs finish together.  Each CTA's load up to the last rounds is summed from a cost model
+  // (the tile's columns times K, K padded to the stage and a fixed part for fill and epilogue);
+  // the remaining tiles, largest first, go to the least loaded CTA that still has a place in
+  // those rounds (its positions stay b, b + grid, ...: only the list order changes).
+  const size_t nt = h->tc_order.size();
+  const size_t rounds = (nt + g - 1) / g, tail = std::min<size_t>(4, rounds);
+  if (tail < 2) return;
+  const size_t first = (rounds - tail) * g;  // positions from here on are re-dealt
+  auto cost = [&](const Tile& t) {
+    const int32_t s = h->parts[t.part].s;
+    const int32_t cols = std::min(128, ((s - t.tj * 128) + 15) & ~15);
+    return (double)cols * (double)(((s + 31) & ~31) + 192);
+  };
+  std::vector<double> load(g, 0.0);
+  for (size_t p = 0; p < first; ++p) load[p % g] += cost(h->tc_order[p]);
+  std::vector<Tile> rest(h->tc_order.begin() + (long)first, h->tc_order.end());
+  std::stable_sort(rest.begin(), rest.end(), [&](const Tile& a, const Tile& b) { return cost(a) > cost(b); });
+  std::vector<size_t> next(g);  // next free position of each CTA
+  for (size_t b = 0; b < g; ++b) next[b] = first + b;
+  for (const Tile& tl : rest) {
+    size_t best = g;
+    for (size_t b = 0; b < g; ++b)
+      if (next[b] < nt && (best == g || load[b] < load[best])) best = b;
+    h->tc_order[next[best]] = tl;
+    next[best] += g;
+    load[best] += cost(tl);
+  }
 }
 
 // Work items of the split reverse steps (both K halves of every upper tile, codes 2 i + half
@@ -771,7 +800,7 @@ static void order_split_items(gsp2_plan* h, int grid) {
     h->split_items.push_back(2 * i);
     h->split_items.push_back(2 * i + 1);
   }
-  if (h->opt.tile_order == 1 && grid >= 2) {
+  if (h->opt.tile_order >= 1 && grid >= 2) {
     const size_t g = (size_t)grid;
     for (size_t r = 0; r * g < h->split_items.size(); ++r)
       if (r & 1) {
@@ -1403,8 +1432,8 @@ extern "C" gsp2_status gsp2_autotune(gsp2_handle h, const double* d_hvals, doubl
   if (!fp64_like(prec) && prec_kind(prec) >= 0)
     cand = {{0, 0, 0, 0}, {0, 1, 0, 0}, {0, 0, 1, 0}, {0, 1, 1, 0}, {1, 0, 0, 0}};
   else if (prec == GSP2_PREC_FP64_EMU && h->split_ok)
-    cand = {{0, 0, 0, 0}, {0, 1, 0, 0}, {0, 0, 0, 1}, {0, 1, 0, 1}};
-  else if (prec == GSP2_PREC_FP64_EMU) cand = {{0, 0, 0, 0}, {0, 1, 0, 0}};
+    cand = {{0, 0, 0, 0}, {0, 1, 0, 0}, {0, 2, 0, 0}, {0, 0, 0, 1}, {0, 1, 0, 1}};
+  else if (prec == GSP2_PREC_FP64_EMU) cand = {{0, 0, 0, 0}, {0, 1, 0, 0}, {0, 2, 0, 0}};
   else cand = {{h->opt.tc_schedule, h->opt.tile_order, h->opt.tile_shape, sp}};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CU(h, cudaEventCreate(&e0));

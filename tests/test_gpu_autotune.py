@@ -37,7 +37,8 @@ def test_tile_orders_give_bitwise_equal_p(g, prec):
     s = make_workload("tb4k")  # more 128-tiles than SMs: the second order differs
     _, _, p0 = run(g, s, precision=prec, tile_order=0)
     _, _, p1 = run(g, s, precision=prec, tile_order=1)
-    assert np.array_equal(p0, p1)
+    _, _, p2 = run(g, s, precision=prec, tile_order=2)
+    assert np.array_equal(p0, p1) and np.array_equal(p0, p2)
 
 
 @pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "tf32", "bf16", "fp16x3"])
@@ -57,9 +58,9 @@ def test_autotune_keeps_a_timed_candidate(g, prec):
     plan, h, p0 = run(g, s, precision=prec)
     rep = plan.autotune(h, trials=2)
     cands = rep["candidates"]
-    # fp64e on this plan (193 tiles, parts above 128 orbitals): both tile orders with and
-    # without split-K work items
-    assert len(cands) == {"tf32x3": 5, "fp16x3": 5, "fp64e": 4, "fp64": 1}[prec]
+    # fp64e on this plan (193 tiles, parts above 128 orbitals): the three tile orders, and the
+    # first two with split-K work items
+    assert len(cands) == {"tf32x3": 5, "fp16x3": 5, "fp64e": 5, "fp64": 1}[prec]
     assert all(c["ms"] > 0 for c in cands)
     best = cands[rep["chosen"]]
     assert best["ms"] == min(c["ms"] for c in cands)

@@ -137,7 +137,7 @@ def test_workspace_size_covers_two_arenas(g):
 def test_tile_order_option(g):
     s = make_tb_system(16, 2, 3.0, seed=5)
     assert g.default_options().tile_order == 1
-    for bad in (-1, 2):
+    for bad in (-1, 3):
         with pytest.raises(g.GSP2Error):
             _plan(g, s, tile_order=bad)
     p = _plan(g, s, precision="tf32x3", tile_order=1, tc_schedule=1)
