@@ -46,6 +46,7 @@ struct WsLayout {
   size_t adj_normf;               // float[sum of s]: the reverse steps' row norms on their grid
   size_t split_acc, split_cnt;    // split-K reverse steps: int64[2 tiles][128 x 128], uint32[tiles]
   size_t split_items;             // int32[2 tiles]: the order in which the CTAs take the items
+  size_t tile_ctr;                // uint32: next tile of the emulated forward steps' dynamic schedule
   // FP32 adjoint of the low-precision plans: FP16 (hi, lo) operand arenas aop[2 set + lo],
   // sets 0..S-1 for rebuilt iterates, S and S + 1 for Xbar's ping-pong (in the FP64 tail
   // arenas d[0], d[1], which the backward does not need); their tensor maps; Xbar's
@@ -285,6 +286,7 @@ static void build_layout(gsp2_plan* h) {
   L.slots = take(nsl * sizeof(double2));
   L.rslots = take(std::max<size_t>(h->tiles.size(), 1) * sizeof(double));
   L.state = take(sizeof(DevState));
+  L.tile_ctr = take(sizeof(uint32_t));
   L.xchg = take(sizeof(ShardSlot));
   L.alpha = take((size_t)h->opt.max_steps + HIST_EXTRA);
   L.traces = take(((size_t)h->opt.max_steps + HIST_EXTRA) * sizeof(double));
@@ -997,6 +999,7 @@ extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t byt
   CU(h, up(L.rowptr, h->rowptr.data(), h->rowptr.size() * sizeof(int64_t)));
   CU(h, up(L.colind, h->colind.data(), h->colind.size() * sizeof(int32_t)));
   CU(h, cudaMemsetAsync(h->ws + L.state, 0, sizeof(DevState), s));
+  CU(h, cudaMemsetAsync(h->ws + L.tile_ctr, 0, sizeof(uint32_t), s));
   CU(h, cudaMemsetAsync(h->ws + L.alpha, 0, (size_t)h->opt.max_steps + HIST_EXTRA, s));
   // the uploads read pageable host vectors; finish them before the call returns
   CU(h, cudaStreamSynchronize(s));
@@ -1021,6 +1024,7 @@ static OzStepArgs oz_args(gsp2_plan* h, const StepCtl& ctl) {
   a.nslots = h->nslots_tc;
   a.acc = (long long*)(w + L.oz_acc);
   a.ctl = ctl;
+  a.tile_ctr = (uint32_t*)(w + L.tile_ctr);
   if (h->split_on) {
     a.split = 1;
     a.split_acc = (long long*)(w + L.split_acc);

@@ -345,7 +345,9 @@ constexpr uint32_t OZ_DTILE = 128u * OZ_BK * 2u;                 // one digit ti
 constexpr uint32_t OZ_STAGE_B = 2u * OZ_SLICES * OZ_DTILE;       // all A and B digit tiles
 constexpr int OZ_EPI_WARPS = 16;                                 // 4 per TMEM lane quarter
 constexpr int OZ_THREADS = 32 * (4 + OZ_EPI_WARPS);
-constexpr int OZ_SMEM = OZ_STAGES * (int)OZ_STAGE_B + 1024 + 8 * (2 * OZ_STAGES + 4) + 16 + 16 * OZ_EPI_WARPS;
+constexpr int OZ_RING = 4;  // dynamic schedule: tiles claimed ahead of the MMA and epilogue warps
+constexpr int OZ_SMEM = OZ_STAGES * (int)OZ_STAGE_B + 1024 + 8 * (2 * OZ_STAGES + 4) + 16 + 16 * OZ_EPI_WARPS +
+                        8 * 2 * OZ_RING + 4 * OZ_RING;
 static_assert(OZ_SLICES - OZ_SPLIT <= 4 && OZ_SPLIT <= 4, "groups of one pass must fit in 512 TMEM columns");
 static_assert(OZ_SMEM <= 232448, "shared memory of the emulated step");
 
@@ -464,6 +466,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
   int* s_err = reinterpret_cast<int*>(tmem_slot + 1);
   int* s_half = reinterpret_cast<int*>(tmem_slot + 2);  // split adjoint: halves of the tile done before
   double2* red = reinterpret_cast<double2*>(sb + OZ_STAGES * OZ_STAGE_B + 8 * (2 * OZ_STAGES + 4) + 16);
+  // dynamic schedule: the producer claims each next tile from a counter in global memory and
+  // passes it on through a ring (full: claimed; empty: read by the MMA thread and every
+  // epilogue warp); -1 ends the walk
+  const uint32_t ring_bars = smem_u32(red + OZ_EPI_WARPS);
+  int* s_items = reinterpret_cast<int*>(reinterpret_cast<uint8_t*>(red + OZ_EPI_WARPS) + 8 * 2 * OZ_RING);
+  auto item_full = [&](int q) { return ring_bars + 8u * q; };
+  auto item_empty = [&](int q) { return ring_bars + 8u * (OZ_RING + q); };
   auto full = [&](int s) { return bars + 8u * s; };
   auto empty = [&](int s) { return bars + 8u * (OZ_STAGES + s); };
   // accumulator barriers: [0] high groups, [1] low groups
@@ -480,6 +489,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
   // work items: the upper tiles, or (split K) each tile's two K halves
   const bool split = a.split != 0;
   const int nitems = split ? 2 * a.ntiles : a.ntiles;
+  // items claimed at run time (forward and tail steps of plain tiles) or dealt in turn
+  const bool dyn = a.tile_ctr != nullptr && !split && !ADJ && !rec;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < OZ_STAGES; ++s) {
@@ -489,6 +500,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
     for (int q = 0; q < 2; ++q) {
       mbar_init(afull(q), 1);
       mbar_init(aempty(q), OZ_EPI_WARPS);
+    }
+    for (int q = 0; q < OZ_RING; ++q) {
+      mbar_init(item_full(q), 1);
+      mbar_init(item_empty(q), 1 + OZ_EPI_WARPS);
     }
     *s_err = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -505,7 +520,18 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
   if (warp == 0 && lane == 0) {
     uint32_t g = 0;
     bool bad = false;
-    for (int it = blockIdx.x; it < nitems && !bad; it += gridDim.x) {
+    for (int v = 0, it = blockIdx.x; !bad; ++v, it += gridDim.x) {
+      if (dyn) {
+        it = (int)atomicAdd(a.tile_ctr, 1u);
+        const int q = v % OZ_RING;
+        if (v >= OZ_RING && !mbar_wait(item_empty(q), ((v / OZ_RING) - 1) & 1, abort_flag)) {
+          bad = true;
+          break;
+        }
+        s_items[q] = it < nitems ? it : -1;
+        mbar_arrive(item_full(q));
+      }
+      if (it >= nitems) break;
       const int code = split ? a.split_items[it] : it;
       const int ti = split ? code >> 1 : it, half = split ? code & 1 : -1;
       const Tile t = a.tiles[ti];
@@ -567,7 +593,18 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
     uint32_t g = 0;
     int u = 0;  // items done by this CTA
     bool bad = false;
-    for (int it = blockIdx.x; it < nitems && !bad; it += gridDim.x, ++u) {
+    for (int it = blockIdx.x; !bad; it += gridDim.x, ++u) {
+      if (dyn) {
+        const int q = u % OZ_RING;
+        if (!mbar_wait(item_full(q), (u / OZ_RING) & 1, abort_flag)) {
+          bad = true;
+          break;
+        }
+        it = s_items[q];
+        mbar_arrive(item_empty(q));
+        if (it < 0) break;
+      }
+      if (it >= nitems) break;
       const int code = split ? a.split_items[it] : it;
       const int ti = split ? code >> 1 : it, half = split ? code & 1 : -1;
       const Tile t = a.tiles[ti];
@@ -644,7 +681,20 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
       xout = const_cast<double*>(a.xin);
     }
     int u = 0;
-    for (int it = blockIdx.x; it < nitems; it += gridDim.x, ++u) {
+    for (int it = blockIdx.x;; it += gridDim.x, ++u) {
+      if (dyn) {
+        const int q = u % OZ_RING;
+        const bool got = __all_sync(0xffffffffu, mbar_wait(item_full(q), (u / OZ_RING) & 1, abort_flag));
+        if (!got) {
+          *s_err = 1;
+          break;
+        }
+        it = s_items[q];
+        __syncwarp();
+        if (lane == 0) mbar_arrive(item_empty(q));
+        if (it < 0) break;
+      }
+      if (it >= nitems) break;
       const int code = split ? a.split_items[it] : it;
       const int ti = split ? code >> 1 : it;
       // a split item's 64-bit partial goes to its own tile of split_acc, which the item that
@@ -884,6 +934,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
         finish_tail(a.ctl, step, sum.y, sum.x, true);
       }
       a.ctl.st->counter = 0;
+      if (dyn) *a.tile_ctr = 0u;  // every CTA has claimed its last tile: ready for the next launch
     }
   }
 }
