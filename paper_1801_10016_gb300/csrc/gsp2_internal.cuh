@@ -184,9 +184,10 @@ struct OzStepArgs {
   long long* split_acc;  // [2 ntiles][128 x 128], indexed by item code 2 t + h
   uint32_t* split_cnt;   // [ntiles]
   const int32_t* split_items;  // [2 ntiles]: item codes in the order the CTAs take them
-  // forward and tail steps: when set, each CTA claims its next tile from this counter (the
-  // tiles are then taken in list order by whichever CTA is free); the step's last block
-  // sets it back to zero.  NULL: CTA b takes tiles b, b + gridDim.x, ...
+  // forward, tail and reverse steps: when set, each CTA claims its next item from this
+  // counter (the items are then taken in list order by whichever CTA is free); the step's
+  // last block sets it back to zero.  NULL (and the rebuilt iterates): CTA b takes items b,
+  // b + gridDim.x, ...
   uint32_t* tile_ctr;
 };
 constexpr int32_t OZ_SIG_NONFINITE = 0x7FFF;  // scale of a part whose Xbar holds NaN or Inf

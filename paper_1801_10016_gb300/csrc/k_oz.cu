@@ -489,8 +489,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
   // work items: the upper tiles, or (split K) each tile's two K halves
   const bool split = a.split != 0;
   const int nitems = split ? 2 * a.ntiles : a.ntiles;
-  // items claimed at run time (forward and tail steps of plain tiles) or dealt in turn
-  const bool dyn = a.tile_ctr != nullptr && !split && !ADJ && !rec;
+  // items claimed at run time (forward, tail and reverse steps; the list order) or dealt in turn
+  // (the rebuilt iterates, which may run beside reverse steps and have no last block)
+  const bool dyn = a.tile_ctr != nullptr && !rec;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < OZ_STAGES; ++s) {
@@ -908,7 +909,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
           }
         }
       }
-      if (threadIdx.x == 0) a.ctl.st->counter = 0;
+      if (threadIdx.x == 0) {
+        a.ctl.st->counter = 0;
+        if (dyn) *a.tile_ctr = 0u;  // every CTA has claimed its last item
+      }
     }
     return;
   }
