@@ -518,6 +518,7 @@ def run_ours(args):
         "sp2_steps_per_s": 1e3 / avg_launch_ms if avg_launch_ms else None,
         "adjoint_checkpoints": "off (forward P-builds only)",
         "schedule": {"tc_schedule": int(plan.info.tc_schedule), "tile_order": int(plan.info.tile_order),
+                     "split_k": int(plan.info.split_k), "tile_claim": int(plan.info.tile_claim),
                      "autotuned": tune is not None,
                      "candidates_ms_per_build": None if tune is None else tune["candidates"]},
         "tflops_dgemm_equiv": dgemm_equiv * steps_applied / (ms_per_step / 1e3) / 1e12,

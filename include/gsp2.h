@@ -134,6 +134,15 @@ typedef struct {
                               may turn it off.  The 64-bit sums are exact; the group sums of each
                               half are rounded in FP32 like the whole K's, so results agree to the
                               last bits only */
+  int32_t tile_claim;      /* persistent 128 x 128 steps (tensor-core steps and reverse steps, FP64_EMU
+                              forward and reverse steps): 1 (default) = each CTA takes its first
+                              tile by its index and claims every next one from a counter in the
+                              workspace, one tile ahead, walking the list of tile_order, so that
+                              CTAs that run faster take more tiles; 0 = the static deal (tile t
+                              to CTA t mod the number of SMs).  The rebuilt iterates of the
+                              adjoint (which may run beside reverse steps), the 128 x 256 tiles
+                              and the one-CTA-per-tile schedule keep the static deal.  Set by
+                              gsp2_autotune */
 } gsp2_options;
 
 /* Per-call report, read back by gsp2_sync_status. */
@@ -171,6 +180,7 @@ typedef struct {
   int32_t tile_order;
   int32_t tile_shape;
   int32_t split_k;         /* 1 if the emulated steps split K into two work items (in use now) */
+  int32_t tile_claim;      /* 1 if the persistent steps claim their tiles from a counter */
 } gsp2_plan_info;
 
 /* Fill `opt` with the defaults listed above. */
@@ -284,18 +294,20 @@ typedef struct {
   int32_t tile_shape[8];
   double ms[8];         /* median device time of one density call, milliseconds */
   int32_t split_k[8];   /* FP64_EMU: 1 if the candidate splits each tile's K into two work items */
+  int32_t tile_claim[8]; /* 1 if the candidate's persistent 128 x 128 steps claim their tiles */
 } gsp2_tune_report;
 
 /*
  * Autotuner of the step schedule (batching of uneven parts, not in the paper): times whole
  * density calls (RECORD mode, `trials` >= 1 each after one untimed call) with every candidate
- * that applies to the plan's precision -- tensor-core steps: persistent with either tile
- * order and either tile shape, and one CTA per tile; FP64_EMU steps: the three tile orders,
- * and for small plans split-K work items;
+ * that applies to the plan's precision -- tensor-core steps: persistent 128 x 128 tiles in
+ * tile orders 0 and 1, each with claimed tiles and with the static deal, 128 x 256 tiles in
+ * either order, and one CTA per tile; FP64_EMU steps: the three tile orders with claimed
+ * tiles, tile order 2 with the static deal, and for small plans split-K work items;
  * FP64 and FP32: the only schedule -- and keeps the fastest in the plan (gsp2_plan_query
- * reports it).  Every
- * candidate computes bitwise the same P (a tile's arithmetic does not depend on the CTA
- * that runs it).
+ * reports it).  Every candidate without split-K work items computes bitwise the same P (a
+ * tile's arithmetic does not depend on the CTA that runs it); split-K agrees to the last
+ * bits.
  *  d_hvals, d_pvals  as for gsp2_density; d_pvals is overwritten
  *  rep               optional output
  * Synchronises `stream`.  Errors: GSP2_E_ARG, GSP2_E_STATE (no workspace), GSP2_E_CUDA, or

@@ -249,6 +249,7 @@ extern "C" void gsp2_default_options(gsp2_options* o) {
   o->fp64_tail_emulated = 1;
   o->tile_order = 1;
   o->split_k = -1;
+  o->tile_claim = 1;
 }
 
 extern "C" const char* gsp2_last_error(gsp2_handle h) { return h ? h->err.c_str() : t_create_err.c_str(); }
@@ -456,6 +457,7 @@ static gsp2_status create_plan(int64_t n, const int64_t* rowptr, const int32_t* 
     if (o.tile_order < 0 || o.tile_order > 2) return bail(GSP2_E_ARG, "tile_order must be 0, 1 or 2");
     if (o.tile_shape < 0 || o.tile_shape > 1) return bail(GSP2_E_ARG, "tile_shape must be 0 or 1");
     if (o.split_k < -1 || o.split_k > 1) return bail(GSP2_E_ARG, "split_k must be -1, 0 or 1");
+    if (o.tile_claim < 0 || o.tile_claim > 1) return bail(GSP2_E_ARG, "tile_claim must be 0 or 1");
     if (o.lp_tail_steps > 0 && (fp64_like(o.precision) || o.precision == GSP2_PREC_FP32))
       return bail(GSP2_E_ARG, "lp_tail_steps needs a tensor-core precision");
     if (o.ckpt_every < -1) return bail(GSP2_E_ARG, "ckpt_every must be >= -1");
@@ -706,6 +708,7 @@ extern "C" gsp2_status gsp2_plan_query(gsp2_handle h, gsp2_plan_info* info, int3
     info->tile_order = h->opt.tile_order;
     info->tile_shape = h->opt.tile_shape;
     info->split_k = h->split_on ? 1 : 0;
+    info->tile_claim = h->opt.tile_claim;
   }
   for (int32_t k = 0; k < h->nparts; ++k) {
     if (s) s[k] = h->parts[k].s;
@@ -1024,7 +1027,7 @@ static OzStepArgs oz_args(gsp2_plan* h, const StepCtl& ctl) {
   a.nslots = h->nslots_tc;
   a.acc = (long long*)(w + L.oz_acc);
   a.ctl = ctl;
-  a.tile_ctr = (uint32_t*)(w + L.tile_ctr);
+  a.tile_ctr = h->opt.tile_claim ? (uint32_t*)(w + L.tile_ctr) : nullptr;
   if (h->split_on) {
     a.split = 1;
     a.split_acc = (long long*)(w + L.split_acc);
@@ -1154,6 +1157,7 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
       tc_args.ntiles = (int)(wide ? h->tc_wide.size() : h->tc_tiles.size());
       tc_args.ctl = lp;
       tc_args.tail = 0;
+      tc_args.tile_ctr = h->opt.tile_claim ? (uint32_t*)(w + L.tile_ctr) : nullptr;
     }
     for (int i = 1; i <= lp.last_step; ++i, ++seg) {
       if (!on()) continue;
@@ -1428,24 +1432,28 @@ extern "C" gsp2_status gsp2_autotune(gsp2_handle h, const double* d_hvals, doubl
   cudaStream_t s = (cudaStream_t)stream;
   // candidates (tc_schedule, tile_order) that change something for this precision
   struct Cand {
-    int sched, order, shape, split;
+    int sched, order, shape, split, claim;
   };
   std::vector<Cand> cand;
   const int prec = h->opt.precision;
   const int sp = h->split_on ? 1 : 0;
   if (!fp64_like(prec) && prec_kind(prec) >= 0)
-    cand = {{0, 0, 0, 0}, {0, 1, 0, 0}, {0, 0, 1, 0}, {0, 1, 1, 0}, {1, 0, 0, 0}};
+    cand = {{0, 0, 0, 0, 1}, {0, 1, 0, 0, 1}, {0, 0, 0, 0, 0}, {0, 1, 0, 0, 0},
+            {0, 0, 1, 0, 0}, {0, 1, 1, 0, 0}, {1, 0, 0, 0, 0}};
   else if (prec == GSP2_PREC_FP64_EMU && h->split_ok)
-    cand = {{0, 0, 0, 0}, {0, 1, 0, 0}, {0, 2, 0, 0}, {0, 0, 0, 1}, {0, 1, 0, 1}};
-  else if (prec == GSP2_PREC_FP64_EMU) cand = {{0, 0, 0, 0}, {0, 1, 0, 0}, {0, 2, 0, 0}};
-  else cand = {{h->opt.tc_schedule, h->opt.tile_order, h->opt.tile_shape, sp}};
+    cand = {{0, 0, 0, 0, 1}, {0, 1, 0, 0, 1}, {0, 2, 0, 0, 1}, {0, 0, 0, 1, 1}, {0, 1, 0, 1, 1}, {0, 2, 0, 0, 0}};
+  else if (prec == GSP2_PREC_FP64_EMU) cand = {{0, 0, 0, 0, 1}, {0, 1, 0, 0, 1}, {0, 2, 0, 0, 1}, {0, 2, 0, 0, 0}};
+  else cand = {{h->opt.tc_schedule, h->opt.tile_order, h->opt.tile_shape, sp, h->opt.tile_claim}};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CU(h, cudaEventCreate(&e0));
   CU(h, cudaEventCreate(&e1));
   auto apply = [&](const Cand& c) -> cudaError_t {
     // schedule and shape are part of the captured launches; the order only of the tile lists
-    if (c.sched != h->opt.tc_schedule || c.shape != h->opt.tile_shape || (c.split != 0) != h->split_on)
+    // (the claim counter's pointer is one of the launches' arguments)
+    if (c.sched != h->opt.tc_schedule || c.shape != h->opt.tile_shape || (c.split != 0) != h->split_on ||
+        c.claim != h->opt.tile_claim)
       drop_graph(h);
+    h->opt.tile_claim = c.claim;
     h->opt.tc_schedule = c.sched;
     h->opt.tile_order = c.order;
     h->opt.tile_shape = c.shape;
@@ -1515,6 +1523,7 @@ extern "C" gsp2_status gsp2_autotune(gsp2_handle h, const double* d_hvals, doubl
       rep->tile_order[c] = cand[c].order;
       rep->tile_shape[c] = cand[c].shape;
       rep->split_k[c] = cand[c].split;
+      rep->tile_claim[c] = cand[c].claim;
       rep->ms[c] = med[c];
     }
   }
@@ -1894,6 +1903,7 @@ static gsp2_status enqueue_backward_lp(gsp2_plan* h, const double* pbar, double*
   int smax = 1;
   for (const PartDesc& d : h->parts) smax = std::max(smax, (int)d.s);
   base.xb_headroom = (int)std::ceil(std::log2(2.0 + 2.0 * std::sqrt((double)smax))) + 1;
+  base.tile_ctr = h->opt.tile_claim ? (uint32_t*)(w + L.tile_ctr) : nullptr;
   for (int b = 0; b < 2; ++b) {
     base.map_hi[b] = amap(nsets + b, 0);
     base.map_lo[b] = amap(nsets + b, 1);

@@ -134,6 +134,9 @@ struct TcStepArgs {
   uint32_t* xb_max;
   int nparts;
   int xb_headroom;
+  // the persistent 128x128 kernel's steps and reverse steps: each CTA claims its next tile
+  // from this counter (zero between launches; the last block resets it); NULL: static deal
+  uint32_t* tile_ctr;
 };
 constexpr int TC_SIG_MIN = -98, TC_SIG_MAX = 126;  // range of the FP16 adjoint's scale exponents
 

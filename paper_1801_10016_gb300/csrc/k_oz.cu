@@ -521,9 +521,15 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
   if (warp == 0 && lane == 0) {
     uint32_t g = 0;
     bool bad = false;
+    // dynamic: the first item is blockIdx.x, the next ones gridDim.x + the counter's count,
+    // each claimed one item ahead so that the atomic's latency hides behind an item's loads
+    int nxt = dyn && (int)blockIdx.x < nitems ? (int)gridDim.x + (int)atomicAdd(a.tile_ctr, 1u) : nitems;
     for (int v = 0, it = blockIdx.x; !bad; ++v, it += gridDim.x) {
       if (dyn) {
-        it = (int)atomicAdd(a.tile_ctr, 1u);
+        if (v > 0) {
+          it = nxt;
+          if (it < nitems) nxt = (int)gridDim.x + (int)atomicAdd(a.tile_ctr, 1u);
+        }
         const int q = v % OZ_RING;
         if (v >= OZ_RING && !mbar_wait(item_empty(q), ((v / OZ_RING) - 1) & 1, abort_flag)) {
           bad = true;

@@ -324,6 +324,7 @@ __host__ __device__ constexpr int tc_tile_cols(int s, int tj) {
 }
 
 constexpr int TC_EPI_WARPS = 16;  // 4 per TMEM lane quarter, 32 columns each
+constexpr int TC_RING = 4;        // dynamic schedule: tiles claimed ahead of the MMA and epilogue warps
 constexpr int TC_THREADS = 32 * (4 + TC_EPI_WARPS);
 enum : int { TC_STEP = 0, TC_REBUILD = 1, TC_ADJOINT = 2 };
 
@@ -387,6 +388,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
   auto tile_addr = [&](int s, int op) { return base + (uint32_t)s * STAGE_B + (uint32_t)op * kTileBytes; };
   int32_t* abort_flag = &a.ctl.st->timeout;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // dynamic schedule (steps and reverse steps; the rebuilt iterates, which may run beside
+  // reverse steps and have no last block, keep the static deal): the producer claims each
+  // next tile from a counter in global memory and passes it to the MMA thread and the
+  // epilogue warps through a ring in shared memory (full: claimed; empty: read by all of
+  // them); -1 ends the walk
+  const bool dyn = a.tile_ctr != nullptr && MODE != TC_REBUILD;
+  const uint32_t ring_bars = smem_u32(red + TC_EPI_WARPS);
+  int* s_items = reinterpret_cast<int*>(reinterpret_cast<uint8_t*>(red + TC_EPI_WARPS) + 8 * 2 * TC_RING);
+  auto item_full = [&](int q) { return ring_bars + 8u * q; };
+  auto item_empty = [&](int q) { return ring_bars + 8u * (TC_RING + q); };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -396,6 +407,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull(b), 1);
       mbar_init(tempty(b), TC_EPI_WARPS);
+    }
+    for (int q = 0; q < TC_RING; ++q) {
+      mbar_init(item_full(q), 1);
+      mbar_init(item_empty(q), 1 + TC_EPI_WARPS);
     }
     *s_err = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -413,7 +428,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
     // producer: one ring of stages across all tiles of this CTA
     uint32_t g = 0;
     bool bad = false;
-    for (int ti = blockIdx.x; ti < a.ntiles && !bad; ti += gridDim.x) {
+    // dynamic: the first item is blockIdx.x, the next ones gridDim.x + the counter's count,
+    // each claimed one item ahead so that the atomic's latency hides behind an item's loads
+    int nxt = dyn && (int)blockIdx.x < a.ntiles ? (int)gridDim.x + (int)atomicAdd(a.tile_ctr, 1u) : a.ntiles;
+    for (int v = 0, ti = blockIdx.x; !bad; ++v, ti += gridDim.x) {
+      if (dyn) {
+        if (v > 0) {
+          ti = nxt;
+          if (ti < a.ntiles) nxt = (int)gridDim.x + (int)atomicAdd(a.tile_ctr, 1u);
+        }
+        const int q = v % TC_RING;
+        if (v >= TC_RING && !mbar_wait(item_empty(q), ((v / TC_RING) - 1) & 1, abort_flag)) {
+          bad = true;
+          break;
+        }
+        s_items[q] = ti < a.ntiles ? ti : -1;
+        mbar_arrive(item_full(q));
+      }
+      if (ti >= a.ntiles) break;
       const Tile t = a.tiles[ti];
       const PartDesc p = a.parts[t.part];
       // operand maps: the step's input iterate (MODE 0: by parity; 1 and 2: the rebuilt X)
@@ -492,7 +524,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
     uint32_t g = 0;
     int i = 0;
     bool bad = false;
-    for (int ti = blockIdx.x; ti < a.ntiles && !bad; ti += gridDim.x, ++i) {
+    for (int ti = blockIdx.x; !bad; ti += gridDim.x, ++i) {
+      if (dyn) {
+        const int q = i % TC_RING;
+        if (!mbar_wait(item_full(q), (i / TC_RING) & 1, abort_flag)) {
+          bad = true;
+          break;
+        }
+        ti = s_items[q];
+        mbar_arrive(item_empty(q));
+        if (ti < 0) break;
+      }
+      if (ti >= a.ntiles) break;
       const Tile t = a.tiles[ti];
       const PartDesc p = a.parts[t.part];
       const bool dg = MODE != TC_ADJOINT && t.ti == t.tj;
@@ -562,7 +605,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
     const int quarter = warp & 3, colq = (warp - 4) >> 2;
     const int m = quarter * 32 + lane;
     int i = 0;
-    for (int ti = blockIdx.x; ti < a.ntiles; ti += gridDim.x, ++i) {
+    for (int ti = blockIdx.x;; ti += gridDim.x, ++i) {
+      if (dyn) {
+        const int q = i % TC_RING;
+        const bool got = __all_sync(0xffffffffu, mbar_wait(item_full(q), (i / TC_RING) & 1, abort_flag));
+        if (!got) {
+          *s_err = 1;
+          break;
+        }
+        ti = s_items[q];
+        __syncwarp();
+        if (lane == 0) mbar_arrive(item_empty(q));
+        if (ti < 0) break;
+      }
+      if (ti >= a.ntiles) break;
       const int b = i & 1, u = i >> 1;
       const bool ok = __all_sync(0xffffffffu, mbar_wait(tfull(b), u & 1, abort_flag));
       tc_fence_after();
@@ -702,7 +758,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
       a.xb_sig[k] = a.xb_sig[a.nparts + k];
       a.xb_sig[a.nparts + k] = e < TC_SIG_MIN ? TC_SIG_MIN : (e > TC_SIG_MAX ? TC_SIG_MAX : e);
     }
-    if (threadIdx.x == 0) a.ctl.st->counter = 0;
+    if (threadIdx.x == 0) {
+      a.ctl.st->counter = 0;
+      if (dyn) *a.tile_ctr = 0u;  // every CTA has claimed its last tile
+    }
   }
   if (MODE != TC_STEP) return;
 
@@ -727,6 +786,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) square_tc_persistent_kernel(TcS
         finish_step(a.ctl, step, sum.y, sum.x);
       }
       a.ctl.st->counter = 0;
+      if (dyn) *a.tile_ctr = 0u;  // every CTA has claimed its last tile: ready for the next launch
     }
   }
 }
@@ -1030,7 +1090,8 @@ template <int KIND, int NPROD, int MODE = TC_STEP>
 static cudaError_t launch_tc_persistent(const TcStepArgs& a, int grid, cudaStream_t s) {
   constexpr int NOPS = NPROD == 3 ? 4 : 2;
   constexpr int STAGES = NPROD == 3 ? 3 : 4;
-  const int smem = STAGES * NOPS * (int)kTileBytes + 1024 + 8 * (2 * STAGES + 4) + 16 + 16 * TC_EPI_WARPS;
+  const int smem =
+      STAGES * NOPS * (int)kTileBytes + 1024 + 8 * (2 * STAGES + 4) + 16 + 16 * TC_EPI_WARPS + 8 * 2 * TC_RING + 4 * TC_RING;
   cudaError_t e = cudaFuncSetAttribute(square_tc_persistent_kernel<KIND, NPROD, MODE>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;

@@ -37,7 +37,8 @@ class Options(C.Structure):
                 ("precision", C.c_int32), ("fp64_tail_steps", C.c_int32), ("ckpt_every", C.c_int32),
                 ("use_graph", C.c_int32), ("time_steps", C.c_int32), ("lp_tail_steps", C.c_int32),
                 ("tc_schedule", C.c_int32), ("report_idem", C.c_int32), ("fp64_tail_emulated", C.c_int32),
-                ("tile_order", C.c_int32), ("tile_shape", C.c_int32), ("split_k", C.c_int32)]
+                ("tile_order", C.c_int32), ("tile_shape", C.c_int32), ("split_k", C.c_int32),
+                ("tile_claim", C.c_int32)]
 
 
 class Report(C.Structure):
@@ -52,13 +53,13 @@ class PlanInfo(C.Structure):
                 ("nnz_p", C.c_int64), ("arena_elems", C.c_int64), ("ntiles", C.c_int64), ("tile", C.c_int32),
                 ("ld_pad", C.c_int32), ("step_launches", C.c_int32), ("fp64_tail_steps", C.c_int32),
                 ("tc_schedule", C.c_int32), ("tile_order", C.c_int32), ("tile_shape", C.c_int32),
-                ("split_k", C.c_int32)]
+                ("split_k", C.c_int32), ("tile_claim", C.c_int32)]
 
 
 class TuneReport(C.Structure):
     _fields_ = [("ncand", C.c_int32), ("chosen", C.c_int32), ("tc_schedule", C.c_int32 * 8),
                 ("tile_order", C.c_int32 * 8), ("tile_shape", C.c_int32 * 8), ("ms", C.c_double * 8),
-                ("split_k", C.c_int32 * 8)]
+                ("split_k", C.c_int32 * 8), ("tile_claim", C.c_int32 * 8)]
 
 
 _lib = None
@@ -291,7 +292,7 @@ class GSP2:
                                             _stream_ptr(stream), C.byref(r)))
         self._refresh_info()
         cands = [dict(tc_schedule=r.tc_schedule[i], tile_order=r.tile_order[i], tile_shape=r.tile_shape[i],
-                      split_k=r.split_k[i], ms=r.ms[i]) for i in range(r.ncand)]
+                      split_k=r.split_k[i], tile_claim=r.tile_claim[i], ms=r.ms[i]) for i in range(r.ncand)]
         return dict(chosen=r.chosen, candidates=cands)
 
     def density_reuse(self, h_vals, alpha, nsteps, out=None, stream=None):
@@ -333,6 +334,7 @@ class GSP2:
         self.options.tc_schedule = info.tc_schedule
         self.options.tile_order = info.tile_order
         self.options.tile_shape = info.tile_shape
+        self.options.tile_claim = info.tile_claim
 
     def status(self):
         """(status code, report dict) of the last density call; waits for it."""

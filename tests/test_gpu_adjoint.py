@@ -286,6 +286,21 @@ def torch_from(x):
     return torch.from_numpy(x).to("cuda:0")
 
 
+@pytest.mark.parametrize("prec", ["fp64e", "fp16x3"])
+def test_adjoint_claimed_tiles_match_the_static_deal(g, prec):
+    """Reverse steps whose CTAs claim their tiles from a counter against the static deal: a
+    tile's arithmetic does not depend on the CTA that runs it, so the same Hbar bit for bit,
+    also on a second backward (the counter is left at zero)."""
+    s = make_workload("tb4k")
+    kw = dict(precision=prec, ckpt_every=8, split_k=0)
+    plan1, _, _, pb, _, hb1 = run_adjoint(g, s, tile_claim=1, **kw)
+    plan0, _, _, _, _, hb0 = run_adjoint(g, s, tile_claim=0, **kw)
+    assert plan1.info.tile_claim == 1 and plan0.info.tile_claim == 0
+    a = hb1.cpu().numpy()
+    assert np.array_equal(a, hb0.cpu().numpy())
+    assert np.array_equal(plan1.backward(torch_from(pb)).cpu().numpy(), a)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp64e", "fp16x3"])
 def test_adjoint_after_a_status_read_is_the_same(g, prec):
     """Once gsp2_sync_status has read the applied step count, the adjoint schedules only those

@@ -1,6 +1,7 @@
-"""The schedule autotuner and the tile orders it chooses between: every tile order computes
-bitwise the same P (a tile's arithmetic does not depend on the CTA that runs it), split-K
-work items the same P to the last bits, and the autotuner keeps a candidate it timed."""
+"""The schedule autotuner and the tile orders it chooses between: every tile order, and the
+static deal or claimed tiles, computes bitwise the same P (a tile's arithmetic does not
+depend on the CTA that runs it), split-K work items the same P to the last bits, and the
+autotuner keeps a candidate it timed."""
 
 import numpy as np
 import pytest
@@ -32,13 +33,17 @@ def run(g, s, **opt):
     return plan, h, p.cpu().numpy()
 
 
-@pytest.mark.parametrize("prec", ["tf32x3", "fp64e"])
+@pytest.mark.parametrize("prec", ["tf32x3", "fp16x3", "fp64e"])
 def test_tile_orders_give_bitwise_equal_p(g, prec):
     s = make_workload("tb4k")  # more 128-tiles than SMs: the second order differs
     _, _, p0 = run(g, s, precision=prec, tile_order=0)
     _, _, p1 = run(g, s, precision=prec, tile_order=1)
     _, _, p2 = run(g, s, precision=prec, tile_order=2)
     assert np.array_equal(p0, p1) and np.array_equal(p0, p2)
+    # the static deal against claimed tiles (the default)
+    pl, _, p3 = run(g, s, precision=prec, tile_order=1, tile_claim=0)
+    assert pl.info.tile_claim == 0
+    assert np.array_equal(p0, p3)
 
 
 @pytest.mark.parametrize("prec", ["tf32x3", "bf16x3", "tf32", "bf16", "fp16x3"])
@@ -58,14 +63,17 @@ def test_autotune_keeps_a_timed_candidate(g, prec):
     plan, h, p0 = run(g, s, precision=prec)
     rep = plan.autotune(h, trials=2)
     cands = rep["candidates"]
-    # fp64e on this plan (193 tiles, parts above 128 orbitals): the three tile orders, and the
-    # first two with split-K work items
-    assert len(cands) == {"tf32x3": 5, "fp16x3": 5, "fp64e": 5, "fp64": 1}[prec]
+    # tensor-core steps: orders 0 and 1 with claimed tiles and with the static deal, the
+    # 128 x 256 tiles in either order, one CTA per tile; fp64e on this plan (193 tiles, parts
+    # above 128 orbitals): the three tile orders with claimed tiles, the first two with
+    # split-K work items, order 2 with the static deal
+    assert len(cands) == {"tf32x3": 7, "fp16x3": 7, "fp64e": 6, "fp64": 1}[prec]
     assert all(c["ms"] > 0 for c in cands)
     best = cands[rep["chosen"]]
     assert best["ms"] == min(c["ms"] for c in cands)
-    assert (plan.info.tc_schedule, plan.info.tile_order, plan.info.tile_shape, plan.info.split_k) == (
-        best["tc_schedule"], best["tile_order"], best["tile_shape"], best["split_k"])
+    assert (plan.info.tc_schedule, plan.info.tile_order, plan.info.tile_shape, plan.info.split_k,
+            plan.info.tile_claim) == (best["tc_schedule"], best["tile_order"], best["tile_shape"], best["split_k"],
+                                      best["tile_claim"])
     p1 = plan.density(h).cpu().numpy()
     if best["split_k"] == 1:  # the default of this plan: bitwise the same
         assert np.array_equal(p0, p1)

@@ -147,6 +147,11 @@ def test_tile_order_option(g):
         with pytest.raises(g.GSP2Error):
             _plan(g, s, tile_shape=bad)
     assert _plan(g, s, precision="tf32x3", tile_shape=1).info.tile_shape == 1
+    assert g.default_options().tile_claim == 1
+    for bad in (-1, 2):
+        with pytest.raises(g.GSP2Error):
+            _plan(g, s, tile_claim=bad)
+    assert _plan(g, s, precision="fp16x3", tile_claim=0).info.tile_claim == 0
 
 
 def test_low_precision_adjoint_layout(g):
