@@ -399,6 +399,42 @@ __device__ __forceinline__ void oz_issue_stage(uint32_t tmem, uint64_t da, uint6
   }
 }
 
+// z[j] += g_d[j] 2^(56 - 7 (d + 2)) for the groups D0 <= d < D1 of one 16-column chunk: the
+// group sums g_d (integers, held exactly in FP32) in units of 2^-56.  A chunk whose sums all
+// lie below 2^22 in magnitude is converted without the conversion unit: g + 1.5 2^23 is a
+// float in [2^23, 2^24) whose bit pattern is 0x4B400000 + g, and a 32 x 32 -> 64-bit
+// multiply-add (by the power of two, or on the upper word for weights of 2^32 and more)
+// accumulates it; any other chunk goes through the exact rounding conversion (|g| < 2^31).
+template <int D0, int D1>
+__device__ __forceinline__ void oz_drain_groups(uint32_t taddr, long long (&z)[16]) {
+#pragma unroll
+  for (int d = D0; d < D1; ++d) {
+    uint32_t v[16];
+    tmem_ld16(taddr + oz_group_col(d), v);
+    const int shift = 56 - 7 * (d + 2);  // group weight 2^{-7(d+2)} in units of 2^-56
+    float mx = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) mx = fmaxf(mx, fabsf(__uint_as_float(v[j])));
+    if (__all_sync(0xffffffffu, mx < 4194304.0f)) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int32_t g = (int32_t)(__float_as_uint(__fadd_rn(__uint_as_float(v[j]), 12582912.0f)) - 0x4B400000u);
+        if (shift < 32) {
+          asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(z[j]) : "r"(g), "r"(1 << (shift & 31)));
+        } else {
+          z[j] += (long long)((unsigned long long)((uint32_t)g << (shift - 32)) << 32);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const long long g = (long long)__float2int_rn(__uint_as_float(v[j]));
+        z[j] += (long long)((unsigned long long)g << shift);
+      }
+    }
+  }
+}
+
 // |v| 2^-56 as FP32 (integer instructions, truncated: at most 2^-23 below), for the row
 // norms of the adjoint's new Xbar on its fixed-point grid.
 __device__ __forceinline__ float fixed_to_f32_abs(long long v) {
@@ -727,7 +763,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
       for (int pass = 0; pass < 2; ++pass) {
         ok = __all_sync(0xffffffffu, mbar_wait(afull(pass), u & 1, abort_flag)) && ok;
         tc_fence_after();
-        const int d0 = pass == 0 ? OZ_SPLIT : 0, d1 = pass == 0 ? T : OZ_SPLIT;
 #pragma unroll 1
         for (int cc = 0; cc < 2 && ok; ++cc) {
           const int cl = colq * 32 + cc * 16;
@@ -736,17 +771,8 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
           long long* zp = acc + (size_t)cl * 128 + m;
 #pragma unroll
           for (int j = 0; j < 16; ++j) z[j] = pass == 0 ? 0ll : zp[(size_t)j * 128];
-#pragma unroll 1
-          for (int d = d0; d < d1; ++d) {
-            uint32_t v[16];
-            tmem_ld16(tmem + lane_off + oz_group_col(d) + (uint32_t)cl, v);
-            const int shift = 56 - 7 * (d + 2);  // group weight 2^{-7(d+2)} in units of 2^-56
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const long long g = (long long)__float2int_rn(__uint_as_float(v[j]));  // exact: |sum| < 2^31
-              z[j] += (long long)((unsigned long long)g << shift);
-            }
-          }
+          if (pass == 0) oz_drain_groups<OZ_SPLIT, T>(tmem + lane_off + (uint32_t)cl, z);
+          else oz_drain_groups<0, OZ_SPLIT>(tmem + lane_off + (uint32_t)cl, z);
 #pragma unroll
           for (int j = 0; j < 16; ++j) zp[(size_t)j * 128] = z[j];
         }
