@@ -30,12 +30,13 @@ UNIT = "P-builds/s"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # nominal dense rates (TFLOP/s) used to derive a dtype's peak from the measured bf16 one
 NOMINAL = {"bf16": 2250.0, "tf32": 1100.0, "fp64": 1.25}
-# DRAM bytes per launch of the dominant kernel from one ncu capture (workload, precision);
-# entries are removed when the kernel changes (fp64e: the emulated step changed after its
-# last capture, so its traffic is reported as null)
-# DRAM bytes (read + write) per launch of the step kernel, from ncu captures (see profiles/):
-# the FP64 step on tb30k directly, the emulated step on tb8k scaled by arena elements (x 4.98)
-TRAFFIC = {("tb30k", "fp64"): 2.80e9, ("tb30k", "fp64e"): 1.058e9 * 191545344 / 38469632}
+# DRAM bytes (read + write) per launch of the step kernel, from one ncu capture of the kernel
+# as it is now (the summaries are under profiles/): the FP64 step on tb30k directly, the
+# emulated and tensor-core steps on tb8k (tb30k's part sizes) scaled to tb30k by arena
+# elements; an entry is dropped when its kernel changes, and the line then reports null
+TB8K_TO_TB30K = 191545344 / 38469632
+TRAFFIC = {("tb30k", "fp64"): 2.80e9, ("tb30k", "fp64e"): 1.1033e9 * TB8K_TO_TB30K,
+           ("tb30k", "fp16x3"): 0.2712e9 * TB8K_TO_TB30K, ("tb30k", "tf32x3"): 0.7313e9 * TB8K_TO_TB30K}
 
 
 def dist_env():
@@ -284,7 +285,7 @@ def step_roofline(precision, sizes, avg_launch_ms, peaks, src, workload, sched=N
     peak = peaks["bf16_tflops"] * NOMINAL["tf32"] / NOMINAL["bf16"] if tf32 else peaks["bf16_tflops"]
     kname = "tf32" if tf32 else ("fp16" if precision.startswith("fp16") else "bf16")
     return {"bound": "tensor", "achieved": flops / t / 1e12, "peak": peak, "unit": "TFLOP/s",
-            "frac": flops / t / 1e12 / peak, "traffic": None,
+            "frac": flops / t / 1e12 / peak, "traffic": TRAFFIC.get((workload, precision)) if trim else None,
             "kernel": f"square_tc_persistent_kernel<{kname},{nprod}>",
             "peak_source": (f"{src}: bf16 burst x nominal tf32/bf16 {NOMINAL['tf32']}/{NOMINAL['bf16']} (of measured)"
                             if tf32 else f"{src}: bf16 burst (of measured; fp16 and bf16 share the 16-bit dense rate)"),
