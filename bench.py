@@ -31,11 +31,11 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # nominal dense rates (TFLOP/s) used to derive a dtype's peak from the measured bf16 one
 NOMINAL = {"bf16": 2250.0, "tf32": 1100.0, "fp64": 1.25}
 # DRAM bytes (read + write) per launch of the step kernel, from one ncu capture of the kernel
-# as it is now (the summaries are under profiles/): the FP64 step on tb30k directly, the
-# emulated and tensor-core steps on tb8k (tb30k's part sizes) scaled to tb30k by arena
-# elements; an entry is dropped when its kernel changes, and the line then reports null
+# as it is now (the summaries are under profiles/): each step on tb8k (tb30k's part sizes)
+# scaled to tb30k by arena elements; an entry is dropped when its kernel changes, and the
+# line then reports null
 TB8K_TO_TB30K = 191545344 / 38469632
-TRAFFIC = {("tb30k", "fp64"): 2.80e9, ("tb30k", "fp64e"): 1.1033e9 * TB8K_TO_TB30K,
+TRAFFIC = {("tb30k", "fp64"): 0.5270e9 * TB8K_TO_TB30K, ("tb30k", "fp64e"): 1.1033e9 * TB8K_TO_TB30K,
            ("tb30k", "fp16x3"): 0.2712e9 * TB8K_TO_TB30K, ("tb30k", "tf32x3"): 0.7313e9 * TB8K_TO_TB30K}
 
 

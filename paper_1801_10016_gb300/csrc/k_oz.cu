@@ -59,11 +59,19 @@ __device__ __forceinline__ void digit_words(long long v, uint32_t (&fw)[OZ_SLICE
   fw[0] = __float_as_uint(__fsub_rn(__uint_as_float(0x4B000000u | (uint32_t)(s0 + 256)), 8388864.0f));
 }
 
-__device__ __forceinline__ void store_digits(uint16_t* const* slices, int64_t e, long long v) {
-  uint32_t fw[OZ_SLICES];
-  digit_words(v, fw);
+// The digits of four consecutive elements e .. e + 3 (e a multiple of 4), one 8-byte store
+// per digit array (a warp's lanes on consecutive groups of four write 256 B per store).
+__device__ __forceinline__ void store_digits4(uint16_t* const* slices, int64_t e, const long long (&v)[4]) {
+  uint32_t fw[4][OZ_SLICES];
 #pragma unroll
-  for (int t = 0; t < OZ_SLICES; ++t) slices[t][e] = (uint16_t)(fw[t] >> 16);
+  for (int i = 0; i < 4; ++i) digit_words(v[i], fw[i]);
+#pragma unroll
+  for (int t = 0; t < OZ_SLICES; ++t) {
+    uint2 pk;  // upper halves of two words per 32 bits
+    pk.x = __byte_perm(fw[0][t], fw[1][t], 0x7632);
+    pk.y = __byte_perm(fw[2][t], fw[3][t], 0x7632);
+    *reinterpret_cast<uint2*>(slices[t] + e) = pk;
+  }
 }
 
 // Conversions between FP64 and the 2^-56 fixed point of x / 2^sig done with integer
@@ -124,8 +132,13 @@ __global__ void __launch_bounds__(256) oz_slice_kernel(const PartDesc* __restric
   const int lane = threadIdx.x & 31;
   const int j = b.j0 + (threadIdx.x >> 5);
   if (j >= p.ld) return;
-  const int64_t cbase = p.off + (int64_t)j * p.ld;
-  for (int r = lane; r < p.ld; r += 32) store_digits(sl.s, cbase + r, to_fixed(X[cbase + r]));
+  const int64_t cbase = p.off + (int64_t)j * p.ld;  // ld and the arena offsets are multiples of 128
+  for (int r = 4 * lane; r < p.ld; r += 128) {
+    long long v[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = to_fixed(X[cbase + r + i]);
+    store_digits4(sl.s, cbase + r, v);
+  }
 }
 
 // Start of the emulated FP64 tail of a low-precision run: the last FP32 iterate (found on the
@@ -147,10 +160,16 @@ __global__ void __launch_bounds__(256) oz_convert_slice_kernel(const PartDesc* _
   if (j >= p.ld) return;
   const int rows = min(p.ld, (j / 128 + 1) * 128);
   const int64_t cbase = p.off + (int64_t)j * p.ld;
-  for (int r = lane; r < rows; r += 32) {
-    const double x = (double)in[cbase + r];
-    X[cbase + r] = x;
-    store_digits(sl.s, cbase + r, to_fixed(x));
+  for (int r = 4 * lane; r < rows; r += 128) {  // rows and cbase are multiples of 128
+    const float4 f = *reinterpret_cast<const float4*>(in + cbase + r);
+    const double x[4] = {(double)f.x, (double)f.y, (double)f.z, (double)f.w};
+    double2* xo = reinterpret_cast<double2*>(X + cbase + r);
+    xo[0] = make_double2(x[0], x[1]);
+    xo[1] = make_double2(x[2], x[3]);
+    long long v[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = to_fixed(x[i]);
+    store_digits4(sl.s, cbase + r, v);
   }
 }
 
@@ -191,7 +210,12 @@ __global__ void __launch_bounds__(32 * COLS_PER_BLOCK) oz_gather_kernel(
     }
     __syncwarp();  // the lanes' stores to the column are visible to the whole warp
     const int64_t cbase = p.off + (int64_t)j * p.ld;
-    for (int r = lane; r < rend; r += 32) store_digits(dig.s, cbase + r, to_fixed(col[r]));
+    for (int r = 4 * lane; r < rend; r += 128) {  // rend and cbase are multiples of 128
+      long long v[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) v[i] = to_fixed(col[r + i]);
+      store_digits4(dig.s, cbase + r, v);
+    }
   }
   const double2 t = block_sum2(tr, 0.0);
   if (threadIdx.x == 0) slots[blockIdx.x] = t.x;
@@ -310,10 +334,12 @@ __global__ void __launch_bounds__(256) oz_digits_kernel(const PartDesc* __restri
   const int sg = sig ? sig[b.part] : 0;
   const int rend = min(p.ld, (j / 128 + 1) * 128);
   const int64_t cbase = p.off + (int64_t)j * p.ld;
-  for (int r = lane; r < rend; r += 32) {
-    long long v = 0;
-    if (r < p.s && j < p.s && sg != OZ_SIG_NONFINITE) v = to_fixed(X[cbase + r], sg);
-    store_digits(out.s, cbase + r, v);
+  for (int r = 4 * lane; r < rend; r += 128) {  // rend and cbase are multiples of 128
+    long long v[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      v[i] = (r + i < p.s && j < p.s && sg != OZ_SIG_NONFINITE) ? to_fixed(X[cbase + r + i], sg) : 0ll;
+    store_digits4(out.s, cbase + r, v);
   }
 }
 
