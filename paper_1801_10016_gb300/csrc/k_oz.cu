@@ -344,7 +344,8 @@ __global__ void __launch_bounds__(256) oz_digits_kernel(const PartDesc* __restri
 }
 
 // One FP64-accurate purification step for every part, in one persistent launch (one CTA
-// per SM walks the upper 128x128 tiles blockIdx.x, blockIdx.x + gridDim.x, ...).
+// per SM walks the upper 128x128 tiles: blockIdx.x, then the ones it claims from a counter,
+// or blockIdx.x + gridDim.x, ... in the static deal).
 //
 // The T(T+1)/2 digit products of a tile need one FP32 accumulator per group d = a + b
 // (T x 128 TMEM columns), more than the 512 columns of an SM, so a tile takes two passes

@@ -298,8 +298,9 @@ __global__ void __launch_bounds__(256, 2) square_tc_kernel(TcStepArgs a) {
   }
 }
 
-// Persistent variant: one CTA per SM walks the tiles blockIdx.x, blockIdx.x + gridDim.x,
-// ... (largest parts first).  Two TMEM accumulators let the epilogue of one tile run
+// Persistent variant: one CTA per SM walks the tiles (largest parts first): blockIdx.x,
+// then the ones its producer claims from a counter (steps and reverse steps), or
+// blockIdx.x + gridDim.x, ... in the static deal.  Two TMEM accumulators let the epilogue of one tile run
 // while the tensor cores work on the next.  20 warps: warp 0 lane 0 issues TMA loads,
 // warp 1 owns TMEM and its lane 0 issues tcgen05.mma, warps 4..19 drain TMEM (four per
 // lane quarter, so that the epilogue, which writes the master and operand copies of the
