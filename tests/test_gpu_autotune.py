@@ -96,6 +96,9 @@ def test_split_k_items_of_the_emulated_steps(g):
     assert np.max(np.abs(p_split - p_one)) <= 1e-14
     _, _, p_split0 = run(g, s, precision="fp64e", split_k=1, tile_order=0)
     assert np.array_equal(p_split, p_split0)
+    # split items dealt statically: the same bits as claimed ones
+    _, _, p_split_static = run(g, s, precision="fp64e", split_k=1, tile_claim=0)
+    assert np.array_equal(p_split, p_split_static)
     from synth.tb import make_tb_system
     small = make_tb_system(33, 5, 3.2, seed=133)  # parts of fewer than 128 orbitals
     pc, _, _ = run(g, small, precision="fp64e", split_k=1)
