@@ -1219,8 +1219,12 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
     if (!on()) return GSP2_OK;
     // emulated tail steps, and the 16-bit steps without a tail, leave the upper 128-tiles only
     const int ub = ((h->use_oz && T > 0) || (lp_upper && T == 0)) ? TC_TILE : 0;
-    CU(h, launch_scatter(parts, sbl, (int)h->sblocks.size(), Sall, perm, pcol, nullptr, d[T & 1], pv, st, s, ub));
+    CU(h, launch_scatter(parts, sbl, (int)h->sblocks.size(), Sall, perm, pcol, nullptr, d[T & 1], pv, st, s, ub,
+                         h->use_oz));
     if (h->opt.report_idem) {
+      // the emulated tail keeps the iterate in 64-bit fixed point: FP64 for the residual
+      if (h->use_oz)
+        CU(h, launch_fixed_to_fp64(nullptr, d[T & 1], st, h->arena_elems, h->num_sms, s));
       if (ub) CU(h, launch_symmetrize(parts, (const Tile*)(w + L.tc_tiles), (int)h->tc_tiles.size(), nullptr, d[T & 1],
                                       st, s));
       CU(h, launch_residual_fp64(parts, tiles, (int)h->tiles.size(), d[T & 1], nullptr, (double*)(w + L.rslots),
@@ -1262,11 +1266,16 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
   }
   if (!on()) return GSP2_OK;
   CU(h, launch_scatter(parts, sbl, (int)h->sblocks.size(), Sall, perm, pcol, (const double* const*)(w + L.step_arena),
-                       nullptr, pv, st, s, emu ? TC_TILE : 0));
+                       nullptr, pv, st, s, emu ? TC_TILE : 0, emu));
   if (h->opt.report_idem) {
-    if (emu)
+    if (emu) {
+      // the emulated steps keep the iterate in 64-bit fixed point: FP64 for the residual
+      // (the backward never reads the last iterate)
+      CU(h, launch_fixed_to_fp64((const double* const*)(w + L.step_arena), nullptr, st, h->arena_elems,
+                                 h->num_sms, s));
       CU(h, launch_symmetrize(parts, (const Tile*)(w + L.tc_tiles), (int)h->tc_tiles.size(),
                               (const double* const*)(w + L.step_arena), nullptr, st, s));
+    }
     CU(h, launch_residual_fp64(parts, tiles, (int)h->tiles.size(), nullptr, (const double* const*)(w + L.step_arena),
                                (double*)(w + L.rslots), h->n, ctl, s));
   }

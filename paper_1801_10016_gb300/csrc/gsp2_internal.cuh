@@ -171,8 +171,8 @@ struct OzStepArgs {
   float* normf;          // adjoint: squared row norms of the new Xbar / 2^sig (zero between steps)
   int nparts;
   OzSlices digits[2];
-  const double* xin;   // FP64 master of X_{step-1}
-  double* xout;        // FP64 master of X_step
+  const double* xin;   // master of X_{step-1}: 64-bit fixed point x 2^56 (the adjoint's Xbar: FP64)
+  double* xout;        // master of X_step, the same form
   double2* slots;      // diagonal-tile trace slots
   int nslots;
   long long* acc;      // OZ_MAX_GRID x 128 x 128 fixed-point partial sums, one tile per CTA
@@ -353,6 +353,51 @@ __device__ __forceinline__ void finish_tail(const StepCtl& c, int step, double t
     st->nonfinite = 1;
     st->status = ST_NONFINITE;
   }
+}
+
+// Conversions between FP64 and the 2^-56 fixed point of x / 2^sig done with integer
+// instructions (the FP64 pipe of GB300 is 64x slower than its integer pipe), rounding to
+// nearest even.  |x| / 2^sig < 2^7; larger inputs saturate, results below 2^-1022 flush to 0.
+__device__ __forceinline__ long long to_fixed(double x, int sig = 0) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  if (ex == 0) return 0;                                    // zero and subnormals (< 2^-1022)
+  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int sh = ex - 1023 - 52 + 56 - sig;                 // (x / 2^sig) * 2^56 = m * 2^sh
+  unsigned long long a;
+  if (sh > 10) {
+    a = 1ull << 62;                                         // out of range: saturate
+  } else if (sh >= 0) {
+    a = m << sh;
+  } else if (sh > -64) {
+    const int k = -sh;
+    const unsigned long long q = m >> k, rem = m & ((1ull << k) - 1), half = 1ull << (k - 1);
+    a = q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull);
+  } else {
+    a = 0;
+  }
+  return (b >> 63) ? -(long long)a : (long long)a;
+}
+
+__device__ __forceinline__ double from_fixed(long long v, int sig = 0) {
+  if (v == 0) return 0.0;
+  const unsigned long long sgn = v < 0 ? (1ull << 63) : 0ull;
+  const unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
+  const int lz = __clzll(a);
+  const unsigned long long m = a << lz;                     // top bit at 63
+  unsigned long long mant = m >> 11;                        // 53 bits with the leading one
+  const unsigned long long rem = m & 0x7FFull;
+  int e = 63 - lz - 56 + sig;                               // value = 1.f x 2^e
+  if (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) {
+    mant += 1;
+    if (mant >> 53) {
+      mant >>= 1;
+      e += 1;
+    }
+  }
+  if (e < -1022) return __longlong_as_double((long long)sgn);
+  const unsigned long long bits = sgn | ((unsigned long long)(e + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFull);
+  return __longlong_as_double((long long)bits);
 }
 
 }  // namespace gsp2

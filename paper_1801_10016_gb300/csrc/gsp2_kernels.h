@@ -24,7 +24,10 @@ cudaError_t launch_square_fp32(const PartDesc* parts, const Tile* tiles, int nti
 cudaError_t launch_scatter(const PartDesc* parts, const ColBlock* blocks, int nblocks, const int32_t* Sall,
                            const int32_t* perm, const int64_t* pcolptr, const double* const* arena_of_step,
                            const double* fixed_arena, double* pvals, const DevState* st, cudaStream_t s,
-                           int upper_block = 0);
+                           int upper_block = 0, int fx = 0);
+// an arena of 64-bit fixed point (x 2^56) to FP64 in place (arena, or arena_of_step[steps])
+cudaError_t launch_fixed_to_fp64(const double* const* arena_of_step, double* arena, const DevState* st, int64_t n,
+                                 int nsm, cudaStream_t s);
 cudaError_t launch_symmetrize(const PartDesc* parts, const Tile* tiles, int ntiles, const double* const* arena_of_step,
                               double* fixed_arena, const DevState* st, cudaStream_t s);
 
@@ -47,10 +50,8 @@ cudaError_t launch_copy_iterate(const float* const* master_of_step, float* out, 
 cudaError_t launch_convert(const float* const* master_of_step, double* out, int64_t n, const DevState* st,
                            cudaStream_t s);
 // FP64 products from BF16 digits (k_oz.cu)
-cudaError_t launch_oz_slice(const PartDesc* parts, const ColBlock* blocks, int nblocks, const double* X,
-                            const OzSlices* digits, const DevState* st, cudaStream_t s);
 cudaError_t launch_oz_step(const OzStepArgs& a, int grid, cudaStream_t s, bool adjoint = false);
-// the last FP32 iterate of a low-precision run as FP64 master and digits (upper rows only)
+// the last FP32 iterate of a low-precision run as fixed-point master and digits (upper rows only)
 cudaError_t launch_oz_convert_slice(const PartDesc* parts, const ColBlock* blocks, int nblocks,
                                     const float* const* master_of_step, double* X, const OzSlices* digits,
                                     const DevState* st, cudaStream_t s);

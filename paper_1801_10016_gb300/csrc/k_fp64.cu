@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(256) scatter_kernel(const PartDesc* __restrict
                                                       const double* const* __restrict__ arena_of_step,
                                                       const double* __restrict__ fixed_arena,
                                                       double* __restrict__ pvals, const DevState* st,
-                                                      int upper_block) {
+                                                      int upper_block, int fx) {
   const ColBlock b = blocks[blockIdx.x];
   const PartDesc p = parts[b.part];
   const int j = b.j0 + (threadIdx.x >> 5);
@@ -377,10 +377,22 @@ __global__ void __launch_bounds__(256) scatter_kernel(const PartDesc* __restrict
   // upper_block > 0: only the tiles of that edge on or above the diagonal are stored (the
   // matrix is symmetric), so X[a, j] below them is read as X[j, a]
   const int jb = upper_block > 0 ? j / upper_block : 0;
+  // fx: the arena holds 64-bit fixed point (x 2^56), as the emulated FP64 steps keep it
   for (int t = lane; t < p.s; t += 32) {
     const int a = pm[t];
-    out[t] = (upper_block > 0 && a / upper_block > jb) ? A[(int64_t)a * p.ld + j] : X[a];
+    const double* v = (upper_block > 0 && a / upper_block > jb) ? A + (int64_t)a * p.ld + j : X + a;
+    out[t] = fx ? from_fixed(*reinterpret_cast<const long long*>(v)) : *v;
   }
+}
+
+// An arena of 64-bit fixed point (x 2^56) turned into FP64 in place, for the FP64 consumers
+// of the final iterate (the idempotency report).
+__global__ void __launch_bounds__(256) fixed_to_fp64_kernel(const double* const* __restrict__ arena_of_step,
+                                                            double* arena, const DevState* st, int64_t n) {
+  double* a = arena ? arena : const_cast<double*>(arena_of_step[st->steps]);
+  long long* v = reinterpret_cast<long long*>(a);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    a[i] = from_fixed(v[i]);
 }
 
 // Fill the lower tiles of arenas that hold only the upper 128-tiles (emulated FP64 steps
@@ -465,9 +477,16 @@ cudaError_t launch_threshold(const double* p, int64_t n, double tau, uint8_t* ma
 
 cudaError_t launch_scatter(const PartDesc* parts, const ColBlock* blocks, int nblocks, const int32_t* Sall,
                            const int32_t* perm, const int64_t* pcolptr, const double* const* arena_of_step,
-                           const double* fixed_arena, double* pvals, const DevState* st, cudaStream_t s, int upper_block) {
+                           const double* fixed_arena, double* pvals, const DevState* st, cudaStream_t s, int upper_block,
+                           int fx) {
   scatter_kernel<<<nblocks, 32 * COLS_PER_BLOCK, 0, s>>>(parts, blocks, Sall, perm, pcolptr, arena_of_step,
-                                                        fixed_arena, pvals, st, upper_block);
+                                                        fixed_arena, pvals, st, upper_block, fx);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fixed_to_fp64(const double* const* arena_of_step, double* arena, const DevState* st, int64_t n,
+                                 int nsm, cudaStream_t s) {
+  fixed_to_fp64_kernel<<<4 * nsm, 256, 0, s>>>(arena_of_step, arena, st, n);
   return cudaGetLastError();
 }
 

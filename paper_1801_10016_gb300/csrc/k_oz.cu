@@ -16,8 +16,8 @@
 // here, so they are exact; later groups carry a rounding of 2^-24 relative on a value
 // scaled by 2^{-49} or less.  The groups are added as integers into a 64-bit fixed-point
 // accumulator (resolution 2^-56), and a final elementwise pass forms X_new = Y or 2X - Y on
-// that grid (kept as FP64 master copy), the core traces in FP64, and the digits of X_new for
-// the next step by integer arithmetic.  With T = 7 (28 BF16 products per tile) the digits
+// that grid (the master copy of the iterate stays in this fixed point), the core traces in
+// FP64, and the digits of X_new for the next step by integer arithmetic.  With T = 7 (28 BF16 products per tile) the digits
 // hold x to 2^-49 and the dropped products are of order 2^-63 K 2^12; the error of Y is
 // about 1e-13, far below the 1e-10 parity of the FP64 path.
 //
@@ -74,75 +74,8 @@ __device__ __forceinline__ void store_digits4(uint16_t* const* slices, int64_t e
   }
 }
 
-// Conversions between FP64 and the 2^-56 fixed point of x / 2^sig done with integer
-// instructions (the FP64 pipe of GB300 is 64x slower than its integer pipe), rounding to
-// nearest even.  |x| / 2^sig < 2^7; larger inputs saturate, results below 2^-1022 flush to 0.
-__device__ __forceinline__ long long to_fixed(double x, int sig = 0) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const int ex = (int)((b >> 52) & 0x7FF);
-  if (ex == 0) return 0;                                    // zero and subnormals (< 2^-1022)
-  const unsigned long long m = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-  const int sh = ex - 1023 - 52 + 56 - sig;                 // (x / 2^sig) * 2^56 = m * 2^sh
-  unsigned long long a;
-  if (sh > 10) {
-    a = 1ull << 62;                                         // out of range: saturate
-  } else if (sh >= 0) {
-    a = m << sh;
-  } else if (sh > -64) {
-    const int k = -sh;
-    const unsigned long long q = m >> k, rem = m & ((1ull << k) - 1), half = 1ull << (k - 1);
-    a = q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull);
-  } else {
-    a = 0;
-  }
-  return (b >> 63) ? -(long long)a : (long long)a;
-}
-
-__device__ __forceinline__ double from_fixed(long long v, int sig = 0) {
-  if (v == 0) return 0.0;
-  const unsigned long long sgn = v < 0 ? (1ull << 63) : 0ull;
-  const unsigned long long a = v < 0 ? (unsigned long long)(-v) : (unsigned long long)v;
-  const int lz = __clzll(a);
-  const unsigned long long m = a << lz;                     // top bit at 63
-  unsigned long long mant = m >> 11;                        // 53 bits with the leading one
-  const unsigned long long rem = m & 0x7FFull;
-  int e = 63 - lz - 56 + sig;                               // value = 1.f x 2^e
-  if (rem > 0x400ull || (rem == 0x400ull && (mant & 1ull))) {
-    mant += 1;
-    if (mant >> 53) {
-      mant >>= 1;
-      e += 1;
-    }
-  }
-  if (e < -1022) return __longlong_as_double((long long)sgn);
-  const unsigned long long bits = sgn | ((unsigned long long)(e + 1023) << 52) | (mant & 0xFFFFFFFFFFFFFull);
-  return __longlong_as_double((long long)bits);
-}
-
-// Digits of an FP64 arena (X0 after the gather, or the converted iterate before an FP64
-// tail): one warp per column up to ld.
-// The digits go to the buffer of the current step count's parity (the buffer the next
-// step reads).
-__global__ void __launch_bounds__(256) oz_slice_kernel(const PartDesc* __restrict__ parts,
-                                                       const ColBlock* __restrict__ blocks, const double* __restrict__ X,
-                                                       OzSlices d0, OzSlices d1, const DevState* st) {
-  const OzSlices& sl = (st->steps & 1) ? d1 : d0;
-  const ColBlock b = blocks[blockIdx.x];
-  const PartDesc p = parts[b.part];
-  const int lane = threadIdx.x & 31;
-  const int j = b.j0 + (threadIdx.x >> 5);
-  if (j >= p.ld) return;
-  const int64_t cbase = p.off + (int64_t)j * p.ld;  // ld and the arena offsets are multiples of 128
-  for (int r = 4 * lane; r < p.ld; r += 128) {
-    long long v[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) v[i] = to_fixed(X[cbase + r + i]);
-    store_digits4(sl.s, cbase + r, v);
-  }
-}
-
 // Start of the emulated FP64 tail of a low-precision run: the last FP32 iterate (found on the
-// device from the step count) converted to the FP64 master and written as digits, in one pass
+// device from the step count) converted to the fixed-point master and written as digits, in one pass
 // over the rows on or above each column's diagonal block, the only ones the emulated steps
 // read (and the scatter, which reads the upper tiles).  One warp per column up to ld.
 __global__ void __launch_bounds__(256) oz_convert_slice_kernel(const PartDesc* __restrict__ parts,
@@ -150,6 +83,7 @@ __global__ void __launch_bounds__(256) oz_convert_slice_kernel(const PartDesc* _
                                                                const float* const* __restrict__ master_of_step,
                                                                double* __restrict__ X, OzSlices d0, OzSlices d1,
                                                                const DevState* st) {
+  long long* __restrict__ xq = reinterpret_cast<long long*>(X);
   const int n = st->steps;
   const OzSlices& sl = (n & 1) ? d1 : d0;
   const float* __restrict__ in = master_of_step[n];
@@ -163,12 +97,12 @@ __global__ void __launch_bounds__(256) oz_convert_slice_kernel(const PartDesc* _
   for (int r = 4 * lane; r < rows; r += 128) {  // rows and cbase are multiples of 128
     const float4 f = *reinterpret_cast<const float4*>(in + cbase + r);
     const double x[4] = {(double)f.x, (double)f.y, (double)f.z, (double)f.w};
-    double2* xo = reinterpret_cast<double2*>(X + cbase + r);
-    xo[0] = make_double2(x[0], x[1]);
-    xo[1] = make_double2(x[2], x[3]);
     long long v[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) v[i] = to_fixed(x[i]);
+    longlong2* xo = reinterpret_cast<longlong2*>(xq + cbase + r);
+    xo[0] = make_longlong2(v[0], v[1]);
+    xo[1] = make_longlong2(v[2], v[3]);
     store_digits4(sl.s, cbase + r, v);
   }
 }
@@ -176,8 +110,9 @@ __global__ void __launch_bounds__(256) oz_convert_slice_kernel(const PartDesc* _
 // Gather of the emulated path: Eq. 1 and the digits of X0 in one pass.  One warp per column
 // j < ld assembles the rows of column j of X0 on or above its diagonal block, the only ones
 // the emulated steps read (zeros, then the stored entries of row S_j of H that fall there,
-// located by binary search in the sorted core and halo lists), then reads them back from
-// L1/L2 and writes their digits, coalesced (rows outside the part are zero).  Blocks store
+// located by binary search in the sorted core and halo lists, each stored in the 64-bit
+// fixed point x 2^56 of the emulated steps' master), then reads them back from L1/L2 and
+// writes their digits, coalesced (rows outside the part are zero).  Blocks store
 // the core-diagonal sum of their columns; the last block forms T_0 and takes the first
 // branch.
 __global__ void __launch_bounds__(32 * COLS_PER_BLOCK) oz_gather_kernel(
@@ -189,13 +124,13 @@ __global__ void __launch_bounds__(32 * COLS_PER_BLOCK) oz_gather_kernel(
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int j = b.j0 + w;
   const int32_t* S = Sall + p.soff;
-  double* col = arena + p.off + (int64_t)j * p.ld;
+  long long* col = reinterpret_cast<long long*>(arena) + p.off + (int64_t)j * p.ld;
   const double emax = ctl.st->eps_max, emin = ctl.st->eps_min;
   const double den = emax - emin;
   double tr = 0.0;
   if (j < p.ld) {
     const int rend = min(p.ld, (j / 128 + 1) * 128);
-    for (int r = lane; r < rend; r += 32) col[r] = 0.0;
+    for (int r = lane; r < rend; r += 32) col[r] = 0ll;
     __syncwarp();
     if (j < p.s) {
       const int32_t g = S[j];
@@ -203,7 +138,7 @@ __global__ void __launch_bounds__(32 * COLS_PER_BLOCK) oz_gather_kernel(
         const int a = find_local(S, p.c, p.s, colind[q]);
         if (a >= 0 && a < rend) {
           const double x = (a == j) ? (emax - vals[q]) / den : (0.0 - vals[q]) / den;
-          col[a] = x;
+          col[a] = to_fixed(x);
           if (a == j && j < p.c) tr = x;
         }
       }
@@ -213,7 +148,7 @@ __global__ void __launch_bounds__(32 * COLS_PER_BLOCK) oz_gather_kernel(
     for (int r = 4 * lane; r < rend; r += 128) {  // rend and cbase are multiples of 128
       long long v[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) v[i] = to_fixed(col[r + i]);
+      for (int i = 0; i < 4; ++i) v[i] = col[r + i];
       store_digits4(dig.s, cbase + r, v);
     }
   }
@@ -315,8 +250,9 @@ __global__ void __launch_bounds__(256) oz_scale_kernel(const PartDesc* __restric
   }
 }
 
-// Digits of the upper 128-tiles of a symmetric FP64 arena, of x / 2^sig[part] (sig NULL:
-// unscaled), into `out`; entries outside the part (rows or columns >= s) get zero digits.
+// Digits of the upper 128-tiles of a symmetric arena, of x / 2^sig[part] from FP64 (an
+// adjoint's Xbar), or, with sig NULL, of a forward iterate held in the 64-bit fixed point
+// x 2^56, into `out`; entries outside the part (rows or columns >= s) get zero digits.
 // One warp per column up to ld.  Skipped where need > n (an iterate the adjoint does not
 // reach) or where `after` names a reverse step that was not run.
 __global__ void __launch_bounds__(256) oz_digits_kernel(const PartDesc* __restrict__ parts,
@@ -338,7 +274,9 @@ __global__ void __launch_bounds__(256) oz_digits_kernel(const PartDesc* __restri
     long long v[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
-      v[i] = (r + i < p.s && j < p.s && sg != OZ_SIG_NONFINITE) ? to_fixed(X[cbase + r + i], sg) : 0ll;
+      v[i] = (r + i >= p.s || j >= p.s || sg == OZ_SIG_NONFINITE) ? 0ll
+             : sig ? to_fixed(X[cbase + r + i], sg)
+                   : reinterpret_cast<const long long*>(X)[cbase + r + i];
     store_digits4(out.s, cbase + r, v);
   }
 }
@@ -357,8 +295,9 @@ __global__ void __launch_bounds__(256) oz_digits_kernel(const PartDesc* __restri
 // MMA each).  The epilogue warps turn the high groups' integer-valued sums into 64-bit
 // fixed point (2^-56) and park them in a per-CTA scratch tile (L2-resident), which frees
 // the columns for the low pass; after the low pass they add the low groups, form
-// X_new = Y or 2X - Y, write the FP64 master copy and the digits of X_new (into the other
-// digit buffer) at (I, J) and mirrored at (J, I) (diagonal tiles from their upper triangle),
+// X_new = Y or 2X - Y, write the master copy (64-bit fixed point) and the digits of X_new
+// (into the other digit buffer) at (I, J) and mirrored at (J, I) (diagonal tiles from their
+// upper triangle),
 // and add the core traces, while the MMAs of the next tile's high pass run.  The new
 // iterate is written with evict-first stores: the next step reads it after this launch,
 // and keeping it out of L2 leaves room for the digit panels the running tiles share.  The last block
@@ -750,6 +689,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
       xin = a.xout;
       xout = const_cast<double*>(a.xin);
     }
+    long long* const xq = reinterpret_cast<long long*>(xout);
     int u = 0;
     for (int it = blockIdx.x;; it += gridDim.x, ++u) {
       if (dyn) {
@@ -824,7 +764,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
         __threadfence();
         other = a.split_acc + (size_t)(code ^ 1) * (128 * 128);
       }
-      // final pass of the tile: X_new on the 2^-56 grid, FP64 master, digits, traces (the
+      // final pass of the tile: X_new on the 2^-56 grid, fixed-point master, digits, traces (the
       // adjoint: Xbar_new, FP64 only); column writes are coalesced across the warp.  Only
       // tiles on or above the diagonal are kept (the next step reads the rest MN-major from
       // them); a diagonal tile mirrors its upper triangle, each thread's row segment in
@@ -845,15 +785,16 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
         for (int sub = 0; sub < 4; ++sub) {
           // loads of the group first (xin is not written by this launch), so that they are
           // in flight together rather than each behind the previous group's stores
-          long long yv[4];
-          double xv[4];
+          // the forward iterates are kept in the fixed point itself; the adjoint's Xbar in FP64
+          long long yv[4], xv[4];
 #pragma unroll
           for (int w = 0; w < 4; ++w) {
             const int j = sub * 4 + w;
             yv[w] = zp[(size_t)j * 128] + (zo ? __ldcg(zo + (size_t)j * 128) : 0ll);
-            xv[w] = alf > 0 ? __ldg(xin + p.off + (int64_t)(cbase + j) * ld + r) : 0.0;
+            xv[w] = alf > 0 ? __ldg(reinterpret_cast<const long long*>(xin) + p.off + (int64_t)(cbase + j) * ld + r)
+                            : 0ll;
           }
-          double xn4[4];
+          long long xn4[4];  // the words stored: fixed point (forward) or FP64 bits (adjoint)
           uint32_t dw4[4][OZ_SLICES];
 #pragma unroll
           for (int w = 0; w < 4; ++w) {
@@ -861,8 +802,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
             const long long yf = yv[w];
             const int64_t e = (int64_t)c * ld + r;
             const bool upper = offd || c >= r;  // diagonal tiles: upper triangle only
-            const long long xf = (alf > 0 && upper) ? 2 * to_fixed(xv[w], sg) - yf : yf;
-            xn4[w] = (ADJ && sg == OZ_SIG_NONFINITE) ? __longlong_as_double(0x7FF8000000000000ll) : from_fixed(xf, sg);
+            const long long xi = ADJ ? to_fixed(__longlong_as_double(xv[w]), sg) : xv[w];
+            const long long xf = (alf > 0 && upper) ? 2 * xi - yf : yf;
+            if (ADJ)
+              xn4[w] = sg == OZ_SIG_NONFINITE ? 0x7FF8000000000000ll : __double_as_longlong(from_fixed(xf, sg));
+            else
+              xn4[w] = xf;
             if (!ADJ) digit_words(xf, dw4[w]);
             if (ADJ && upper && r < p.s && c < p.s) {
               // every stored entry (r, c) adds to the norm of row r, and of row c unless c = r
@@ -871,7 +816,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
               if (c != r) coln[sub * 4 + w] = f * f;
             }
             if (upper) {
-              __stcs(xout + p.off + e, xn4[w]);
+              __stcs(xq + p.off + e, xn4[w]);
               if (!ADJ) {
 #pragma unroll
                 for (int q = 0; q < OZ_SLICES; ++q)
@@ -879,7 +824,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
               }
               if (!ADJ && !rec && c == r && diag && r < p.c) {
                 tY += from_fixed(yf);
-                tN += xn4[w];
+                tN += from_fixed(xf);
               }
             }
           }
@@ -887,9 +832,9 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
           if (!offd && cbase + sub * 4 > r) {
             // the four mirrored elements are contiguous in column r: vector stores whenever
             // all four lie right of the diagonal
-            double2* xm = reinterpret_cast<double2*>(xout + em);
-            __stcs(xm, make_double2(xn4[0], xn4[1]));
-            __stcs(xm + 1, make_double2(xn4[2], xn4[3]));
+            longlong2* xm = reinterpret_cast<longlong2*>(xq + em);
+            __stcs(xm, make_longlong2(xn4[0], xn4[1]));
+            __stcs(xm + 1, make_longlong2(xn4[2], xn4[3]));
             if (!ADJ) {
 #pragma unroll
               for (int q = 0; q < OZ_SLICES; ++q) {
@@ -903,7 +848,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
 #pragma unroll
             for (int w = 0; w < 4; ++w) {
               if (cbase + sub * 4 + w <= r) continue;
-              __stcs(xout + em + w, xn4[w]);
+              __stcs(xq + em + w, xn4[w]);
               if (!ADJ) {
 #pragma unroll
                 for (int q = 0; q < OZ_SLICES; ++q)
@@ -1006,12 +951,6 @@ cudaError_t launch_oz_convert_slice(const PartDesc* parts, const ColBlock* block
                                     const float* const* master_of_step, double* X, const OzSlices* digits,
                                     const DevState* st, cudaStream_t s) {
   oz_convert_slice_kernel<<<nblocks, 256, 0, s>>>(parts, blocks, master_of_step, X, digits[0], digits[1], st);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_oz_slice(const PartDesc* parts, const ColBlock* blocks, int nblocks, const double* X,
-                            const OzSlices* digits, const DevState* st, cudaStream_t s) {
-  oz_slice_kernel<<<nblocks, 32 * COLS_PER_BLOCK, 0, s>>>(parts, blocks, X, digits[0], digits[1], st);
   return cudaGetLastError();
 }
 
