@@ -24,6 +24,7 @@ constexpr int BOUNDS_BLOCKS = 608;  // 152 SMs x 4
 struct WsLayout {
   size_t parts, S, perm, invperm, tiles, tc_tiles, tc_wide, tc_wide_nb, gblocks, gblocks_ld, sblocks, pcolptr, rowptr,
       colind;
+  size_t locptr, loc;  // the gathers' local indices of the stored entries of the rows S_k[j]
   size_t memptr, mempart, memloc;
   // low-precision paths
   size_t mf[2];        // FP32 master copies of X (ping-pong)
@@ -89,6 +90,8 @@ struct gsp2_plan {
   std::vector<PartDesc> parts;
   std::vector<int32_t> S, perm, invperm;
   std::vector<int64_t> memptr;           // vertex -> parts holding it (CSR)
+  std::vector<int64_t> locptr;           // per entry of S: its row's first slot in the local-index table
+  int64_t nloc = 0;                      // slots of that table (stored entries of all rows S_k[j])
   std::vector<int32_t> mempart, memloc;  // part id, local index in S_part
   std::vector<Tile> tiles;                 // 64x64 upper tiles (CUDA-core steps)
   std::vector<Tile> tc_tiles;              // 128x128 upper tiles (tensor-core steps)
@@ -282,6 +285,14 @@ static void build_layout(gsp2_plan* h) {
   L.pcolptr = take(h->pcolptr.size() * sizeof(int64_t));
   L.rowptr = take(h->rowptr.size() * sizeof(int64_t));
   L.colind = take(h->colind.size() * sizeof(int32_t));
+  h->locptr.resize(h->S.size());
+  h->nloc = 0;
+  for (size_t q = 0; q < h->S.size(); ++q) {
+    h->locptr[q] = h->nloc;
+    h->nloc += h->rowptr[(size_t)h->S[q] + 1] - h->rowptr[(size_t)h->S[q]];
+  }
+  L.locptr = take(h->locptr.size() * sizeof(int64_t));
+  L.loc = take((size_t)h->nloc * sizeof(int32_t));
   const size_t nsl = std::max<size_t>({(size_t)h->nslots, (size_t)h->nslots_tc, h->gblocks.size(),
                                         h->gblocks_ld.size(), (size_t)BOUNDS_BLOCKS, 1});
   L.slots = take(nsl * sizeof(double2));
@@ -1001,6 +1012,11 @@ extern "C" gsp2_status gsp2_bind_workspace(gsp2_handle h, void* d_ws, size_t byt
   CU(h, up(L.pcolptr, h->pcolptr.data(), h->pcolptr.size() * sizeof(int64_t)));
   CU(h, up(L.rowptr, h->rowptr.data(), h->rowptr.size() * sizeof(int64_t)));
   CU(h, up(L.colind, h->colind.data(), h->colind.size() * sizeof(int32_t)));
+  CU(h, up(L.locptr, h->locptr.data(), h->locptr.size() * sizeof(int64_t)));
+  CU(h, launch_locate((const PartDesc*)(h->ws + L.parts), (const ColBlock*)(h->ws + L.gblocks_ld),
+                      (int)h->gblocks_ld.size(), (const int32_t*)(h->ws + L.S), (const int64_t*)(h->ws + L.rowptr),
+                      (const int32_t*)(h->ws + L.colind), (const int64_t*)(h->ws + L.locptr),
+                      (int32_t*)(h->ws + L.loc), s));
   CU(h, cudaMemsetAsync(h->ws + L.state, 0, sizeof(DevState), s));
   CU(h, cudaMemsetAsync(h->ws + L.tile_ctr, 0, sizeof(uint32_t), s));
   CU(h, cudaMemsetAsync(h->ws + L.alpha, 0, (size_t)h->opt.max_steps + HIST_EXTRA, s));
@@ -1102,6 +1118,8 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
   auto pcol = (const int64_t*)(w + L.pcolptr);
   auto rp = (const int64_t*)(w + L.rowptr);
   auto ci = (const int32_t*)(w + L.colind);
+  auto loc = (const int32_t*)(w + L.loc);
+  auto locp = (const int64_t*)(w + L.locptr);
   auto slots = (double2*)(w + L.slots);
   auto st = (DevState*)(w + L.state);
   auto alpha = (int8_t*)(w + L.alpha);
@@ -1134,7 +1152,7 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
     const bool upper_rows = (kind == 0 || kind == 2) && pgrid > 0 && !wide;
     if (on())
       CU(h, launch_gather_lp(kind, nprod, parts, (const ColBlock*)(w + L.gblocks_ld), (int)h->gblocks_ld.size(), Sall,
-                             rp, ci, hv, mfs(0), kind >= 0 ? oh[0] : nullptr, nprod == 3 ? ol[0] : nullptr,
+                             rp, loc, locp, hv, mfs(0), kind >= 0 ? oh[0] : nullptr, nprod == 3 ? ol[0] : nullptr,
                              (double*)slots, lp, s, upper_rows ? 1 : 0));
     ++seg;
     if (kind >= 0) {
@@ -1240,10 +1258,11 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
   if (on()) {
     if (emu) {
       // X0 and its digits in one pass (the digits to buffer 0, read by step 1)
-      CU(h, launch_oz_gather(parts, gbl, (int)h->gblocks_ld.size(), Sall, rp, ci, hv, A(0), oz.digits[0],
+      CU(h, launch_oz_gather(parts, gbl, (int)h->gblocks_ld.size(), Sall, rp, loc, locp, hv, A(0), oz.digits[0],
                              (double*)slots, ctl, s));
     } else {
-      CU(h, launch_gather(parts, gbl, (int)h->gblocks_ld.size(), Sall, rp, ci, hv, A(0), (double*)slots, ctl, s));
+      CU(h, launch_gather(parts, gbl, (int)h->gblocks_ld.size(), Sall, rp, loc, locp, hv, A(0), (double*)slots, ctl,
+                          s));
     }
   }
   ++seg;

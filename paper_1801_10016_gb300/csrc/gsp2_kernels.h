@@ -10,8 +10,12 @@ cudaError_t launch_reset(DevState* st, int8_t* alpha, const int8_t* alpha_in, in
 cudaError_t launch_bounds(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* vals,
                           double2* slots, int nblocks, DevState* st, cudaStream_t s);
 cudaError_t launch_gather(const PartDesc* parts, const ColBlock* blocks, int nblocks, const int32_t* Sall,
-                          const int64_t* rowptr, const int32_t* colind, const double* vals, double* arena,
-                          double* slots, const StepCtl& ctl, cudaStream_t s);
+                          const int64_t* rowptr, const int32_t* loc, const int64_t* locptr, const double* vals,
+                          double* arena, double* slots, const StepCtl& ctl, cudaStream_t s);
+// the gathers' table of local indices (once per bound workspace)
+cudaError_t launch_locate(const PartDesc* parts, const ColBlock* blocks, int nblocks, const int32_t* Sall,
+                          const int64_t* rowptr, const int32_t* colind, const int64_t* locptr, int32_t* loc,
+                          cudaStream_t s);
 cudaError_t launch_square_fp64(const PartDesc* parts, const Tile* tiles, int ntiles, const double* xin,
                                double* xout, double2* slots, int nslots, const StepCtl& ctl, int step, int mode,
                                cudaStream_t s);
@@ -35,9 +39,9 @@ cudaError_t launch_symmetrize(const PartDesc* parts, const Tile* tiles, int ntil
 cudaError_t launch_square_tc(int kind, int nprod, const TcStepArgs& a, int ntiles, int persistent_grid,
                              cudaStream_t s);
 cudaError_t launch_gather_lp(int kind, int nprod, const PartDesc* parts, const ColBlock* blocks, int nblocks,
-                             const int32_t* Sall, const int64_t* rowptr, const int32_t* colind, const double* vals,
-                             float* master, void* op_hi, void* op_lo, double* slots, const StepCtl& ctl,
-                             cudaStream_t s, int upper_rows = 0);
+                             const int32_t* Sall, const int64_t* rowptr, const int32_t* loc, const int64_t* locptr,
+                             const double* vals, float* master, void* op_hi, void* op_lo, double* slots,
+                             const StepCtl& ctl, cudaStream_t s, int upper_rows = 0);
 // FP32 adjoint of the low-precision plans on the tensor cores (FP16 hi + lo operands)
 cudaError_t launch_tc_adjoint(const TcStepArgs& a, int grid, bool rebuild, cudaStream_t s);
 cudaError_t launch_split_f16(const PartDesc* parts, const ColBlock* blocks, int nblocks, const float* x, void* hi,
@@ -57,8 +61,8 @@ cudaError_t launch_oz_convert_slice(const PartDesc* parts, const ColBlock* block
                                     const DevState* st, cudaStream_t s);
 // gather with Eq. 1 and the digits of X0 in one pass (emulated path)
 cudaError_t launch_oz_gather(const PartDesc* parts, const ColBlock* blocks, int nblocks, const int32_t* Sall,
-                             const int64_t* rowptr, const int32_t* colind, const double* vals, double* arena,
-                             const OzSlices& dig, double* slots, const StepCtl& ctl, cudaStream_t s);
+                             const int64_t* rowptr, const int32_t* loc, const int64_t* locptr, const double* vals,
+                             double* arena, const OzSlices& dig, double* slots, const StepCtl& ctl, cudaStream_t s);
 // the emulated adjoint's Xbar digits: row norms and per-part scales, then the digits
 cudaError_t launch_oz_adj_scale(const PartDesc* parts, int nparts, const Tile* tiles, int ntiles, const double* xb0,
                                 const double* xb1, int after, double* norm, int32_t* sig, const DevState* st,

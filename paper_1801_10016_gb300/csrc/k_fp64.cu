@@ -77,10 +77,36 @@ __global__ void reset_kernel(DevState* st, int8_t* alpha, const int8_t* alpha_in
 }
 
 // ------------------------------------------------------------------------------------
+// Local indices of the stored entries of H that the gathers place (Section 2.2: the rows
+// S_k[j] of H restricted to the columns S_k): for the stored entry t of row S_k[j],
+// loc[locptr[soff_k + j] + t] = a with S_k[a] its column, or -1 when that column is not in
+// S_k.  Found by binary search in the ascending core (S_k[0, c)) and halo (S_k[c, s)) lists,
+// once per bound workspace: the pattern of H and the parts are fixed by the plan, so every
+// gather then reads one index per entry.  One warp per local column j < s_k.
+// ------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) locate_kernel(const PartDesc* __restrict__ parts,
+                                                     const ColBlock* __restrict__ blocks,
+                                                     const int32_t* __restrict__ Sall,
+                                                     const int64_t* __restrict__ rowptr,
+                                                     const int32_t* __restrict__ colind,
+                                                     const int64_t* __restrict__ locptr, int32_t* __restrict__ loc) {
+  const ColBlock b = blocks[blockIdx.x];
+  const PartDesc p = parts[b.part];
+  const int lane = threadIdx.x & 31;
+  const int j = b.j0 + (threadIdx.x >> 5);
+  if (j >= p.s) return;
+  const int32_t* S = Sall + p.soff;
+  const int32_t g = S[j];
+  const int64_t q0 = rowptr[g], nq = rowptr[g + 1] - q0;
+  int32_t* lj = loc + locptr[p.soff + j];
+  for (int64_t t = lane; t < nq; t += 32) lj[t] = find_local(S, p.c, p.s, colind[q0 + t]);
+}
+
+// ------------------------------------------------------------------------------------
 // Gather + Eq. 1: X0_k[a, j] = (eps_max [a == j] - H[S_k[j], S_k[a]]) / (eps_max - eps_min)
 // for a, j < s_k; zero in the padding.  One warp per local column j; the row S_k[j]
-// of H is walked once and every stored column is located in S_k by binary search
-// in the (ascending) core and halo lists.  The diagonal entry must be stored.
+// of H is walked once, each stored entry's local index a read from the plan's table
+// (locate_kernel, once per bound workspace).  The diagonal entry must be stored.
 // Blocks store the core-diagonal sum of their columns; the last block forms T_0 and
 // chooses the first branch.
 // ------------------------------------------------------------------------------------
@@ -88,7 +114,8 @@ __global__ void __launch_bounds__(256) gather_kernel(const PartDesc* __restrict_
                                                      const ColBlock* __restrict__ blocks,
                                                      const int32_t* __restrict__ Sall,
                                                      const int64_t* __restrict__ rowptr,
-                                                     const int32_t* __restrict__ colind,
+                                                     const int32_t* __restrict__ loc,
+                                                     const int64_t* __restrict__ locptr,
                                                      const double* __restrict__ vals, double* __restrict__ arena,
                                                      double* __restrict__ slots, StepCtl ctl) {
   const ColBlock b = blocks[blockIdx.x];
@@ -107,8 +134,11 @@ __global__ void __launch_bounds__(256) gather_kernel(const PartDesc* __restrict_
     __syncwarp();
     if (j < p.s) {
       const int32_t g = S[j];
-      for (int64_t q = rowptr[g] + lane; q < rowptr[g + 1]; q += 32) {
-        const int a = find_local(S, p.c, p.s, colind[q]);
+      const int64_t q0 = rowptr[g], nq = rowptr[g + 1] - q0;
+      const int32_t* lj = loc + locptr[p.soff + j];
+      for (int64_t t = lane; t < nq; t += 32) {
+        const int a = lj[t];
+        const int64_t q = q0 + t;
         if (a >= 0) {
           const double x = (a == j) ? (emax - vals[q]) / den : (0.0 - vals[q]) / den;
           col[a] = x;
@@ -434,10 +464,18 @@ cudaError_t launch_bounds(int64_t n, const int64_t* rowptr, const int32_t* colin
 }
 
 cudaError_t launch_gather(const PartDesc* parts, const ColBlock* blocks, int nblocks, const int32_t* Sall,
-                          const int64_t* rowptr, const int32_t* colind, const double* vals, double* arena,
-                          double* slots, const StepCtl& ctl, cudaStream_t s) {
-  gather_kernel<<<nblocks, 32 * COLS_PER_BLOCK, 0, s>>>(parts, blocks, Sall, rowptr, colind, vals, arena, slots,
-                                                       ctl);
+                          const int64_t* rowptr, const int32_t* loc, const int64_t* locptr, const double* vals,
+                          double* arena, double* slots, const StepCtl& ctl, cudaStream_t s) {
+  gather_kernel<<<nblocks, 32 * COLS_PER_BLOCK, 0, s>>>(parts, blocks, Sall, rowptr, loc, locptr, vals, arena,
+                                                       slots, ctl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_locate(const PartDesc* parts, const ColBlock* blocks, int nblocks, const int32_t* Sall,
+                          const int64_t* rowptr, const int32_t* colind, const int64_t* locptr, int32_t* loc,
+                          cudaStream_t s) {
+  if (nblocks == 0) return cudaSuccess;
+  locate_kernel<<<nblocks, 32 * COLS_PER_BLOCK, 0, s>>>(parts, blocks, Sall, rowptr, colind, locptr, loc);
   return cudaGetLastError();
 }
 

@@ -110,15 +110,16 @@ __global__ void __launch_bounds__(256) oz_convert_slice_kernel(const PartDesc* _
 // Gather of the emulated path: Eq. 1 and the digits of X0 in one pass.  One warp per column
 // j < ld assembles the rows of column j of X0 on or above its diagonal block, the only ones
 // the emulated steps read (zeros, then the stored entries of row S_j of H that fall there,
-// located by binary search in the sorted core and halo lists, each stored in the 64-bit
+// at the local indices of the plan's table (locate_kernel), each stored in the 64-bit
 // fixed point x 2^56 of the emulated steps' master), then reads them back from L1/L2 and
 // writes their digits, coalesced (rows outside the part are zero).  Blocks store
 // the core-diagonal sum of their columns; the last block forms T_0 and takes the first
 // branch.
 __global__ void __launch_bounds__(32 * COLS_PER_BLOCK) oz_gather_kernel(
     const PartDesc* __restrict__ parts, const ColBlock* __restrict__ blocks, const int32_t* __restrict__ Sall,
-    const int64_t* __restrict__ rowptr, const int32_t* __restrict__ colind, const double* __restrict__ vals,
-    double* __restrict__ arena, OzSlices dig, double* __restrict__ slots, StepCtl ctl) {
+    const int64_t* __restrict__ rowptr, const int32_t* __restrict__ loc, const int64_t* __restrict__ locptr,
+    const double* __restrict__ vals, double* __restrict__ arena, OzSlices dig, double* __restrict__ slots,
+    StepCtl ctl) {
   const ColBlock b = blocks[blockIdx.x];
   const PartDesc p = parts[b.part];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -134,8 +135,11 @@ __global__ void __launch_bounds__(32 * COLS_PER_BLOCK) oz_gather_kernel(
     __syncwarp();
     if (j < p.s) {
       const int32_t g = S[j];
-      for (int64_t q = rowptr[g] + lane; q < rowptr[g + 1]; q += 32) {
-        const int a = find_local(S, p.c, p.s, colind[q]);
+      const int64_t q0 = rowptr[g], nq = rowptr[g + 1] - q0;
+      const int32_t* lj = loc + locptr[p.soff + j];
+      for (int64_t t = lane; t < nq; t += 32) {
+        const int a = lj[t];
+        const int64_t q = q0 + t;
         if (a >= 0 && a < rend) {
           const double x = (a == j) ? (emax - vals[q]) / den : (0.0 - vals[q]) / den;
           col[a] = to_fixed(x);
@@ -966,10 +970,10 @@ cudaError_t launch_oz_step(const OzStepArgs& a, int grid, cudaStream_t s, bool a
 }
 
 cudaError_t launch_oz_gather(const PartDesc* parts, const ColBlock* blocks, int nblocks, const int32_t* Sall,
-                             const int64_t* rowptr, const int32_t* colind, const double* vals, double* arena,
-                             const OzSlices& dig, double* slots, const StepCtl& ctl, cudaStream_t s) {
-  oz_gather_kernel<<<nblocks, 32 * COLS_PER_BLOCK, 0, s>>>(parts, blocks, Sall, rowptr, colind, vals, arena, dig, slots,
-                                                            ctl);
+                             const int64_t* rowptr, const int32_t* loc, const int64_t* locptr, const double* vals,
+                             double* arena, const OzSlices& dig, double* slots, const StepCtl& ctl, cudaStream_t s) {
+  oz_gather_kernel<<<nblocks, 32 * COLS_PER_BLOCK, 0, s>>>(parts, blocks, Sall, rowptr, loc, locptr, vals, arena, dig,
+                                                            slots, ctl);
   return cudaGetLastError();
 }
 

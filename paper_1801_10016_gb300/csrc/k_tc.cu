@@ -1222,7 +1222,8 @@ __global__ void __launch_bounds__(256) gather_lp_kernel(const PartDesc* __restri
                                                         const ColBlock* __restrict__ blocks,
                                                         const int32_t* __restrict__ Sall,
                                                         const int64_t* __restrict__ rowptr,
-                                                        const int32_t* __restrict__ colind,
+                                                        const int32_t* __restrict__ loc,
+                                                        const int64_t* __restrict__ locptr,
                                                         const double* __restrict__ vals, float* __restrict__ master,
                                                         void* op_hi, void* op_lo, double* __restrict__ slots,
                                                         StepCtl ctl, int upper_rows) {
@@ -1242,8 +1243,11 @@ __global__ void __launch_bounds__(256) gather_lp_kernel(const PartDesc* __restri
     __syncwarp();
     if (j < p.s) {
       const int32_t g = S[j];
-      for (int64_t q = rowptr[g] + lane; q < rowptr[g + 1]; q += 32) {
-        const int a = find_local(S, p.c, p.s, colind[q]);
+      const int64_t q0 = rowptr[g], nq = rowptr[g + 1] - q0;
+      const int32_t* lj = loc + locptr[p.soff + j];
+      for (int64_t t = lane; t < nq; t += 32) {
+        const int a = lj[t];
+        const int64_t q = q0 + t;
         if (a >= 0 && a < rend) {
           const double x = (a == j) ? (emax - vals[q]) / den : (0.0 - vals[q]) / den;
           const float xf = (float)x;
@@ -1273,27 +1277,27 @@ __global__ void __launch_bounds__(256) gather_lp_kernel(const PartDesc* __restri
 }
 
 cudaError_t launch_gather_lp(int kind, int nprod, const PartDesc* parts, const ColBlock* blocks, int nblocks,
-                             const int32_t* Sall, const int64_t* rowptr, const int32_t* colind, const double* vals,
-                             float* master, void* op_hi, void* op_lo, double* slots, const StepCtl& ctl,
-                             cudaStream_t s, int upper_rows) {
+                             const int32_t* Sall, const int64_t* rowptr, const int32_t* loc, const int64_t* locptr,
+                             const double* vals, float* master, void* op_hi, void* op_lo, double* slots,
+                             const StepCtl& ctl, cudaStream_t s, int upper_rows) {
   const dim3 g(nblocks), b(32 * COLS_PER_BLOCK);
   if (kind < 0)
-    gather_lp_kernel<-1, 1><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, colind, vals, master, op_hi, op_lo,
+    gather_lp_kernel<-1, 1><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, loc, locptr, vals, master, op_hi, op_lo,
                                             slots, ctl, upper_rows);
   else if (kind == 0 && nprod == 1)
-    gather_lp_kernel<0, 1><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, colind, vals, master, op_hi, op_lo,
+    gather_lp_kernel<0, 1><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, loc, locptr, vals, master, op_hi, op_lo,
                                            slots, ctl, upper_rows);
   else if (kind == 0 && nprod == 3)
-    gather_lp_kernel<0, 3><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, colind, vals, master, op_hi, op_lo,
+    gather_lp_kernel<0, 3><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, loc, locptr, vals, master, op_hi, op_lo,
                                            slots, ctl, upper_rows);
   else if (kind == 1 && nprod == 1)
-    gather_lp_kernel<1, 1><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, colind, vals, master, op_hi, op_lo,
+    gather_lp_kernel<1, 1><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, loc, locptr, vals, master, op_hi, op_lo,
                                            slots, ctl, upper_rows);
   else if (kind == 1 && nprod == 3)
-    gather_lp_kernel<1, 3><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, colind, vals, master, op_hi, op_lo,
+    gather_lp_kernel<1, 3><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, loc, locptr, vals, master, op_hi, op_lo,
                                            slots, ctl, upper_rows);
   else if (kind == 2 && nprod == 3)
-    gather_lp_kernel<2, 3><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, colind, vals, master, op_hi, op_lo,
+    gather_lp_kernel<2, 3><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, loc, locptr, vals, master, op_hi, op_lo,
                                            slots, ctl, upper_rows);
   else
     return cudaErrorInvalidValue;
