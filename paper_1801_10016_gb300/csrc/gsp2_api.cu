@@ -25,6 +25,7 @@ struct WsLayout {
   size_t parts, S, perm, invperm, tiles, tc_tiles, tc_wide, tc_wide_nb, gblocks, gblocks_ld, sblocks, pcolptr, rowptr,
       colind;
   size_t locptr, loc;  // the gathers' local indices of the stored entries of the rows S_k[j]
+  size_t x0;           // Eq. 1 on the stored entries of H (FP64, per P-build)
   size_t memptr, mempart, memloc;
   // low-precision paths
   size_t mf[2];        // FP32 master copies of X (ping-pong)
@@ -293,6 +294,7 @@ static void build_layout(gsp2_plan* h) {
   }
   L.locptr = take(h->locptr.size() * sizeof(int64_t));
   L.loc = take((size_t)h->nloc * sizeof(int32_t));
+  L.x0 = take(h->colind.size() * sizeof(double));
   const size_t nsl = std::max<size_t>({(size_t)h->nslots, (size_t)h->nslots_tc, h->gblocks.size(),
                                         h->gblocks_ld.size(), (size_t)BOUNDS_BLOCKS, 1});
   L.slots = take(nsl * sizeof(double2));
@@ -1120,6 +1122,7 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
   auto ci = (const int32_t*)(w + L.colind);
   auto loc = (const int32_t*)(w + L.loc);
   auto locp = (const int64_t*)(w + L.locptr);
+  auto x0 = (double*)(w + L.x0);
   auto slots = (double2*)(w + L.slots);
   auto st = (DevState*)(w + L.state);
   auto alpha = (int8_t*)(w + L.alpha);
@@ -1131,6 +1134,7 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
     CU(h, launch_reset(st, alpha, mode == MODE_REPLAY ? alpha_user : nullptr, nsteps, h->opt.max_steps + HIST_EXTRA,
                        s));
     CU(h, launch_bounds(h->n, rp, ci, hv, slots, BOUNDS_BLOCKS, st, s));
+    CU(h, launch_x0_values(h->n, rp, ci, hv, st, x0, h->num_sms, s));
   }
   const int prec = h->opt.precision;
   if (!fp64_like(prec)) {
@@ -1152,7 +1156,7 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
     const bool upper_rows = (kind == 0 || kind == 2) && pgrid > 0 && !wide;
     if (on())
       CU(h, launch_gather_lp(kind, nprod, parts, (const ColBlock*)(w + L.gblocks_ld), (int)h->gblocks_ld.size(), Sall,
-                             rp, loc, locp, hv, mfs(0), kind >= 0 ? oh[0] : nullptr, nprod == 3 ? ol[0] : nullptr,
+                             rp, loc, locp, x0, mfs(0), kind >= 0 ? oh[0] : nullptr, nprod == 3 ? ol[0] : nullptr,
                              (double*)slots, lp, s, upper_rows ? 1 : 0));
     ++seg;
     if (kind >= 0) {
@@ -1258,10 +1262,10 @@ static gsp2_status enqueue_forward(gsp2_plan* h, const double* hv, double* pv, i
   if (on()) {
     if (emu) {
       // X0 and its digits in one pass (the digits to buffer 0, read by step 1)
-      CU(h, launch_oz_gather(parts, gbl, (int)h->gblocks_ld.size(), Sall, rp, loc, locp, hv, A(0), oz.digits[0],
+      CU(h, launch_oz_gather(parts, gbl, (int)h->gblocks_ld.size(), Sall, rp, loc, locp, x0, A(0), oz.digits[0],
                              (double*)slots, ctl, s));
     } else {
-      CU(h, launch_gather(parts, gbl, (int)h->gblocks_ld.size(), Sall, rp, loc, locp, hv, A(0), (double*)slots, ctl,
+      CU(h, launch_gather(parts, gbl, (int)h->gblocks_ld.size(), Sall, rp, loc, locp, x0, A(0), (double*)slots, ctl,
                           s));
     }
   }

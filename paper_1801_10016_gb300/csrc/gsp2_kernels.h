@@ -10,8 +10,11 @@ cudaError_t launch_reset(DevState* st, int8_t* alpha, const int8_t* alpha_in, in
 cudaError_t launch_bounds(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* vals,
                           double2* slots, int nblocks, DevState* st, cudaStream_t s);
 cudaError_t launch_gather(const PartDesc* parts, const ColBlock* blocks, int nblocks, const int32_t* Sall,
-                          const int64_t* rowptr, const int32_t* loc, const int64_t* locptr, const double* vals,
+                          const int64_t* rowptr, const int32_t* loc, const int64_t* locptr, const double* x0,
                           double* arena, double* slots, const StepCtl& ctl, cudaStream_t s);
+// Eq. 1 on the stored entries of H (the gathers' values)
+cudaError_t launch_x0_values(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* vals,
+                             const DevState* st, double* x0, int nsm, cudaStream_t s);
 // the gathers' table of local indices (once per bound workspace)
 cudaError_t launch_locate(const PartDesc* parts, const ColBlock* blocks, int nblocks, const int32_t* Sall,
                           const int64_t* rowptr, const int32_t* colind, const int64_t* locptr, int32_t* loc,
@@ -40,7 +43,7 @@ cudaError_t launch_square_tc(int kind, int nprod, const TcStepArgs& a, int ntile
                              cudaStream_t s);
 cudaError_t launch_gather_lp(int kind, int nprod, const PartDesc* parts, const ColBlock* blocks, int nblocks,
                              const int32_t* Sall, const int64_t* rowptr, const int32_t* loc, const int64_t* locptr,
-                             const double* vals, float* master, void* op_hi, void* op_lo, double* slots,
+                             const double* x0, float* master, void* op_hi, void* op_lo, double* slots,
                              const StepCtl& ctl, cudaStream_t s, int upper_rows = 0);
 // FP32 adjoint of the low-precision plans on the tensor cores (FP16 hi + lo operands)
 cudaError_t launch_tc_adjoint(const TcStepArgs& a, int grid, bool rebuild, cudaStream_t s);
@@ -61,7 +64,7 @@ cudaError_t launch_oz_convert_slice(const PartDesc* parts, const ColBlock* block
                                     const DevState* st, cudaStream_t s);
 // gather with Eq. 1 and the digits of X0 in one pass (emulated path)
 cudaError_t launch_oz_gather(const PartDesc* parts, const ColBlock* blocks, int nblocks, const int32_t* Sall,
-                             const int64_t* rowptr, const int32_t* loc, const int64_t* locptr, const double* vals,
+                             const int64_t* rowptr, const int32_t* loc, const int64_t* locptr, const double* x0,
                              double* arena, const OzSlices& dig, double* slots, const StepCtl& ctl, cudaStream_t s);
 // the emulated adjoint's Xbar digits: row norms and per-part scales, then the digits
 cudaError_t launch_oz_adj_scale(const PartDesc* parts, int nparts, const Tile* tiles, int ntiles, const double* xb0,

@@ -77,6 +77,26 @@ __global__ void reset_kernel(DevState* st, int8_t* alpha, const int8_t* alpha_in
 }
 
 // ------------------------------------------------------------------------------------
+// Eq. 1 on the stored entries of H, once per P-build: x0[q] = (eps_max [col = row] - H_q) /
+// (eps_max - eps_min).  Every entry lies in several parts (each of which gathers it), so
+// dividing once here keeps the divisions, which run on GB300's slow FP64 pipe, out of the
+// gathers.  One warp per row.
+// ------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) x0_values_kernel(int64_t n, const int64_t* __restrict__ rowptr,
+                                                        const int32_t* __restrict__ colind,
+                                                        const double* __restrict__ vals, const DevState* st,
+                                                        double* __restrict__ x0) {
+  const double emax = st->eps_max, emin = st->eps_min;
+  const double den = emax - emin;
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t g = w0; g < n; g += nw)
+    for (int64_t q = rowptr[g] + lane; q < rowptr[g + 1]; q += 32)
+      x0[q] = (colind[q] == g) ? (emax - vals[q]) / den : (0.0 - vals[q]) / den;
+}
+
+// ------------------------------------------------------------------------------------
 // Local indices of the stored entries of H that the gathers place (Section 2.2: the rows
 // S_k[j] of H restricted to the columns S_k): for the stored entry t of row S_k[j],
 // loc[locptr[soff_k + j] + t] = a with S_k[a] its column, or -1 when that column is not in
@@ -105,8 +125,9 @@ __global__ void __launch_bounds__(256) locate_kernel(const PartDesc* __restrict_
 // ------------------------------------------------------------------------------------
 // Gather + Eq. 1: X0_k[a, j] = (eps_max [a == j] - H[S_k[j], S_k[a]]) / (eps_max - eps_min)
 // for a, j < s_k; zero in the padding.  One warp per local column j; the row S_k[j]
-// of H is walked once, each stored entry's local index a read from the plan's table
-// (locate_kernel, once per bound workspace).  The diagonal entry must be stored.
+// of H is walked once, each stored entry's value taken from x0_values_kernel and its
+// local index a from the plan's table (locate_kernel, once per bound workspace).  The
+// diagonal entry must be stored.
 // Blocks store the core-diagonal sum of their columns; the last block forms T_0 and
 // chooses the first branch.
 // ------------------------------------------------------------------------------------
@@ -116,15 +137,13 @@ __global__ void __launch_bounds__(256) gather_kernel(const PartDesc* __restrict_
                                                      const int64_t* __restrict__ rowptr,
                                                      const int32_t* __restrict__ loc,
                                                      const int64_t* __restrict__ locptr,
-                                                     const double* __restrict__ vals, double* __restrict__ arena,
+                                                     const double* __restrict__ x0, double* __restrict__ arena,
                                                      double* __restrict__ slots, StepCtl ctl) {
   const ColBlock b = blocks[blockIdx.x];
   const PartDesc p = parts[b.part];
   const int lane = threadIdx.x & 31;
   const int j = b.j0 + (threadIdx.x >> 5);
   const int32_t* S = Sall + p.soff;
-  const double emax = ctl.st->eps_max, emin = ctl.st->eps_min;
-  const double den = emax - emin;
   double tr = 0.0;
   // columns [s, ld) are zero padding: the squares read it up to the tile edge, and the
   // emulated steps up to ld (their K slices are packed within 128-blocks)
@@ -140,7 +159,7 @@ __global__ void __launch_bounds__(256) gather_kernel(const PartDesc* __restrict_
         const int a = lj[t];
         const int64_t q = q0 + t;
         if (a >= 0) {
-          const double x = (a == j) ? (emax - vals[q]) / den : (0.0 - vals[q]) / den;
+          const double x = x0[q];
           col[a] = x;
           if (a == j && j < p.c) tr = x;
         }
@@ -464,10 +483,16 @@ cudaError_t launch_bounds(int64_t n, const int64_t* rowptr, const int32_t* colin
 }
 
 cudaError_t launch_gather(const PartDesc* parts, const ColBlock* blocks, int nblocks, const int32_t* Sall,
-                          const int64_t* rowptr, const int32_t* loc, const int64_t* locptr, const double* vals,
+                          const int64_t* rowptr, const int32_t* loc, const int64_t* locptr, const double* x0,
                           double* arena, double* slots, const StepCtl& ctl, cudaStream_t s) {
-  gather_kernel<<<nblocks, 32 * COLS_PER_BLOCK, 0, s>>>(parts, blocks, Sall, rowptr, loc, locptr, vals, arena,
+  gather_kernel<<<nblocks, 32 * COLS_PER_BLOCK, 0, s>>>(parts, blocks, Sall, rowptr, loc, locptr, x0, arena,
                                                        slots, ctl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_x0_values(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* vals,
+                             const DevState* st, double* x0, int nsm, cudaStream_t s) {
+  x0_values_kernel<<<8 * nsm, 256, 0, s>>>(n, rowptr, colind, vals, st, x0);
   return cudaGetLastError();
 }
 

@@ -110,7 +110,8 @@ __global__ void __launch_bounds__(256) oz_convert_slice_kernel(const PartDesc* _
 // Gather of the emulated path: Eq. 1 and the digits of X0 in one pass.  One warp per column
 // j < ld assembles the rows of column j of X0 on or above its diagonal block, the only ones
 // the emulated steps read (zeros, then the stored entries of row S_j of H that fall there,
-// at the local indices of the plan's table (locate_kernel), each stored in the 64-bit
+// at the local indices of the plan's table (locate_kernel), with the values of Eq. 1 from
+// x0_values_kernel, each stored in the 64-bit
 // fixed point x 2^56 of the emulated steps' master), then reads them back from L1/L2 and
 // writes their digits, coalesced (rows outside the part are zero).  Blocks store
 // the core-diagonal sum of their columns; the last block forms T_0 and takes the first
@@ -118,7 +119,7 @@ __global__ void __launch_bounds__(256) oz_convert_slice_kernel(const PartDesc* _
 __global__ void __launch_bounds__(32 * COLS_PER_BLOCK) oz_gather_kernel(
     const PartDesc* __restrict__ parts, const ColBlock* __restrict__ blocks, const int32_t* __restrict__ Sall,
     const int64_t* __restrict__ rowptr, const int32_t* __restrict__ loc, const int64_t* __restrict__ locptr,
-    const double* __restrict__ vals, double* __restrict__ arena, OzSlices dig, double* __restrict__ slots,
+    const double* __restrict__ x0, double* __restrict__ arena, OzSlices dig, double* __restrict__ slots,
     StepCtl ctl) {
   const ColBlock b = blocks[blockIdx.x];
   const PartDesc p = parts[b.part];
@@ -126,8 +127,6 @@ __global__ void __launch_bounds__(32 * COLS_PER_BLOCK) oz_gather_kernel(
   const int j = b.j0 + w;
   const int32_t* S = Sall + p.soff;
   long long* col = reinterpret_cast<long long*>(arena) + p.off + (int64_t)j * p.ld;
-  const double emax = ctl.st->eps_max, emin = ctl.st->eps_min;
-  const double den = emax - emin;
   double tr = 0.0;
   if (j < p.ld) {
     const int rend = min(p.ld, (j / 128 + 1) * 128);
@@ -141,7 +140,7 @@ __global__ void __launch_bounds__(32 * COLS_PER_BLOCK) oz_gather_kernel(
         const int a = lj[t];
         const int64_t q = q0 + t;
         if (a >= 0 && a < rend) {
-          const double x = (a == j) ? (emax - vals[q]) / den : (0.0 - vals[q]) / den;
+          const double x = x0[q];
           col[a] = to_fixed(x);
           if (a == j && j < p.c) tr = x;
         }
@@ -970,9 +969,9 @@ cudaError_t launch_oz_step(const OzStepArgs& a, int grid, cudaStream_t s, bool a
 }
 
 cudaError_t launch_oz_gather(const PartDesc* parts, const ColBlock* blocks, int nblocks, const int32_t* Sall,
-                             const int64_t* rowptr, const int32_t* loc, const int64_t* locptr, const double* vals,
+                             const int64_t* rowptr, const int32_t* loc, const int64_t* locptr, const double* x0,
                              double* arena, const OzSlices& dig, double* slots, const StepCtl& ctl, cudaStream_t s) {
-  oz_gather_kernel<<<nblocks, 32 * COLS_PER_BLOCK, 0, s>>>(parts, blocks, Sall, rowptr, loc, locptr, vals, arena, dig,
+  oz_gather_kernel<<<nblocks, 32 * COLS_PER_BLOCK, 0, s>>>(parts, blocks, Sall, rowptr, loc, locptr, x0, arena, dig,
                                                             slots, ctl);
   return cudaGetLastError();
 }

@@ -1224,7 +1224,7 @@ __global__ void __launch_bounds__(256) gather_lp_kernel(const PartDesc* __restri
                                                         const int64_t* __restrict__ rowptr,
                                                         const int32_t* __restrict__ loc,
                                                         const int64_t* __restrict__ locptr,
-                                                        const double* __restrict__ vals, float* __restrict__ master,
+                                                        const double* __restrict__ x0, float* __restrict__ master,
                                                         void* op_hi, void* op_lo, double* __restrict__ slots,
                                                         StepCtl ctl, int upper_rows) {
   const ColBlock b = blocks[blockIdx.x];
@@ -1232,8 +1232,6 @@ __global__ void __launch_bounds__(256) gather_lp_kernel(const PartDesc* __restri
   const int lane = threadIdx.x & 31;
   const int j = b.j0 + (threadIdx.x >> 5);
   const int32_t* S = Sall + p.soff;
-  const double emax = ctl.st->eps_max, emin = ctl.st->eps_min;
-  const double den = emax - emin;
   double tr = 0.0;
   if (j < p.ld) {
     const int64_t cbase = p.off + (int64_t)j * p.ld;
@@ -1249,7 +1247,7 @@ __global__ void __launch_bounds__(256) gather_lp_kernel(const PartDesc* __restri
         const int a = lj[t];
         const int64_t q = q0 + t;
         if (a >= 0 && a < rend) {
-          const double x = (a == j) ? (emax - vals[q]) / den : (0.0 - vals[q]) / den;
+          const double x = x0[q];
           const float xf = (float)x;
           col[a] = xf;
           if (a == j && j < p.c) tr = (double)xf;
@@ -1278,26 +1276,26 @@ __global__ void __launch_bounds__(256) gather_lp_kernel(const PartDesc* __restri
 
 cudaError_t launch_gather_lp(int kind, int nprod, const PartDesc* parts, const ColBlock* blocks, int nblocks,
                              const int32_t* Sall, const int64_t* rowptr, const int32_t* loc, const int64_t* locptr,
-                             const double* vals, float* master, void* op_hi, void* op_lo, double* slots,
+                             const double* x0, float* master, void* op_hi, void* op_lo, double* slots,
                              const StepCtl& ctl, cudaStream_t s, int upper_rows) {
   const dim3 g(nblocks), b(32 * COLS_PER_BLOCK);
   if (kind < 0)
-    gather_lp_kernel<-1, 1><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, loc, locptr, vals, master, op_hi, op_lo,
+    gather_lp_kernel<-1, 1><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, loc, locptr, x0, master, op_hi, op_lo,
                                             slots, ctl, upper_rows);
   else if (kind == 0 && nprod == 1)
-    gather_lp_kernel<0, 1><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, loc, locptr, vals, master, op_hi, op_lo,
+    gather_lp_kernel<0, 1><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, loc, locptr, x0, master, op_hi, op_lo,
                                            slots, ctl, upper_rows);
   else if (kind == 0 && nprod == 3)
-    gather_lp_kernel<0, 3><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, loc, locptr, vals, master, op_hi, op_lo,
+    gather_lp_kernel<0, 3><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, loc, locptr, x0, master, op_hi, op_lo,
                                            slots, ctl, upper_rows);
   else if (kind == 1 && nprod == 1)
-    gather_lp_kernel<1, 1><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, loc, locptr, vals, master, op_hi, op_lo,
+    gather_lp_kernel<1, 1><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, loc, locptr, x0, master, op_hi, op_lo,
                                            slots, ctl, upper_rows);
   else if (kind == 1 && nprod == 3)
-    gather_lp_kernel<1, 3><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, loc, locptr, vals, master, op_hi, op_lo,
+    gather_lp_kernel<1, 3><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, loc, locptr, x0, master, op_hi, op_lo,
                                            slots, ctl, upper_rows);
   else if (kind == 2 && nprod == 3)
-    gather_lp_kernel<2, 3><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, loc, locptr, vals, master, op_hi, op_lo,
+    gather_lp_kernel<2, 3><<<g, b, 0, s>>>(parts, blocks, Sall, rowptr, loc, locptr, x0, master, op_hi, op_lo,
                                            slots, ctl, upper_rows);
   else
     return cudaErrorInvalidValue;
