@@ -5,21 +5,26 @@
 // Rump, 2012).  With T = OZ_SLICES digits:
 //
 //   every entry of X (|x| <= 1: the spectrum of X stays in [0, 1]) is written in base 2^7
-//   with rounded signed digits, x = sum_{t<T} S_t 2^{-7(t+1)} + r, |S_0| <= 2^7 + 1,
+//   with rounded signed digits, x = sum_{t<T} S_t 2^{-7(t+1)} + r, |S_0| <= 2^7 |x| + 1,
 //   |S_t| <= 2^6 (t >= 1), |r| <= 2^{-7T-1} (+ 2^-57 from the fixed point); every S_t is an
-//   integer exact in BF16;
+//   integer of at most 8 bits, stored in BF16 as S_t 2^{-7t} (still exact) so that the
+//   product of digits a and b carries the factor 2^{-7(a+b)} of its group;
 //
 //   X X = sum_{d<T} 2^{-7(d+2)} G_d + (terms below 2^{-7(T+2)}), G_d = sum_{a+b=d} S_a S_b.
 //
-// Each G_d is a sum of integer products accumulated in FP32 in TMEM.  Because ||X||_2 <= 1,
-// sum_k |x_ik x_kj| <= 1, which keeps the leading groups (d <= 4) below 2^24 at the sizes
-// here, so they are exact; later groups carry a rounding of 2^-24 relative on a value
-// scaled by 2^{-49} or less.  The groups are added as integers into a 64-bit fixed-point
-// accumulator (resolution 2^-56), and a final elementwise pass forms X_new = Y or 2X - Y on
-// that grid (the master copy of the iterate stays in this fixed point), the core traces in
-// FP64, and the digits of X_new for the next step by integer arithmetic.  With T = 7 (28 BF16 products per tile) the digits
-// hold x to 2^-49 and the dropped products are of order 2^-63 K 2^12; the error of Y is
-// about 1e-13, far below the 1e-10 parity of the FP64 path.
+// Each 2^{-7d} G_d is a sum of such products accumulated in FP32 in TMEM.  Because
+// ||X||_2 <= 1, sum_k |x_ik x_kj| <= 1, which keeps the leading groups (d <= 4) below 2^24
+// (in units of their own scale) at the sizes here, so they are exact; later groups carry a
+// rounding of 2^-24 relative on a value scaled by 2^{-49} or less.  G_0 and G_1 share one
+// accumulator, G_0 + 2^-7 G_1: its terms are multiples of 2^-7 whose magnitudes sum to at
+// most 2^14 + 3 2^7 (sum_k |x_ik| + |x_kj|) / 2 + 2 K (with sum_k |x_ik| <= sqrt(K)), below
+// 2^16 for K <= 4096, so it is exact as well.  The groups are added as integers into a
+// 64-bit fixed-point accumulator (resolution 2^-56), and a final elementwise pass forms
+// X_new = Y or 2X - Y on that grid (the master copy of the iterate stays in this fixed
+// point), the core traces in FP64, and the digits of X_new for the next step by integer
+// arithmetic.  With T = 7 (28 BF16 products per tile) the digits hold x to 2^-49 and the
+// dropped products are of order 2^-63 K 2^12; the error of Y is about 1e-13, far below the
+// 1e-10 parity of the FP64 path.
 //
 // The adjoint step Xbar <- Xbar X + X Xbar (or 2 Xbar minus that) runs on the same
 // machinery: an upper tile (I, J) of Xbar X + X Xbar is one product over K = 2s, rows I of
@@ -43,9 +48,12 @@ namespace gsp2 {
 // the rest in S_0 (|S_0| <= 2^7 + 1 for |x| <= 1), w = sum_t S_t 2^{7(T-1-t)} exactly.
 // The balanced digits of w are the plain base-2^7 digits of w + 64 (1 + 2^7 + ... +
 // 2^{7(T-2)}) less 64, so each is one shift-and-mask; the small integer becomes exact BF16
-// bits through the FP32 magic-number form (2^23 + u, then subtracting 2^23 + 64 is exact).
-// Returned are the FP32 bit patterns whose upper halves are the BF16 digits (digit t
-// weighs 2^{-7(t+1)}).
+// bits through the FP32 magic-number form.  Digit t is stored as S_t 2^{-7t} (exact: a
+// power-of-two scale of an integer of at most 8 bits): the float 2^{23-7t} + u 2^{-7t}
+// less (2^23 + 64) 2^{-7t}, one OR and one exact subtraction, so that the product of digits
+// a and b lands at 2^{-7(a+b)} and groups can share an accumulator at their own scale.
+// Returned are the FP32 bit patterns whose upper halves are the BF16 digits (S_t weighs
+// 2^{-7(t+1)} in x, so every stored digit S_t 2^{-7t} weighs 2^-7).
 __device__ __forceinline__ void digit_words(long long v, uint32_t (&fw)[OZ_SLICES]) {
   constexpr int drop = 56 - 7 * OZ_SLICES;
   constexpr long long bias = 64ll * (((1ll << (7 * (OZ_SLICES - 1))) - 1) / 127);
@@ -53,7 +61,8 @@ __device__ __forceinline__ void digit_words(long long v, uint32_t (&fw)[OZ_SLICE
 #pragma unroll
   for (int t = OZ_SLICES - 1; t >= 1; --t) {
     const uint32_t u = (uint32_t)(w >> (7 * (OZ_SLICES - 1 - t))) & 127u;
-    fw[t] = __float_as_uint(__fsub_rn(__uint_as_float(0x4B000000u | u), 8388672.0f));  // 2^23 + 64
+    const uint32_t e = (uint32_t)(150 - 7 * t) << 23;  // exponent field of 2^{23-7t}
+    fw[t] = __float_as_uint(__fsub_rn(__uint_as_float(e | u), __uint_as_float(e | 64u)));  // (2^23 + 64) 2^{-7t}
   }
   const int s0 = (int)(w >> (7 * (OZ_SLICES - 1)));  // |s0| < 256
   fw[0] = __float_as_uint(__fsub_rn(__uint_as_float(0x4B000000u | (uint32_t)(s0 + 256)), 8388864.0f));
@@ -288,20 +297,20 @@ __global__ void __launch_bounds__(256) oz_digits_kernel(const PartDesc* __restri
 // per SM walks the upper 128x128 tiles: blockIdx.x, then the ones it claims from a counter,
 // or blockIdx.x + gridDim.x, ... in the static deal).
 //
-// The T(T+1)/2 digit products of a tile need one FP32 accumulator per group d = a + b
-// (T x 128 TMEM columns), more than the 512 columns of an SM, so a tile takes two passes
-// over K: first the high groups d >= OZ_SPLIT (all seven digits; 22 of the 28 products),
-// then the low groups d < OZ_SPLIT (digits below OZ_SPLIT).  A stage of the TMA ring holds
-// one K = OZ_BK slice of
-// every digit the pass needs, for rows I (A) and rows J (B; diagonal tiles reuse A), so each
+// The T(T+1)/2 digit products of a tile need an FP32 accumulator per group d = a + b
+// (128 TMEM columns each; G_0 and G_1 share one), more than the 512 columns of an SM, so a
+// tile takes two passes over K: first the high groups d >= OZ_SPLIT (all seven digits; 22
+// of the 28 products, columns 0-511), then the low groups d < OZ_SPLIT (digits below
+// OZ_SPLIT, columns 0-255).  A stage of the TMA ring holds one K = OZ_BK slice of every
+// digit the pass needs, for rows I (A) and rows J (B; diagonal tiles reuse A), so each
 // distinct digit tile is loaded once per slice and feeds all its products (one K = 16 BF16
-// MMA each).  The epilogue warps turn the high groups' integer-valued sums into 64-bit
-// fixed point (2^-56) and park them in a per-CTA scratch tile (L2-resident), which frees
-// the columns for the low pass; after the low pass they add the low groups, form
-// X_new = Y or 2X - Y, write the master copy (64-bit fixed point) and the digits of X_new
-// (into the other digit buffer) at (I, J) and mirrored at (J, I) (diagonal tiles from their
-// upper triangle),
-// and add the core traces, while the MMAs of the next tile's high pass run.  The new
+// MMA each).  The epilogue warps turn the high groups' sums into 64-bit fixed point (2^-56)
+// and park them in TMEM columns 256-511, which the low pass leaves alone; after the low
+// pass they add the low groups, hand all 512 columns back and keep the tile's sums in a
+// per-CTA scratch tile (L2-resident) for the final pass, which forms X_new = Y or 2X - Y,
+// writes the master copy (64-bit fixed point) and the digits of X_new (into the other
+// digit buffer) at (I, J) and mirrored at (J, I) (diagonal tiles from their upper
+// triangle), and adds the core traces, while the MMAs of the next tile's high pass run.  The new
 // iterate is written with evict-first stores: the next step reads it after this launch,
 // and keeping it out of L2 leaves room for the digit panels the running tiles share.  The last block
 // runs the step bookkeeping.
@@ -336,8 +345,13 @@ __host__ __device__ constexpr int oz_tile_cols(int s, int tj) {
   return s - tj * 128 >= 128 ? 128 : ((s - tj * 128 + 15) & ~15);
 }
 
-__device__ __forceinline__ uint32_t oz_group_col(int d) {
-  return (uint32_t)(d >= OZ_SPLIT ? 128 * (d - OZ_SPLIT + 4 - (OZ_SLICES - OZ_SPLIT)) : 128 * d);
+// Accumulator of group d: the high pass's four groups in columns 0-511; the low pass's
+// G_0 + 2^-7 G_1 in columns 0-127 and G_2 in 128-255, which leaves 256-511 to the high
+// pass's 64-bit sums (low and high words) until the low pass is drained.
+static_assert(OZ_SPLIT == 3 && OZ_SLICES - OZ_SPLIT == 4, "the TMEM plan of the emulated step");
+constexpr uint32_t OZ_PARK_LO = 256, OZ_PARK_HI = 384;
+__host__ __device__ constexpr uint32_t oz_group_col(int d) {
+  return (uint32_t)(d >= OZ_SPLIT ? 128 * (d - OZ_SPLIT) : (d <= 1 ? 0 : 128));
 }
 
 // The MMAs of one stage for the groups d0 <= d < d1, fully unrolled: every pair (q, d - q)
@@ -347,7 +361,8 @@ __device__ __forceinline__ uint32_t oz_group_col(int d) {
 // A digit q (one per group d >= q) follow one another and share their A operand through the
 // collector buffer, so each A digit tile is read from shared memory once per K = 16 slice
 // instead of once per product (the MMAs' shared-memory reads, A and B, set the pace of the
-// tensor pipe otherwise).  Every accumulator's first product is the one with q = 0.
+// tensor pipe otherwise).  Every accumulator's first product is the one with q = 0 (for the
+// shared G_0 + 2^-7 G_1, the product (0, 0)).
 template <int D0, int D1>
 __device__ __forceinline__ void oz_issue_stage(uint32_t tmem, uint64_t da, uint64_t db, uint32_t adv_a,
                                                uint32_t adv_b, uint32_t idesc, bool first_k) {
@@ -360,48 +375,65 @@ __device__ __forceinline__ void oz_issue_stage(uint32_t tmem, uint64_t da, uint6
 #pragma unroll
       for (int d = dlo; d < D1; ++d) {
         const int op = (D1 - dlo == 1) ? 0 : (d == dlo ? 1 : (d == D1 - 1 ? 3 : 2));
+        // the first product into each accumulator is (0, d) of its lowest group
+        const bool opens = q == 0 && !(D0 == 0 && d == 1);
         mma_f16_col(op, tmem + oz_group_col(d), da + (uint64_t)q * step + (uint64_t)(adv_a * kk),
                     db + (uint64_t)(d - q) * step + (uint64_t)(adv_b * kk), idesc,
-                    (q > 0 || kk > 0 || !first_k) ? 1u : 0u);
+                    (!opens || kk > 0 || !first_k) ? 1u : 0u);
       }
     }
   }
 }
 
-// z[j] += g_d[j] 2^(56 - 7 (d + 2)) for the groups D0 <= d < D1 of one 16-column chunk: the
-// group sums g_d (integers, held exactly in FP32) in units of 2^-56.  A chunk whose sums all
-// lie below 2^22 in magnitude is converted without the conversion unit: g + 1.5 2^23 is a
-// float in [2^23, 2^24) whose bit pattern is 0x4B400000 + g, and a 32 x 32 -> 64-bit
-// multiply-add (by the power of two, or on the upper word for weights of 2^32 and more)
-// accumulates it; any other chunk goes through the exact rounding conversion (|g| < 2^31).
-template <int D0, int D1>
-__device__ __forceinline__ void oz_drain_groups(uint32_t taddr, long long (&z)[16]) {
+// z[j] += u[j] 2^SHIFT for one accumulator of one 16-column chunk, where u = v 2^M is the
+// integer its FP32 sums v hold at the scale 2^-M: the groups d >= 3 alone (M = 7 d, SHIFT =
+// 56 - 7 (d + 2)), G_2 (M = 14, SHIFT = 28), G_0 + 2^-7 G_1 (M = 7, SHIFT = 35: u = 2^7 G_0 +
+// G_1).  A chunk whose integers all lie below 2^22 in magnitude is converted without the
+// conversion unit: v + 1.5 2^(23 - M) is a float in [2^(23 - M), 2^(24 - M)) with spacing 2^-M,
+// whose bit pattern less that of 1.5 2^(23 - M) is u, and a 32 x 32 -> 64-bit multiply-add
+// (by the power of two, or on the upper word for shifts of 32 and more) accumulates it; any
+// other chunk goes through the exact rounding conversion of v 2^M (|u| < 2^31).
+template <int M, int SHIFT>
+__device__ __forceinline__ void oz_drain_slot(uint32_t taddr, long long (&z)[16]) {
+  uint32_t v[16];
+  tmem_ld16(taddr, v);
+  const float magic = __uint_as_float(((uint32_t)(150 - M) << 23) | 0x400000u);  // 1.5 2^(23 - M)
+  const float lim = __uint_as_float((uint32_t)(149 - M) << 23);                   // 2^(22 - M)
+  float mx = 0.0f;
 #pragma unroll
-  for (int d = D0; d < D1; ++d) {
-    uint32_t v[16];
-    tmem_ld16(taddr + oz_group_col(d), v);
-    const int shift = 56 - 7 * (d + 2);  // group weight 2^{-7(d+2)} in units of 2^-56
-    float mx = 0.0f;
+  for (int j = 0; j < 16; ++j) mx = fmaxf(mx, fabsf(__uint_as_float(v[j])));
+  if (__all_sync(0xffffffffu, mx < lim)) {
 #pragma unroll
-    for (int j = 0; j < 16; ++j) mx = fmaxf(mx, fabsf(__uint_as_float(v[j])));
-    if (__all_sync(0xffffffffu, mx < 4194304.0f)) {
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int32_t g = (int32_t)(__float_as_uint(__fadd_rn(__uint_as_float(v[j]), 12582912.0f)) - 0x4B400000u);
-        if (shift < 32) {
-          asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(z[j]) : "r"(g), "r"(1 << (shift & 31)));
-        } else {
-          z[j] += (long long)((unsigned long long)((uint32_t)g << (shift - 32)) << 32);
-        }
-      }
-    } else {
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const long long g = (long long)__float2int_rn(__uint_as_float(v[j]));
-        z[j] += (long long)((unsigned long long)g << shift);
+    for (int j = 0; j < 16; ++j) {
+      const int32_t g = (int32_t)(__float_as_uint(__fadd_rn(__uint_as_float(v[j]), magic)) - __float_as_uint(magic));
+      if constexpr (SHIFT < 32) {
+        asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(z[j]) : "r"(g), "r"(1 << SHIFT));
+      } else {
+        z[j] += (long long)((unsigned long long)((uint32_t)g << (SHIFT - 32)) << 32);
       }
     }
+  } else {
+    const float scale = __uint_as_float((uint32_t)(127 + M) << 23);  // 2^M
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const long long g = (long long)__float2int_rn(__fmul_rn(__uint_as_float(v[j]), scale));
+      z[j] += (long long)((unsigned long long)g << SHIFT);
+    }
   }
+}
+
+// The high pass of one chunk: the sums of groups 3-6 (columns 0-511) into z.
+__device__ __forceinline__ void oz_drain_high(uint32_t taddr, long long (&z)[16]) {
+  oz_drain_slot<21, 21>(taddr + oz_group_col(3), z);
+  oz_drain_slot<28, 14>(taddr + oz_group_col(4), z);
+  oz_drain_slot<35, 7>(taddr + oz_group_col(5), z);
+  oz_drain_slot<42, 0>(taddr + oz_group_col(6), z);
+}
+
+// The low pass of one chunk: G_0 + 2^-7 G_1 and G_2 into z.
+__device__ __forceinline__ void oz_drain_low(uint32_t taddr, long long (&z)[16]) {
+  oz_drain_slot<7, 35>(taddr + oz_group_col(0), z);
+  oz_drain_slot<14, 28>(taddr + oz_group_col(2), z);
 }
 
 // |v| 2^-56 as FP32 (integer instructions, truncated: at most 2^-23 below), for the row
@@ -727,9 +759,10 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
       const int cskip = (t.ti == t.tj) ? quarter * 32 : 0;
       double tY = 0.0, tN = 0.0;
       bool ok = true;
-      // the two passes: read the groups' sums (integers held exactly in FP32), add them as
-      // 64-bit integers into the scratch tile (thread-private entries: column cl, row m),
-      // then hand the columns back
+      // the two passes: read the groups' sums (integers at their groups' scales, held
+      // exactly in FP32) and add them as 64-bit integers, parked in TMEM between the passes
+      // and then in the scratch tile (thread-private entries: column cl, row m); each pass
+      // hands its columns back
       for (int pass = 0; pass < 2; ++pass) {
         ok = __all_sync(0xffffffffu, mbar_wait(afull(pass), u & 1, abort_flag)) && ok;
         tc_fence_after();
@@ -737,15 +770,35 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
         for (int cc = 0; cc < 2 && ok; ++cc) {
           const int cl = colq * 32 + cc * 16;
           if (cl >= ncols || cl + 16 <= cskip) continue;
+          const uint32_t tc = tmem + lane_off + (uint32_t)cl;
           long long z[16];
-          long long* zp = acc + (size_t)cl * 128 + m;
+          uint32_t w[16];
+          if (pass == 0) {
+            // the high groups' sum waits in the columns this warp has just drained (its own
+            // columns of groups 5 and 6), which the low pass leaves alone
 #pragma unroll
-          for (int j = 0; j < 16; ++j) z[j] = pass == 0 ? 0ll : zp[(size_t)j * 128];
-          if (pass == 0) oz_drain_groups<OZ_SPLIT, T>(tmem + lane_off + (uint32_t)cl, z);
-          else oz_drain_groups<0, OZ_SPLIT>(tmem + lane_off + (uint32_t)cl, z);
+            for (int j = 0; j < 16; ++j) z[j] = 0ll;
+            oz_drain_high(tc, z);
 #pragma unroll
-          for (int j = 0; j < 16; ++j) zp[(size_t)j * 128] = z[j];
+            for (int j = 0; j < 16; ++j) w[j] = (uint32_t)(unsigned long long)z[j];
+            tmem_st16(tc + OZ_PARK_LO, w);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) w[j] = (uint32_t)((unsigned long long)z[j] >> 32);
+            tmem_st16(tc + OZ_PARK_HI, w);
+          } else {
+            tmem_ld16(tc + OZ_PARK_LO, w);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) z[j] = (long long)(unsigned long long)w[j];
+            tmem_ld16(tc + OZ_PARK_HI, w);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) z[j] += (long long)((unsigned long long)w[j] << 32);
+            oz_drain_low(tc, z);
+            long long* zp = acc + (size_t)cl * 128 + m;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) zp[(size_t)j * 128] = z[j];
+          }
         }
+        if (pass == 0) tmem_wait_st();
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(aempty(pass));
