@@ -345,13 +345,14 @@ __host__ __device__ constexpr int oz_tile_cols(int s, int tj) {
   return s - tj * 128 >= 128 ? 128 : ((s - tj * 128 + 15) & ~15);
 }
 
-// Accumulator of group d: the high pass's four groups in columns 0-511; the low pass's
-// G_0 + 2^-7 G_1 in columns 0-127 and G_2 in 128-255, which leaves 256-511 to the high
-// pass's 64-bit sums (low and high words) until the low pass is drained.
+// Accumulator of group d: the high pass's groups 5, 6, 3, 4 in columns 0-127, 128-255,
+// 256-383, 384-511; the low pass's G_0 + 2^-7 G_1 in columns 0-127 and G_2 in 128-255, so the
+// low pass can start once groups 5 and 6 are read, and columns 256-511 hold the high pass's
+// 64-bit sums (low and high words) until the low pass is drained.
 static_assert(OZ_SPLIT == 3 && OZ_SLICES - OZ_SPLIT == 4, "the TMEM plan of the emulated step");
 constexpr uint32_t OZ_PARK_LO = 256, OZ_PARK_HI = 384;
 __host__ __device__ constexpr uint32_t oz_group_col(int d) {
-  return (uint32_t)(d >= OZ_SPLIT ? 128 * (d - OZ_SPLIT) : (d <= 1 ? 0 : 128));
+  return (uint32_t)(d >= OZ_SPLIT ? (d >= 5 ? 128 * (d - 5) : 256 + 128 * (d - 3)) : (d <= 1 ? 0 : 128));
 }
 
 // The MMAs of one stage for the groups d0 <= d < d1, fully unrolled: every pair (q, d - q)
@@ -422,12 +423,15 @@ __device__ __forceinline__ void oz_drain_slot(uint32_t taddr, long long (&z)[16]
   }
 }
 
-// The high pass of one chunk: the sums of groups 3-6 (columns 0-511) into z.
-__device__ __forceinline__ void oz_drain_high(uint32_t taddr, long long (&z)[16]) {
-  oz_drain_slot<21, 21>(taddr + oz_group_col(3), z);
-  oz_drain_slot<28, 14>(taddr + oz_group_col(4), z);
+// The high pass of one chunk, in two halves: groups 5 and 6 (the columns the low pass
+// reuses), then groups 3 and 4 (the columns that then hold the sums), into z.
+__device__ __forceinline__ void oz_drain_high56(uint32_t taddr, long long (&z)[16]) {
   oz_drain_slot<35, 7>(taddr + oz_group_col(5), z);
   oz_drain_slot<42, 0>(taddr + oz_group_col(6), z);
+}
+__device__ __forceinline__ void oz_drain_high34(uint32_t taddr, long long (&z)[16]) {
+  oz_drain_slot<21, 21>(taddr + oz_group_col(3), z);
+  oz_drain_slot<28, 14>(taddr + oz_group_col(4), z);
 }
 
 // The low pass of one chunk: G_0 + 2^-7 G_1 and G_2 into z.
@@ -766,6 +770,12 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
       for (int pass = 0; pass < 2; ++pass) {
         ok = __all_sync(0xffffffffu, mbar_wait(afull(pass), u & 1, abort_flag)) && ok;
         tc_fence_after();
+        // the high pass hands its columns back as soon as the warp's last chunk has read
+        // groups 5 and 6, which the low pass reuses (-1: no chunk, hand back at the end)
+        const int clast = (colq * 32 + 16 < ncols && colq * 32 + 32 > cskip) ? 1
+                          : (colq * 32 < ncols && colq * 32 + 16 > cskip)   ? 0
+                                                                            : -1;
+        bool released = false;
 #pragma unroll 1
         for (int cc = 0; cc < 2 && ok; ++cc) {
           const int cl = colq * 32 + cc * 16;
@@ -775,10 +785,17 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
           uint32_t w[16];
           if (pass == 0) {
             // the high groups' sum waits in the columns this warp has just drained (its own
-            // columns of groups 5 and 6), which the low pass leaves alone
+            // columns of groups 3 and 4), which the low pass leaves alone
 #pragma unroll
             for (int j = 0; j < 16; ++j) z[j] = 0ll;
-            oz_drain_high(tc, z);
+            oz_drain_high56(tc, z);
+            if (cc == clast) {
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(aempty(0));
+              released = true;
+            }
+            oz_drain_high34(tc, z);
 #pragma unroll
             for (int j = 0; j < 16; ++j) w[j] = (uint32_t)(unsigned long long)z[j];
             tmem_st16(tc + OZ_PARK_LO, w);
@@ -799,9 +816,11 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) oz_step_kernel(OzStepArgs a) {
           }
         }
         if (pass == 0) tmem_wait_st();
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(aempty(pass));
+        if (!released) {
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(aempty(pass));
+        }
       }
       if (!ok) *s_err = 1;
       // split K: the first half to finish leaves its partial; the second adds the first's
