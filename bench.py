@@ -35,7 +35,7 @@ NOMINAL = {"bf16": 2250.0, "tf32": 1100.0, "fp64": 1.25}
 # scaled to tb30k by arena elements; an entry is dropped when its kernel changes, and the
 # line then reports null
 TB8K_TO_TB30K = 191545344 / 38469632
-TRAFFIC = {("tb30k", "fp64"): 0.5270e9 * TB8K_TO_TB30K, ("tb30k", "fp64e"): 1.0486e9 * TB8K_TO_TB30K,
+TRAFFIC = {("tb30k", "fp64"): 0.5270e9 * TB8K_TO_TB30K, ("tb30k", "fp64e"): 1.0497e9 * TB8K_TO_TB30K,
            ("tb30k", "fp16x3"): 0.2712e9 * TB8K_TO_TB30K, ("tb30k", "tf32x3"): 0.7313e9 * TB8K_TO_TB30K}
 
 
