@@ -68,7 +68,7 @@ typedef enum {
   GSP2_PREC_TF32X3 = 5, /* split operands hi+lo in TF32, three products, FP32 accumulate */
   GSP2_PREC_FP64_EMU = 6, /* FP64 results; every product X X rebuilt from 7 base-2^7 digits of X
                              held in BF16 (28 exact BF16 tensor-core products per tile, groups
-                             summed as 64-bit fixed point), FP64 master copy and epilogue */
+                             summed as 64-bit fixed point), master copy in that fixed point */
   GSP2_PREC_FP16X3 = 7  /* split operands hi+lo in FP16 of X 2^14 (22 bits like TF32X3, entries
                            down to 2^-28 in FP16's normal range), three products at the
                            16-bit tensor rate, FP32 accumulate, sums scaled back by 2^-28 */
