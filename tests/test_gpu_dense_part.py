@@ -22,7 +22,7 @@ from synth import TBSystem, csr_from_dense, dense_from_csr, random_symmetric_on_
 
 pytestmark = pytest.mark.gpu
 
-N = 1536  # K = 1536 forward, 3072 in the adjoint's products
+N = 2048  # K = 2048 forward, 4096 (the limit of the exactness bounds) in the adjoint
 
 
 @pytest.fixture(scope="module")
@@ -48,7 +48,7 @@ def dense():
     rowptr, colind, vals = csr_from_dense(H)
     assert rowptr[-1] == N * N
     # one part holding every orbital: no halo, so the dependency graph can stay empty
-    return TBSystem(name="dense1536", n_sites=N // 4, n=N, nocc=nocc, rowptr=rowptr, colind=colind, vals=vals,
+    return TBSystem(name="dense2048", n_sites=N // 4, n=N, nocc=nocc, rowptr=rowptr, colind=colind, vals=vals,
                     coords=np.zeros((N // 4, 3)), part=np.zeros(N, dtype=np.int32), nparts=1,
                     g_rowptr=np.zeros(N + 1, dtype=np.int64), g_colind=np.zeros(0, dtype=np.int32))
 
