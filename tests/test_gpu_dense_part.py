@@ -10,7 +10,7 @@ run the paper's G-SP2 (Section 2.1) on the single part; the oracle runs its own 
 branch sequence.  Once X is idempotent to rounding its trace equals N_occ to the last bit
 (the oracle's last two traces differ from N_occ by exactly 0.0), so the branch rule takes
 either side there and the stopping test, which asks whether the idempotency error still
-falls, may end one step apart: the branches are compared where the trace is more than
+falls, may end a step or two apart: the branches are compared where the trace is more than
 1e-9 from N_occ (the GPU's traces carry about 1e-12), P against the oracle's own run and
 against the oracle replaying the GPU's sequence."""
 
