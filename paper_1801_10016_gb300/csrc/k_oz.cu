@@ -13,9 +13,11 @@
 //   X X = sum_{d<T} 2^{-7(d+2)} G_d + (terms below 2^{-7(T+2)}), G_d = sum_{a+b=d} S_a S_b.
 //
 // Each 2^{-7d} G_d is a sum of such products accumulated in FP32 in TMEM.  Because
-// ||X||_2 <= 1, sum_k |x_ik x_kj| <= 1, which keeps the leading groups (d <= 4) below 2^24
-// (in units of their own scale) at the sizes here, so they are exact; later groups carry a
-// rounding of 2^-24 relative on a value scaled by 2^{-49} or less.  G_0 and G_1 share one
+// ||X||_2 <= 1, sum_k |x_ik x_kj| <= 1 bounds G_0; the groups up to d = 4 add products of
+// lower digits, which behave like independent values except on the diagonal (sums of
+// squares, about K 2^10.4), and stay below 2^24 (in units of their own scale) for K up to
+// 4096, so they are exact; later groups carry a rounding of 2^-24 relative on a value
+// scaled by 2^{-49} or less.  G_0 and G_1 share one
 // accumulator, G_0 + 2^-7 G_1: its terms are multiples of 2^-7 whose magnitudes sum to at
 // most 2^14 + 3 2^7 (sum_k |x_ik| + |x_kj|) / 2 + 2 K (with sum_k |x_ik| <= sqrt(K)), below
 // 2^16 for K <= 4096, so it is exact as well.  The groups are added as integers into a
