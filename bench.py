@@ -295,17 +295,17 @@ def step_roofline(precision, sizes, avg_launch_ms, peaks, src, workload, sched=N
             "executed_frac": exe / t / 1e12 / peak}
 
 
-def kernels_per_build(precision, info, lp_tail=0, report_idem=0, emulated_tail=True):
+def kernels_per_build(precision, info, lp_tail=0, emulated_tail=True, upper_steps=True):
     """Kernel launches of one density call (all launched, including the step launches that
     return at once after the stopping test)."""
-    n = 4 + report_idem  # reset, bounds, gather, scatter (+ idempotency report)
-    if precision == "fp64":
-        return n + info.step_launches
-    if precision == "fp64e":
-        return n + info.step_launches  # gather with the digits of X0, then one fused launch per step
+    n = 5  # reset, bounds, Eq. 1 values of the stored entries, gather, scatter
+    if precision in ("fp64", "fp64e"):
+        return n + info.step_launches  # the emulated gather writes the digits of X0 too
     tail = info.fp64_tail_steps
-    # low-precision steps, low-precision tail, conversion, digits of the converted iterate
-    return n + info.step_launches + lp_tail + 1 + (1 if (tail > 0 and emulated_tail) else 0) + tail
+    # the FP64 tail's start: one launch for the conversion and the digits (emulated tail), or
+    # the conversion and, after steps that keep upper tiles only, the mirror of the lower ones
+    start = 1 if emulated_tail else 1 + (1 if (upper_steps and tail > 0) else 0)
+    return n + info.step_launches + lp_tail + start + tail
 
 
 def aggregate(local_seconds, units_per_rank, world, device):
